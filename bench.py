@@ -1,0 +1,343 @@
+"""Benchmark of one time step of the vorticity--stream-vector phase-field
+method (phi update, mu, source, six Poisson solves) on GB300.
+
+Default: N = 1 GPU, the Couette vesicle at 512 x 256 x 256 (x flow axis,
+256 x 256 cross-section, the 256^2 x 512 workload), mixed precision (FP32
+storage and smoothing, exact FP64-class defect, FP64 reductions), beside the
+plain-FP64 step with the same multigrid schedule.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank advances its own replica (the method has no
+exchange step on one GPU per problem); value = all ranks' cell-steps / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Mcell-steps/s at 256^2x512 (mixed FP32/FP64-defect; plain FP64 beside it)"
+UNIT = "Mcell-steps/s"
+ALGO_BYTES_HALF_SWEEP_F32 = 6.0   # bytes per cell per red or black half-sweep (read x-nb, b; write x)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--nx", type=int, default=512)
+    ap.add_argument("--ny", type=int, default=256)
+    ap.add_argument("--nz", type=int, default=256)
+    ap.add_argument("--cycles", type=int, default=2, help="V-cycles per Poisson solve")
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(REASONS, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def make_sim(w, prec, cycles):
+    from paper_2601_05031_gb300 import vsv as V
+    from paper_2601_05031_gb300.sim import Simulation
+    sim = Simulation.from_workload(w, prec)
+    sp = sim.solver_params()
+    sp.fixed_cycles = cycles
+    sp.tol = 1e-7 if prec == V.VSV_MIXED else 1e-12
+    V.vsv_set_solver(sim.g, sp)
+    sim.set_phi(w.phi0)
+    return sim
+
+
+def timed_steps(sim, nsteps, dt, torch, barrier):
+    st = sim.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    sim.step(nsteps, dt)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    import inputs
+    from paper_2601_05031_gb300 import build as B
+    from paper_2601_05031_gb300 import vsv as V
+
+    if rank == 0 or not B.up_to_date():
+        B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = inputs.vesicle_couette_512x256x256(nx=args.nx, ny=args.ny, nz=args.nz)
+    N = w.ncells
+    sim = make_sim(w, V.VSV_MIXED, args.cycles)
+    for _ in range(args.warmup):
+        sim.step(1, w.dt)
+    torch.cuda.synchronize()
+    launches0 = sim.kernel_launches()
+    with ClockSampler(local) as clk:
+        ms = timed_steps(sim, args.steps, w.dt, torch, barrier)
+    launches = sim.kernel_launches() - launches0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N * args.steps / (ms * 1e-3) / 1e6
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded prolate vesicle, V_r 0.9, eps 1.5, Couette +-0.05)",
+        "config": {"workload": w.name, "grid_xyz": [w.nx, w.ny, w.nz], "cells": N,
+                   "precision": "mixed: f32 fields and smoothing, exact (FP64-class) defect, "
+                                "f64 reductions",
+                   "solver": f"multigrid V({w and 2},{2}) red-black GS, {args.cycles} cycles per "
+                             "Poisson solve, 6 solves per step",
+                   "l2": "inputs larger than L2 (about 2 GB of resident fields per replica)",
+                   "dt": w.dt, "parallelism": f"replicas x{ws}"},
+        "gpu_launches": int(launches),
+    }
+    # roofline of the dominant kernel: fine-level red-black half-sweeps, timed
+    # live with events on the library's stream during extra timed steps
+    V.vsv_profile_enable(sim.g, V.VSV_KCLASS_SMOOTH_FINE)
+    nprof = max(2, min(args.steps, 5))
+    timed_steps(sim, nprof, w.dt, torch, barrier)
+    pms, pn = V.vsv_profile_read(sim.g, V.VSV_KCLASS_SMOOTH_FINE)
+    V.vsv_profile_enable(sim.g, V.VSV_KCLASS_SMOOTH_FINE, False)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    per_launch_s = pms * 1e-3 / max(pn, 1)
+    algo = ALGO_BYTES_HALF_SWEEP_F32 * N * 3
+    achieved = algo / per_launch_s / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "k_rb_sweep<float> (finest level, one colour, "
+                       "3 components)", "achieved": round(achieved, 1), "peak": peak,
+                       "unit": "GB/s", "frac": round(achieved / peak, 4),
+                       "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                       "algorithmic_bytes_per_launch": algo, "launches_timed": int(pn),
+                       "avg_launch_us": round(per_launch_s * 1e6, 2),
+                       "traffic": None}
+    out["clocks"] = clk.summary()
+    # plain FP64 step with the same schedule, and the accuracy of mixed vs FP64
+    if not args.no_fp64:
+        k64 = args.fp64_steps or max(3, args.steps // 4)
+        sim64 = make_sim(w, V.VSV_FP64, args.cycles)
+        for _ in range(min(args.warmup, 3)):
+            sim64.step(1, w.dt)
+        ms64 = timed_steps(sim64, k64, w.dt, torch, barrier)
+        v64 = N * k64 / (ms64 * 1e-3) / 1e6
+        # accuracy: fresh mixed and FP64 runs from the same phi0, same steps
+        nacc = 10
+        simA = make_sim(w, V.VSV_MIXED, args.cycles)
+        simB = make_sim(w, V.VSV_FP64, args.cycles)
+        simA.step(nacc, w.dt)
+        simB.step(nacc, w.dt)
+        errs = {}
+        for name, fid in (("phi", V.VSV_FIELD_PHI), ("vel_x", V.VSV_FIELD_VEL_X),
+                          ("vel_y", V.VSV_FIELD_VEL_Y), ("vel_z", V.VSV_FIELD_VEL_Z)):
+            a = simA.field(fid, np.float64, on_device=True)
+            b = simB.field(fid, np.float64, on_device=True)
+            errs[name] = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        va = torch.stack([simA.field(V.VSV_FIELD_VEL_X + c, np.float64, on_device=True) for c in range(3)])
+        vb = torch.stack([simB.field(V.VSV_FIELD_VEL_X + c, np.float64, on_device=True) for c in range(3)])
+        errs["vel"] = float(torch.linalg.vector_norm(va - vb) / torch.linalg.vector_norm(vb))
+        del va, vb
+        simA.close(); simB.close()
+        out["fp64"] = {"value": round(v64, 3), "unit": UNIT, "ms_per_step": round(ms64 / k64, 3),
+                       "steps": k64, "speedup_mixed_over_fp64": round(value / (ws * v64), 3)}
+        out["accuracy_mixed_vs_fp64"] = {"steps": nacc, "rel_l2": errs}
+        sim64.close()
+    # end to end through the C ABI with host buffers: phi in from pinned host
+    # memory, one step, phi out to pinned host memory, every step
+    if not args.no_e2e:
+        host_in = torch.empty((w.nz, w.ny, w.nx), dtype=torch.float32, pin_memory=True)
+        host_out = torch.empty_like(host_in)
+        sim.field(V.VSV_FIELD_PHI, np.float32, on_device=True)
+        host_in.copy_(sim.field(V.VSV_FIELD_PHI, np.float32, on_device=True).cpu())
+        ke = max(2, min(args.steps, 5))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            V.vsv_set_field(sim.g, V.VSV_FIELD_PHI, host_in.data_ptr(), V.VSV_DTYPE_F32, 0)
+            sim.step(1, w.dt)
+            V.vsv_get_field(sim.g, V.VSV_FIELD_PHI, host_out.data_ptr(), V.VSV_DTYPE_F32, 0)
+        te = time.perf_counter() - t0
+        barrier()
+        out["e2e"] = {"value": round(ws * N * ke / te / 1e6, 3), "unit": UNIT,
+                      "h2d_bytes_per_step": N * 4, "d2h_bytes_per_step": N * 4, "steps": ke}
+    sim.close()
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample_workload(nsteps_hint=3):
+    """The same recipe (Couette, V_r 0.9, eps 1.5, seeded axes scaled to the
+    cross-section) at 128 x 64 x 64: 1/64 of the benchmark's cells."""
+    import inputs
+    return inputs.vesicle_couette_512x256x256(nx=128, ny=64, nz=64, nsteps=nsteps_hint)
+
+
+def cpu_baseline(w_full, steps=3):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle
+    ws = oracle_sample_workload(steps)
+    p = oracle.params_from_workload(ws)
+    st = oracle.init_state(p, ws.phi0)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.step(st, ws.dt)
+    t = time.perf_counter() - t0
+    return {"value": round(ws.ncells * steps / t / 1e6, 4), "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"{steps} oracle steps of the same recipe at {ws.nx}x{ws.ny}x{ws.nz} "
+                      f"(1/{w_full.ncells // ws.ncells} of the cells), exact DST/FFT Poisson "
+                      "solves, numpy FP64, one thread"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import inputs
+    w_full = inputs.vesicle_couette_512x256x256(nx=args.nx, ny=args.ny, nz=args.nz)
+    import oracle
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    ws_ = oracle_sample_workload()
+    p = oracle.params_from_workload(ws_)
+    st = oracle.init_state(p, ws_.phi0)
+    for _ in range(args.warmup):
+        oracle.step(st, ws_.dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(st, ws_.dt)
+    t = time.perf_counter() - t0
+    value = ws_.ncells * args.steps / t / 1e6
+    sample = (f"each step one oracle step of the same recipe at {ws_.nx}x{ws_.ny}x{ws_.nz} "
+              f"(1/{w_full.ncells // ws_.ncells} of the cells), numpy FP64, one thread")
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(t / args.steps * 1e3, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w_full.name, "grid_xyz": [w_full.nx, w_full.ny, w_full.nz],
+                      "sampled_grid_xyz": [ws_.nx, ws_.ny, ws_.nz]},
+           "impl": "reference",
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

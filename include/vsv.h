@@ -1,0 +1,268 @@
+/*
+ * vsv.h -- C ABI of the GB300 vorticity--stream-vector phase-field library.
+ *
+ * The library advances the system of Gallen et al. ("Deformable bodies in a
+ * 3-dimensional viscous flow: vorticity-stream vector formulation"),
+ * main-text eqs. gen2, gen1, gen3 (= supplementary eq. 29):
+ *
+ *     d(phi)/dt  = M (lap mu + lambda_V) - (curl psi) . grad phi
+ *     lap omega  = (1/eta) grad phi x grad mu
+ *     lap psi    = -omega,          v = curl psi   (eq. vecpot)
+ *
+ * on a uniform cubic grid (numerical-implementation section), forward Euler
+ * for phi and the segregated order "advance phi, solve omega, solve psi"
+ * within one step.  Every step runs as CUDA kernels on one GPU, enqueued on
+ * the caller's stream; there is no CPU fallback.
+ *
+ * Grid and layout.  nx x ny x nz cells of spacing h; x is the periodic flow
+ * axis (boundary-conditions section: periodic in the flow direction), y is
+ * always walled, z is walled (duct, quiescent) or periodic (Couette, planar
+ * Poiseuille).  Every field crossing this ABI is a dense C-ordered array
+ * [nz][ny][nx] (x fastest) without halos.  Flow walls sit on the ghost
+ * nodes j = -1 and j = n, where omega and psi take the body-free flow's
+ * values (boundary-conditions section); phi and mu have no-flux (mirror)
+ * walls.
+ *
+ * Precision.  VSV_FP64 stores and computes everything in FP64.  VSV_MIXED
+ * stores fields in FP32 and smooths in FP32; the defect b - L x driving each
+ * multigrid correction is evaluated exactly (error-free FP32 transforms,
+ * i.e. at least FP64 accuracy) before rounding, and all volume / area /
+ * norm / stress reductions accumulate in FP64.
+ *
+ * Ownership.  The caller owns the device workspace, the stream and every
+ * input / output buffer; the library owns only the opaque host handle.  The
+ * workspace must stay valid until vsv_destroy.  A handle is not thread-safe;
+ * calls on one handle must be serialised by the caller.
+ *
+ * Errors.  Every function returns a vsv_status (0 = success); none aborts or
+ * exits.  After a failure vsv_last_error() describes it.  Kernel launches are
+ * asynchronous: faults inside kernels surface at the next synchronising call
+ * (vsv_check, vsv_get_field to host, vsv_get_diagnostics).
+ */
+#ifndef VSV_H
+#define VSV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vsv_grid vsv_grid;
+
+typedef enum {
+  VSV_OK = 0,
+  VSV_EINVAL = -1,       /* bad argument or shape; nothing was launched        */
+  VSV_ENOMEM = -2,       /* workspace smaller than vsv_workspace_bytes()       */
+  VSV_ECUDA = -3,        /* a CUDA runtime call failed (message has the name)  */
+  VSV_ENOCONV = -4,      /* Poisson solve hit max_cycles above tol; fields valid */
+  VSV_ENONFINITE = -5,   /* a NaN / Inf appeared in phi (device flag)          */
+  VSV_EUNSTABLE = -6,    /* dt above the explicit stability bound              */
+  VSV_ESTATE = -7        /* call out of order (e.g. step before set_phi)       */
+} vsv_status;
+
+typedef enum { VSV_FP64 = 0, VSV_MIXED = 1 } vsv_precision;
+
+/* Body-free flows supplying the wall data (boundary-conditions section). */
+typedef enum {
+  VSV_POISEUILLE_DUCT = 0,   /* walls in y and z, pressure-driven along x     */
+  VSV_POISEUILLE_PLANAR = 1, /* walls in y, z periodic                        */
+  VSV_COUETTE = 2,           /* walls in y moving along x, z periodic         */
+  VSV_QUIESCENT = 3          /* walls in y and z at rest                      */
+} vsv_flow_kind;
+
+/* Free energies: Cahn-Hilliard (eq. 31) or phase-field Helfrich (eq. 30). */
+typedef enum { VSV_CAHN_HILLIARD = 0, VSV_HELFRICH = 1 } vsv_fe_kind;
+
+typedef enum { VSV_SOLVER_MG = 0, VSV_SOLVER_SOR = 1 } vsv_solver_kind;
+typedef enum { VSV_DTYPE_F32 = 0, VSV_DTYPE_F64 = 1 } vsv_dtype;
+
+typedef enum {
+  VSV_FIELD_PHI = 0,
+  VSV_FIELD_MU = 1,
+  VSV_FIELD_OMEGA_X = 2, VSV_FIELD_OMEGA_Y = 3, VSV_FIELD_OMEGA_Z = 4,   /* full omega */
+  VSV_FIELD_PSI_X = 5, VSV_FIELD_PSI_Y = 6, VSV_FIELD_PSI_Z = 7,         /* full psi   */
+  VSV_FIELD_VEL_X = 8, VSV_FIELD_VEL_Y = 9, VSV_FIELD_VEL_Z = 10,        /* v = curl psi */
+  VSV_FIELD_STRESS_T = 11,          /* sigma_t of the in-plane-shear section        */
+  VSV_FIELD_OMEGA_PERT_X = 12, VSV_FIELD_OMEGA_PERT_Y = 13, VSV_FIELD_OMEGA_PERT_Z = 14,
+  VSV_FIELD_PSI_PERT_X = 15, VSV_FIELD_PSI_PERT_Y = 16, VSV_FIELD_PSI_PERT_Z = 17,
+  VSV_FIELD_COUNT = 18
+} vsv_field;
+
+/* Body-free flow.  u_max: Poiseuille maximum speed over the cells;
+ * v_lo / v_hi: Couette wall speeds (along x) at the y = 0 and y = H walls;
+ * eta: dynamic viscosity (eq. gen1). */
+typedef struct {
+  int kind;
+  double u_max;
+  double v_lo;
+  double v_hi;
+  double eta;
+} vsv_flow_params;
+
+/* Free energy.  sigma: CH gradient coefficient; kappa, eps: Helfrich bending
+ * modulus and interface width (also the width in the area functional, SM
+ * eq. 32); mobility M; k_area, k_vol: penalty stiffnesses of the area and
+ * volume multipliers (gamma_A = k_area (A - A0) 3 eps / (2 sqrt 2),
+ * lambda_V = k_vol (V - V0)); mu_prefactor_half selects the SM eq. 35
+ * prefactor 3 sqrt2 kappa / (8 eps^3) instead of the exact derivative of
+ * eq. 30 (twice that). */
+typedef struct {
+  int kind;
+  double sigma;
+  double kappa;
+  double eps;
+  double mobility;
+  double k_area;
+  double k_vol;
+  int mu_prefactor_half;
+} vsv_fe_params;
+
+/* Poisson solver (the paper says only "an iterative method").
+ * kind: MG (cell-centred V-cycles, red-black Gauss-Seidel smoothing) or SOR
+ *   (red-black, FP64 only).
+ * fixed_cycles > 0: every solve inside vsv_step runs exactly that many
+ *   V-cycles (SOR: sweeps) with no host synchronisation; 0: iterate until
+ *   ||b - L x||_2 <= tol ||b||_2 or max_cycles, checking every check_every.
+ * nu1 / nu2: pre / post smoothing sweeps; max_levels: multigrid depth cap;
+ * coarse_sweeps: red-black sweeps on the coarsest level; omega_sor <= 0
+ * picks the optimal SOR weight for the grid. */
+typedef struct {
+  int kind;
+  double tol;
+  int max_cycles;
+  int fixed_cycles;
+  int check_every;
+  int nu1;
+  int nu2;
+  int max_levels;
+  int coarse_sweeps;
+  double omega_sor;
+} vsv_solver_params;
+
+/* Per-axis boundary of a standalone Poisson problem: periodic (1) or zero
+ * Dirichlet data on the ghost nodes -1 and n (0).  Order x, y, z. */
+typedef struct {
+  int periodic[3];
+} vsv_bc;
+
+/* Observables (in-plane-shear section, results section, SM eq. 40). */
+typedef struct {
+  double time;
+  int64_t steps;
+  double volume;          /* V = h^3/2 sum (1 - phi)                          */
+  double area;            /* A of SM eq. 32                                   */
+  double volume0, area0;  /* reference values fixed by vsv_set_phi             */
+  double reduced_volume;  /* SM eq. 40                                        */
+  double energy;          /* Helfrich C_F h^3 sum g^2, or CH energy            */
+  double lambda_v, gamma_a;
+  double com[3];          /* centre of the body, weights (1 - phi)/2          */
+  double dissipation;     /* (eta/2) int sum_ij (d_j v_i + d_i v_j)^2           */
+  double dissipation0;    /* same for the body-free flow                        */
+  double resistance_rel;  /* (D - D0) / D0                                      */
+  double omega_dev2;      /* int |omega - omega0|^2                             */
+  double psi_dev2;        /* int |psi - psi0|^2                                 */
+  double max_div_v, max_div_psi, max_sigma_t;
+  int last_cycles_omega, last_cycles_psi;   /* of the last step's solves        */
+  double last_relres_omega, last_relres_psi;/* -1 when not measured             */
+  int nonfinite;
+} vsv_diag;
+
+/* Library version string. */
+const char* vsv_version(void);
+
+/* Bytes of device workspace a grid needs (all fields, the multigrid
+ * hierarchy, base-flow tables, reduction scratch).  0 for invalid shapes. */
+size_t vsv_workspace_bytes(int nx, int ny, int nz, int precision);
+
+/* Create a grid over caller-owned device memory `workspace` (>= 256-byte
+ * aligned, ws_bytes >= vsv_workspace_bytes) and caller stream `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  Periodic axes must have
+ * even extent or extent 1.  Defaults: quiescent flow, eta = 1, CH with
+ * sigma = eps = M = 1, default solver for the precision. */
+vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int precision,
+                      void* workspace, size_t ws_bytes, void* cuda_stream);
+
+/* Free the host handle (the workspace stays the caller's).  NULL is a no-op. */
+vsv_status vsv_destroy(vsv_grid* g);
+
+/* Choose the body-free flow (builds the wall data and base-flow tables on
+ * the device; a duct runs 2-D FP64 Poisson solves).  Must precede set_phi. */
+vsv_status vsv_set_flow(vsv_grid* g, const vsv_flow_params* fp);
+vsv_status vsv_set_free_energy(vsv_grid* g, const vsv_fe_params* fe);
+vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp);
+vsv_status vsv_default_solver(vsv_solver_params* out, int precision);
+
+/* Load phi^0 (dtype VSV_DTYPE_*, host or device pointer), then compute mu,
+ * V0 = V[phi^0], A0 = A[phi^0] and solve omega, psi for phi^0 (zero initial
+ * guess, iterating to tol).  Returns VSV_ENOCONV if a solve stalls. */
+vsv_status vsv_set_phi(vsv_grid* g, const void* phi, int dtype, int on_device);
+
+/* Advance nsteps steps of size dt (step order in the file comment).
+ * Asynchronous when the solver uses fixed_cycles; returns VSV_EUNSTABLE if
+ * dt exceeds vsv_stability_limit, VSV_ENONFINITE if the previous step set
+ * the non-finite flag. */
+vsv_status vsv_step(vsv_grid* g, int nsteps, double dt);
+
+/* Largest dt the explicit update tolerates (linear analysis about phi = +-1:
+ * Model-B diffusion of the chosen mu, and the volume penalty). */
+vsv_status vsv_stability_limit(const vsv_grid* g, double* dt_max);
+
+/* Standalone Poisson solve L_h x = rhs on this grid's shape with boundary
+ * `bc`, spacing h, using the grid's solver and precision.  rhs and x are
+ * [nz][ny][nx] arrays of dtype on host or device; x holds the initial guess
+ * on entry.  Uses the grid's scratch (it clobbers the grid's flow
+ * perturbation of component z; call vsv_set_phi again afterwards to resume
+ * time stepping).  cycles_out / relres_out may be NULL. */
+vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, int on_device,
+                             const vsv_bc* bc, double tol, int max_cycles, int* cycles_out,
+                             double* relres_out);
+
+/* Copy a field out (full omega / psi include the base flow).  Synchronous
+ * for host destinations. */
+vsv_status vsv_get_field(vsv_grid* g, int field, void* dst, int dtype, int on_device);
+
+/* Replace phi (mu, V, A are recomputed before the next step; V0, A0 and the
+ * flow are kept) or a perturbation component OMEGA_PERT_* / PSI_PERT_*. */
+vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int on_device);
+
+/* Observables of the current state; synchronises. */
+vsv_status vsv_get_diagnostics(vsv_grid* g, vsv_diag* out);
+
+/* <sigma_xy> averaged over x and z, one value per y row (ny doubles, host). */
+vsv_status vsv_get_stress_profile(vsv_grid* g, double* out);
+
+/* Checkpoint / resume: a flat host blob of the state (phi, omega', psi',
+ * V0, A0, time, step count). */
+size_t vsv_state_bytes(const vsv_grid* g);
+vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes);
+vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes);
+
+/* Synchronise the stream and report deferred kernel errors / flags. */
+vsv_status vsv_check(vsv_grid* g);
+
+/* Message of the last failure on this handle ("" if none); the pointer stays
+ * valid until the next call on the handle. */
+const char* vsv_last_error(const vsv_grid* g);
+
+/* Kernel accounting.  vsv_kernel_launches: kernels this handle has launched.
+ * Profiling brackets every launch of one kernel class with CUDA events on the
+ * grid's stream; vsv_profile_read synchronises and returns the summed device
+ * time and launch count since the last vsv_profile_enable. */
+typedef enum {
+  VSV_KCLASS_SMOOTH = 0,        /* red-black Gauss-Seidel sweeps, all levels   */
+  VSV_KCLASS_SMOOTH_FINE = 1,   /* red-black sweeps on the finest level only   */
+  VSV_KCLASS_RESTRICT = 2,      /* exact residual + restriction                */
+  VSV_KCLASS_PROLONG = 3,       /* prolongation + correction                   */
+  VSV_KCLASS_PHASE = 4,         /* phi update, mu, source, reductions          */
+  VSV_KCLASS_COUNT = 5
+} vsv_kernel_class;
+int64_t vsv_kernel_launches(const vsv_grid* g);
+vsv_status vsv_profile_enable(vsv_grid* g, int kernel_class, int enable);
+vsv_status vsv_profile_read(vsv_grid* g, int kernel_class, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VSV_H */

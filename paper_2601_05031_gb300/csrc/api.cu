@@ -1,0 +1,1091 @@
+// C ABI of the vorticity--stream-vector library (declared in include/vsv.h):
+// workspace layout, multigrid / SOR drivers, base-flow set-up and the time
+// step of main-text eqs. gen2, gen1, gen3 in the segregated order of the
+// numerical-implementation section.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace vsv;
+
+struct vsv_grid {
+  Ctx cx;
+  int nx = 0, ny = 0, nz = 0;
+  double h = 1.0;
+  int prec = VSV_MIXED;
+  size_t tsize = 4;
+  long long N = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+
+  vsv_flow_params flow{};
+  vsv_fe_params fe{};
+  vsv_solver_params sol{};
+  bool flow_set = false, phi_set = false, phase_stale = false;
+
+  void* phi[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* mu = nullptr;
+  void* g = nullptr;
+  void* f[3] = {};
+  void* om[3] = {};
+  void* ps[3] = {};
+  void* stage_a = nullptr;   // N * 8 bytes
+  void* stage_b = nullptr;   // N * 8 bytes
+  void* mg_e[kMaxLevels][3] = {};
+  void* mg_r[kMaxLevels][3] = {};
+  long long mg_cap[kMaxLevels] = {};
+  int mg_nlev_cap = 0;
+
+  double* om_ring[3] = {};   // (ny+2)(nz+2) FP64, ring + interior body-free values
+  double* ps_ring[3] = {};
+  double* v0d[3] = {};       // ny nz FP64
+  double* s_om_d[3] = {};
+  double* s_ps_d[3] = {};
+  void* v0t[3] = {};         // typed copies (T)
+  void* s_om_t[3] = {};
+  void* s_ps_neg_t[3] = {};
+  double* su0 = nullptr;     // 2-D set-up scratch (ny nz each)
+  double* schi = nullptr;
+  double* sx = nullptr;
+  double* sb = nullptr;
+
+  double* partials = nullptr;
+  int red_blocks = 0;
+  Scalars* S = nullptr;
+  double* dout = nullptr;     // kDiagQ doubles
+  double* profile = nullptr;  // ny doubles
+  double* scratch1 = nullptr;
+
+  std::vector<Level> flow_levels;
+  int* flag_host = nullptr;        // pinned copy of the device non-finite flag
+  cudaEvent_t flag_event = nullptr;
+  bool flag_pending = false;
+  int last_cycles[2] = {0, 0};
+  double last_relres[2] = {-1.0, -1.0};
+  double time = 0.0;
+  long long steps = 0;
+  std::string err;
+};
+
+namespace {
+
+const size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Upper bound of the multigrid hierarchy: halve every axis longer than one
+// cell while all of them are even (any boundary choice coarsens no further).
+int plan_levels(int nx, int ny, int nz, long long* cells) {
+  int n[3] = {nx, ny, nz};
+  int L = 0;
+  cells[L++] = (long long)nx * ny * nz;
+  while (L < kMaxLevels) {
+    bool ok = true, any = false;
+    for (int a = 0; a < 3; ++a)
+      if (n[a] > 1) {
+        any = true;
+        if (n[a] % 2) ok = false;
+      }
+    if (!ok || !any) break;
+    for (int a = 0; a < 3; ++a)
+      if (n[a] > 1) n[a] /= 2;
+    cells[L++] = (long long)n[0] * n[1] * n[2];
+  }
+  return L;
+}
+
+int reduction_blocks(long long N) {
+  long long b = (N + kBlock - 1) / kBlock;
+  return (int)std::max(1LL, std::min(b, 1216LL));
+}
+
+// Carve the workspace (g == nullptr: only measure).
+size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
+  const size_t ts = (prec == VSV_FP64) ? 8 : 4;
+  const long long N = (long long)nx * ny * nz;
+  const long long N2 = (long long)ny * nz;
+  const long long R2 = (long long)(ny + 2) * (nz + 2);
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = base ? (void*)(base + off) : nullptr;
+    off = align_up(off + bytes);
+    return p;
+  };
+  auto tf = [&](long long n) { return take((size_t)n * ts); };
+  auto df = [&](long long n) { return (double*)take((size_t)n * 8); };
+  void* p;
+  p = tf(N); if (g) g->phi[0] = p;
+  p = tf(N); if (g) g->phi[1] = p;
+  p = tf(N); if (g) g->mu = p;
+  p = tf(N); if (g) g->g = p;
+  for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->f[c] = p; }
+  for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->om[c] = p; }
+  for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->ps[c] = p; }
+  p = take((size_t)N * 8); if (g) g->stage_a = p;
+  p = take((size_t)N * 8); if (g) g->stage_b = p;
+  long long cells[kMaxLevels];
+  const int nl = plan_levels(nx, ny, nz, cells);
+  if (g) g->mg_nlev_cap = nl;
+  for (int l = 1; l < nl; ++l) {
+    for (int c = 0; c < 3; ++c) { p = tf(cells[l]); if (g) g->mg_e[l][c] = p; }
+    for (int c = 0; c < 3; ++c) { p = tf(cells[l]); if (g) g->mg_r[l][c] = p; }
+    if (g) g->mg_cap[l] = cells[l];
+  }
+  for (int c = 0; c < 3; ++c) { double* d = df(R2); if (g) g->om_ring[c] = d; }
+  for (int c = 0; c < 3; ++c) { double* d = df(R2); if (g) g->ps_ring[c] = d; }
+  for (int c = 0; c < 3; ++c) { double* d = df(N2); if (g) g->v0d[c] = d; }
+  for (int c = 0; c < 3; ++c) { double* d = df(N2); if (g) g->s_om_d[c] = d; }
+  for (int c = 0; c < 3; ++c) { double* d = df(N2); if (g) g->s_ps_d[c] = d; }
+  for (int c = 0; c < 3; ++c) { p = tf(N2); if (g) g->v0t[c] = p; }
+  for (int c = 0; c < 3; ++c) { p = tf(N2); if (g) g->s_om_t[c] = p; }
+  for (int c = 0; c < 3; ++c) { p = tf(N2); if (g) g->s_ps_neg_t[c] = p; }
+  double* d;
+  d = df(N2); if (g) g->su0 = d;
+  d = df(N2); if (g) g->schi = d;
+  d = df(N2); if (g) g->sx = d;
+  d = df(N2); if (g) g->sb = d;
+  const int rb = reduction_blocks(N);
+  d = df((long long)rb * 32); if (g) { g->partials = d; g->red_blocks = rb; }
+  p = take(sizeof(Scalars)); if (g) g->S = (Scalars*)p;
+  d = df(kDiagQ); if (g) g->dout = d;
+  d = df(ny); if (g) g->profile = d;
+  d = df(8); if (g) g->scratch1 = d;
+  return off;
+}
+
+bool valid_shape(int nx, int ny, int nz) {
+  return nx >= 1 && ny >= 2 && nz >= 1 && (long long)nx * ny * nz <= (1LL << 33);
+}
+
+vsv_status fail(vsv_grid* g, vsv_status s, const char* fmt, const char* detail = "") {
+  if (g) {
+    char buf[512];
+    snprintf(buf, sizeof buf, fmt, detail);
+    g->err = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return fail(g, VSV_ECUDA, #call ": %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKL()                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess) return fail(g, VSV_ECUDA, "kernel launch: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+bool z_periodic(const vsv_grid* g) {
+  return g->flow.kind == VSV_COUETTE || g->flow.kind == VSV_POISEUILLE_PLANAR;
+}
+
+// Multigrid levels for per-axis periodic flags: all active axes are halved
+// together while every active extent is even (periodic extents must stay
+// even); coarse wall closure alpha_l = (2^l - 1) / (2^l + 1).
+std::vector<Level> build_levels(int nx, int ny, int nz, double h, const int per[3], int max_levels,
+                                int cap_levels) {
+  std::vector<Level> lv;
+  Level L{};
+  L.n[0] = nx; L.n[1] = ny; L.n[2] = nz;
+  for (int a = 0; a < 3; ++a) {
+    L.per[a] = per[a];
+    L.act[a] = !(per[a] && L.n[a] == 1);
+  }
+  L.alpha = 0.0;
+  L.inv_h2 = 1.0 / (h * h);
+  L.alphaf = 0.f;
+  L.inv_h2f = (float)L.inv_h2;
+  lv.push_back(L);
+  const int maxl = std::min(std::max(max_levels, 1), cap_levels);
+  while ((int)lv.size() < maxl) {
+    const Level& P = lv.back();
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      if (!P.act[a]) continue;
+      if (P.n[a] < 2 || P.n[a] % 2) ok = false;
+      else if (P.per[a] && (P.n[a] / 2) % 2) ok = false;
+    }
+    bool any = false;
+    for (int a = 0; a < 3; ++a) any |= (P.act[a] && P.n[a] > 1);
+    if (!ok || !any) break;
+    Level C = P;
+    for (int a = 0; a < 3; ++a)
+      if (P.act[a] && P.n[a] > 1) C.n[a] = P.n[a] / 2;
+    const int l = (int)lv.size();
+    const double p2 = std::ldexp(1.0, l);
+    C.alpha = (p2 - 1.0) / (p2 + 1.0);
+    C.inv_h2 = 1.0 / (h * h * p2 * p2);
+    C.alphaf = (float)C.alpha;
+    C.inv_h2f = (float)C.inv_h2;
+    lv.push_back(C);
+  }
+  return lv;
+}
+
+double sor_weight(const Level& L) {
+  double lam = 0.0;
+  int d = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (!L.act[a]) continue;
+    ++d;
+    if (!L.per[a]) lam += 2.0 - 2.0 * std::cos(M_PI / (L.n[a] + 1.0));
+  }
+  if (d == 0) return 1.0;
+  const double rho = 1.0 - lam / (2.0 * d);
+  return 2.0 / (1.0 + std::sqrt(std::max(0.0, 1.0 - rho * rho)));
+}
+
+Comp3<const double> ring3(double* const p[3]) { return Comp3<const double>{{p[0], p[1], p[2]}}; }
+
+template <class T>
+Comp3<T> comp3(void* a, void* b, void* c) {
+  return Comp3<T>{{(T*)a, (T*)b, (T*)c}};
+}
+
+// ---------------------------------------------------------------- solvers
+template <class T>
+void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T> R, int ncomp) {
+  const Level& L = lv[l];
+  const double h2 = 1.0 / L.inv_h2;
+  const bool last = (l + 1 == (int)lv.size());
+  const int kc = (l == 0) ? VSV_KCLASS_SMOOTH_FINE : VSV_KCLASS_SMOOTH;
+  if (last) {
+    if (l > 0) {
+      Comp3<T> E = X;
+      Comp3<T> RR{{(T*)R.B[0], (T*)R.B[1], (T*)R.B[2]}};
+      if (launch_coarse_solve<T>(g->cx, L, E, RR, ncomp, g->sol.coarse_sweeps, h2)) return;
+      launch_zero<T>(g->cx, E, L.cells(), ncomp);
+    }
+    for (int s = 0; s < g->sol.coarse_sweeps; ++s) {
+      launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
+      launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
+    }
+    return;
+  }
+  for (int s = 0; s < g->sol.nu1; ++s) {
+    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
+    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
+  }
+  const Level& C = lv[l + 1];
+  Comp3<T> EC = comp3<T>(g->mg_e[l + 1][0], g->mg_e[l + 1][1], g->mg_e[l + 1][2]);
+  Comp3<T> RC = comp3<T>(g->mg_r[l + 1][0], g->mg_r[l + 1][1], g->mg_r[l + 1][2]);
+  const bool exact = std::is_same<T, float>::value && l == 0;
+  launch_resid_restrict<T>(g->cx, L, C, X, R, RC, ncomp, exact);
+  if (l + 2 < (int)lv.size()) launch_zero<T>(g->cx, EC, C.cells(), ncomp);
+  Rhs3<T> RCr{{RC.p[0], RC.p[1], RC.p[2]}, {nullptr, nullptr, nullptr}, (T)1};
+  vcycle<T>(g, lv, l + 1, EC, RCr, ncomp);
+  launch_prolong_add<T>(g->cx, L, C, X, EC, ncomp);
+  for (int s = 0; s < g->sol.nu2; ++s) {
+    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
+    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
+  }
+}
+
+// relres = max over components of ||b - L x|| / ||b|| (||b|| = 0 -> ||r||).
+template <class T>
+vsv_status residual(vsv_grid* g, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, double* relres) {
+  launch_resid_norm<T>(g->cx, L, X, R, ncomp, std::is_same<T, float>::value, g->partials,
+                       g->red_blocks, g->S);
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, g->S, sizeof(Scalars), cudaMemcpyDeviceToHost, g->cx.stream));
+  CK(cudaStreamSynchronize(g->cx.stream));
+  double m = 0.0;
+  for (int c = 0; c < ncomp; ++c) {
+    const double rn = std::sqrt(hs.rnorm2[c]), bn = std::sqrt(hs.bnorm2[c]);
+    m = std::max(m, bn > 0 ? rn / bn : rn);
+  }
+  *relres = m;
+  return VSV_OK;
+}
+
+// Solve L x = b (per component) on hierarchy lv.  fixed > 0: exactly that many
+// cycles (SOR: sweeps), no synchronisation; else to tol within max_cycles.
+template <class T>
+vsv_status solve(vsv_grid* g, const std::vector<Level>& lv, Comp3<T> X, Rhs3<T> R, int ncomp,
+                 int kind, int fixed, double tol, int max_cycles, int check_every, int* cycles_out,
+                 double* relres_out) {
+  const Level& L = lv[0];
+  double w = g->sol.omega_sor > 0 ? g->sol.omega_sor : sor_weight(L);
+  const double h2 = 1.0 / L.inv_h2;
+  auto one = [&]() {
+    if (kind == VSV_SOLVER_SOR) {
+      launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, w, h2, VSV_KCLASS_SMOOTH_FINE);
+      launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, w, h2, VSV_KCLASS_SMOOTH_FINE);
+    } else {
+      vcycle<T>(g, lv, 0, X, R, ncomp);
+    }
+  };
+  if (fixed > 0) {
+    for (int c = 0; c < fixed; ++c) one();
+    CKL();
+    if (cycles_out) *cycles_out = fixed;
+    if (relres_out) *relres_out = -1.0;
+    return VSV_OK;
+  }
+  const int every = std::max(1, check_every);
+  double rr = 0.0;
+  vsv_status st = residual<T>(g, L, X, R, ncomp, &rr);
+  if (st != VSV_OK) return st;
+  int c = 0;
+  double prev = rr;
+  int stall = 0;
+  bool floor_reached = false;
+  while (rr > tol && c < max_cycles) {
+    const int todo = std::min(every, max_cycles - c);
+    for (int q = 0; q < todo; ++q) one();
+    c += todo;
+    CKL();
+    st = residual<T>(g, L, X, R, ncomp, &rr);
+    if (st != VSV_OK) return st;
+    if (!(rr < 0.9 * prev)) {
+      if (++stall >= 3) {
+        // No further decrease: the iterate sits at the rounding floor of its
+        // storage.  In FP32 storage that floor is u ||L|| ||x|| / ||b||
+        // (often 1e-6 .. 1e-4 for smooth solutions) while the error of x
+        // itself is O(u): accepted as converged for the mixed precision.
+        floor_reached = std::is_same<T, float>::value && rr < 1e-3;
+        break;
+      }
+    } else {
+      stall = 0;
+    }
+    prev = std::min(prev, rr);
+  }
+  if (cycles_out) *cycles_out = c;
+  if (relres_out) *relres_out = rr;
+  if (!std::isfinite(rr)) return fail(g, VSV_ENONFINITE, "non-finite residual%s");
+  if (rr > tol && !floor_reached) return fail(g, VSV_ENOCONV, "Poisson solve stopped above tolerance%s");
+  return VSV_OK;
+}
+
+// ---------------------------------------------------------------- phase-field helpers
+PhaseParams phase_params(const vsv_grid* g) {
+  PhaseParams P{};
+  P.nx = g->nx; P.ny = g->ny; P.nz = g->nz;
+  P.zper = z_periodic(g);
+  P.h = g->h; P.inv_h = 1.0 / g->h; P.inv_h2 = 1.0 / (g->h * g->h);
+  P.fe_kind = g->fe.kind;
+  P.sigma = g->fe.sigma;
+  P.eps = g->fe.eps;
+  const double cf = 3.0 * std::sqrt(2.0) * g->fe.kappa / (8.0 * std::pow(g->fe.eps, 3));
+  P.cf2 = g->fe.mu_prefactor_half ? cf : 2.0 * cf;
+  P.mobility = g->fe.mobility;
+  P.inv_eta = 1.0 / g->flow.eta;
+  std::memset(P.vwall, 0, sizeof P.vwall);
+  if (g->flow.kind == VSV_COUETTE) {
+    P.vwall[0][0] = g->flow.v_lo;
+    P.vwall[1][0] = g->flow.v_hi;
+  }
+  return P;
+}
+
+void upload_scalar_params(vsv_grid* g) {
+  // k_vol, k_area, eps, h3 live in the device scalars (read by the finalizer)
+  struct { double k_vol, k_area, eps, h3; } v{g->fe.k_vol, g->fe.k_area, g->fe.eps,
+                                                g->h * g->h * g->h};
+  cudaMemcpyAsync(&g->S->k_vol, &v, sizeof v, cudaMemcpyHostToDevice, g->cx.stream);
+  cudaStreamSynchronize(g->cx.stream);
+}
+
+template <class T>
+Rhs3<T> rhs_omega(vsv_grid* g) {
+  return Rhs3<T>{{(T*)g->f[0], (T*)g->f[1], (T*)g->f[2]}, {nullptr, nullptr, nullptr}, (T)1};
+}
+template <class T>
+Rhs3<T> rhs_psi(vsv_grid* g) {
+  return Rhs3<T>{{(T*)g->om[0], (T*)g->om[1], (T*)g->om[2]},
+                 {(T*)g->s_ps_neg_t[0], (T*)g->s_ps_neg_t[1], (T*)g->s_ps_neg_t[2]}, (T)-1};
+}
+
+template <class T>
+vsv_status flow_solves(vsv_grid* g, bool initial) {
+  Comp3<T> O = comp3<T>(g->om[0], g->om[1], g->om[2]);
+  Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
+  const vsv_solver_params& s = g->sol;
+  const int fixed = initial ? 0 : s.fixed_cycles;
+  vsv_status st = solve<T>(g, g->flow_levels, O, rhs_omega<T>(g), 3, s.kind, fixed, s.tol,
+                           s.max_cycles, s.check_every, &g->last_cycles[0], &g->last_relres[0]);
+  if (st != VSV_OK) return st;
+  st = solve<T>(g, g->flow_levels, Pp, rhs_psi<T>(g), 3, s.kind, fixed, s.tol, s.max_cycles,
+                s.check_every, &g->last_cycles[1], &g->last_relres[1]);
+  return st;
+}
+
+// mu (and V, A, multipliers) of the current phi; init fixes V0, A0.
+template <class T>
+void refresh_phase(vsv_grid* g, int init) {
+  PhaseParams P = phase_params(g);
+  T* phi = (T*)g->phi[g->cur];
+  launch_reduce_va<T>(g->cx, P, phi, g->partials, g->red_blocks, g->S, init);
+  launch_mu<T>(g->cx, P, phi, (T*)g->g, (T*)g->mu, g->S);
+}
+
+template <class T>
+vsv_status step_impl(vsv_grid* g, double dt) {
+  PhaseParams P = phase_params(g);
+  if (g->phase_stale) {
+    refresh_phase<T>(g, 0);
+    g->phase_stale = false;
+  }
+  T* phi = (T*)g->phi[g->cur];
+  T* phin = (T*)g->phi[1 - g->cur];
+  Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
+  Comp3<T> V0 = comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]);
+  // 1-3: explicit phi update with v^n = v0 + curl psi'^n and lambda_V^n
+  launch_phi_update<T>(g->cx, P, phi, (const T*)g->mu, Pp, V0, g->S, (T)dt, phin);
+  g->cur = 1 - g->cur;
+  // 4-5: V, A of phi^{n+1}, gamma_A, then mu^{n+1}
+  refresh_phase<T>(g, 0);
+  // 6: source f = grad phi x grad mu / eta - s_omega
+  Comp3<T> SO = comp3<T>(g->s_om_t[0], g->s_om_t[1], g->s_om_t[2]);
+  Comp3<T> F = comp3<T>(g->f[0], g->f[1], g->f[2]);
+  launch_source<T>(g->cx, P, phin, (const T*)g->mu, SO, F);
+  CKL();
+  // 7-8: vorticity then stream-vector Poisson solves
+  vsv_status st = flow_solves<T>(g, false);
+  g->time += dt;
+  g->steps += 1;
+  return st;
+}
+
+template <class T>
+vsv_status set_phi_impl(vsv_grid* g) {
+  refresh_phase<T>(g, 1);
+  PhaseParams P = phase_params(g);
+  Comp3<T> SO = comp3<T>(g->s_om_t[0], g->s_om_t[1], g->s_om_t[2]);
+  Comp3<T> F = comp3<T>(g->f[0], g->f[1], g->f[2]);
+  launch_source<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->mu, SO, F);
+  launch_zero<T>(g->cx, comp3<T>(g->om[0], g->om[1], g->om[2]), g->N, 3);
+  launch_zero<T>(g->cx, comp3<T>(g->ps[0], g->ps[1], g->ps[2]), g->N, 3);
+  CKL();
+  g->phase_stale = false;
+  return flow_solves<T>(g, true);
+}
+
+// ---------------------------------------------------------------- data movement
+// Copy `n` elements of dtype `dt` from user memory into a T buffer `dst`.
+template <class T>
+vsv_status import_field(vsv_grid* g, const void* src, int dt, int on_device, T* dst, long long n) {
+  const size_t in_sz = (dt == VSV_DTYPE_F64) ? 8 : 4;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (in_sz == sizeof(T)) {
+    CK(cudaMemcpyAsync(dst, src, n * in_sz, kind, g->cx.stream));
+  } else {
+    CK(cudaMemcpyAsync(g->stage_b, src, n * in_sz, kind, g->cx.stream));
+    if (dt == VSV_DTYPE_F64) launch_convert<double, T>(g->cx, (const double*)g->stage_b, dst, n);
+    else launch_convert<float, T>(g->cx, (const float*)g->stage_b, dst, n);
+    CKL();
+  }
+  if (!on_device) CK(cudaStreamSynchronize(g->cx.stream));
+  return VSV_OK;
+}
+
+template <class T>
+vsv_status export_field(vsv_grid* g, const T* src, int dt, int on_device, void* dst, long long n) {
+  const size_t out_sz = (dt == VSV_DTYPE_F64) ? 8 : 4;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (out_sz == sizeof(T)) {
+    CK(cudaMemcpyAsync(dst, src, n * out_sz, kind, g->cx.stream));
+  } else {
+    if (dt == VSV_DTYPE_F64) launch_convert<T, double>(g->cx, src, (double*)g->stage_b, n);
+    else launch_convert<T, float>(g->cx, src, (float*)g->stage_b, n);
+    CKL();
+    CK(cudaMemcpyAsync(dst, g->stage_b, n * out_sz, kind, g->cx.stream));
+  }
+  if (!on_device) CK(cudaStreamSynchronize(g->cx.stream));
+  return VSV_OK;
+}
+
+template <class T>
+vsv_status get_field_impl(vsv_grid* g, int field, void* dst, int dt, int on_device) {
+  PhaseParams P = phase_params(g);
+  if (g->phase_stale && (field == VSV_FIELD_MU || field == VSV_FIELD_STRESS_T)) {
+    refresh_phase<T>(g, 0);
+    g->phase_stale = false;
+  }
+  const T* src = nullptr;
+  T* tmp = (T*)g->stage_a;
+  if (field == VSV_FIELD_PHI) src = (const T*)g->phi[g->cur];
+  else if (field == VSV_FIELD_MU) src = (const T*)g->mu;
+  else if (field >= VSV_FIELD_OMEGA_X && field <= VSV_FIELD_OMEGA_Z) {
+    const int c = field - VSV_FIELD_OMEGA_X;
+    launch_full_field<T>(g->cx, P, (const T*)g->om[c], g->om_ring[c], 1, tmp);
+    src = tmp;
+  } else if (field >= VSV_FIELD_PSI_X && field <= VSV_FIELD_PSI_Z) {
+    const int c = field - VSV_FIELD_PSI_X;
+    launch_full_field<T>(g->cx, P, (const T*)g->ps[c], g->ps_ring[c], 1, tmp);
+    src = tmp;
+  } else if (field >= VSV_FIELD_VEL_X && field <= VSV_FIELD_VEL_Z) {
+    Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
+    launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+                       comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
+    src = V.p[field - VSV_FIELD_VEL_X];
+  } else if (field == VSV_FIELD_STRESS_T) {
+    Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
+    launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+                       comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
+    launch_diag<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->g, V,
+                   comp3<T>(g->om[0], g->om[1], g->om[2]), comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+                   ring3(g->ps_ring), ring3(g->v0d), tmp, g->partials, g->red_blocks, g->dout);
+    src = tmp;
+  } else if (field >= VSV_FIELD_OMEGA_PERT_X && field <= VSV_FIELD_OMEGA_PERT_Z) {
+    src = (const T*)g->om[field - VSV_FIELD_OMEGA_PERT_X];
+  } else if (field >= VSV_FIELD_PSI_PERT_X && field <= VSV_FIELD_PSI_PERT_Z) {
+    src = (const T*)g->ps[field - VSV_FIELD_PSI_PERT_X];
+  } else {
+    return fail(g, VSV_EINVAL, "unknown field%s");
+  }
+  CKL();
+  return export_field<T>(g, src, dt, on_device, dst, g->N);
+}
+
+// ---------------------------------------------------------------- base flow
+vsv_status upload_d(vsv_grid* g, double* dst, const std::vector<double>& v) {
+  CK(cudaMemcpyAsync(dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice, g->cx.stream));
+  CK(cudaStreamSynchronize(g->cx.stream));
+  return VSV_OK;
+}
+
+// 2-D (y, z) FP64 solve of lap x = b, zero data on the wall nodes (duct).
+vsv_status solve2d(vsv_grid* g, double* x, const double* b, double tol) {
+  const int per[3] = {1, 0, 0};
+  std::vector<Level> lv = build_levels(1, g->ny, g->nz, g->h, per, 1, 1);
+  Comp3<double> X{{x, nullptr, nullptr}};
+  Rhs3<double> R{{b, nullptr, nullptr}, {nullptr, nullptr, nullptr}, 1.0};
+  launch_fill(g->cx, x, (long long)g->ny * g->nz, 0.0);
+  int cyc = 0;
+  double rr = 0.0;
+  vsv_status st = solve<double>(g, lv, X, R, 1, VSV_SOLVER_SOR, 0, tol, 200000, 50, &cyc, &rr);
+  if (st == VSV_ENOCONV && rr < 1e-11) st = VSV_OK;   // rounding floor of the 2-D solve
+  return st;
+}
+
+template <class T>
+void typed_tables(vsv_grid* g) {
+  const long long n2 = (long long)g->ny * g->nz;
+  for (int c = 0; c < 3; ++c) {
+    launch_convert<double, T>(g->cx, g->v0d[c], (T*)g->v0t[c], n2);
+    launch_convert<double, T>(g->cx, g->s_om_d[c], (T*)g->s_om_t[c], n2);
+    launch_scale_copy<double>(g->cx, g->s_ps_d[c], g->sx, n2, -1.0);
+    launch_convert<double, T>(g->cx, g->sx, (T*)g->s_ps_neg_t[c], n2);
+  }
+}
+
+vsv_status build_base_flow(vsv_grid* g) {
+  const int ny = g->ny, nz = g->nz;
+  const long long R2 = (long long)(ny + 2) * (nz + 2), n2 = (long long)ny * nz;
+  const double h = g->h;
+  for (int c = 0; c < 3; ++c) {
+    launch_fill(g->cx, g->om_ring[c], R2, 0.0);
+    launch_fill(g->cx, g->ps_ring[c], R2, 0.0);
+  }
+  const double H = (ny + 1) * h;
+  auto ridx = [&](int j, int k) { return (size_t)((j + 1) + (long long)(k + 1) * (ny + 2)); };
+  if (g->flow.kind == VSV_COUETTE || g->flow.kind == VSV_POISEUILLE_PLANAR) {
+    // closed forms on every node (y = (j + 1) h), x- and z-invariant
+    std::vector<double> om(R2, 0.0), ps(R2, 0.0);
+    for (int k = -1; k <= nz; ++k)
+      for (int j = -1; j <= ny; ++j) {
+        const double y = (j + 1) * h;
+        double o, p;
+        if (g->flow.kind == VSV_COUETTE) {
+          const double vl = g->flow.v_lo, vh = g->flow.v_hi;
+          p = vl * y + (vh - vl) * y * y / (2.0 * H);
+          o = -(vh - vl) / H;
+        } else {
+          const double U = g->flow.u_max;
+          p = 4.0 * U * (H * y * y / 2.0 - y * y * y / 3.0) / (H * H);
+          o = -4.0 * U * (H - 2.0 * y) / (H * H);
+        }
+        om[ridx(j, k)] = o;
+        ps[ridx(j, k)] = p;
+      }
+    vsv_status st = upload_d(g, g->om_ring[2], om);
+    if (st != VSV_OK) return st;
+    st = upload_d(g, g->ps_ring[2], ps);
+    if (st != VSV_OK) return st;
+  } else if (g->flow.kind == VSV_POISEUILLE_DUCT) {
+    if (ny < 2 || nz < 2) return fail(g, VSV_EINVAL, "duct needs ny, nz >= 2%s");
+    // u0: lap u0 = -1, scaled to max U; chi: lap chi = u0 (zero wall data)
+    launch_fill(g->cx, g->sb, n2, -1.0);
+    vsv_status st = solve2d(g, g->su0, g->sb, 1e-13);
+    if (st != VSV_OK) return st;
+    const double mx = device_max_abs(g->cx, g->su0, n2, g->scratch1);
+    launch_scale_copy<double>(g->cx, g->su0, g->su0, n2, g->flow.u_max / mx);
+    st = solve2d(g, g->schi, g->su0, 1e-13);
+    if (st != VSV_OK) return st;
+    launch_duct_ring(g->cx, ny, nz, h, g->su0, g->schi, g->om_ring[1], g->om_ring[2], g->ps_ring[1],
+                     g->ps_ring[2]);
+    // body-free interior: lap omega0 = 0, lap psi0 = -omega0 with the ring
+    // data (u0 and chi are no longer needed: their buffers hold omega0_y, _z)
+    double* om_int[3] = {nullptr, g->su0, g->schi};
+    for (int c = 1; c < 3; ++c) {
+      launch_ring_boundary_rhs(g->cx, ny, nz, h, g->om_ring[c], 0.0, nullptr, g->sb);
+      st = solve2d(g, g->sx, g->sb, 1e-12);
+      if (st != VSV_OK) return st;
+      launch_ring_fill_interior(g->cx, ny, nz, g->sx, g->om_ring[c]);
+      launch_scale_copy<double>(g->cx, g->sx, om_int[c], n2, 1.0);
+    }
+    for (int c = 1; c < 3; ++c) {
+      launch_ring_boundary_rhs(g->cx, ny, nz, h, g->ps_ring[c], -1.0, om_int[c], g->sb);
+      st = solve2d(g, g->sx, g->sb, 1e-12);
+      if (st != VSV_OK) return st;
+      launch_ring_fill_interior(g->cx, ny, nz, g->sx, g->ps_ring[c]);
+    }
+  } else if (g->flow.kind != VSV_QUIESCENT) {
+    return fail(g, VSV_EINVAL, "unknown flow kind%s");
+  }
+  const double* om[3] = {g->om_ring[0], g->om_ring[1], g->om_ring[2]};
+  const double* ps[3] = {g->ps_ring[0], g->ps_ring[1], g->ps_ring[2]};
+  launch_base_derived(g->cx, ny, nz, z_periodic(g), h, om, ps, g->v0d, g->s_om_d, g->s_ps_d);
+  if (g->prec == VSV_FP64) typed_tables<double>(g);
+  else typed_tables<float>(g);
+  CKL();
+  CK(cudaStreamSynchronize(g->cx.stream));
+  return VSV_OK;
+}
+
+void default_solver(vsv_solver_params* s, int prec) {
+  s->kind = VSV_SOLVER_MG;
+  s->tol = prec == VSV_FP64 ? 1e-12 : 1e-7;
+  s->max_cycles = 200;
+  s->fixed_cycles = 0;
+  s->check_every = 1;
+  s->nu1 = 2;
+  s->nu2 = 2;
+  s->max_levels = kMaxLevels;
+  s->coarse_sweeps = 24;
+  s->omega_sor = 0.0;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* vsv_version(void) { return "vsv-gb300 0.1 (sm_103a)"; }
+
+size_t vsv_workspace_bytes(int nx, int ny, int nz, int precision) {
+  if (!valid_shape(nx, ny, nz) || (precision != VSV_FP64 && precision != VSV_MIXED)) return 0;
+  return carve(nx, ny, nz, precision, nullptr, nullptr);
+}
+
+vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int precision,
+                      void* workspace, size_t ws_bytes, void* cuda_stream) {
+  if (!out) return VSV_EINVAL;
+  *out = nullptr;
+  if (!valid_shape(nx, ny, nz) || !(h > 0) || (precision != VSV_FP64 && precision != VSV_MIXED))
+    return VSV_EINVAL;
+  if ((nx > 1 && nx % 2) || !workspace || ((uintptr_t)workspace % kAlign)) return VSV_EINVAL;
+  const size_t need = carve(nx, ny, nz, precision, nullptr, nullptr);
+  if (ws_bytes < need) return VSV_ENOMEM;
+  vsv_grid* g = new vsv_grid();
+  g->nx = nx; g->ny = ny; g->nz = nz; g->h = h;
+  g->prec = precision;
+  g->tsize = precision == VSV_FP64 ? 8 : 4;
+  g->N = (long long)nx * ny * nz;
+  g->ws = (char*)workspace;
+  g->ws_bytes = ws_bytes;
+  g->cx.stream = (cudaStream_t)cuda_stream;
+  carve(nx, ny, nz, precision, g, g->ws);
+  g->flow = vsv_flow_params{VSV_QUIESCENT, 0.0, 0.0, 0.0, 1.0};
+  g->fe = vsv_fe_params{VSV_CAHN_HILLIARD, 1.0, 0.0, 1.0, 1.0, 0.0, 0.0, 0};
+  default_solver(&g->sol, precision);
+  if (cudaMemsetAsync(g->S, 0, sizeof(Scalars), g->cx.stream) != cudaSuccess) {
+    delete g;
+    return VSV_ECUDA;
+  }
+  upload_scalar_params(g);
+  *out = g;
+  return VSV_OK;
+}
+
+vsv_status vsv_destroy(vsv_grid* g) {
+  if (!g) return VSV_OK;
+  for (auto e : g->cx.ev) cudaEventDestroy(e);
+  if (g->flag_event) {
+    cudaEventSynchronize(g->flag_event);
+    cudaEventDestroy(g->flag_event);
+  }
+  if (g->flag_host) cudaFreeHost(g->flag_host);
+  delete g;
+  return VSV_OK;
+}
+
+vsv_status vsv_default_solver(vsv_solver_params* out, int precision) {
+  if (!out) return VSV_EINVAL;
+  default_solver(out, precision);
+  return VSV_OK;
+}
+
+vsv_status vsv_set_flow(vsv_grid* g, const vsv_flow_params* fp) {
+  if (!g || !fp) return VSV_EINVAL;
+  if (fp->kind < 0 || fp->kind > VSV_QUIESCENT || !(fp->eta > 0))
+    return fail(g, VSV_EINVAL, "invalid flow parameters%s");
+  const bool zper = fp->kind == VSV_COUETTE || fp->kind == VSV_POISEUILLE_PLANAR;
+  if (zper && g->nz > 1 && g->nz % 2) return fail(g, VSV_EINVAL, "periodic z needs even nz%s");
+  g->flow = *fp;
+  const int per[3] = {1, 0, zper ? 1 : 0};
+  g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);
+  vsv_status st = build_base_flow(g);
+  if (st != VSV_OK) return st;
+  g->flow_set = true;
+  g->phi_set = false;
+  return VSV_OK;
+}
+
+vsv_status vsv_set_free_energy(vsv_grid* g, const vsv_fe_params* fe) {
+  if (!g || !fe) return VSV_EINVAL;
+  if ((fe->kind != VSV_CAHN_HILLIARD && fe->kind != VSV_HELFRICH) || !(fe->eps > 0) ||
+      fe->mobility < 0 || fe->k_vol < 0 || fe->k_area < 0)
+    return fail(g, VSV_EINVAL, "invalid free-energy parameters%s");
+  g->fe = *fe;
+  upload_scalar_params(g);
+  if (g->phi_set) g->phase_stale = true;
+  return VSV_OK;
+}
+
+vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
+  if (!g || !sp) return VSV_EINVAL;
+  if (sp->kind != VSV_SOLVER_MG && sp->kind != VSV_SOLVER_SOR) return fail(g, VSV_EINVAL, "bad solver kind%s");
+  if (sp->kind == VSV_SOLVER_SOR && g->prec != VSV_FP64)
+    return fail(g, VSV_EINVAL, "SOR is provided for the FP64 precision only%s");
+  if (sp->nu1 < 0 || sp->nu2 < 0 || sp->nu1 + sp->nu2 < 1 || sp->coarse_sweeps < 1 ||
+      sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->max_levels < 1 || !(sp->tol >= 0))
+    return fail(g, VSV_EINVAL, "invalid solver parameters%s");
+  g->sol = *sp;
+  if (g->flow_set) {
+    const int per[3] = {1, 0, z_periodic(g) ? 1 : 0};
+    g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);
+  }
+  return VSV_OK;
+}
+
+vsv_status vsv_set_phi(vsv_grid* g, const void* phi, int dtype, int on_device) {
+  if (!g || !phi || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64)) return VSV_EINVAL;
+  if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_set_phi%s");
+  g->err.clear();
+  vsv_status st;
+  if (g->prec == VSV_FP64) {
+    st = import_field<double>(g, phi, dtype, on_device, (double*)g->phi[g->cur], g->N);
+    if (st == VSV_OK) st = set_phi_impl<double>(g);
+  } else {
+    st = import_field<float>(g, phi, dtype, on_device, (float*)g->phi[g->cur], g->N);
+    if (st == VSV_OK) st = set_phi_impl<float>(g);
+  }
+  g->time = 0.0;
+  g->steps = 0;
+  if (st == VSV_OK || st == VSV_ENOCONV) g->phi_set = true;
+  return st;
+}
+
+vsv_status vsv_stability_limit(const vsv_grid* g, double* dt_max) {
+  if (!g || !dt_max) return VSV_EINVAL;
+  const double h2 = g->h * g->h;
+  int d = 1 + (g->ny > 1) + (g->nz > 1);
+  if (g->nx > 1) d = 3;
+  const double lam = 4.0 * d / h2;   // largest eigenvalue of -lap
+  const double M = g->fe.mobility;
+  double lim = INFINITY;
+  if (M > 0) {
+    if (g->fe.kind == VSV_CAHN_HILLIARD) {
+      lim = 2.0 / (M * lam * (2.0 + g->fe.sigma * lam));
+    } else {
+      const double e2 = g->fe.eps * g->fe.eps;
+      const double cf = 3.0 * std::sqrt(2.0) * g->fe.kappa / (8.0 * std::pow(g->fe.eps, 3));
+      const double c2 = g->fe.mu_prefactor_half ? cf : 2.0 * cf;
+      const double t = 2.0 + e2 * lam;
+      lim = 2.0 / (M * c2 * lam * t * t);
+    }
+    if (g->fe.k_vol > 0) {
+      const double v = 4.0 / (M * g->fe.k_vol * (double)g->N * g->h * h2);
+      lim = std::min(lim, v);
+    }
+  }
+  *dt_max = lim;
+  return VSV_OK;
+}
+
+vsv_status vsv_step(vsv_grid* g, int nsteps, double dt) {
+  if (!g || nsteps < 0 || !(dt > 0)) return VSV_EINVAL;
+  if (!g->phi_set) return fail(g, VSV_ESTATE, "vsv_set_phi must precede vsv_step%s");
+  double lim;
+  vsv_stability_limit(g, &lim);
+  if (dt > lim) {
+    char buf[128];
+    snprintf(buf, sizeof buf, " (dt %.3g > limit %.3g)", dt, lim);
+    return fail(g, VSV_EUNSTABLE, "time step above the explicit stability bound%s", buf);
+  }
+  // flag of an earlier call, read without waiting if its copy has landed
+  if (g->flag_pending && cudaEventQuery(g->flag_event) == cudaSuccess) {
+    g->flag_pending = false;
+    if (*g->flag_host) return fail(g, VSV_ENONFINITE, "non-finite phi%s");
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    vsv_status st = g->prec == VSV_FP64 ? step_impl<double>(g, dt) : step_impl<float>(g, dt);
+    if (st != VSV_OK) return st;
+  }
+  CKL();
+  if (!g->flag_host) {
+    CK(cudaMallocHost((void**)&g->flag_host, sizeof(int)));
+    CK(cudaEventCreateWithFlags(&g->flag_event, cudaEventDisableTiming));
+  }
+  CK(cudaMemcpyAsync(g->flag_host, &g->S->nonfinite, sizeof(int), cudaMemcpyDeviceToHost,
+                     g->cx.stream));
+  CK(cudaEventRecord(g->flag_event, g->cx.stream));
+  g->flag_pending = true;
+  return VSV_OK;
+}
+
+vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, int on_device,
+                             const vsv_bc* bc, double tol, int max_cycles, int* cycles_out,
+                             double* relres_out) {
+  if (!g || !rhs || !x || !bc || max_cycles < 1 || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64))
+    return VSV_EINVAL;
+  const int per[3] = {bc->periodic[0] ? 1 : 0, bc->periodic[1] ? 1 : 0, bc->periodic[2] ? 1 : 0};
+  const int n[3] = {g->nx, g->ny, g->nz};
+  for (int a = 0; a < 3; ++a)
+    if (per[a] && n[a] > 1 && n[a] % 2) return fail(g, VSV_EINVAL, "periodic axes need even extent%s");
+  if (per[0] && per[1] && per[2]) return fail(g, VSV_EINVAL, "all-periodic problem is singular%s");
+  g->err.clear();
+  std::vector<Level> lv = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels,
+                                       g->mg_nlev_cap);
+  vsv_status st;
+  g->phi_set = false;
+  auto run = [&](auto tag) -> vsv_status {
+    using T = decltype(tag);
+    T* b = (T*)g->f[0];
+    T* xx = (T*)g->f[1];
+    vsv_status s = import_field<T>(g, rhs, dtype, on_device, b, g->N);
+    if (s != VSV_OK) return s;
+    s = import_field<T>(g, x, dtype, on_device, xx, g->N);
+    if (s != VSV_OK) return s;
+    Comp3<T> X{{xx, nullptr, nullptr}};
+    Rhs3<T> R{{b, nullptr, nullptr}, {nullptr, nullptr, nullptr}, (T)1};
+    vsv_status s2 = solve<T>(g, lv, X, R, 1, g->sol.kind, 0, tol, max_cycles, g->sol.check_every,
+                             cycles_out, relres_out);
+    s = export_field<T>(g, xx, dtype, on_device, x, g->N);
+    if (s != VSV_OK) return s;
+    return s2;
+  };
+  if (g->prec == VSV_FP64) st = run(double{});
+  else st = run(float{});
+  return st;
+}
+
+vsv_status vsv_get_field(vsv_grid* g, int field, void* dst, int dtype, int on_device) {
+  if (!g || !dst || field < 0 || field >= VSV_FIELD_COUNT ||
+      (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64))
+    return VSV_EINVAL;
+  if (!g->phi_set) return fail(g, VSV_ESTATE, "no state: call vsv_set_phi first%s");
+  return g->prec == VSV_FP64 ? get_field_impl<double>(g, field, dst, dtype, on_device)
+                             : get_field_impl<float>(g, field, dst, dtype, on_device);
+}
+
+vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int on_device) {
+  if (!g || !src || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64)) return VSV_EINVAL;
+  if (!g->phi_set) return fail(g, VSV_ESTATE, "no state: call vsv_set_phi first%s");
+  void* dst = nullptr;
+  if (field == VSV_FIELD_PHI) dst = g->phi[g->cur];
+  else if (field >= VSV_FIELD_OMEGA_PERT_X && field <= VSV_FIELD_OMEGA_PERT_Z)
+    dst = g->om[field - VSV_FIELD_OMEGA_PERT_X];
+  else if (field >= VSV_FIELD_PSI_PERT_X && field <= VSV_FIELD_PSI_PERT_Z)
+    dst = g->ps[field - VSV_FIELD_PSI_PERT_X];
+  else
+    return fail(g, VSV_EINVAL, "field cannot be set%s");
+  vsv_status st = g->prec == VSV_FP64
+                      ? import_field<double>(g, src, dtype, on_device, (double*)dst, g->N)
+                      : import_field<float>(g, src, dtype, on_device, (float*)dst, g->N);
+  if (st == VSV_OK && field == VSV_FIELD_PHI) g->phase_stale = true;
+  return st;
+}
+
+vsv_status vsv_get_diagnostics(vsv_grid* g, vsv_diag* out) {
+  if (!g || !out) return VSV_EINVAL;
+  if (!g->phi_set) return fail(g, VSV_ESTATE, "no state: call vsv_set_phi first%s");
+  PhaseParams P = phase_params(g);
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    if (g->phase_stale) {
+      refresh_phase<T>(g, 0);
+      g->phase_stale = false;
+    }
+    Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
+    launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+                       comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
+    launch_diag<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->g, V,
+                   comp3<T>(g->om[0], g->om[1], g->om[2]), comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+                   ring3(g->ps_ring), ring3(g->v0d), (T*)nullptr, g->partials, g->red_blocks,
+                   g->dout);
+  };
+  if (g->prec == VSV_FP64) run(double{});
+  else run(float{});
+  CKL();
+  double q[kDiagQ];
+  Scalars hs;
+  CK(cudaMemcpyAsync(q, g->dout, sizeof q, cudaMemcpyDeviceToHost, g->cx.stream));
+  CK(cudaMemcpyAsync(&hs, g->S, sizeof hs, cudaMemcpyDeviceToHost, g->cx.stream));
+  CK(cudaStreamSynchronize(g->cx.stream));
+  const double h3 = g->h * g->h * g->h, eta = g->flow.eta;
+  std::memset(out, 0, sizeof *out);
+  out->time = g->time;
+  out->steps = g->steps;
+  out->volume = hs.V;
+  out->area = hs.A;
+  out->volume0 = hs.V0;
+  out->area0 = hs.A0;
+  out->reduced_volume = hs.A > 0 ? hs.V / (4.0 / 3.0 * M_PI * std::pow(hs.A / (4.0 * M_PI), 1.5)) : 0.0;
+  if (g->fe.kind == VSV_HELFRICH) {
+    const double cf = 3.0 * std::sqrt(2.0) * g->fe.kappa / (8.0 * std::pow(g->fe.eps, 3));
+    out->energy = cf * h3 * q[8];
+  } else {
+    out->energy = h3 * q[8];
+  }
+  out->lambda_v = hs.lambda_v;
+  out->gamma_a = hs.gamma_a;
+  for (int a = 0; a < 3; ++a) out->com[a] = q[4] > 0 ? q[5 + a] / q[4] : 0.0;
+  out->dissipation = 0.5 * eta * h3 * q[0];
+  out->dissipation0 = 0.5 * eta * h3 * q[1];
+  out->resistance_rel = out->dissipation0 > 0 ? (out->dissipation - out->dissipation0) / out->dissipation0 : 0.0;
+  out->omega_dev2 = h3 * q[2];
+  out->psi_dev2 = h3 * q[3];
+  out->max_div_v = q[9];
+  out->max_div_psi = q[10];
+  out->max_sigma_t = q[11];
+  out->last_cycles_omega = g->last_cycles[0];
+  out->last_cycles_psi = g->last_cycles[1];
+  out->last_relres_omega = g->last_relres[0];
+  out->last_relres_psi = g->last_relres[1];
+  out->nonfinite = hs.nonfinite;
+  return VSV_OK;
+}
+
+vsv_status vsv_get_stress_profile(vsv_grid* g, double* out) {
+  if (!g || !out) return VSV_EINVAL;
+  if (!g->phi_set) return fail(g, VSV_ESTATE, "no state: call vsv_set_phi first%s");
+  PhaseParams P = phase_params(g);
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
+    launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+                       comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
+    launch_stress_profile<T>(g->cx, P, V, g->profile);
+  };
+  if (g->prec == VSV_FP64) run(double{});
+  else run(float{});
+  CKL();
+  CK(cudaMemcpyAsync(out, g->profile, g->ny * sizeof(double), cudaMemcpyDeviceToHost, g->cx.stream));
+  CK(cudaStreamSynchronize(g->cx.stream));
+  return VSV_OK;
+}
+
+struct StateHeader {
+  char magic[8];
+  int nx, ny, nz, prec;
+  double V0, A0, time;
+  long long steps;
+};
+
+size_t vsv_state_bytes(const vsv_grid* g) {
+  if (!g) return 0;
+  return sizeof(StateHeader) + (size_t)g->N * g->tsize * 7;
+}
+
+vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes) {
+  if (!g || !dst || bytes < vsv_state_bytes(g)) return VSV_EINVAL;
+  if (!g->phi_set) return fail(g, VSV_ESTATE, "no state: call vsv_set_phi first%s");
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, g->S, sizeof hs, cudaMemcpyDeviceToHost, g->cx.stream));
+  char* p = (char*)dst;
+  StateHeader hd{};
+  std::memcpy(hd.magic, "VSVSTAT", 8);
+  hd.nx = g->nx; hd.ny = g->ny; hd.nz = g->nz; hd.prec = g->prec;
+  const size_t fb = (size_t)g->N * g->tsize;
+  char* q = p + sizeof hd;
+  CK(cudaMemcpyAsync(q, g->phi[g->cur], fb, cudaMemcpyDeviceToHost, g->cx.stream));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(q + fb * (1 + c), g->om[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(q + fb * (4 + c), g->ps[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
+  CK(cudaStreamSynchronize(g->cx.stream));
+  hd.V0 = hs.V0; hd.A0 = hs.A0; hd.time = g->time; hd.steps = g->steps;
+  std::memcpy(p, &hd, sizeof hd);
+  return VSV_OK;
+}
+
+vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes) {
+  if (!g || !src || bytes < vsv_state_bytes(g)) return VSV_EINVAL;
+  if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_set_state%s");
+  StateHeader hd;
+  std::memcpy(&hd, src, sizeof hd);
+  if (std::memcmp(hd.magic, "VSVSTAT", 8) || hd.nx != g->nx || hd.ny != g->ny || hd.nz != g->nz ||
+      hd.prec != g->prec)
+    return fail(g, VSV_EINVAL, "state blob does not match this grid%s");
+  const size_t fb = (size_t)g->N * g->tsize;
+  const char* q = (const char*)src + sizeof hd;
+  CK(cudaMemcpyAsync(g->phi[g->cur], q, fb, cudaMemcpyHostToDevice, g->cx.stream));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(g->om[c], q + fb * (1 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(g->ps[c], q + fb * (4 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
+  double v[2] = {hd.V0, hd.A0};
+  CK(cudaMemcpyAsync(&g->S->V0, v, sizeof v, cudaMemcpyHostToDevice, g->cx.stream));
+  CK(cudaStreamSynchronize(g->cx.stream));
+  g->time = hd.time;
+  g->steps = hd.steps;
+  g->phi_set = true;
+  g->phase_stale = true;
+  return VSV_OK;
+}
+
+vsv_status vsv_check(vsv_grid* g) {
+  if (!g) return VSV_EINVAL;
+  CK(cudaStreamSynchronize(g->cx.stream));
+  CKL();
+  int flag = 0;
+  CK(cudaMemcpy(&flag, &g->S->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) return fail(g, VSV_ENONFINITE, "non-finite phi%s");
+  return VSV_OK;
+}
+
+const char* vsv_last_error(const vsv_grid* g) { return g ? g->err.c_str() : "null handle"; }
+
+int64_t vsv_kernel_launches(const vsv_grid* g) { return g ? g->cx.launches : 0; }
+
+vsv_status vsv_profile_enable(vsv_grid* g, int kclass, int enable) {
+  if (!g || kclass < 0 || kclass >= VSV_KCLASS_COUNT) return VSV_EINVAL;
+  if (g->cx.ev.empty()) {
+    g->cx.ev.resize(2 * 8192);
+    for (auto& e : g->cx.ev) CK(cudaEventCreate(&e));
+  }
+  g->cx.prof_class = enable ? kclass : -1;
+  g->cx.ev_used = 0;
+  g->cx.prof_launches = 0;
+  return VSV_OK;
+}
+
+vsv_status vsv_profile_read(vsv_grid* g, int kclass, double* total_ms, int64_t* launches) {
+  if (!g || !total_ms || !launches) return VSV_EINVAL;
+  if (g->cx.prof_class != kclass) return fail(g, VSV_ESTATE, "profiling not enabled for this class%s");
+  CK(cudaStreamSynchronize(g->cx.stream));
+  double t = 0.0;
+  for (int i = 0; i < g->cx.ev_used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, g->cx.ev[2 * i], g->cx.ev[2 * i + 1]));
+    t += ms;
+  }
+  *total_ms = t;
+  *launches = g->cx.prof_launches;
+  return VSV_OK;
+}
+
+}  // extern "C"

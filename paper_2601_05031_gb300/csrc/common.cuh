@@ -1,0 +1,96 @@
+// Shared device/host definitions of the vorticity--stream-vector library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace vsv {
+
+constexpr int kMaxLevels = 16;
+constexpr int kBlock = 256;
+
+// One grid level of a Poisson problem (the fine grid is level 0).
+// Dirichlet walls sit on the ghost nodes of the fine grid; on a coarse level
+// l the wall lies between the ghost and the first cell, and the ghost value
+// is the linear extrapolation through zero at the wall:
+//   ghost = -alpha_l * (adjacent cell),  alpha_l = (2^l - 1) / (2^l + 1).
+struct Level {
+  int n[3];          // nx, ny, nz
+  int per[3];        // 1 = periodic axis
+  int act[3];        // 0 for a periodic axis of extent 1 (no coupling)
+  double alpha;      // Dirichlet closure coefficient (0 on the fine level)
+  double inv_h2;     // 1 / h_l^2
+  float alphaf;      // the same in FP32 (FP32 kernels never touch FP64 units)
+  float inv_h2f;
+  __host__ __device__ long long cells() const { return (long long)n[0] * n[1] * n[2]; }
+};
+
+template <class T> __host__ __device__ inline T lv_alpha(const Level& L);
+template <> __host__ __device__ inline float lv_alpha<float>(const Level& L) { return L.alphaf; }
+template <> __host__ __device__ inline double lv_alpha<double>(const Level& L) { return L.alpha; }
+template <class T> __host__ __device__ inline T lv_ih2(const Level& L);
+template <> __host__ __device__ inline float lv_ih2<float>(const Level& L) { return L.inv_h2f; }
+template <> __host__ __device__ inline double lv_ih2<double>(const Level& L) { return L.inv_h2; }
+
+// Up to three components processed by one launch (gridDim.y = component).
+template <class T>
+struct Comp3 {
+  T* p[3];
+};
+
+// Right-hand side b = beta * B[c] + S[j + k * ny] (S may be null).
+template <class T>
+struct Rhs3 {
+  const T* B[3];
+  const T* S[3];
+  T beta;
+};
+
+// Device scalars written by reductions and read by later kernels.
+struct Scalars {
+  double V, A, V0, A0;
+  double lambda_v, gamma_a;
+  double k_vol, k_area, eps;   // copies of the penalty parameters
+  double h3;
+  double rnorm2[3], bnorm2[3];
+  float lambda_vf, gamma_af;   // FP32 copies read by the FP32 kernels
+  int nonfinite;
+  int pad;
+};
+
+// ---------------------------------------------------------------- device helpers
+__host__ __device__ inline long long lin(int i, int j, int k, int nx, int ny) {
+  return ((long long)k * ny + j) * nx + i;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Cascaded (compensated) summation accumulator, Ogita-Rump-Oishi "Sum2":
+// the running sum is kept as hi + lo with every rounding error of hi
+// collected in lo.
+struct CascadeSum {
+  float hi, lo;
+  __device__ __forceinline__ CascadeSum(float a) : hi(a), lo(0.f) {}
+  __device__ __forceinline__ void add(float t) {
+    float s, e;
+    two_sum(hi, t, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  // exact product of a float by a small integer constant (error term by FMA)
+  __device__ __forceinline__ void add_scaled(float c, float x) {
+    float p = __fmul_rn(c, x);
+    float pe = __fmaf_rn(c, x, -p);
+    add(p);
+    lo = __fadd_rn(lo, pe);
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
+};
+
+}  // namespace vsv

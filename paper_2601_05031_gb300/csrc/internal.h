@@ -1,0 +1,156 @@
+// Host-side internals shared by the kernel files and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/vsv.h"
+#include "common.cuh"
+
+namespace vsv {
+
+// Launch context: the caller's stream, a launch counter and optional CUDA
+// event brackets around every launch of one kernel class.
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  long long launches = 0;
+  int prof_class = -1;
+  std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+  int ev_used = 0;               // pairs recorded since enable
+  long long prof_launches = 0;
+  int pending = 0;
+
+  bool match(int kclass) const {
+    if (prof_class < 0 || kclass < 0) return false;
+    if (prof_class == kclass) return true;
+    return prof_class == VSV_KCLASS_SMOOTH && kclass == VSV_KCLASS_SMOOTH_FINE;
+  }
+  void before(int kclass) {
+    ++launches;
+    pending = 0;
+    if (match(kclass) && 2 * ev_used + 1 < (int)ev.size()) {
+      cudaEventRecord(ev[2 * ev_used], stream);
+      pending = 1;
+    }
+  }
+  void after(int kclass) {
+    if (pending) {
+      cudaEventRecord(ev[2 * ev_used + 1], stream);
+      ++ev_used;
+      ++prof_launches;
+      pending = 0;
+    }
+  }
+};
+
+// FP64 block reduction (all threads get the block total); blockDim.x must be a
+// multiple of 32 and at most 1024.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red_buf[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red_buf[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double t = (threadIdx.x < nw) ? red_buf[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __syncthreads();
+  if (threadIdx.x == 0) red_buf[0] = t;
+  __syncthreads();
+  const double r = red_buf[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double redm_buf[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) redm_buf[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double t = (threadIdx.x < nw) ? redm_buf[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+  __syncthreads();
+  if (threadIdx.x == 0) redm_buf[0] = t;
+  __syncthreads();
+  const double r = redm_buf[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------- Poisson launchers (mg.cu)
+template <class T>
+void launch_rb_sweep(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, int color,
+                     double omega, double h2, int kclass);
+template <class T>
+void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Rhs3<T> R,
+                           Comp3<T> RC, int ncomp, bool exact);
+template <class T>
+void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Comp3<T> E, int ncomp);
+template <class T>
+void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp);
+template <class T>
+bool launch_coarse_solve(Ctx& cx, const Level& L, Comp3<T> E, Comp3<T> R, int ncomp, int sweeps,
+                         double h2);
+template <class T>
+void launch_resid_norm(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, bool exact,
+                       double* partials, int nblocks, Scalars* S);
+
+// ---------------------------------------------------------------- phase-field (phase.cu)
+struct PhaseParams {
+  int nx, ny, nz, zper;
+  double h, inv_h, inv_h2;
+  int fe_kind;
+  double sigma, eps, cf2;       // cf2 = prefactor of the Helfrich mu
+  double mobility, inv_eta;
+  // wall velocity on the wall nodes: [0] y = 0 wall, [1] y = H, [2] z = 0, [3] z = H
+  double vwall[4][3];
+};
+
+template <class T>
+void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Comp3<T> psi,
+                       Comp3<T> v0, const Scalars* S, T dt, T* phi_out);
+template <class T>
+void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, double* partials, int nblocks,
+                      Scalars* S, int init);
+template <class T>
+void launch_mu(Ctx& cx, const PhaseParams& P, const T* phi, T* g, T* mu, const Scalars* S);
+template <class T>
+void launch_source(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Comp3<T> s_omega,
+                   Comp3<T> f);
+template <class T>
+void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> v0, Comp3<T> v);
+// Diagnostic partial sums; out has kDiagQ doubles per block.
+constexpr int kDiagQ = 16;
+template <class T>
+void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* g, Comp3<T> vel,
+                 Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0_ring,
+                 Comp3<const double> v0d, T* sigma_t, double* partials, int nblocks, double* out);
+template <class T>
+void launch_stress_profile(Ctx& cx, const PhaseParams& P, Comp3<T> vel, double* out);
+template <class Tin, class Tout>
+void launch_convert(Ctx& cx, const Tin* in, Tout* out, long long n);
+template <class T>
+void launch_full_field(Ctx& cx, const PhaseParams& P, const T* pert, const double* table2d,
+                       int ring, T* out);
+template <class T>
+void launch_scale_copy(Ctx& cx, const T* in, T* out, long long n, double a);
+
+// base-flow helpers (FP64 2-D tables; phase.cu)
+void launch_duct_ring(Ctx& cx, int ny, int nz, double h, const double* u0, const double* chi,
+                      double* om_ring_y, double* om_ring_z, double* ps_ring_y, double* ps_ring_z);
+void launch_ring_boundary_rhs(Ctx& cx, int ny, int nz, double h, const double* ring, double scale_in,
+                              const double* in, double* out);
+void launch_ring_fill_interior(Ctx& cx, int ny, int nz, const double* interior, double* ring);
+void launch_base_derived(Ctx& cx, int ny, int nz, int zper, double h, const double* om_ring[3],
+                         const double* ps_ring[3], double* v0[3], double* s_om[3], double* s_ps[3]);
+double device_max_abs(Ctx& cx, const double* x, long long n, double* scratch);
+void launch_fill(Ctx& cx, double* x, long long n, double v);
+
+}  // namespace vsv

@@ -1,0 +1,722 @@
+// Phase-field kernels: explicit phi update (eq. gen2), chemical potentials
+// (eq. 31 Cahn-Hilliard; eq. 30 / SM eq. 35 Helfrich), vorticity source
+// (eq. gen1), volume / area reductions (SM eqs. 32, 37-38), velocity
+// v = curl psi (eq. vecpot), the observables of the in-plane-shear and
+// results sections, and the FP64 base-flow tables of the channel flows
+// (boundary-conditions section).
+//
+// Fields are [nz][ny][nx] without halos.  Scalars (phi, mu, g) use the
+// face mirror at walls and wrap on periodic axes; the flow perturbation
+// psi' = psi - psi0 is zero on the wall nodes.
+#include <cmath>
+
+#include "internal.h"
+
+namespace vsv {
+
+__device__ __forceinline__ int mirror_idx(int j, int n) {
+  return j < 0 ? -1 - j : (j >= n ? 2 * n - 1 - j : j);
+}
+__device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <class T>
+struct ScalarView {  // periodic x, mirror y, mirror / periodic z
+  const T* __restrict__ a;
+  int nx, ny, nz, zper;
+  __device__ __forceinline__ T operator()(int i, int j, int k) const {
+    i = wrap_idx(i, nx);
+    j = mirror_idx(j, ny);
+    k = zper ? wrap_idx(k, nz) : mirror_idx(k, nz);
+    return a[lin(i, j, k, nx, ny)];
+  }
+};
+
+template <class T>
+struct PertView {  // periodic x, zero on the wall nodes
+  const T* __restrict__ a;
+  int nx, ny, nz, zper;
+  __device__ __forceinline__ T operator()(int i, int j, int k) const {
+    i = wrap_idx(i, nx);
+    if (zper) k = wrap_idx(k, nz);
+    if (j < 0 || j >= ny || k < 0 || k >= nz) return (T)0;
+    return a[lin(i, j, k, nx, ny)];
+  }
+};
+
+template <class T, class V>
+__device__ __forceinline__ T lap7(const V& f, int i, int j, int k, T ih2) {
+  return (f(i + 1, j, k) + f(i - 1, j, k) + f(i, j + 1, k) + f(i, j - 1, k) + f(i, j, k + 1) +
+          f(i, j, k - 1) - (T)6 * f(i, j, k)) * ih2;
+}
+
+__device__ __forceinline__ void cell_of(long long t, int nx, int ny, int& i, int& j, int& k) {
+  i = (int)(t % nx);
+  const long long q = t / nx;
+  j = (int)(q % ny);
+  k = (int)(q / ny);
+}
+
+template <class T> __device__ __forceinline__ T sc_lambda(const Scalars* S);
+template <> __device__ __forceinline__ float sc_lambda<float>(const Scalars* S) { return S->lambda_vf; }
+template <> __device__ __forceinline__ double sc_lambda<double>(const Scalars* S) { return S->lambda_v; }
+template <class T> __device__ __forceinline__ T sc_gamma(const Scalars* S);
+template <> __device__ __forceinline__ float sc_gamma<float>(const Scalars* S) { return S->gamma_af; }
+template <> __device__ __forceinline__ double sc_gamma<double>(const Scalars* S) { return S->gamma_a; }
+
+static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// ---------------------------------------------------------------- phi update (eq. gen2)
+// phi^{n+1} = phi^n + dt [ M (lap mu + lambda_V) - v . grad phi ],
+// v = v0(y, z) + curl psi' (central differences).
+template <class T>
+__global__ void k_phi_update(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ mu,
+                             Comp3<T> psi, Comp3<T> v0, Scalars* S, T dt, T* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  const T ih2 = (T)P.inv_h2, hih = (T)(0.5 * P.inv_h);
+  ScalarView<T> M{mu, P.nx, P.ny, P.nz, P.zper};
+  ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
+  PertView<T> X{psi.p[0], P.nx, P.ny, P.nz, P.zper};
+  PertView<T> Y{psi.p[1], P.nx, P.ny, P.nz, P.zper};
+  PertView<T> Z{psi.p[2], P.nx, P.ny, P.nz, P.zper};
+  const T lmu = lap7<T>(M, i, j, k, ih2);
+  const T gx = (F(i + 1, j, k) - F(i - 1, j, k)) * hih;
+  const T gy = (F(i, j + 1, k) - F(i, j - 1, k)) * hih;
+  const T gz = (F(i, j, k + 1) - F(i, j, k - 1)) * hih;
+  const long long jk = j + (long long)k * P.ny;
+  const T vx = v0.p[0][jk] + ((Z(i, j + 1, k) - Z(i, j - 1, k)) - (Y(i, j, k + 1) - Y(i, j, k - 1))) * hih;
+  const T vy = v0.p[1][jk] + ((X(i, j, k + 1) - X(i, j, k - 1)) - (Z(i + 1, j, k) - Z(i - 1, j, k))) * hih;
+  const T vz = v0.p[2][jk] + ((Y(i + 1, j, k) - Y(i - 1, j, k)) - (X(i, j + 1, k) - X(i, j - 1, k))) * hih;
+  const T rate = (T)P.mobility * (lmu + sc_lambda<T>(S)) - (vx * gx + vy * gy + vz * gz);
+  const T v = phi[t] + dt * rate;
+  out[t] = v;
+  if (!isfinite(v)) atomicOr(&S->nonfinite, 1);
+}
+
+// ---------------------------------------------------------------- reductions (SM eqs. 32, 37)
+// Per-block partial sums of sum(phi) and of the area density
+// 3/(2 sqrt2) [eps/2 |grad phi|^2 + (phi^2 - 1)^2 / (4 eps)].
+template <class T>
+__global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, double* partials) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
+  const T hih = (T)(0.5 * P.inv_h);
+  const T c_a = (T)(3.0 / (2.0 * 1.4142135623730951));
+  const T he = (T)(0.5 * P.eps), q = (T)(0.25 / P.eps);
+  double sphi = 0.0, sarea = 0.0;
+  if constexpr (std::is_same<T, float>::value) {
+    CascadeSum cp(0.f), ca(0.f);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+      int i, j, k;
+      cell_of(t, P.nx, P.ny, i, j, k);
+      const float f = phi[t];
+      const float gx = (F(i + 1, j, k) - F(i - 1, j, k)) * hih;
+      const float gy = (F(i, j + 1, k) - F(i, j - 1, k)) * hih;
+      const float gz = (F(i, j, k + 1) - F(i, j, k - 1)) * hih;
+      const float w = f * f - 1.f;
+      cp.add(f);
+      ca.add(c_a * (he * (gx * gx + gy * gy + gz * gz) + w * w * q));
+    }
+    sphi = (double)cp.hi + (double)cp.lo;
+    sarea = (double)ca.hi + (double)ca.lo;
+  } else {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+      int i, j, k;
+      cell_of(t, P.nx, P.ny, i, j, k);
+      const double f = phi[t];
+      const double gx = (F(i + 1, j, k) - F(i - 1, j, k)) * hih;
+      const double gy = (F(i, j + 1, k) - F(i, j - 1, k)) * hih;
+      const double gz = (F(i, j, k + 1) - F(i, j, k - 1)) * hih;
+      const double w = f * f - 1.0;
+      sphi += f;
+      sarea += c_a * (he * (gx * gx + gy * gy + gz * gz) + w * w * q);
+    }
+  }
+  sphi = block_sum(sphi);
+  sarea = block_sum(sarea);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = sphi;
+    partials[2 * blockIdx.x + 1] = sarea;
+  }
+}
+
+// Fixed-order total of the partials; sets V, A and the multipliers
+// lambda_V = K_V (V - V0), gamma_A = K_A (A - A0) 3 eps / (2 sqrt 2).
+__global__ void k_va_finalize(const double* partials, int nblocks, long long ncells, Scalars* S,
+                              int init) {
+  double sp = 0.0, sa = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    sp += partials[2 * b];
+    sa += partials[2 * b + 1];
+  }
+  sp = block_sum(sp);
+  sa = block_sum(sa);
+  if (threadIdx.x == 0) {
+    const double V = 0.5 * S->h3 * ((double)ncells - sp);
+    const double A = S->h3 * sa;
+    S->V = V;
+    S->A = A;
+    if (init) {
+      S->V0 = V;
+      S->A0 = A;
+    }
+    S->lambda_v = S->k_vol * (V - S->V0);
+    S->gamma_a = S->k_area * (A - S->A0) * 3.0 * S->eps / (2.0 * 1.4142135623730951);
+    S->lambda_vf = (float)S->lambda_v;
+    S->gamma_af = (float)S->gamma_a;
+  }
+}
+
+// ---------------------------------------------------------------- chemical potential
+// Helfrich: g = phi^3 - phi - eps^2 lap phi.
+template <class T>
+__global__ void k_helfrich_g(PhaseParams P, const T* __restrict__ phi, T* __restrict__ g) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
+  const T f = phi[t];
+  g[t] = f * f * f - f - (T)(P.eps * P.eps) * lap7<T>(F, i, j, k, (T)P.inv_h2);
+}
+
+// CH (fe_kind 0): mu = phi^3 - phi - sigma lap phi.
+// Helfrich: mu = cf2 [(3 phi^2 - 1) g - eps^2 lap g] - gamma_A lap phi.
+template <class T>
+__global__ void k_mu(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ g,
+                     const Scalars* S, T* __restrict__ mu) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  const T ih2 = (T)P.inv_h2;
+  ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
+  const T f = phi[t];
+  const T lphi = lap7<T>(F, i, j, k, ih2);
+  if (P.fe_kind == VSV_CAHN_HILLIARD) {
+    mu[t] = f * f * f - f - (T)P.sigma * lphi;
+  } else {
+    ScalarView<T> G{g, P.nx, P.ny, P.nz, P.zper};
+    const T lg = lap7<T>(G, i, j, k, ih2);
+    mu[t] = (T)P.cf2 * (((T)3 * f * f - (T)1) * g[t] - (T)(P.eps * P.eps) * lg) -
+            sc_gamma<T>(S) * lphi;
+  }
+}
+
+// ---------------------------------------------------------------- vorticity source (eq. gen1)
+// f = grad phi x grad mu / eta - s_omega(y, z)   (rhs of lap omega' = f - s_omega)
+template <class T>
+__global__ void k_source(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ mu,
+                         Comp3<T> s_omega, Comp3<T> f) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  const T hih = (T)(0.5 * P.inv_h), ie = (T)P.inv_eta;
+  ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
+  ScalarView<T> M{mu, P.nx, P.ny, P.nz, P.zper};
+  const T ax = (F(i + 1, j, k) - F(i - 1, j, k)) * hih;
+  const T ay = (F(i, j + 1, k) - F(i, j - 1, k)) * hih;
+  const T az = (F(i, j, k + 1) - F(i, j, k - 1)) * hih;
+  const T bx = (M(i + 1, j, k) - M(i - 1, j, k)) * hih;
+  const T by = (M(i, j + 1, k) - M(i, j - 1, k)) * hih;
+  const T bz = (M(i, j, k + 1) - M(i, j, k - 1)) * hih;
+  const long long jk = j + (long long)k * P.ny;
+  f.p[0][t] = (ay * bz - az * by) * ie - s_omega.p[0][jk];
+  f.p[1][t] = (az * bx - ax * bz) * ie - s_omega.p[1][jk];
+  f.p[2][t] = (ax * by - ay * bx) * ie - s_omega.p[2][jk];
+}
+
+// ---------------------------------------------------------------- velocity (eq. vecpot)
+template <class T>
+__global__ void k_velocity(PhaseParams P, Comp3<T> psi, Comp3<T> v0, Comp3<T> v) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  const T hih = (T)(0.5 * P.inv_h);
+  PertView<T> X{psi.p[0], P.nx, P.ny, P.nz, P.zper};
+  PertView<T> Y{psi.p[1], P.nx, P.ny, P.nz, P.zper};
+  PertView<T> Z{psi.p[2], P.nx, P.ny, P.nz, P.zper};
+  const long long jk = j + (long long)k * P.ny;
+  v.p[0][t] = v0.p[0][jk] + ((Z(i, j + 1, k) - Z(i, j - 1, k)) - (Y(i, j, k + 1) - Y(i, j, k - 1))) * hih;
+  v.p[1][t] = v0.p[1][jk] + ((X(i, j, k + 1) - X(i, j, k - 1)) - (Z(i + 1, j, k) - Z(i - 1, j, k))) * hih;
+  v.p[2][t] = v0.p[2][jk] + ((Y(i + 1, j, k) - Y(i - 1, j, k)) - (X(i, j + 1, k) - X(i, j - 1, k))) * hih;
+}
+
+// ---------------------------------------------------------------- observables
+// Velocity (materialised) with the no-slip wall velocity on the wall nodes.
+template <class T>
+struct VelView {
+  const T* __restrict__ a;
+  int nx, ny, nz, zper, comp;
+  const PhaseParams* P;
+  __device__ __forceinline__ double operator()(int i, int j, int k) const {
+    i = wrap_idx(i, nx);
+    if (zper) k = wrap_idx(k, nz);
+    if (j < 0) return P->vwall[0][comp];
+    if (j >= ny) return P->vwall[1][comp];
+    if (k < 0) return P->vwall[2][comp];
+    if (k >= nz) return P->vwall[3][comp];
+    return (double)a[lin(i, j, k, nx, ny)];
+  }
+};
+
+// Base-flow velocity table (x-invariant) with the same wall values.
+struct V0View {
+  const double* a;
+  int ny, nz, zper, comp;
+  const PhaseParams* P;
+  __device__ __forceinline__ double operator()(int j, int k) const {
+    if (zper) k = wrap_idx(k, nz);
+    if (j < 0) return P->vwall[0][comp];
+    if (j >= ny) return P->vwall[1][comp];
+    if (k < 0) return P->vwall[2][comp];
+    if (k >= nz) return P->vwall[3][comp];
+    return a[j + (long long)k * ny];
+  }
+};
+
+// q: 0 dissipation integrand, 1 body-free dissipation integrand, 2 |omega'|^2,
+// 3 |psi'|^2, 4 w = (1-phi)/2, 5..7 w x, w y, w z, 8 energy density,
+// 9 max |div v|, 10 max |div psi|, 11 max sigma_t.
+template <class T>
+__global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ g,
+                       Comp3<T> vel, Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0r,
+                       Comp3<const double> v0d, T* sigma_t, double* partials) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  double q[kDiagQ];
+  for (int a = 0; a < kDiagQ; ++a) q[a] = 0.0;
+  const double hih = 0.5 * P.inv_h, eta = 1.0 / P.inv_eta, h = P.h;
+  const int ny2 = P.ny + 2;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(t, P.nx, P.ny, i, j, k);
+    double G[3][3], G0[3][3];
+    for (int c = 0; c < 3; ++c) {
+      VelView<T> V{vel.p[c], P.nx, P.ny, P.nz, P.zper, c, &P};
+      G[c][0] = (V(i + 1, j, k) - V(i - 1, j, k)) * hih;
+      G[c][1] = (V(i, j + 1, k) - V(i, j - 1, k)) * hih;
+      G[c][2] = (V(i, j, k + 1) - V(i, j, k - 1)) * hih;
+      V0View W{v0d.p[c], P.ny, P.nz, P.zper, c, &P};
+      G0[c][0] = 0.0;
+      G0[c][1] = (W(j + 1, k) - W(j - 1, k)) * hih;
+      G0[c][2] = (W(j, k + 1) - W(j, k - 1)) * hih;
+    }
+    double d = 0.0, d0 = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double e = G[a][b] + G[b][a], e0 = G0[a][b] + G0[b][a];
+        d += e * e;
+        d0 += e0 * e0;
+      }
+    q[0] += d;
+    q[1] += d0;
+    double o2 = 0.0, p2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double o = omega.p[c][t], p = psi.p[c][t];
+      o2 += o * o;
+      p2 += p * p;
+    }
+    q[2] += o2;
+    q[3] += p2;
+    const double f = phi[t];
+    const double w = 0.5 * (1.0 - f);
+    q[4] += w;
+    q[5] += w * (i + 0.5) * h;
+    q[6] += w * (j + 1.0) * h;
+    q[7] += w * (P.zper ? (k + 0.5) : (k + 1.0)) * h;
+    if (P.fe_kind == VSV_HELFRICH) {
+      const double gg = g[t];
+      q[8] += gg * gg;
+    } else {
+      ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
+      double e = 0.25 * (f * f - 1.0) * (f * f - 1.0);
+      const double dx = ((double)F(i + 1, j, k) - f) * P.inv_h;
+      double faces = dx * dx;
+      if (j + 1 < P.ny) {
+        const double dy = ((double)F(i, j + 1, k) - f) * P.inv_h;
+        faces += dy * dy;
+      }
+      if (P.zper || k + 1 < P.nz) {
+        const double dz = ((double)F(i, j, k + 1) - f) * P.inv_h;
+        faces += dz * dz;
+      }
+      q[8] += e + 0.5 * P.sigma * faces;
+    }
+    q[9] = fmax(q[9], fabs(G[0][0] + G[1][1] + G[2][2]));
+    // div psi with psi = psi0(y, z) + psi'; psi0 ring table holds the wall data
+    PertView<T> PX{psi.p[0], P.nx, P.ny, P.nz, P.zper};
+    PertView<T> PY{psi.p[1], P.nx, P.ny, P.nz, P.zper};
+    PertView<T> PZ{psi.p[2], P.nx, P.ny, P.nz, P.zper};
+    auto r0 = [&](int c, int jj, int kk) -> double {
+      if (P.zper) kk = wrap_idx(kk, P.nz);
+      return psi0r.p[c][(jj + 1) + (long long)(kk + 1) * ny2];
+    };
+    const double dpx = ((double)PX(i + 1, j, k) - (double)PX(i - 1, j, k)) * hih;
+    const double dpy = ((double)PY(i, j + 1, k) - (double)PY(i, j - 1, k) + r0(1, j + 1, k) -
+                        r0(1, j - 1, k)) * hih;
+    const double dpz = ((double)PZ(i, j, k + 1) - (double)PZ(i, j, k - 1) + r0(2, j, k + 1) -
+                        r0(2, j, k - 1)) * hih;
+    q[10] = fmax(q[10], fabs(dpx + dpy + dpz));
+    const double sxy = eta * (G[0][1] + G[1][0]);
+    const double syz = eta * (G[1][2] + G[2][1]);
+    const double sxz = eta * (G[0][2] + G[2][0]);
+    const double st = sqrt(sxy * sxy + syz * syz + sxz * sxz);
+    q[11] = fmax(q[11], st);
+    if (sigma_t) sigma_t[t] = (T)st;
+  }
+  for (int a = 0; a < 9; ++a) {
+    const double s = block_sum(q[a]);
+    if (threadIdx.x == 0) partials[(long long)blockIdx.x * kDiagQ + a] = s;
+  }
+  for (int a = 9; a < 12; ++a) {
+    const double s = block_max(q[a]);
+    if (threadIdx.x == 0) partials[(long long)blockIdx.x * kDiagQ + a] = s;
+  }
+}
+
+__global__ void k_diag_finalize(const double* partials, int nblocks, double* out) {
+  for (int a = 0; a < 12; ++a) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+      const double v = partials[(long long)b * kDiagQ + a];
+      s = (a < 9) ? s + v : fmax(s, v);
+    }
+    s = (a < 9) ? block_sum(s) : block_max(s);
+    if (threadIdx.x == 0) out[a] = s;
+  }
+}
+
+// <sigma_xy>(y): one block per y row, fixed-order sum over x and z.
+template <class T>
+__global__ void k_stress_profile(PhaseParams P, Comp3<T> vel, double* out) {
+  const int j = blockIdx.x;
+  const double hih = 0.5 * P.inv_h, eta = 1.0 / P.inv_eta;
+  VelView<T> VX{vel.p[0], P.nx, P.ny, P.nz, P.zper, 0, &P};
+  VelView<T> VY{vel.p[1], P.nx, P.ny, P.nz, P.zper, 1, &P};
+  double s = 0.0;
+  const long long m = (long long)P.nx * P.nz;
+  for (long long t = threadIdx.x; t < m; t += blockDim.x) {
+    const int i = (int)(t % P.nx), k = (int)(t / P.nx);
+    const double dvx_dy = (VX(i, j + 1, k) - VX(i, j - 1, k)) * hih;
+    const double dvy_dx = (VY(i + 1, j, k) - VY(i - 1, j, k)) * hih;
+    s += eta * (dvx_dy + dvy_dx);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[j] = s / (double)m;
+}
+
+// ---------------------------------------------------------------- small utilities
+template <class Tin, class Tout>
+__global__ void k_convert(const Tin* __restrict__ in, Tout* __restrict__ out, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (Tout)in[t];
+}
+
+// out = pert + table(y, z); ring = 1: table in ring layout ((ny+2) x (nz+2)).
+template <class T>
+__global__ void k_full_field(PhaseParams P, const T* __restrict__ pert, const double* __restrict__ tab,
+                             int ring, T* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  const double b = ring ? tab[(j + 1) + (long long)(k + 1) * (P.ny + 2)] : tab[j + (long long)k * P.ny];
+  out[t] = (T)((double)pert[t] + b);
+}
+
+template <class T>
+__global__ void k_scale_copy(const T* __restrict__ in, T* __restrict__ out, long long n, T a) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = a * in[t];
+}
+
+// ---------------------------------------------------------------- base-flow tables (FP64)
+// Ring layout: entry (j, k), j in [-1, ny], k in [-1, nz], at (j+1) + (k+1)(ny+2).
+__device__ __forceinline__ long long ring_at(int j, int k, int ny) {
+  return (j + 1) + (long long)(k + 1) * (ny + 2);
+}
+
+// Duct wall data from u0 and chi (interior layout j + k ny): normal
+// derivative on a wall node by (4 f_1 - f_2) / (2h) (f = 0 on the wall),
+// tangential derivatives zero.
+__global__ void k_duct_ring(int ny, int nz, double h, const double* u0, const double* chi,
+                            double* omy, double* omz, double* psy, double* psz) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const double ih = 1.0 / (2.0 * h);
+  if (t < nz) {  // y walls at row k = t
+    const int k = t;
+    const double* u = u0 + (long long)k * ny;
+    const double* c = chi + (long long)k * ny;
+    const double du_lo = (4.0 * u[0] - u[1]) * ih, du_hi = -(4.0 * u[ny - 1] - u[ny - 2]) * ih;
+    const double dc_lo = (4.0 * c[0] - c[1]) * ih, dc_hi = -(4.0 * c[ny - 1] - c[ny - 2]) * ih;
+    omz[ring_at(-1, k, ny)] = -du_lo;
+    omz[ring_at(ny, k, ny)] = -du_hi;
+    psz[ring_at(-1, k, ny)] = dc_lo;
+    psz[ring_at(ny, k, ny)] = dc_hi;
+    omy[ring_at(-1, k, ny)] = 0.0;
+    omy[ring_at(ny, k, ny)] = 0.0;
+    psy[ring_at(-1, k, ny)] = 0.0;
+    psy[ring_at(ny, k, ny)] = 0.0;
+  }
+  if (t < ny) {  // z walls at column j = t
+    const int j = t;
+    const double el = (4.0 * u0[j] - u0[j + ny]) * ih;
+    const double eh = -(4.0 * u0[j + (long long)(nz - 1) * ny] - u0[j + (long long)(nz - 2) * ny]) * ih;
+    const double cl = (4.0 * chi[j] - chi[j + ny]) * ih;
+    const double ch = -(4.0 * chi[j + (long long)(nz - 1) * ny] - chi[j + (long long)(nz - 2) * ny]) * ih;
+    omy[ring_at(j, -1, ny)] = el;
+    omy[ring_at(j, nz, ny)] = eh;
+    psy[ring_at(j, -1, ny)] = -cl;
+    psy[ring_at(j, nz, ny)] = -ch;
+    omz[ring_at(j, -1, ny)] = 0.0;
+    omz[ring_at(j, nz, ny)] = 0.0;
+    psz[ring_at(j, -1, ny)] = 0.0;
+    psz[ring_at(j, nz, ny)] = 0.0;
+  }
+}
+
+// out = scale * in - (wall-node contribution of `ring` to the 2-D
+// Laplacian), both walls in y and z (the duct section).
+__global__ void k_ring_rhs(int ny, int nz, double h, const double* ring, double scale,
+                           const double* in, double* out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ny * nz) return;
+  const int j = (int)(t % ny), k = (int)(t / ny);
+  double b = 0.0;
+  if (j == 0) b += ring[ring_at(-1, k, ny)];
+  if (j == ny - 1) b += ring[ring_at(ny, k, ny)];
+  if (k == 0) b += ring[ring_at(j, -1, ny)];
+  if (k == nz - 1) b += ring[ring_at(j, nz, ny)];
+  out[t] = (in ? scale * in[t] : 0.0) - b / (h * h);
+}
+
+__global__ void k_ring_fill(int ny, int nz, const double* interior, double* ring) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ny * nz) return;
+  const int j = (int)(t % ny), k = (int)(t / ny);
+  ring[ring_at(j, k, ny)] = interior[t];
+}
+
+// v0 = curl psi0 (x-invariant), s_omega = lap omega0, s_psi = lap psi0 + omega0,
+// all on the interior (y, z) cells from ring tables.
+__global__ void k_base_derived(int ny, int nz, int zper, double h, Comp3<const double> om,
+                               Comp3<const double> ps, Comp3<double> v0, Comp3<double> som,
+                               Comp3<double> sps) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ny * nz) return;
+  const int j = (int)(t % ny), k = (int)(t / ny);
+  auto at = [&](const double* r, int jj, int kk) -> double {
+    if (zper) kk = wrap_idx(kk, nz);
+    return r[ring_at(jj, kk, ny)];
+  };
+  const double hih = 0.5 / h, ih2 = 1.0 / (h * h);
+  const double* px = ps.p[0];
+  const double* py = ps.p[1];
+  const double* pz = ps.p[2];
+  v0.p[0][t] = ((at(pz, j + 1, k) - at(pz, j - 1, k)) - (at(py, j, k + 1) - at(py, j, k - 1))) * hih;
+  v0.p[1][t] = (at(px, j, k + 1) - at(px, j, k - 1)) * hih;
+  v0.p[2][t] = -(at(px, j + 1, k) - at(px, j - 1, k)) * hih;
+  for (int c = 0; c < 3; ++c) {
+    const double* o = om.p[c];
+    const double* p = ps.p[c];
+    const double lo = (at(o, j + 1, k) + at(o, j - 1, k) + at(o, j, k + 1) + at(o, j, k - 1) -
+                       4.0 * at(o, j, k)) * ih2;
+    const double lp = (at(p, j + 1, k) + at(p, j - 1, k) + at(p, j, k + 1) + at(p, j, k - 1) -
+                       4.0 * at(p, j, k)) * ih2;
+    som.p[c][t] = lo;
+    sps.p[c][t] = lp + at(o, j, k);
+  }
+}
+
+__global__ void k_max_abs(const double* x, long long n, double* out) {
+  double m = 0.0;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) m = fmax(m, fabs(x[t]));
+  m = block_max(m);
+  if (threadIdx.x == 0) *out = m;
+}
+
+__global__ void k_fill(double* x, long long n, double v) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) x[t] = v;
+}
+
+// ---------------------------------------------------------------- launchers
+template <class T>
+void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Comp3<T> psi,
+                       Comp3<T> v0, const Scalars* S, T dt, T* out) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  cx.before(VSV_KCLASS_PHASE);
+  k_phi_update<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, mu, psi, v0, const_cast<Scalars*>(S),
+                                                     dt, out);
+  cx.after(VSV_KCLASS_PHASE);
+}
+
+template <class T>
+void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, double* partials, int nblocks,
+                      Scalars* S, int init) {
+  cx.before(VSV_KCLASS_PHASE);
+  k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, partials);
+  cx.after(VSV_KCLASS_PHASE);
+  cx.before(-1);
+  k_va_finalize<<<1, kBlock, 0, cx.stream>>>(partials, nblocks, (long long)P.nx * P.ny * P.nz, S,
+                                             init);
+  cx.after(-1);
+}
+
+template <class T>
+void launch_mu(Ctx& cx, const PhaseParams& P, const T* phi, T* g, T* mu, const Scalars* S) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (P.fe_kind == VSV_HELFRICH) {
+    cx.before(VSV_KCLASS_PHASE);
+    k_helfrich_g<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, g);
+    cx.after(VSV_KCLASS_PHASE);
+  }
+  cx.before(VSV_KCLASS_PHASE);
+  k_mu<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, g, S, mu);
+  cx.after(VSV_KCLASS_PHASE);
+}
+
+template <class T>
+void launch_source(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Comp3<T> s_omega,
+                   Comp3<T> f) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  cx.before(VSV_KCLASS_PHASE);
+  k_source<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, mu, s_omega, f);
+  cx.after(VSV_KCLASS_PHASE);
+}
+
+template <class T>
+void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> v0, Comp3<T> v) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  cx.before(-1);
+  k_velocity<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, psi, v0, v);
+  cx.after(-1);
+}
+
+template <class T>
+void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* g, Comp3<T> vel,
+                 Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0_ring,
+                 Comp3<const double> v0d, T* sigma_t, double* partials, int nblocks, double* out) {
+  cx.before(-1);
+  k_diag<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, g, vel, omega, psi, psi0_ring, v0d, sigma_t,
+                                               partials);
+  cx.after(-1);
+  cx.before(-1);
+  k_diag_finalize<<<1, kBlock, 0, cx.stream>>>(partials, nblocks, out);
+  cx.after(-1);
+}
+
+template <class T>
+void launch_stress_profile(Ctx& cx, const PhaseParams& P, Comp3<T> vel, double* out) {
+  cx.before(-1);
+  k_stress_profile<T><<<P.ny, kBlock, 0, cx.stream>>>(P, vel, out);
+  cx.after(-1);
+}
+
+template <class Tin, class Tout>
+void launch_convert(Ctx& cx, const Tin* in, Tout* out, long long n) {
+  cx.before(-1);
+  k_convert<Tin, Tout><<<nblk(n), kBlock, 0, cx.stream>>>(in, out, n);
+  cx.after(-1);
+}
+
+template <class T>
+void launch_full_field(Ctx& cx, const PhaseParams& P, const T* pert, const double* tab, int ring,
+                       T* out) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  cx.before(-1);
+  k_full_field<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, pert, tab, ring, out);
+  cx.after(-1);
+}
+
+template <class T>
+void launch_scale_copy(Ctx& cx, const T* in, T* out, long long n, double a) {
+  cx.before(-1);
+  k_scale_copy<T><<<nblk(n), kBlock, 0, cx.stream>>>(in, out, n, (T)a);
+  cx.after(-1);
+}
+
+void launch_duct_ring(Ctx& cx, int ny, int nz, double h, const double* u0, const double* chi,
+                      double* omy, double* omz, double* psy, double* psz) {
+  const int m = ny > nz ? ny : nz;
+  cx.before(-1);
+  k_duct_ring<<<nblk(m), kBlock, 0, cx.stream>>>(ny, nz, h, u0, chi, omy, omz, psy, psz);
+  cx.after(-1);
+}
+
+void launch_ring_boundary_rhs(Ctx& cx, int ny, int nz, double h, const double* ring, double scale,
+                              const double* in, double* out) {
+  cx.before(-1);
+  k_ring_rhs<<<nblk((long long)ny * nz), kBlock, 0, cx.stream>>>(ny, nz, h, ring, scale, in, out);
+  cx.after(-1);
+}
+
+void launch_ring_fill_interior(Ctx& cx, int ny, int nz, const double* interior, double* ring) {
+  cx.before(-1);
+  k_ring_fill<<<nblk((long long)ny * nz), kBlock, 0, cx.stream>>>(ny, nz, interior, ring);
+  cx.after(-1);
+}
+
+void launch_base_derived(Ctx& cx, int ny, int nz, int zper, double h, const double* om[3],
+                         const double* ps[3], double* v0[3], double* s_om[3], double* s_ps[3]) {
+  Comp3<const double> O{{om[0], om[1], om[2]}}, Pp{{ps[0], ps[1], ps[2]}};
+  Comp3<double> V{{v0[0], v0[1], v0[2]}}, SO{{s_om[0], s_om[1], s_om[2]}},
+      SP{{s_ps[0], s_ps[1], s_ps[2]}};
+  cx.before(-1);
+  k_base_derived<<<nblk((long long)ny * nz), kBlock, 0, cx.stream>>>(ny, nz, zper, h, O, Pp, V, SO, SP);
+  cx.after(-1);
+}
+
+double device_max_abs(Ctx& cx, const double* x, long long n, double* scratch) {
+  cx.before(-1);
+  k_max_abs<<<1, 1024, 0, cx.stream>>>(x, n, scratch);
+  cx.after(-1);
+  double h = 0.0;
+  cudaMemcpyAsync(&h, scratch, sizeof(double), cudaMemcpyDeviceToHost, cx.stream);
+  cudaStreamSynchronize(cx.stream);
+  return h;
+}
+
+void launch_fill(Ctx& cx, double* x, long long n, double v) {
+  cx.before(-1);
+  k_fill<<<nblk(n), kBlock, 0, cx.stream>>>(x, n, v);
+  cx.after(-1);
+}
+
+#define VSV_INST(T)                                                                               \
+  template void launch_phi_update<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>,      \
+                                     Comp3<T>, const Scalars*, T, T*);                            \
+  template void launch_reduce_va<T>(Ctx&, const PhaseParams&, const T*, double*, int, Scalars*,   \
+                                    int);                                                         \
+  template void launch_mu<T>(Ctx&, const PhaseParams&, const T*, T*, T*, const Scalars*);         \
+  template void launch_source<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>,          \
+                                 Comp3<T>);                                                       \
+  template void launch_velocity<T>(Ctx&, const PhaseParams&, Comp3<T>, Comp3<T>, Comp3<T>);       \
+  template void launch_diag<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>, Comp3<T>,  \
+                               Comp3<T>, Comp3<const double>, Comp3<const double>, T*, double*,   \
+                               int, double*);                                                     \
+  template void launch_stress_profile<T>(Ctx&, const PhaseParams&, Comp3<T>, double*);            \
+  template void launch_full_field<T>(Ctx&, const PhaseParams&, const T*, const double*, int, T*); \
+  template void launch_scale_copy<T>(Ctx&, const T*, T*, long long, double);
+VSV_INST(float)
+VSV_INST(double)
+#undef VSV_INST
+template void launch_convert<float, double>(Ctx&, const float*, double*, long long);
+template void launch_convert<double, float>(Ctx&, const double*, float*, long long);
+template void launch_convert<float, float>(Ctx&, const float*, float*, long long);
+template void launch_convert<double, double>(Ctx&, const double*, double*, long long);
+
+}  // namespace vsv

@@ -1,0 +1,85 @@
+"""The C-ABI library loads, exports every function include/vsv.h declares,
+and validates arguments on the host before touching a GPU (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_2601_05031_gb300 import build
+    build.build()
+    from paper_2601_05031_gb300 import vsv
+    return vsv
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "vsv.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(vsv_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_matches_binding(V):
+    assert _declared() == sorted(V.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(V):
+    lib = V.lib()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert V.vsv_version().startswith("vsv-gb300")
+
+
+def test_workspace_bytes_host_only(V):
+    n32 = V.vsv_workspace_bytes(48, 24, 24, V.VSV_MIXED)
+    n64 = V.vsv_workspace_bytes(48, 24, 24, V.VSV_FP64)
+    N = 48 * 24 * 24
+    assert n32 > 13 * 4 * N and n64 > 13 * 8 * N and n64 > n32
+    assert V.vsv_workspace_bytes(0, 24, 24, V.VSV_MIXED) == 0
+    assert V.vsv_workspace_bytes(8, 1, 8, V.VSV_MIXED) == 0
+    assert V.vsv_workspace_bytes(8, 8, 8, 7) == 0
+
+
+def test_create_rejects_bad_arguments_before_any_launch(V):
+    lib = V.lib()
+    out = ctypes.c_void_p()
+    fake = ctypes.c_void_p(1 << 20)        # aligned, never dereferenced
+    nb = V.vsv_workspace_bytes(16, 8, 8, V.VSV_MIXED)
+    # odd periodic x
+    assert lib.vsv_create(ctypes.byref(out), 15, 8, 8, 1.0, V.VSV_MIXED, fake, nb, None) == V.VSV_EINVAL
+    # misaligned workspace
+    assert lib.vsv_create(ctypes.byref(out), 16, 8, 8, 1.0, V.VSV_MIXED, ctypes.c_void_p(1 << 20 | 8),
+                          nb, None) == V.VSV_EINVAL
+    # too small
+    assert lib.vsv_create(ctypes.byref(out), 16, 8, 8, 1.0, V.VSV_MIXED, fake, nb - 1, None) == V.VSV_ENOMEM
+    # bad spacing / precision / null workspace
+    assert lib.vsv_create(ctypes.byref(out), 16, 8, 8, 0.0, V.VSV_MIXED, fake, nb, None) == V.VSV_EINVAL
+    assert lib.vsv_create(ctypes.byref(out), 16, 8, 8, 1.0, 5, fake, nb, None) == V.VSV_EINVAL
+    assert lib.vsv_create(ctypes.byref(out), 16, 8, 8, 1.0, V.VSV_MIXED, None, nb, None) == V.VSV_EINVAL
+    assert out.value is None
+
+
+def test_null_handles_are_rejected(V):
+    lib = V.lib()
+    assert lib.vsv_step(None, 1, 0.1) == V.VSV_EINVAL
+    assert lib.vsv_destroy(None) == V.VSV_OK
+    assert lib.vsv_check(None) == V.VSV_EINVAL
+    assert lib.vsv_state_bytes(None) == 0
+    assert lib.vsv_kernel_launches(None) == 0
+    p = V.vsv_default_solver(V.VSV_MIXED)
+    assert p.kind == V.VSV_SOLVER_MG and p.nu1 >= 1 and p.max_cycles > 0
+
+
+def test_binding_structs_match_header_sizes(V):
+    # field counts of the C structs as declared in the header
+    txt = open(os.path.join(ROOT, "include", "vsv.h")).read()
+    for cname, pyt in (("vsv_flow_params", V.vsv_flow_params), ("vsv_fe_params", V.vsv_fe_params),
+                       ("vsv_solver_params", V.vsv_solver_params)):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + ";", txt).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = re.findall(r"\b([a-z_0-9]+)\s*(?:\[\d+\])?\s*[;,]", body)
+        assert [n for n, _ in pyt._fields_] == names, cname

@@ -1,0 +1,307 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  FP64 path: relative L2 <= 1e-10 on phi and velocity;
+mixed path: <= 1e-6 (tolerances of the hot-path specification)."""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from oracle.poisson import solve_poisson_dense, solve_poisson
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_05031_gb300 import build
+    build.build()
+    from paper_2601_05031_gb300 import vsv
+    vsv.lib()
+    return vsv
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make_sim(V, w, prec, tol=None, kind=None, fixed=0, **kw):
+    from paper_2601_05031_gb300.sim import Simulation
+    sim = Simulation.from_workload(w, prec)
+    sp = sim.solver_params()
+    if tol is not None:
+        sp.tol = tol
+    if kind is not None:
+        sp.kind = kind
+    sp.fixed_cycles = fixed
+    for k, v in kw.items():
+        setattr(sp, k, v)
+    V.vsv_set_solver(sim.g, sp)
+    return sim
+
+
+# ------------------------------------------------------------ workloads
+def small_droplet():
+    return inputs.droplet_duct(nx=16, ny=12, nz=12, radius=3.5, dt=0.01)
+
+
+def small_vesicle(kind, nx=32, ny=16, nz=16, eps=1.0, vr=0.9, dt=5e-4):
+    w = inputs.vesicle(nx, ny, nz, kind, vr, eps, dt=dt, b_range=(0.24, 0.28), k_area=0.05)
+    return w
+
+
+WORKLOADS = {
+    "droplet_duct": small_droplet,
+    "vesicle_couette": lambda: small_vesicle(inputs.COUETTE),
+    "vesicle_planar": lambda: small_vesicle(inputs.POISEUILLE_PLANAR),
+    "vesicle_duct": lambda: small_vesicle(inputs.POISEUILLE_DUCT),
+    "droplet_quiescent": lambda: inputs.droplet_duct(nx=16, ny=10, nz=12, radius=3.0, u_max=0.0,
+                                                     flow_kind=inputs.QUIESCENT),
+}
+
+
+def oracle_fields(st):
+    v = oracle.velocity(st)
+    return {"phi": st.phi, "mu": st.mu, "omega": st.omega, "psi": st.psi, "vel": list(v)}
+
+
+def gpu_fields(V, sim):
+    F = {"phi": sim.field(V.VSV_FIELD_PHI), "mu": sim.field(V.VSV_FIELD_MU)}
+    F["omega"] = [sim.field(V.VSV_FIELD_OMEGA_X + c) for c in range(3)]
+    F["psi"] = [sim.field(V.VSV_FIELD_PSI_X + c) for c in range(3)]
+    F["vel"] = [sim.field(V.VSV_FIELD_VEL_X + c) for c in range(3)]
+    return F
+
+
+def field_errors(G, O):
+    e = {"phi": rel(G["phi"], O["phi"]), "mu": rel(G["mu"], O["mu"])}
+    for key in ("omega", "psi", "vel"):
+        e[key] = rel(np.stack(G[key]), np.stack(O[key]))
+    return e
+
+
+# ------------------------------------------------------------ Poisson
+BCS = [((16, 8, 12), (True, False, False)), ((16, 10, 8), (True, False, True)),
+       ((12, 9, 7), (False, False, False)), ((1, 16, 16), (True, False, False)),
+       ((24, 6, 10), (True, True, False))]
+
+
+@pytest.mark.parametrize("shape,bc", BCS)
+@pytest.mark.parametrize("prec,kind", [("fp64", "mg"), ("fp64", "sor"), ("mixed", "mg")])
+def test_poisson_vs_oracle(V, shape, bc, prec, kind):
+    nx, ny, nz = shape
+    if nx > 1 and nx % 2 and bc[0]:
+        pytest.skip("odd periodic")
+    from paper_2601_05031_gb300.sim import Simulation
+    P = V.VSV_FP64 if prec == "fp64" else V.VSV_MIXED
+    sim = Simulation(nx, ny, nz, 0.8, P)
+    sp = sim.solver_params()
+    sp.kind = V.VSV_SOLVER_SOR if kind == "sor" else V.VSV_SOLVER_MG
+    V.vsv_set_solver(sim.g, sp)
+    b = inputs.random_field((nz, ny, nx), seed=11)
+    ref = solve_poisson_dense(b, 0.8, bc)
+    tol = 1e-13 if prec == "fp64" else 1e-7
+    x, cyc, rr, st = sim.solve_poisson(b, periodic=bc, tol=tol, max_cycles=20000)
+    lim = FP64_TOL if prec == "fp64" else MIXED_TOL
+    assert rel(x, ref) < lim, (rel(x, ref), cyc, rr)
+    sim.close()
+
+
+def test_poisson_manufactured_eigenvector(V):
+    """C-P1 on the GPU: sin-product eigenvector recovered by the FP64 MG."""
+    from paper_2601_05031_gb300.sim import Simulation
+    nx, ny, nz, h = 32, 24, 16, 1.0
+    sim = Simulation(nx, ny, nz, h, V.VSV_FP64)
+    i, j, k = np.arange(nx), np.arange(ny), np.arange(nz)
+    tx, ty, tz = 2 * math.pi * 3 / nx, math.pi * 2 / (ny + 1), math.pi * 1 / (nz + 1)
+    u = (np.sin(tz * (k + 1))[:, None, None] * np.sin(ty * (j + 1))[None, :, None]
+         * np.cos(tx * i + 0.2)[None, None, :])
+    lam = sum(2 * math.cos(t) - 2 for t in (tx, ty, tz)) / h ** 2
+    x, cyc, rr, st = sim.solve_poisson(lam * u, periodic=(True, False, False), tol=1e-13)
+    assert rel(x, u) < 1e-11, (rel(x, u), cyc, rr)
+    sim.close()
+
+
+def test_mixed_solution_error_near_fp32_rounding(V):
+    """With the exact defect the FP32-stored iterate converges to the FP32
+    rounding level of the solution itself (relative error a few 1e-8),
+    although its relative residual stalls near u ||L|| ||x|| / ||b||."""
+    from paper_2601_05031_gb300.sim import Simulation
+    nx, ny, nz = 64, 32, 32
+    sim = Simulation(nx, ny, nz, 1.0, V.VSV_MIXED)
+    b = inputs.random_field((nz, ny, nx), seed=5)
+    x, cyc, rr, st = sim.solve_poisson(b, periodic=(True, False, False), tol=1e-9,
+                                       max_cycles=60, check=False)
+    ref = solve_poisson(b, 1.0, (True, False, False))
+    assert st == V.VSV_OK and rr < 1e-5, (st, rr, cyc)
+    assert rel(x, ref) < 2e-7, rel(x, ref)
+    sim.close()
+
+
+# ------------------------------------------------------------ initial state
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_initial_state_fp64(V, name):
+    w = WORKLOADS[name]()
+    st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
+    sim = make_sim(V, w, V.VSV_FP64, tol=1e-13)
+    sim.set_phi(w.phi0)
+    e = field_errors(gpu_fields(V, sim), oracle_fields(st))
+    for key, val in e.items():
+        assert val < FP64_TOL, (key, e)
+    sim.close()
+
+
+# ------------------------------------------------------------ time steps
+@pytest.mark.parametrize("name,nsteps", [("droplet_duct", 5), ("vesicle_couette", 4),
+                                         ("vesicle_planar", 3), ("vesicle_duct", 3),
+                                         ("droplet_quiescent", 4)])
+def test_steps_fp64(V, name, nsteps):
+    w = WORKLOADS[name]()
+    st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
+    for _ in range(nsteps):
+        oracle.step(st, w.dt)
+    sim = make_sim(V, w, V.VSV_FP64, tol=1e-13)
+    sim.set_phi(w.phi0)
+    sim.step(nsteps, w.dt)
+    e = field_errors(gpu_fields(V, sim), oracle_fields(st))
+    assert e["phi"] < FP64_TOL and e["vel"] < FP64_TOL, e
+    for key in ("mu", "omega", "psi"):
+        assert e[key] < 1e-9, (key, e)
+    sim.close()
+
+
+def test_droplet_24x24x48_sor_fp64(V):
+    """The plain-FP64 droplet workload: 48x24x24 duct, red-black SOR to a
+    relative residual of 1e-13 (tighter than the 1e-10 it asks for, so that
+    the discrete answer, not the stopping point, is compared), 10 steps."""
+    w = inputs.droplet_24x24x48()
+    st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
+    for _ in range(w.nsteps):
+        oracle.step(st, w.dt)
+    sim = make_sim(V, w, V.VSV_FP64, tol=1e-13, kind=V.VSV_SOLVER_SOR, max_cycles=20000,
+                   check_every=10)
+    sim.set_phi(w.phi0)
+    sim.step(w.nsteps, w.dt)
+    e = field_errors(gpu_fields(V, sim), oracle_fields(st))
+    assert e["phi"] < FP64_TOL and e["vel"] < FP64_TOL, e
+    sim.close()
+
+
+@pytest.mark.parametrize("name,nsteps", [("droplet_duct", 5), ("vesicle_couette", 4),
+                                         ("vesicle_duct", 3)])
+def test_steps_mixed(V, name, nsteps):
+    w = WORKLOADS[name]()
+    st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
+    for _ in range(nsteps):
+        oracle.step(st, w.dt)
+    sim = make_sim(V, w, V.VSV_MIXED, tol=1e-8)
+    sim.set_phi(w.phi0)
+    sim.step(nsteps, w.dt)
+    e = field_errors(gpu_fields(V, sim), oracle_fields(st))
+    assert e["phi"] < MIXED_TOL and e["vel"] < MIXED_TOL, e
+    sim.close()
+
+
+def test_fixed_cycle_schedule_matches_converged(V):
+    """Mixed path with a fixed two-V-cycle schedule per solve (the launch
+    configuration of the benchmark) stays within 1e-6 of the oracle."""
+    w = small_vesicle(inputs.COUETTE, nx=64, ny=32, nz=32, eps=1.5, dt=1e-4)
+    nsteps = 20
+    st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
+    for _ in range(nsteps):
+        oracle.step(st, w.dt)
+    sim = make_sim(V, w, V.VSV_MIXED, tol=1e-8, fixed=2)
+    sim.set_phi(w.phi0)
+    sim.step(nsteps, w.dt)
+    e = field_errors(gpu_fields(V, sim), oracle_fields(st))
+    assert e["phi"] < MIXED_TOL and e["vel"] < MIXED_TOL, e
+    sim.close()
+
+
+# ------------------------------------------------------------ diagnostics
+def test_diagnostics_vs_oracle(V):
+    w = small_vesicle(inputs.COUETTE)
+    st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
+    for _ in range(2):
+        oracle.step(st, w.dt)
+    od = oracle.diagnostics(st)
+    sim = make_sim(V, w, V.VSV_FP64, tol=1e-13)
+    sim.set_phi(w.phi0)
+    sim.step(2, w.dt)
+    gd = sim.diagnostics()
+    for key in ("volume", "area", "reduced_volume", "energy", "dissipation", "dissipation0",
+                "resistance_rel", "omega_dev2", "psi_dev2", "max_sigma_t"):
+        assert abs(gd[key] - od[key]) <= 1e-9 * max(1.0, abs(od[key])), (key, gd[key], od[key])
+    for a in range(3):
+        assert abs(gd["com"][a] - od["com"][a]) < 1e-9
+    assert gd["max_div_v"] < 1e-12 and od["max_div_v"] < 1e-12
+    assert abs(gd["max_div_psi"] - od["max_div_psi"]) < 1e-9
+    prof = sim.stress_profile()
+    assert np.max(np.abs(prof - od["stress_profile"])) < 1e-11 * max(1.0, np.abs(od["stress_profile"]).max())
+    sig = sim.field(V.VSV_FIELD_STRESS_T)
+    assert rel(sig, od["sigma_t"]) < 1e-9
+    sim.close()
+
+
+# ------------------------------------------------------------ state, errors, determinism
+def test_state_roundtrip_and_determinism(V):
+    w = small_droplet()
+    sim = make_sim(V, w, V.VSV_MIXED, fixed=2)
+    sim.set_phi(w.phi0)
+    sim.step(2, w.dt)
+    nb = V.vsv_state_bytes(sim.g)
+    blob = np.empty(nb, dtype=np.uint8)
+    V.vsv_get_state(sim.g, blob.ctypes.data, nb)
+    sim.step(3, w.dt)
+    a = sim.field(V.VSV_FIELD_PHI, np.float32)
+    V.vsv_set_state(sim.g, blob.ctypes.data, nb)
+    sim.step(3, w.dt)
+    b = sim.field(V.VSV_FIELD_PHI, np.float32)
+    assert np.array_equal(a, b)
+    sim2 = make_sim(V, w, V.VSV_MIXED, fixed=2)
+    sim2.set_phi(w.phi0)
+    sim2.step(5, w.dt)
+    assert np.array_equal(a, sim2.field(V.VSV_FIELD_PHI, np.float32))
+    sim.close()
+    sim2.close()
+
+
+def test_error_statuses(V):
+    from paper_2601_05031_gb300.sim import Simulation
+    w = small_droplet()
+    sim = Simulation(w.nx, w.ny, w.nz, 1.0, V.VSV_MIXED)
+    assert V.vsv_step(sim.g, 1, 0.01, check=False) == V.VSV_ESTATE
+    sim.configure(w)
+    sim.set_phi(w.phi0)
+    lim = sim.stability_limit()
+    assert 0.0119 < lim < 0.0120   # CH bound 2 / (M lam (2 + sigma lam)), lam = 12
+    assert V.vsv_step(sim.g, 1, 2 * lim, check=False) == V.VSV_EUNSTABLE
+    bad = w.phi0.copy()
+    bad[3, 4, 5] = np.nan
+    sim.set_field(V.VSV_FIELD_PHI, bad)
+    sp = sim.solver_params()
+    sp.fixed_cycles = 1
+    V.vsv_set_solver(sim.g, sp)
+    V.vsv_step(sim.g, 1, w.dt, check=False)
+    assert V.vsv_check(sim.g, check=False) == V.VSV_ENONFINITE
+    sim.close()
+
+
+def test_kernel_launch_accounting(V):
+    w = small_droplet()
+    sim = make_sim(V, w, V.VSV_MIXED, fixed=2)
+    sim.set_phi(w.phi0)
+    n0 = sim.kernel_launches()
+    V.vsv_profile_enable(sim.g, V.VSV_KCLASS_SMOOTH_FINE)
+    sim.step(2, w.dt)
+    ms, n = V.vsv_profile_read(sim.g, V.VSV_KCLASS_SMOOTH_FINE)
+    assert sim.kernel_launches() > n0 and n > 0 and ms > 0
+    sim.close()
