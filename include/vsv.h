@@ -127,7 +127,14 @@ typedef struct {
  *   ||b - L x||_2 <= tol ||b||_2 or max_cycles, checking every check_every.
  * nu1 / nu2: pre / post smoothing sweeps; max_levels: multigrid depth cap;
  * coarse_sweeps: red-black sweeps on the coarsest level; omega_sor <= 0
- * picks the optimal SOR weight for the grid. */
+ * picks the optimal SOR weight for the grid.  variant 0 uses the fastest
+ * kernels available for each level (fused single-pass red-black sweeps where
+ * the tile shape allows); 1 forces the reference per-colour kernels (same
+ * arithmetic, bit-identical results; for cross-checks).  extrapolate = 1
+ * starts each solve of a time step from 2 x^n - x^{n-1} (linear extrapolation
+ * of the two previous solutions) instead of x^n, which shrinks the initial
+ * error from O(dt) to O(dt^2); it changes the iterate, not the converged
+ * answer. */
 typedef struct {
   int kind;
   double tol;
@@ -139,6 +146,8 @@ typedef struct {
   int max_levels;
   int coarse_sweeps;
   double omega_sor;
+  int variant;
+  int extrapolate;
 } vsv_solver_params;
 
 /* Per-axis boundary of a standalone Poisson problem: periodic (1) or zero
@@ -233,8 +242,9 @@ vsv_status vsv_get_diagnostics(vsv_grid* g, vsv_diag* out);
 /* <sigma_xy> averaged over x and z, one value per y row (ny doubles, host). */
 vsv_status vsv_get_stress_profile(vsv_grid* g, double* out);
 
-/* Checkpoint / resume: a flat host blob of the state (phi, omega', psi',
- * V0, A0, time, step count). */
+/* Checkpoint / resume: a flat host blob of the state (phi, omega', psi', the
+ * previous step's omega' and psi', V0, A0, time, step count); resuming from
+ * it continues bit-identically. */
 size_t vsv_state_bytes(const vsv_grid* g);
 vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes);
 vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes);

@@ -29,16 +29,22 @@ struct vsv_grid {
   bool flow_set = false, phi_set = false, phase_stale = false;
 
   void* phi[2] = {nullptr, nullptr};
+  float* phi_lo[2] = {nullptr, nullptr};   // mixed path: low words of phi
   int cur = 0;
   void* mu = nullptr;
   void* g = nullptr;
+  float* g_lo = nullptr;
   void* f[3] = {};
   void* om[3] = {};
   void* ps[3] = {};
+  void* om_prev[3] = {};     // previous step's solutions (initial-guess extrapolation)
+  void* ps_prev[3] = {};
+  bool prev_valid = false;
   void* stage_a = nullptr;   // N * 8 bytes
   void* stage_b = nullptr;   // N * 8 bytes
   void* mg_e[kMaxLevels][3] = {};
   void* mg_r[kMaxLevels][3] = {};
+  void* mg_t[kMaxLevels][3] = {};  // ping-pong partner of the fused sweep (mixed path)
   long long mg_cap[kMaxLevels] = {};
   int mg_nlev_cap = 0;
 
@@ -124,9 +130,16 @@ size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
   p = tf(N); if (g) g->phi[1] = p;
   p = tf(N); if (g) g->mu = p;
   p = tf(N); if (g) g->g = p;
+  if (prec == VSV_MIXED) {
+    p = take((size_t)N * 4); if (g) g->phi_lo[0] = (float*)p;
+    p = take((size_t)N * 4); if (g) g->phi_lo[1] = (float*)p;
+    p = take((size_t)N * 4); if (g) g->g_lo = (float*)p;
+  }
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->f[c] = p; }
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->om[c] = p; }
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->ps[c] = p; }
+  for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->om_prev[c] = p; }
+  for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->ps_prev[c] = p; }
   p = take((size_t)N * 8); if (g) g->stage_a = p;
   p = take((size_t)N * 8); if (g) g->stage_b = p;
   long long cells[kMaxLevels];
@@ -137,6 +150,9 @@ size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
     for (int c = 0; c < 3; ++c) { p = tf(cells[l]); if (g) g->mg_r[l][c] = p; }
     if (g) g->mg_cap[l] = cells[l];
   }
+  if (prec == VSV_MIXED)
+    for (int l = 0; l < nl; ++l)
+      for (int c = 0; c < 3; ++c) { p = tf(cells[l]); if (g) g->mg_t[l][c] = p; }
   for (int c = 0; c < 3; ++c) { double* d = df(R2); if (g) g->om_ring[c] = d; }
   for (int c = 0; c < 3; ++c) { double* d = df(R2); if (g) g->ps_ring[c] = d; }
   for (int c = 0; c < 3; ++c) { double* d = df(N2); if (g) g->v0d[c] = d; }
@@ -252,6 +268,37 @@ Comp3<T> comp3(void* a, void* b, void* c) {
 }
 
 // ---------------------------------------------------------------- solvers
+// nu red-black sweeps on level l: the fused single-pass kernel (ping-pong
+// with the level's scratch) where it applies, else the per-colour kernels.
+template <class T>
+void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp, int nu) {
+  const double h2 = 1.0 / L.inv_h2;
+  const int kc = (l == 0) ? VSV_KCLASS_SMOOTH_FINE : VSV_KCLASS_SMOOTH;
+  if constexpr (std::is_same<T, float>::value) {
+    if (g->sol.variant == 0 && fused_sweep_ok(L) && g->mg_t[l][0] && nu >= 2) {
+      Comp3<float> Tt = comp3<float>(g->mg_t[l][0], g->mg_t[l][1], g->mg_t[l][2]);
+      const long long tiles = (long long)(L.n[0] / 128) * (L.n[1] / 16) * ncomp;
+      const long long want = 8LL * 152;
+      int nzc = (int)std::max(1LL, (want + tiles - 1) / tiles);
+      int zchunk = std::max(16, (L.n[2] + nzc - 1) / nzc);
+      int s = 0;
+      for (; s + 1 < nu; s += 2) {
+        launch_rbgs_fused(g->cx, L, X, Tt, R, ncomp, zchunk, kc);
+        launch_rbgs_fused(g->cx, L, Tt, X, R, ncomp, zchunk, kc);
+      }
+      for (; s < nu; ++s) {
+        launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
+        launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
+      }
+      return;
+    }
+  }
+  for (int s = 0; s < nu; ++s) {
+    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
+    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
+  }
+}
+
 template <class T>
 void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T> R, int ncomp) {
   const Level& L = lv[l];
@@ -271,10 +318,7 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
     }
     return;
   }
-  for (int s = 0; s < g->sol.nu1; ++s) {
-    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
-    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
-  }
+  smooth<T>(g, L, l, X, R, ncomp, g->sol.nu1);
   const Level& C = lv[l + 1];
   Comp3<T> EC = comp3<T>(g->mg_e[l + 1][0], g->mg_e[l + 1][1], g->mg_e[l + 1][2]);
   Comp3<T> RC = comp3<T>(g->mg_r[l + 1][0], g->mg_r[l + 1][1], g->mg_r[l + 1][2]);
@@ -284,10 +328,7 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
   Rhs3<T> RCr{{RC.p[0], RC.p[1], RC.p[2]}, {nullptr, nullptr, nullptr}, (T)1};
   vcycle<T>(g, lv, l + 1, EC, RCr, ncomp);
   launch_prolong_add<T>(g->cx, L, C, X, EC, ncomp);
-  for (int s = 0; s < g->sol.nu2; ++s) {
-    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
-    launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
-  }
+  smooth<T>(g, L, l, X, R, ncomp, g->sol.nu2);
 }
 
 // relres = max over components of ||b - L x|| / ||b|| (||b|| = 0 -> ||r||).
@@ -380,6 +421,18 @@ PhaseParams phase_params(const vsv_grid* g) {
   P.cf2 = g->fe.mu_prefactor_half ? cf : 2.0 * cf;
   P.mobility = g->fe.mobility;
   P.inv_eta = 1.0 / g->flow.eta;
+  auto split = [](double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  split(P.inv_h2, P.ih2_hi, P.ih2_lo);
+  split(g->fe.eps * g->fe.eps, P.e2_hi, P.e2_lo);
+  split(P.cf2, P.cf2_hi, P.cf2_lo);
+  split(g->fe.sigma, P.sig_hi, P.sig_lo);
+  split(0.5 * P.inv_h, P.hih_hi, P.hih_lo);
+  split(0.5 * g->fe.eps, P.he_hi, P.he_lo);
+  split(0.25 / g->fe.eps, P.q_hi, P.q_lo);
+  split(3.0 / (2.0 * std::sqrt(2.0)), P.ca_hi, P.ca_lo);
   std::memset(P.vwall, 0, sizeof P.vwall);
   if (g->flow.kind == VSV_COUETTE) {
     P.vwall[0][0] = g->flow.v_lo;
@@ -412,11 +465,22 @@ vsv_status flow_solves(vsv_grid* g, bool initial) {
   Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
   const vsv_solver_params& s = g->sol;
   const int fixed = initial ? 0 : s.fixed_cycles;
+  // initial guesses: 2 x^n - x^{n-1} once two solutions exist, else x^n
+  const bool extrap = !initial && s.extrapolate && g->prev_valid;
+  if (!initial) {
+    launch_extrapolate<T>(g->cx, O, comp3<T>(g->om_prev[0], g->om_prev[1], g->om_prev[2]), g->N, 3,
+                          extrap ? 1 : 0);
+  }
   vsv_status st = solve<T>(g, g->flow_levels, O, rhs_omega<T>(g), 3, s.kind, fixed, s.tol,
                            s.max_cycles, s.check_every, &g->last_cycles[0], &g->last_relres[0]);
   if (st != VSV_OK) return st;
+  if (!initial) {
+    launch_extrapolate<T>(g->cx, Pp, comp3<T>(g->ps_prev[0], g->ps_prev[1], g->ps_prev[2]), g->N, 3,
+                          extrap ? 1 : 0);
+  }
   st = solve<T>(g, g->flow_levels, Pp, rhs_psi<T>(g), 3, s.kind, fixed, s.tol, s.max_cycles,
                 s.check_every, &g->last_cycles[1], &g->last_relres[1]);
+  g->prev_valid = !initial;
   return st;
 }
 
@@ -425,8 +489,14 @@ template <class T>
 void refresh_phase(vsv_grid* g, int init) {
   PhaseParams P = phase_params(g);
   T* phi = (T*)g->phi[g->cur];
-  launch_reduce_va<T>(g->cx, P, phi, g->partials, g->red_blocks, g->S, init);
-  launch_mu<T>(g->cx, P, phi, (T*)g->g, (T*)g->mu, g->S);
+  if constexpr (std::is_same<T, float>::value) {
+    const float* lo = g->phi_lo[g->cur];
+    launch_reduce_va<float>(g->cx, P, phi, lo, g->partials, g->red_blocks, g->S, init);
+    launch_mu_ff(g->cx, P, phi, lo, (float*)g->g, g->g_lo, (float*)g->mu, g->S);
+  } else {
+    launch_reduce_va<T>(g->cx, P, phi, nullptr, g->partials, g->red_blocks, g->S, init);
+    launch_mu<T>(g->cx, P, phi, (T*)g->g, (T*)g->mu, g->S);
+  }
 }
 
 template <class T>
@@ -441,7 +511,11 @@ vsv_status step_impl(vsv_grid* g, double dt) {
   Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
   Comp3<T> V0 = comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]);
   // 1-3: explicit phi update with v^n = v0 + curl psi'^n and lambda_V^n
-  launch_phi_update<T>(g->cx, P, phi, (const T*)g->mu, Pp, V0, g->S, (T)dt, phin);
+  if constexpr (std::is_same<T, float>::value)
+    launch_phi_update_ff(g->cx, P, phi, g->phi_lo[g->cur], (const float*)g->mu, Pp, V0, g->S,
+                         (float)dt, phin, g->phi_lo[1 - g->cur]);
+  else
+    launch_phi_update<T>(g->cx, P, phi, (const T*)g->mu, Pp, V0, g->S, (T)dt, phin);
   g->cur = 1 - g->cur;
   // 4-5: V, A of phi^{n+1}, gamma_A, then mu^{n+1}
   refresh_phase<T>(g, 0);
@@ -505,6 +579,44 @@ vsv_status export_field(vsv_grid* g, const T* src, int dt, int on_device, void* 
   return VSV_OK;
 }
 
+// phi in: FP64 input splits into hi + lo words on the mixed path.
+template <class T>
+vsv_status import_phi(vsv_grid* g, const void* src, int dt, int on_device) {
+  T* hi = (T*)g->phi[g->cur];
+  if constexpr (std::is_same<T, float>::value) {
+    float* lo = g->phi_lo[g->cur];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (dt == VSV_DTYPE_F64) {
+      CK(cudaMemcpyAsync(g->stage_b, src, g->N * 8, kind, g->cx.stream));
+      launch_split_ff(g->cx, (const double*)g->stage_b, hi, lo, g->N);
+    } else {
+      CK(cudaMemcpyAsync(hi, src, g->N * 4, kind, g->cx.stream));
+      CK(cudaMemsetAsync(lo, 0, g->N * 4, g->cx.stream));
+    }
+    CKL();
+    if (!on_device) CK(cudaStreamSynchronize(g->cx.stream));
+    return VSV_OK;
+  } else {
+    return import_field<T>(g, src, dt, on_device, hi, g->N);
+  }
+}
+
+template <class T>
+vsv_status export_phi(vsv_grid* g, int dt, int on_device, void* dst) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (dt == VSV_DTYPE_F64) {
+      launch_merge_ff(g->cx, (const float*)g->phi[g->cur], g->phi_lo[g->cur], (double*)g->stage_a,
+                      g->N);
+      CKL();
+      CK(cudaMemcpyAsync(dst, g->stage_a, g->N * 8,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->cx.stream));
+      if (!on_device) CK(cudaStreamSynchronize(g->cx.stream));
+      return VSV_OK;
+    }
+  }
+  return export_field<T>(g, (const T*)g->phi[g->cur], dt, on_device, dst, g->N);
+}
+
 template <class T>
 vsv_status get_field_impl(vsv_grid* g, int field, void* dst, int dt, int on_device) {
   PhaseParams P = phase_params(g);
@@ -514,7 +626,7 @@ vsv_status get_field_impl(vsv_grid* g, int field, void* dst, int dt, int on_devi
   }
   const T* src = nullptr;
   T* tmp = (T*)g->stage_a;
-  if (field == VSV_FIELD_PHI) src = (const T*)g->phi[g->cur];
+  if (field == VSV_FIELD_PHI) return export_phi<T>(g, dt, on_device, dst);
   else if (field == VSV_FIELD_MU) src = (const T*)g->mu;
   else if (field >= VSV_FIELD_OMEGA_X && field <= VSV_FIELD_OMEGA_Z) {
     const int c = field - VSV_FIELD_OMEGA_X;
@@ -533,7 +645,8 @@ vsv_status get_field_impl(vsv_grid* g, int field, void* dst, int dt, int on_devi
     Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
     launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
                        comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
-    launch_diag<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->g, V,
+    launch_diag<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->phi_lo[g->cur],
+                   (const T*)g->g, (const T*)g->g_lo, V,
                    comp3<T>(g->om[0], g->om[1], g->om[2]), comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
                    ring3(g->ps_ring), ring3(g->v0d), tmp, g->partials, g->red_blocks, g->dout);
     src = tmp;
@@ -665,6 +778,8 @@ void default_solver(vsv_solver_params* s, int prec) {
   s->max_levels = kMaxLevels;
   s->coarse_sweeps = 24;
   s->omega_sor = 0.0;
+  s->variant = 0;
+  s->extrapolate = 1;
 }
 
 }  // namespace
@@ -760,7 +875,8 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
   if (sp->kind == VSV_SOLVER_SOR && g->prec != VSV_FP64)
     return fail(g, VSV_EINVAL, "SOR is provided for the FP64 precision only%s");
   if (sp->nu1 < 0 || sp->nu2 < 0 || sp->nu1 + sp->nu2 < 1 || sp->coarse_sweeps < 1 ||
-      sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->max_levels < 1 || !(sp->tol >= 0))
+      sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->max_levels < 1 || !(sp->tol >= 0) ||
+      sp->variant < 0 || sp->variant > 1 || sp->extrapolate < 0 || sp->extrapolate > 1)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
   if (g->flow_set) {
@@ -776,10 +892,10 @@ vsv_status vsv_set_phi(vsv_grid* g, const void* phi, int dtype, int on_device) {
   g->err.clear();
   vsv_status st;
   if (g->prec == VSV_FP64) {
-    st = import_field<double>(g, phi, dtype, on_device, (double*)g->phi[g->cur], g->N);
+    st = import_phi<double>(g, phi, dtype, on_device);
     if (st == VSV_OK) st = set_phi_impl<double>(g);
   } else {
-    st = import_field<float>(g, phi, dtype, on_device, (float*)g->phi[g->cur], g->N);
+    st = import_phi<float>(g, phi, dtype, on_device);
     if (st == VSV_OK) st = set_phi_impl<float>(g);
   }
   g->time = 0.0;
@@ -895,8 +1011,12 @@ vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int
   if (!g || !src || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64)) return VSV_EINVAL;
   if (!g->phi_set) return fail(g, VSV_ESTATE, "no state: call vsv_set_phi first%s");
   void* dst = nullptr;
-  if (field == VSV_FIELD_PHI) dst = g->phi[g->cur];
-  else if (field >= VSV_FIELD_OMEGA_PERT_X && field <= VSV_FIELD_OMEGA_PERT_Z)
+  if (field == VSV_FIELD_PHI) {
+    vsv_status st = g->prec == VSV_FP64 ? import_phi<double>(g, src, dtype, on_device)
+                                        : import_phi<float>(g, src, dtype, on_device);
+    if (st == VSV_OK) g->phase_stale = true;
+    return st;
+  } else if (field >= VSV_FIELD_OMEGA_PERT_X && field <= VSV_FIELD_OMEGA_PERT_Z)
     dst = g->om[field - VSV_FIELD_OMEGA_PERT_X];
   else if (field >= VSV_FIELD_PSI_PERT_X && field <= VSV_FIELD_PSI_PERT_Z)
     dst = g->ps[field - VSV_FIELD_PSI_PERT_X];
@@ -906,6 +1026,7 @@ vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int
                       ? import_field<double>(g, src, dtype, on_device, (double*)dst, g->N)
                       : import_field<float>(g, src, dtype, on_device, (float*)dst, g->N);
   if (st == VSV_OK && field == VSV_FIELD_PHI) g->phase_stale = true;
+  if (st == VSV_OK && field != VSV_FIELD_PHI) g->prev_valid = false;
   return st;
 }
 
@@ -922,7 +1043,8 @@ vsv_status vsv_get_diagnostics(vsv_grid* g, vsv_diag* out) {
     Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
     launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
                        comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
-    launch_diag<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->g, V,
+    launch_diag<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->phi_lo[g->cur],
+                   (const T*)g->g, (const T*)g->g_lo, V,
                    comp3<T>(g->om[0], g->om[1], g->om[2]), comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
                    ring3(g->ps_ring), ring3(g->v0d), (T*)nullptr, g->partials, g->red_blocks,
                    g->dout);
@@ -988,16 +1110,21 @@ vsv_status vsv_get_stress_profile(vsv_grid* g, double* out) {
   return VSV_OK;
 }
 
+// Blob: header, then phi, omega'(3), psi'(3), the previous step's omega'(3)
+// and psi'(3) (initial-guess extrapolation), then (mixed) the low words of phi.
 struct StateHeader {
   char magic[8];
   int nx, ny, nz, prec;
   double V0, A0, time;
   long long steps;
+  int prev_valid, pad;
 };
+constexpr int kStateFields = 13;
 
 size_t vsv_state_bytes(const vsv_grid* g) {
   if (!g) return 0;
-  return sizeof(StateHeader) + (size_t)g->N * g->tsize * 7;
+  return sizeof(StateHeader) + (size_t)g->N * g->tsize * kStateFields +
+         (g->prec == VSV_MIXED ? (size_t)g->N * 4 : 0);
 }
 
 vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes) {
@@ -1016,6 +1143,14 @@ vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes) {
     CK(cudaMemcpyAsync(q + fb * (1 + c), g->om[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
   for (int c = 0; c < 3; ++c)
     CK(cudaMemcpyAsync(q + fb * (4 + c), g->ps[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(q + fb * (7 + c), g->om_prev[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(q + fb * (10 + c), g->ps_prev[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
+  if (g->prec == VSV_MIXED)
+    CK(cudaMemcpyAsync(q + fb * kStateFields, g->phi_lo[g->cur], (size_t)g->N * 4,
+                       cudaMemcpyDeviceToHost, g->cx.stream));
+  hd.prev_valid = g->prev_valid ? 1 : 0;
   CK(cudaStreamSynchronize(g->cx.stream));
   hd.V0 = hs.V0; hd.A0 = hs.A0; hd.time = g->time; hd.steps = g->steps;
   std::memcpy(p, &hd, sizeof hd);
@@ -1037,6 +1172,13 @@ vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes) {
     CK(cudaMemcpyAsync(g->om[c], q + fb * (1 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
   for (int c = 0; c < 3; ++c)
     CK(cudaMemcpyAsync(g->ps[c], q + fb * (4 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(g->om_prev[c], q + fb * (7 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(g->ps_prev[c], q + fb * (10 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
+  if (g->prec == VSV_MIXED)
+    CK(cudaMemcpyAsync(g->phi_lo[g->cur], q + fb * kStateFields, (size_t)g->N * 4,
+                       cudaMemcpyHostToDevice, g->cx.stream));
   double v[2] = {hd.V0, hd.A0};
   CK(cudaMemcpyAsync(&g->S->V0, v, sizeof v, cudaMemcpyHostToDevice, g->cx.stream));
   CK(cudaStreamSynchronize(g->cx.stream));
@@ -1044,6 +1186,7 @@ vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes) {
   g->steps = hd.steps;
   g->phi_set = true;
   g->phase_stale = true;
+  g->prev_valid = hd.prev_valid != 0;
   return VSV_OK;
 }
 

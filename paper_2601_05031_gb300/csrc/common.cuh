@@ -71,6 +71,44 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Double-word ("float-float") value hi + lo with |lo| <= ulp(hi) / 2, built
+// from the error-free transforms TwoSum (Knuth), Fast2Sum (Dekker) and
+// TwoProd by FMA; the sloppy add / multiply of Joldes, Muller and Popescu
+// (2017) give a relative error of a few 2^-44.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_from(float a) { return FF{a, 0.f}; }
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s, e);
+}
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  return fast_two_sum(s, __fadd_rn(e, a.lo));
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ float ff_round(FF a) { return __fadd_rn(a.hi, a.lo); }
+
 // Cascaded (compensated) summation accumulator, Ogita-Rump-Oishi "Sum2":
 // the running sum is kept as hi + lo with every rounding error of hi
 // collected in lo.

@@ -95,12 +95,20 @@ template <class T>
 void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Comp3<T> E, int ncomp);
 template <class T>
 void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp);
+// x <- 2 x - xp, xp <- old x (extrapolate = 1) or xp <- x (extrapolate = 0)
+template <class T>
+void launch_extrapolate(Ctx& cx, Comp3<T> X, Comp3<T> XP, long long n, int ncomp, int extrapolate);
 template <class T>
 bool launch_coarse_solve(Ctx& cx, const Level& L, Comp3<T> E, Comp3<T> R, int ncomp, int sweeps,
                          double h2);
 template <class T>
 void launch_resid_norm(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, bool exact,
                        double* partials, int nblocks, Scalars* S);
+
+// fused single-pass red-black sweep (smooth.cu)
+bool fused_sweep_ok(const Level& L);
+void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
+                       int ncomp, int zchunk, int kclass);
 
 // ---------------------------------------------------------------- phase-field (phase.cu)
 struct PhaseParams {
@@ -109,6 +117,9 @@ struct PhaseParams {
   int fe_kind;
   double sigma, eps, cf2;       // cf2 = prefactor of the Helfrich mu
   double mobility, inv_eta;
+  // the same coefficients as double-word FP32 pairs (hi, lo) for the mixed path
+  float ih2_hi, ih2_lo, e2_hi, e2_lo, cf2_hi, cf2_lo, sig_hi, sig_lo;
+  float hih_hi, hih_lo, he_hi, he_lo, q_hi, q_lo, ca_hi, ca_lo;   // area density
   // wall velocity on the wall nodes: [0] y = 0 wall, [1] y = H, [2] z = 0, [3] z = H
   double vwall[4][3];
 };
@@ -117,8 +128,17 @@ template <class T>
 void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Comp3<T> psi,
                        Comp3<T> v0, const Scalars* S, T dt, T* phi_out);
 template <class T>
-void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, double* partials, int nblocks,
-                      Scalars* S, int init);
+void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo,
+                      double* partials, int nblocks, Scalars* S, int init);
+// Mixed path: phi carried as FP32 pairs (hi, lo); mu and g computed with
+// double-word FP32 arithmetic, mu rounded to FP32.
+void launch_phi_update_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo,
+                          const float* mu, Comp3<float> psi, Comp3<float> v0, const Scalars* S,
+                          float dt, float* out, float* out_lo);
+void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo, float* g,
+                  float* g_lo, float* mu, const Scalars* S);
+void launch_split_ff(Ctx& cx, const double* in, float* hi, float* lo, long long n);
+void launch_merge_ff(Ctx& cx, const float* hi, const float* lo, double* out, long long n);
 template <class T>
 void launch_mu(Ctx& cx, const PhaseParams& P, const T* phi, T* g, T* mu, const Scalars* S);
 template <class T>
@@ -129,7 +149,8 @@ void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> v0, C
 // Diagnostic partial sums; out has kDiagQ doubles per block.
 constexpr int kDiagQ = 16;
 template <class T>
-void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* g, Comp3<T> vel,
+void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo, const T* g,
+                 const T* g_lo, Comp3<T> vel,
                  Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0_ring,
                  Comp3<const double> v0d, T* sigma_t, double* partials, int nblocks, double* out);
 template <class T>

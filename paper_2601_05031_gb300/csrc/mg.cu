@@ -5,6 +5,8 @@
 // (numerical-implementation section) -- this file is that method on the GPU:
 // cell-centred multigrid V-cycles (or red-black SOR), templated on the
 // storage type (float for the mixed path, double for the FP64 path).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace vsv {
@@ -220,6 +222,21 @@ __global__ void k_zero(Comp3<T> X, long long n) {
   if (t < n) X.p[blockIdx.y][t] = (T)0;
 }
 
+// Linear extrapolation in time of the initial guess: x <- 2 x - xp and
+// xp <- x (old); with extrapolate = 0 only xp <- x.
+template <class T>
+__global__ void k_extrapolate(Comp3<T> X, Comp3<T> XP, long long n, int extrapolate) {
+  const int comp = blockIdx.y;
+  T* __restrict__ x = X.p[comp];
+  T* __restrict__ xp = XP.p[comp];
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const T a = x[t];
+    if (extrapolate) x[t] = (T)2 * a - xp[t];
+    xp[t] = a;
+  }
+}
+
 // Coarsest level: e = 0, then `sweeps` red-black Gauss-Seidel sweeps in
 // shared memory by one block per component.
 template <class T>
@@ -346,6 +363,15 @@ void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp) {
 }
 
 template <class T>
+void launch_extrapolate(Ctx& cx, Comp3<T> X, Comp3<T> XP, long long n, int ncomp, int extrapolate) {
+  const long long b = std::min<long long>(blocks_for(n), 4 * 152);
+  dim3 grid((unsigned)b, ncomp);
+  cx.before(-1);
+  k_extrapolate<T><<<grid, kBlock, 0, cx.stream>>>(X, XP, n, extrapolate);
+  cx.after(-1);
+}
+
+template <class T>
 bool launch_coarse_solve(Ctx& cx, const Level& L, Comp3<T> E, Comp3<T> R, int ncomp, int sweeps,
                          double h2) {
   const long long n = L.cells();
@@ -387,6 +413,7 @@ void launch_resid_norm(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp
                                          Comp3<T>, int, bool);                                     \
   template void launch_prolong_add<T>(Ctx&, const Level&, const Level&, Comp3<T>, Comp3<T>, int);  \
   template void launch_zero<T>(Ctx&, Comp3<T>, long long, int);                                    \
+  template void launch_extrapolate<T>(Ctx&, Comp3<T>, Comp3<T>, long long, int, int);              \
   template bool launch_coarse_solve<T>(Ctx&, const Level&, Comp3<T>, Comp3<T>, int, int, double);  \
   template void launch_resid_norm<T>(Ctx&, const Level&, Comp3<T>, Rhs3<T>, int, bool, double*,    \
                                      int, Scalars*);

@@ -100,7 +100,8 @@ __global__ void k_phi_update(PhaseParams P, const T* __restrict__ phi, const T* 
 // Per-block partial sums of sum(phi) and of the area density
 // 3/(2 sqrt2) [eps/2 |grad phi|^2 + (phi^2 - 1)^2 / (4 eps)].
 template <class T>
-__global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, double* partials) {
+__global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ phi_lo,
+                            double* partials) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
   const T hih = (T)(0.5 * P.inv_h);
@@ -108,18 +109,31 @@ __global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, double* pa
   const T he = (T)(0.5 * P.eps), q = (T)(0.25 / P.eps);
   double sphi = 0.0, sarea = 0.0;
   if constexpr (std::is_same<T, float>::value) {
+    // The penalty multipliers use the small differences V - V0 and A - A0,
+    // so both sums are formed in double-word arithmetic from phi = hi + lo.
+    ScalarView<float> FL{phi_lo, P.nx, P.ny, P.nz, P.zper};
     CascadeSum cp(0.f), ca(0.f);
+    const FF hihf{P.hih_hi, P.hih_lo}, hef{P.he_hi, P.he_lo}, qf{P.q_hi, P.q_lo},
+        caf{P.ca_hi, P.ca_lo};
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
       int i, j, k;
       cell_of(t, P.nx, P.ny, i, j, k);
-      const float f = phi[t];
-      const float gx = (F(i + 1, j, k) - F(i - 1, j, k)) * hih;
-      const float gy = (F(i, j + 1, k) - F(i, j - 1, k)) * hih;
-      const float gz = (F(i, j, k + 1) - F(i, j, k - 1)) * hih;
-      const float w = f * f - 1.f;
-      cp.add(f);
-      ca.add(c_a * (he * (gx * gx + gy * gy + gz * gz) + w * w * q));
+      const FF f{phi[t], phi_lo[t]};
+      auto diff = [&](int i1, int j1, int k1, int i0, int j0, int k0) {
+        const FF a{F(i1, j1, k1), FL(i1, j1, k1)}, b{F(i0, j0, k0), FL(i0, j0, k0)};
+        return ff_mul(ff_add(a, ff_neg(b)), hihf);
+      };
+      const FF gx = diff(i + 1, j, k, i - 1, j, k);
+      const FF gy = diff(i, j + 1, k, i, j - 1, k);
+      const FF gz = diff(i, j, k + 1, i, j, k - 1);
+      const FF g2 = ff_add(ff_add(ff_mul(gx, gx), ff_mul(gy, gy)), ff_mul(gz, gz));
+      const FF w = ff_add_f(ff_mul(f, f), -1.f);
+      const FF dens = ff_mul(ff_add(ff_mul(g2, hef), ff_mul(ff_mul(w, w), qf)), caf);
+      cp.add(f.hi);
+      cp.add(f.lo);
+      ca.add(dens.hi);
+      ca.add(dens.lo);
     }
     sphi = (double)cp.hi + (double)cp.lo;
     sarea = (double)ca.hi + (double)ca.lo;
@@ -290,8 +304,8 @@ struct V0View {
 // 3 |psi'|^2, 4 w = (1-phi)/2, 5..7 w x, w y, w z, 8 energy density,
 // 9 max |div v|, 10 max |div psi|, 11 max sigma_t.
 template <class T>
-__global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ g,
-                       Comp3<T> vel, Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0r,
+__global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ phi_lo,
+                       const T* __restrict__ g, const T* __restrict__ g_lo, Comp3<T> vel, Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0r,
                        Comp3<const double> v0d, T* sigma_t, double* partials) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   double q[kDiagQ];
@@ -330,14 +344,14 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
     }
     q[2] += o2;
     q[3] += p2;
-    const double f = phi[t];
+    const double f = (double)phi[t] + (phi_lo ? (double)phi_lo[t] : 0.0);
     const double w = 0.5 * (1.0 - f);
     q[4] += w;
     q[5] += w * (i + 0.5) * h;
     q[6] += w * (j + 1.0) * h;
     q[7] += w * (P.zper ? (k + 0.5) : (k + 1.0)) * h;
     if (P.fe_kind == VSV_HELFRICH) {
-      const double gg = g[t];
+      const double gg = (double)g[t] + (g_lo ? (double)g_lo[t] : 0.0);
       q[8] += gg * gg;
     } else {
       ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
@@ -553,6 +567,158 @@ __global__ void k_fill(double* x, long long n, double v) {
   if (t < n) x[t] = v;
 }
 
+// ---------------------------------------------------------------- mixed path: double-word phi
+// Exact 7-point Laplacian of a double-word field: the hi parts are summed by
+// cascaded summation (error-free up to the final rounding), the lo parts in
+// FP32 (their own rounding is below 2^-48 of the field).
+template <class V>
+__device__ __forceinline__ FF lap7_ff(const V& H, const V& L, int i, int j, int k, float ih_hi,
+                                      float ih_lo) {
+  CascadeSum s(0.f);
+  s.add(H(i + 1, j, k));
+  s.add(H(i - 1, j, k));
+  s.add(H(i, j + 1, k));
+  s.add(H(i, j - 1, k));
+  s.add(H(i, j, k + 1));
+  s.add(H(i, j, k - 1));
+  s.add_scaled(-6.f, H(i, j, k));
+  const float lsum = L(i + 1, j, k) + L(i - 1, j, k) + L(i, j + 1, k) + L(i, j - 1, k) +
+                     L(i, j, k + 1) + L(i, j, k - 1) - 6.f * L(i, j, k);
+  const FF v = fast_two_sum(s.hi, __fadd_rn(s.lo, lsum));
+  return ff_mul(v, FF{ih_hi, ih_lo});
+}
+
+// phi^{n+1} = phi^n + dt * rate with phi^n = hi + lo; the rate itself is an
+// O(1e-4) increment and is formed in FP32 as in the FP64 path.
+__global__ void k_phi_update_ff(PhaseParams P, const float* __restrict__ phi,
+                                const float* __restrict__ phi_lo, const float* __restrict__ mu,
+                                Comp3<float> psi, Comp3<float> v0, Scalars* S, float dt,
+                                float* __restrict__ out, float* __restrict__ out_lo) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  const float ih2 = (float)P.inv_h2, hih = (float)(0.5 * P.inv_h);
+  ScalarView<float> M{mu, P.nx, P.ny, P.nz, P.zper};
+  ScalarView<float> F{phi, P.nx, P.ny, P.nz, P.zper};
+  PertView<float> X{psi.p[0], P.nx, P.ny, P.nz, P.zper};
+  PertView<float> Y{psi.p[1], P.nx, P.ny, P.nz, P.zper};
+  PertView<float> Z{psi.p[2], P.nx, P.ny, P.nz, P.zper};
+  const float lmu = lap7<float>(M, i, j, k, ih2);
+  const float gx = (F(i + 1, j, k) - F(i - 1, j, k)) * hih;
+  const float gy = (F(i, j + 1, k) - F(i, j - 1, k)) * hih;
+  const float gz = (F(i, j, k + 1) - F(i, j, k - 1)) * hih;
+  const long long jk = j + (long long)k * P.ny;
+  const float vx = v0.p[0][jk] + ((Z(i, j + 1, k) - Z(i, j - 1, k)) - (Y(i, j, k + 1) - Y(i, j, k - 1))) * hih;
+  const float vy = v0.p[1][jk] + ((X(i, j, k + 1) - X(i, j, k - 1)) - (Z(i + 1, j, k) - Z(i - 1, j, k))) * hih;
+  const float vz = v0.p[2][jk] + ((Y(i + 1, j, k) - Y(i - 1, j, k)) - (X(i, j + 1, k) - X(i, j - 1, k))) * hih;
+  const float rate = (float)P.mobility * (lmu + S->lambda_vf) - (vx * gx + vy * gy + vz * gz);
+  const FF v = ff_add_f(FF{phi[t], phi_lo[t]}, dt * rate);
+  out[t] = v.hi;
+  out_lo[t] = v.lo;
+  if (!isfinite(v.hi)) atomicOr(&S->nonfinite, 1);
+}
+
+// g = phi^3 - phi - eps^2 lap phi in double-word arithmetic.
+__global__ void k_helfrich_g_ff(PhaseParams P, const float* __restrict__ phi,
+                                const float* __restrict__ phi_lo, float* __restrict__ g,
+                                float* __restrict__ g_lo) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  ScalarView<float> H{phi, P.nx, P.ny, P.nz, P.zper};
+  ScalarView<float> L{phi_lo, P.nx, P.ny, P.nz, P.zper};
+  const FF f{phi[t], phi_lo[t]};
+  const FF lphi = lap7_ff(H, L, i, j, k, P.ih2_hi, P.ih2_lo);
+  const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
+  const FF r = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.e2_hi, P.e2_lo})));
+  g[t] = r.hi;
+  g_lo[t] = r.lo;
+}
+
+// CH:       mu = phi^3 - phi - sigma lap phi
+// Helfrich: mu = cf2 [(3 phi^2 - 1) g - eps^2 lap g] - gamma_A lap phi
+__global__ void k_mu_ff(PhaseParams P, const float* __restrict__ phi, const float* __restrict__ phi_lo,
+                        const float* __restrict__ g, const float* __restrict__ g_lo,
+                        const Scalars* S, float* __restrict__ mu) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (t >= n) return;
+  int i, j, k;
+  cell_of(t, P.nx, P.ny, i, j, k);
+  ScalarView<float> H{phi, P.nx, P.ny, P.nz, P.zper};
+  ScalarView<float> L{phi_lo, P.nx, P.ny, P.nz, P.zper};
+  const FF f{phi[t], phi_lo[t]};
+  const FF lphi = lap7_ff(H, L, i, j, k, P.ih2_hi, P.ih2_lo);
+  if (P.fe_kind == VSV_CAHN_HILLIARD) {
+    const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
+    mu[t] = ff_round(ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.sig_hi, P.sig_lo}))));
+    return;
+  }
+  ScalarView<float> GH{g, P.nx, P.ny, P.nz, P.zper};
+  ScalarView<float> GL{g_lo, P.nx, P.ny, P.nz, P.zper};
+  const FF gg{g[t], g_lo[t]};
+  const FF lg = lap7_ff(GH, GL, i, j, k, P.ih2_hi, P.ih2_lo);
+  const FF w = ff_add_f(ff_mul_f(ff_mul(f, f), 3.f), -1.f);
+  const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2_hi, P.e2_lo})));
+  const FF m = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, S->gamma_af)));
+  mu[t] = ff_round(m);
+}
+
+__global__ void k_split_ff(const double* __restrict__ in, float* __restrict__ hi,
+                           float* __restrict__ lo, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double d = in[t];
+  const float h = (float)d;
+  hi[t] = h;
+  lo[t] = (float)(d - (double)h);
+}
+
+__global__ void k_merge_ff(const float* __restrict__ hi, const float* __restrict__ lo,
+                           double* __restrict__ out, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (double)hi[t] + (double)lo[t];
+}
+
+void launch_phi_update_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo,
+                          const float* mu, Comp3<float> psi, Comp3<float> v0, const Scalars* S,
+                          float dt, float* out, float* out_lo) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  cx.before(VSV_KCLASS_PHASE);
+  k_phi_update_ff<<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, phi_lo, mu, psi, v0,
+                                                      const_cast<Scalars*>(S), dt, out, out_lo);
+  cx.after(VSV_KCLASS_PHASE);
+}
+
+void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo, float* g,
+                  float* g_lo, float* mu, const Scalars* S) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  if (P.fe_kind == VSV_HELFRICH) {
+    cx.before(VSV_KCLASS_PHASE);
+    k_helfrich_g_ff<<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, phi_lo, g, g_lo);
+    cx.after(VSV_KCLASS_PHASE);
+  }
+  cx.before(VSV_KCLASS_PHASE);
+  k_mu_ff<<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, S, mu);
+  cx.after(VSV_KCLASS_PHASE);
+}
+
+void launch_split_ff(Ctx& cx, const double* in, float* hi, float* lo, long long n) {
+  cx.before(-1);
+  k_split_ff<<<nblk(n), kBlock, 0, cx.stream>>>(in, hi, lo, n);
+  cx.after(-1);
+}
+
+void launch_merge_ff(Ctx& cx, const float* hi, const float* lo, double* out, long long n) {
+  cx.before(-1);
+  k_merge_ff<<<nblk(n), kBlock, 0, cx.stream>>>(hi, lo, out, n);
+  cx.after(-1);
+}
+
 // ---------------------------------------------------------------- launchers
 template <class T>
 void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Comp3<T> psi,
@@ -565,10 +731,10 @@ void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu,
 }
 
 template <class T>
-void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, double* partials, int nblocks,
-                      Scalars* S, int init) {
+void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo,
+                      double* partials, int nblocks, Scalars* S, int init) {
   cx.before(VSV_KCLASS_PHASE);
-  k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, partials);
+  k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
   cx.after(VSV_KCLASS_PHASE);
   cx.before(-1);
   k_va_finalize<<<1, kBlock, 0, cx.stream>>>(partials, nblocks, (long long)P.nx * P.ny * P.nz, S,
@@ -607,11 +773,12 @@ void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> v0, C
 }
 
 template <class T>
-void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* g, Comp3<T> vel,
+void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo, const T* g,
+                 const T* g_lo, Comp3<T> vel,
                  Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0_ring,
                  Comp3<const double> v0d, T* sigma_t, double* partials, int nblocks, double* out) {
   cx.before(-1);
-  k_diag<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, g, vel, omega, psi, psi0_ring, v0d, sigma_t,
+  k_diag<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, vel, omega, psi, psi0_ring, v0d, sigma_t,
                                                partials);
   cx.after(-1);
   cx.before(-1);
@@ -699,13 +866,14 @@ void launch_fill(Ctx& cx, double* x, long long n, double v) {
 #define VSV_INST(T)                                                                               \
   template void launch_phi_update<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>,      \
                                      Comp3<T>, const Scalars*, T, T*);                            \
-  template void launch_reduce_va<T>(Ctx&, const PhaseParams&, const T*, double*, int, Scalars*,   \
-                                    int);                                                         \
+  template void launch_reduce_va<T>(Ctx&, const PhaseParams&, const T*, const T*, double*, int,   \
+                                    Scalars*, int);                                               \
   template void launch_mu<T>(Ctx&, const PhaseParams&, const T*, T*, T*, const Scalars*);         \
   template void launch_source<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>,          \
                                  Comp3<T>);                                                       \
   template void launch_velocity<T>(Ctx&, const PhaseParams&, Comp3<T>, Comp3<T>, Comp3<T>);       \
-  template void launch_diag<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>, Comp3<T>,  \
+  template void launch_diag<T>(Ctx&, const PhaseParams&, const T*, const T*, const T*, const T*,  \
+                               Comp3<T>, Comp3<T>,                                                \
                                Comp3<T>, Comp3<const double>, Comp3<const double>, T*, double*,   \
                                int, double*);                                                     \
   template void launch_stress_profile<T>(Ctx&, const PhaseParams&, Comp3<T>, double*);            \
