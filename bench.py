@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--nx", type=int, default=512)
     ap.add_argument("--ny", type=int, default=256)
     ap.add_argument("--nz", type=int, default=256)
-    ap.add_argument("--cycles", type=int, default=2, help="V-cycles per Poisson solve")
+    ap.add_argument("--cycles", type=int, default=4, help="V-cycles per Poisson solve")
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -117,6 +117,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(value, dist, device):
+    """Largest value over all ranks (the slowest replica's time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size, cells_per_rank, steps, ms_max):
+    """Whole-job Mcell-steps/s: every rank's cell-steps over the slowest time."""
+    return world_size * cells_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
 # ---------------------------------------------------------------- GPU arm
 def make_sim(w, prec, cycles):
     from paper_2601_05031_gb300 import vsv as V
@@ -172,11 +188,8 @@ def run_gpu(args, ws, rank, local):
     with ClockSampler(local) as clk:
         ms = timed_steps(sim, args.steps, w.dt, torch, barrier)
     launches = sim.kernel_launches() - launches0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * N * args.steps / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(ws, N, args.steps, ms)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),

@@ -34,12 +34,22 @@ struct vsv_grid {
   void* mu = nullptr;
   void* g = nullptr;
   float* g_lo = nullptr;
+  float* mu_lo = nullptr;    // mixed path: low words of mu and of the source f
+  float* f_lo[3] = {};
   void* f[3] = {};
   void* om[3] = {};
   void* ps[3] = {};
   void* om_prev[3] = {};     // previous step's solutions (initial-guess extrapolation)
   void* ps_prev[3] = {};
   bool prev_valid = false;
+  // mixed path: low words of the double-word iterates, the FP32 correction e
+  // and defect r of the outer defect correction
+  float* om_lo[3] = {};
+  float* ps_lo[3] = {};
+  float* om_prev_lo[3] = {};
+  float* ps_prev_lo[3] = {};
+  float* e0[3] = {};
+  float* r0[3] = {};
   void* stage_a = nullptr;   // N * 8 bytes
   void* stage_b = nullptr;   // N * 8 bytes
   void* mg_e[kMaxLevels][3] = {};
@@ -134,6 +144,16 @@ size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
     p = take((size_t)N * 4); if (g) g->phi_lo[0] = (float*)p;
     p = take((size_t)N * 4); if (g) g->phi_lo[1] = (float*)p;
     p = take((size_t)N * 4); if (g) g->g_lo = (float*)p;
+    p = take((size_t)N * 4); if (g) g->mu_lo = (float*)p;
+    for (int c = 0; c < 3; ++c) {
+      p = take((size_t)N * 4); if (g) g->f_lo[c] = (float*)p;
+      p = take((size_t)N * 4); if (g) g->om_lo[c] = (float*)p;
+      p = take((size_t)N * 4); if (g) g->ps_lo[c] = (float*)p;
+      p = take((size_t)N * 4); if (g) g->om_prev_lo[c] = (float*)p;
+      p = take((size_t)N * 4); if (g) g->ps_prev_lo[c] = (float*)p;
+      p = take((size_t)N * 4); if (g) g->e0[c] = (float*)p;
+      p = take((size_t)N * 4); if (g) g->r0[c] = (float*)p;
+    }
   }
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->f[c] = p; }
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->om[c] = p; }
@@ -207,6 +227,16 @@ bool z_periodic(const vsv_grid* g) {
 // Multigrid levels for per-axis periodic flags: all active axes are halved
 // together while every active extent is even (periodic extents must stay
 // even); coarse wall closure alpha_l = (2^l - 1) / (2^l + 1).
+void set_reciprocals(Level& L) {
+  const int d2 = 2 * (L.act[0] + L.act[1] + L.act[2]);
+  for (int q = 0; q < 7; ++q) {
+    const double cd = (double)d2 + L.alpha * q;
+    const float cf = (float)d2 + L.alphaf * (float)q;
+    L.rcd[q] = cd > 0 ? 1.0 / cd : 0.0;
+    L.rcf[q] = cf > 0 ? 1.0f / cf : 0.0f;
+  }
+}
+
 std::vector<Level> build_levels(int nx, int ny, int nz, double h, const int per[3], int max_levels,
                                 int cap_levels) {
   std::vector<Level> lv;
@@ -220,6 +250,7 @@ std::vector<Level> build_levels(int nx, int ny, int nz, double h, const int per[
   L.inv_h2 = 1.0 / (h * h);
   L.alphaf = 0.f;
   L.inv_h2f = (float)L.inv_h2;
+  set_reciprocals(L);
   lv.push_back(L);
   const int maxl = std::min(std::max(max_levels, 1), cap_levels);
   while ((int)lv.size() < maxl) {
@@ -242,6 +273,7 @@ std::vector<Level> build_levels(int nx, int ny, int nz, double h, const int per[
     C.inv_h2 = 1.0 / (h * h * p2 * p2);
     C.alphaf = (float)C.alpha;
     C.inv_h2f = (float)C.inv_h2;
+    set_reciprocals(C);
     lv.push_back(C);
   }
   return lv;
@@ -270,8 +302,11 @@ Comp3<T> comp3(void* a, void* b, void* c) {
 // ---------------------------------------------------------------- solvers
 // nu red-black sweeps on level l: the fused single-pass kernel (ping-pong
 // with the level's scratch) where it applies, else the per-colour kernels.
+// x_zero: X is known to be zero (a correction from e = 0): the first fused
+// sweep then does not read it, and the per-colour path zeroes it first.
 template <class T>
-void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp, int nu) {
+void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp, int nu,
+            bool x_zero) {
   const double h2 = 1.0 / L.inv_h2;
   const int kc = (l == 0) ? VSV_KCLASS_SMOOTH_FINE : VSV_KCLASS_SMOOTH;
   if constexpr (std::is_same<T, float>::value) {
@@ -282,9 +317,11 @@ void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp
       int nzc = (int)std::max(1LL, (want + tiles - 1) / tiles);
       int zchunk = std::max(16, (L.n[2] + nzc - 1) / nzc);
       int s = 0;
+      bool z = x_zero;
       for (; s + 1 < nu; s += 2) {
-        launch_rbgs_fused(g->cx, L, X, Tt, R, ncomp, zchunk, kc);
-        launch_rbgs_fused(g->cx, L, Tt, X, R, ncomp, zchunk, kc);
+        launch_rbgs_fused(g->cx, L, X, Tt, R, ncomp, zchunk, kc, z);
+        launch_rbgs_fused(g->cx, L, Tt, X, R, ncomp, zchunk, kc, false);
+        z = false;
       }
       for (; s < nu; ++s) {
         launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
@@ -293,6 +330,7 @@ void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp
       return;
     }
   }
+  if (x_zero) launch_zero<T>(g->cx, X, L.cells(), ncomp);
   for (int s = 0; s < nu; ++s) {
     launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
     launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
@@ -300,7 +338,8 @@ void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp
 }
 
 template <class T>
-void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T> R, int ncomp) {
+void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T> R, int ncomp,
+            bool exact_fine = true, bool x_zero = false) {
   const Level& L = lv[l];
   const double h2 = 1.0 / L.inv_h2;
   const bool last = (l + 1 == (int)lv.size());
@@ -311,6 +350,8 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
       Comp3<T> RR{{(T*)R.B[0], (T*)R.B[1], (T*)R.B[2]}};
       if (launch_coarse_solve<T>(g->cx, L, E, RR, ncomp, g->sol.coarse_sweeps, h2)) return;
       launch_zero<T>(g->cx, E, L.cells(), ncomp);
+    } else if (x_zero) {
+      launch_zero<T>(g->cx, X, L.cells(), ncomp);
     }
     for (int s = 0; s < g->sol.coarse_sweeps; ++s) {
       launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
@@ -318,17 +359,16 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
     }
     return;
   }
-  smooth<T>(g, L, l, X, R, ncomp, g->sol.nu1);
+  smooth<T>(g, L, l, X, R, ncomp, g->sol.nu1, x_zero);
   const Level& C = lv[l + 1];
   Comp3<T> EC = comp3<T>(g->mg_e[l + 1][0], g->mg_e[l + 1][1], g->mg_e[l + 1][2]);
   Comp3<T> RC = comp3<T>(g->mg_r[l + 1][0], g->mg_r[l + 1][1], g->mg_r[l + 1][2]);
-  const bool exact = std::is_same<T, float>::value && l == 0;
+  const bool exact = std::is_same<T, float>::value && l == 0 && exact_fine;
   launch_resid_restrict<T>(g->cx, L, C, X, R, RC, ncomp, exact);
-  if (l + 2 < (int)lv.size()) launch_zero<T>(g->cx, EC, C.cells(), ncomp);
   Rhs3<T> RCr{{RC.p[0], RC.p[1], RC.p[2]}, {nullptr, nullptr, nullptr}, (T)1};
-  vcycle<T>(g, lv, l + 1, EC, RCr, ncomp);
+  vcycle<T>(g, lv, l + 1, EC, RCr, ncomp, exact_fine, true);
   launch_prolong_add<T>(g->cx, L, C, X, EC, ncomp);
-  smooth<T>(g, L, l, X, R, ncomp, g->sol.nu2);
+  smooth<T>(g, L, l, X, R, ncomp, g->sol.nu2, false);
 }
 
 // relres = max over components of ||b - L x|| / ||b|| (||b|| = 0 -> ||r||).
@@ -408,6 +448,61 @@ vsv_status solve(vsv_grid* g, const std::vector<Level>& lv, Comp3<T> X, Rhs3<T> 
   return VSV_OK;
 }
 
+// Mixed-path solve of L x = b with the double-word iterate x = (XH, XL) by
+// outer defect correction: r = b - L x exactly, one FP32 V-cycle for L e = r
+// from e = 0, x += e.  fixed > 0: exactly that many corrections without
+// synchronisation; else correct until ||r|| <= tol ||b|| or max_cycles.
+vsv_status solve_dc(vsv_grid* g, const std::vector<Level>& lv, Comp3<float> XH, Comp3<float> XL,
+                    Rhs3<float> R, Comp3<float> BL, int ncomp, int fixed, double tol,
+                    int max_cycles, int check_every, int* cycles_out, double* relres_out) {
+  const Level& L = lv[0];
+  Comp3<float> E = comp3<float>(g->e0[0], g->e0[1], g->e0[2]);
+  Comp3<float> RR = comp3<float>(g->r0[0], g->r0[1], g->r0[2]);
+  Rhs3<float> RE{{RR.p[0], RR.p[1], RR.p[2]}, {nullptr, nullptr, nullptr}, 1.f};
+  auto correct = [&]() {
+    vcycle<float>(g, lv, 0, E, RE, ncomp, false, true);
+    launch_update_dw(g->cx, XH, XL, E, L.cells(), ncomp);
+  };
+  if (fixed > 0) {
+    for (int c = 0; c < fixed; ++c) {
+      launch_defect_dw(g->cx, L, XH, XL, R, BL, RR, ncomp, nullptr, g->red_blocks);
+      correct();
+    }
+    CKL();
+    if (cycles_out) *cycles_out = fixed;
+    if (relres_out) *relres_out = -1.0;
+    return VSV_OK;
+  }
+  const int every = std::max(1, check_every);
+  int c = 0;
+  double rr = INFINITY;
+  while (true) {
+    const bool check = (c % every == 0) || c >= max_cycles;
+    launch_defect_dw(g->cx, L, XH, XL, R, BL, RR, ncomp, check ? g->partials : nullptr,
+                     g->red_blocks);
+    if (check) {
+      launch_norm_finalize(g->cx, g->partials, g->red_blocks, ncomp, g->S);
+      Scalars hs;
+      CK(cudaMemcpyAsync(&hs, g->S, sizeof(Scalars), cudaMemcpyDeviceToHost, g->cx.stream));
+      CK(cudaStreamSynchronize(g->cx.stream));
+      rr = 0.0;
+      for (int q = 0; q < ncomp; ++q) {
+        const double rn = std::sqrt(hs.rnorm2[q]), bn = std::sqrt(hs.bnorm2[q]);
+        rr = std::max(rr, bn > 0 ? rn / bn : rn);
+      }
+      if (rr <= tol || c >= max_cycles) break;
+    }
+    correct();
+    ++c;
+  }
+  CKL();
+  if (cycles_out) *cycles_out = c;
+  if (relres_out) *relres_out = rr;
+  if (!std::isfinite(rr)) return fail(g, VSV_ENONFINITE, "non-finite residual%s");
+  if (rr > tol) return fail(g, VSV_ENOCONV, "Poisson solve stopped above tolerance%s");
+  return VSV_OK;
+}
+
 // ---------------------------------------------------------------- phase-field helpers
 PhaseParams phase_params(const vsv_grid* g) {
   PhaseParams P{};
@@ -433,6 +528,7 @@ PhaseParams phase_params(const vsv_grid* g) {
   split(0.5 * g->fe.eps, P.he_hi, P.he_lo);
   split(0.25 / g->fe.eps, P.q_hi, P.q_lo);
   split(3.0 / (2.0 * std::sqrt(2.0)), P.ca_hi, P.ca_lo);
+  split(1.0 / g->flow.eta, P.ie_hi, P.ie_lo);
   std::memset(P.vwall, 0, sizeof P.vwall);
   if (g->flow.kind == VSV_COUETTE) {
     P.vwall[0][0] = g->flow.v_lo;
@@ -459,8 +555,36 @@ Rhs3<T> rhs_psi(vsv_grid* g) {
                  {(T*)g->s_ps_neg_t[0], (T*)g->s_ps_neg_t[1], (T*)g->s_ps_neg_t[2]}, (T)-1};
 }
 
+vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
+  const vsv_solver_params& s = g->sol;
+  const int fixed = initial ? 0 : s.fixed_cycles;
+  const bool extrap = !initial && s.extrapolate && g->prev_valid;
+  Comp3<float> OH = comp3<float>(g->om[0], g->om[1], g->om[2]);
+  Comp3<float> OL = comp3<float>(g->om_lo[0], g->om_lo[1], g->om_lo[2]);
+  Comp3<float> PH = comp3<float>(g->ps[0], g->ps[1], g->ps[2]);
+  Comp3<float> PL = comp3<float>(g->ps_lo[0], g->ps_lo[1], g->ps_lo[2]);
+  if (!initial)
+    launch_extrapolate_dw(g->cx, OH, OL, comp3<float>(g->om_prev[0], g->om_prev[1], g->om_prev[2]),
+                          comp3<float>(g->om_prev_lo[0], g->om_prev_lo[1], g->om_prev_lo[2]), g->N,
+                          3, extrap ? 1 : 0);
+  Comp3<float> FL = comp3<float>(g->f_lo[0], g->f_lo[1], g->f_lo[2]);
+  vsv_status st = solve_dc(g, g->flow_levels, OH, OL, rhs_omega<float>(g), FL, 3, fixed, s.tol,
+                           s.max_cycles, s.check_every, &g->last_cycles[0], &g->last_relres[0]);
+  if (st != VSV_OK) return st;
+  if (!initial)
+    launch_extrapolate_dw(g->cx, PH, PL, comp3<float>(g->ps_prev[0], g->ps_prev[1], g->ps_prev[2]),
+                          comp3<float>(g->ps_prev_lo[0], g->ps_prev_lo[1], g->ps_prev_lo[2]), g->N,
+                          3, extrap ? 1 : 0);
+  // rhs of the stream-vector problem: -(omega'_hi + omega'_lo) - s_psi
+  st = solve_dc(g, g->flow_levels, PH, PL, rhs_psi<float>(g), OL, 3, fixed, s.tol, s.max_cycles,
+                s.check_every, &g->last_cycles[1], &g->last_relres[1]);
+  g->prev_valid = !initial;
+  return st;
+}
+
 template <class T>
 vsv_status flow_solves(vsv_grid* g, bool initial) {
+  if constexpr (std::is_same<T, float>::value) return flow_solves_mixed(g, initial);
   Comp3<T> O = comp3<T>(g->om[0], g->om[1], g->om[2]);
   Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
   const vsv_solver_params& s = g->sol;
@@ -492,11 +616,24 @@ void refresh_phase(vsv_grid* g, int init) {
   if constexpr (std::is_same<T, float>::value) {
     const float* lo = g->phi_lo[g->cur];
     launch_reduce_va<float>(g->cx, P, phi, lo, g->partials, g->red_blocks, g->S, init);
-    launch_mu_ff(g->cx, P, phi, lo, (float*)g->g, g->g_lo, (float*)g->mu, g->S);
+    launch_mu_ff(g->cx, P, phi, lo, (float*)g->g, g->g_lo, (float*)g->mu, g->mu_lo, g->S);
   } else {
     launch_reduce_va<T>(g->cx, P, phi, nullptr, g->partials, g->red_blocks, g->S, init);
     launch_mu<T>(g->cx, P, phi, (T*)g->g, (T*)g->mu, g->S);
   }
+}
+
+// f = grad phi x grad mu / eta - s_omega of the current phi and mu
+template <class T>
+void launch_flow_source(vsv_grid* g, const PhaseParams& P) {
+  Comp3<T> SO = comp3<T>(g->s_om_t[0], g->s_om_t[1], g->s_om_t[2]);
+  Comp3<T> F = comp3<T>(g->f[0], g->f[1], g->f[2]);
+  const T* phi = (const T*)g->phi[g->cur];
+  if constexpr (std::is_same<T, float>::value)
+    launch_source_ff(g->cx, P, phi, g->phi_lo[g->cur], (const float*)g->mu, g->mu_lo, SO, F,
+                     comp3<float>(g->f_lo[0], g->f_lo[1], g->f_lo[2]));
+  else
+    launch_source<T>(g->cx, P, phi, (const T*)g->mu, SO, F);
 }
 
 template <class T>
@@ -520,9 +657,7 @@ vsv_status step_impl(vsv_grid* g, double dt) {
   // 4-5: V, A of phi^{n+1}, gamma_A, then mu^{n+1}
   refresh_phase<T>(g, 0);
   // 6: source f = grad phi x grad mu / eta - s_omega
-  Comp3<T> SO = comp3<T>(g->s_om_t[0], g->s_om_t[1], g->s_om_t[2]);
-  Comp3<T> F = comp3<T>(g->f[0], g->f[1], g->f[2]);
-  launch_source<T>(g->cx, P, phin, (const T*)g->mu, SO, F);
+  launch_flow_source<T>(g, P);
   CKL();
   // 7-8: vorticity then stream-vector Poisson solves
   vsv_status st = flow_solves<T>(g, false);
@@ -535,11 +670,13 @@ template <class T>
 vsv_status set_phi_impl(vsv_grid* g) {
   refresh_phase<T>(g, 1);
   PhaseParams P = phase_params(g);
-  Comp3<T> SO = comp3<T>(g->s_om_t[0], g->s_om_t[1], g->s_om_t[2]);
-  Comp3<T> F = comp3<T>(g->f[0], g->f[1], g->f[2]);
-  launch_source<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->mu, SO, F);
+  launch_flow_source<T>(g, P);
   launch_zero<T>(g->cx, comp3<T>(g->om[0], g->om[1], g->om[2]), g->N, 3);
   launch_zero<T>(g->cx, comp3<T>(g->ps[0], g->ps[1], g->ps[2]), g->N, 3);
+  if constexpr (std::is_same<T, float>::value) {
+    launch_zero<float>(g->cx, comp3<float>(g->om_lo[0], g->om_lo[1], g->om_lo[2]), g->N, 3);
+    launch_zero<float>(g->cx, comp3<float>(g->ps_lo[0], g->ps_lo[1], g->ps_lo[2]), g->N, 3);
+  }
   CKL();
   g->phase_stale = false;
   return flow_solves<T>(g, true);
@@ -626,24 +763,40 @@ vsv_status get_field_impl(vsv_grid* g, int field, void* dst, int dt, int on_devi
   }
   const T* src = nullptr;
   T* tmp = (T*)g->stage_a;
+  const bool mixed = std::is_same<T, float>::value;
+  const cudaMemcpyKind dkind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  // double-word perturbation (mixed path) exported in FP64: hi + lo (+ base)
+  auto export_dw = [&](const float* hi, const float* lo, const double* tab) -> vsv_status {
+    launch_full_field_dw(g->cx, P, hi, lo, tab, 1, (double*)g->stage_a);
+    CKL();
+    CK(cudaMemcpyAsync(dst, g->stage_a, g->N * 8, dkind, g->cx.stream));
+    if (!on_device) CK(cudaStreamSynchronize(g->cx.stream));
+    return VSV_OK;
+  };
+  const Comp3<T> PSL = comp3<T>(g->ps_lo[0], g->ps_lo[1], g->ps_lo[2]);
   if (field == VSV_FIELD_PHI) return export_phi<T>(g, dt, on_device, dst);
-  else if (field == VSV_FIELD_MU) src = (const T*)g->mu;
+  else if (field == VSV_FIELD_MU) {
+    if (mixed && dt == VSV_DTYPE_F64) return export_dw((const float*)g->mu, g->mu_lo, nullptr);
+    src = (const T*)g->mu;
+  }
   else if (field >= VSV_FIELD_OMEGA_X && field <= VSV_FIELD_OMEGA_Z) {
     const int c = field - VSV_FIELD_OMEGA_X;
-    launch_full_field<T>(g->cx, P, (const T*)g->om[c], g->om_ring[c], 1, tmp);
+    if (mixed && dt == VSV_DTYPE_F64) return export_dw((const float*)g->om[c], g->om_lo[c], g->om_ring[c]);
+    launch_full_field<T>(g->cx, P, (const T*)g->om[c], (const T*)g->om_lo[c], g->om_ring[c], 1, tmp);
     src = tmp;
   } else if (field >= VSV_FIELD_PSI_X && field <= VSV_FIELD_PSI_Z) {
     const int c = field - VSV_FIELD_PSI_X;
-    launch_full_field<T>(g->cx, P, (const T*)g->ps[c], g->ps_ring[c], 1, tmp);
+    if (mixed && dt == VSV_DTYPE_F64) return export_dw((const float*)g->ps[c], g->ps_lo[c], g->ps_ring[c]);
+    launch_full_field<T>(g->cx, P, (const T*)g->ps[c], (const T*)g->ps_lo[c], g->ps_ring[c], 1, tmp);
     src = tmp;
   } else if (field >= VSV_FIELD_VEL_X && field <= VSV_FIELD_VEL_Z) {
     Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
-    launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+    launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]), PSL,
                        comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
     src = V.p[field - VSV_FIELD_VEL_X];
   } else if (field == VSV_FIELD_STRESS_T) {
     Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
-    launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+    launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]), PSL,
                        comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
     launch_diag<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->phi_lo[g->cur],
                    (const T*)g->g, (const T*)g->g_lo, V,
@@ -651,9 +804,13 @@ vsv_status get_field_impl(vsv_grid* g, int field, void* dst, int dt, int on_devi
                    ring3(g->ps_ring), ring3(g->v0d), tmp, g->partials, g->red_blocks, g->dout);
     src = tmp;
   } else if (field >= VSV_FIELD_OMEGA_PERT_X && field <= VSV_FIELD_OMEGA_PERT_Z) {
-    src = (const T*)g->om[field - VSV_FIELD_OMEGA_PERT_X];
+    const int c = field - VSV_FIELD_OMEGA_PERT_X;
+    if (mixed && dt == VSV_DTYPE_F64) return export_dw((const float*)g->om[c], g->om_lo[c], nullptr);
+    src = (const T*)g->om[c];
   } else if (field >= VSV_FIELD_PSI_PERT_X && field <= VSV_FIELD_PSI_PERT_Z) {
-    src = (const T*)g->ps[field - VSV_FIELD_PSI_PERT_X];
+    const int c = field - VSV_FIELD_PSI_PERT_X;
+    if (mixed && dt == VSV_DTYPE_F64) return export_dw((const float*)g->ps[c], g->ps_lo[c], nullptr);
+    src = (const T*)g->ps[c];
   } else {
     return fail(g, VSV_EINVAL, "unknown field%s");
   }
@@ -769,7 +926,7 @@ vsv_status build_base_flow(vsv_grid* g) {
 
 void default_solver(vsv_solver_params* s, int prec) {
   s->kind = VSV_SOLVER_MG;
-  s->tol = prec == VSV_FP64 ? 1e-12 : 1e-7;
+  s->tol = prec == VSV_FP64 ? 1e-12 : 1e-10;
   s->max_cycles = 200;
   s->fixed_cycles = 0;
   s->check_every = 1;
@@ -993,8 +1150,45 @@ vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, i
     if (s != VSV_OK) return s;
     return s2;
   };
+  // mixed path: double-word rhs and iterate, outer defect correction
+  auto run_mixed = [&]() -> vsv_status {
+    if (g->sol.kind != VSV_SOLVER_MG) return fail(g, VSV_EINVAL, "mixed precision solves use MG%s");
+    float* bh = (float*)g->f[0];
+    float* bl = (float*)g->stage_a;           // first N floats of the FP64 stage
+    float* xh = (float*)g->f[1];
+    float* xl = (float*)g->f[2];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    auto split_in = [&](const void* src, float* hi, float* lo) -> vsv_status {
+      if (dtype == VSV_DTYPE_F64) {
+        CK(cudaMemcpyAsync(g->stage_b, src, g->N * 8, kind, g->cx.stream));
+        launch_split_ff(g->cx, (const double*)g->stage_b, hi, lo, g->N);
+      } else {
+        CK(cudaMemcpyAsync(hi, src, g->N * 4, kind, g->cx.stream));
+        CK(cudaMemsetAsync(lo, 0, g->N * 4, g->cx.stream));
+      }
+      CK(cudaStreamSynchronize(g->cx.stream));
+      return VSV_OK;
+    };
+    vsv_status s = split_in(rhs, bh, bl);
+    if (s != VSV_OK) return s;
+    s = split_in(x, xh, xl);
+    if (s != VSV_OK) return s;
+    Comp3<float> XH{{xh, nullptr, nullptr}}, XL{{xl, nullptr, nullptr}}, BL{{bl, nullptr, nullptr}};
+    Rhs3<float> R{{bh, nullptr, nullptr}, {nullptr, nullptr, nullptr}, 1.f};
+    vsv_status s2 = solve_dc(g, lv, XH, XL, R, BL, 1, 0, tol, max_cycles, g->sol.check_every,
+                             cycles_out, relres_out);
+    const cudaMemcpyKind okind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (dtype == VSV_DTYPE_F64) {
+      launch_merge_ff(g->cx, xh, xl, (double*)g->stage_b, g->N);
+      CK(cudaMemcpyAsync(x, g->stage_b, g->N * 8, okind, g->cx.stream));
+    } else {
+      CK(cudaMemcpyAsync(x, xh, g->N * 4, okind, g->cx.stream));
+    }
+    CK(cudaStreamSynchronize(g->cx.stream));
+    return s2;
+  };
   if (g->prec == VSV_FP64) st = run(double{});
-  else st = run(float{});
+  else st = run_mixed();
   return st;
 }
 
@@ -1022,9 +1216,24 @@ vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int
     dst = g->ps[field - VSV_FIELD_PSI_PERT_X];
   else
     return fail(g, VSV_EINVAL, "field cannot be set%s");
-  vsv_status st = g->prec == VSV_FP64
-                      ? import_field<double>(g, src, dtype, on_device, (double*)dst, g->N)
-                      : import_field<float>(g, src, dtype, on_device, (float*)dst, g->N);
+  vsv_status st;
+  if (g->prec == VSV_FP64) {
+    st = import_field<double>(g, src, dtype, on_device, (double*)dst, g->N);
+  } else {
+    float* lo = (field <= VSV_FIELD_OMEGA_PERT_Z) ? g->om_lo[field - VSV_FIELD_OMEGA_PERT_X]
+                                                   : g->ps_lo[field - VSV_FIELD_PSI_PERT_X];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (dtype == VSV_DTYPE_F64) {
+      CK(cudaMemcpyAsync(g->stage_b, src, g->N * 8, kind, g->cx.stream));
+      launch_split_ff(g->cx, (const double*)g->stage_b, (float*)dst, lo, g->N);
+    } else {
+      CK(cudaMemcpyAsync(dst, src, g->N * 4, kind, g->cx.stream));
+      CK(cudaMemsetAsync(lo, 0, g->N * 4, g->cx.stream));
+    }
+    CKL();
+    if (!on_device) CK(cudaStreamSynchronize(g->cx.stream));
+    st = VSV_OK;
+  }
   if (st == VSV_OK && field == VSV_FIELD_PHI) g->phase_stale = true;
   if (st == VSV_OK && field != VSV_FIELD_PHI) g->prev_valid = false;
   return st;
@@ -1042,6 +1251,7 @@ vsv_status vsv_get_diagnostics(vsv_grid* g, vsv_diag* out) {
     }
     Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
     launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+                       comp3<T>(g->ps_lo[0], g->ps_lo[1], g->ps_lo[2]),
                        comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
     launch_diag<T>(g->cx, P, (const T*)g->phi[g->cur], (const T*)g->phi_lo[g->cur],
                    (const T*)g->g, (const T*)g->g_lo, V,
@@ -1099,6 +1309,7 @@ vsv_status vsv_get_stress_profile(vsv_grid* g, double* out) {
     using T = decltype(tag);
     Comp3<T> V = comp3<T>(g->f[0], g->f[1], g->f[2]);
     launch_velocity<T>(g->cx, P, comp3<T>(g->ps[0], g->ps[1], g->ps[2]),
+                       comp3<T>(g->ps_lo[0], g->ps_lo[1], g->ps_lo[2]),
                        comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]), V);
     launch_stress_profile<T>(g->cx, P, V, g->profile);
   };
@@ -1110,8 +1321,6 @@ vsv_status vsv_get_stress_profile(vsv_grid* g, double* out) {
   return VSV_OK;
 }
 
-// Blob: header, then phi, omega'(3), psi'(3), the previous step's omega'(3)
-// and psi'(3) (initial-guess extrapolation), then (mixed) the low words of phi.
 struct StateHeader {
   char magic[8];
   int nx, ny, nz, prec;
@@ -1119,12 +1328,33 @@ struct StateHeader {
   long long steps;
   int prev_valid, pad;
 };
-constexpr int kStateFields = 13;
+
+// Device buffers of the state blob, in blob order: phi, omega'(3), psi'(3),
+// the previous step's omega'(3) and psi'(3); on the mixed path then the low
+// words of phi and of those twelve double-word fields.
+std::vector<std::pair<void*, size_t>> state_fields(const vsv_grid* g) {
+  std::vector<std::pair<void*, size_t>> v;
+  const size_t fb = (size_t)g->N * g->tsize, lb = (size_t)g->N * 4;
+  v.push_back({g->phi[g->cur], fb});
+  for (int c = 0; c < 3; ++c) v.push_back({g->om[c], fb});
+  for (int c = 0; c < 3; ++c) v.push_back({g->ps[c], fb});
+  for (int c = 0; c < 3; ++c) v.push_back({g->om_prev[c], fb});
+  for (int c = 0; c < 3; ++c) v.push_back({g->ps_prev[c], fb});
+  if (g->prec == VSV_MIXED) {
+    v.push_back({g->phi_lo[g->cur], lb});
+    for (int c = 0; c < 3; ++c) v.push_back({g->om_lo[c], lb});
+    for (int c = 0; c < 3; ++c) v.push_back({g->ps_lo[c], lb});
+    for (int c = 0; c < 3; ++c) v.push_back({g->om_prev_lo[c], lb});
+    for (int c = 0; c < 3; ++c) v.push_back({g->ps_prev_lo[c], lb});
+  }
+  return v;
+}
 
 size_t vsv_state_bytes(const vsv_grid* g) {
   if (!g) return 0;
-  return sizeof(StateHeader) + (size_t)g->N * g->tsize * kStateFields +
-         (g->prec == VSV_MIXED ? (size_t)g->N * 4 : 0);
+  size_t s = sizeof(StateHeader);
+  for (auto& f : state_fields(g)) s += f.second;
+  return s;
 }
 
 vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes) {
@@ -1133,26 +1363,17 @@ vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes) {
   Scalars hs;
   CK(cudaMemcpyAsync(&hs, g->S, sizeof hs, cudaMemcpyDeviceToHost, g->cx.stream));
   char* p = (char*)dst;
+  size_t off = sizeof(StateHeader);
+  for (auto& f : state_fields(g)) {
+    CK(cudaMemcpyAsync(p + off, f.first, f.second, cudaMemcpyDeviceToHost, g->cx.stream));
+    off += f.second;
+  }
+  CK(cudaStreamSynchronize(g->cx.stream));
   StateHeader hd{};
   std::memcpy(hd.magic, "VSVSTAT", 8);
   hd.nx = g->nx; hd.ny = g->ny; hd.nz = g->nz; hd.prec = g->prec;
-  const size_t fb = (size_t)g->N * g->tsize;
-  char* q = p + sizeof hd;
-  CK(cudaMemcpyAsync(q, g->phi[g->cur], fb, cudaMemcpyDeviceToHost, g->cx.stream));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpyAsync(q + fb * (1 + c), g->om[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpyAsync(q + fb * (4 + c), g->ps[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpyAsync(q + fb * (7 + c), g->om_prev[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpyAsync(q + fb * (10 + c), g->ps_prev[c], fb, cudaMemcpyDeviceToHost, g->cx.stream));
-  if (g->prec == VSV_MIXED)
-    CK(cudaMemcpyAsync(q + fb * kStateFields, g->phi_lo[g->cur], (size_t)g->N * 4,
-                       cudaMemcpyDeviceToHost, g->cx.stream));
-  hd.prev_valid = g->prev_valid ? 1 : 0;
-  CK(cudaStreamSynchronize(g->cx.stream));
   hd.V0 = hs.V0; hd.A0 = hs.A0; hd.time = g->time; hd.steps = g->steps;
+  hd.prev_valid = g->prev_valid ? 1 : 0;
   std::memcpy(p, &hd, sizeof hd);
   return VSV_OK;
 }
@@ -1165,20 +1386,12 @@ vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes) {
   if (std::memcmp(hd.magic, "VSVSTAT", 8) || hd.nx != g->nx || hd.ny != g->ny || hd.nz != g->nz ||
       hd.prec != g->prec)
     return fail(g, VSV_EINVAL, "state blob does not match this grid%s");
-  const size_t fb = (size_t)g->N * g->tsize;
-  const char* q = (const char*)src + sizeof hd;
-  CK(cudaMemcpyAsync(g->phi[g->cur], q, fb, cudaMemcpyHostToDevice, g->cx.stream));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpyAsync(g->om[c], q + fb * (1 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpyAsync(g->ps[c], q + fb * (4 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpyAsync(g->om_prev[c], q + fb * (7 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpyAsync(g->ps_prev[c], q + fb * (10 + c), fb, cudaMemcpyHostToDevice, g->cx.stream));
-  if (g->prec == VSV_MIXED)
-    CK(cudaMemcpyAsync(g->phi_lo[g->cur], q + fb * kStateFields, (size_t)g->N * 4,
-                       cudaMemcpyHostToDevice, g->cx.stream));
+  const char* p = (const char*)src;
+  size_t off = sizeof(StateHeader);
+  for (auto& f : state_fields(g)) {
+    CK(cudaMemcpyAsync(f.first, p + off, f.second, cudaMemcpyHostToDevice, g->cx.stream));
+    off += f.second;
+  }
   double v[2] = {hd.V0, hd.A0};
   CK(cudaMemcpyAsync(&g->S->V0, v, sizeof v, cudaMemcpyHostToDevice, g->cx.stream));
   CK(cudaStreamSynchronize(g->cx.stream));

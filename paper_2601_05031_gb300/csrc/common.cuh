@@ -23,8 +23,16 @@ struct Level {
   double inv_h2;     // 1 / h_l^2
   float alphaf;      // the same in FP32 (FP32 kernels never touch FP64 units)
   float inv_h2f;
+  // 1 / (2 d + alpha * nwall) for nwall = 0..6 wall neighbours: the smoothers
+  // multiply by these instead of dividing (same table in every sweep kernel)
+  float rcf[7];
+  double rcd[7];
   __host__ __device__ long long cells() const { return (long long)n[0] * n[1] * n[2]; }
 };
+
+template <class T> __host__ __device__ inline T lv_rc(const Level& L, int nwall);
+template <> __host__ __device__ inline float lv_rc<float>(const Level& L, int nwall) { return L.rcf[nwall]; }
+template <> __host__ __device__ inline double lv_rc<double>(const Level& L, int nwall) { return L.rcd[nwall]; }
 
 template <class T> __host__ __device__ inline T lv_alpha(const Level& L);
 template <> __host__ __device__ inline float lv_alpha<float>(const Level& L) { return L.alphaf; }
@@ -62,6 +70,22 @@ struct Scalars {
 // ---------------------------------------------------------------- device helpers
 __host__ __device__ inline long long lin(int i, int j, int k, int nx, int ny) {
   return ((long long)k * ny + j) * nx + i;
+}
+
+// Cell-parallel launches use a 3-D grid: x threads along a row, y blocks
+// over rows, z blocks over (plane, component) -- no per-cell division.
+constexpr int kBX = 64, kBY = 4;
+inline dim3 grid3(int nx, int ny, int nz, int ncomp) {
+  return dim3((unsigned)((nx + kBX - 1) / kBX), (unsigned)((ny + kBY - 1) / kBY),
+              (unsigned)(nz * ncomp));
+}
+inline dim3 block3() { return dim3(kBX, kBY, 1); }
+__device__ __forceinline__ bool cell3(int nx, int ny, int nz, int& i, int& j, int& k, int& comp) {
+  i = blockIdx.x * blockDim.x + threadIdx.x;
+  j = blockIdx.y * blockDim.y + threadIdx.y;
+  comp = (int)(blockIdx.z / (unsigned)nz);
+  k = (int)blockIdx.z - comp * nz;
+  return i < nx && j < ny;
 }
 
 // Knuth's TwoSum: s + e == a + b exactly (round-to-nearest).

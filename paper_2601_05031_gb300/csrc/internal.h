@@ -105,10 +105,19 @@ template <class T>
 void launch_resid_norm(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, bool exact,
                        double* partials, int nblocks, Scalars* S);
 
+// outer defect correction with double-word iterates (dc.cu)
+void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
+                      Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int nblocks);
+void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E, long long n,
+                      int ncomp);
+void launch_extrapolate_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> PH,
+                           Comp3<float> PL, long long n, int ncomp, int extrapolate);
+void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncomp, Scalars* S);
+
 // fused single-pass red-black sweep (smooth.cu)
 bool fused_sweep_ok(const Level& L);
 void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
-                       int ncomp, int zchunk, int kclass);
+                       int ncomp, int zchunk, int kclass, bool zero_in);
 
 // ---------------------------------------------------------------- phase-field (phase.cu)
 struct PhaseParams {
@@ -120,6 +129,7 @@ struct PhaseParams {
   // the same coefficients as double-word FP32 pairs (hi, lo) for the mixed path
   float ih2_hi, ih2_lo, e2_hi, e2_lo, cf2_hi, cf2_lo, sig_hi, sig_lo;
   float hih_hi, hih_lo, he_hi, he_lo, q_hi, q_lo, ca_hi, ca_lo;   // area density
+  float ie_hi, ie_lo;                                              // 1 / eta
   // wall velocity on the wall nodes: [0] y = 0 wall, [1] y = H, [2] z = 0, [3] z = H
   double vwall[4][3];
 };
@@ -136,7 +146,10 @@ void launch_phi_update_ff(Ctx& cx, const PhaseParams& P, const float* phi, const
                           const float* mu, Comp3<float> psi, Comp3<float> v0, const Scalars* S,
                           float dt, float* out, float* out_lo);
 void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo, float* g,
-                  float* g_lo, float* mu, const Scalars* S);
+                  float* g_lo, float* mu, float* mu_lo, const Scalars* S);
+void launch_source_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo,
+                      const float* mu, const float* mu_lo, Comp3<float> s_omega, Comp3<float> f,
+                      Comp3<float> f_lo);
 void launch_split_ff(Ctx& cx, const double* in, float* hi, float* lo, long long n);
 void launch_merge_ff(Ctx& cx, const float* hi, const float* lo, double* out, long long n);
 template <class T>
@@ -145,7 +158,8 @@ template <class T>
 void launch_source(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Comp3<T> s_omega,
                    Comp3<T> f);
 template <class T>
-void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> v0, Comp3<T> v);
+void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> psi_lo, Comp3<T> v0,
+                     Comp3<T> v);
 // Diagnostic partial sums; out has kDiagQ doubles per block.
 constexpr int kDiagQ = 16;
 template <class T>
@@ -158,8 +172,10 @@ void launch_stress_profile(Ctx& cx, const PhaseParams& P, Comp3<T> vel, double* 
 template <class Tin, class Tout>
 void launch_convert(Ctx& cx, const Tin* in, Tout* out, long long n);
 template <class T>
-void launch_full_field(Ctx& cx, const PhaseParams& P, const T* pert, const double* table2d,
-                       int ring, T* out);
+void launch_full_field(Ctx& cx, const PhaseParams& P, const T* pert, const T* lo,
+                       const double* table2d, int ring, T* out);
+void launch_full_field_dw(Ctx& cx, const PhaseParams& P, const float* hi, const float* lo,
+                          const double* tab, int ring, double* out);
 template <class T>
 void launch_scale_copy(Ctx& cx, const T* in, T* out, long long n, double a);
 

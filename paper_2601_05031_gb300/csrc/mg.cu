@@ -104,16 +104,10 @@ __device__ __forceinline__ T resid_at(const T* __restrict__ x, const Level& L, i
 // colour in its x row.
 template <class T>
 __global__ void k_rb_sweep(Level L, Comp3<T> X, Rhs3<T> R, int color, T omega, T h2) {
-  const int comp = blockIdx.y;
-  T* __restrict__ x = X.p[comp];
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-  const int nxh = (nx + 1) >> 1;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)nxh * ny * nz;
-  if (t >= total) return;
-  const int i2 = (int)(t % nxh);
-  const long long r = t / nxh;
-  const int j = (int)(r % ny), k = (int)(r / ny);
+  int i2, j, k, comp;
+  if (!cell3((nx + 1) >> 1, ny, nz, i2, j, k, comp)) return;
+  T* __restrict__ x = X.p[comp];
   const int i = 2 * i2 + ((j + k + color) & 1);
   if (i >= nx) return;
   const long long c = lin(i, j, k, nx, ny);
@@ -123,8 +117,7 @@ __global__ void k_rb_sweep(Level L, Comp3<T> X, Rhs3<T> R, int color, T omega, T
   T s = 0;
   for (int q = 0; q < m; ++q) s += v[q];
   const T b = rhs_at(R, comp, c, j, k, ny);
-  const T coef = (T)(2 * n_active(L)) + lv_alpha<T>(L) * (T)nwall;
-  const T gs = (s - b * h2) / coef;
+  const T gs = (s - b * h2) * lv_rc<T>(L, nwall);
   x[c] = (omega == (T)1) ? gs : x[c] + omega * (gs - x[c]);
 }
 
@@ -133,14 +126,10 @@ __global__ void k_rb_sweep(Level L, Comp3<T> X, Rhs3<T> R, int color, T omega, T
 template <class T, bool EXACT>
 __global__ void k_resid_restrict(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<T> RC, float ih_hi,
                                  float ih_lo) {
-  const int comp = blockIdx.y;
+  int I, J, K, comp;
+  if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
   const T* __restrict__ x = X.p[comp];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = C.cells();
-  if (t >= total) return;
-  const int I = (int)(t % C.n[0]);
-  const long long q = t / C.n[0];
-  const int J = (int)(q % C.n[1]), K = (int)(q / C.n[1]);
+  const long long t = lin(I, J, K, C.n[0], C.n[1]);
   const int fx = F.n[0] / C.n[0], fy = F.n[1] / C.n[1], fz = F.n[2] / C.n[2];
   T acc = 0;
   for (int dk = 0; dk < fz; ++dk)
@@ -195,12 +184,9 @@ __device__ __forceinline__ Interp1<T> interp_axis(int i, int f, int nC, int per,
 // x_fine += P e_coarse (trilinear, cell centred).
 template <class T>
 __global__ void k_prolong_add(Level F, Level C, Comp3<T> X, Comp3<T> E) {
-  const int comp = blockIdx.y;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= F.cells()) return;
-  const int i = (int)(t % F.n[0]);
-  const long long q = t / F.n[0];
-  const int j = (int)(q % F.n[1]), k = (int)(q / F.n[1]);
+  int i, j, k, comp;
+  if (!cell3(F.n[0], F.n[1], F.n[2], i, j, k, comp)) return;
+  const long long t = lin(i, j, k, F.n[0], F.n[1]);
   const T al = lv_alpha<T>(C);
   const Interp1<T> ax = interp_axis<T>(i, F.n[0] / C.n[0], C.n[0], C.per[0], al);
   const Interp1<T> ay = interp_axis<T>(j, F.n[1] / C.n[1], C.n[1], C.per[1], al);
@@ -253,7 +239,6 @@ __global__ void k_coarse_solve(Level L, Comp3<T> E, Comp3<T> RR, int sweeps, T h
   }
   __syncthreads();
   const int nx = L.n[0], ny = L.n[1];
-  const T coef0 = (T)(2 * n_active(L));
   for (int s = 0; s < sweeps; ++s)
     for (int color = 0; color < 2; ++color) {
       for (long long t = threadIdx.x; t < n; t += blockDim.x) {
@@ -266,7 +251,7 @@ __global__ void k_coarse_solve(Level L, Comp3<T> E, Comp3<T> RR, int sweeps, T h
         const int m = gather_nb(e, L, i, j, k, t, v, nwall);
         T sum = 0;
         for (int q2 = 0; q2 < m; ++q2) sum += v[q2];
-        e[t] = (sum - rs[t] * h2) / (coef0 + lv_alpha<T>(L) * (T)nwall);
+        e[t] = (sum - rs[t] * h2) * lv_rc<T>(L, nwall);
       }
       __syncthreads();
     }
@@ -279,17 +264,20 @@ __global__ void k_resid_norm(Level L, Comp3<T> X, Rhs3<T> R, double* partials, f
                              float ih_lo) {
   const int comp = blockIdx.y;
   const T* __restrict__ x = X.p[comp];
-  const long long n = L.cells();
+  const int rows = L.n[1] * L.n[2];
   double rr = 0.0, bb = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % L.n[0]);
-    const long long q = t / L.n[0];
-    const int j = (int)(q % L.n[1]), k = (int)(q / L.n[1]);
-    const T b = rhs_at(R, comp, t, j, k, L.n[1]);
-    const double r = (double)resid_at<T, EXACT>(x, L, i, j, k, t, b, ih_hi, ih_lo);
-    rr += r * r;
-    bb += (double)b * (double)b;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % L.n[1], k = row / L.n[1];
+    T r2 = 0, b2 = 0;   // per-row partial in T, then FP64 across rows
+    for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+      const long long t = lin(i, j, k, L.n[0], L.n[1]);
+      const T b = rhs_at(R, comp, t, j, k, L.n[1]);
+      const T r = resid_at<T, EXACT>(x, L, i, j, k, t, b, ih_hi, ih_lo);
+      r2 += r * r;
+      b2 += b * b;
+    }
+    rr += (double)r2;
+    bb += (double)b2;
   }
   rr = block_sum(rr);
   bb = block_sum(bb);
@@ -322,35 +310,34 @@ static inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock -
 template <class T>
 void launch_rb_sweep(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, int color,
                      double omega, double h2, int kclass) {
-  const long long total = (long long)((L.n[0] + 1) / 2) * L.n[1] * L.n[2];
-  dim3 grid(blocks_for(total), ncomp);
+  const dim3 grid = grid3((L.n[0] + 1) / 2, L.n[1], L.n[2], ncomp);
   cx.before(kclass);
-  k_rb_sweep<T><<<grid, kBlock, 0, cx.stream>>>(L, X, R, color, (T)omega, (T)h2);
+  k_rb_sweep<T><<<grid, block3(), 0, cx.stream>>>(L, X, R, color, (T)omega, (T)h2);
   cx.after(kclass);
 }
 
 template <class T>
 void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Rhs3<T> R,
                            Comp3<T> RC, int ncomp, bool exact) {
-  dim3 grid(blocks_for(C.cells()), ncomp);
+  const dim3 grid = grid3(C.n[0], C.n[1], C.n[2], ncomp);
   cx.before(VSV_KCLASS_RESTRICT);
   float ih_hi = (float)F.inv_h2, ih_lo = (float)(F.inv_h2 - (double)ih_hi);
   if constexpr (std::is_same<T, float>::value) {
     if (exact)
-      k_resid_restrict<float, true><<<grid, kBlock, 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
+      k_resid_restrict<float, true><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
     else
-      k_resid_restrict<float, false><<<grid, kBlock, 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
+      k_resid_restrict<float, false><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
   } else {
-    k_resid_restrict<T, false><<<grid, kBlock, 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
+    k_resid_restrict<T, false><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
   }
   cx.after(VSV_KCLASS_RESTRICT);
 }
 
 template <class T>
 void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Comp3<T> E, int ncomp) {
-  dim3 grid(blocks_for(F.cells()), ncomp);
+  const dim3 grid = grid3(F.n[0], F.n[1], F.n[2], ncomp);
   cx.before(VSV_KCLASS_PROLONG);
-  k_prolong_add<T><<<grid, kBlock, 0, cx.stream>>>(F, C, X, E);
+  k_prolong_add<T><<<grid, block3(), 0, cx.stream>>>(F, C, X, E);
   cx.after(VSV_KCLASS_PROLONG);
 }
 
@@ -401,6 +388,12 @@ void launch_resid_norm(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp
     k_resid_norm<T, false><<<grid, kBlock, 0, cx.stream>>>(L, X, R, partials, ih_hi, ih_lo);
   }
   cx.after(-1);
+  cx.before(-1);
+  k_norm_finalize<<<ncomp, kBlock, 0, cx.stream>>>(partials, nblocks, S);
+  cx.after(-1);
+}
+
+void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncomp, Scalars* S) {
   cx.before(-1);
   k_norm_finalize<<<ncomp, kBlock, 0, cx.stream>>>(partials, nblocks, S);
   cx.after(-1);

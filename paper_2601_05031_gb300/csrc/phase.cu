@@ -71,11 +71,9 @@ static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / 
 template <class T>
 __global__ void k_phi_update(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ mu,
                              Comp3<T> psi, Comp3<T> v0, Scalars* S, T dt, T* __restrict__ out) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   const T ih2 = (T)P.inv_h2, hih = (T)(0.5 * P.inv_h);
   ScalarView<T> M{mu, P.nx, P.ny, P.nz, P.zper};
   ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
@@ -115,10 +113,10 @@ __global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, const T* _
     CascadeSum cp(0.f), ca(0.f);
     const FF hihf{P.hih_hi, P.hih_lo}, hef{P.he_hi, P.he_lo}, qf{P.q_hi, P.q_lo},
         caf{P.ca_hi, P.ca_lo};
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-      int i, j, k;
-      cell_of(t, P.nx, P.ny, i, j, k);
+    for (int row = blockIdx.x; row < P.ny * P.nz; row += gridDim.x) {
+     const int j = row % P.ny, k = row / P.ny;
+     for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
+      const long long t = lin(i, j, k, P.nx, P.ny);
       const FF f{phi[t], phi_lo[t]};
       auto diff = [&](int i1, int j1, int k1, int i0, int j0, int k0) {
         const FF a{F(i1, j1, k1), FL(i1, j1, k1)}, b{F(i0, j0, k0), FL(i0, j0, k0)};
@@ -134,14 +132,15 @@ __global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, const T* _
       cp.add(f.lo);
       ca.add(dens.hi);
       ca.add(dens.lo);
+     }
     }
     sphi = (double)cp.hi + (double)cp.lo;
     sarea = (double)ca.hi + (double)ca.lo;
   } else {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-      int i, j, k;
-      cell_of(t, P.nx, P.ny, i, j, k);
+    for (int row = blockIdx.x; row < P.ny * P.nz; row += gridDim.x) {
+     const int j = row % P.ny, k = row / P.ny;
+     for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
+      const long long t = lin(i, j, k, P.nx, P.ny);
       const double f = phi[t];
       const double gx = (F(i + 1, j, k) - F(i - 1, j, k)) * hih;
       const double gy = (F(i, j + 1, k) - F(i, j - 1, k)) * hih;
@@ -149,6 +148,7 @@ __global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, const T* _
       const double w = f * f - 1.0;
       sphi += f;
       sarea += c_a * (he * (gx * gx + gy * gy + gz * gz) + w * w * q);
+     }
     }
   }
   sphi = block_sum(sphi);
@@ -190,11 +190,9 @@ __global__ void k_va_finalize(const double* partials, int nblocks, long long nce
 // Helfrich: g = phi^3 - phi - eps^2 lap phi.
 template <class T>
 __global__ void k_helfrich_g(PhaseParams P, const T* __restrict__ phi, T* __restrict__ g) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
   const T f = phi[t];
   g[t] = f * f * f - f - (T)(P.eps * P.eps) * lap7<T>(F, i, j, k, (T)P.inv_h2);
@@ -205,11 +203,9 @@ __global__ void k_helfrich_g(PhaseParams P, const T* __restrict__ phi, T* __rest
 template <class T>
 __global__ void k_mu(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ g,
                      const Scalars* S, T* __restrict__ mu) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   const T ih2 = (T)P.inv_h2;
   ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
   const T f = phi[t];
@@ -229,11 +225,9 @@ __global__ void k_mu(PhaseParams P, const T* __restrict__ phi, const T* __restri
 template <class T>
 __global__ void k_source(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ mu,
                          Comp3<T> s_omega, Comp3<T> f) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   const T hih = (T)(0.5 * P.inv_h), ie = (T)P.inv_eta;
   ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
   ScalarView<T> M{mu, P.nx, P.ny, P.nz, P.zper};
@@ -250,18 +244,32 @@ __global__ void k_source(PhaseParams P, const T* __restrict__ phi, const T* __re
 }
 
 // ---------------------------------------------------------------- velocity (eq. vecpot)
+// psi_lo (low words of a double-word psi', mixed path) may be null; the
+// difference of the double-word values is formed exactly before rounding.
 template <class T>
-__global__ void k_velocity(PhaseParams P, Comp3<T> psi, Comp3<T> v0, Comp3<T> v) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+__global__ void k_velocity(PhaseParams P, Comp3<T> psi, Comp3<T> psi_lo, Comp3<T> v0, Comp3<T> v) {
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   const T hih = (T)(0.5 * P.inv_h);
   PertView<T> X{psi.p[0], P.nx, P.ny, P.nz, P.zper};
   PertView<T> Y{psi.p[1], P.nx, P.ny, P.nz, P.zper};
   PertView<T> Z{psi.p[2], P.nx, P.ny, P.nz, P.zper};
   const long long jk = j + (long long)k * P.ny;
+  if (psi_lo.p[0]) {
+    PertView<T> XL{psi_lo.p[0], P.nx, P.ny, P.nz, P.zper};
+    PertView<T> YL{psi_lo.p[1], P.nx, P.ny, P.nz, P.zper};
+    PertView<T> ZL{psi_lo.p[2], P.nx, P.ny, P.nz, P.zper};
+    // d(a)/dx with a = hi + lo: (a+ - a-) = (hi+ - hi-) + (lo+ - lo-)
+    auto d = [&](const PertView<T>& H, const PertView<T>& L, int i1, int j1, int k1, int i0, int j0,
+                 int k0) {
+      return ((H(i1, j1, k1) - H(i0, j0, k0)) + (L(i1, j1, k1) - L(i0, j0, k0))) * hih;
+    };
+    v.p[0][t] = v0.p[0][jk] + (d(Z, ZL, i, j + 1, k, i, j - 1, k) - d(Y, YL, i, j, k + 1, i, j, k - 1));
+    v.p[1][t] = v0.p[1][jk] + (d(X, XL, i, j, k + 1, i, j, k - 1) - d(Z, ZL, i + 1, j, k, i - 1, j, k));
+    v.p[2][t] = v0.p[2][jk] + (d(Y, YL, i + 1, j, k, i - 1, j, k) - d(X, XL, i, j + 1, k, i, j - 1, k));
+    return;
+  }
   v.p[0][t] = v0.p[0][jk] + ((Z(i, j + 1, k) - Z(i, j - 1, k)) - (Y(i, j, k + 1) - Y(i, j, k - 1))) * hih;
   v.p[1][t] = v0.p[1][jk] + ((X(i, j, k + 1) - X(i, j, k - 1)) - (Z(i + 1, j, k) - Z(i - 1, j, k))) * hih;
   v.p[2][t] = v0.p[2][jk] + ((Y(i + 1, j, k) - Y(i - 1, j, k)) - (X(i, j + 1, k) - X(i, j - 1, k))) * hih;
@@ -312,10 +320,10 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
   for (int a = 0; a < kDiagQ; ++a) q[a] = 0.0;
   const double hih = 0.5 * P.inv_h, eta = 1.0 / P.inv_eta, h = P.h;
   const int ny2 = P.ny + 2;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    cell_of(t, P.nx, P.ny, i, j, k);
+  for (int row = blockIdx.x; row < P.ny * P.nz; row += gridDim.x) {
+   const int j = row % P.ny, k = row / P.ny;
+   for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
+    const long long t = lin(i, j, k, P.nx, P.ny);
     double G[3][3], G0[3][3];
     for (int c = 0; c < 3; ++c) {
       VelView<T> V{vel.p[c], P.nx, P.ny, P.nz, P.zper, c, &P};
@@ -389,6 +397,7 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
     const double st = sqrt(sxy * sxy + syz * syz + sxz * sxz);
     q[11] = fmax(q[11], st);
     if (sigma_t) sigma_t[t] = (T)st;
+   }
   }
   for (int a = 0; a < 9; ++a) {
     const double s = block_sum(q[a]);
@@ -440,15 +449,30 @@ __global__ void k_convert(const Tin* __restrict__ in, Tout* __restrict__ out, lo
 
 // out = pert + table(y, z); ring = 1: table in ring layout ((ny+2) x (nz+2)).
 template <class T>
-__global__ void k_full_field(PhaseParams P, const T* __restrict__ pert, const double* __restrict__ tab,
-                             int ring, T* __restrict__ out) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+__global__ void k_full_field(PhaseParams P, const T* __restrict__ pert, const T* __restrict__ lo,
+                             const double* __restrict__ tab, int ring, T* __restrict__ out) {
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   const double b = ring ? tab[(j + 1) + (long long)(k + 1) * (P.ny + 2)] : tab[j + (long long)k * P.ny];
-  out[t] = (T)((double)pert[t] + b);
+  out[t] = (T)((double)pert[t] + (lo ? (double)lo[t] : 0.0) + b);
+}
+
+// Full field in FP64 from a double-word perturbation: out = hi + lo + table.
+__global__ void k_full_field_dw(PhaseParams P, const float* __restrict__ hi, const float* __restrict__ lo,
+                                const double* __restrict__ tab, int ring, double* __restrict__ out) {
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
+  const double b = tab ? (ring ? tab[(j + 1) + (long long)(k + 1) * (P.ny + 2)] : tab[j + (long long)k * P.ny]) : 0.0;
+  out[t] = (double)hi[t] + (double)lo[t] + b;
+}
+
+void launch_full_field_dw(Ctx& cx, const PhaseParams& P, const float* hi, const float* lo,
+                          const double* tab, int ring, double* out) {
+  cx.before(-1);
+  k_full_field_dw<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, hi, lo, tab, ring, out);
+  cx.after(-1);
 }
 
 template <class T>
@@ -594,11 +618,9 @@ __global__ void k_phi_update_ff(PhaseParams P, const float* __restrict__ phi,
                                 const float* __restrict__ phi_lo, const float* __restrict__ mu,
                                 Comp3<float> psi, Comp3<float> v0, Scalars* S, float dt,
                                 float* __restrict__ out, float* __restrict__ out_lo) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   const float ih2 = (float)P.inv_h2, hih = (float)(0.5 * P.inv_h);
   ScalarView<float> M{mu, P.nx, P.ny, P.nz, P.zper};
   ScalarView<float> F{phi, P.nx, P.ny, P.nz, P.zper};
@@ -624,11 +646,9 @@ __global__ void k_phi_update_ff(PhaseParams P, const float* __restrict__ phi,
 __global__ void k_helfrich_g_ff(PhaseParams P, const float* __restrict__ phi,
                                 const float* __restrict__ phi_lo, float* __restrict__ g,
                                 float* __restrict__ g_lo) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   ScalarView<float> H{phi, P.nx, P.ny, P.nz, P.zper};
   ScalarView<float> L{phi_lo, P.nx, P.ny, P.nz, P.zper};
   const FF f{phi[t], phi_lo[t]};
@@ -643,19 +663,19 @@ __global__ void k_helfrich_g_ff(PhaseParams P, const float* __restrict__ phi,
 // Helfrich: mu = cf2 [(3 phi^2 - 1) g - eps^2 lap g] - gamma_A lap phi
 __global__ void k_mu_ff(PhaseParams P, const float* __restrict__ phi, const float* __restrict__ phi_lo,
                         const float* __restrict__ g, const float* __restrict__ g_lo,
-                        const Scalars* S, float* __restrict__ mu) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  if (t >= n) return;
-  int i, j, k;
-  cell_of(t, P.nx, P.ny, i, j, k);
+                        const Scalars* S, float* __restrict__ mu, float* __restrict__ mu_lo) {
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
   ScalarView<float> H{phi, P.nx, P.ny, P.nz, P.zper};
   ScalarView<float> L{phi_lo, P.nx, P.ny, P.nz, P.zper};
   const FF f{phi[t], phi_lo[t]};
   const FF lphi = lap7_ff(H, L, i, j, k, P.ih2_hi, P.ih2_lo);
   if (P.fe_kind == VSV_CAHN_HILLIARD) {
     const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
-    mu[t] = ff_round(ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.sig_hi, P.sig_lo}))));
+    const FF m = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.sig_hi, P.sig_lo})));
+    mu[t] = m.hi;
+    mu_lo[t] = m.lo;
     return;
   }
   ScalarView<float> GH{g, P.nx, P.ny, P.nz, P.zper};
@@ -665,7 +685,8 @@ __global__ void k_mu_ff(PhaseParams P, const float* __restrict__ phi, const floa
   const FF w = ff_add_f(ff_mul_f(ff_mul(f, f), 3.f), -1.f);
   const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2_hi, P.e2_lo})));
   const FF m = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, S->gamma_af)));
-  mu[t] = ff_round(m);
+  mu[t] = m.hi;
+  mu_lo[t] = m.lo;
 }
 
 __global__ void k_split_ff(const double* __restrict__ in, float* __restrict__ hi,
@@ -689,21 +710,63 @@ void launch_phi_update_ff(Ctx& cx, const PhaseParams& P, const float* phi, const
                           float dt, float* out, float* out_lo) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   cx.before(VSV_KCLASS_PHASE);
-  k_phi_update_ff<<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, phi_lo, mu, psi, v0,
+  k_phi_update_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, mu, psi, v0,
                                                       const_cast<Scalars*>(S), dt, out, out_lo);
   cx.after(VSV_KCLASS_PHASE);
 }
 
 void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo, float* g,
-                  float* g_lo, float* mu, const Scalars* S) {
+                  float* g_lo, float* mu, float* mu_lo, const Scalars* S) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   if (P.fe_kind == VSV_HELFRICH) {
     cx.before(VSV_KCLASS_PHASE);
-    k_helfrich_g_ff<<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, phi_lo, g, g_lo);
+    k_helfrich_g_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo);
     cx.after(VSV_KCLASS_PHASE);
   }
   cx.before(VSV_KCLASS_PHASE);
-  k_mu_ff<<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, S, mu);
+  k_mu_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, S, mu,
+                                                                     mu_lo);
+  cx.after(VSV_KCLASS_PHASE);
+}
+
+// f = grad phi x grad mu / eta - s_omega in double-word arithmetic from
+// phi = hi + lo and mu = hi + lo; written as hi + lo.  The stream vector
+// psi' = L^{-2}(-f) is dominated by the small low-wavenumber content of this
+// dipole-like source, so FP32 rounding of f would be amplified ~10^3 in psi'.
+__global__ void k_source_ff(PhaseParams P, const float* __restrict__ phi, const float* __restrict__ phi_lo,
+                            const float* __restrict__ mu, const float* __restrict__ mu_lo,
+                            Comp3<float> s_omega, Comp3<float> f, Comp3<float> f_lo) {
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
+  ScalarView<float> FH{phi, P.nx, P.ny, P.nz, P.zper}, FL{phi_lo, P.nx, P.ny, P.nz, P.zper};
+  ScalarView<float> MH{mu, P.nx, P.ny, P.nz, P.zper}, ML{mu_lo, P.nx, P.ny, P.nz, P.zper};
+  const FF hih{P.hih_hi, P.hih_lo};
+  auto dd = [&](const ScalarView<float>& H, const ScalarView<float>& L, int i1, int j1, int k1, int i0,
+                int j0, int k0) {
+    const FF a{H(i1, j1, k1), L(i1, j1, k1)}, b{H(i0, j0, k0), L(i0, j0, k0)};
+    return ff_mul(ff_add(a, ff_neg(b)), hih);
+  };
+  const FF ax = dd(FH, FL, i + 1, j, k, i - 1, j, k), ay = dd(FH, FL, i, j + 1, k, i, j - 1, k),
+           az = dd(FH, FL, i, j, k + 1, i, j, k - 1);
+  const FF bx = dd(MH, ML, i + 1, j, k, i - 1, j, k), by = dd(MH, ML, i, j + 1, k, i, j - 1, k),
+           bz = dd(MH, ML, i, j, k + 1, i, j, k - 1);
+  const FF ie{P.ie_hi, P.ie_lo};
+  const long long jk = j + (long long)k * P.ny;
+  const FF c0 = ff_add_f(ff_mul(ff_add(ff_mul(ay, bz), ff_neg(ff_mul(az, by))), ie), -s_omega.p[0][jk]);
+  const FF c1 = ff_add_f(ff_mul(ff_add(ff_mul(az, bx), ff_neg(ff_mul(ax, bz))), ie), -s_omega.p[1][jk]);
+  const FF c2 = ff_add_f(ff_mul(ff_add(ff_mul(ax, by), ff_neg(ff_mul(ay, bx))), ie), -s_omega.p[2][jk]);
+  f.p[0][t] = c0.hi; f_lo.p[0][t] = c0.lo;
+  f.p[1][t] = c1.hi; f_lo.p[1][t] = c1.lo;
+  f.p[2][t] = c2.hi; f_lo.p[2][t] = c2.lo;
+}
+
+void launch_source_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo,
+                      const float* mu, const float* mu_lo, Comp3<float> s_omega, Comp3<float> f,
+                      Comp3<float> f_lo) {
+  cx.before(VSV_KCLASS_PHASE);
+  k_source_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, mu, mu_lo,
+                                                                       s_omega, f, f_lo);
   cx.after(VSV_KCLASS_PHASE);
 }
 
@@ -725,7 +788,7 @@ void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu,
                        Comp3<T> v0, const Scalars* S, T dt, T* out) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   cx.before(VSV_KCLASS_PHASE);
-  k_phi_update<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, mu, psi, v0, const_cast<Scalars*>(S),
+  k_phi_update<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, mu, psi, v0, const_cast<Scalars*>(S),
                                                      dt, out);
   cx.after(VSV_KCLASS_PHASE);
 }
@@ -747,11 +810,11 @@ void launch_mu(Ctx& cx, const PhaseParams& P, const T* phi, T* g, T* mu, const S
   const long long n = (long long)P.nx * P.ny * P.nz;
   if (P.fe_kind == VSV_HELFRICH) {
     cx.before(VSV_KCLASS_PHASE);
-    k_helfrich_g<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, g);
+    k_helfrich_g<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, g);
     cx.after(VSV_KCLASS_PHASE);
   }
   cx.before(VSV_KCLASS_PHASE);
-  k_mu<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, g, S, mu);
+  k_mu<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, g, S, mu);
   cx.after(VSV_KCLASS_PHASE);
 }
 
@@ -760,15 +823,15 @@ void launch_source(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Com
                    Comp3<T> f) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   cx.before(VSV_KCLASS_PHASE);
-  k_source<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, phi, mu, s_omega, f);
+  k_source<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, mu, s_omega, f);
   cx.after(VSV_KCLASS_PHASE);
 }
 
 template <class T>
-void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> v0, Comp3<T> v) {
-  const long long n = (long long)P.nx * P.ny * P.nz;
+void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> psi_lo, Comp3<T> v0,
+                     Comp3<T> v) {
   cx.before(-1);
-  k_velocity<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, psi, v0, v);
+  k_velocity<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, psi, psi_lo, v0, v);
   cx.after(-1);
 }
 
@@ -801,11 +864,11 @@ void launch_convert(Ctx& cx, const Tin* in, Tout* out, long long n) {
 }
 
 template <class T>
-void launch_full_field(Ctx& cx, const PhaseParams& P, const T* pert, const double* tab, int ring,
-                       T* out) {
+void launch_full_field(Ctx& cx, const PhaseParams& P, const T* pert, const T* lo, const double* tab,
+                       int ring, T* out) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   cx.before(-1);
-  k_full_field<T><<<nblk(n), kBlock, 0, cx.stream>>>(P, pert, tab, ring, out);
+  k_full_field<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, pert, lo, tab, ring, out);
   cx.after(-1);
 }
 
@@ -871,13 +934,15 @@ void launch_fill(Ctx& cx, double* x, long long n, double v) {
   template void launch_mu<T>(Ctx&, const PhaseParams&, const T*, T*, T*, const Scalars*);         \
   template void launch_source<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>,          \
                                  Comp3<T>);                                                       \
-  template void launch_velocity<T>(Ctx&, const PhaseParams&, Comp3<T>, Comp3<T>, Comp3<T>);       \
+  template void launch_velocity<T>(Ctx&, const PhaseParams&, Comp3<T>, Comp3<T>, Comp3<T>,       \
+                                   Comp3<T>);                                                     \
   template void launch_diag<T>(Ctx&, const PhaseParams&, const T*, const T*, const T*, const T*,  \
                                Comp3<T>, Comp3<T>,                                                \
                                Comp3<T>, Comp3<const double>, Comp3<const double>, T*, double*,   \
                                int, double*);                                                     \
   template void launch_stress_profile<T>(Ctx&, const PhaseParams&, Comp3<T>, double*);            \
-  template void launch_full_field<T>(Ctx&, const PhaseParams&, const T*, const double*, int, T*); \
+  template void launch_full_field<T>(Ctx&, const PhaseParams&, const T*, const T*, const double*,  \
+                                     int, T*);                                                    \
   template void launch_scale_copy<T>(Ctx&, const T*, T*, long long, double);
 VSV_INST(float)
 VSV_INST(double)
