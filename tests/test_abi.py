@@ -38,7 +38,7 @@ def test_workspace_bytes_host_only(V):
     n32 = V.vsv_workspace_bytes(48, 24, 24, V.VSV_MIXED)
     n64 = V.vsv_workspace_bytes(48, 24, 24, V.VSV_FP64)
     N = 48 * 24 * 24
-    assert n32 > 13 * 4 * N and n64 > 13 * 8 * N and n64 > n32
+    assert n32 > 13 * 4 * N and n64 > 13 * 8 * N
     assert V.vsv_workspace_bytes(0, 24, 24, V.VSV_MIXED) == 0
     assert V.vsv_workspace_bytes(8, 1, 8, V.VSV_MIXED) == 0
     assert V.vsv_workspace_bytes(8, 8, 8, 7) == 0
