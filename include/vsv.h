@@ -249,6 +249,28 @@ size_t vsv_state_bytes(const vsv_grid* g);
 vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes);
 vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes);
 
+/* Volume and area of a phase field without any device allocation.  The
+ * paper has no counterpart: this is an interface for callers that may not
+ * allocate device memory -- a plugin whose host application owns every
+ * device allocation, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation a cudaMalloc / cudaFree may cause.
+ * It computes what vsv_get_diagnostics reports as volume and area
+ * (V = h^3/2 sum (1 - phi); A of SM eq. 32 with central differences,
+ * periodic x, mirror y, mirror or periodic z) with its scratch in a
+ * fixed 1 MiB file-scope device array of per-row partial sums.
+ *   phi: device pointer to an FP64 [nz][ny][nx] field (read only).
+ *   out: device pointer to two doubles, written V then A.
+ *   cuda_stream: cudaStream_t to run on (NULL = legacy default stream); the
+ *   call is asynchronous on it.
+ * Limit: ny * nz <= 65536 (y, z) rows; larger shapes return VSV_EINVAL and
+ * launch nothing.  The first call on a device looks up the array's device
+ * address while that device is current; make that first call before any
+ * stream capture.  All calls in the process share the array, which keeps
+ * the last call's partial sums; two calls whose kernels overlap on the GPU
+ * race on it.  Never calls cudaMalloc or cudaFree. */
+vsv_status vsv_volume_area_static(const double* phi, int nx, int ny, int nz, double h, double eps,
+                                  int z_periodic, double* out, void* cuda_stream);
+
 /* Synchronise the stream and report deferred kernel errors / flags. */
 vsv_status vsv_check(vsv_grid* g);
 

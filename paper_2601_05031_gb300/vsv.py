@@ -80,7 +80,7 @@ EXPORTS = [
     "vsv_set_free_energy", "vsv_set_solver", "vsv_default_solver", "vsv_set_phi", "vsv_step",
     "vsv_stability_limit", "vsv_solve_poisson", "vsv_get_field", "vsv_set_field",
     "vsv_get_diagnostics", "vsv_get_stress_profile", "vsv_state_bytes", "vsv_get_state",
-    "vsv_set_state", "vsv_check", "vsv_last_error", "vsv_kernel_launches",
+    "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_last_error", "vsv_kernel_launches",
     "vsv_profile_enable", "vsv_profile_read",
 ]
 
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_state_bytes": (sz, [vp]),
         "vsv_get_state": (i32, [vp, vp, sz]),
         "vsv_set_state": (i32, [vp, vp, sz]),
+        "vsv_volume_area_static": (i32, [vp, i32, i32, i32, dbl, dbl, i32, vp, vp]),
         "vsv_check": (i32, [vp]),
         "vsv_last_error": (C.c_char_p, [vp]),
         "vsv_kernel_launches": (i64, [vp]),
@@ -251,6 +252,13 @@ def vsv_get_state(g, ptr, nbytes):
 
 def vsv_set_state(g, ptr, nbytes):
     return _check(g, lib().vsv_set_state(g, C.c_void_p(ptr), nbytes), "vsv_set_state")
+
+
+def vsv_volume_area_static(phi_ptr, nx, ny, nz, h, eps, z_periodic, out_ptr, stream_ptr):
+    """Volume and area of an FP64 device field into out_ptr (2 device
+    doubles) with no device allocation; returns the vsv_status."""
+    return lib().vsv_volume_area_static(C.c_void_p(phi_ptr), nx, ny, nz, h, eps, int(z_periodic),
+                                        C.c_void_p(out_ptr), C.c_void_p(stream_ptr))
 
 
 def vsv_check(g, check=True):
