@@ -463,9 +463,21 @@ vsv_status solve_dc(vsv_grid* g, const std::vector<Level>& lv, Comp3<float> XH, 
     vcycle<float>(g, lv, 0, E, RE, ncomp, false, true);
     launch_update_dw(g->cx, XH, XL, E, L.cells(), ncomp);
   };
+  // defect r = b - L x (tiled kernel where the level allows it); returns the
+  // number of partial-sum blocks per component written when `norms`
+  auto defect = [&](bool norms) -> int {
+    double* part = norms ? g->partials : nullptr;
+    if (g->sol.variant == 0) {
+      const int nb = launch_defect_tiled(g->cx, L, XH, XL, R, BL, RR, ncomp, part,
+                                         g->red_blocks * 32 / (2 * ncomp));
+      if (nb > 0) return nb;
+    }
+    launch_defect_dw(g->cx, L, XH, XL, R, BL, RR, ncomp, part, g->red_blocks);
+    return g->red_blocks;
+  };
   if (fixed > 0) {
     for (int c = 0; c < fixed; ++c) {
-      launch_defect_dw(g->cx, L, XH, XL, R, BL, RR, ncomp, nullptr, g->red_blocks);
+      defect(false);
       correct();
     }
     CKL();
@@ -478,10 +490,9 @@ vsv_status solve_dc(vsv_grid* g, const std::vector<Level>& lv, Comp3<float> XH, 
   double rr = INFINITY;
   while (true) {
     const bool check = (c % every == 0) || c >= max_cycles;
-    launch_defect_dw(g->cx, L, XH, XL, R, BL, RR, ncomp, check ? g->partials : nullptr,
-                     g->red_blocks);
+    const int nb = defect(check);
     if (check) {
-      launch_norm_finalize(g->cx, g->partials, g->red_blocks, ncomp, g->S);
+      launch_norm_finalize(g->cx, g->partials, nb, ncomp, g->S);
       Scalars hs;
       CK(cudaMemcpyAsync(&hs, g->S, sizeof(Scalars), cudaMemcpyDeviceToHost, g->cx.stream));
       CK(cudaStreamSynchronize(g->cx.stream));

@@ -8,7 +8,7 @@
 // rounding and the relative residual is a meaningful stopping test.
 #include <algorithm>
 
-#include "internal.h"
+#include "tile.cuh"
 
 namespace vsv {
 
@@ -143,6 +143,193 @@ void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL,
   cx.before(VSV_KCLASS_RESTRICT);
   k_defect_dw<<<grid, kBlock, 0, cx.stream>>>(L, XH, XL, R, BL, OUT, partials, ih_hi, ih_lo);
   cx.after(VSV_KCLASS_RESTRICT);
+}
+
+// ---------------------------------------------------------------- tiled defect
+// The same exact defect as k_defect_dw (same summation order, hence the same
+// bits) on a 128 x 16 tile marching along z: x_hi and x_lo planes staged in
+// shared memory (one-cell halo), each thread's own float4 groups of the
+// planes below and above held in registers, rhs read straight from memory.
+namespace {
+constexpr int kDR = tile::kTY + 2;                                   // staged rows
+constexpr int kDS = 3;                                               // ring slots
+constexpr int kDStage = (kDR * tile::kNV + tile::kThreads - 1) / tile::kThreads;
+
+struct DefGeom : tile::Geom {
+  float ih_hi, ih_lo, beta;
+};
+
+__device__ __forceinline__ float comp4(const float4& v, int o) {
+  return o == 0 ? v.x : (o == 1 ? v.y : (o == 2 ? v.z : v.w));
+}
+
+// exact b - L x at one cell: hi neighbours by cascaded summation in the
+// order x-, x+, y-, y+, z-, z+, then -6 x_c; lo parts in FP32.
+__device__ __forceinline__ float defect_cell(float xmh, float xph, float ymh, float yph, float zmh,
+                                             float zph, float ch, float xml, float xpl, float yml,
+                                             float ypl, float zml, float zpl, float cl, float b1,
+                                             float b2, bool has_b2, float s, float ih_hi,
+                                             float ih_lo) {
+  CascadeSum lh(0.f);
+  lh.add(xmh); lh.add(xph);
+  lh.add(ymh); lh.add(yph);
+  lh.add(zmh); lh.add(zph);
+  float llo = 0.f;
+  llo += xml + xpl;
+  llo += yml + ypl;
+  llo += zml + zpl;
+  lh.add_scaled(-6.f, ch);
+  llo = __fmaf_rn(-6.f, cl, llo);
+  const float p = __fmul_rn(ih_hi, lh.hi);
+  const float pe = __fmaf_rn(ih_hi, lh.hi, -p);
+  const float rest = __fmaf_rn(ih_hi, __fadd_rn(lh.lo, llo), __fmaf_rn(ih_lo, lh.hi, pe));
+  CascadeSum r(b1);
+  if (has_b2) r.add(b2);
+  r.add(s);
+  r.add(-p);
+  r.add(-rest);
+  return r.value();
+}
+}  // namespace
+
+__global__ void __launch_bounds__(tile::kThreads, 2)
+k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3<float> BL,
+               Comp3<float> OUT, double* partials) {
+  using namespace tile;
+  extern __shared__ float4 smem_d4[];
+  float* sH = reinterpret_cast<float*>(smem_d4);
+  float* sL = sH + kDS * kDR * kW;
+  const int comp = blockIdx.z;
+  const float* __restrict__ xh = XH.p[comp];
+  const float* __restrict__ xl = XL.p[comp];
+  const float* __restrict__ bh = R.B[comp];
+  const float* __restrict__ bl = BL.p[comp];
+  const float* __restrict__ S = R.S[comp];
+  float* __restrict__ out = OUT.p[comp];
+  const int tx = blockIdx.x % G.ntx, tyb = blockIdx.x / G.ntx;
+  const int x0 = tx * kTX, y0 = tyb * kTY;
+  const int zb = blockIdx.y * G.zchunk;
+  const int ze = min(zb + G.zchunk, G.nz);
+  const int tid = threadIdx.x, gx = tid & 31, ty = tid >> 5;
+  const int q = gx + 1;
+  const float beta = G.beta;
+  auto slot = [&](float* base, int plane) { return base + (((plane % kDS) + kDS) % kDS) * (kDR * kW); };
+  StageDesc<kDStage> ds;
+  ds.init(G, x0, y0, 1, kDR);
+  int rown[2], jown[2];
+  for (int h = 0; h < 2; ++h) {
+    rown[h] = ty + 8 * h + 1;
+    jown[h] = y0 + ty + 8 * h;
+  }
+  ds.stage(slot(sH, zb - 1), xh, G, zb - 1, false);
+  ds.stage(slot(sL, zb - 1), xl, G, zb - 1, false);
+  ds.stage(slot(sH, zb), xh, G, zb, false);
+  ds.stage(slot(sL, zb), xl, G, zb, false);
+  ds.stage(slot(sH, zb + 1), xh, G, zb + 1, false);
+  ds.stage(slot(sL, zb + 1), xl, G, zb + 1, false);
+  cp_async_commit();
+  cp_async_wait0();
+  __syncthreads();
+  float4 Mh[2], Ml[2], Vh[2], Vl[2], Ph[2], Pl[2];
+  for (int h = 0; h < 2; ++h) {
+    Vh[h] = lds4(slot(sH, zb - 1) + rown[h] * kW + 4 * q);
+    Vl[h] = lds4(slot(sL, zb - 1) + rown[h] * kW + 4 * q);
+    Ph[h] = lds4(slot(sH, zb) + rown[h] * kW + 4 * q);
+    Pl[h] = lds4(slot(sL, zb) + rown[h] * kW + 4 * q);
+  }
+  __syncthreads();
+  double rr = 0.0, bb = 0.0;
+  for (int p = zb; p < ze; ++p) {
+    if (p + 2 <= ze) {   // plane p+2 is needed by step p+1
+      ds.stage(slot(sH, p + 2), xh, G, p + 2, false);
+      ds.stage(slot(sL, p + 2), xl, G, p + 2, false);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const float* cH = slot(sH, p);
+    const float* cL = slot(sL, p);
+    for (int h = 0; h < 2; ++h) {
+      Mh[h] = Vh[h]; Ml[h] = Vl[h];
+      Vh[h] = Ph[h]; Vl[h] = Pl[h];
+      Ph[h] = lds4(slot(sH, p + 1) + rown[h] * kW + 4 * q);
+      Pl[h] = lds4(slot(sL, p + 1) + rown[h] * kW + 4 * q);
+    }
+    float r2 = 0.f, b2 = 0.f;
+    for (int h = 0; h < 2; ++h) {
+      const int r = rown[h], j = jown[h];
+      const float* rowH = cH + r * kW;
+      const float* rowL = cL + r * kW;
+      const float4 Uh = lds4(rowH - kW + 4 * q), Dh = lds4(rowH + kW + 4 * q);
+      const float4 Ul = lds4(rowL - kW + 4 * q), Dl = lds4(rowL + kW + 4 * q);
+      const float Lh = rowH[4 * q - 1], Rh = rowH[4 * q + 4];
+      const float Ll = rowL[4 * q - 1], Rl = rowL[4 * q + 4];
+      const long long gi = ((long long)p * G.ny + j) * G.nx + x0 + 4 * gx;
+      const float4 B1 = *reinterpret_cast<const float4*>(bh + gi);
+      float4 B2 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (bl) B2 = *reinterpret_cast<const float4*>(bl + gi);
+      const float s = S ? S[j + (long long)p * G.ny] : 0.f;
+      float res[4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const float xmh = o == 0 ? Lh : comp4(Vh[h], o - 1), xph = o == 3 ? Rh : comp4(Vh[h], o + 1);
+        const float xml = o == 0 ? Ll : comp4(Vl[h], o - 1), xpl = o == 3 ? Rl : comp4(Vl[h], o + 1);
+        const float b1v = beta * comp4(B1, o), b2v = beta * comp4(B2, o);
+        res[o] = defect_cell(xmh, xph, comp4(Uh, o), comp4(Dh, o), comp4(Mh[h], o), comp4(Ph[h], o),
+                             comp4(Vh[h], o), xml, xpl, comp4(Ul, o), comp4(Dl, o), comp4(Ml[h], o),
+                             comp4(Pl[h], o), comp4(Vl[h], o), b1v, b2v, bl != nullptr, s, G.ih_hi,
+                             G.ih_lo);
+        if (partials) {
+          const float bv = b1v + (bl ? b2v : 0.f) + s;
+          r2 = __fmaf_rn(res[o], res[o], r2);
+          b2 = __fmaf_rn(bv, bv, b2);
+        }
+      }
+      *reinterpret_cast<float4*>(out + gi) = make_float4(res[0], res[1], res[2], res[3]);
+    }
+    rr += (double)r2;
+    bb += (double)b2;
+    __syncthreads();
+  }
+  cp_async_wait0();
+  if (partials) {
+    rr = block_sum(rr);
+    bb = block_sum(bb);
+    if (threadIdx.x == 0) {
+      const long long nb = (long long)gridDim.x * gridDim.y;
+      double* o = partials + ((long long)comp * nb + blockIdx.x + (long long)gridDim.x * blockIdx.y) * 2;
+      o[0] = rr;
+      o[1] = bb;
+    }
+  }
+}
+
+// launches the tiled defect when the level allows it; returns the number of
+// partial-sum blocks per component (0 if it did not launch)
+int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
+                        Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int max_blocks) {
+  if (!tile::level_ok(L)) return 0;
+  const int tiles = (L.n[0] / tile::kTX) * (L.n[1] / tile::kTY);
+  int nzc = std::max(1, std::min((8 * 152 + tiles * ncomp - 1) / (tiles * ncomp), L.n[2] / 16));
+  while (nzc > 1 && tiles * nzc * ncomp > max_blocks) --nzc;
+  if (tiles * nzc * ncomp > max_blocks) return 0;
+  DefGeom G;
+  static_cast<tile::Geom&>(G) = tile::geom(L, (L.n[2] + nzc - 1) / nzc);
+  G.ih_hi = (float)L.inv_h2;
+  G.ih_lo = (float)(L.inv_h2 - (double)G.ih_hi);
+  G.beta = R.beta;
+  const int nz = (L.n[2] + G.zchunk - 1) / G.zchunk;
+  const size_t smem = (size_t)2 * kDS * kDR * tile::kW * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_defect_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  dim3 grid(tiles, nz, ncomp);
+  cx.before(VSV_KCLASS_RESTRICT);
+  k_defect_tiled<<<grid, tile::kThreads, smem, cx.stream>>>(G, XH, XL, R, BL, OUT, partials);
+  cx.after(VSV_KCLASS_RESTRICT);
+  return tiles * nz;
 }
 
 void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E, long long n,

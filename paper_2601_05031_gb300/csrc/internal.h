@@ -105,11 +105,28 @@ template <class T>
 void launch_resid_norm(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, bool exact,
                        double* partials, int nblocks, Scalars* S);
 
+// Lower part of a V-cycle (levels first .. last) run by one CTA per component
+// in shared memory: E (level first) <- approximate solution of L e = R.
+struct CoarseCycle {
+  Level lv[kMaxLevels];
+  int first, last;
+  int nu1, nu2, coarse_sweeps;
+  double h2[kMaxLevels];       // 1 / inv_h2 of each level (rounded to T in the kernel)
+  long long off[kMaxLevels];   // element offset of level l's (e, r) pair
+  long long total;             // elements of shared memory
+};
+constexpr size_t kCoarseCycleSmem = 200 * 1024;
+template <class T>
+bool launch_coarse_vcycle(Ctx& cx, const CoarseCycle& CC, Comp3<T> E, Comp3<T> R, int ncomp);
+
 // outer defect correction with double-word iterates (dc.cu)
 void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
                       Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int nblocks);
 void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E, long long n,
                       int ncomp);
+int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
+                        Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials,
+                        int max_blocks);
 void launch_extrapolate_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> PH,
                            Comp3<float> PL, long long n, int ncomp, int extrapolate);
 void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncomp, Scalars* S);

@@ -304,6 +304,311 @@ __global__ void k_norm_finalize(const double* partials, int nblocks, Scalars* S)
   }
 }
 
+// ---------------------------------------------------------------- blocked transfers
+// Both kernels below take one coarse cell per thread and handle its 2x2x2
+// fine children together; they require every axis to be coarsened by two
+// (the coarse-level index I owns fine cells 2I and 2I+1 on every axis).
+
+// Index of an outer neighbour (one cell beyond a 2-cell block) along one
+// axis: wrapped on a periodic axis, -1 for a Dirichlet ghost.
+__device__ __forceinline__ int outer_idx(int i, int n, int per) {
+  if (i < 0) return per ? i + n : -1;
+  if (i >= n) return per ? i - n : -1;
+  return i;
+}
+
+template <class T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <class T>
+__device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
+  const typename Vec2<T>::type v = *reinterpret_cast<const typename Vec2<T>::type*>(p);
+  a = v.x;
+  b = v.y;
+}
+
+// Residual of the 8 children, averaged onto the coarse cell (plain
+// arithmetic, neighbour order x-, x+, y-, y+, z-, z+ as gather_nb).  The
+// children of coarse x index I are fine 2I, 2I+1 (an aligned pair).
+template <class T>
+__global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<T> RC) {
+  int I, J, K, comp;
+  if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
+  const T* __restrict__ x = X.p[comp];
+  const int nx = F.n[0], ny = F.n[1], nz = F.n[2];
+  const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+  const int xm = outer_idx(i0 - 1, nx, F.per[0]), xp = outer_idx(i0 + 2, nx, F.per[0]);
+  const int ym = outer_idx(j0 - 1, ny, F.per[1]), yp = outer_idx(j0 + 2, ny, F.per[1]);
+  const int zm = outer_idx(k0 - 1, nz, F.per[2]), zp = outer_idx(k0 + 2, nz, F.per[2]);
+  auto row = [&](int j, int k) { return x + ((long long)k * ny + j) * nx; };
+  T c[2][2][2], fxm[2][2], fxp[2][2], fym[2][2], fyp[2][2], fzm[2][2], fzp[2][2], b[2][2][2];
+#pragma unroll
+  for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+    for (int jy = 0; jy < 2; ++jy) {
+      const T* r = row(j0 + jy, k0 + kz);
+      ld2(r + i0, c[kz][jy][0], c[kz][jy][1]);
+      fxm[kz][jy] = xm >= 0 ? r[xm] : (T)0;
+      fxp[kz][jy] = xp >= 0 ? r[xp] : (T)0;
+      const long long t = ((long long)(k0 + kz) * ny + j0 + jy) * nx + i0;
+      ld2(R.B[comp] + t, b[kz][jy][0], b[kz][jy][1]);
+      const T s = R.S[comp] ? R.S[comp][j0 + jy + (long long)(k0 + kz) * ny] : (T)0;
+      b[kz][jy][0] = R.beta * b[kz][jy][0] + s;
+      b[kz][jy][1] = R.beta * b[kz][jy][1] + s;
+    }
+#pragma unroll
+  for (int kz = 0; kz < 2; ++kz) {
+    if (ym >= 0) ld2(row(ym, k0 + kz) + i0, fym[kz][0], fym[kz][1]); else fym[kz][0] = fym[kz][1] = (T)0;
+    if (yp >= 0) ld2(row(yp, k0 + kz) + i0, fyp[kz][0], fyp[kz][1]); else fyp[kz][0] = fyp[kz][1] = (T)0;
+  }
+#pragma unroll
+  for (int jy = 0; jy < 2; ++jy) {
+    if (zm >= 0) ld2(row(j0 + jy, zm) + i0, fzm[jy][0], fzm[jy][1]); else fzm[jy][0] = fzm[jy][1] = (T)0;
+    if (zp >= 0) ld2(row(j0 + jy, zp) + i0, fzp[jy][0], fzp[jy][1]); else fzp[jy][0] = fzp[jy][1] = (T)0;
+  }
+  const T ih2 = lv_ih2<T>(F), al = lv_alpha<T>(F);
+  T acc = 0;
+#pragma unroll
+  for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+    for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+      for (int ix = 0; ix < 2; ++ix) {
+        const T v_xm = ix == 0 ? fxm[kz][jy] : c[kz][jy][0];
+        const T v_xp = ix == 1 ? fxp[kz][jy] : c[kz][jy][1];
+        const T v_ym = jy == 0 ? fym[kz][ix] : c[kz][0][ix];
+        const T v_yp = jy == 1 ? fyp[kz][ix] : c[kz][1][ix];
+        const T v_zm = kz == 0 ? fzm[jy][ix] : c[0][jy][ix];
+        const T v_zp = kz == 1 ? fzp[jy][ix] : c[1][jy][ix];
+        const int nwall = (ix == 0 && xm < 0) + (ix == 1 && xp < 0) + (jy == 0 && ym < 0) +
+                          (jy == 1 && yp < 0) + (kz == 0 && zm < 0) + (kz == 1 && zp < 0);
+        const T s = v_xm + v_xp + v_ym + v_yp + v_zm + v_zp;
+        acc += b[kz][jy][ix] - (s - ((T)6 + al * (T)nwall) * c[kz][jy][ix]) * ih2;
+      }
+  RC.p[comp][lin(I, J, K, C.n[0], C.n[1])] = acc * (T)0.125;
+}
+
+// x_fine += P e (trilinear, weights 3/4 and 1/4 per axis) for the 8 children
+// of one coarse cell; the coarse neighbours come from the coarse level's
+// boundary rule: periodic wrap, or -alpha * (adjacent cell) per
+// out-of-range axis (the linear extrapolation through zero at the wall).
+// Increments P e for the 8 children of coarse cell (I,J,K): weights 3/4 and
+// 1/4 per axis; the coarse neighbours come from the coarse level's boundary
+// rule: periodic wrap, or -alpha * (adjacent cell) per out-of-range axis (the
+// linear extrapolation through zero at the wall).  v[c][b][a] is the child
+// (2K+c, 2J+b, 2I+a).
+template <class T>
+__device__ __forceinline__ void prolong_children(const Level& C, const T* __restrict__ e, int I,
+                                                 int J, int K, T v[2][2][2]) {
+  const int cx_ = C.n[0], cy = C.n[1], cz = C.n[2];
+  const T ma = -lv_alpha<T>(C);
+  int ix[3], iy[3], iz[3];
+  T fx[3], fy[3], fz[3];
+  ix[1] = I; iy[1] = J; iz[1] = K;
+  fx[1] = fy[1] = fz[1] = (T)1;
+#pragma unroll
+  for (int s = 0; s < 3; s += 2) {
+    const int d = s - 1;
+    int t = outer_idx(I + d, cx_, C.per[0]);
+    ix[s] = t >= 0 ? t : I; fx[s] = t >= 0 ? (T)1 : ma;
+    t = outer_idx(J + d, cy, C.per[1]);
+    iy[s] = t >= 0 ? t : J; fy[s] = t >= 0 ? (T)1 : ma;
+    t = outer_idx(K + d, cz, C.per[2]);
+    iz[s] = t >= 0 ? t : K; fz[s] = t >= 0 ? (T)1 : ma;
+  }
+  T n[3][3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T* r = e + ((long long)iz[c] * cy + iy[b]) * cx_;
+      const T f = fz[c] * fy[b];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) n[c][b][a] = f * fx[a] * r[ix[a]];
+    }
+  const T w1 = (T)0.75, w2 = (T)0.25;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int ax = 2 * a, by = 2 * b, cz2 = 2 * c;
+        T acc = 0;
+#pragma unroll
+        for (int zz = 0; zz < 2; ++zz) {
+          const int kk = zz ? cz2 : 1;
+          const T wz = zz ? w2 : w1;
+#pragma unroll
+          for (int yy = 0; yy < 2; ++yy) {
+            const int jj = yy ? by : 1;
+            const T wy = yy ? w2 : w1;
+            acc += wz * wy * (w1 * n[kk][jj][1] + w2 * n[kk][jj][ax]);
+          }
+        }
+        v[c][b][a] = acc;
+      }
+}
+
+// x_fine += P e for the 8 children of one coarse cell per thread.
+template <class T>
+__global__ void k_prolong_block(Level F, Level C, Comp3<T> X, Comp3<T> E) {
+  int I, J, K, comp;
+  if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
+  T v[2][2][2];
+  prolong_children<T>(C, E.p[comp], I, J, K, v);
+  T* __restrict__ x = X.p[comp];
+  const int nx = F.n[0], ny = F.n[1];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      T* p = x + ((long long)(2 * K + c) * ny + 2 * J + b) * nx + 2 * I;
+      typename Vec2<T>::type cur = *reinterpret_cast<typename Vec2<T>::type*>(p);
+      cur.x += v[c][b][0];
+      cur.y += v[c][b][1];
+      *reinterpret_cast<typename Vec2<T>::type*>(p) = cur;
+    }
+}
+
+__host__ __device__ bool blocked_transfer_ok(const Level& F, const Level& C) {
+  for (int a = 0; a < 3; ++a)
+    if (F.n[a] != 2 * C.n[a]) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------- coarse V-cycle in one CTA
+// The levels from `first` down to the coarsest are small enough to live in
+// shared memory; one CTA per component runs the whole lower part of the
+// V-cycle there (same operations as the level-by-level kernels: red-black
+// sweeps, residual restricted by averaging, trilinear prolongation), which
+// replaces dozens of latency-bound launches per V-cycle by one.
+template <class T>
+__device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2) {
+  const int nx = L.n[0], ny = L.n[1];
+  const int n = (int)L.cells();
+  for (int s = 0; s < sweeps; ++s)
+    for (int color = 0; color < 2; ++color) {
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int i = t % nx, q = t / nx;
+        const int j = q % ny, k = q / ny;
+        if (((i + j + k) & 1) != color) continue;
+        T v[6];
+        int nwall;
+        const int m = gather_nb(e, L, i, j, k, t, v, nwall);
+        T sum = 0;
+        for (int q2 = 0; q2 < m; ++q2) sum += v[q2];
+        e[t] = (sum - r[t] * h2) * lv_rc<T>(L, nwall);
+      }
+      __syncthreads();
+    }
+}
+
+template <class T>
+__device__ void cv_restrict(const Level& F, const Level& C, const T* e, const T* r, T* rc) {
+  const int nc = (int)C.cells();
+  const int fx = F.n[0] / C.n[0], fy = F.n[1] / C.n[1], fz = F.n[2] / C.n[2];
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    const int I = t % C.n[0], q = t / C.n[0];
+    const int J = q % C.n[1], K = q / C.n[1];
+    T acc = 0;
+    for (int dk = 0; dk < fz; ++dk)
+      for (int dj = 0; dj < fy; ++dj)
+        for (int di = 0; di < fx; ++di) {
+          const int i = I * fx + di, j = J * fy + dj, k = K * fz + dk;
+          const int c = (k * F.n[1] + j) * F.n[0] + i;
+          acc += resid_plain(e, F, i, j, k, c, r[c]);
+        }
+    rc[t] = acc / (T)(fx * fy * fz);
+  }
+  __syncthreads();
+}
+
+template <class T>
+__device__ void cv_prolong(const Level& F, const Level& C, T* e, const T* ec) {
+  if (blocked_transfer_ok(F, C)) {   // as k_prolong_block
+    const int nc = (int)C.cells();
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+      const int I = t % C.n[0], q = t / C.n[0];
+      const int J = q % C.n[1], K = q / C.n[1];
+      T v[2][2][2];
+      prolong_children<T>(C, ec, I, J, K, v);
+      for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a)
+            e[((2 * K + c) * F.n[1] + 2 * J + b) * F.n[0] + 2 * I + a] += v[c][b][a];
+    }
+    __syncthreads();
+    return;
+  }
+  const int nf = (int)F.cells();   // as k_prolong_add
+  const T al = lv_alpha<T>(C);
+  for (int t = threadIdx.x; t < nf; t += blockDim.x) {
+    const int i = t % F.n[0], q = t / F.n[0];
+    const int j = q % F.n[1], k = q / F.n[1];
+    const Interp1<T> ax = interp_axis<T>(i, F.n[0] / C.n[0], C.n[0], C.per[0], al);
+    const Interp1<T> ay = interp_axis<T>(j, F.n[1] / C.n[1], C.n[1], C.per[1], al);
+    const Interp1<T> az = interp_axis<T>(k, F.n[2] / C.n[2], C.n[2], C.per[2], al);
+    T acc = 0;
+    for (int c2 = 0; c2 < 2; ++c2)
+      for (int b2 = 0; b2 < 2; ++b2)
+        for (int a2 = 0; a2 < 2; ++a2) {
+          const T w = ax.w[a2] * ay.w[b2] * az.w[c2];
+          if (w != (T)0) acc += w * ec[(az.idx[c2] * C.n[1] + ay.idx[b2]) * C.n[0] + ax.idx[a2]];
+        }
+    e[t] += acc;
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseCycle CC, Comp3<T> E, Comp3<T> RR) {
+  extern __shared__ unsigned char smem_cv[];
+  T* base = reinterpret_cast<T*>(smem_cv);
+  const int comp = blockIdx.x;
+  const int f = CC.first, l_last = CC.last;
+  T* e[kMaxLevels];
+  T* r[kMaxLevels];
+  for (int l = f; l <= l_last; ++l) {
+    e[l] = base + CC.off[l];
+    r[l] = e[l] + CC.lv[l].cells();
+  }
+  const int n0 = (int)CC.lv[f].cells();
+  for (int t = threadIdx.x; t < n0; t += blockDim.x) {
+    r[f][t] = RR.p[comp][t];
+    e[f][t] = (T)0;
+  }
+  __syncthreads();
+  for (int l = f; l < l_last; ++l) {
+    cv_sweep<T>(CC.lv[l], e[l], r[l], CC.nu1, (T)CC.h2[l]);
+    cv_restrict<T>(CC.lv[l], CC.lv[l + 1], e[l], r[l], r[l + 1]);
+    const int nc = (int)CC.lv[l + 1].cells();
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) e[l + 1][t] = (T)0;
+    __syncthreads();
+  }
+  cv_sweep<T>(CC.lv[l_last], e[l_last], r[l_last], CC.coarse_sweeps, (T)CC.h2[l_last]);
+  for (int l = l_last - 1; l >= f; --l) {
+    cv_prolong<T>(CC.lv[l], CC.lv[l + 1], e[l], e[l + 1]);
+    cv_sweep<T>(CC.lv[l], e[l], r[l], CC.nu2, (T)CC.h2[l]);
+  }
+  for (int t = threadIdx.x; t < n0; t += blockDim.x) E.p[comp][t] = e[f][t];
+}
+
+template <class T>
+bool launch_coarse_vcycle(Ctx& cx, const CoarseCycle& CC, Comp3<T> E, Comp3<T> R, int ncomp) {
+  const size_t smem = (size_t)CC.total * sizeof(T);
+  if (smem > kCoarseCycleSmem) return false;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_coarse_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return false;
+  cx.before(VSV_KCLASS_SMOOTH);
+  k_coarse_vcycle<T><<<ncomp, 1024, smem, cx.stream>>>(CC, E, R);
+  cx.after(VSV_KCLASS_SMOOTH);
+  return true;
+}
+
 // ---------------------------------------------------------------- launchers
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
@@ -320,6 +625,12 @@ template <class T>
 void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Rhs3<T> R,
                            Comp3<T> RC, int ncomp, bool exact) {
   const dim3 grid = grid3(C.n[0], C.n[1], C.n[2], ncomp);
+  if (!exact && blocked_transfer_ok(F, C)) {
+    cx.before(VSV_KCLASS_RESTRICT);
+    k_restrict_block<T><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC);
+    cx.after(VSV_KCLASS_RESTRICT);
+    return;
+  }
   cx.before(VSV_KCLASS_RESTRICT);
   float ih_hi = (float)F.inv_h2, ih_lo = (float)(F.inv_h2 - (double)ih_hi);
   if constexpr (std::is_same<T, float>::value) {
@@ -335,6 +646,12 @@ void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, 
 
 template <class T>
 void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Comp3<T> E, int ncomp) {
+  if (blocked_transfer_ok(F, C)) {
+    cx.before(VSV_KCLASS_PROLONG);
+    k_prolong_block<T><<<grid3(C.n[0], C.n[1], C.n[2], ncomp), block3(), 0, cx.stream>>>(F, C, X, E);
+    cx.after(VSV_KCLASS_PROLONG);
+    return;
+  }
   const dim3 grid = grid3(F.n[0], F.n[1], F.n[2], ncomp);
   cx.before(VSV_KCLASS_PROLONG);
   k_prolong_add<T><<<grid, block3(), 0, cx.stream>>>(F, C, X, E);
@@ -407,6 +724,7 @@ void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncom
   template void launch_prolong_add<T>(Ctx&, const Level&, const Level&, Comp3<T>, Comp3<T>, int);  \
   template void launch_zero<T>(Ctx&, Comp3<T>, long long, int);                                    \
   template void launch_extrapolate<T>(Ctx&, Comp3<T>, Comp3<T>, long long, int, int);              \
+  template bool launch_coarse_vcycle<T>(Ctx&, const CoarseCycle&, Comp3<T>, Comp3<T>, int);        \
   template bool launch_coarse_solve<T>(Ctx&, const Level&, Comp3<T>, Comp3<T>, int, int, double);  \
   template void launch_resid_norm<T>(Ctx&, const Level&, Comp3<T>, Rhs3<T>, int, bool, double*,    \
                                      int, Scalars*);

@@ -18,83 +18,27 @@
 // Planes are staged by cp.async (16-byte vectors, zero fill on Dirichlet
 // ghosts, wrap on periodic axes; two planes in flight) into a ring of five
 // x-planes and three rhs planes.
-#include "internal.h"
+#include "tile.cuh"
 
 namespace vsv {
 
+using namespace tile;
+
 namespace {
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gmem), "r"(n));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
-constexpr int kTX = 128;   // tile width (x)
-constexpr int kTY = 16;    // tile height (y)
-constexpr int kH = 2;      // halo rows of x
-constexpr int kHX = 4;     // halo columns (one 16-byte vector)
-constexpr int kW = kTX + 2 * kHX;        // staged row length (floats)
-constexpr int kNV = kW / 4;              // 16-byte vectors per staged row
+constexpr int kH = 2;                    // halo rows of x
 constexpr int kRA = kTY + 2 * kH;        // staged x rows
 constexpr int kRB = kTY + 2 * (kH - 1);  // staged rhs rows
-constexpr int kNA = 5;     // x-plane ring slots
-constexpr int kNB = 3;     // rhs-plane ring slots
-constexpr int kThreads = 256;
+constexpr int kNA = 5;                   // x-plane ring slots
+constexpr int kNB = 3;                   // rhs-plane ring slots
 constexpr int kStageA = (kRA * kNV + kThreads - 1) / kThreads;   // vectors per thread
 constexpr int kStageB = (kRB * kNV + kThreads - 1) / kThreads;
 
-struct FusedGeom {
-  int nx, ny, nz;
-  int per_y, per_z;
-  int ntx, nty;          // tiles along x, y
-  int zchunk;
+struct FusedGeom : Geom {
   float rc[7];           // 1 / (6 + alpha * nwall), as in Level::rcf
   float h2;
   float beta;            // b = beta * B + S
 };
-
-__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
-// Per-thread staging descriptors: shared offset, global row offset within a
-// plane (j * nx + x) and whether the row exists (else zero fill).
-template <int NS>
-struct StageDesc {
-  int soff[NS];
-  int goff[NS];
-  bool ok[NS];
-  bool used[NS];
-  __device__ __forceinline__ void init(const FusedGeom& G, int x0, int y0, int hr, int rows) {
-    for (int s = 0; s < NS; ++s) {
-      const int t = threadIdx.x + kThreads * s;
-      used[s] = t < rows * kNV;
-      const int r = t / kNV, v = t - r * kNV;
-      int j = y0 - hr + r;
-      bool okr = true;
-      if (G.per_y) j = wrapi(j, G.ny);
-      else if (j < 0 || j >= G.ny) okr = false;
-      const int x = wrapi(x0 - kHX + 4 * v, G.nx);
-      soff[s] = r * kW + 4 * v;
-      goff[s] = okr ? j * G.nx + x : 0;
-      ok[s] = okr;
-    }
-  }
-  __device__ __forceinline__ void stage(float* slot, const float* __restrict__ src, const FusedGeom& G,
-                                        int plane, bool zero) const {
-    bool pvalid = !zero;
-    int k = plane;
-    if (G.per_z) k = wrapi(k, G.nz);
-    else if (k < 0 || k >= G.nz) pvalid = false;
-    const float* base = src + (pvalid ? (long long)k * G.ny * G.nx : 0LL);
-    for (int s = 0; s < NS; ++s)
-      if (used[s]) cp_async16(slot + soff[s], base + goff[s], pvalid && ok[s]);
-  }
-};
-
-__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
 // Red (or black) update of one float4 group: the two cells at offsets par and
 // par + 2, given own V (centre row), U / D (rows above / below), M / P
@@ -278,10 +222,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
 
 // Can the fused sweep handle this level?  (All three axes active, x
 // periodic, tile-aligned extents.)
-bool fused_sweep_ok(const Level& L) {
-  return L.act[0] && L.act[1] && L.act[2] && L.per[0] && L.n[0] % kTX == 0 &&
-         L.n[1] % kTY == 0 && L.n[2] >= 2;
-}
+bool fused_sweep_ok(const Level& L) { return level_ok(L); }
 
 size_t fused_sweep_smem() { return (size_t)(kNA * kRA + kNB * kRB) * kW * sizeof(float); }
 

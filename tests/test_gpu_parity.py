@@ -325,7 +325,8 @@ def test_fused_sweep_bit_identical_to_reference(V, bc):
         x, cyc, rr, st = sim.solve_poisson(b, periodic=bc, tol=0.0, max_cycles=3, check=False)
         out.append((x, rr))
         sim.close()
-    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
+    assert abs(out[0][1] - out[1][1]) <= 1e-6 * abs(out[1][1])   # FP32 norm partials, other order
     ref = solve_poisson(b, 1.0, bc)
     assert rel(out[0][0], ref) < 3e-2   # three V-cycles from zero
 
