@@ -312,10 +312,7 @@ void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp
   if constexpr (std::is_same<T, float>::value) {
     if (g->sol.variant == 0 && fused_sweep_ok(L) && g->mg_t[l][0] && nu >= 2) {
       Comp3<float> Tt = comp3<float>(g->mg_t[l][0], g->mg_t[l][1], g->mg_t[l][2]);
-      const long long tiles = (long long)(L.n[0] / 128) * (L.n[1] / 16) * ncomp;
-      const long long want = 8LL * 152;
-      int nzc = (int)std::max(1LL, (want + tiles - 1) / tiles);
-      int zchunk = std::max(16, (L.n[2] + nzc - 1) / nzc);
+      const int zchunk = 0;   // chosen by the launcher
       int s = 0;
       bool z = x_zero;
       for (; s + 1 < nu; s += 2) {
@@ -358,6 +355,25 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
       launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
     }
     return;
+  }
+  if (l > 0 && x_zero && g->sol.variant == 0 && R.beta == (T)1 && !R.S[0] && !R.S[1] && !R.S[2]) {
+    // the remaining levels fit in one CTA's shared memory: one launch
+    CoarseCycle CC{};
+    CC.first = l;
+    CC.last = (int)lv.size() - 1;
+    CC.nu1 = g->sol.nu1;
+    CC.nu2 = g->sol.nu2;
+    CC.coarse_sweeps = g->sol.coarse_sweeps;
+    long long off = 0;
+    for (int q = l; q <= CC.last; ++q) {
+      CC.lv[q] = lv[q];
+      CC.h2[q] = 1.0 / lv[q].inv_h2;
+      CC.off[q] = off;
+      off += 2 * lv[q].cells();
+    }
+    CC.total = off;
+    Comp3<T> RR{{(T*)R.B[0], (T*)R.B[1], (T*)R.B[2]}};
+    if (launch_coarse_vcycle<T>(g->cx, CC, X, RR, ncomp)) return;
   }
   smooth<T>(g, L, l, X, R, ncomp, g->sol.nu1, x_zero);
   const Level& C = lv[l + 1];
@@ -979,6 +995,12 @@ vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int prec
   g->ws = (char*)workspace;
   g->ws_bytes = ws_bytes;
   g->cx.stream = (cudaStream_t)cuda_stream;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      g->cx.sms = sms;
+  }
   carve(nx, ny, nz, precision, g, g->ws);
   g->flow = vsv_flow_params{VSV_QUIESCENT, 0.0, 0.0, 0.0, 1.0};
   g->fe = vsv_fe_params{VSV_CAHN_HILLIARD, 1.0, 0.0, 1.0, 1.0, 0.0, 0.0, 0};

@@ -45,6 +45,11 @@ template <> __host__ __device__ inline double lv_ih2<double>(const Level& L) { r
 template <class T>
 struct Comp3 {
   T* p[3];
+  // p[c] without a runtime index into the array (a kernel parameter indexed
+  // at run time is copied to local memory first)
+  __host__ __device__ __forceinline__ T* at(int c) const {
+    return c == 0 ? p[0] : (c == 1 ? p[1] : p[2]);
+  }
 };
 
 // Right-hand side b = beta * B[c] + S[j + k * ny] (S may be null).
@@ -53,6 +58,12 @@ struct Rhs3 {
   const T* B[3];
   const T* S[3];
   T beta;
+  __host__ __device__ __forceinline__ const T* b_at(int c) const {
+    return c == 0 ? B[0] : (c == 1 ? B[1] : B[2]);
+  }
+  __host__ __device__ __forceinline__ const T* s_at(int c) const {
+    return c == 0 ? S[0] : (c == 1 ? S[1] : S[2]);
+  }
 };
 
 // Device scalars written by reductions and read by later kernels.

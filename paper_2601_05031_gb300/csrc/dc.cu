@@ -37,12 +37,12 @@ __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<floa
                             float ih_lo) {
   const int comp = blockIdx.y;
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-  NbFetch H{XH.p[comp], nx, ny, nz, {L.per[0], L.per[1], L.per[2]}, {L.act[0], L.act[1], L.act[2]}};
-  NbFetch Lo{XL.p[comp], nx, ny, nz, {L.per[0], L.per[1], L.per[2]}, {L.act[0], L.act[1], L.act[2]}};
-  const float* __restrict__ bh = R.B[comp];
-  const float* __restrict__ bl = BL.p[comp];
-  const float* __restrict__ S = R.S[comp];
-  float* __restrict__ out = OUT.p[comp];
+  NbFetch H{XH.at(comp), nx, ny, nz, {L.per[0], L.per[1], L.per[2]}, {L.act[0], L.act[1], L.act[2]}};
+  NbFetch Lo{XL.at(comp), nx, ny, nz, {L.per[0], L.per[1], L.per[2]}, {L.act[0], L.act[1], L.act[2]}};
+  const float* __restrict__ bh = R.b_at(comp);
+  const float* __restrict__ bl = BL.at(comp);
+  const float* __restrict__ S = R.s_at(comp);
+  float* __restrict__ out = OUT.at(comp);
   const float beta = R.beta;
   const float dcoef = (float)(2 * (L.act[0] + L.act[1] + L.act[2]));
   double rr = 0.0, bb = 0.0;
@@ -103,9 +103,9 @@ __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<floa
 // (x_hi, x_lo) <- (x_hi, x_lo) + e
 __global__ void k_update_dw(Comp3<float> XH, Comp3<float> XL, Comp3<float> E, long long n) {
   const int comp = blockIdx.y;
-  float* __restrict__ xh = XH.p[comp];
-  float* __restrict__ xl = XL.p[comp];
-  const float* __restrict__ e = E.p[comp];
+  float* __restrict__ xh = XH.at(comp);
+  float* __restrict__ xl = XL.at(comp);
+  const float* __restrict__ e = E.at(comp);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     const FF v = ff_add_f(FF{xh[t], xl[t]}, e[t]);
@@ -119,10 +119,10 @@ __global__ void k_update_dw(Comp3<float> XH, Comp3<float> XL, Comp3<float> E, lo
 __global__ void k_extrapolate_dw(Comp3<float> XH, Comp3<float> XL, Comp3<float> PH, Comp3<float> PL,
                                  long long n, int extrapolate) {
   const int comp = blockIdx.y;
-  float* __restrict__ xh = XH.p[comp];
-  float* __restrict__ xl = XL.p[comp];
-  float* __restrict__ ph = PH.p[comp];
-  float* __restrict__ pl = PL.p[comp];
+  float* __restrict__ xh = XH.at(comp);
+  float* __restrict__ xl = XL.at(comp);
+  float* __restrict__ ph = PH.at(comp);
+  float* __restrict__ pl = PL.at(comp);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     const FF x{xh[t], xl[t]};
@@ -150,9 +150,13 @@ void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL,
 // bits) on a 128 x 16 tile marching along z: x_hi and x_lo planes staged in
 // shared memory (one-cell halo), each thread's own float4 groups of the
 // planes below and above held in registers, rhs read straight from memory.
+// At step p the CTA issues the copies of plane p + 3 and waits for those of
+// plane p + 1 (two steps of copies in flight); five ring slots keep the copies
+// clear of the planes p - 1 and p that a warp still in step p - 1 may read,
+// so one barrier per step suffices.
 namespace {
 constexpr int kDR = tile::kTY + 2;                                   // staged rows
-constexpr int kDS = 3;                                               // ring slots
+constexpr int kDS = 5;                                               // ring slots
 constexpr int kDStage = (kDR * tile::kNV + tile::kThreads - 1) / tile::kThreads;
 
 struct DefGeom : tile::Geom {
@@ -200,12 +204,12 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
   float* sH = reinterpret_cast<float*>(smem_d4);
   float* sL = sH + kDS * kDR * kW;
   const int comp = blockIdx.z;
-  const float* __restrict__ xh = XH.p[comp];
-  const float* __restrict__ xl = XL.p[comp];
-  const float* __restrict__ bh = R.B[comp];
-  const float* __restrict__ bl = BL.p[comp];
-  const float* __restrict__ S = R.S[comp];
-  float* __restrict__ out = OUT.p[comp];
+  const float* __restrict__ xh = XH.at(comp);
+  const float* __restrict__ xl = XL.at(comp);
+  const float* __restrict__ bh = R.b_at(comp);
+  const float* __restrict__ bl = BL.at(comp);
+  const float* __restrict__ S = R.s_at(comp);
+  float* __restrict__ out = OUT.at(comp);
   const int tx = blockIdx.x % G.ntx, tyb = blockIdx.x / G.ntx;
   const int x0 = tx * kTX, y0 = tyb * kTY;
   const int zb = blockIdx.y * G.zchunk;
@@ -213,42 +217,50 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
   const int tid = threadIdx.x, gx = tid & 31, ty = tid >> 5;
   const int q = gx + 1;
   const float beta = G.beta;
-  auto slot = [&](float* base, int plane) { return base + (((plane % kDS) + kDS) % kDS) * (kDR * kW); };
+  auto slot = [&](float* base, int plane) {
+    return base + ((unsigned)(plane + kDS) % (unsigned)kDS) * (kDR * kW);   // plane >= -1
+  };
   StageDesc<kDStage> ds;
   ds.init(G, x0, y0, 1, kDR);
   int rown[2], jown[2];
+#pragma unroll
   for (int h = 0; h < 2; ++h) {
     rown[h] = ty + 8 * h + 1;
     jown[h] = y0 + ty + 8 * h;
   }
-  ds.stage(slot(sH, zb - 1), xh, G, zb - 1, false);
-  ds.stage(slot(sL, zb - 1), xl, G, zb - 1, false);
-  ds.stage(slot(sH, zb), xh, G, zb, false);
-  ds.stage(slot(sL, zb), xl, G, zb, false);
-  ds.stage(slot(sH, zb + 1), xh, G, zb + 1, false);
-  ds.stage(slot(sL, zb + 1), xl, G, zb + 1, false);
+  // group 0: planes zb-1 .. zb+1 (step zb); group 1: plane zb+2 (step zb+1)
+  for (int pl = zb - 1; pl <= zb + 1; ++pl) {
+    ds.stage(slot(sH, pl), xh, G, pl, false);
+    ds.stage(slot(sL, pl), xl, G, pl, false);
+  }
   cp_async_commit();
-  cp_async_wait0();
+  if (zb + 2 <= ze) {
+    ds.stage(slot(sH, zb + 2), xh, G, zb + 2, false);
+    ds.stage(slot(sL, zb + 2), xl, G, zb + 2, false);
+  }
+  cp_async_commit();
+  cp_async_wait1();
   __syncthreads();
   float4 Mh[2], Ml[2], Vh[2], Vl[2], Ph[2], Pl[2];
+#pragma unroll
   for (int h = 0; h < 2; ++h) {
     Vh[h] = lds4(slot(sH, zb - 1) + rown[h] * kW + 4 * q);
     Vl[h] = lds4(slot(sL, zb - 1) + rown[h] * kW + 4 * q);
     Ph[h] = lds4(slot(sH, zb) + rown[h] * kW + 4 * q);
     Pl[h] = lds4(slot(sL, zb) + rown[h] * kW + 4 * q);
   }
-  __syncthreads();
   double rr = 0.0, bb = 0.0;
   for (int p = zb; p < ze; ++p) {
-    if (p + 2 <= ze) {   // plane p+2 is needed by step p+1
-      ds.stage(slot(sH, p + 2), xh, G, p + 2, false);
-      ds.stage(slot(sL, p + 2), xl, G, p + 2, false);
+    if (p + 3 <= ze) {   // plane p+3 is needed by step p+2
+      ds.stage(slot(sH, p + 3), xh, G, p + 3, false);
+      ds.stage(slot(sL, p + 3), xl, G, p + 3, false);
     }
     cp_async_commit();
-    cp_async_wait1();
+    cp_async_wait2();
     __syncthreads();
     const float* cH = slot(sH, p);
     const float* cL = slot(sL, p);
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       Mh[h] = Vh[h]; Ml[h] = Vl[h];
       Vh[h] = Ph[h]; Vl[h] = Pl[h];
@@ -256,6 +268,7 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
       Pl[h] = lds4(slot(sL, p + 1) + rown[h] * kW + 4 * q);
     }
     float r2 = 0.f, b2 = 0.f;
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = rown[h], j = jown[h];
       const float* rowH = cH + r * kW;
@@ -289,7 +302,6 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
     }
     rr += (double)r2;
     bb += (double)b2;
-    __syncthreads();
   }
   cp_async_wait0();
   if (partials) {
@@ -310,19 +322,20 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
                         Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int max_blocks) {
   if (!tile::level_ok(L)) return 0;
   const int tiles = (L.n[0] / tile::kTX) * (L.n[1] / tile::kTY);
-  int nzc = std::max(1, std::min((8 * 152 + tiles * ncomp - 1) / (tiles * ncomp), L.n[2] / 16));
-  while (nzc > 1 && tiles * nzc * ncomp > max_blocks) --nzc;
-  if (tiles * nzc * ncomp > max_blocks) return 0;
+  int chunk = tile::pick_zchunk(L, ncomp, 2 * cx.sms, 2);
+  while (tiles * ((L.n[2] + chunk - 1) / chunk) * ncomp > max_blocks && chunk < L.n[2]) ++chunk;
+  const int nz = (L.n[2] + chunk - 1) / chunk;
+  if (tiles * nz * ncomp > max_blocks) return 0;
   DefGeom G;
-  static_cast<tile::Geom&>(G) = tile::geom(L, (L.n[2] + nzc - 1) / nzc);
+  static_cast<tile::Geom&>(G) = tile::geom(L, chunk);
   G.ih_hi = (float)L.inv_h2;
   G.ih_lo = (float)(L.inv_h2 - (double)G.ih_hi);
   G.beta = R.beta;
-  const int nz = (L.n[2] + G.zchunk - 1) / G.zchunk;
   const size_t smem = (size_t)2 * kDS * kDR * tile::kW * sizeof(float);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_defect_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_defect_tiled, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = true;
   }
   dim3 grid(tiles, nz, ncomp);
@@ -334,7 +347,7 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
 
 void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E, long long n,
                       int ncomp) {
-  const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8 * 152);
+  const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(VSV_KCLASS_PROLONG);
   k_update_dw<<<grid, kBlock, 0, cx.stream>>>(XH, XL, E, n);
@@ -343,7 +356,7 @@ void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E,
 
 void launch_extrapolate_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> PH,
                            Comp3<float> PL, long long n, int ncomp, int extrapolate) {
-  const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8 * 152);
+  const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
   k_extrapolate_dw<<<grid, kBlock, 0, cx.stream>>>(XH, XL, PH, PL, n, extrapolate);

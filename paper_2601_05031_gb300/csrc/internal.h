@@ -14,6 +14,7 @@ namespace vsv {
 // event brackets around every launch of one kernel class.
 struct Ctx {
   cudaStream_t stream = nullptr;
+  int sms = 148;                 // multiprocessors of the grid's device (set at create)
   long long launches = 0;
   int prof_class = -1;
   std::vector<cudaEvent_t> ev;   // pairs (start, stop)

@@ -11,35 +11,42 @@
 
 namespace vsv {
 
-// Neighbour values of cell (i,j,k) on level L; Dirichlet ghosts are not
-// returned but counted in nwall (their value is -alpha * x_c, zero on the
-// fine level).  Returns the number of values written to v.
-template <class T>
-__device__ __forceinline__ int gather_nb(const T* __restrict__ x, const Level& L, int i, int j,
-                                         int k, long long c, T* v, int& nwall) {
-  int m = 0;
+// Visit the neighbour values of cell (i,j,k) on level L in the order x-, x+,
+// y-, y+, z-, z+, skipping Dirichlet ghosts, which are counted in nwall
+// instead (their value is -alpha * x_c, zero on the fine level).
+template <class T, class F>
+__device__ __forceinline__ void for_nb(const T* __restrict__ x, const Level& L, int i, int j, int k,
+                                       long long c, int& nwall, F&& f) {
   nwall = 0;
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
   const long long sy = nx, sz = (long long)nx * ny;
   if (L.act[0]) {
-    if (i > 0) v[m++] = x[c - 1]; else if (L.per[0]) v[m++] = x[c + nx - 1]; else ++nwall;
-    if (i < nx - 1) v[m++] = x[c + 1]; else if (L.per[0]) v[m++] = x[c - (nx - 1)]; else ++nwall;
+    if (i > 0) f(x[c - 1]); else if (L.per[0]) f(x[c + nx - 1]); else ++nwall;
+    if (i < nx - 1) f(x[c + 1]); else if (L.per[0]) f(x[c - (nx - 1)]); else ++nwall;
   }
   if (L.act[1]) {
-    if (j > 0) v[m++] = x[c - sy]; else if (L.per[1]) v[m++] = x[c + (ny - 1) * sy]; else ++nwall;
-    if (j < ny - 1) v[m++] = x[c + sy]; else if (L.per[1]) v[m++] = x[c - (ny - 1) * sy]; else ++nwall;
+    if (j > 0) f(x[c - sy]); else if (L.per[1]) f(x[c + (ny - 1) * sy]); else ++nwall;
+    if (j < ny - 1) f(x[c + sy]); else if (L.per[1]) f(x[c - (ny - 1) * sy]); else ++nwall;
   }
   if (L.act[2]) {
-    if (k > 0) v[m++] = x[c - sz]; else if (L.per[2]) v[m++] = x[c + (nz - 1) * sz]; else ++nwall;
-    if (k < nz - 1) v[m++] = x[c + sz]; else if (L.per[2]) v[m++] = x[c - (nz - 1) * sz]; else ++nwall;
+    if (k > 0) f(x[c - sz]); else if (L.per[2]) f(x[c + (nz - 1) * sz]); else ++nwall;
+    if (k < nz - 1) f(x[c + sz]); else if (L.per[2]) f(x[c - (nz - 1) * sz]); else ++nwall;
   }
-  return m;
+}
+
+// Sum of the neighbour values, accumulated from zero in the order of for_nb.
+template <class T>
+__device__ __forceinline__ T sum_nb(const T* __restrict__ x, const Level& L, int i, int j, int k,
+                                    long long c, int& nwall) {
+  T s = 0;
+  for_nb(x, L, i, j, k, c, nwall, [&](T v) { s += v; });
+  return s;
 }
 
 template <class T>
 __device__ __forceinline__ T rhs_at(const Rhs3<T>& R, int comp, long long c, int j, int k, int ny) {
-  T b = R.beta * R.B[comp][c];
-  if (R.S[comp]) b += R.S[comp][j + (long long)k * ny];
+  T b = R.beta * R.b_at(comp)[c];
+  if (R.s_at(comp)) b += R.s_at(comp)[j + (long long)k * ny];
   return b;
 }
 
@@ -50,11 +57,8 @@ __device__ __forceinline__ int n_active(const Level& L) { return L.act[0] + L.ac
 template <class T>
 __device__ __forceinline__ T resid_plain(const T* __restrict__ x, const Level& L, int i, int j, int k,
                                          long long c, T b) {
-  T v[6];
   int nwall;
-  int m = gather_nb(x, L, i, j, k, c, v, nwall);
-  T s = 0;
-  for (int q = 0; q < m; ++q) s += v[q];
+  const T s = sum_nb(x, L, i, j, k, c, nwall);
   T coef = (T)(2 * n_active(L)) + lv_alpha<T>(L) * (T)nwall;
   return b - (s - coef * x[c]) * lv_ih2<T>(L);
 }
@@ -65,12 +69,10 @@ __device__ __forceinline__ T resid_plain(const T* __restrict__ x, const Level& L
 __device__ __forceinline__ float resid_exact(const float* __restrict__ x, const Level& L, int i,
                                              int j, int k, long long c, float b, float ih_hi,
                                              float ih_lo) {
-  float v[6];
   int nwall;
-  int m = gather_nb(x, L, i, j, k, c, v, nwall);
-  const float coef = (float)(2 * n_active(L)) + L.alphaf * (float)nwall;
   CascadeSum t(0.f);
-  for (int q = 0; q < m; ++q) t.add(v[q]);
+  for_nb(x, L, i, j, k, c, nwall, [&](float v) { t.add(v); });
+  const float coef = (float)(2 * n_active(L)) + L.alphaf * (float)nwall;
   t.add_scaled(-coef, x[c]);
   if (ih_hi == 1.f && ih_lo == 0.f) {
     CascadeSum r(b);
@@ -107,15 +109,12 @@ __global__ void k_rb_sweep(Level L, Comp3<T> X, Rhs3<T> R, int color, T omega, T
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
   int i2, j, k, comp;
   if (!cell3((nx + 1) >> 1, ny, nz, i2, j, k, comp)) return;
-  T* __restrict__ x = X.p[comp];
+  T* __restrict__ x = X.at(comp);
   const int i = 2 * i2 + ((j + k + color) & 1);
   if (i >= nx) return;
   const long long c = lin(i, j, k, nx, ny);
-  T v[6];
   int nwall;
-  const int m = gather_nb(x, L, i, j, k, c, v, nwall);
-  T s = 0;
-  for (int q = 0; q < m; ++q) s += v[q];
+  const T s = sum_nb(x, L, i, j, k, c, nwall);
   const T b = rhs_at(R, comp, c, j, k, ny);
   const T gs = (s - b * h2) * lv_rc<T>(L, nwall);
   x[c] = (omega == (T)1) ? gs : x[c] + omega * (gs - x[c]);
@@ -128,7 +127,7 @@ __global__ void k_resid_restrict(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<
                                  float ih_lo) {
   int I, J, K, comp;
   if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
-  const T* __restrict__ x = X.p[comp];
+  const T* __restrict__ x = X.at(comp);
   const long long t = lin(I, J, K, C.n[0], C.n[1]);
   const int fx = F.n[0] / C.n[0], fy = F.n[1] / C.n[1], fz = F.n[2] / C.n[2];
   T acc = 0;
@@ -140,7 +139,7 @@ __global__ void k_resid_restrict(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<
         const T b = rhs_at(R, comp, c, j, k, F.n[1]);
         acc += resid_at<T, EXACT>(x, F, i, j, k, c, b, ih_hi, ih_lo);
       }
-  RC.p[comp][t] = acc / (T)(fx * fy * fz);
+  RC.at(comp)[t] = acc / (T)(fx * fy * fz);
 }
 
 // One axis of the cell-centred linear interpolation: the two coarse indices
@@ -191,7 +190,7 @@ __global__ void k_prolong_add(Level F, Level C, Comp3<T> X, Comp3<T> E) {
   const Interp1<T> ax = interp_axis<T>(i, F.n[0] / C.n[0], C.n[0], C.per[0], al);
   const Interp1<T> ay = interp_axis<T>(j, F.n[1] / C.n[1], C.n[1], C.per[1], al);
   const Interp1<T> az = interp_axis<T>(k, F.n[2] / C.n[2], C.n[2], C.per[2], al);
-  const T* __restrict__ e = E.p[comp];
+  const T* __restrict__ e = E.at(comp);
   T acc = 0;
   for (int c2 = 0; c2 < 2; ++c2)
     for (int b2 = 0; b2 < 2; ++b2)
@@ -199,13 +198,13 @@ __global__ void k_prolong_add(Level F, Level C, Comp3<T> X, Comp3<T> E) {
         const T w = ax.w[a2] * ay.w[b2] * az.w[c2];
         if (w != (T)0) acc += w * e[lin(ax.idx[a2], ay.idx[b2], az.idx[c2], C.n[0], C.n[1])];
       }
-  X.p[comp][t] += acc;
+  X.at(comp)[t] += acc;
 }
 
 template <class T>
 __global__ void k_zero(Comp3<T> X, long long n) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) X.p[blockIdx.y][t] = (T)0;
+  if (t < n) X.at(blockIdx.y)[t] = (T)0;
 }
 
 // Linear extrapolation in time of the initial guess: x <- 2 x - xp and
@@ -213,8 +212,8 @@ __global__ void k_zero(Comp3<T> X, long long n) {
 template <class T>
 __global__ void k_extrapolate(Comp3<T> X, Comp3<T> XP, long long n, int extrapolate) {
   const int comp = blockIdx.y;
-  T* __restrict__ x = X.p[comp];
-  T* __restrict__ xp = XP.p[comp];
+  T* __restrict__ x = X.at(comp);
+  T* __restrict__ xp = XP.at(comp);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     const T a = x[t];
@@ -231,7 +230,7 @@ __global__ void k_coarse_solve(Level L, Comp3<T> E, Comp3<T> RR, int sweeps, T h
   T* e = reinterpret_cast<T*>(smem_raw);
   const int comp = blockIdx.y;
   const long long n = L.cells();
-  const T* __restrict__ r = RR.p[comp];
+  const T* __restrict__ r = RR.at(comp);
   T* rs = e + n;
   for (long long t = threadIdx.x; t < n; t += blockDim.x) {
     e[t] = 0;
@@ -246,16 +245,13 @@ __global__ void k_coarse_solve(Level L, Comp3<T> E, Comp3<T> RR, int sweeps, T h
         const long long q = t / nx;
         const int j = (int)(q % ny), k = (int)(q / ny);
         if (((i + j + k) & 1) != color) continue;
-        T v[6];
         int nwall;
-        const int m = gather_nb(e, L, i, j, k, t, v, nwall);
-        T sum = 0;
-        for (int q2 = 0; q2 < m; ++q2) sum += v[q2];
+        const T sum = sum_nb(e, L, i, j, k, t, nwall);
         e[t] = (sum - rs[t] * h2) * lv_rc<T>(L, nwall);
       }
       __syncthreads();
     }
-  for (long long t = threadIdx.x; t < n; t += blockDim.x) E.p[comp][t] = e[t];
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) E.at(comp)[t] = e[t];
 }
 
 // Per-block partial sums of ||b - L x||^2 and ||b||^2 (FP64 accumulation).
@@ -263,7 +259,7 @@ template <class T, bool EXACT>
 __global__ void k_resid_norm(Level L, Comp3<T> X, Rhs3<T> R, double* partials, float ih_hi,
                              float ih_lo) {
   const int comp = blockIdx.y;
-  const T* __restrict__ x = X.p[comp];
+  const T* __restrict__ x = X.at(comp);
   const int rows = L.n[1] * L.n[2];
   double rr = 0.0, bb = 0.0;
   for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -329,13 +325,13 @@ __device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
 }
 
 // Residual of the 8 children, averaged onto the coarse cell (plain
-// arithmetic, neighbour order x-, x+, y-, y+, z-, z+ as gather_nb).  The
+// arithmetic, neighbour order x-, x+, y-, y+, z-, z+ as for_nb).  The
 // children of coarse x index I are fine 2I, 2I+1 (an aligned pair).
 template <class T>
 __global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<T> RC) {
   int I, J, K, comp;
   if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
-  const T* __restrict__ x = X.p[comp];
+  const T* __restrict__ x = X.at(comp);
   const int nx = F.n[0], ny = F.n[1], nz = F.n[2];
   const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
   const int xm = outer_idx(i0 - 1, nx, F.per[0]), xp = outer_idx(i0 + 2, nx, F.per[0]);
@@ -352,8 +348,8 @@ __global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<
       fxm[kz][jy] = xm >= 0 ? r[xm] : (T)0;
       fxp[kz][jy] = xp >= 0 ? r[xp] : (T)0;
       const long long t = ((long long)(k0 + kz) * ny + j0 + jy) * nx + i0;
-      ld2(R.B[comp] + t, b[kz][jy][0], b[kz][jy][1]);
-      const T s = R.S[comp] ? R.S[comp][j0 + jy + (long long)(k0 + kz) * ny] : (T)0;
+      ld2(R.b_at(comp) + t, b[kz][jy][0], b[kz][jy][1]);
+      const T s = R.s_at(comp) ? R.s_at(comp)[j0 + jy + (long long)(k0 + kz) * ny] : (T)0;
       b[kz][jy][0] = R.beta * b[kz][jy][0] + s;
       b[kz][jy][1] = R.beta * b[kz][jy][1] + s;
     }
@@ -386,7 +382,7 @@ __global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<
         const T s = v_xm + v_xp + v_ym + v_yp + v_zm + v_zp;
         acc += b[kz][jy][ix] - (s - ((T)6 + al * (T)nwall) * c[kz][jy][ix]) * ih2;
       }
-  RC.p[comp][lin(I, J, K, C.n[0], C.n[1])] = acc * (T)0.125;
+  RC.at(comp)[lin(I, J, K, C.n[0], C.n[1])] = acc * (T)0.125;
 }
 
 // x_fine += P e (trilinear, weights 3/4 and 1/4 per axis) for the 8 children
@@ -457,8 +453,8 @@ __global__ void k_prolong_block(Level F, Level C, Comp3<T> X, Comp3<T> E) {
   int I, J, K, comp;
   if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
   T v[2][2][2];
-  prolong_children<T>(C, E.p[comp], I, J, K, v);
-  T* __restrict__ x = X.p[comp];
+  prolong_children<T>(C, E.at(comp), I, J, K, v);
+  T* __restrict__ x = X.at(comp);
   const int nx = F.n[0], ny = F.n[1];
 #pragma unroll
   for (int c = 0; c < 2; ++c)
@@ -494,11 +490,8 @@ __device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2) {
         const int i = t % nx, q = t / nx;
         const int j = q % ny, k = q / ny;
         if (((i + j + k) & 1) != color) continue;
-        T v[6];
         int nwall;
-        const int m = gather_nb(e, L, i, j, k, t, v, nwall);
-        T sum = 0;
-        for (int q2 = 0; q2 < m; ++q2) sum += v[q2];
+        const T sum = sum_nb(e, L, i, j, k, t, nwall);
         e[t] = (sum - r[t] * h2) * lv_rc<T>(L, nwall);
       }
       __syncthreads();
@@ -576,7 +569,7 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseCycle CC, Comp3<T>
   }
   const int n0 = (int)CC.lv[f].cells();
   for (int t = threadIdx.x; t < n0; t += blockDim.x) {
-    r[f][t] = RR.p[comp][t];
+    r[f][t] = RR.at(comp)[t];
     e[f][t] = (T)0;
   }
   __syncthreads();
@@ -592,7 +585,7 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseCycle CC, Comp3<T>
     cv_prolong<T>(CC.lv[l], CC.lv[l + 1], e[l], e[l + 1]);
     cv_sweep<T>(CC.lv[l], e[l], r[l], CC.nu2, (T)CC.h2[l]);
   }
-  for (int t = threadIdx.x; t < n0; t += blockDim.x) E.p[comp][t] = e[f][t];
+  for (int t = threadIdx.x; t < n0; t += blockDim.x) E.at(comp)[t] = e[f][t];
 }
 
 template <class T>
@@ -668,7 +661,7 @@ void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp) {
 
 template <class T>
 void launch_extrapolate(Ctx& cx, Comp3<T> X, Comp3<T> XP, long long n, int ncomp, int extrapolate) {
-  const long long b = std::min<long long>(blocks_for(n), 4 * 152);
+  const long long b = std::min<long long>(blocks_for(n), 4LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
   k_extrapolate<T><<<grid, kBlock, 0, cx.stream>>>(X, XP, n, extrapolate);

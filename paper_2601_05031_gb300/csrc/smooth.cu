@@ -16,8 +16,8 @@
 // from the staged plane in shared memory by 128-bit loads.  Warps 0 and 7
 // also do the red cells of the halo rows, 36 threads the two halo columns.
 // Planes are staged by cp.async (16-byte vectors, zero fill on Dirichlet
-// ghosts, wrap on periodic axes; two planes in flight) into a ring of five
-// x-planes and three rhs planes.
+// ghosts, wrap on periodic axes; two steps of copies in flight) into a ring
+// of six x-planes and five rhs planes.
 #include "tile.cuh"
 
 namespace vsv {
@@ -29,16 +29,22 @@ namespace {
 constexpr int kH = 2;                    // halo rows of x
 constexpr int kRA = kTY + 2 * kH;        // staged x rows
 constexpr int kRB = kTY + 2 * (kH - 1);  // staged rhs rows
-constexpr int kNA = 5;                   // x-plane ring slots
-constexpr int kNB = 3;                   // rhs-plane ring slots
+constexpr int kNA = 6;                   // x-plane ring slots
+constexpr int kNB = 5;                   // rhs-plane ring slots
 constexpr int kStageA = (kRA * kNV + kThreads - 1) / kThreads;   // vectors per thread
 constexpr int kStageB = (kRB * kNV + kThreads - 1) / kThreads;
 
 struct FusedGeom : Geom {
-  float rc[7];           // 1 / (6 + alpha * nwall), as in Level::rcf
+  float rc0, rc1, rc2;   // 1 / (6 + alpha * nwall) for nwall = 0, 1, 2 (Level::rcf)
   float h2;
   float beta;            // b = beta * B + S
 };
+
+// nwall is at most 2 on a tile-aligned level (ny >= 16 and nz >= 2 keep the
+// two walls of an axis apart, and x is periodic).
+__device__ __forceinline__ float rc_of(const FusedGeom& G, int nwall) {
+  return nwall == 0 ? G.rc0 : (nwall == 1 ? G.rc1 : G.rc2);
+}
 
 // Red (or black) update of one float4 group: the two cells at offsets par and
 // par + 2, given own V (centre row), U / D (rows above / below), M / P
@@ -64,11 +70,24 @@ __device__ __forceinline__ float4 rb_group(float4 V, float4 U, float4 D, float4 
   return V;
 }
 
+__device__ __forceinline__ float* ring(float* base, int plane, int slots, int slot_elems) {
+  return base + ((unsigned)(plane + slots) % (unsigned)slots) * slot_elems;   // plane >= -2
+}
+
 }  // namespace
 
 // One full red-black sweep A -> B for one component per blockIdx.z.
 // Grid: x = ntx * nty tiles, y = z chunks, z = components.  ZERO_IN: A is
 // taken as zero (first sweep of a correction from e = 0; A is not read).
+//
+// Pipeline: at step p the CTA issues the copies of x plane p + 3 and rhs
+// plane p + 2 and waits for those of step p - 2 (x plane p + 1, rhs plane
+// p), so two steps of copies are in flight.  One barrier per step suffices:
+// within a step the red phase writes only red cells of slot p and reads
+// black cells of slots p - 1 .. p + 1, and the black phase reads slot p - 1,
+// finished one step earlier, plus registers; the ring is deep enough (six x
+// and five rhs slots) that the copies a step issues never land in a slot a
+// warp still in the previous step may read.
 template <bool ZERO_IN, bool HAS_S>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
@@ -76,10 +95,10 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
   float* sA = reinterpret_cast<float*>(smem_f4);
   float* sB = sA + kNA * kRA * kW;
   const int comp = blockIdx.z;
-  const float* __restrict__ a = A.p[comp];
-  float* __restrict__ out = B.p[comp];
-  const float* __restrict__ bsrc = R.B[comp];
-  const float* __restrict__ S = R.S[comp];
+  const float* __restrict__ a = A.at(comp);
+  float* __restrict__ out = B.at(comp);
+  const float* __restrict__ bsrc = R.b_at(comp);
+  const float* __restrict__ S = R.s_at(comp);
   const int tx = blockIdx.x % G.ntx, tyb = blockIdx.x / G.ntx;
   const int x0 = tx * kTX, y0 = tyb * kTY;
   const int zb = blockIdx.y * G.zchunk;
@@ -88,8 +107,8 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
   const int tid = threadIdx.x, gx = tid & 31, ty = tid >> 5;
   const int q = gx + 1;                    // own float4 group (staged columns 4q .. 4q+3)
 
-  auto slotA = [&](int plane) { return sA + (((plane % kNA) + kNA) % kNA) * (kRA * kW); };
-  auto slotB = [&](int plane) { return sB + (((plane % kNB) + kNB) % kNB) * (kRB * kW); };
+  auto slotA = [&](int plane) { return ring(sA, plane, kNA, kRA * kW); };
+  auto slotB = [&](int plane) { return ring(sB, plane, kNB, kRB * kW); };
   auto ghost_plane = [&](int p) { return !G.per_z && (p < 0 || p >= G.nz); };
   auto zwall = [&](int p) { return G.per_z ? 0 : (p == 0) + (p == G.nz - 1); };
   auto srow = [&](int j, int p) -> float {
@@ -103,25 +122,34 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
   da.init(G, x0, y0, kH, kRA);
   db.init(G, x0, y0, kH - 1, kRB);
 
-  // own rows
-  int rown[2], jown[2], ywall[2];
+  // own rows and their 1 / diagonal for z-interior (0) and z-wall (1) planes
+  int rown[2], jown[2];
+  float rco[2][2];
+#pragma unroll
   for (int h = 0; h < 2; ++h) {
     rown[h] = ty + 8 * h + kH;
     jown[h] = y0 + ty + 8 * h;
-    ywall[h] = G.per_y ? 0 : (jown[h] == 0) + (jown[h] == G.ny - 1);
+    const int yw = G.per_y ? 0 : (jown[h] == 0) + (jown[h] == G.ny - 1);
+    rco[h][0] = rc_of(G, yw);
+    rco[h][1] = rc_of(G, yw + 1);
   }
 
-  // prologue: x planes zb-2 .. zb and rhs plane zb-1
+  // prologue: group 0 = x planes zb-2 .. zb, rhs plane zb-1 (step zb-1);
+  // group 1 = x plane zb+1, rhs plane zb (step zb)
   da.stage(slotA(zb - 2), a, G, zb - 2, ZERO_IN);
   da.stage(slotA(zb - 1), a, G, zb - 1, ZERO_IN);
   da.stage(slotA(zb), a, G, zb, ZERO_IN);
   db.stage(slotB(zb - 1), bsrc, G, zb - 1, false);
   cp_async_commit();
-  cp_async_wait0();
+  da.stage(slotA(zb + 1), a, G, zb + 1, ZERO_IN);
+  db.stage(slotB(zb), bsrc, G, zb, false);
+  cp_async_commit();
+  cp_async_wait1();
   __syncthreads();
   // register pipeline: MM = plane p-2, M = p-1, V = p, P = p+1 (own groups);
   // rotated at the top of every step
   float4 MM[2], M[2], V[2], P[2];
+#pragma unroll
   for (int h = 0; h < 2; ++h) {
     V[h] = lds4(slotA(zb - 2) + rown[h] * kW + 4 * q);
     P[h] = lds4(slotA(zb - 1) + rown[h] * kW + 4 * q);
@@ -130,15 +158,16 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
   }
 
   for (int p = zb - 1; p <= ze; ++p) {
-    if (p + 1 <= ze) {
-      da.stage(slotA(p + 2), a, G, p + 2, ZERO_IN);
-      db.stage(slotB(p + 1), bsrc, G, p + 1, false);
+    if (p + 2 <= ze) {
+      da.stage(slotA(p + 3), a, G, p + 3, ZERO_IN);
+      db.stage(slotB(p + 2), bsrc, G, p + 2, false);
     }
     cp_async_commit();
-    cp_async_wait1();
+    cp_async_wait2();
     __syncthreads();
     float* cA = slotA(p);
     const float* cB = slotB(p);
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       MM[h] = M[h];
       M[h] = V[h];
@@ -148,6 +177,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
     // ---- red cells of plane p: own groups, halo rows, halo columns
     if (!ghost_plane(p)) {
       const int zw = zwall(p);
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int r = rown[h], j = jown[h];
         const float* row = cA + r * kW;
@@ -156,7 +186,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
         const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
         const int par = (j + p) & 1;
         V[h] = rb_group(V[h], U, D, M[h], P[h], Lx, Rx, Bv, par, beta, srow(j, p), h2,
-                        G.rc[ywall[h] + zw]);
+                        zw ? rco[h][1] : rco[h][0]);
         float* dst = cA + r * kW + 4 * q;
         if (par == 0) { dst[0] = V[h].x; dst[2] = V[h].z; }
         else { dst[1] = V[h].y; dst[3] = V[h].w; }
@@ -174,7 +204,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
           const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
           const int par = (j + p) & 1;
           const float4 Vn = rb_group(Vh, U, D, Mh, Ph, Lx, Rx, Bv, par, beta, srow(j, p), h2,
-                                     G.rc[jw + zw]);
+                                     rc_of(G, jw + zw));
           float* dst = cA + r * kW + 4 * q;
           if (par == 0) { dst[0] = Vn.x; dst[2] = Vn.z; }
           else { dst[1] = Vn.y; dst[3] = Vn.w; }
@@ -192,17 +222,17 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
           const float s = cA[id - 1] + cA[id + 1] + cA[id - kW] + cA[id + kW] + slotA(p - 1)[id] +
                           slotA(p + 1)[id];
           const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
-          cA[id] = (s - bb * h2) * G.rc[jw + zw];
+          cA[id] = (s - bb * h2) * rc_of(G, jw + zw);
         }
       }
     }
-    __syncthreads();
     // ---- black cells of plane p-1 on the tile, stored straight from registers
     const int qp = p - 1;
     if (qp >= zb && qp < ze) {
       const int zw = zwall(qp);
       const float* cAq = slotA(qp);
       const float* cBq = slotB(qp);
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int r = rown[h], j = jown[h];
         const float* row = cAq + r * kW;
@@ -211,11 +241,10 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
         const float4 Bv = lds4(cBq + (r - 1) * kW + 4 * q);
         const int par = (j + qp + 1) & 1;
         M[h] = rb_group(M[h], U, D, MM[h], V[h], Lx, Rx, Bv, par, beta, srow(j, qp), h2,
-                        G.rc[ywall[h] + zw]);
+                        zw ? rco[h][1] : rco[h][0]);
         *reinterpret_cast<float4*>(out + ((long long)qp * G.ny + j) * G.nx + x0 + 4 * gx) = M[h];
       }
     }
-    __syncthreads();
   }
   cp_async_wait0();
 }
@@ -232,12 +261,14 @@ static void launch_variant(dim3 grid, size_t smem, cudaStream_t s, const FusedGe
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_rbgs_fused<Z, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_rbgs_fused<Z, HS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
   k_rbgs_fused<Z, HS><<<grid, kThreads, smem, s>>>(G, A, B, R);
 }
 
-// One fused full sweep A -> B on `ncomp` components (zero_in: A taken as 0).
+// One fused full sweep A -> B on `ncomp` components (zero_in: A taken as 0;
+// zchunk <= 0: chosen for whole waves of two CTAs per SM).
 void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
                        int ncomp, int zchunk, int kclass, bool zero_in) {
   const size_t smem = fused_sweep_smem();
@@ -245,8 +276,11 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   G.nx = L.n[0]; G.ny = L.n[1]; G.nz = L.n[2];
   G.per_y = L.per[1]; G.per_z = L.per[2];
   G.ntx = L.n[0] / kTX; G.nty = L.n[1] / kTY;
-  G.zchunk = zchunk > 0 ? std::min(zchunk, L.n[2]) : L.n[2];
-  for (int q = 0; q < 7; ++q) G.rc[q] = L.rcf[q];
+  if (zchunk <= 0) zchunk = pick_zchunk(L, ncomp, 2 * cx.sms, 2);
+  G.zchunk = std::min(zchunk, L.n[2]);
+  G.rc0 = L.rcf[0];
+  G.rc1 = L.rcf[1];
+  G.rc2 = L.rcf[2];
   G.h2 = (float)(1.0 / L.inv_h2);
   G.beta = R.beta;
   const int nzc = (L.n[2] + G.zchunk - 1) / G.zchunk;

@@ -16,6 +16,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::); }
 
 constexpr int kTX = 128;              // tile width (x)
 constexpr int kTY = 16;               // tile height (y)
@@ -33,28 +34,36 @@ struct Geom {
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Per-thread staging descriptors: shared offset, global row offset within a
-// plane (j * nx + x) and whether the row exists (else zero fill).
+// Per-thread staging descriptors for the (up to three) 16-byte vectors a
+// thread copies per plane: shared offset (-1: unused), global row offset
+// within a plane (j * nx + x), and whether the row exists (else zero fill).
+// Plain scalar members, so the descriptors stay in registers.
+struct StageVec {
+  int soff, goff;
+  bool ok;
+  __device__ __forceinline__ void init(const Geom& G, int t, int x0, int y0, int hr, int rows) {
+    const int r = t / kNV, v = t - r * kNV;
+    int j = y0 - hr + r;
+    ok = true;
+    if (G.per_y) j = wrapi(j, G.ny);
+    else if (j < 0 || j >= G.ny) ok = false;
+    const int x = wrapi(x0 - kHX + 4 * v, G.nx);
+    soff = t < rows * kNV ? r * kW + 4 * v : -1;
+    goff = ok ? j * G.nx + x : 0;
+  }
+  __device__ __forceinline__ void issue(float* slot, const float* base, bool pvalid) const {
+    if (soff >= 0) cp_async16(slot + soff, base + goff, pvalid && ok);
+  }
+};
+
 template <int NS>
 struct StageDesc {
-  int soff[NS];
-  int goff[NS];
-  bool ok[NS];
-  bool used[NS];
+  static_assert(NS >= 1 && NS <= 3, "at most three vectors per thread and plane");
+  StageVec v0, v1, v2;
   __device__ __forceinline__ void init(const Geom& G, int x0, int y0, int hr, int rows) {
-    for (int s = 0; s < NS; ++s) {
-      const int t = threadIdx.x + kThreads * s;
-      used[s] = t < rows * kNV;
-      const int r = t / kNV, v = t - r * kNV;
-      int j = y0 - hr + r;
-      bool okr = true;
-      if (G.per_y) j = wrapi(j, G.ny);
-      else if (j < 0 || j >= G.ny) okr = false;
-      const int x = wrapi(x0 - kHX + 4 * v, G.nx);
-      soff[s] = r * kW + 4 * v;
-      goff[s] = okr ? j * G.nx + x : 0;
-      ok[s] = okr;
-    }
+    v0.init(G, threadIdx.x, x0, y0, hr, rows);
+    v1.init(G, threadIdx.x + kThreads, x0, y0, hr, NS > 1 ? rows : 0);
+    v2.init(G, threadIdx.x + 2 * kThreads, x0, y0, hr, NS > 2 ? rows : 0);
   }
   __device__ __forceinline__ void stage(float* slot, const float* __restrict__ src, const Geom& G,
                                         int plane, bool zero) const {
@@ -63,8 +72,9 @@ struct StageDesc {
     if (G.per_z) k = wrapi(k, G.nz);
     else if (k < 0 || k >= G.nz) pvalid = false;
     const float* base = src + (pvalid ? (long long)k * G.ny * G.nx : 0LL);
-    for (int s = 0; s < NS; ++s)
-      if (used[s]) cp_async16(slot + soff[s], base + goff[s], pvalid && ok[s]);
+    v0.issue(slot, base, pvalid);
+    if (NS > 1) v1.issue(slot, base, pvalid);
+    if (NS > 2) v2.issue(slot, base, pvalid);
   }
 };
 
@@ -75,6 +85,30 @@ __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cas
 inline bool level_ok(const Level& L) {
   return L.act[0] && L.act[1] && L.act[2] && L.per[0] && L.n[0] % kTX == 0 &&
          L.n[1] % kTY == 0 && L.n[2] >= 2;
+}
+
+// z-chunk length for a tiled z-marching kernel on level L: the grid is
+// (tiles x chunks x ncomp) CTAs, `slots` of which are resident at a time, and
+// a chunk costs its planes plus about `halo` extra planes of pipeline fill.
+// Picks the chunk that minimises waves x (chunk + halo).
+inline int pick_zchunk(const Level& L, int ncomp, int slots, int halo) {
+  const int nz = L.n[2];
+  const long long tiles = (long long)(L.n[0] / kTX) * (L.n[1] / kTY) * ncomp;
+  if (slots < 1) slots = 1;
+  double best = 0.0;
+  int best_chunk = nz;
+  for (int nzc = 1; nzc <= nz; ++nzc) {
+    const int chunk = (nz + nzc - 1) / nzc;
+    if (chunk < 8 && nzc > 1) break;
+    const long long blocks = tiles * ((nz + chunk - 1) / chunk);
+    const long long waves = (blocks + slots - 1) / slots;
+    const double eff = (double)(tiles * nz) / ((double)waves * slots * (chunk + halo));
+    if (eff > best * (1.0 + 1e-9)) {
+      best = eff;
+      best_chunk = chunk;
+    }
+  }
+  return best_chunk;
 }
 
 inline Geom geom(const Level& L, int zchunk) {
