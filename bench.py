@@ -260,24 +260,24 @@ def run_gpu(args, ws, rank, local):
                                          "relative residual 1e-12", "rel_l2": errs}
         sim64.close()
     # end to end through the C ABI with host buffers: phi in from pinned host
-    # memory, one step, phi out to pinned host memory, every step
+    # memory, one step, phi out to pinned host memory, every step.  phi goes
+    # both ways in FP64, which carries the double-word state exactly.
     if not args.no_e2e:
-        host_in = torch.empty((w.nz, w.ny, w.nx), dtype=torch.float32, pin_memory=True)
+        host_in = torch.empty((w.nz, w.ny, w.nx), dtype=torch.float64, pin_memory=True)
         host_out = torch.empty_like(host_in)
-        sim.field(V.VSV_FIELD_PHI, np.float32, on_device=True)
-        host_in.copy_(sim.field(V.VSV_FIELD_PHI, np.float32, on_device=True).cpu())
+        host_in.copy_(sim.field(V.VSV_FIELD_PHI, np.float64, on_device=True).cpu())
         ke = max(2, min(args.steps, 5))
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
-            V.vsv_set_field(sim.g, V.VSV_FIELD_PHI, host_in.data_ptr(), V.VSV_DTYPE_F32, 0)
+            V.vsv_set_field(sim.g, V.VSV_FIELD_PHI, host_in.data_ptr(), V.VSV_DTYPE_F64, 0)
             sim.step(1, w.dt)
-            V.vsv_get_field(sim.g, V.VSV_FIELD_PHI, host_out.data_ptr(), V.VSV_DTYPE_F32, 0)
+            V.vsv_get_field(sim.g, V.VSV_FIELD_PHI, host_out.data_ptr(), V.VSV_DTYPE_F64, 0)
         te = time.perf_counter() - t0
-        barrier()
+        te = max_over_ranks(te * 1e3, dist, "cuda") * 1e-3
         out["e2e"] = {"value": round(ws * N * ke / te / 1e6, 3), "unit": UNIT,
-                      "h2d_bytes_per_step": N * 4, "d2h_bytes_per_step": N * 4, "steps": ke}
+                      "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8, "steps": ke}
     sim.close()
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)

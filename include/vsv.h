@@ -128,9 +128,10 @@ typedef struct {
  * nu1 / nu2: pre / post smoothing sweeps; max_levels: multigrid depth cap;
  * coarse_sweeps: red-black sweeps on the coarsest level; omega_sor <= 0
  * picks the optimal SOR weight for the grid.  variant 0 uses the fastest
- * kernels available for each level (fused single-pass red-black sweeps where
- * the tile shape allows); 1 forces the reference per-colour kernels (same
- * arithmetic, bit-identical results; for cross-checks).  extrapolate = 1
+ * kernels available for each level (fused single-pass red-black sweeps,
+ * tiled transfers and defects where the tile shape allows, the lower levels
+ * of a V-cycle in one launch); 1 forces the reference per-level, per-colour
+ * kernels (same arithmetic, bit-identical results; for cross-checks).  extrapolate = 1
  * starts each solve of a time step from 2 x^n - x^{n-1} (linear extrapolation
  * of the two previous solutions) instead of x^n, which shrinks the initial
  * error from O(dt) to O(dt^2); it changes the iterate, not the converged

@@ -304,27 +304,32 @@ Comp3<T> comp3(void* a, void* b, void* c) {
 // with the level's scratch) where it applies, else the per-colour kernels.
 // x_zero: X is known to be zero (a correction from e = 0): the first fused
 // sweep then does not read it, and the per-colour path zeroes it first.
+// uh / ul (FP32 storage only): a double-word iterate to which the result is
+// to be added; returns true if the last fused sweep did that (X then does not
+// hold the result), false if the caller still has to.
 template <class T>
-void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp, int nu,
-            bool x_zero) {
+bool smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp, int nu,
+            bool x_zero, const Comp3<float>* uh = nullptr, const Comp3<float>* ul = nullptr) {
   const double h2 = 1.0 / L.inv_h2;
   const int kc = (l == 0) ? VSV_KCLASS_SMOOTH_FINE : VSV_KCLASS_SMOOTH;
   if constexpr (std::is_same<T, float>::value) {
     if (g->sol.variant == 0 && fused_sweep_ok(L) && g->mg_t[l][0] && nu >= 2) {
       Comp3<float> Tt = comp3<float>(g->mg_t[l][0], g->mg_t[l][1], g->mg_t[l][2]);
       const int zchunk = 0;   // chosen by the launcher
-      int s = 0;
+      const bool fuse_upd = uh && ul && nu % 2 == 0;
       bool z = x_zero;
-      for (; s + 1 < nu; s += 2) {
+      for (int s = 0; s + 1 < nu; s += 2) {
+        const bool last = s + 2 == nu;
         launch_rbgs_fused(g->cx, L, X, Tt, R, ncomp, zchunk, kc, z);
-        launch_rbgs_fused(g->cx, L, Tt, X, R, ncomp, zchunk, kc, false);
+        launch_rbgs_fused(g->cx, L, Tt, X, R, ncomp, zchunk, kc, false,
+                          fuse_upd && last ? uh : nullptr, fuse_upd && last ? ul : nullptr);
         z = false;
       }
-      for (; s < nu; ++s) {
+      if (nu % 2) {
         launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
         launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
       }
-      return;
+      return fuse_upd;
     }
   }
   if (x_zero) launch_zero<T>(g->cx, X, L.cells(), ncomp);
@@ -332,11 +337,15 @@ void smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp
     launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
     launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
   }
+  return false;
 }
 
+// One V-cycle from level l for L x = R.  uh / ul as in smooth(): returns
+// true if the correction was added to that iterate by the last sweep.
 template <class T>
-void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T> R, int ncomp,
-            bool exact_fine = true, bool x_zero = false) {
+bool vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T> R, int ncomp,
+            bool exact_fine = true, bool x_zero = false, const Comp3<float>* uh = nullptr,
+            const Comp3<float>* ul = nullptr) {
   const Level& L = lv[l];
   const double h2 = 1.0 / L.inv_h2;
   const bool last = (l + 1 == (int)lv.size());
@@ -345,7 +354,7 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
     if (l > 0) {
       Comp3<T> E = X;
       Comp3<T> RR{{(T*)R.B[0], (T*)R.B[1], (T*)R.B[2]}};
-      if (launch_coarse_solve<T>(g->cx, L, E, RR, ncomp, g->sol.coarse_sweeps, h2)) return;
+      if (launch_coarse_solve<T>(g->cx, L, E, RR, ncomp, g->sol.coarse_sweeps, h2)) return false;
       launch_zero<T>(g->cx, E, L.cells(), ncomp);
     } else if (x_zero) {
       launch_zero<T>(g->cx, X, L.cells(), ncomp);
@@ -354,7 +363,7 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
       launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
       launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
     }
-    return;
+    return false;
   }
   if (l > 0 && x_zero && g->sol.variant == 0 && R.beta == (T)1 && !R.S[0] && !R.S[1] && !R.S[2]) {
     // the remaining levels fit in one CTA's shared memory: one launch
@@ -373,7 +382,7 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
     }
     CC.total = off;
     Comp3<T> RR{{(T*)R.B[0], (T*)R.B[1], (T*)R.B[2]}};
-    if (launch_coarse_vcycle<T>(g->cx, CC, X, RR, ncomp)) return;
+    if (launch_coarse_vcycle<T>(g->cx, CC, X, RR, ncomp)) return false;
   }
   smooth<T>(g, L, l, X, R, ncomp, g->sol.nu1, x_zero);
   const Level& C = lv[l + 1];
@@ -384,7 +393,7 @@ void vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
   Rhs3<T> RCr{{RC.p[0], RC.p[1], RC.p[2]}, {nullptr, nullptr, nullptr}, (T)1};
   vcycle<T>(g, lv, l + 1, EC, RCr, ncomp, exact_fine, true);
   launch_prolong_add<T>(g->cx, L, C, X, EC, ncomp);
-  smooth<T>(g, L, l, X, R, ncomp, g->sol.nu2, false);
+  return smooth<T>(g, L, l, X, R, ncomp, g->sol.nu2, false, uh, ul);
 }
 
 // relres = max over components of ||b - L x|| / ||b|| (||b|| = 0 -> ||r||).
@@ -476,8 +485,8 @@ vsv_status solve_dc(vsv_grid* g, const std::vector<Level>& lv, Comp3<float> XH, 
   Comp3<float> RR = comp3<float>(g->r0[0], g->r0[1], g->r0[2]);
   Rhs3<float> RE{{RR.p[0], RR.p[1], RR.p[2]}, {nullptr, nullptr, nullptr}, 1.f};
   auto correct = [&]() {
-    vcycle<float>(g, lv, 0, E, RE, ncomp, false, true);
-    launch_update_dw(g->cx, XH, XL, E, L.cells(), ncomp);
+    if (!vcycle<float>(g, lv, 0, E, RE, ncomp, false, true, &XH, &XL))
+      launch_update_dw(g->cx, XH, XL, E, L.cells(), ncomp);
   };
   // defect r = b - L x (tiled kernel where the level allows it); returns the
   // number of partial-sum blocks per component written when `norms`
@@ -1069,6 +1078,7 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
       sp->variant < 0 || sp->variant > 1 || sp->extrapolate < 0 || sp->extrapolate > 1)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
+  g->cx.tiled = sp->variant == 0;
   if (g->flow_set) {
     const int per[3] = {1, 0, z_periodic(g) ? 1 : 0};
     g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);

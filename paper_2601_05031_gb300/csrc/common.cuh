@@ -52,6 +52,23 @@ struct Comp3 {
   }
 };
 
+// Prolongation increment of one fine cell (cell-centred trilinear, weights
+// 3/4 and 1/4 per axis).  The arguments are the (x-centre, x-neighbour) pairs
+// of coarse values, already multiplied by their boundary factors, for the
+// (centre plane, centre row), (centre plane, neighbour row), (neighbour
+// plane, centre row) and (neighbour plane, neighbour row).  Every
+// prolongation kernel calls this, so they agree bit for bit.
+template <class T>
+__device__ __forceinline__ T prolong_value(T aC, T aX, T bC, T bX, T cC, T cX, T dC, T dX) {
+  const T w1 = (T)0.75, w2 = (T)0.25;
+  T acc = 0;
+  acc += w1 * w1 * (w1 * aC + w2 * aX);
+  acc += w1 * w2 * (w1 * bC + w2 * bX);
+  acc += w2 * w1 * (w1 * cC + w2 * cX);
+  acc += w2 * w2 * (w1 * dC + w2 * dX);
+  return acc;
+}
+
 // Right-hand side b = beta * B[c] + S[j + k * ny] (S may be null).
 template <class T>
 struct Rhs3 {

@@ -15,6 +15,7 @@ namespace vsv {
 struct Ctx {
   cudaStream_t stream = nullptr;
   int sms = 148;                 // multiprocessors of the grid's device (set at create)
+  int tiled = 1;                 // use the tiled transfer kernels (solver variant 0)
   long long launches = 0;
   int prof_class = -1;
   std::vector<cudaEvent_t> ev;   // pairs (start, stop)
@@ -132,10 +133,18 @@ void launch_extrapolate_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<floa
                            Comp3<float> PL, long long n, int ncomp, int extrapolate);
 void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncomp, Scalars* S);
 
+// tiled restriction / prolongation for tile-aligned levels halved on every
+// axis (transfer.cu); false: not applicable, nothing launched
+bool launch_restrict_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> X,
+                           Rhs3<float> R, Comp3<float> RC, int ncomp);
+bool launch_prolong_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> X, Comp3<float> E,
+                          int ncomp);
+
 // fused single-pass red-black sweep (smooth.cu)
 bool fused_sweep_ok(const Level& L);
 void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
-                       int ncomp, int zchunk, int kclass, bool zero_in);
+                       int ncomp, int zchunk, int kclass, bool zero_in,
+                       const Comp3<float>* upd_hi = nullptr, const Comp3<float>* upd_lo = nullptr);
 
 // ---------------------------------------------------------------- phase-field (phase.cu)
 struct PhaseParams {

@@ -34,13 +34,34 @@ __device__ __forceinline__ void for_nb(const T* __restrict__ x, const Level& L, 
   }
 }
 
-// Sum of the neighbour values, accumulated from zero in the order of for_nb.
+// Sum of the neighbour values as ((x- + x+) + (y- + y+)) + (z- + z+), a
+// Dirichlet ghost or an inactive axis contributing zero.  Every sweep,
+// residual and transfer kernel sums in this order, so they agree bit for bit.
 template <class T>
 __device__ __forceinline__ T sum_nb(const T* __restrict__ x, const Level& L, int i, int j, int k,
                                     long long c, int& nwall) {
-  T s = 0;
-  for_nb(x, L, i, j, k, c, nwall, [&](T v) { s += v; });
-  return s;
+  nwall = 0;
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  const long long sy = nx, sz = (long long)nx * ny;
+  T a = 0, b = 0, s[3];
+  if (L.act[0]) {
+    if (i > 0) a = x[c - 1]; else if (L.per[0]) a = x[c + nx - 1]; else ++nwall;
+    if (i < nx - 1) b = x[c + 1]; else if (L.per[0]) b = x[c - (nx - 1)]; else ++nwall;
+  }
+  s[0] = a + b;
+  a = 0; b = 0;
+  if (L.act[1]) {
+    if (j > 0) a = x[c - sy]; else if (L.per[1]) a = x[c + (ny - 1) * sy]; else ++nwall;
+    if (j < ny - 1) b = x[c + sy]; else if (L.per[1]) b = x[c - (ny - 1) * sy]; else ++nwall;
+  }
+  s[1] = a + b;
+  a = 0; b = 0;
+  if (L.act[2]) {
+    if (k > 0) a = x[c - sz]; else if (L.per[2]) a = x[c + (nz - 1) * sz]; else ++nwall;
+    if (k < nz - 1) b = x[c + sz]; else if (L.per[2]) b = x[c - (nz - 1) * sz]; else ++nwall;
+  }
+  s[2] = a + b;
+  return (s[0] + s[1]) + s[2];
 }
 
 template <class T>
@@ -325,7 +346,7 @@ __device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
 }
 
 // Residual of the 8 children, averaged onto the coarse cell (plain
-// arithmetic, neighbour order x-, x+, y-, y+, z-, z+ as for_nb).  The
+// arithmetic, neighbours summed pairwise as in sum_nb).  The
 // children of coarse x index I are fine 2I, 2I+1 (an aligned pair).
 template <class T>
 __global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<T> RC) {
@@ -379,16 +400,12 @@ __global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<
         const T v_zp = kz == 1 ? fzp[jy][ix] : c[1][jy][ix];
         const int nwall = (ix == 0 && xm < 0) + (ix == 1 && xp < 0) + (jy == 0 && ym < 0) +
                           (jy == 1 && yp < 0) + (kz == 0 && zm < 0) + (kz == 1 && zp < 0);
-        const T s = v_xm + v_xp + v_ym + v_yp + v_zm + v_zp;
+        const T s = ((v_xm + v_xp) + (v_ym + v_yp)) + (v_zm + v_zp);
         acc += b[kz][jy][ix] - (s - ((T)6 + al * (T)nwall) * c[kz][jy][ix]) * ih2;
       }
   RC.at(comp)[lin(I, J, K, C.n[0], C.n[1])] = acc * (T)0.125;
 }
 
-// x_fine += P e (trilinear, weights 3/4 and 1/4 per axis) for the 8 children
-// of one coarse cell; the coarse neighbours come from the coarse level's
-// boundary rule: periodic wrap, or -alpha * (adjacent cell) per
-// out-of-range axis (the linear extrapolation through zero at the wall).
 // Increments P e for the 8 children of coarse cell (I,J,K): weights 3/4 and
 // 1/4 per axis; the coarse neighbours come from the coarse level's boundary
 // rule: periodic wrap, or -alpha * (adjacent cell) per out-of-range axis (the
@@ -423,7 +440,6 @@ __device__ __forceinline__ void prolong_children(const Level& C, const T* __rest
 #pragma unroll
       for (int a = 0; a < 3; ++a) n[c][b][a] = f * fx[a] * r[ix[a]];
     }
-  const T w1 = (T)0.75, w2 = (T)0.25;
 #pragma unroll
   for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -431,19 +447,8 @@ __device__ __forceinline__ void prolong_children(const Level& C, const T* __rest
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const int ax = 2 * a, by = 2 * b, cz2 = 2 * c;
-        T acc = 0;
-#pragma unroll
-        for (int zz = 0; zz < 2; ++zz) {
-          const int kk = zz ? cz2 : 1;
-          const T wz = zz ? w2 : w1;
-#pragma unroll
-          for (int yy = 0; yy < 2; ++yy) {
-            const int jj = yy ? by : 1;
-            const T wy = yy ? w2 : w1;
-            acc += wz * wy * (w1 * n[kk][jj][1] + w2 * n[kk][jj][ax]);
-          }
-        }
-        v[c][b][a] = acc;
+        v[c][b][a] = prolong_value<T>(n[1][1][1], n[1][1][ax], n[1][by][1], n[1][by][ax],
+                                      n[cz2][1][1], n[cz2][1][ax], n[cz2][by][1], n[cz2][by][ax]);
       }
 }
 
@@ -618,6 +623,9 @@ template <class T>
 void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Rhs3<T> R,
                            Comp3<T> RC, int ncomp, bool exact) {
   const dim3 grid = grid3(C.n[0], C.n[1], C.n[2], ncomp);
+  if constexpr (std::is_same<T, float>::value) {
+    if (!exact && cx.tiled && launch_restrict_tiled(cx, F, C, X, R, RC, ncomp)) return;
+  }
   if (!exact && blocked_transfer_ok(F, C)) {
     cx.before(VSV_KCLASS_RESTRICT);
     k_restrict_block<T><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC);
@@ -639,6 +647,9 @@ void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, 
 
 template <class T>
 void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Comp3<T> E, int ncomp) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (cx.tiled && launch_prolong_tiled(cx, F, C, X, E, ncomp)) return;
+  }
   if (blocked_transfer_ok(F, C)) {
     cx.before(VSV_KCLASS_PROLONG);
     k_prolong_block<T><<<grid3(C.n[0], C.n[1], C.n[2], ncomp), block3(), 0, cx.stream>>>(F, C, X, E);

@@ -49,21 +49,21 @@ __device__ __forceinline__ float rc_of(const FusedGeom& G, int nwall) {
 // Red (or black) update of one float4 group: the two cells at offsets par and
 // par + 2, given own V (centre row), U / D (rows above / below), M / P
 // (planes below / above), the scalar neighbours Lx / Rx and the rhs group
-// Bv.  Returns V with those two components replaced.  Summation order x-, x+,
-// y-, y+, z-, z+ as in the per-colour kernel.
+// Bv.  Returns V with those two components replaced.  Neighbours summed as
+// ((x- + x+) + (y- + y+)) + (z- + z+), as in the per-colour kernel.
 __device__ __forceinline__ float4 rb_group(float4 V, float4 U, float4 D, float4 M, float4 P, float Lx,
                                            float Rx, float4 Bv, int par, float beta, float S,
                                            float h2, float rc) {
   if (par == 0) {
     const float b0 = beta * Bv.x + S, b2 = beta * Bv.z + S;
-    const float s0 = Lx + V.y + U.x + D.x + M.x + P.x;
-    const float s2 = V.y + V.w + U.z + D.z + M.z + P.z;
+    const float s0 = ((Lx + V.y) + (U.x + D.x)) + (M.x + P.x);
+    const float s2 = ((V.y + V.w) + (U.z + D.z)) + (M.z + P.z);
     V.x = (s0 - b0 * h2) * rc;
     V.z = (s2 - b2 * h2) * rc;
   } else {
     const float b1 = beta * Bv.y + S, b3 = beta * Bv.w + S;
-    const float s1 = V.x + V.z + U.y + D.y + M.y + P.y;
-    const float s3 = V.z + Rx + U.w + D.w + M.w + P.w;
+    const float s1 = ((V.x + V.z) + (U.y + D.y)) + (M.y + P.y);
+    const float s3 = ((V.z + Rx) + (U.w + D.w)) + (M.w + P.w);
     V.y = (s1 - b1 * h2) * rc;
     V.w = (s3 - b3 * h2) * rc;
   }
@@ -79,6 +79,9 @@ __device__ __forceinline__ float* ring(float* base, int plane, int slots, int sl
 // One full red-black sweep A -> B for one component per blockIdx.z.
 // Grid: x = ntx * nty tiles, y = z chunks, z = components.  ZERO_IN: A is
 // taken as zero (first sweep of a correction from e = 0; A is not read).
+// UPD: the swept values are not stored to B but added to the double-word
+// iterate, (XH, XL) <- (XH, XL) + e, with the arithmetic of k_update_dw (the
+// last sweep of a correction's V-cycle; e itself is not needed afterwards).
 //
 // Pipeline: at step p the CTA issues the copies of x plane p + 3 and rhs
 // plane p + 2 and waits for those of step p - 2 (x plane p + 1, rhs plane
@@ -88,15 +91,18 @@ __device__ __forceinline__ float* ring(float* base, int plane, int slots, int sl
 // finished one step earlier, plus registers; the ring is deep enough (six x
 // and five rhs slots) that the copies a step issues never land in a slot a
 // warp still in the previous step may read.
-template <bool ZERO_IN, bool HAS_S>
+template <bool ZERO_IN, bool HAS_S, bool UPD>
 __global__ void __launch_bounds__(kThreads, 2)
-k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
+k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<float> XH,
+             Comp3<float> XL) {
   extern __shared__ float4 smem_f4[];
   float* sA = reinterpret_cast<float*>(smem_f4);
   float* sB = sA + kNA * kRA * kW;
   const int comp = blockIdx.z;
   const float* __restrict__ a = A.at(comp);
   float* __restrict__ out = B.at(comp);
+  float* __restrict__ uh = XH.at(comp);
+  float* __restrict__ ul = XL.at(comp);
   const float* __restrict__ bsrc = R.b_at(comp);
   const float* __restrict__ S = R.s_at(comp);
   const int tx = blockIdx.x % G.ntx, tyb = blockIdx.x / G.ntx;
@@ -167,6 +173,19 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
     __syncthreads();
     float* cA = slotA(p);
     const float* cB = slotB(p);
+    const int qp = p - 1;
+    const bool black = qp >= zb && qp < ze;
+    float4 XHp[2], XLp[2];   // UPD: iterate of plane p-1, loaded ahead of its use
+    if constexpr (UPD) {
+      if (black) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
+          XHp[h] = *reinterpret_cast<const float4*>(uh + gi);
+          XLp[h] = *reinterpret_cast<const float4*>(ul + gi);
+        }
+      }
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       MM[h] = M[h];
@@ -177,17 +196,28 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
     // ---- red cells of plane p: own groups, halo rows, halo columns
     if (!ghost_plane(p)) {
       const int zw = zwall(p);
+      // both rows' operands first, then both updates, then the stores (the
+      // stores could alias the loads as far as the compiler knows); the two
+      // rows are 8 apart, so they share the parity
+      const int par = (jown[0] + p) & 1;
+      float4 U[2], D[2], Bv[2];
+      float Lx[2], Rx[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int r = rown[h], j = jown[h];
-        const float* row = cA + r * kW;
-        const float4 U = lds4(row - kW + 4 * q), D = lds4(row + kW + 4 * q);
-        const float Lx = row[4 * q - 1], Rx = row[4 * q + 4];
-        const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
-        const int par = (j + p) & 1;
-        V[h] = rb_group(V[h], U, D, M[h], P[h], Lx, Rx, Bv, par, beta, srow(j, p), h2,
-                        zw ? rco[h][1] : rco[h][0]);
-        float* dst = cA + r * kW + 4 * q;
+        const float* row = cA + rown[h] * kW;
+        U[h] = lds4(row - kW + 4 * q);
+        D[h] = lds4(row + kW + 4 * q);
+        Lx[h] = row[4 * q - 1];
+        Rx[h] = row[4 * q + 4];
+        Bv[h] = lds4(cB + (rown[h] - 1) * kW + 4 * q);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        V[h] = rb_group(V[h], U[h], D[h], M[h], P[h], Lx[h], Rx[h], Bv[h], par, beta,
+                        srow(jown[h], p), h2, zw ? rco[h][1] : rco[h][0]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float* dst = cA + rown[h] * kW + 4 * q;
         if (par == 0) { dst[0] = V[h].x; dst[2] = V[h].z; }
         else { dst[1] = V[h].y; dst[3] = V[h].w; }
       }
@@ -219,30 +249,45 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
         if ((G.per_y || (j >= 0 && j < G.ny)) && (((x + j + p) & 1) == 0)) {
           const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
           const int id = r * kW + c;
-          const float s = cA[id - 1] + cA[id + 1] + cA[id - kW] + cA[id + kW] + slotA(p - 1)[id] +
-                          slotA(p + 1)[id];
+          const float s = ((cA[id - 1] + cA[id + 1]) + (cA[id - kW] + cA[id + kW])) +
+                          (slotA(p - 1)[id] + slotA(p + 1)[id]);
           const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
           cA[id] = (s - bb * h2) * rc_of(G, jw + zw);
         }
       }
     }
     // ---- black cells of plane p-1 on the tile, stored straight from registers
-    const int qp = p - 1;
-    if (qp >= zb && qp < ze) {
+    if (black) {
       const int zw = zwall(qp);
       const float* cAq = slotA(qp);
       const float* cBq = slotB(qp);
+      const int par = (jown[0] + qp + 1) & 1;
+      float4 U[2], D[2], Bv[2];
+      float Lx[2], Rx[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int r = rown[h], j = jown[h];
-        const float* row = cAq + r * kW;
-        const float4 U = lds4(row - kW + 4 * q), D = lds4(row + kW + 4 * q);
-        const float Lx = row[4 * q - 1], Rx = row[4 * q + 4];
-        const float4 Bv = lds4(cBq + (r - 1) * kW + 4 * q);
-        const int par = (j + qp + 1) & 1;
-        M[h] = rb_group(M[h], U, D, MM[h], V[h], Lx, Rx, Bv, par, beta, srow(j, qp), h2,
-                        zw ? rco[h][1] : rco[h][0]);
-        *reinterpret_cast<float4*>(out + ((long long)qp * G.ny + j) * G.nx + x0 + 4 * gx) = M[h];
+        const float* row = cAq + rown[h] * kW;
+        U[h] = lds4(row - kW + 4 * q);
+        D[h] = lds4(row + kW + 4 * q);
+        Lx[h] = row[4 * q - 1];
+        Rx[h] = row[4 * q + 4];
+        Bv[h] = lds4(cBq + (rown[h] - 1) * kW + 4 * q);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        M[h] = rb_group(M[h], U[h], D[h], MM[h], V[h], Lx[h], Rx[h], Bv[h], par, beta,
+                        srow(jown[h], qp), h2, zw ? rco[h][1] : rco[h][0]);
+        const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
+        if constexpr (UPD) {
+          const FF v0 = ff_add_f(FF{XHp[h].x, XLp[h].x}, M[h].x);
+          const FF v1 = ff_add_f(FF{XHp[h].y, XLp[h].y}, M[h].y);
+          const FF v2 = ff_add_f(FF{XHp[h].z, XLp[h].z}, M[h].z);
+          const FF v3 = ff_add_f(FF{XHp[h].w, XLp[h].w}, M[h].w);
+          *reinterpret_cast<float4*>(uh + gi) = make_float4(v0.hi, v1.hi, v2.hi, v3.hi);
+          *reinterpret_cast<float4*>(ul + gi) = make_float4(v0.lo, v1.lo, v2.lo, v3.lo);
+        } else {
+          *reinterpret_cast<float4*>(out + gi) = M[h];
+        }
       }
     }
   }
@@ -255,22 +300,27 @@ bool fused_sweep_ok(const Level& L) { return level_ok(L); }
 
 size_t fused_sweep_smem() { return (size_t)(kNA * kRA + kNB * kRB) * kW * sizeof(float); }
 
-template <bool Z, bool HS>
+template <bool Z, bool HS, bool U>
 static void launch_variant(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G,
-                           Comp3<float> A, Comp3<float> B, Rhs3<float> R) {
+                           Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<float> XH,
+                           Comp3<float> XL) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_rbgs_fused<Z, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_rbgs_fused<Z, HS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_rbgs_fused<Z, HS, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_rbgs_fused<Z, HS, U>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
-  k_rbgs_fused<Z, HS><<<grid, kThreads, smem, s>>>(G, A, B, R);
+  k_rbgs_fused<Z, HS, U><<<grid, kThreads, smem, s>>>(G, A, B, R, XH, XL);
 }
 
 // One fused full sweep A -> B on `ncomp` components (zero_in: A taken as 0;
-// zchunk <= 0: chosen for whole waves of two CTAs per SM).
+// zchunk <= 0: chosen for whole waves of two CTAs per SM).  With upd_hi /
+// upd_lo given (and zero_in false) the result is added to that double-word
+// iterate instead of being stored to B.
 void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
-                       int ncomp, int zchunk, int kclass, bool zero_in) {
+                       int ncomp, int zchunk, int kclass, bool zero_in, const Comp3<float>* upd_hi,
+                       const Comp3<float>* upd_lo) {
   const size_t smem = fused_sweep_smem();
   FusedGeom G;
   G.nx = L.n[0]; G.ny = L.n[1]; G.nz = L.n[2];
@@ -286,13 +336,19 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   const int nzc = (L.n[2] + G.zchunk - 1) / G.zchunk;
   dim3 grid(G.ntx * G.nty, nzc, ncomp);
   const bool hs = R.S[0] != nullptr;
+  const bool upd = upd_hi && upd_lo && !zero_in;
+  const Comp3<float> XH = upd ? *upd_hi : Comp3<float>{{nullptr, nullptr, nullptr}};
+  const Comp3<float> XL = upd ? *upd_lo : Comp3<float>{{nullptr, nullptr, nullptr}};
   cx.before(kclass);
-  if (zero_in) {
-    if (hs) launch_variant<true, true>(grid, smem, cx.stream, G, A, B, R);
-    else launch_variant<true, false>(grid, smem, cx.stream, G, A, B, R);
+  if (upd) {
+    if (hs) launch_variant<false, true, true>(grid, smem, cx.stream, G, A, B, R, XH, XL);
+    else launch_variant<false, false, true>(grid, smem, cx.stream, G, A, B, R, XH, XL);
+  } else if (zero_in) {
+    if (hs) launch_variant<true, true, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
+    else launch_variant<true, false, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
   } else {
-    if (hs) launch_variant<false, true>(grid, smem, cx.stream, G, A, B, R);
-    else launch_variant<false, false>(grid, smem, cx.stream, G, A, B, R);
+    if (hs) launch_variant<false, true, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
+    else launch_variant<false, false, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
   }
   cx.after(kclass);
 }
