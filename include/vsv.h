@@ -282,7 +282,13 @@ const char* vsv_last_error(const vsv_grid* g);
 /* Kernel accounting.  vsv_kernel_launches: kernels this handle has launched.
  * Profiling brackets every launch of one kernel class with CUDA events on the
  * grid's stream; vsv_profile_read synchronises and returns the summed device
- * time and launch count since the last vsv_profile_enable. */
+ * time and launch count since the last vsv_profile_enable, and (alg_bytes not
+ * NULL) the summed algorithmic memory traffic of those launches: the bytes
+ * each kernel must read and write at least (fused sweep: 12 per cell and
+ * component, 8 when the input is known to be zero, 24 when it also updates
+ * the double-word iterate; tiled defect 16 or 20, tiled restriction and
+ * prolongation 8.5 per fine cell).  Launches of kernels without a tally add
+ * 0.  Fails with VSV_ESTATE if that class is not being profiled. */
 typedef enum {
   VSV_KCLASS_SMOOTH = 0,        /* red-black Gauss-Seidel sweeps, all levels   */
   VSV_KCLASS_SMOOTH_FINE = 1,   /* red-black sweeps on the finest level only   */
@@ -293,7 +299,8 @@ typedef enum {
 } vsv_kernel_class;
 int64_t vsv_kernel_launches(const vsv_grid* g);
 vsv_status vsv_profile_enable(vsv_grid* g, int kernel_class, int enable);
-vsv_status vsv_profile_read(vsv_grid* g, int kernel_class, double* total_ms, int64_t* launches);
+vsv_status vsv_profile_read(vsv_grid* g, int kernel_class, double* total_ms, int64_t* launches,
+                            double* alg_bytes);
 
 #ifdef __cplusplus
 }

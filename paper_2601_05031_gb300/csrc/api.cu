@@ -1469,10 +1469,12 @@ vsv_status vsv_profile_enable(vsv_grid* g, int kclass, int enable) {
   g->cx.prof_class = enable ? kclass : -1;
   g->cx.ev_used = 0;
   g->cx.prof_launches = 0;
+  g->cx.prof_bytes = 0.0;
   return VSV_OK;
 }
 
-vsv_status vsv_profile_read(vsv_grid* g, int kclass, double* total_ms, int64_t* launches) {
+vsv_status vsv_profile_read(vsv_grid* g, int kclass, double* total_ms, int64_t* launches,
+                            double* alg_bytes) {
   if (!g || !total_ms || !launches) return VSV_EINVAL;
   if (g->cx.prof_class != kclass) return fail(g, VSV_ESTATE, "profiling not enabled for this class%s");
   CK(cudaStreamSynchronize(g->cx.stream));
@@ -1484,6 +1486,7 @@ vsv_status vsv_profile_read(vsv_grid* g, int kclass, double* total_ms, int64_t* 
   }
   *total_ms = t;
   *launches = g->cx.prof_launches;
+  if (alg_bytes) *alg_bytes = g->cx.prof_bytes;
   return VSV_OK;
 }
 

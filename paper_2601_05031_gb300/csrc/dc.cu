@@ -341,7 +341,8 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
   dim3 grid(tiles, nz, ncomp);
   cx.before(VSV_KCLASS_RESTRICT);
   k_defect_tiled<<<grid, tile::kThreads, smem, cx.stream>>>(G, XH, XL, R, BL, OUT, partials);
-  cx.after(VSV_KCLASS_RESTRICT);
+  // x_hi, x_lo, b_hi (, b_lo) read, r written
+  cx.after(VSV_KCLASS_RESTRICT, (BL.p[0] ? 20.0 : 16.0) * (double)L.cells() * ncomp);
   return tiles * nz;
 }
 

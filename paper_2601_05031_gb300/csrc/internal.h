@@ -21,6 +21,7 @@ struct Ctx {
   std::vector<cudaEvent_t> ev;   // pairs (start, stop)
   int ev_used = 0;               // pairs recorded since enable
   long long prof_launches = 0;
+  double prof_bytes = 0.0;
   int pending = 0;
 
   bool match(int kclass) const {
@@ -36,11 +37,13 @@ struct Ctx {
       pending = 1;
     }
   }
-  void after(int kclass) {
+  // bytes: the launch's algorithmic memory traffic (0 where not tallied)
+  void after(int kclass, double bytes = 0.0) {
     if (pending) {
       cudaEventRecord(ev[2 * ev_used + 1], stream);
       ++ev_used;
       ++prof_launches;
+      prof_bytes += bytes;
       pending = 0;
     }
   }

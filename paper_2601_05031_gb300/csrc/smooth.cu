@@ -339,6 +339,9 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   const bool upd = upd_hi && upd_lo && !zero_in;
   const Comp3<float> XH = upd ? *upd_hi : Comp3<float>{{nullptr, nullptr, nullptr}};
   const Comp3<float> XL = upd ? *upd_lo : Comp3<float>{{nullptr, nullptr, nullptr}};
+  // algorithmic bytes per cell: rhs and result (+ x unless zero_in, + the
+  // iterate's two words read and written when updating)
+  const double bpc = zero_in ? 8.0 : (upd ? 24.0 : 12.0);
   cx.before(kclass);
   if (upd) {
     if (hs) launch_variant<false, true, true>(grid, smem, cx.stream, G, A, B, R, XH, XL);
@@ -350,7 +353,7 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
     if (hs) launch_variant<false, true, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
     else launch_variant<false, false, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
   }
-  cx.after(kclass);
+  cx.after(kclass, bpc * (double)L.cells() * ncomp);
 }
 
 }  // namespace vsv

@@ -307,7 +307,7 @@ bool launch_restrict_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float>
   cx.before(VSV_KCLASS_RESTRICT);
   if (R.S[0]) k_restrict_tiled<true><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
   else k_restrict_tiled<false><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
-  cx.after(VSV_KCLASS_RESTRICT);
+  cx.after(VSV_KCLASS_RESTRICT, 8.5 * (double)F.cells() * ncomp);   // e, b read; r_c written
   return true;
 }
 
@@ -324,7 +324,7 @@ bool launch_prolong_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> 
   dim3 grid(G.ntx * G.nty, (F.n[2] + G.zchunk - 1) / G.zchunk, ncomp);
   cx.before(VSV_KCLASS_PROLONG);
   k_prolong_tiled<<<grid, kThreads, 0, cx.stream>>>(G, X, E);
-  cx.after(VSV_KCLASS_PROLONG);
+  cx.after(VSV_KCLASS_PROLONG, 8.5 * (double)F.cells() * ncomp);   // e read and written, e_c read
   return true;
 }
 

@@ -118,7 +118,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_last_error": (C.c_char_p, [vp]),
         "vsv_kernel_launches": (i64, [vp]),
         "vsv_profile_enable": (i32, [vp, i32, i32]),
-        "vsv_profile_read": (i32, [vp, i32, C.POINTER(dbl), C.POINTER(i64)]),
+        "vsv_profile_read": (i32, [vp, i32, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -278,7 +278,9 @@ def vsv_profile_enable(g, kclass, enable=True):
     return _check(g, lib().vsv_profile_enable(g, kclass, int(enable)), "vsv_profile_enable")
 
 
-def vsv_profile_read(g, kclass):
-    ms, n = C.c_double(), C.c_int64()
-    _check(g, lib().vsv_profile_read(g, kclass, C.byref(ms), C.byref(n)), "vsv_profile_read")
-    return ms.value, n.value
+def vsv_profile_read(g, kclass, with_bytes=False):
+    """(total_ms, launches), or (total_ms, launches, algorithmic_bytes)."""
+    ms, n, b = C.c_double(), C.c_int64(), C.c_double()
+    _check(g, lib().vsv_profile_read(g, kclass, C.byref(ms), C.byref(n), C.byref(b)),
+           "vsv_profile_read")
+    return (ms.value, n.value, b.value) if with_bytes else (ms.value, n.value)

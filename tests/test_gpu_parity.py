@@ -307,6 +307,23 @@ def test_kernel_launch_accounting(V):
     sim.close()
 
 
+def test_profile_byte_tally(V):
+    """On a tile-aligned grid every finest-level sweep of a correction's
+    V(2,2)-cycle is a fused launch: zero-input (8 B/cell), plain (12), plain,
+    and the one that updates the double-word iterate (24), for 3 components;
+    a step runs the vorticity and the stream-vector solve."""
+    nx, ny, nz, cycles = 256, 32, 32, 2
+    w = inputs.vesicle_couette_512x256x256(nx=nx, ny=ny, nz=nz, nsteps=1)
+    sim = make_sim(V, w, V.VSV_MIXED, fixed=cycles)
+    sim.set_phi(w.phi0)
+    V.vsv_profile_enable(sim.g, V.VSV_KCLASS_SMOOTH_FINE)
+    sim.step(1, w.dt)
+    ms, n, nbytes = V.vsv_profile_read(sim.g, V.VSV_KCLASS_SMOOTH_FINE, with_bytes=True)
+    sim.close()
+    assert n == 2 * cycles * 4
+    assert nbytes == 2 * cycles * (8 + 12 + 12 + 24) * nx * ny * nz * 3
+
+
 # ------------------------------------------------------------ fused sweep
 @pytest.mark.parametrize("bc", [(True, False, True), (True, False, False)])
 def test_fused_sweep_bit_identical_to_reference(V, bc):
