@@ -258,14 +258,16 @@ __global__ void k_coarse_solve(Level L, Comp3<T> E, Comp3<T> RR, int sweeps, T h
     rs[t] = r[t];
   }
   __syncthreads();
-  const int nx = L.n[0], ny = L.n[1];
+  const int nx = L.n[0], ny = L.n[1], nxh = (nx + 1) >> 1;
+  const int nh = nxh * ny * L.n[2];   // cells of one colour, rounded up per row
   for (int s = 0; s < sweeps; ++s)
     for (int color = 0; color < 2; ++color) {
-      for (long long t = threadIdx.x; t < n; t += blockDim.x) {
-        const int i = (int)(t % nx);
-        const long long q = t / nx;
-        const int j = (int)(q % ny), k = (int)(q / ny);
-        if (((i + j + k) & 1) != color) continue;
+      for (int t2 = threadIdx.x; t2 < nh; t2 += blockDim.x) {
+        const int i2 = t2 % nxh, q = t2 / nxh;
+        const int j = q % ny, k = q / ny;
+        const int i = 2 * i2 + ((j + k + color) & 1);
+        if (i >= nx) continue;
+        const int t = (k * ny + j) * nx + i;
         int nwall;
         const T sum = sum_nb(e, L, i, j, k, t, nwall);
         e[t] = (sum - rs[t] * h2) * lv_rc<T>(L, nwall);
@@ -487,14 +489,16 @@ __host__ __device__ bool blocked_transfer_ok(const Level& F, const Level& C) {
 // replaces dozens of latency-bound launches per V-cycle by one.
 template <class T>
 __device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2) {
-  const int nx = L.n[0], ny = L.n[1];
-  const int n = (int)L.cells();
+  const int nx = L.n[0], ny = L.n[1], nxh = (nx + 1) >> 1;
+  const int nh = nxh * ny * L.n[2];   // cells of one colour, rounded up per row
   for (int s = 0; s < sweeps; ++s)
     for (int color = 0; color < 2; ++color) {
-      for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int i = t % nx, q = t / nx;
+      for (int t2 = threadIdx.x; t2 < nh; t2 += blockDim.x) {
+        const int i2 = t2 % nxh, q = t2 / nxh;
         const int j = q % ny, k = q / ny;
-        if (((i + j + k) & 1) != color) continue;
+        const int i = 2 * i2 + ((j + k + color) & 1);
+        if (i >= nx) continue;
+        const int t = (k * ny + j) * nx + i;
         int nwall;
         const T sum = sum_nb(e, L, i, j, k, t, nwall);
         e[t] = (sum - r[t] * h2) * lv_rc<T>(L, nwall);
