@@ -183,10 +183,12 @@ def run_gpu(args, ws, rank, local):
     for _ in range(args.warmup):
         sim.step(1, w.dt)
     torch.cuda.synchronize()
-    launches0 = sim.kernel_launches()
+    launches0, bytes0 = sim.kernel_launches(), sim.kernel_bytes()
     with ClockSampler(local) as clk:
-        ms = timed_steps(sim, args.steps, w.dt, torch, barrier)
+        ms_local = timed_steps(sim, args.steps, w.dt, torch, barrier)
     launches = sim.kernel_launches() - launches0
+    step_bytes = (sim.kernel_bytes() - bytes0) / args.steps
+    ms = ms_local
     ms = max_over_ranks(ms, dist, "cuda")
     value = job_throughput(ws, N, args.steps, ms)
     out = {
@@ -203,6 +205,20 @@ def run_gpu(args, ws, rank, local):
                    "dt": w.dt, "parallelism": f"replicas x{ws}"},
         "gpu_launches": int(launches),
     }
+    # whole-step HBM rate in the algorithmic sense: the bytes every kernel of
+    # a step must move (tallied by the library per launch) over the step time
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    step_gbs = step_bytes / (ms_local / args.steps * 1e-3) / 1e9
+    out["hbm_step"] = {"algorithmic_bytes_per_step": round(step_bytes),
+                       "bytes_per_cell_step": round(step_bytes / N, 1),
+                       "achieved_gbs": round(step_gbs, 1), "unit": "GB/s",
+                       "frac_of_measured": round(step_gbs / peak, 4),
+                       "frac_of_nominal_8tbs": round(step_gbs / 8000.0, 4)}
     # roofline of the dominant kernel: fine-level red-black half-sweeps, timed
     # live with events on the library's stream during extra timed steps
     V.vsv_profile_enable(sim.g, V.VSV_KCLASS_SMOOTH_FINE)
@@ -210,12 +226,6 @@ def run_gpu(args, ws, rank, local):
     timed_steps(sim, nprof, w.dt, torch, barrier)
     pms, pn, pbytes = V.vsv_profile_read(sim.g, V.VSV_KCLASS_SMOOTH_FINE, with_bytes=True)
     V.vsv_profile_enable(sim.g, V.VSV_KCLASS_SMOOTH_FINE, False)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
     per_launch_s = pms * 1e-3 / max(pn, 1)
     algo = pbytes / max(pn, 1)
     achieved = algo / per_launch_s / 1e9

@@ -298,6 +298,14 @@ typedef enum {
   VSV_KCLASS_COUNT = 5
 } vsv_kernel_class;
 int64_t vsv_kernel_launches(const vsv_grid* g);
+/* Algorithmic memory traffic, in bytes, of all kernels this handle has
+ * launched that carry a tally (every kernel of vsv_step and of the solves):
+ * for each launch, the bytes it must read and write at least (each input
+ * word read once, each output word written once; the per-kernel counts are
+ * listed with vsv_profile_read).  A host-side counter; no synchronisation.
+ * Divided by a measured time it gives the achieved HBM bandwidth of a step
+ * in the algorithmic sense.  0 for a NULL handle. */
+double vsv_kernel_bytes(const vsv_grid* g);
 vsv_status vsv_profile_enable(vsv_grid* g, int kernel_class, int enable);
 vsv_status vsv_profile_read(vsv_grid* g, int kernel_class, double* total_ms, int64_t* launches,
                             double* alg_bytes);

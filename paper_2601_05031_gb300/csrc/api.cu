@@ -1460,6 +1460,8 @@ const char* vsv_last_error(const vsv_grid* g) { return g ? g->err.c_str() : "nul
 
 int64_t vsv_kernel_launches(const vsv_grid* g) { return g ? g->cx.launches : 0; }
 
+double vsv_kernel_bytes(const vsv_grid* g) { return g ? g->cx.bytes_total : 0.0; }
+
 vsv_status vsv_profile_enable(vsv_grid* g, int kclass, int enable) {
   if (!g || kclass < 0 || kclass >= VSV_KCLASS_COUNT) return VSV_EINVAL;
   if (g->cx.ev.empty()) {

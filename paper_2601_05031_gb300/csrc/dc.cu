@@ -142,7 +142,7 @@ void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL,
   dim3 grid(nblocks, ncomp);
   cx.before(VSV_KCLASS_RESTRICT);
   k_defect_dw<<<grid, kBlock, 0, cx.stream>>>(L, XH, XL, R, BL, OUT, partials, ih_hi, ih_lo);
-  cx.after(VSV_KCLASS_RESTRICT);
+  cx.after(VSV_KCLASS_RESTRICT, (BL.p[0] ? 20.0 : 16.0) * (double)L.cells() * ncomp);
 }
 
 // ---------------------------------------------------------------- tiled defect
@@ -352,7 +352,7 @@ void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E,
   dim3 grid((unsigned)b, ncomp);
   cx.before(VSV_KCLASS_PROLONG);
   k_update_dw<<<grid, kBlock, 0, cx.stream>>>(XH, XL, E, n);
-  cx.after(VSV_KCLASS_PROLONG);
+  cx.after(VSV_KCLASS_PROLONG, 20.0 * (double)n * ncomp);   // x_hi, x_lo, e read; x_hi, x_lo written
 }
 
 void launch_extrapolate_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> PH,
@@ -361,7 +361,8 @@ void launch_extrapolate_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<floa
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
   k_extrapolate_dw<<<grid, kBlock, 0, cx.stream>>>(XH, XL, PH, PL, n, extrapolate);
-  cx.after(-1);
+  // x and the previous x (two words each) read, both written (only xp <- x without extrapolation)
+  cx.after(-1, (extrapolate ? 32.0 : 16.0) * (double)n * ncomp);
 }
 
 }  // namespace vsv

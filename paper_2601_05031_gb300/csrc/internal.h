@@ -22,6 +22,7 @@ struct Ctx {
   int ev_used = 0;               // pairs recorded since enable
   long long prof_launches = 0;
   double prof_bytes = 0.0;
+  double bytes_total = 0.0;      // algorithmic bytes of every tallied launch so far
   int pending = 0;
 
   bool match(int kclass) const {
@@ -39,6 +40,7 @@ struct Ctx {
   }
   // bytes: the launch's algorithmic memory traffic (0 where not tallied)
   void after(int kclass, double bytes = 0.0) {
+    bytes_total += bytes;
     if (pending) {
       cudaEventRecord(ev[2 * ev_used + 1], stream);
       ++ev_used;

@@ -607,7 +607,8 @@ bool launch_coarse_vcycle(Ctx& cx, const CoarseCycle& CC, Comp3<T> E, Comp3<T> R
     return false;
   cx.before(VSV_KCLASS_SMOOTH);
   k_coarse_vcycle<T><<<ncomp, 1024, smem, cx.stream>>>(CC, E, R);
-  cx.after(VSV_KCLASS_SMOOTH);
+  // r of the first level read, e written; the rest stays in shared memory
+  cx.after(VSV_KCLASS_SMOOTH, 2.0 * (double)sizeof(T) * (double)CC.lv[CC.first].cells() * ncomp);
   return true;
 }
 
@@ -620,7 +621,9 @@ void launch_rb_sweep(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, 
   const dim3 grid = grid3((L.n[0] + 1) / 2, L.n[1], L.n[2], ncomp);
   cx.before(kclass);
   k_rb_sweep<T><<<grid, block3(), 0, cx.stream>>>(L, X, R, color, (T)omega, (T)h2);
-  cx.after(kclass);
+  // one colour: the other colour's values and this colour's rhs read, this colour written
+  // (and read, for SOR): 1.5 words per cell
+  cx.after(kclass, (omega == 1.0 ? 1.5 : 2.0) * (double)sizeof(T) * (double)L.cells() * ncomp);
 }
 
 template <class T>
@@ -633,7 +636,7 @@ void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, 
   if (!exact && blocked_transfer_ok(F, C)) {
     cx.before(VSV_KCLASS_RESTRICT);
     k_restrict_block<T><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC);
-    cx.after(VSV_KCLASS_RESTRICT);
+    cx.after(VSV_KCLASS_RESTRICT, 2.125 * (double)sizeof(T) * (double)F.cells() * ncomp);
     return;
   }
   cx.before(VSV_KCLASS_RESTRICT);
@@ -646,7 +649,7 @@ void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, 
   } else {
     k_resid_restrict<T, false><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
   }
-  cx.after(VSV_KCLASS_RESTRICT);
+  cx.after(VSV_KCLASS_RESTRICT, (2.0 * (double)F.cells() + (double)C.cells()) * (double)sizeof(T) * ncomp);
 }
 
 template <class T>
@@ -657,13 +660,13 @@ void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Com
   if (blocked_transfer_ok(F, C)) {
     cx.before(VSV_KCLASS_PROLONG);
     k_prolong_block<T><<<grid3(C.n[0], C.n[1], C.n[2], ncomp), block3(), 0, cx.stream>>>(F, C, X, E);
-    cx.after(VSV_KCLASS_PROLONG);
+    cx.after(VSV_KCLASS_PROLONG, 2.125 * (double)sizeof(T) * (double)F.cells() * ncomp);
     return;
   }
   const dim3 grid = grid3(F.n[0], F.n[1], F.n[2], ncomp);
   cx.before(VSV_KCLASS_PROLONG);
   k_prolong_add<T><<<grid, block3(), 0, cx.stream>>>(F, C, X, E);
-  cx.after(VSV_KCLASS_PROLONG);
+  cx.after(VSV_KCLASS_PROLONG, (2.0 * (double)F.cells() + (double)C.cells()) * (double)sizeof(T) * ncomp);
 }
 
 template <class T>
@@ -671,7 +674,7 @@ void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp) {
   dim3 grid(blocks_for(n), ncomp);
   cx.before(-1);
   k_zero<T><<<grid, kBlock, 0, cx.stream>>>(X, n);
-  cx.after(-1);
+  cx.after(-1, (double)sizeof(T) * (double)n * ncomp);
 }
 
 template <class T>
@@ -680,7 +683,7 @@ void launch_extrapolate(Ctx& cx, Comp3<T> X, Comp3<T> XP, long long n, int ncomp
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
   k_extrapolate<T><<<grid, kBlock, 0, cx.stream>>>(X, XP, n, extrapolate);
-  cx.after(-1);
+  cx.after(-1, (extrapolate ? 4.0 : 2.0) * (double)sizeof(T) * (double)n * ncomp);
 }
 
 template <class T>
@@ -694,7 +697,7 @@ bool launch_coarse_solve(Ctx& cx, const Level& L, Comp3<T> E, Comp3<T> R, int nc
   dim3 grid(1, ncomp);
   cx.before(VSV_KCLASS_SMOOTH);
   k_coarse_solve<T><<<grid, 512, smem, cx.stream>>>(L, E, R, sweeps, (T)h2);
-  cx.after(VSV_KCLASS_SMOOTH);
+  cx.after(VSV_KCLASS_SMOOTH, 2.0 * (double)sizeof(T) * (double)n * ncomp);
   return true;
 }
 

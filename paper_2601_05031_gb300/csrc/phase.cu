@@ -705,14 +705,309 @@ __global__ void k_merge_ff(const float* __restrict__ hi, const float* __restrict
   if (t < n) out[t] = (double)hi[t] + (double)lo[t];
 }
 
+// ---------------------------------------------------------------- 4-cell kernels
+// The same double-word kernels with one thread per 4 consecutive x cells
+// (nx a multiple of 4): the own cells and the y / z neighbours are 16-byte
+// loads, the x neighbours two scalars, and the boundary index arithmetic is
+// done once per row instead of once per access.  Per-cell arithmetic is that
+// of the 1-cell kernels above, term for term.
+namespace {
+
+// A field around the 4 cells (i0 .. i0+3, j, k): own values c, the rows
+// above / below (ym, yp), the planes below / above (zm, zp) and the x
+// neighbours xl (i0 - 1) and xr (i0 + 4).
+struct St4 {
+  float4 c, ym, yp, zm, zp;
+  float xl, xr;
+};
+
+__device__ __forceinline__ float e4(const float4& v, int o) {
+  return o == 0 ? v.x : (o == 1 ? v.y : (o == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float4 ld4g(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// Row offsets of the 4-cell group's neighbourhood, with the boundary rule of
+// scalars (mirror at walls) or of the flow perturbation (zero beyond walls,
+// flagged by a negative offset); x wraps in both.
+struct Geo4 {
+  long long rc, rym, ryp, rzm, rzp;   // row offsets (plane * ny + row) * nx
+  int il, ir;                          // x indices of the two x neighbours
+  int i0;
+};
+
+__device__ __forceinline__ Geo4 geo4(const PhaseParams& P, int i0, int j, int k, bool pert) {
+  Geo4 G;
+  const long long nx = P.nx, ny = P.ny;
+  auto row = [&](int jj, int kk) { return ((long long)kk * ny + jj) * nx; };
+  G.i0 = i0;
+  G.il = i0 == 0 ? P.nx - 1 : i0 - 1;
+  G.ir = i0 + 4 == P.nx ? 0 : i0 + 4;
+  G.rc = row(j, k);
+  if (pert) {
+    G.rym = j > 0 ? row(j - 1, k) : -1;
+    G.ryp = j < P.ny - 1 ? row(j + 1, k) : -1;
+    const int km = P.zper ? wrap_idx(k - 1, P.nz) : k - 1;
+    const int kp = P.zper ? wrap_idx(k + 1, P.nz) : k + 1;
+    G.rzm = km >= 0 ? row(j, km) : -1;
+    G.rzp = kp < P.nz ? row(j, kp) : -1;
+  } else {
+    G.rym = row(mirror_idx(j - 1, P.ny), k);
+    G.ryp = row(mirror_idx(j + 1, P.ny), k);
+    G.rzm = row(j, P.zper ? wrap_idx(k - 1, P.nz) : mirror_idx(k - 1, P.nz));
+    G.rzp = row(j, P.zper ? wrap_idx(k + 1, P.nz) : mirror_idx(k + 1, P.nz));
+  }
+  return G;
+}
+
+__device__ __forceinline__ St4 load4(const float* __restrict__ a, const Geo4& G) {
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  St4 S;
+  S.c = ld4g(a + G.rc + G.i0);
+  S.ym = G.rym >= 0 ? ld4g(a + G.rym + G.i0) : z;
+  S.yp = G.ryp >= 0 ? ld4g(a + G.ryp + G.i0) : z;
+  S.zm = G.rzm >= 0 ? ld4g(a + G.rzm + G.i0) : z;
+  S.zp = G.rzp >= 0 ? ld4g(a + G.rzp + G.i0) : z;
+  S.xl = a[G.rc + G.il];
+  S.xr = a[G.rc + G.ir];
+  return S;
+}
+
+// neighbours of cell o of the group
+__device__ __forceinline__ float xp4(const St4& S, int o) { return o == 3 ? S.xr : e4(S.c, o + 1); }
+__device__ __forceinline__ float xm4(const St4& S, int o) { return o == 0 ? S.xl : e4(S.c, o - 1); }
+
+// lap7_ff on cell o (same order of operations)
+__device__ __forceinline__ FF lap7_ff4(const St4& H, const St4& L, int o, float ih_hi, float ih_lo) {
+  CascadeSum s(0.f);
+  s.add(xp4(H, o));
+  s.add(xm4(H, o));
+  s.add(e4(H.yp, o));
+  s.add(e4(H.ym, o));
+  s.add(e4(H.zp, o));
+  s.add(e4(H.zm, o));
+  s.add_scaled(-6.f, e4(H.c, o));
+  const float lsum = xp4(L, o) + xm4(L, o) + e4(L.yp, o) + e4(L.ym, o) + e4(L.zp, o) +
+                     e4(L.zm, o) - 6.f * e4(L.c, o);
+  const FF v = fast_two_sum(s.hi, __fadd_rn(s.lo, lsum));
+  return ff_mul(v, FF{ih_hi, ih_lo});
+}
+
+// lap7 in plain FP32 on cell o (same order as lap7)
+__device__ __forceinline__ float lap7_4(const St4& M, int o, float ih2) {
+  return (xp4(M, o) + xm4(M, o) + e4(M.yp, o) + e4(M.ym, o) + e4(M.zp, o) + e4(M.zm, o) -
+          6.f * e4(M.c, o)) * ih2;
+}
+
+__device__ __forceinline__ bool cell4(const PhaseParams& P, int& i0, int& j, int& k) {
+  i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  j = blockIdx.y * blockDim.y + threadIdx.y;
+  k = blockIdx.z;
+  return i0 < P.nx && j < P.ny;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_phi_update_ff4(PhaseParams P, const float* __restrict__ phi,
+                                 const float* __restrict__ phi_lo, const float* __restrict__ mu,
+                                 Comp3<float> psi, Comp3<float> v0, Scalars* S, float dt,
+                                 float* __restrict__ out, float* __restrict__ out_lo) {
+  int i0, j, k;
+  if (!cell4(P, i0, j, k)) return;
+  const float ih2 = (float)P.inv_h2, hih = (float)(0.5 * P.inv_h);
+  const Geo4 Gs = geo4(P, i0, j, k, false), Gp = geo4(P, i0, j, k, true);
+  const St4 M = load4(mu, Gs), F = load4(phi, Gs);
+  const St4 X = load4(psi.p[0], Gp), Y = load4(psi.p[1], Gp), Z = load4(psi.p[2], Gp);
+  const long long jk = j + (long long)k * P.ny;
+  const float v0x = v0.p[0][jk], v0y = v0.p[1][jk], v0z = v0.p[2][jk];
+  const float lam = S->lambda_vf, mob = (float)P.mobility;
+  const float4 fh = ld4g(phi + Gs.rc + i0), fl = ld4g(phi_lo + Gs.rc + i0);
+  float oh[4], ol[4];
+  bool finite = true;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const float lmu = lap7_4(M, o, ih2);
+    const float gx = (xp4(F, o) - xm4(F, o)) * hih;
+    const float gy = (e4(F.yp, o) - e4(F.ym, o)) * hih;
+    const float gz = (e4(F.zp, o) - e4(F.zm, o)) * hih;
+    const float vx = v0x + ((e4(Z.yp, o) - e4(Z.ym, o)) - (e4(Y.zp, o) - e4(Y.zm, o))) * hih;
+    const float vy = v0y + ((e4(X.zp, o) - e4(X.zm, o)) - (xp4(Z, o) - xm4(Z, o))) * hih;
+    const float vz = v0z + ((xp4(Y, o) - xm4(Y, o)) - (e4(X.yp, o) - e4(X.ym, o))) * hih;
+    const float rate = mob * (lmu + lam) - (vx * gx + vy * gy + vz * gz);
+    const FF v = ff_add_f(FF{e4(fh, o), e4(fl, o)}, dt * rate);
+    oh[o] = v.hi;
+    ol[o] = v.lo;
+    finite = finite && isfinite(v.hi);
+  }
+  *reinterpret_cast<float4*>(out + Gs.rc + i0) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+  *reinterpret_cast<float4*>(out_lo + Gs.rc + i0) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+  if (!finite) atomicOr(&S->nonfinite, 1);
+}
+
+__global__ void __launch_bounds__(256) k_helfrich_g_ff4(PhaseParams P, const float* __restrict__ phi,
+                                 const float* __restrict__ phi_lo, float* __restrict__ g,
+                                 float* __restrict__ g_lo) {
+  int i0, j, k;
+  if (!cell4(P, i0, j, k)) return;
+  const Geo4 G = geo4(P, i0, j, k, false);
+  const St4 H = load4(phi, G), L = load4(phi_lo, G);
+  float oh[4], ol[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const FF f{e4(H.c, o), e4(L.c, o)};
+    const FF lphi = lap7_ff4(H, L, o, P.ih2_hi, P.ih2_lo);
+    const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
+    const FF r = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.e2_hi, P.e2_lo})));
+    oh[o] = r.hi;
+    ol[o] = r.lo;
+  }
+  *reinterpret_cast<float4*>(g + G.rc + i0) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+  *reinterpret_cast<float4*>(g_lo + G.rc + i0) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+}
+
+__global__ void __launch_bounds__(256) k_mu_ff4(PhaseParams P, const float* __restrict__ phi,
+                                                const float* __restrict__ phi_lo,
+                                                const float* __restrict__ g,
+                                                const float* __restrict__ g_lo, const Scalars* S,
+                                                float* __restrict__ mu, float* __restrict__ mu_lo) {
+  int i0, j, k;
+  if (!cell4(P, i0, j, k)) return;
+  const Geo4 G = geo4(P, i0, j, k, false);
+  const St4 H = load4(phi, G), L = load4(phi_lo, G);
+  float oh[4], ol[4];
+  if (P.fe_kind == VSV_CAHN_HILLIARD) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const FF f{e4(H.c, o), e4(L.c, o)};
+      const FF lphi = lap7_ff4(H, L, o, P.ih2_hi, P.ih2_lo);
+      const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
+      const FF mm = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.sig_hi, P.sig_lo})));
+      oh[o] = mm.hi;
+      ol[o] = mm.lo;
+    }
+  } else {
+    const St4 GH = load4(g, G), GL = load4(g_lo, G);
+    const float gam = S->gamma_af;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const FF f{e4(H.c, o), e4(L.c, o)};
+      const FF lphi = lap7_ff4(H, L, o, P.ih2_hi, P.ih2_lo);
+      const FF gg{e4(GH.c, o), e4(GL.c, o)};
+      const FF lg = lap7_ff4(GH, GL, o, P.ih2_hi, P.ih2_lo);
+      const FF w = ff_add_f(ff_mul_f(ff_mul(f, f), 3.f), -1.f);
+      const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2_hi, P.e2_lo})));
+      const FF mm = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, gam)));
+      oh[o] = mm.hi;
+      ol[o] = mm.lo;
+    }
+  }
+  *reinterpret_cast<float4*>(mu + G.rc + i0) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+  *reinterpret_cast<float4*>(mu_lo + G.rc + i0) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+}
+
+__global__ void __launch_bounds__(256) k_source_ff4(PhaseParams P, const float* __restrict__ phi,
+                                                    const float* __restrict__ phi_lo,
+                                                    const float* __restrict__ mu,
+                                                    const float* __restrict__ mu_lo,
+                                                    Comp3<float> s_omega, Comp3<float> f,
+                                                    Comp3<float> f_lo) {
+  int i0, j, k;
+  if (!cell4(P, i0, j, k)) return;
+  const Geo4 G = geo4(P, i0, j, k, false);
+  const St4 FH = load4(phi, G), FL = load4(phi_lo, G), MH = load4(mu, G), ML = load4(mu_lo, G);
+  const FF hih{P.hih_hi, P.hih_lo};
+  const FF ie{P.ie_hi, P.ie_lo};
+  const long long jk = j + (long long)k * P.ny;
+  const float s0 = s_omega.p[0][jk], s1 = s_omega.p[1][jk], s2 = s_omega.p[2][jk];
+  auto dd = [&](float ah, float al, float bh, float bl) {
+    return ff_mul(ff_add(FF{ah, al}, ff_neg(FF{bh, bl})), hih);
+  };
+  float o0h[4], o0l[4], o1h[4], o1l[4], o2h[4], o2l[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const FF ax = dd(xp4(FH, o), xp4(FL, o), xm4(FH, o), xm4(FL, o));
+    const FF ay = dd(e4(FH.yp, o), e4(FL.yp, o), e4(FH.ym, o), e4(FL.ym, o));
+    const FF az = dd(e4(FH.zp, o), e4(FL.zp, o), e4(FH.zm, o), e4(FL.zm, o));
+    const FF bx = dd(xp4(MH, o), xp4(ML, o), xm4(MH, o), xm4(ML, o));
+    const FF by = dd(e4(MH.yp, o), e4(ML.yp, o), e4(MH.ym, o), e4(ML.ym, o));
+    const FF bz = dd(e4(MH.zp, o), e4(ML.zp, o), e4(MH.zm, o), e4(ML.zm, o));
+    const FF c0 = ff_add_f(ff_mul(ff_add(ff_mul(ay, bz), ff_neg(ff_mul(az, by))), ie), -s0);
+    const FF c1 = ff_add_f(ff_mul(ff_add(ff_mul(az, bx), ff_neg(ff_mul(ax, bz))), ie), -s1);
+    const FF c2 = ff_add_f(ff_mul(ff_add(ff_mul(ax, by), ff_neg(ff_mul(ay, bx))), ie), -s2);
+    o0h[o] = c0.hi; o0l[o] = c0.lo;
+    o1h[o] = c1.hi; o1l[o] = c1.lo;
+    o2h[o] = c2.hi; o2l[o] = c2.lo;
+  }
+  const long long t = G.rc + i0;
+  *reinterpret_cast<float4*>(f.p[0] + t) = make_float4(o0h[0], o0h[1], o0h[2], o0h[3]);
+  *reinterpret_cast<float4*>(f_lo.p[0] + t) = make_float4(o0l[0], o0l[1], o0l[2], o0l[3]);
+  *reinterpret_cast<float4*>(f.p[1] + t) = make_float4(o1h[0], o1h[1], o1h[2], o1h[3]);
+  *reinterpret_cast<float4*>(f_lo.p[1] + t) = make_float4(o1l[0], o1l[1], o1l[2], o1l[3]);
+  *reinterpret_cast<float4*>(f.p[2] + t) = make_float4(o2h[0], o2h[1], o2h[2], o2h[3]);
+  *reinterpret_cast<float4*>(f_lo.p[2] + t) = make_float4(o2l[0], o2l[1], o2l[2], o2l[3]);
+}
+
+// Partial sums of sum(phi) and of the area density over 4-cell groups,
+// grid-strided; one (phi, area) pair per block, as k_reduce_va.
+__global__ void __launch_bounds__(256) k_reduce_va_ff4(PhaseParams P, const float* __restrict__ phi,
+                                                       const float* __restrict__ phi_lo,
+                                                       double* partials) {
+  const int ng = P.nx >> 2;
+  const long long total = (long long)ng * P.ny * P.nz;
+  const FF hihf{P.hih_hi, P.hih_lo}, hef{P.he_hi, P.he_lo}, qf{P.q_hi, P.q_lo}, caf{P.ca_hi, P.ca_lo};
+  CascadeSum cp(0.f), ca(0.f);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / ng;
+    const int i0 = 4 * (int)(t - row * ng);
+    const int j = (int)(row % P.ny), k = (int)(row / P.ny);
+    const Geo4 G = geo4(P, i0, j, k, false);
+    const St4 H = load4(phi, G), L = load4(phi_lo, G);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const FF f{e4(H.c, o), e4(L.c, o)};
+      auto diff = [&](float ah, float al, float bh, float bl) {
+        return ff_mul(ff_add(FF{ah, al}, ff_neg(FF{bh, bl})), hihf);
+      };
+      const FF gx = diff(xp4(H, o), xp4(L, o), xm4(H, o), xm4(L, o));
+      const FF gy = diff(e4(H.yp, o), e4(L.yp, o), e4(H.ym, o), e4(L.ym, o));
+      const FF gz = diff(e4(H.zp, o), e4(L.zp, o), e4(H.zm, o), e4(L.zm, o));
+      const FF g2 = ff_add(ff_add(ff_mul(gx, gx), ff_mul(gy, gy)), ff_mul(gz, gz));
+      const FF w = ff_add_f(ff_mul(f, f), -1.f);
+      const FF dens = ff_mul(ff_add(ff_mul(g2, hef), ff_mul(ff_mul(w, w), qf)), caf);
+      cp.add(f.hi);
+      cp.add(f.lo);
+      ca.add(dens.hi);
+      ca.add(dens.lo);
+    }
+  }
+  double sphi = (double)cp.hi + (double)cp.lo;
+  double sarea = (double)ca.hi + (double)ca.lo;
+  sphi = block_sum(sphi);
+  sarea = block_sum(sarea);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = sphi;
+    partials[2 * blockIdx.x + 1] = sarea;
+  }
+}
+
+static bool use4(const PhaseParams& P) { return P.nx % 4 == 0 && P.nx >= 8; }
+static dim3 grid4(const PhaseParams& P) {
+  return dim3((unsigned)((P.nx / 4 + 31) / 32), (unsigned)((P.ny + 7) / 8), (unsigned)P.nz);
+}
+
 void launch_phi_update_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo,
                           const float* mu, Comp3<float> psi, Comp3<float> v0, const Scalars* S,
                           float dt, float* out, float* out_lo) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   cx.before(VSV_KCLASS_PHASE);
-  k_phi_update_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, mu, psi, v0,
-                                                      const_cast<Scalars*>(S), dt, out, out_lo);
-  cx.after(VSV_KCLASS_PHASE);
+  if (use4(P))
+    k_phi_update_ff4<<<grid4(P), dim3(32, 8), 0, cx.stream>>>(P, phi, phi_lo, mu, psi, v0,
+                                                             const_cast<Scalars*>(S), dt, out, out_lo);
+  else
+    k_phi_update_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(
+        P, phi, phi_lo, mu, psi, v0, const_cast<Scalars*>(S), dt, out, out_lo);
+  // phi (two words), mu, psi' (3) read; phi (two words) written
+  cx.after(VSV_KCLASS_PHASE, 32.0 * (double)n);
 }
 
 void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo, float* g,
@@ -720,13 +1015,20 @@ void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* 
   const long long n = (long long)P.nx * P.ny * P.nz;
   if (P.fe_kind == VSV_HELFRICH) {
     cx.before(VSV_KCLASS_PHASE);
-    k_helfrich_g_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo);
-    cx.after(VSV_KCLASS_PHASE);
+    if (use4(P))
+      k_helfrich_g_ff4<<<grid4(P), dim3(32, 8), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo);
+    else
+      k_helfrich_g_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo);
+    cx.after(VSV_KCLASS_PHASE, 16.0 * (double)n);   // phi read, g written (two words each)
   }
   cx.before(VSV_KCLASS_PHASE);
-  k_mu_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, S, mu,
-                                                                     mu_lo);
-  cx.after(VSV_KCLASS_PHASE);
+  if (use4(P))
+    k_mu_ff4<<<grid4(P), dim3(32, 8), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, S, mu, mu_lo);
+  else
+    k_mu_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, S, mu,
+                                                                       mu_lo);
+  // phi (and g for Helfrich) read, mu written, two words each
+  cx.after(VSV_KCLASS_PHASE, (P.fe_kind == VSV_HELFRICH ? 24.0 : 16.0) * (double)n);
 }
 
 // f = grad phi x grad mu / eta - s_omega in double-word arithmetic from
@@ -765,9 +1067,13 @@ void launch_source_ff(Ctx& cx, const PhaseParams& P, const float* phi, const flo
                       const float* mu, const float* mu_lo, Comp3<float> s_omega, Comp3<float> f,
                       Comp3<float> f_lo) {
   cx.before(VSV_KCLASS_PHASE);
-  k_source_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, mu, mu_lo,
-                                                                       s_omega, f, f_lo);
-  cx.after(VSV_KCLASS_PHASE);
+  if (use4(P))
+    k_source_ff4<<<grid4(P), dim3(32, 8), 0, cx.stream>>>(P, phi, phi_lo, mu, mu_lo, s_omega, f, f_lo);
+  else
+    k_source_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, mu, mu_lo,
+                                                                         s_omega, f, f_lo);
+  // phi, mu read, f (3) written, two words each
+  cx.after(VSV_KCLASS_PHASE, 40.0 * (double)((long long)P.nx * P.ny * P.nz));
 }
 
 void launch_split_ff(Ctx& cx, const double* in, float* hi, float* lo, long long n) {
@@ -790,15 +1096,23 @@ void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu,
   cx.before(VSV_KCLASS_PHASE);
   k_phi_update<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, mu, psi, v0, const_cast<Scalars*>(S),
                                                      dt, out);
-  cx.after(VSV_KCLASS_PHASE);
+  cx.after(VSV_KCLASS_PHASE, 6.0 * sizeof(T) * (double)n);   // phi, mu, psi' (3) read, phi written
 }
 
 template <class T>
 void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo,
                       double* partials, int nblocks, Scalars* S, int init) {
   cx.before(VSV_KCLASS_PHASE);
-  k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
-  cx.after(VSV_KCLASS_PHASE);
+  if constexpr (std::is_same<T, float>::value) {
+    if (use4(P))
+      k_reduce_va_ff4<<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
+    else
+      k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
+  } else {
+    k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
+  }
+  // phi read (two FP32 words, or one FP64)
+  cx.after(VSV_KCLASS_PHASE, 8.0 * (double)((long long)P.nx * P.ny * P.nz));
   cx.before(-1);
   k_va_finalize<<<1, kBlock, 0, cx.stream>>>(partials, nblocks, (long long)P.nx * P.ny * P.nz, S,
                                              init);
@@ -811,11 +1125,11 @@ void launch_mu(Ctx& cx, const PhaseParams& P, const T* phi, T* g, T* mu, const S
   if (P.fe_kind == VSV_HELFRICH) {
     cx.before(VSV_KCLASS_PHASE);
     k_helfrich_g<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, g);
-    cx.after(VSV_KCLASS_PHASE);
+    cx.after(VSV_KCLASS_PHASE, 2.0 * sizeof(T) * (double)n);
   }
   cx.before(VSV_KCLASS_PHASE);
   k_mu<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, g, S, mu);
-  cx.after(VSV_KCLASS_PHASE);
+  cx.after(VSV_KCLASS_PHASE, (P.fe_kind == VSV_HELFRICH ? 3.0 : 2.0) * sizeof(T) * (double)n);
 }
 
 template <class T>
@@ -824,7 +1138,7 @@ void launch_source(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Com
   const long long n = (long long)P.nx * P.ny * P.nz;
   cx.before(VSV_KCLASS_PHASE);
   k_source<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, mu, s_omega, f);
-  cx.after(VSV_KCLASS_PHASE);
+  cx.after(VSV_KCLASS_PHASE, 5.0 * sizeof(T) * (double)n);   // phi, mu read, f (3) written
 }
 
 template <class T>

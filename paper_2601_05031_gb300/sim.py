@@ -101,6 +101,9 @@ class Simulation:
     def kernel_launches(self):
         return V.vsv_kernel_launches(self.g)
 
+    def kernel_bytes(self):
+        return V.vsv_kernel_bytes(self.g)
+
     def close(self):
         if self.g is not None:
             V.vsv_destroy(self.g)

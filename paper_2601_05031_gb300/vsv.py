@@ -81,7 +81,7 @@ EXPORTS = [
     "vsv_stability_limit", "vsv_solve_poisson", "vsv_get_field", "vsv_set_field",
     "vsv_get_diagnostics", "vsv_get_stress_profile", "vsv_state_bytes", "vsv_get_state",
     "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_last_error", "vsv_kernel_launches",
-    "vsv_profile_enable", "vsv_profile_read",
+    "vsv_kernel_bytes", "vsv_profile_enable", "vsv_profile_read",
 ]
 
 
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_check": (i32, [vp]),
         "vsv_last_error": (C.c_char_p, [vp]),
         "vsv_kernel_launches": (i64, [vp]),
+        "vsv_kernel_bytes": (dbl, [vp]),
         "vsv_profile_enable": (i32, [vp, i32, i32]),
         "vsv_profile_read": (i32, [vp, i32, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl)]),
     }
@@ -272,6 +273,10 @@ def vsv_last_error(g) -> str:
 
 def vsv_kernel_launches(g) -> int:
     return lib().vsv_kernel_launches(g)
+
+
+def vsv_kernel_bytes(g) -> float:
+    return lib().vsv_kernel_bytes(g)
 
 
 def vsv_profile_enable(g, kclass, enable=True):

@@ -324,6 +324,22 @@ def test_profile_byte_tally(V):
     assert nbytes == 2 * cycles * (8 + 12 + 12 + 24) * nx * ny * nz * 3
 
 
+def test_step_byte_tally_covers_the_sweeps(V):
+    """The always-on tally of a step counts the finest-level sweeps and more
+    (defects, transfers, coarse levels, phase kernels)."""
+    nx, ny, nz, cycles = 256, 32, 32, 2
+    w = inputs.vesicle_couette_512x256x256(nx=nx, ny=ny, nz=nz, nsteps=1)
+    sim = make_sim(V, w, V.VSV_MIXED, fixed=cycles)
+    sim.set_phi(w.phi0)
+    b0 = sim.kernel_bytes()
+    sim.step(1, w.dt)
+    step_bytes = sim.kernel_bytes() - b0
+    sim.close()
+    sweeps = 2 * cycles * (8 + 12 + 12 + 24) * nx * ny * nz * 3
+    defects = 2 * cycles * 20 * nx * ny * nz * 3
+    assert sweeps + defects < step_bytes < 3 * (sweeps + defects)
+
+
 # ------------------------------------------------------------ fused sweep
 @pytest.mark.parametrize("bc", [(True, False, True), (True, False, False)])
 def test_fused_sweep_bit_identical_to_reference(V, bc):
