@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--ny", type=int, default=256)
     ap.add_argument("--nz", type=int, default=256)
     ap.add_argument("--cycles", type=int, default=4, help="V-cycles per Poisson solve")
+    ap.add_argument("--extrapolate", type=int, default=1, choices=[0, 1, 2],
+                    help="order of the first guess of each solve from the previous solutions")
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -133,12 +135,25 @@ def job_throughput(world_size, cells_per_rank, steps, ms_max):
 
 
 # ---------------------------------------------------------------- GPU arm
-def make_sim(w, prec, cycles):
+GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
+         2: "extrapolated guess 3x^n - 3x^(n-1) + x^(n-2)"}
+
+# DRAM traffic of the finest-level fused sweeps per launch, averaged over the
+# four sweeps of a correction (zero input, plain, plain, iterate update): ncu
+# dram__bytes_read.sum + dram__bytes_write.sum at 512 x 256 x 128 (692 MB),
+# scaled by the cells to the launch at hand.  From one ncu capture of the
+# current kernel; to be retaken (and set to None meanwhile) whenever
+# k_rbgs_fused changes.
+FUSED_SWEEP_TRAFFIC_PER_CELL = 692.0e6 / (512 * 256 * 128 * 3)
+
+
+def make_sim(w, prec, cycles, extrapolate=1):
     from paper_2601_05031_gb300 import vsv as V
     from paper_2601_05031_gb300.sim import Simulation
     sim = Simulation.from_workload(w, prec)
     sp = sim.solver_params()
     sp.fixed_cycles = cycles
+    sp.extrapolate = extrapolate
     sp.tol = 1e-7 if prec == V.VSV_MIXED else 1e-12
     V.vsv_set_solver(sim.g, sp)
     sim.set_phi(w.phi0)
@@ -179,7 +194,7 @@ def run_gpu(args, ws, rank, local):
 
     w = inputs.vesicle_couette_512x256x256(nx=args.nx, ny=args.ny, nz=args.nz)
     N = w.ncells
-    sim = make_sim(w, V.VSV_MIXED, args.cycles)
+    sim = make_sim(w, V.VSV_MIXED, args.cycles, args.extrapolate)
     for _ in range(args.warmup):
         sim.step(1, w.dt)
     torch.cuda.synchronize()
@@ -200,7 +215,7 @@ def run_gpu(args, ws, rank, local):
                    "precision": "mixed: f32 fields and smoothing, exact (FP64-class) defect, "
                                 "f64 reductions",
                    "solver": f"multigrid V(2,2) red-black GS, {args.cycles} cycles per Poisson "
-                             "solve from the extrapolated guess 2x^n - x^(n-1), 6 solves per step",
+                             f"solve from the {GUESS[args.extrapolate]}, 6 solves per step",
                    "l2": "inputs larger than L2 (about 2 GB of resident fields per replica)",
                    "dt": w.dt, "parallelism": f"replicas x{ws}"},
         "gpu_launches": int(launches),
@@ -236,12 +251,14 @@ def run_gpu(args, ws, rank, local):
                        "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                        "algorithmic_bytes_per_launch": round(algo), "launches_timed": int(pn),
                        "avg_launch_us": round(per_launch_s * 1e6, 2),
-                       "traffic": None}
+                       "traffic": (None if FUSED_SWEEP_TRAFFIC_PER_CELL is None else
+                                   round(FUSED_SWEEP_TRAFFIC_PER_CELL * N * 3)),
+                       "traffic_source": "ncu capture at 512x256x128, scaled by cells"}
     out["clocks"] = clk.summary()
     # plain FP64 step with the same schedule, and the accuracy of mixed vs FP64
     if not args.no_fp64:
         k64 = args.fp64_steps or max(3, args.steps // 4)
-        sim64 = make_sim(w, V.VSV_FP64, args.cycles)
+        sim64 = make_sim(w, V.VSV_FP64, args.cycles, args.extrapolate)
         for _ in range(min(args.warmup, 3)):
             sim64.step(1, w.dt)
         ms64 = timed_steps(sim64, k64, w.dt, torch, barrier)
@@ -249,7 +266,7 @@ def run_gpu(args, ws, rank, local):
         # accuracy: the benchmarked mixed schedule against FP64 solved to a
         # relative residual of 1e-12 every step, same phi0 and steps
         nacc = 10
-        simA = make_sim(w, V.VSV_MIXED, args.cycles)
+        simA = make_sim(w, V.VSV_MIXED, args.cycles, args.extrapolate)
         simB = make_sim(w, V.VSV_FP64, 0)
         simA.step(nacc, w.dt)
         simB.step(nacc, w.dt)

@@ -131,11 +131,14 @@ typedef struct {
  * kernels available for each level (fused single-pass red-black sweeps,
  * tiled transfers and defects where the tile shape allows, the lower levels
  * of a V-cycle in one launch); 1 forces the reference per-level, per-colour
- * kernels (same arithmetic, bit-identical results; for cross-checks).  extrapolate = 1
- * starts each solve of a time step from 2 x^n - x^{n-1} (linear extrapolation
- * of the two previous solutions) instead of x^n, which shrinks the initial
- * error from O(dt) to O(dt^2); it changes the iterate, not the converged
- * answer. */
+ * kernels (same arithmetic, bit-identical results; for cross-checks).
+ * extrapolate: order of the first guess of each solve of a time step, from
+ * the previous solutions: 0 starts from x^n; 1 from 2 x^n - x^{n-1} (linear
+ * extrapolation in time, initial error O(dt^2) instead of O(dt)); 2 from
+ * 3 x^n - 3 x^{n-1} + x^{n-2} (quadratic, O(dt^3)).  The order drops to what
+ * the history allows for the first steps after vsv_set_phi, vsv_set_field
+ * of omega' / psi', or vsv_set_state of a blob without history.  It changes
+ * the iterate, not the converged answer.  Values outside 0..2: VSV_EINVAL. */
 typedef struct {
   int kind;
   double tol;

@@ -39,15 +39,21 @@ struct vsv_grid {
   void* f[3] = {};
   void* om[3] = {};
   void* ps[3] = {};
-  void* om_prev[3] = {};     // previous step's solutions (initial-guess extrapolation)
+  // the two previous steps' solutions (initial-guess extrapolation); the
+  // three buffers of a field rotate instead of being copied
+  void* om_prev[3] = {};
   void* ps_prev[3] = {};
-  bool prev_valid = false;
+  void* om_prev2[3] = {};
+  void* ps_prev2[3] = {};
+  int hist = 0;              // how many of those previous solutions are valid (0..2)
   // mixed path: low words of the double-word iterates, the FP32 correction e
   // and defect r of the outer defect correction
   float* om_lo[3] = {};
   float* ps_lo[3] = {};
   float* om_prev_lo[3] = {};
   float* ps_prev_lo[3] = {};
+  float* om_prev2_lo[3] = {};
+  float* ps_prev2_lo[3] = {};
   float* e0[3] = {};
   float* r0[3] = {};
   void* stage_a = nullptr;   // N * 8 bytes
@@ -151,6 +157,8 @@ size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
       p = take((size_t)N * 4); if (g) g->ps_lo[c] = (float*)p;
       p = take((size_t)N * 4); if (g) g->om_prev_lo[c] = (float*)p;
       p = take((size_t)N * 4); if (g) g->ps_prev_lo[c] = (float*)p;
+      p = take((size_t)N * 4); if (g) g->om_prev2_lo[c] = (float*)p;
+      p = take((size_t)N * 4); if (g) g->ps_prev2_lo[c] = (float*)p;
       p = take((size_t)N * 4); if (g) g->e0[c] = (float*)p;
       p = take((size_t)N * 4); if (g) g->r0[c] = (float*)p;
     }
@@ -160,6 +168,8 @@ size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->ps[c] = p; }
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->om_prev[c] = p; }
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->ps_prev[c] = p; }
+  for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->om_prev2[c] = p; }
+  for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->ps_prev2[c] = p; }
   p = take((size_t)N * 8); if (g) g->stage_a = p;
   p = take((size_t)N * 8); if (g) g->stage_b = p;
   long long cells[kMaxLevels];
@@ -591,56 +601,80 @@ Rhs3<T> rhs_psi(vsv_grid* g) {
                  {(T*)g->s_ps_neg_t[0], (T*)g->s_ps_neg_t[1], (T*)g->s_ps_neg_t[2]}, (T)-1};
 }
 
+// First guess of a solve from the field's history: x^n (order 0), 2 x^n -
+// x^{n-1} (order 1) or 3 x^n - 3 x^{n-1} + x^{n-2} (order 2), limited by how
+// many previous solutions exist.  The guess is written into the oldest
+// buffer, and the three buffers rotate: (x, x_prev, x_prev2) <- (guess, x^n,
+// x^{n-1}), so no field is copied.
+template <class T>
+void guess_from_history(vsv_grid* g, void* x[3], void* xp[3], void* xpp[3], float* xl[3],
+                        float* xpl[3], float* xppl[3], int order) {
+  const bool mixed = std::is_same<T, float>::value && g->prec == VSV_MIXED;
+  if (mixed)
+    launch_extrapolate_rot_dw(g->cx, comp3<float>(x[0], x[1], x[2]), comp3<float>(xl[0], xl[1], xl[2]),
+                              comp3<float>(xp[0], xp[1], xp[2]), comp3<float>(xpl[0], xpl[1], xpl[2]),
+                              comp3<float>(xpp[0], xpp[1], xpp[2]),
+                              comp3<float>(xppl[0], xppl[1], xppl[2]), g->N, 3, order);
+  else
+    launch_extrapolate_rot<T>(g->cx, comp3<T>(x[0], x[1], x[2]), comp3<T>(xp[0], xp[1], xp[2]),
+                              comp3<T>(xpp[0], xpp[1], xpp[2]), g->N, 3, order);
+  for (int c = 0; c < 3; ++c) {
+    void* t = xpp[c];
+    xpp[c] = xp[c];
+    xp[c] = x[c];
+    x[c] = t;
+    if (mixed) {
+      float* tl = xppl[c];
+      xppl[c] = xpl[c];
+      xpl[c] = xl[c];
+      xl[c] = tl;
+    }
+  }
+}
+
 vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
   const vsv_solver_params& s = g->sol;
   const int fixed = initial ? 0 : s.fixed_cycles;
-  const bool extrap = !initial && s.extrapolate && g->prev_valid;
+  const int order = std::min(s.extrapolate, g->hist);
+  if (!initial)
+    guess_from_history<float>(g, g->om, g->om_prev, g->om_prev2, g->om_lo, g->om_prev_lo,
+                              g->om_prev2_lo, order);
   Comp3<float> OH = comp3<float>(g->om[0], g->om[1], g->om[2]);
   Comp3<float> OL = comp3<float>(g->om_lo[0], g->om_lo[1], g->om_lo[2]);
-  Comp3<float> PH = comp3<float>(g->ps[0], g->ps[1], g->ps[2]);
-  Comp3<float> PL = comp3<float>(g->ps_lo[0], g->ps_lo[1], g->ps_lo[2]);
-  if (!initial)
-    launch_extrapolate_dw(g->cx, OH, OL, comp3<float>(g->om_prev[0], g->om_prev[1], g->om_prev[2]),
-                          comp3<float>(g->om_prev_lo[0], g->om_prev_lo[1], g->om_prev_lo[2]), g->N,
-                          3, extrap ? 1 : 0);
   Comp3<float> FL = comp3<float>(g->f_lo[0], g->f_lo[1], g->f_lo[2]);
   vsv_status st = solve_dc(g, g->flow_levels, OH, OL, rhs_omega<float>(g), FL, 3, fixed, s.tol,
                            s.max_cycles, s.check_every, &g->last_cycles[0], &g->last_relres[0]);
   if (st != VSV_OK) return st;
   if (!initial)
-    launch_extrapolate_dw(g->cx, PH, PL, comp3<float>(g->ps_prev[0], g->ps_prev[1], g->ps_prev[2]),
-                          comp3<float>(g->ps_prev_lo[0], g->ps_prev_lo[1], g->ps_prev_lo[2]), g->N,
-                          3, extrap ? 1 : 0);
+    guess_from_history<float>(g, g->ps, g->ps_prev, g->ps_prev2, g->ps_lo, g->ps_prev_lo,
+                              g->ps_prev2_lo, order);
+  Comp3<float> PH = comp3<float>(g->ps[0], g->ps[1], g->ps[2]);
+  Comp3<float> PL = comp3<float>(g->ps_lo[0], g->ps_lo[1], g->ps_lo[2]);
   // rhs of the stream-vector problem: -(omega'_hi + omega'_lo) - s_psi
   st = solve_dc(g, g->flow_levels, PH, PL, rhs_psi<float>(g), OL, 3, fixed, s.tol, s.max_cycles,
                 s.check_every, &g->last_cycles[1], &g->last_relres[1]);
-  g->prev_valid = !initial;
+  g->hist = initial ? 0 : std::min(g->hist + 1, 2);
   return st;
 }
 
 template <class T>
 vsv_status flow_solves(vsv_grid* g, bool initial) {
   if constexpr (std::is_same<T, float>::value) return flow_solves_mixed(g, initial);
-  Comp3<T> O = comp3<T>(g->om[0], g->om[1], g->om[2]);
-  Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
   const vsv_solver_params& s = g->sol;
   const int fixed = initial ? 0 : s.fixed_cycles;
-  // initial guesses: 2 x^n - x^{n-1} once two solutions exist, else x^n
-  const bool extrap = !initial && s.extrapolate && g->prev_valid;
-  if (!initial) {
-    launch_extrapolate<T>(g->cx, O, comp3<T>(g->om_prev[0], g->om_prev[1], g->om_prev[2]), g->N, 3,
-                          extrap ? 1 : 0);
-  }
+  const int order = std::min(s.extrapolate, g->hist);
+  if (!initial)
+    guess_from_history<T>(g, g->om, g->om_prev, g->om_prev2, nullptr, nullptr, nullptr, order);
+  Comp3<T> O = comp3<T>(g->om[0], g->om[1], g->om[2]);
   vsv_status st = solve<T>(g, g->flow_levels, O, rhs_omega<T>(g), 3, s.kind, fixed, s.tol,
                            s.max_cycles, s.check_every, &g->last_cycles[0], &g->last_relres[0]);
   if (st != VSV_OK) return st;
-  if (!initial) {
-    launch_extrapolate<T>(g->cx, Pp, comp3<T>(g->ps_prev[0], g->ps_prev[1], g->ps_prev[2]), g->N, 3,
-                          extrap ? 1 : 0);
-  }
+  if (!initial)
+    guess_from_history<T>(g, g->ps, g->ps_prev, g->ps_prev2, nullptr, nullptr, nullptr, order);
+  Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
   st = solve<T>(g, g->flow_levels, Pp, rhs_psi<T>(g), 3, s.kind, fixed, s.tol, s.max_cycles,
                 s.check_every, &g->last_cycles[1], &g->last_relres[1]);
-  g->prev_valid = !initial;
+  g->hist = initial ? 0 : std::min(g->hist + 1, 2);
   return st;
 }
 
@@ -1075,7 +1109,7 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
     return fail(g, VSV_EINVAL, "SOR is provided for the FP64 precision only%s");
   if (sp->nu1 < 0 || sp->nu2 < 0 || sp->nu1 + sp->nu2 < 1 || sp->coarse_sweeps < 1 ||
       sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->max_levels < 1 || !(sp->tol >= 0) ||
-      sp->variant < 0 || sp->variant > 1 || sp->extrapolate < 0 || sp->extrapolate > 1)
+      sp->variant < 0 || sp->variant > 1 || sp->extrapolate < 0 || sp->extrapolate > 2)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
   g->cx.tiled = sp->variant == 0;
@@ -1278,7 +1312,7 @@ vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int
     st = VSV_OK;
   }
   if (st == VSV_OK && field == VSV_FIELD_PHI) g->phase_stale = true;
-  if (st == VSV_OK && field != VSV_FIELD_PHI) g->prev_valid = false;
+  if (st == VSV_OK && field != VSV_FIELD_PHI) g->hist = 0;
   return st;
 }
 
@@ -1369,12 +1403,12 @@ struct StateHeader {
   int nx, ny, nz, prec;
   double V0, A0, time;
   long long steps;
-  int prev_valid, pad;
+  int hist, pad;
 };
 
 // Device buffers of the state blob, in blob order: phi, omega'(3), psi'(3),
-// the previous step's omega'(3) and psi'(3); on the mixed path then the low
-// words of phi and of those twelve double-word fields.
+// the two previous steps' omega'(3) and psi'(3); on the mixed path then the
+// low words of phi and of those eighteen double-word fields.
 std::vector<std::pair<void*, size_t>> state_fields(const vsv_grid* g) {
   std::vector<std::pair<void*, size_t>> v;
   const size_t fb = (size_t)g->N * g->tsize, lb = (size_t)g->N * 4;
@@ -1383,12 +1417,16 @@ std::vector<std::pair<void*, size_t>> state_fields(const vsv_grid* g) {
   for (int c = 0; c < 3; ++c) v.push_back({g->ps[c], fb});
   for (int c = 0; c < 3; ++c) v.push_back({g->om_prev[c], fb});
   for (int c = 0; c < 3; ++c) v.push_back({g->ps_prev[c], fb});
+  for (int c = 0; c < 3; ++c) v.push_back({g->om_prev2[c], fb});
+  for (int c = 0; c < 3; ++c) v.push_back({g->ps_prev2[c], fb});
   if (g->prec == VSV_MIXED) {
     v.push_back({g->phi_lo[g->cur], lb});
     for (int c = 0; c < 3; ++c) v.push_back({g->om_lo[c], lb});
     for (int c = 0; c < 3; ++c) v.push_back({g->ps_lo[c], lb});
     for (int c = 0; c < 3; ++c) v.push_back({g->om_prev_lo[c], lb});
     for (int c = 0; c < 3; ++c) v.push_back({g->ps_prev_lo[c], lb});
+    for (int c = 0; c < 3; ++c) v.push_back({g->om_prev2_lo[c], lb});
+    for (int c = 0; c < 3; ++c) v.push_back({g->ps_prev2_lo[c], lb});
   }
   return v;
 }
@@ -1416,7 +1454,7 @@ vsv_status vsv_get_state(vsv_grid* g, void* dst, size_t bytes) {
   std::memcpy(hd.magic, "VSVSTAT", 8);
   hd.nx = g->nx; hd.ny = g->ny; hd.nz = g->nz; hd.prec = g->prec;
   hd.V0 = hs.V0; hd.A0 = hs.A0; hd.time = g->time; hd.steps = g->steps;
-  hd.prev_valid = g->prev_valid ? 1 : 0;
+  hd.hist = g->hist;
   std::memcpy(p, &hd, sizeof hd);
   return VSV_OK;
 }
@@ -1442,7 +1480,7 @@ vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes) {
   g->steps = hd.steps;
   g->phi_set = true;
   g->phase_stale = true;
-  g->prev_valid = hd.prev_valid != 0;
+  g->hist = (hd.hist >= 0 && hd.hist <= 2) ? hd.hist : 0;
   return VSV_OK;
 }
 

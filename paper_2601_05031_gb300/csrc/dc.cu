@@ -114,25 +114,31 @@ __global__ void k_update_dw(Comp3<float> XH, Comp3<float> XL, Comp3<float> E, lo
   }
 }
 
-// x <- 2 x - xp and xp <- old x in double-word arithmetic (extrapolate = 1);
-// xp <- x only (extrapolate = 0).
-__global__ void k_extrapolate_dw(Comp3<float> XH, Comp3<float> XL, Comp3<float> PH, Comp3<float> PL,
-                                 long long n, int extrapolate) {
+// First guess from the history, in double-word arithmetic, written into the
+// oldest buffer C: order 0: A; 1: 2A - B; 2: 3A - 3B + C (A = x^n, B =
+// x^{n-1}, C = x^{n-2}).
+__global__ void k_extrapolate_rot_dw(Comp3<float> AH, Comp3<float> AL, Comp3<float> BH,
+                                     Comp3<float> BL, Comp3<float> CH, Comp3<float> CL, long long n,
+                                     int order) {
   const int comp = blockIdx.y;
-  float* __restrict__ xh = XH.at(comp);
-  float* __restrict__ xl = XL.at(comp);
-  float* __restrict__ ph = PH.at(comp);
-  float* __restrict__ pl = PL.at(comp);
+  const float* __restrict__ ah = AH.at(comp);
+  const float* __restrict__ al = AL.at(comp);
+  const float* __restrict__ bh = BH.at(comp);
+  const float* __restrict__ bl = BL.at(comp);
+  float* __restrict__ ch = CH.at(comp);
+  float* __restrict__ cl = CL.at(comp);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    const FF x{xh[t], xl[t]};
-    if (extrapolate) {
-      const FF v = ff_add(FF{2.f * x.hi, 2.f * x.lo}, ff_neg(FF{ph[t], pl[t]}));
-      xh[t] = v.hi;
-      xl[t] = v.lo;
+    const FF a{ah[t], al[t]};
+    FF v = a;
+    if (order == 1) {
+      v = ff_add(FF{2.f * a.hi, 2.f * a.lo}, ff_neg(FF{bh[t], bl[t]}));
+    } else if (order == 2) {
+      const FF d = ff_add(a, ff_neg(FF{bh[t], bl[t]}));   // A - B
+      v = ff_add(ff_mul_f(d, 3.f), FF{ch[t], cl[t]});
     }
-    ph[t] = x.hi;
-    pl[t] = x.lo;
+    ch[t] = v.hi;
+    cl[t] = v.lo;
   }
 }
 
@@ -155,9 +161,15 @@ void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL,
 // clear of the planes p - 1 and p that a warp still in step p - 1 may read,
 // so one barrier per step suffices.
 namespace {
-constexpr int kDR = tile::kTY + 2;                                   // staged rows
-constexpr int kDS = 5;                                               // ring slots
-constexpr int kDStage = (kDR * tile::kNV + tile::kThreads - 1) / tile::kThreads;
+constexpr int kDS = 5;   // ring slots
+// ROWS rows per thread: a tile of 8 ROWS rows, 8 ROWS + 2 staged with the halo
+template <int ROWS>
+struct DefShape {
+  static constexpr int kRows = 8 * ROWS;
+  static constexpr int kDR = kRows + 2;
+  static constexpr int kStage = (kDR * tile::kNV + tile::kThreads - 1) / tile::kThreads;
+  static constexpr size_t kSmem = (size_t)2 * kDS * kDR * tile::kW * sizeof(float);
+};
 
 struct DefGeom : tile::Geom {
   float ih_hi, ih_lo, beta;
@@ -196,10 +208,13 @@ __device__ __forceinline__ float defect_cell(float xmh, float xph, float ymh, fl
 }
 }  // namespace
 
-__global__ void __launch_bounds__(tile::kThreads, 2)
+template <int ROWS>
+__global__ void __launch_bounds__(tile::kThreads, ROWS == 1 ? 3 : 2)
 k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3<float> BL,
                Comp3<float> OUT, double* partials) {
   using namespace tile;
+  constexpr int kDR = DefShape<ROWS>::kDR, kRows = DefShape<ROWS>::kRows;
+  constexpr int kDStage = DefShape<ROWS>::kStage;
   extern __shared__ float4 smem_d4[];
   float* sH = reinterpret_cast<float*>(smem_d4);
   float* sL = sH + kDS * kDR * kW;
@@ -211,7 +226,7 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
   const float* __restrict__ S = R.s_at(comp);
   float* __restrict__ out = OUT.at(comp);
   const int tx = blockIdx.x % G.ntx, tyb = blockIdx.x / G.ntx;
-  const int x0 = tx * kTX, y0 = tyb * kTY;
+  const int x0 = tx * kTX, y0 = tyb * kRows;
   const int zb = blockIdx.y * G.zchunk;
   const int ze = min(zb + G.zchunk, G.nz);
   const int tid = threadIdx.x, gx = tid & 31, ty = tid >> 5;
@@ -222,9 +237,9 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
   };
   StageDesc<kDStage> ds;
   ds.init(G, x0, y0, 1, kDR);
-  int rown[2], jown[2];
+  int rown[ROWS], jown[ROWS];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < ROWS; ++h) {
     rown[h] = ty + 8 * h + 1;
     jown[h] = y0 + ty + 8 * h;
   }
@@ -241,9 +256,9 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
   cp_async_commit();
   cp_async_wait1();
   __syncthreads();
-  float4 Mh[2], Ml[2], Vh[2], Vl[2], Ph[2], Pl[2];
+  float4 Mh[ROWS], Ml[ROWS], Vh[ROWS], Vl[ROWS], Ph[ROWS], Pl[ROWS];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < ROWS; ++h) {
     Vh[h] = lds4(slot(sH, zb - 1) + rown[h] * kW + 4 * q);
     Vl[h] = lds4(slot(sL, zb - 1) + rown[h] * kW + 4 * q);
     Ph[h] = lds4(slot(sH, zb) + rown[h] * kW + 4 * q);
@@ -261,7 +276,7 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
     const float* cH = slot(sH, p);
     const float* cL = slot(sL, p);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < ROWS; ++h) {
       Mh[h] = Vh[h]; Ml[h] = Vl[h];
       Vh[h] = Ph[h]; Vl[h] = Pl[h];
       Ph[h] = lds4(slot(sH, p + 1) + rown[h] * kW + 4 * q);
@@ -269,7 +284,7 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
     }
     float r2 = 0.f, b2 = 0.f;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < ROWS; ++h) {
       const int r = rown[h], j = jown[h];
       const float* rowH = cH + r * kW;
       const float* rowL = cL + r * kW;
@@ -321,26 +336,32 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
 int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
                         Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int max_blocks) {
   if (!tile::level_ok(L)) return 0;
-  const int tiles = (L.n[0] / tile::kTX) * (L.n[1] / tile::kTY);
-  int chunk = tile::pick_zchunk(L, ncomp, 2 * cx.sms, 2);
+  // one row per thread: 8-row tiles, three CTAs per SM
+  constexpr int ROWS = 1;
+  using Sh = DefShape<ROWS>;
+  const int tiles = (L.n[0] / tile::kTX) * (L.n[1] / Sh::kRows);
+  int chunk = tile::pick_zchunk(L, ncomp, 3 * cx.sms, 2);
+  chunk = std::max(chunk, 1);
+  // pick_zchunk counts 128 x 16 tiles; there are twice as many 8-row tiles
+  chunk = std::min(L.n[2], 2 * chunk);
   while (tiles * ((L.n[2] + chunk - 1) / chunk) * ncomp > max_blocks && chunk < L.n[2]) ++chunk;
   const int nz = (L.n[2] + chunk - 1) / chunk;
   if (tiles * nz * ncomp > max_blocks) return 0;
   DefGeom G;
   static_cast<tile::Geom&>(G) = tile::geom(L, chunk);
+  G.nty = L.n[1] / Sh::kRows;
   G.ih_hi = (float)L.inv_h2;
   G.ih_lo = (float)(L.inv_h2 - (double)G.ih_hi);
   G.beta = R.beta;
-  const size_t smem = (size_t)2 * kDS * kDR * tile::kW * sizeof(float);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_defect_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_defect_tiled, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_defect_tiled<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmem);
+    cudaFuncSetAttribute(k_defect_tiled<ROWS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = true;
   }
   dim3 grid(tiles, nz, ncomp);
   cx.before(VSV_KCLASS_RESTRICT);
-  k_defect_tiled<<<grid, tile::kThreads, smem, cx.stream>>>(G, XH, XL, R, BL, OUT, partials);
+  k_defect_tiled<ROWS><<<grid, tile::kThreads, Sh::kSmem, cx.stream>>>(G, XH, XL, R, BL, OUT, partials);
   // x_hi, x_lo, b_hi (, b_lo) read, r written
   cx.after(VSV_KCLASS_RESTRICT, (BL.p[0] ? 20.0 : 16.0) * (double)L.cells() * ncomp);
   return tiles * nz;
@@ -355,14 +376,15 @@ void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E,
   cx.after(VSV_KCLASS_PROLONG, 20.0 * (double)n * ncomp);   // x_hi, x_lo, e read; x_hi, x_lo written
 }
 
-void launch_extrapolate_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> PH,
-                           Comp3<float> PL, long long n, int ncomp, int extrapolate) {
+void launch_extrapolate_rot_dw(Ctx& cx, Comp3<float> AH, Comp3<float> AL, Comp3<float> BH,
+                               Comp3<float> BL, Comp3<float> CH, Comp3<float> CL, long long n,
+                               int ncomp, int order) {
   const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
-  k_extrapolate_dw<<<grid, kBlock, 0, cx.stream>>>(XH, XL, PH, PL, n, extrapolate);
-  // x and the previous x (two words each) read, both written (only xp <- x without extrapolation)
-  cx.after(-1, (extrapolate ? 32.0 : 16.0) * (double)n * ncomp);
+  k_extrapolate_rot_dw<<<grid, kBlock, 0, cx.stream>>>(AH, AL, BH, BL, CH, CL, n, order);
+  // the history words read (A; A, B; A, B, C), the guess written (two words each)
+  cx.after(-1, 8.0 * (double)(order + 2) * (double)n * ncomp);
 }
 
 }  // namespace vsv

@@ -102,9 +102,10 @@ template <class T>
 void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Comp3<T> E, int ncomp);
 template <class T>
 void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp);
-// x <- 2 x - xp, xp <- old x (extrapolate = 1) or xp <- x (extrapolate = 0)
+// first guess of order 0..2 from (A, B, C) = (x^n, x^{n-1}, x^{n-2}), written into C
 template <class T>
-void launch_extrapolate(Ctx& cx, Comp3<T> X, Comp3<T> XP, long long n, int ncomp, int extrapolate);
+void launch_extrapolate_rot(Ctx& cx, Comp3<T> A, Comp3<T> B, Comp3<T> C, long long n, int ncomp,
+                            int order);
 template <class T>
 bool launch_coarse_solve(Ctx& cx, const Level& L, Comp3<T> E, Comp3<T> R, int ncomp, int sweeps,
                          double h2);
@@ -134,8 +135,10 @@ void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E,
 int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
                         Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials,
                         int max_blocks);
-void launch_extrapolate_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> PH,
-                           Comp3<float> PL, long long n, int ncomp, int extrapolate);
+// first guess of order 0..2 from (A, B, C) = (x^n, x^{n-1}, x^{n-2}), written into C
+void launch_extrapolate_rot_dw(Ctx& cx, Comp3<float> AH, Comp3<float> AL, Comp3<float> BH,
+                               Comp3<float> BL, Comp3<float> CH, Comp3<float> CL, long long n,
+                               int ncomp, int order);
 void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncomp, Scalars* S);
 
 // tiled restriction / prolongation for tile-aligned levels halved on every

@@ -228,18 +228,21 @@ __global__ void k_zero(Comp3<T> X, long long n) {
   if (t < n) X.at(blockIdx.y)[t] = (T)0;
 }
 
-// Linear extrapolation in time of the initial guess: x <- 2 x - xp and
-// xp <- x (old); with extrapolate = 0 only xp <- x.
+// First guess of a solve from the history, written into the oldest buffer
+// C: order 0: A; 1: 2A - B; 2: 3(A - B) + C (A = x^n, B = x^{n-1}, C =
+// x^{n-2}; extrapolation in time of order 0, 1, 2).
 template <class T>
-__global__ void k_extrapolate(Comp3<T> X, Comp3<T> XP, long long n, int extrapolate) {
+__global__ void k_extrapolate_rot(Comp3<T> A, Comp3<T> B, Comp3<T> C, long long n, int order) {
   const int comp = blockIdx.y;
-  T* __restrict__ x = X.at(comp);
-  T* __restrict__ xp = XP.at(comp);
+  const T* __restrict__ a = A.at(comp);
+  const T* __restrict__ b = B.at(comp);
+  T* __restrict__ c = C.at(comp);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    const T a = x[t];
-    if (extrapolate) x[t] = (T)2 * a - xp[t];
-    xp[t] = a;
+    const T x = a[t];
+    if (order == 0) c[t] = x;
+    else if (order == 1) c[t] = (T)2 * x - b[t];
+    else c[t] = (T)3 * (x - b[t]) + c[t];
   }
 }
 
@@ -678,12 +681,14 @@ void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp) {
 }
 
 template <class T>
-void launch_extrapolate(Ctx& cx, Comp3<T> X, Comp3<T> XP, long long n, int ncomp, int extrapolate) {
+void launch_extrapolate_rot(Ctx& cx, Comp3<T> A, Comp3<T> B, Comp3<T> C, long long n, int ncomp,
+                            int order) {
   const long long b = std::min<long long>(blocks_for(n), 4LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
-  k_extrapolate<T><<<grid, kBlock, 0, cx.stream>>>(X, XP, n, extrapolate);
-  cx.after(-1, (extrapolate ? 4.0 : 2.0) * (double)sizeof(T) * (double)n * ncomp);
+  k_extrapolate_rot<T><<<grid, kBlock, 0, cx.stream>>>(A, B, C, n, order);
+  // the history words read (A; A, B; A, B, C), the guess written
+  cx.after(-1, (double)(order + 2) * (double)sizeof(T) * (double)n * ncomp);
 }
 
 template <class T>
@@ -734,7 +739,7 @@ void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncom
                                          Comp3<T>, int, bool);                                     \
   template void launch_prolong_add<T>(Ctx&, const Level&, const Level&, Comp3<T>, Comp3<T>, int);  \
   template void launch_zero<T>(Ctx&, Comp3<T>, long long, int);                                    \
-  template void launch_extrapolate<T>(Ctx&, Comp3<T>, Comp3<T>, long long, int, int);              \
+  template void launch_extrapolate_rot<T>(Ctx&, Comp3<T>, Comp3<T>, Comp3<T>, long long, int, int); \
   template bool launch_coarse_vcycle<T>(Ctx&, const CoarseCycle&, Comp3<T>, Comp3<T>, int);        \
   template bool launch_coarse_solve<T>(Ctx&, const Level&, Comp3<T>, Comp3<T>, int, int, double);  \
   template void launch_resid_norm<T>(Ctx&, const Level&, Comp3<T>, Rhs3<T>, int, bool, double*,    \
