@@ -92,13 +92,21 @@ typedef enum {
 
 /* Body-free flow.  u_max: Poiseuille maximum speed over the cells;
  * v_lo / v_hi: Couette wall speeds (along x) at the y = 0 and y = H walls;
- * eta: dynamic viscosity (eq. gen1). */
+ * eta: dynamic viscosity (eq. gen1).
+ * rho: fluid density.  0 (the paper's results) gives the non-inertial
+ * vorticity equation gen1.  rho > 0 selects the inertial variant of SM
+ * eq. 36, (rho / eta) d omega / dt - lap omega = -(1/eta) grad phi x grad mu,
+ * advanced by one backward-Euler step per time step:
+ * (lap - s) omega^{n+1} = f - s omega^n with s = rho / (eta dt), solved by the
+ * same multigrid with the shifted operator.  vsv_set_phi still starts from
+ * the non-inertial vorticity of phi^0.  rho < 0 or non-finite: VSV_EINVAL. */
 typedef struct {
   int kind;
   double u_max;
   double v_lo;
   double v_hi;
   double eta;
+  double rho;
 } vsv_flow_params;
 
 /* Free energy.  sigma: CH gradient coefficient; kappa, eps: Helfrich bending
@@ -152,12 +160,19 @@ typedef struct {
   double omega_sor;
   int variant;
   int extrapolate;
+  int fixed_cycles_psi;   /* > 0: fixed cycle count of the stream-vector solves
+                             (fixed_cycles then applies to the vorticity
+                             solves only); 0: same as fixed_cycles */
 } vsv_solver_params;
 
 /* Per-axis boundary of a standalone Poisson problem: periodic (1) or zero
- * Dirichlet data on the ghost nodes -1 and n (0).  Order x, y, z. */
+ * Dirichlet data on the ghost nodes -1 and n (0).  Order x, y, z.
+ * shift >= 0: solve the shifted problem (L_h - shift) x = rhs instead (the
+ * operator of one backward-Euler step of the inertial vorticity equation,
+ * SM eq. 36); 0 for the Poisson problem. */
 typedef struct {
   int periodic[3];
+  double shift;
 } vsv_bc;
 
 /* Observables (in-plane-shear section, results section, SM eq. 40). */
@@ -222,8 +237,10 @@ vsv_status vsv_step(vsv_grid* g, int nsteps, double dt);
  * Model-B diffusion of the chosen mu, and the volume penalty). */
 vsv_status vsv_stability_limit(const vsv_grid* g, double* dt_max);
 
-/* Standalone Poisson solve L_h x = rhs on this grid's shape with boundary
- * `bc`, spacing h, using the grid's solver and precision.  rhs and x are
+/* Standalone Poisson solve L_h x = rhs (or (L_h - bc->shift) x = rhs) on
+ * this grid's shape with boundary `bc`, spacing h, using the grid's solver
+ * and precision.  All-periodic boundaries need shift > 0 (else VSV_EINVAL,
+ * as for a negative or non-finite shift).  rhs and x are
  * [nz][ny][nx] arrays of dtype on host or device; x holds the initial guess
  * on entry.  Uses the grid's scratch (it clobbers the grid's flow
  * perturbation of component z; call vsv_set_phi again afterwards to resume

@@ -65,6 +65,7 @@ class Workload:
     seed: int
     body: dict = field(default_factory=dict)   # geometry actually drawn
     phi0: Optional[np.ndarray] = None          # float64 [nz][ny][nx]
+    rho: float = 0.0                           # fluid density (0: no inertia)
 
     @property
     def z_periodic(self) -> bool:

@@ -20,8 +20,12 @@ caller, see ``boundary_term``).  Two exact methods:
   2 cos(pi (k+1)/(n+1)) - 2; the periodic one by the discrete Fourier
   transform with eigenvalue 2 cos(2 pi k / n) - 2.
 
-Pinned by: sin-product eigenvectors (closed form), agreement of the two
-methods, pure-loop assembly on tiny grids.
+The inertial variant (SM eq. 36) needs the shifted operator L_h - s I
+(s >= 0): the same two methods with every eigenvalue lowered by s, or the
+matrix with s subtracted on the diagonal.
+
+Pinned by: sin-product eigenvectors (closed form, with and without a
+shift), agreement of the two methods, pure-loop assembly on tiny grids.
 """
 from __future__ import annotations
 
@@ -64,8 +68,11 @@ def apply_poisson(x: np.ndarray, h: float, periodic) -> np.ndarray:
     return lap(pad_homogeneous(x, periodic), h)
 
 
-def solve_poisson_dense(b: np.ndarray, h: float, periodic) -> np.ndarray:
+def solve_poisson_dense(b: np.ndarray, h: float, periodic, shift: float = 0.0) -> np.ndarray:
+    """(L_h - shift I) x = b by a sparse direct solve of the assembled matrix."""
     L = poisson_matrix(b.shape, h, periodic)
+    if shift:
+        L = L - shift * sp.identity(L.shape[0], format="csr")
     x = spla.spsolve(L.tocsc(), b.reshape(-1))
     return np.asarray(x).reshape(b.shape)
 
@@ -77,11 +84,12 @@ def _eigenvalues(n: int, h: float, periodic: bool) -> np.ndarray:
     return (2.0 * np.cos(np.pi * (k + 1.0) / (n + 1.0)) - 2.0) / (h * h)
 
 
-def solve_poisson(b: np.ndarray, h: float, periodic) -> np.ndarray:
-    """Exact solve by eigen-decomposition (see module docstring)."""
+def solve_poisson(b: np.ndarray, h: float, periodic, shift: float = 0.0) -> np.ndarray:
+    """Exact solve of (L_h - shift I) x = b by eigen-decomposition (see
+    module docstring)."""
     nz, ny, nx = b.shape
     px, py, pz = periodic
-    if px and py and pz:
+    if px and py and pz and shift <= 0.0:
         raise ValueError("all-periodic Poisson problem is singular")
     X = np.array(b, dtype=np.float64, copy=True)
     dirichlet_axes = [ax for ax, per in ((2, px), (1, py), (0, pz)) if not per]
@@ -92,7 +100,7 @@ def solve_poisson(b: np.ndarray, h: float, periodic) -> np.ndarray:
         X = sfft.fftn(X, axes=periodic_axes)
     lam = (_eigenvalues(nz, h, pz)[:, None, None]
            + _eigenvalues(ny, h, py)[None, :, None]
-           + _eigenvalues(nx, h, px)[None, None, :])
+           + _eigenvalues(nx, h, px)[None, None, :]) - shift
     X = X / lam
     if periodic_axes:
         X = sfft.ifftn(X, axes=periodic_axes).real
@@ -109,8 +117,10 @@ def boundary_term(ghost_yz: np.ndarray, shape, h: float, z_periodic: bool) -> np
 
 
 def solve_flow_component(f: np.ndarray, ghost_yz: np.ndarray, h: float,
-                         z_periodic: bool) -> np.ndarray:
-    """Solve L_h u = f for one Cartesian component with Dirichlet wall data
-    ``ghost_yz`` and periodic x (and z when ``z_periodic``)."""
+                         z_periodic: bool, shift: float = 0.0) -> np.ndarray:
+    """Solve (L_h - shift I) u = f for one Cartesian component with Dirichlet
+    wall data ``ghost_yz`` and periodic x (and z when ``z_periodic``).  The
+    shift does not couple neighbours, so the wall data enter exactly as for
+    L_h."""
     rhs = f - boundary_term(ghost_yz, f.shape, h, z_periodic)
-    return solve_poisson(rhs, h, (True, False, z_periodic))
+    return solve_poisson(rhs, h, (True, False, z_periodic), shift)

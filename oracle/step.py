@@ -19,6 +19,15 @@ Stokes for the current interface); advection uses the velocity of the
 previous stream vector, as the segregated order implies; the initial state
 solves 5-8 for phi^0 with gamma_A = 0 (A = A0).
 
+Inertial variant (SM eq. 36, density rho > 0): the vorticity obeys
+(rho / eta) d omega / dt - lap omega = -f, a heat equation.  Reading: one
+backward-Euler step per time step, so step 7 becomes
+
+  7'. (lap - s) omega^{n+1} = f - s omega^n,  s = rho / (eta dt),
+
+with the same wall data; phi and psi are unchanged.  The initial vorticity
+is the non-inertial (Stokes) solution for phi^0.  rho = 0 is eq. gen1.
+
 Pinned by the module pins of grid / poisson / flow / free_energy, by the
 Couette and Poiseuille body-free steady states, by the closed-form
 advection of a sine profile, by the free-energy dissipation identity and by a
@@ -56,6 +65,7 @@ class OracleParams:
     k_area: float
     k_vol: float
     mu_prefactor_half: bool = False
+    rho: float = 0.0            # fluid density; > 0 selects SM eq. 36
 
     @property
     def z_periodic(self):
@@ -67,7 +77,8 @@ def params_from_workload(w) -> OracleParams:
     return OracleParams(nx=w.nx, ny=w.ny, nz=w.nz, h=w.h, flow_kind=w.flow_kind,
                         u_max=w.u_max, v_lo=w.v_lo, v_hi=w.v_hi, eta=w.eta,
                         fe_kind=w.fe_kind, sigma=w.sigma, kappa=w.kappa, eps=w.eps,
-                        mobility=w.mobility, k_area=w.k_area, k_vol=w.k_vol)
+                        mobility=w.mobility, k_area=w.k_area, k_vol=w.k_vol,
+                        rho=getattr(w, "rho", 0.0))
 
 
 @dataclass
@@ -109,10 +120,22 @@ def vorticity_source(phi, mu, p):
     return [fx, fy, fz]
 
 
-def flow_solve(phi, mu, p, bf):
-    """Steps 6-8: source, vorticity and stream-vector solves."""
+def inertial_shift(p, dt) -> float:
+    """s = rho / (eta dt) of the backward-Euler vorticity step (0: Stokes)."""
+    return p.rho / (p.eta * dt) if p.rho > 0.0 else 0.0
+
+
+def flow_solve(phi, mu, p, bf, omega_prev=None, dt=None):
+    """Steps 6-8: source, vorticity and stream-vector solves.  With
+    omega_prev and p.rho > 0 the vorticity solve is the backward-Euler step
+    7' of the inertial variant."""
     f = vorticity_source(phi, mu, p)
-    omega = [solve_flow_component(f[c], bf.omega_b[c], p.h, p.z_periodic) for c in range(3)]
+    s = inertial_shift(p, dt) if omega_prev is not None else 0.0
+    if s > 0.0:
+        omega = [solve_flow_component(f[c] - s * omega_prev[c], bf.omega_b[c], p.h,
+                                      p.z_periodic, shift=s) for c in range(3)]
+    else:
+        omega = [solve_flow_component(f[c], bf.omega_b[c], p.h, p.z_periodic) for c in range(3)]
     psi = [solve_flow_component(-omega[c], bf.psi_b[c], p.h, p.z_periodic) for c in range(3)]
     return omega, psi
 
@@ -149,7 +172,7 @@ def step(st: OracleState, dt: float) -> OracleState:
     V_new = volume(phi_new, p.h)
     gamma_a = area_multiplier(p.k_area, A_new, st.A0, p.eps)
     mu_new = _mu(phi_new, p, gamma_a)
-    omega, psi = flow_solve(phi_new, mu_new, p, st.bf)
+    omega, psi = flow_solve(phi_new, mu_new, p, st.bf, omega_prev=st.omega, dt=dt)
     st.phi, st.mu, st.omega, st.psi = phi_new, mu_new, omega, psi
     st.V, st.A, st.gamma_a, st.lambda_v = V_new, A_new, gamma_a, lam_v
     st.t += dt

@@ -85,6 +85,10 @@ struct vsv_grid {
   double* scratch1 = nullptr;
 
   std::vector<Level> flow_levels;
+  // inertial variant: the hierarchy of L_h - s, s = rho / (eta dt), for the
+  // vorticity solves, rebuilt when dt changes
+  std::vector<Level> omega_levels;
+  double omega_dt = 0.0;
   int* flag_host = nullptr;        // pinned copy of the device non-finite flag
   cudaEvent_t flag_event = nullptr;
   bool flag_pending = false;
@@ -240,15 +244,18 @@ bool z_periodic(const vsv_grid* g) {
 void set_reciprocals(Level& L) {
   const int d2 = 2 * (L.act[0] + L.act[1] + L.act[2]);
   for (int q = 0; q < 7; ++q) {
-    const double cd = (double)d2 + L.alpha * q;
-    const float cf = (float)d2 + L.alphaf * (float)q;
+    const double cd = (double)d2 + L.alpha * q + L.sh2;
+    const float cf = (float)d2 + L.alphaf * (float)q + L.sh2f;
     L.rcd[q] = cd > 0 ? 1.0 / cd : 0.0;
     L.rcf[q] = cf > 0 ? 1.0f / cf : 0.0f;
+    L.cdh[q] = (float)cd;
+    L.cdl[q] = (float)(cd - (double)L.cdh[q]);
   }
 }
 
+// shift: s of the operator L_h - s (0 for the Poisson problems)
 std::vector<Level> build_levels(int nx, int ny, int nz, double h, const int per[3], int max_levels,
-                                int cap_levels) {
+                                int cap_levels, double shift = 0.0) {
   std::vector<Level> lv;
   Level L{};
   L.n[0] = nx; L.n[1] = ny; L.n[2] = nz;
@@ -260,6 +267,8 @@ std::vector<Level> build_levels(int nx, int ny, int nz, double h, const int per[
   L.inv_h2 = 1.0 / (h * h);
   L.alphaf = 0.f;
   L.inv_h2f = (float)L.inv_h2;
+  L.sh2 = shift * h * h;
+  L.sh2f = (float)L.sh2;
   set_reciprocals(L);
   lv.push_back(L);
   const int maxl = std::min(std::max(max_levels, 1), cap_levels);
@@ -283,6 +292,8 @@ std::vector<Level> build_levels(int nx, int ny, int nz, double h, const int per[
     C.inv_h2 = 1.0 / (h * h * p2 * p2);
     C.alphaf = (float)C.alpha;
     C.inv_h2f = (float)C.inv_h2;
+    C.sh2 = shift * h * h * p2 * p2;
+    C.sh2f = (float)C.sh2;
     set_reciprocals(C);
     lv.push_back(C);
   }
@@ -635,6 +646,8 @@ void guess_from_history(vsv_grid* g, void* x[3], void* xp[3], void* xpp[3], floa
 vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
   const vsv_solver_params& s = g->sol;
   const int fixed = initial ? 0 : s.fixed_cycles;
+  const int fixed_psi = (initial || !s.fixed_cycles) ? fixed
+                        : (s.fixed_cycles_psi > 0 ? s.fixed_cycles_psi : s.fixed_cycles);
   const int order = std::min(s.extrapolate, g->hist);
   if (!initial)
     guess_from_history<float>(g, g->om, g->om_prev, g->om_prev2, g->om_lo, g->om_prev_lo,
@@ -642,7 +655,9 @@ vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
   Comp3<float> OH = comp3<float>(g->om[0], g->om[1], g->om[2]);
   Comp3<float> OL = comp3<float>(g->om_lo[0], g->om_lo[1], g->om_lo[2]);
   Comp3<float> FL = comp3<float>(g->f_lo[0], g->f_lo[1], g->f_lo[2]);
-  vsv_status st = solve_dc(g, g->flow_levels, OH, OL, rhs_omega<float>(g), FL, 3, fixed, s.tol,
+  const std::vector<Level>& lvo =
+      (!initial && g->flow.rho > 0.0 && !g->omega_levels.empty()) ? g->omega_levels : g->flow_levels;
+  vsv_status st = solve_dc(g, lvo, OH, OL, rhs_omega<float>(g), FL, 3, fixed, s.tol,
                            s.max_cycles, s.check_every, &g->last_cycles[0], &g->last_relres[0]);
   if (st != VSV_OK) return st;
   if (!initial)
@@ -651,7 +666,7 @@ vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
   Comp3<float> PH = comp3<float>(g->ps[0], g->ps[1], g->ps[2]);
   Comp3<float> PL = comp3<float>(g->ps_lo[0], g->ps_lo[1], g->ps_lo[2]);
   // rhs of the stream-vector problem: -(omega'_hi + omega'_lo) - s_psi
-  st = solve_dc(g, g->flow_levels, PH, PL, rhs_psi<float>(g), OL, 3, fixed, s.tol, s.max_cycles,
+  st = solve_dc(g, g->flow_levels, PH, PL, rhs_psi<float>(g), OL, 3, fixed_psi, s.tol, s.max_cycles,
                 s.check_every, &g->last_cycles[1], &g->last_relres[1]);
   g->hist = initial ? 0 : std::min(g->hist + 1, 2);
   return st;
@@ -662,17 +677,21 @@ vsv_status flow_solves(vsv_grid* g, bool initial) {
   if constexpr (std::is_same<T, float>::value) return flow_solves_mixed(g, initial);
   const vsv_solver_params& s = g->sol;
   const int fixed = initial ? 0 : s.fixed_cycles;
+  const int fixed_psi = (initial || !s.fixed_cycles) ? fixed
+                        : (s.fixed_cycles_psi > 0 ? s.fixed_cycles_psi : s.fixed_cycles);
   const int order = std::min(s.extrapolate, g->hist);
   if (!initial)
     guess_from_history<T>(g, g->om, g->om_prev, g->om_prev2, nullptr, nullptr, nullptr, order);
   Comp3<T> O = comp3<T>(g->om[0], g->om[1], g->om[2]);
-  vsv_status st = solve<T>(g, g->flow_levels, O, rhs_omega<T>(g), 3, s.kind, fixed, s.tol,
+  const std::vector<Level>& lvo =
+      (!initial && g->flow.rho > 0.0 && !g->omega_levels.empty()) ? g->omega_levels : g->flow_levels;
+  vsv_status st = solve<T>(g, lvo, O, rhs_omega<T>(g), 3, s.kind, fixed, s.tol,
                            s.max_cycles, s.check_every, &g->last_cycles[0], &g->last_relres[0]);
   if (st != VSV_OK) return st;
   if (!initial)
     guess_from_history<T>(g, g->ps, g->ps_prev, g->ps_prev2, nullptr, nullptr, nullptr, order);
   Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
-  st = solve<T>(g, g->flow_levels, Pp, rhs_psi<T>(g), 3, s.kind, fixed, s.tol, s.max_cycles,
+  st = solve<T>(g, g->flow_levels, Pp, rhs_psi<T>(g), 3, s.kind, fixed_psi, s.tol, s.max_cycles,
                 s.check_every, &g->last_cycles[1], &g->last_relres[1]);
   g->hist = initial ? 0 : std::min(g->hist + 1, 2);
   return st;
@@ -728,6 +747,24 @@ vsv_status step_impl(vsv_grid* g, double dt) {
   refresh_phase<T>(g, 0);
   // 6: source f = grad phi x grad mu / eta - s_omega
   launch_flow_source<T>(g, P);
+  // inertial variant (SM eq. 36), backward Euler: (L_h - s) omega'^{n+1} =
+  // f - s_omega - s omega'^n, s = rho / (eta dt); omega' still holds omega'^n
+  if (g->flow.rho > 0.0) {
+    const double s = g->flow.rho / (g->flow.eta * dt);
+    if (g->omega_dt != dt || g->omega_levels.empty()) {
+      const int per[3] = {1, 0, z_periodic(g) ? 1 : 0};
+      g->omega_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels,
+                                     g->mg_nlev_cap, s);
+      g->omega_dt = dt;
+    }
+    Comp3<T> F = comp3<T>(g->f[0], g->f[1], g->f[2]);
+    Comp3<T> O = comp3<T>(g->om[0], g->om[1], g->om[2]);
+    if constexpr (std::is_same<T, float>::value)
+      launch_axpy_dw(g->cx, F, comp3<float>(g->f_lo[0], g->f_lo[1], g->f_lo[2]), O,
+                     comp3<float>(g->om_lo[0], g->om_lo[1], g->om_lo[2]), -s, g->N, 3);
+    else
+      launch_axpy<T>(g->cx, F, O, -s, g->N, 3);
+  }
   CKL();
   // 7-8: vorticity then stream-vector Poisson solves
   vsv_status st = flow_solves<T>(g, false);
@@ -1007,6 +1044,7 @@ void default_solver(vsv_solver_params* s, int prec) {
   s->omega_sor = 0.0;
   s->variant = 0;
   s->extrapolate = 1;
+  s->fixed_cycles_psi = 0;
 }
 
 }  // namespace
@@ -1045,7 +1083,7 @@ vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int prec
       g->cx.sms = sms;
   }
   carve(nx, ny, nz, precision, g, g->ws);
-  g->flow = vsv_flow_params{VSV_QUIESCENT, 0.0, 0.0, 0.0, 1.0};
+  g->flow = vsv_flow_params{VSV_QUIESCENT, 0.0, 0.0, 0.0, 1.0, 0.0};
   g->fe = vsv_fe_params{VSV_CAHN_HILLIARD, 1.0, 0.0, 1.0, 1.0, 0.0, 0.0, 0};
   default_solver(&g->sol, precision);
   if (cudaMemsetAsync(g->S, 0, sizeof(Scalars), g->cx.stream) != cudaSuccess) {
@@ -1077,13 +1115,15 @@ vsv_status vsv_default_solver(vsv_solver_params* out, int precision) {
 
 vsv_status vsv_set_flow(vsv_grid* g, const vsv_flow_params* fp) {
   if (!g || !fp) return VSV_EINVAL;
-  if (fp->kind < 0 || fp->kind > VSV_QUIESCENT || !(fp->eta > 0))
+  if (fp->kind < 0 || fp->kind > VSV_QUIESCENT || !(fp->eta > 0) || !(fp->rho >= 0) ||
+      !std::isfinite(fp->rho))
     return fail(g, VSV_EINVAL, "invalid flow parameters%s");
   const bool zper = fp->kind == VSV_COUETTE || fp->kind == VSV_POISEUILLE_PLANAR;
   if (zper && g->nz > 1 && g->nz % 2) return fail(g, VSV_EINVAL, "periodic z needs even nz%s");
   g->flow = *fp;
   const int per[3] = {1, 0, zper ? 1 : 0};
   g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);
+  g->omega_levels.clear();
   vsv_status st = build_base_flow(g);
   if (st != VSV_OK) return st;
   g->flow_set = true;
@@ -1108,7 +1148,7 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
   if (sp->kind == VSV_SOLVER_SOR && g->prec != VSV_FP64)
     return fail(g, VSV_EINVAL, "SOR is provided for the FP64 precision only%s");
   if (sp->nu1 < 0 || sp->nu2 < 0 || sp->nu1 + sp->nu2 < 1 || sp->coarse_sweeps < 1 ||
-      sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->max_levels < 1 || !(sp->tol >= 0) ||
+      sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->fixed_cycles_psi < 0 || sp->max_levels < 1 || !(sp->tol >= 0) ||
       sp->variant < 0 || sp->variant > 1 || sp->extrapolate < 0 || sp->extrapolate > 2)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
@@ -1116,6 +1156,7 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
   if (g->flow_set) {
     const int per[3] = {1, 0, z_periodic(g) ? 1 : 0};
     g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);
+    g->omega_levels.clear();   // rebuilt with the new depth at the next step
   }
   return VSV_OK;
 }
@@ -1205,10 +1246,13 @@ vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, i
   const int n[3] = {g->nx, g->ny, g->nz};
   for (int a = 0; a < 3; ++a)
     if (per[a] && n[a] > 1 && n[a] % 2) return fail(g, VSV_EINVAL, "periodic axes need even extent%s");
-  if (per[0] && per[1] && per[2]) return fail(g, VSV_EINVAL, "all-periodic problem is singular%s");
+  if (!(bc->shift >= 0) || !std::isfinite(bc->shift))
+    return fail(g, VSV_EINVAL, "shift must be finite and >= 0%s");
+  if (per[0] && per[1] && per[2] && bc->shift == 0.0)
+    return fail(g, VSV_EINVAL, "all-periodic problem is singular%s");
   g->err.clear();
   std::vector<Level> lv = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels,
-                                       g->mg_nlev_cap);
+                                       g->mg_nlev_cap, bc->shift);
   vsv_status st;
   g->phi_set = false;
   auto run = [&](auto tag) -> vsv_status {

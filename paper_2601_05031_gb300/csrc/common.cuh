@@ -15,6 +15,9 @@ constexpr int kBlock = 256;
 // l the wall lies between the ghost and the first cell, and the ghost value
 // is the linear extrapolation through zero at the wall:
 //   ghost = -alpha_l * (adjacent cell),  alpha_l = (2^l - 1) / (2^l + 1).
+// A level may carry a diagonal shift: the operator is L_h - s (the
+// backward-Euler vorticity step of the inertial variant), which adds
+// sh2 = s h_l^2 to the diagonal coefficient 2 d + alpha * nwall.
 struct Level {
   int n[3];          // nx, ny, nz
   int per[3];        // 1 = periodic axis
@@ -23,10 +26,16 @@ struct Level {
   double inv_h2;     // 1 / h_l^2
   float alphaf;      // the same in FP32 (FP32 kernels never touch FP64 units)
   float inv_h2f;
-  // 1 / (2 d + alpha * nwall) for nwall = 0..6 wall neighbours: the smoothers
-  // multiply by these instead of dividing (same table in every sweep kernel)
+  double sh2;        // s h_l^2 (0: plain Poisson)
+  float sh2f;
+  // 1 / (2 d + alpha * nwall + sh2) for nwall = 0..6 wall neighbours: the
+  // smoothers multiply by these instead of dividing (same table in every
+  // sweep kernel)
   float rcf[7];
   double rcd[7];
+  // the diagonal coefficient 2 d + alpha * nwall + sh2 as an FP32 pair
+  // (hi + lo) for the exact defect
+  float cdh[7], cdl[7];
   __host__ __device__ long long cells() const { return (long long)n[0] * n[1] * n[2]; }
 };
 
@@ -37,6 +46,9 @@ template <> __host__ __device__ inline double lv_rc<double>(const Level& L, int 
 template <class T> __host__ __device__ inline T lv_alpha(const Level& L);
 template <> __host__ __device__ inline float lv_alpha<float>(const Level& L) { return L.alphaf; }
 template <> __host__ __device__ inline double lv_alpha<double>(const Level& L) { return L.alpha; }
+template <class T> __host__ __device__ inline T lv_sh2(const Level& L);
+template <> __host__ __device__ inline float lv_sh2<float>(const Level& L) { return L.sh2f; }
+template <> __host__ __device__ inline double lv_sh2<double>(const Level& L) { return L.sh2; }
 template <class T> __host__ __device__ inline T lv_ih2(const Level& L);
 template <> __host__ __device__ inline float lv_ih2<float>(const Level& L) { return L.inv_h2f; }
 template <> __host__ __device__ inline double lv_ih2<double>(const Level& L) { return L.inv_h2; }

@@ -44,7 +44,8 @@ __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<floa
   const float* __restrict__ S = R.s_at(comp);
   float* __restrict__ out = OUT.at(comp);
   const float beta = R.beta;
-  const float dcoef = (float)(2 * (L.act[0] + L.act[1] + L.act[2]));
+  // diagonal 2 d + s h^2 as a pair (alpha = 0 on the finest level)
+  const float dch = L.cdh[0], dcl = L.cdl[0];
   double rr = 0.0, bb = 0.0;
   for (int row = blockIdx.x; row < ny * nz; row += gridDim.x) {
     const int j = row % ny, k = row / ny;
@@ -66,8 +67,9 @@ __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<floa
         lh.add(H.get(i, j, k - 1)); lh.add(H.get(i, j, k + 1));
         llo += Lo.get(i, j, k - 1) + Lo.get(i, j, k + 1);
       }
-      lh.add_scaled(-dcoef, H.a[t]);
-      llo = __fmaf_rn(-dcoef, Lo.a[t], llo);
+      lh.add_scaled(-dch, H.a[t]);
+      if (dcl != 0.f) lh.add(-dcl * H.a[t]);   // adding -0 would change nothing
+      llo = __fmaf_rn(-dch, Lo.a[t], llo);
       // L x = (lh.hi + lh.lo + llo) * inv_h2, leading product split exactly
       const float p = __fmul_rn(ih_hi, lh.hi);
       const float pe = __fmaf_rn(ih_hi, lh.hi, -p);
@@ -142,6 +144,23 @@ __global__ void k_extrapolate_rot_dw(Comp3<float> AH, Comp3<float> AL, Comp3<flo
   }
 }
 
+// (YH, YL) += a (XH, XL) in double-word arithmetic, a given in FP64 and
+// split into an FP32 pair (the inertial right-hand side f - s omega'^n).
+__global__ void k_axpy_dw(Comp3<float> YH, Comp3<float> YL, Comp3<float> XH, Comp3<float> XL,
+                          float a_hi, float a_lo, long long n) {
+  const int comp = blockIdx.y;
+  float* __restrict__ yh = YH.at(comp);
+  float* __restrict__ yl = YL.at(comp);
+  const float* __restrict__ xh = XH.at(comp);
+  const float* __restrict__ xl = XL.at(comp);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const FF v = ff_add(FF{yh[t], yl[t]}, ff_mul(FF{xh[t], xl[t]}, FF{a_hi, a_lo}));
+    yh[t] = v.hi;
+    yl[t] = v.lo;
+  }
+}
+
 void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
                       Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int nblocks) {
   const float ih_hi = (float)L.inv_h2, ih_lo = (float)(L.inv_h2 - (double)ih_hi);
@@ -173,6 +192,7 @@ struct DefShape {
 
 struct DefGeom : tile::Geom {
   float ih_hi, ih_lo, beta;
+  float dch, dcl;   // diagonal 6 + s h^2 as a pair (alpha = 0 on the finest level)
 };
 
 __device__ __forceinline__ float comp4(const float4& v, int o) {
@@ -185,7 +205,7 @@ __device__ __forceinline__ float defect_cell(float xmh, float xph, float ymh, fl
                                              float zph, float ch, float xml, float xpl, float yml,
                                              float ypl, float zml, float zpl, float cl, float b1,
                                              float b2, bool has_b2, float s, float ih_hi,
-                                             float ih_lo) {
+                                             float ih_lo, float dch, float dcl) {
   CascadeSum lh(0.f);
   lh.add(xmh); lh.add(xph);
   lh.add(ymh); lh.add(yph);
@@ -194,8 +214,9 @@ __device__ __forceinline__ float defect_cell(float xmh, float xph, float ymh, fl
   llo += xml + xpl;
   llo += yml + ypl;
   llo += zml + zpl;
-  lh.add_scaled(-6.f, ch);
-  llo = __fmaf_rn(-6.f, cl, llo);
+  lh.add_scaled(-dch, ch);
+  if (dcl != 0.f) lh.add(-dcl * ch);   // adding -0 would change nothing
+  llo = __fmaf_rn(-dch, cl, llo);
   const float p = __fmul_rn(ih_hi, lh.hi);
   const float pe = __fmaf_rn(ih_hi, lh.hi, -p);
   const float rest = __fmaf_rn(ih_hi, __fadd_rn(lh.lo, llo), __fmaf_rn(ih_lo, lh.hi, pe));
@@ -306,7 +327,7 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
         res[o] = defect_cell(xmh, xph, comp4(Uh, o), comp4(Dh, o), comp4(Mh[h], o), comp4(Ph[h], o),
                              comp4(Vh[h], o), xml, xpl, comp4(Ul, o), comp4(Dl, o), comp4(Ml[h], o),
                              comp4(Pl[h], o), comp4(Vl[h], o), b1v, b2v, bl != nullptr, s, G.ih_hi,
-                             G.ih_lo);
+                             G.ih_lo, G.dch, G.dcl);
         if (partials) {
           const float bv = b1v + (bl ? b2v : 0.f) + s;
           r2 = __fmaf_rn(res[o], res[o], r2);
@@ -353,6 +374,8 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
   G.ih_hi = (float)L.inv_h2;
   G.ih_lo = (float)(L.inv_h2 - (double)G.ih_hi);
   G.beta = R.beta;
+  G.dch = L.cdh[0];
+  G.dcl = L.cdl[0];
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_defect_tiled<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmem);
@@ -385,6 +408,16 @@ void launch_extrapolate_rot_dw(Ctx& cx, Comp3<float> AH, Comp3<float> AL, Comp3<
   k_extrapolate_rot_dw<<<grid, kBlock, 0, cx.stream>>>(AH, AL, BH, BL, CH, CL, n, order);
   // the history words read (A; A, B; A, B, C), the guess written (two words each)
   cx.after(-1, 8.0 * (double)(order + 2) * (double)n * ncomp);
+}
+
+void launch_axpy_dw(Ctx& cx, Comp3<float> YH, Comp3<float> YL, Comp3<float> XH, Comp3<float> XL,
+                    double a, long long n, int ncomp) {
+  const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8LL * cx.sms);
+  dim3 grid((unsigned)b, ncomp);
+  const float a_hi = (float)a, a_lo = (float)(a - (double)a_hi);
+  cx.before(-1);
+  k_axpy_dw<<<grid, kBlock, 0, cx.stream>>>(YH, YL, XH, XL, a_hi, a_lo, n);
+  cx.after(-1, 24.0 * (double)n * ncomp);   // y, x read, y written (two words each)
 }
 
 }  // namespace vsv

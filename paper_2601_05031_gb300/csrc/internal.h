@@ -102,6 +102,9 @@ template <class T>
 void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Comp3<T> E, int ncomp);
 template <class T>
 void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp);
+// Y += a X
+template <class T>
+void launch_axpy(Ctx& cx, Comp3<T> Y, Comp3<T> X, double a, long long n, int ncomp);
 // first guess of order 0..2 from (A, B, C) = (x^n, x^{n-1}, x^{n-2}), written into C
 template <class T>
 void launch_extrapolate_rot(Ctx& cx, Comp3<T> A, Comp3<T> B, Comp3<T> C, long long n, int ncomp,
@@ -140,6 +143,9 @@ void launch_extrapolate_rot_dw(Ctx& cx, Comp3<float> AH, Comp3<float> AL, Comp3<
                                Comp3<float> BL, Comp3<float> CH, Comp3<float> CL, long long n,
                                int ncomp, int order);
 void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncomp, Scalars* S);
+// (YH, YL) += a (XH, XL), double-word
+void launch_axpy_dw(Ctx& cx, Comp3<float> YH, Comp3<float> YL, Comp3<float> XH, Comp3<float> XL,
+                    double a, long long n, int ncomp);
 
 // tiled restriction / prolongation for tile-aligned levels halved on every
 // axis (transfer.cu); false: not applicable, nothing launched

@@ -80,21 +80,22 @@ __device__ __forceinline__ T resid_plain(const T* __restrict__ x, const Level& L
                                          long long c, T b) {
   int nwall;
   const T s = sum_nb(x, L, i, j, k, c, nwall);
-  T coef = (T)(2 * n_active(L)) + lv_alpha<T>(L) * (T)nwall;
+  T coef = (T)(2 * n_active(L)) + lv_alpha<T>(L) * (T)nwall + lv_sh2<T>(L);
   return b - (s - coef * x[c]) * lv_ih2<T>(L);
 }
 
 // Exact defect in FP32 storage: every term of b - (sum_nb - coef x_c)/h^2 is
 // accumulated by cascaded summation, so the result equals the real-number
-// defect up to one final rounding (coef is an integer on the fine level).
+// defect up to one final rounding (the diagonal coefficient enters as an
+// FP32 pair; it is the integer 2 d on the fine level of a Poisson problem).
 __device__ __forceinline__ float resid_exact(const float* __restrict__ x, const Level& L, int i,
                                              int j, int k, long long c, float b, float ih_hi,
                                              float ih_lo) {
   int nwall;
   CascadeSum t(0.f);
   for_nb(x, L, i, j, k, c, nwall, [&](float v) { t.add(v); });
-  const float coef = (float)(2 * n_active(L)) + L.alphaf * (float)nwall;
-  t.add_scaled(-coef, x[c]);
+  t.add_scaled(-L.cdh[nwall], x[c]);
+  if (L.cdl[nwall] != 0.f) t.add(-L.cdl[nwall] * x[c]);   // adding -0 would change nothing
   if (ih_hi == 1.f && ih_lo == 0.f) {
     CascadeSum r(b);
     r.add(-t.hi);
@@ -246,6 +247,17 @@ __global__ void k_extrapolate_rot(Comp3<T> A, Comp3<T> B, Comp3<T> C, long long 
   }
 }
 
+// y += a x (the inertial right-hand side f - s omega'^n, FP64 path).
+template <class T>
+__global__ void k_axpy(Comp3<T> Y, Comp3<T> X, T a, long long n) {
+  const int comp = blockIdx.y;
+  T* __restrict__ y = Y.at(comp);
+  const T* __restrict__ x = X.at(comp);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] += a * x[t];
+}
+
 // Coarsest level: e = 0, then `sweeps` red-black Gauss-Seidel sweeps in
 // shared memory by one block per component.
 template <class T>
@@ -389,7 +401,7 @@ __global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<
     if (zm >= 0) ld2(row(j0 + jy, zm) + i0, fzm[jy][0], fzm[jy][1]); else fzm[jy][0] = fzm[jy][1] = (T)0;
     if (zp >= 0) ld2(row(j0 + jy, zp) + i0, fzp[jy][0], fzp[jy][1]); else fzp[jy][0] = fzp[jy][1] = (T)0;
   }
-  const T ih2 = lv_ih2<T>(F), al = lv_alpha<T>(F);
+  const T ih2 = lv_ih2<T>(F), al = lv_alpha<T>(F), sh = lv_sh2<T>(F);
   T acc = 0;
 #pragma unroll
   for (int kz = 0; kz < 2; ++kz)
@@ -406,7 +418,7 @@ __global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<
         const int nwall = (ix == 0 && xm < 0) + (ix == 1 && xp < 0) + (jy == 0 && ym < 0) +
                           (jy == 1 && yp < 0) + (kz == 0 && zm < 0) + (kz == 1 && zp < 0);
         const T s = ((v_xm + v_xp) + (v_ym + v_yp)) + (v_zm + v_zp);
-        acc += b[kz][jy][ix] - (s - ((T)6 + al * (T)nwall) * c[kz][jy][ix]) * ih2;
+        acc += b[kz][jy][ix] - (s - ((T)6 + al * (T)nwall + sh) * c[kz][jy][ix]) * ih2;
       }
   RC.at(comp)[lin(I, J, K, C.n[0], C.n[1])] = acc * (T)0.125;
 }
@@ -692,6 +704,15 @@ void launch_extrapolate_rot(Ctx& cx, Comp3<T> A, Comp3<T> B, Comp3<T> C, long lo
 }
 
 template <class T>
+void launch_axpy(Ctx& cx, Comp3<T> Y, Comp3<T> X, double a, long long n, int ncomp) {
+  const long long b = std::min<long long>(blocks_for(n), 4LL * cx.sms);
+  dim3 grid((unsigned)b, ncomp);
+  cx.before(-1);
+  k_axpy<T><<<grid, kBlock, 0, cx.stream>>>(Y, X, (T)a, n);
+  cx.after(-1, 3.0 * (double)sizeof(T) * (double)n * ncomp);
+}
+
+template <class T>
 bool launch_coarse_solve(Ctx& cx, const Level& L, Comp3<T> E, Comp3<T> R, int ncomp, int sweeps,
                          double h2) {
   const long long n = L.cells();
@@ -739,6 +760,7 @@ void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncom
                                          Comp3<T>, int, bool);                                     \
   template void launch_prolong_add<T>(Ctx&, const Level&, const Level&, Comp3<T>, Comp3<T>, int);  \
   template void launch_zero<T>(Ctx&, Comp3<T>, long long, int);                                    \
+  template void launch_axpy<T>(Ctx&, Comp3<T>, Comp3<T>, double, long long, int);                  \
   template void launch_extrapolate_rot<T>(Ctx&, Comp3<T>, Comp3<T>, Comp3<T>, long long, int, int); \
   template bool launch_coarse_vcycle<T>(Ctx&, const CoarseCycle&, Comp3<T>, Comp3<T>, int);        \
   template bool launch_coarse_solve<T>(Ctx&, const Level&, Comp3<T>, Comp3<T>, int, int, double);  \

@@ -18,7 +18,7 @@ constexpr int kRS = 5;         // ring slots
 constexpr int kRStage = (kRR * kNV + kThreads - 1) / kThreads;
 
 struct RGeom : Geom {
-  float ih2, alpha, beta;
+  float ih2, alpha, beta, sh2;
   int cnx, cny;   // coarse extents (x, y)
 };
 
@@ -115,7 +115,7 @@ k_restrict_tiled(RGeom G, Comp3<float> X, Rhs3<float> R, Comp3<float> RC) {
         const float xp = o == 3 ? Rx : c4(Vz[h], o + 1);
         const float s = ((xm + xp) + (c4(U, o) + c4(D, o))) + (c4(Mz[h], o) + c4(Pz[h], o));
         const float b = G.beta * c4(Bc[h], o) + s_;
-        const float r = b - (s - (6.f + G.alpha * (float)nwall) * c4(Vz[h], o)) * G.ih2;
+        const float r = b - (s - (6.f + G.alpha * (float)nwall + G.sh2) * c4(Vz[h], o)) * G.ih2;
         if (o < 2) acc0 += r; else acc1 += r;
       }
     }
@@ -293,6 +293,7 @@ bool launch_restrict_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float>
   static_cast<Geom&>(G) = geom(F, even_chunk(F, ncomp, cx.sms, 2));
   G.ih2 = F.inv_h2f;
   G.alpha = F.alphaf;
+  G.sh2 = F.sh2f;
   G.beta = R.beta;
   G.cnx = C.n[0];
   G.cny = C.n[1];

@@ -42,7 +42,7 @@ class Simulation:
         return s
 
     def configure(self, w, solver=None):
-        V.vsv_set_flow(self.g, w.flow_kind, w.u_max, w.v_lo, w.v_hi, w.eta)
+        V.vsv_set_flow(self.g, w.flow_kind, w.u_max, w.v_lo, w.v_hi, w.eta, getattr(w, "rho", 0.0))
         V.vsv_set_free_energy(self.g, w.fe_kind, w.sigma, w.kappa, w.eps, w.mobility, w.k_area,
                               w.k_vol)
         if solver is not None:
@@ -87,12 +87,12 @@ class Simulation:
         return V.vsv_get_stress_profile(self.g, self.ny)
 
     def solve_poisson(self, rhs, x0=None, periodic=(True, False, False), tol=1e-12,
-                      max_cycles=200, check=True):
+                      max_cycles=200, check=True, shift=0.0):
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)
         x = np.zeros_like(rhs) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
         st, cyc, rr = V.vsv_solve_poisson(self.g, rhs.ctypes.data, x.ctypes.data,
                                           V.VSV_DTYPE_F64, 0, periodic, tol, max_cycles,
-                                          check=check)
+                                          check=check, shift=shift)
         return x, cyc, rr, st
 
     def stability_limit(self):

@@ -33,7 +33,7 @@ VSV_DTYPE_F32, VSV_DTYPE_F64 = 0, 1
 
 class vsv_flow_params(C.Structure):
     _fields_ = [("kind", C.c_int), ("u_max", C.c_double), ("v_lo", C.c_double),
-                ("v_hi", C.c_double), ("eta", C.c_double)]
+                ("v_hi", C.c_double), ("eta", C.c_double), ("rho", C.c_double)]
 
 
 class vsv_fe_params(C.Structure):
@@ -46,11 +46,12 @@ class vsv_solver_params(C.Structure):
     _fields_ = [("kind", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("fixed_cycles", C.c_int), ("check_every", C.c_int), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("max_levels", C.c_int), ("coarse_sweeps", C.c_int),
-                ("omega_sor", C.c_double), ("variant", C.c_int), ("extrapolate", C.c_int)]
+                ("omega_sor", C.c_double), ("variant", C.c_int), ("extrapolate", C.c_int),
+                ("fixed_cycles_psi", C.c_int)]
 
 
 class vsv_bc(C.Structure):
-    _fields_ = [("periodic", C.c_int * 3)]
+    _fields_ = [("periodic", C.c_int * 3), ("shift", C.c_double)]
 
 
 class vsv_diag(C.Structure):
@@ -173,8 +174,8 @@ def vsv_destroy(g):
     return lib().vsv_destroy(g)
 
 
-def vsv_set_flow(g, kind, u_max=0.0, v_lo=0.0, v_hi=0.0, eta=1.0):
-    p = vsv_flow_params(kind, u_max, v_lo, v_hi, eta)
+def vsv_set_flow(g, kind, u_max=0.0, v_lo=0.0, v_hi=0.0, eta=1.0, rho=0.0):
+    p = vsv_flow_params(kind, u_max, v_lo, v_hi, eta, rho)
     return _check(g, lib().vsv_set_flow(g, C.byref(p)), "vsv_set_flow")
 
 
@@ -210,8 +211,9 @@ def vsv_stability_limit(g) -> float:
     return d.value
 
 
-def vsv_solve_poisson(g, rhs_ptr, x_ptr, dtype, on_device, periodic, tol, max_cycles, check=True):
-    bc = vsv_bc((C.c_int * 3)(*[int(bool(p)) for p in periodic]))
+def vsv_solve_poisson(g, rhs_ptr, x_ptr, dtype, on_device, periodic, tol, max_cycles, check=True,
+                      shift=0.0):
+    bc = vsv_bc((C.c_int * 3)(*[int(bool(p)) for p in periodic]), shift)
     cyc, rr = C.c_int(), C.c_double()
     st = lib().vsv_solve_poisson(g, C.c_void_p(rhs_ptr), C.c_void_p(x_ptr), dtype, on_device,
                                  C.byref(bc), tol, max_cycles, C.byref(cyc), C.byref(rr))

@@ -101,6 +101,80 @@ def test_matrix_equals_stencil_and_loops():
     assert np.max(np.abs(xb - x)) < 1e-11
 
 
+# ------------------------------------------------------------ inertial variant (SM eq. 36)
+def _eigvec(shape, h, periodic, ks, phase=0.3):
+    """Sin/cos-product eigenvector of the 7-point operator and its eigenvalue
+    (Dirichlet data on the ghost nodes, or wrap)."""
+    nz, ny, nx = shape
+    lam = 0.0
+    facs = []
+    for n, per, kk in ((nx, periodic[0], ks[0]), (ny, periodic[1], ks[1]), (nz, periodic[2], ks[2])):
+        j = np.arange(n)
+        if per:
+            th = 2 * math.pi * kk / n
+            facs.append(np.cos(th * j + phase))
+        else:
+            th = math.pi * kk / (n + 1)
+            facs.append(np.sin(th * (j + 1)))
+        lam += (2 * math.cos(th) - 2) / h ** 2
+    return facs[2][:, None, None] * facs[1][None, :, None] * facs[0][None, None, :], lam
+
+
+@pytest.mark.parametrize("periodic", [(True, False, False), (True, False, True), (True, True, True)])
+def test_shifted_eigenvector(periodic):
+    """(L_h - s) u = (lambda - s) u for the product eigenvectors; both exact
+    solvers invert the shifted operator, also with every axis periodic."""
+    shape, h, s = (6, 5, 8), 0.7, 3.7
+    u, lam = _eigvec(shape, h, periodic, (2, 1, 1))
+    Lu = apply_poisson(u, h, periodic) - s * u
+    assert np.max(np.abs(Lu - (lam - s) * u)) < 1e-12
+    for solver in (solve_poisson, solve_poisson_dense):
+        x = solver((lam - s) * u, h, periodic, s)
+        assert np.max(np.abs(x - u)) < 1e-12
+
+
+def test_inertial_vorticity_decays_as_backward_euler():
+    """No body, walls at rest: one backward-Euler step of SM eq. 36 maps a
+    vorticity eigenmode to s / (s - lambda) times itself (s = rho / (eta dt)),
+    and the stream vector follows as psi = -omega / lambda."""
+    nx, ny, nz = 8, 7, 6
+    p = _params(nx, ny, nz, flow_kind=inputs.QUIESCENT, eta=0.7, rho=2.0)
+    st = init_state(p, _no_body(nx, ny, nz))
+    u, lam = _eigvec((nz, ny, nx), 1.0, (True, False, False), (1, 2, 1))
+    amp = (0.3, -0.1, 0.2)
+    st.omega = [a * u for a in amp]
+    dt = 0.05
+    s = p.rho / (p.eta * dt)
+    g = s / (s - lam)
+    assert 0.0 < g < 1.0
+    for k in range(1, 4):
+        step(st, dt)
+        assert np.max(np.abs(st.phi - 1.0)) == 0.0
+        for c in range(3):
+            w = amp[c] * g ** k * u
+            assert np.max(np.abs(st.omega[c] - w)) < 1e-13
+            assert np.max(np.abs(st.psi[c] + w / lam)) < 1e-12
+
+
+def test_inertial_step_tends_to_stokes_linearly_in_density():
+    """As rho -> 0 the inertial step tends to the non-inertial one (eq.
+    gen1): the difference in omega is proportional to rho."""
+    w = inputs.droplet_duct(nx=12, ny=8, nz=8, radius=2.5, dt=0.01)
+    base = dict(nx=w.nx, ny=w.ny, nz=w.nz, h=1.0, flow_kind=w.flow_kind, u_max=w.u_max,
+                v_lo=0.0, v_hi=0.0, eta=w.eta, fe_kind=w.fe_kind, sigma=w.sigma, kappa=0.0,
+                eps=w.eps, mobility=1.0, k_area=0.0, k_vol=0.0)
+    om = {}
+    for rho in (0.0, 1e-6, 2e-6):
+        st = init_state(OracleParams(**base, rho=rho), w.phi0)
+        st.omega = [o * 0.5 for o in st.omega]   # start away from the Stokes vorticity
+        step(st, w.dt)
+        om[rho] = np.stack(st.omega)
+    d1 = np.max(np.abs(om[1e-6] - om[0.0]))
+    d2 = np.max(np.abs(om[2e-6] - om[0.0]))
+    assert d1 > 0.0
+    assert abs(d2 / d1 - 2.0) < 1e-3
+
+
 # ------------------------------------------------------------ base flows (C-P3..5)
 def _no_body(nx, ny, nz):
     return np.ones((nz, ny, nx))
