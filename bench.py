@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead of the 512x256x256 line: N independent seeded problems of "
+                         "a parameter sweep stepped together (batched CUDA graph)")
     return ap.parse_args()
 
 
@@ -339,6 +342,77 @@ def cpu_baseline(w_full, steps=3):
                       "solves, numpy FP64, one thread"}
 
 
+def run_batch(args, ws, rank, local):
+    """N independent problems (sizes 32-192 x 32-96 x 32-96, droplets and
+    vesicles, Ca log-uniform 0.05-5) stepped as one batch: a captured CUDA
+    graph of six steps of all of them, each on its own stream.  Beside it,
+    the same problems stepped one call per grid (streams, no graph)."""
+    import torch
+    import inputs
+    from paper_2601_05031_gb300 import build as B
+    from paper_2601_05031_gb300 import vsv as V
+    from paper_2601_05031_gb300.sim import Simulation, Batch
+    if not B.up_to_date():
+        B.build()
+    torch.cuda.set_device(local)
+    wl = inputs.batch_instances(n=args.batch, seed=rank)
+    cells = sum(w.ncells for w in wl)
+    dt = wl[0].dt
+
+    def make():
+        sims = []
+        for w in wl:
+            s = Simulation.from_workload(w, V.VSV_MIXED, stream=torch.cuda.Stream())
+            sp = s.solver_params()
+            sp.fixed_cycles = args.cycles
+            sp.extrapolate = args.extrapolate
+            V.vsv_set_solver(s.g, sp)
+            s.set_phi(w.phi0)
+            sims.append(s)
+        return sims
+
+    steps = max(6, (args.steps // 6) * 6)
+    sims = make()
+    batch = Batch(sims)
+    batch.step(max(args.warmup, 2) + 6, dt)        # warm-up, history, capture
+    torch.cuda.synchronize()
+    launches0 = sum(s.kernel_launches() for s in sims)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(batch.stream)
+        batch.step(steps, dt)
+        e1.record(batch.stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = sum(s.kernel_launches() for s in sims) - launches0
+    batch.close()
+    # the same work without the graph: one vsv_step call per grid and step
+    for s in sims:
+        s.step(2, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for s in sims:
+            s.step(1, dt, check=False)
+    torch.cuda.synchronize()
+    ms_plain = (time.perf_counter() - t0) * 1e3
+    for s in sims:
+        s.close()
+    value = cells * steps / (ms * 1e-3) / 1e6
+    out = {"metric": "Mcell-steps/s (batch of independent problems)", "value": round(value, 3),
+           "unit": "Mcell-steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+           "ms_per_step": round(ms / steps, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded parameter sweep)",
+           "config": {"workload": f"batch_{args.batch}_instances", "instances": args.batch,
+                      "cells": cells, "solver": f"{args.cycles} V(2,2)-cycles per solve",
+                      "launch": "one captured CUDA graph of 6 steps of every instance"},
+           "gpu_launches": int(launches), "clocks": clk.summary(),
+           "without_graph": {"value": round(cells * steps / (ms_plain * 1e-3) / 1e6, 3),
+                             "unit": "Mcell-steps/s",
+                             "launch": "one vsv_step call per instance and step"}}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -377,6 +451,9 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.batch > 0:
+        run_batch(args, ws, rank, local)
         return
     run_gpu(args, ws, rank, local)
 

@@ -330,6 +330,37 @@ vsv_status vsv_profile_enable(vsv_grid* g, int kernel_class, int enable);
 vsv_status vsv_profile_read(vsv_grid* g, int kernel_class, double* total_ms, int64_t* launches,
                             double* alg_bytes);
 
+/* Batched stepping of independent grids.  The paper simulates one body at a
+ * time and has no counterpart; this serves many small problems at once (a
+ * parameter sweep), where launch latency, not bandwidth, bounds a step.
+ *
+ * vsv_batch_create groups n existing grids (each with its own workspace and
+ * stream, vsv_set_phi done, solver in fixed_cycles mode) under a master
+ * stream `cuda_stream`, which must be a created stream (graphs cannot be
+ * captured on the legacy default stream).  The batch does not own the
+ * grids: destroy it before them.  VSV_EINVAL on n < 1, NULL or repeated
+ * grids, or a NULL / legacy master stream.
+ *
+ * vsv_batch_step advances every grid by nsteps steps of dt.  Each grid first
+ * takes plain steps, on its own stream, until its solution history is full
+ * and its phase fields are current.  Then one CUDA graph is captured with
+ * six steps of every grid, each grid on its own branch so that small grids
+ * run concurrently, and replayed; six steps bring the phi double buffer and
+ * the three-buffer solution histories back to the captured layout.  Steps
+ * left over run plainly.  The graph is captured again when dt changes.
+ * Results are bit-identical to vsv_step on each grid.  Every grid must
+ * satisfy its stability bound (else VSV_EUNSTABLE), must use fixed_cycles
+ * > 0 (else VSV_EINVAL), and must not be profiling (else VSV_ESTATE).
+ * Work already queued on a grid's stream completes first, and later work on
+ * it waits for the batch.  Non-finite flags are not read per step: call
+ * vsv_check on a grid for them.
+ *
+ * vsv_batch_destroy frees the graph and the events (NULL is a no-op). */
+typedef struct vsv_batch vsv_batch;
+vsv_status vsv_batch_create(vsv_batch** out, vsv_grid* const* grids, int n, void* cuda_stream);
+vsv_status vsv_batch_step(vsv_batch* b, int nsteps, double dt);
+vsv_status vsv_batch_destroy(vsv_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -177,13 +177,14 @@ def droplet_duct(nx=48, ny=24, nz=24, radius=6.0, seed=0, nsteps=10, dt=0.01,
 
 def vesicle(nx, ny, nz, flow_kind, vr, eps, seed=0, nsteps=10, dt=1e-4,
             u_max=0.05, v_wall=0.05, ca=1.0, kappa=1.0, k_area=0.05,
-            vol_factor=0.5, b_range=(0.11, 0.16), name="vesicle") -> Workload:
+            vol_factor=0.5, b_range=(0.11, 0.16), name="vesicle", b_ref=None) -> Workload:
     """Prolate Helfrich vesicle with seeded equatorial semi-axis b ~
-    U(b_range) * ny and long axis a (along x) fixed by the reduced volume.
-    eta from Ca = tau_kappa * shear_rate, tau_kappa = eta V / kappa."""
+    U(b_range) * b_ref (default ny) and long axis a (along x) fixed by the
+    reduced volume.  eta from Ca = tau_kappa * shear_rate, tau_kappa = eta V /
+    kappa."""
     h = 1.0
     rng = np.random.default_rng(seed)
-    b = float(rng.uniform(*b_range)) * ny * h
+    b = float(rng.uniform(*b_range)) * (ny if b_ref is None else b_ref) * h
     a = prolate_axis_for(vr, b)
     zper = flow_kind in (COUETTE, POISEUILLE_PLANAR)
     c = channel_centre(nx, ny, nz, h, zper)
@@ -226,6 +227,38 @@ def vesicle_couette_512x256x256(seed=0, nx=512, ny=256, nz=256, nsteps=500) -> W
     """Helfrich vesicle, V_r = 0.9, eps = 1.5, Couette walls at +-0.05."""
     return vesicle(nx, ny, nz, COUETTE, 0.9, 1.5, seed=seed, nsteps=nsteps,
                    name=f"vesicle_couette_{nx}x{ny}x{nz}")
+
+
+def batch_instances(n=64, seed=0, dt=1e-4, nsteps=60) -> list:
+    """Independent problems of a parameter sweep (batched stepping): sizes
+    multiples of 8 with ny, nz in [32, 96] and nx in [32, 192]; Ca log-uniform
+    in [0.05, 5]; half spherical Cahn-Hilliard droplets (radius a quarter of
+    the smallest extent), half Helfrich vesicles with V_r ~ U(0.7, 0.98) and
+    the body sized by the smallest extent (nx / 3 for the long axis); duct
+    Poiseuille or Couette flow, 50/50.  All with eps = 1 and step dt."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        ny = 8 * int(rng.integers(4, 13))
+        nz = 8 * int(rng.integers(4, 13))
+        nx = 8 * int(rng.integers(4, 25))
+        ca = float(math.exp(rng.uniform(math.log(0.05), math.log(5.0))))
+        flow = POISEUILLE_DUCT if rng.uniform() < 0.5 else COUETTE
+        if rng.uniform() < 0.5:
+            r = 0.25 * min(nx, ny, nz)
+            w = droplet_duct(nx=nx, ny=ny, nz=nz, radius=r, seed=seed, nsteps=nsteps, dt=dt,
+                             ca=ca, flow_kind=flow, name=f"batch{i}_droplet_{nx}x{ny}x{nz}")
+            if flow == COUETTE:   # Ca = eta gamma_dot R / gamma with the wall shear rate
+                shear = 2.0 * 0.05 / channel_extent(ny, 1.0, True)
+                w.u_max, w.v_lo, w.v_hi = 0.0, -0.05, 0.05
+                w.eta = ca * surface_tension(w.sigma) / (shear * r)
+        else:
+            vr = float(rng.uniform(0.7, 0.98))
+            ref = min(ny, nz, nx / 3.0)
+            w = vesicle(nx, ny, nz, flow, vr, 1.0, seed=seed + i, nsteps=nsteps, dt=dt, ca=ca,
+                        b_range=(0.2, 0.3), b_ref=ref, name=f"batch{i}_vesicle_{nx}x{ny}x{nz}")
+        out.append(w)
+    return out
 
 
 def random_field(shape, seed, scale=1.0) -> np.ndarray:

@@ -1237,6 +1237,220 @@ vsv_status vsv_step(vsv_grid* g, int nsteps, double dt) {
   return VSV_OK;
 }
 
+// ---------------------------------------------------------------- batches
+}  // extern "C"
+
+struct vsv_batch {
+  std::vector<vsv_grid*> grids;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double dt = 0.0;
+  std::vector<long long> launches_per_replay;
+  std::vector<double> bytes_per_replay;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+};
+
+namespace {
+
+constexpr int kReplaySteps = 6;   // phi ping-pong (2) x history rotation (3)
+
+// the host-side state a step advances
+struct GridHostState {
+  int cur, hist;
+  void *om[3], *ps[3], *om_prev[3], *ps_prev[3], *om_prev2[3], *ps_prev2[3];
+  float *om_lo[3], *ps_lo[3], *om_prev_lo[3], *ps_prev_lo[3], *om_prev2_lo[3], *ps_prev2_lo[3];
+  double time;
+  long long steps, launches;
+  double bytes;
+};
+
+GridHostState save_host(const vsv_grid* g) {
+  GridHostState s;
+  s.cur = g->cur;
+  s.hist = g->hist;
+  for (int c = 0; c < 3; ++c) {
+    s.om[c] = g->om[c]; s.ps[c] = g->ps[c];
+    s.om_prev[c] = g->om_prev[c]; s.ps_prev[c] = g->ps_prev[c];
+    s.om_prev2[c] = g->om_prev2[c]; s.ps_prev2[c] = g->ps_prev2[c];
+    s.om_lo[c] = g->om_lo[c]; s.ps_lo[c] = g->ps_lo[c];
+    s.om_prev_lo[c] = g->om_prev_lo[c]; s.ps_prev_lo[c] = g->ps_prev_lo[c];
+    s.om_prev2_lo[c] = g->om_prev2_lo[c]; s.ps_prev2_lo[c] = g->ps_prev2_lo[c];
+  }
+  s.time = g->time;
+  s.steps = g->steps;
+  s.launches = g->cx.launches;
+  s.bytes = g->cx.bytes_total;
+  return s;
+}
+
+bool same_layout(const GridHostState& a, const GridHostState& b) {
+  if (a.cur != b.cur || a.hist != b.hist) return false;
+  for (int c = 0; c < 3; ++c)
+    if (a.om[c] != b.om[c] || a.ps[c] != b.ps[c] || a.om_prev[c] != b.om_prev[c] ||
+        a.ps_prev[c] != b.ps_prev[c] || a.om_prev2[c] != b.om_prev2[c] ||
+        a.ps_prev2[c] != b.ps_prev2[c] || a.om_lo[c] != b.om_lo[c] || a.ps_lo[c] != b.ps_lo[c] ||
+        a.om_prev_lo[c] != b.om_prev_lo[c] || a.ps_prev_lo[c] != b.ps_prev_lo[c] ||
+        a.om_prev2_lo[c] != b.om_prev2_lo[c] || a.ps_prev2_lo[c] != b.ps_prev2_lo[c])
+      return false;
+  return true;
+}
+
+// A grid can be captured once its history and phase fields no longer
+// change the work a step enqueues.
+bool steady(const vsv_grid* g) { return g->hist == 2 && !g->phase_stale; }
+
+vsv_status step_one(vsv_grid* g, double dt) {
+  return g->prec == VSV_FP64 ? step_impl<double>(g, dt) : step_impl<float>(g, dt);
+}
+
+}  // namespace
+
+extern "C" {
+
+vsv_status vsv_batch_create(vsv_batch** out, vsv_grid* const* grids, int n, void* cuda_stream) {
+  if (!out || !grids || n < 1) return VSV_EINVAL;
+  *out = nullptr;
+  // graphs cannot be captured on the legacy default stream
+  if (cuda_stream == nullptr || (cudaStream_t)cuda_stream == cudaStreamLegacy) return VSV_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!grids[i]) return VSV_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (grids[j] == grids[i]) return VSV_EINVAL;
+  }
+  vsv_batch* b = new vsv_batch();
+  b->grids.assign(grids, grids + n);
+  b->stream = (cudaStream_t)cuda_stream;
+  b->join.resize(n, nullptr);
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < n && ok; ++i)
+    ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    vsv_batch_destroy(b);
+    return VSV_ECUDA;
+  }
+  *out = b;
+  return VSV_OK;
+}
+
+vsv_status vsv_batch_destroy(vsv_batch* b) {
+  if (!b) return VSV_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (auto e : b->join)
+    if (e) cudaEventDestroy(e);
+  delete b;
+  return VSV_OK;
+}
+
+vsv_status vsv_batch_step(vsv_batch* b, int nsteps, double dt) {
+  if (!b || nsteps < 0 || !(dt > 0)) return VSV_EINVAL;
+  const int n = (int)b->grids.size();
+  for (vsv_grid* g : b->grids) {
+    if (!g->phi_set) return fail(g, VSV_ESTATE, "vsv_set_phi must precede vsv_batch_step%s");
+    if (g->sol.fixed_cycles <= 0)
+      return fail(g, VSV_EINVAL, "batched steps need fixed_cycles > 0%s");
+    if (g->cx.prof_class >= 0) return fail(g, VSV_ESTATE, "profiling is on for a batched grid%s");
+    double lim;
+    vsv_stability_limit(g, &lim);
+    if (dt > lim) return fail(g, VSV_EUNSTABLE, "time step above the explicit stability bound%s");
+  }
+  int done = 0;
+  // plain steps until every grid is steady
+  while (done < nsteps) {
+    bool all = true;
+    for (vsv_grid* g : b->grids) all = all && steady(g);
+    if (all) break;
+    for (vsv_grid* g : b->grids) {
+      const vsv_status st = step_one(g, dt);
+      if (st != VSV_OK) return st;
+    }
+    ++done;
+  }
+  if (nsteps - done >= kReplaySteps && (!b->exec || b->dt != dt)) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    std::vector<GridHostState> saved;
+    for (vsv_grid* g : b->grids) saved.push_back(save_host(g));
+    cudaGraph_t graph = nullptr;
+    vsv_grid* g0 = b->grids[0];
+    const cudaError_t eb = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+    if (eb != cudaSuccess) {
+      cudaGetLastError();
+      return fail(g0, VSV_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(eb));
+    }
+    vsv_status st = VSV_OK;
+    cudaEventRecord(b->fork, b->stream);
+    for (vsv_grid* g : b->grids) cudaStreamWaitEvent(g->cx.stream, b->fork, 0);
+    for (int k = 0; k < kReplaySteps && st == VSV_OK; ++k)
+      for (vsv_grid* g : b->grids) {
+        st = step_one(g, dt);
+        if (st != VSV_OK) break;
+      }
+    for (int i = 0; i < n; ++i) {
+      cudaEventRecord(b->join[i], b->grids[i]->cx.stream);
+      cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+    b->launches_per_replay.assign(n, 0);
+    b->bytes_per_replay.assign(n, 0.0);
+    bool layout_ok = true;
+    for (int i = 0; i < n; ++i) {
+      vsv_grid* g = b->grids[i];
+      const GridHostState after = save_host(g);
+      layout_ok = layout_ok && same_layout(after, saved[i]);
+      b->launches_per_replay[i] = after.launches - saved[i].launches;
+      b->bytes_per_replay[i] = after.bytes - saved[i].bytes;
+      g->time = saved[i].time;   // the captured steps have not run yet
+      g->steps = saved[i].steps;
+      g->cx.launches = saved[i].launches;
+      g->cx.bytes_total = saved[i].bytes;
+    }
+    if (st != VSV_OK || ec != cudaSuccess || !layout_ok) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return st != VSV_OK ? st : fail(g0, VSV_ECUDA, "capture of the batched steps failed%s");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      b->exec = nullptr;
+      return fail(g0, VSV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    }
+    b->dt = dt;
+  }
+  if (nsteps - done >= kReplaySteps && b->exec) {
+    // work queued on the grids' streams first, then the replays, then the grids wait
+    for (int i = 0; i < n; ++i) {
+      cudaEventRecord(b->join[i], b->grids[i]->cx.stream);
+      cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    while (nsteps - done >= kReplaySteps) {
+      const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+      if (e != cudaSuccess)
+        return fail(b->grids[0], VSV_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+      for (int i = 0; i < n; ++i) {
+        vsv_grid* g = b->grids[i];
+        g->time += kReplaySteps * dt;
+        g->steps += kReplaySteps;
+        g->cx.launches += b->launches_per_replay[i];
+        g->cx.bytes_total += b->bytes_per_replay[i];
+      }
+      done += kReplaySteps;
+    }
+    cudaEventRecord(b->fork, b->stream);
+    for (vsv_grid* g : b->grids) cudaStreamWaitEvent(g->cx.stream, b->fork, 0);
+  }
+  for (; done < nsteps; ++done)
+    for (vsv_grid* g : b->grids) {
+      const vsv_status st = step_one(g, dt);
+      if (st != VSV_OK) return st;
+    }
+  return VSV_OK;
+}
+
 vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, int on_device,
                              const vsv_bc* bc, double tol, int max_cycles, int* cycles_out,
                              double* relres_out) {

@@ -36,8 +36,8 @@ class Simulation:
 
     # ------------------------------------------------------------ set-up
     @classmethod
-    def from_workload(cls, w, precision=V.VSV_MIXED, solver=None, device="cuda:0"):
-        s = cls(w.nx, w.ny, w.nz, w.h, precision, device)
+    def from_workload(cls, w, precision=V.VSV_MIXED, solver=None, device="cuda:0", stream=None):
+        s = cls(w.nx, w.ny, w.nz, w.h, precision, device, stream)
         s.configure(w, solver)
         return s
 
@@ -108,6 +108,34 @@ class Simulation:
         if self.g is not None:
             V.vsv_destroy(self.g)
             self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent simulations stepped together through one captured CUDA
+    graph (vsv_batch_*).  Give each simulation its own stream so that the
+    small ones run concurrently; the batch orders itself after their queued
+    work and they after it."""
+
+    def __init__(self, sims, stream=None):
+        self.sims = list(sims)
+        dev = self.sims[0].device
+        # a stream of its own: graphs cannot be captured on the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        self.b = V.vsv_batch_create([s.g for s in self.sims], self.stream.cuda_stream)
+
+    def step(self, nsteps, dt):
+        return V.vsv_batch_step(self.b, nsteps, dt, grids=[s.g for s in self.sims])
+
+    def close(self):
+        if self.b is not None:
+            V.vsv_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

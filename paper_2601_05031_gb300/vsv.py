@@ -82,7 +82,8 @@ EXPORTS = [
     "vsv_stability_limit", "vsv_solve_poisson", "vsv_get_field", "vsv_set_field",
     "vsv_get_diagnostics", "vsv_get_stress_profile", "vsv_state_bytes", "vsv_get_state",
     "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_last_error", "vsv_kernel_launches",
-    "vsv_kernel_bytes", "vsv_profile_enable", "vsv_profile_read",
+    "vsv_kernel_bytes", "vsv_profile_enable", "vsv_profile_read", "vsv_batch_create",
+    "vsv_batch_step", "vsv_batch_destroy",
 ]
 
 
@@ -121,6 +122,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_kernel_bytes": (dbl, [vp]),
         "vsv_profile_enable": (i32, [vp, i32, i32]),
         "vsv_profile_read": (i32, [vp, i32, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl)]),
+        "vsv_batch_create": (i32, [C.POINTER(vp), C.POINTER(vp), i32, vp]),
+        "vsv_batch_step": (i32, [vp, i32, dbl]),
+        "vsv_batch_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -291,3 +295,25 @@ def vsv_profile_read(g, kclass, with_bytes=False):
     _check(g, lib().vsv_profile_read(g, kclass, C.byref(ms), C.byref(n), C.byref(b)),
            "vsv_profile_read")
     return (ms.value, n.value, b.value) if with_bytes else (ms.value, n.value)
+
+
+def vsv_batch_create(grids, stream_ptr):
+    """grids: vsv_grid handles (c_void_p); returns the batch handle."""
+    arr = (C.c_void_p * len(grids))(*[g.value if isinstance(g, C.c_void_p) else g for g in grids])
+    out = C.c_void_p()
+    st = lib().vsv_batch_create(C.byref(out), arr, len(grids), C.c_void_p(stream_ptr))
+    if st != VSV_OK:
+        raise VsvError(st, "vsv_batch_create")
+    return out
+
+
+def vsv_batch_step(b, nsteps, dt, grids=()):
+    st = lib().vsv_batch_step(b, nsteps, dt)
+    if st != VSV_OK:
+        msg = "; ".join(lib().vsv_last_error(g).decode() for g in grids)
+        raise VsvError(st, f"vsv_batch_step: {msg}")
+    return st
+
+
+def vsv_batch_destroy(b):
+    return lib().vsv_batch_destroy(b)

@@ -70,6 +70,16 @@ def test_null_handles_are_rejected(V):
     assert lib.vsv_check(None) == V.VSV_EINVAL
     assert lib.vsv_state_bytes(None) == 0
     assert lib.vsv_kernel_launches(None) == 0
+    assert lib.vsv_kernel_bytes(None) == 0.0
+    assert lib.vsv_batch_step(None, 1, 0.1) == V.VSV_EINVAL
+    assert lib.vsv_batch_destroy(None) == V.VSV_OK
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.vsv_batch_create(ctypes.byref(out), arr, 0, None) == V.VSV_EINVAL
+    assert lib.vsv_batch_create(ctypes.byref(out), arr, 1, None) == V.VSV_EINVAL
+    arr2 = (ctypes.c_void_p * 1)(1234)   # never dereferenced: the NULL stream is rejected first
+    assert lib.vsv_batch_create(ctypes.byref(out), arr2, 1, None) == V.VSV_EINVAL
+    assert out.value is None
     p = V.vsv_default_solver(V.VSV_MIXED)
     assert p.kind == V.VSV_SOLVER_MG and p.nu1 >= 1 and p.max_cycles > 0
 
@@ -78,7 +88,7 @@ def test_binding_structs_match_header_sizes(V):
     # field counts of the C structs as declared in the header
     txt = open(os.path.join(ROOT, "include", "vsv.h")).read()
     for cname, pyt in (("vsv_flow_params", V.vsv_flow_params), ("vsv_fe_params", V.vsv_fe_params),
-                       ("vsv_solver_params", V.vsv_solver_params)):
+                       ("vsv_solver_params", V.vsv_solver_params), ("vsv_bc", V.vsv_bc)):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + ";", txt).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         names = re.findall(r"\b([a-z_0-9]+)\s*(?:\[\d+\])?\s*[;,]", body)
