@@ -147,7 +147,7 @@ GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
 # scaled by the cells to the launch at hand.  From one ncu capture of the
 # current kernel; to be retaken (and set to None meanwhile) whenever
 # k_rbgs_fused changes.
-FUSED_SWEEP_TRAFFIC_PER_CELL = 692.0e6 / (512 * 256 * 128 * 3)
+FUSED_SWEEP_TRAFFIC_PER_CELL = None   # kernel changed since the last ncu capture
 
 
 def make_sim(w, prec, cycles, extrapolate=1):

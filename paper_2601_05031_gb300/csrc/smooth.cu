@@ -128,13 +128,15 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   da.init(G, x0, y0, kH, kRA);
   db.init(G, x0, y0, kH - 1, kRB);
 
-  // own rows and their 1 / diagonal for z-interior (0) and z-wall (1) planes
+  // own rows (2 ty and 2 ty + 1: each is the other's y neighbour, straight
+  // from registers) and their 1 / diagonal for z-interior (0) and z-wall (1)
+  // planes
   int rown[2], jown[2];
   float rco[2][2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    rown[h] = ty + 8 * h + kH;
-    jown[h] = y0 + ty + 8 * h;
+    rown[h] = 2 * ty + h + kH;
+    jown[h] = y0 + 2 * ty + h;
     const int yw = G.per_y ? 0 : (jown[h] == 0) + (jown[h] == G.ny - 1);
     rco[h][0] = rc_of(G, yw);
     rco[h][1] = rc_of(G, yw + 1);
@@ -196,30 +198,36 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     // ---- red cells of plane p: own groups, halo rows, halo columns
     if (!ghost_plane(p)) {
       const int zw = zwall(p);
-      // both rows' operands first, then both updates, then the stores (the
-      // stores could alias the loads as far as the compiler knows); the two
-      // rows are 8 apart, so they share the parity
-      const int par = (jown[0] + p) & 1;
-      float4 U[2], D[2], Bv[2];
+      // rows 2ty and 2ty+1 have opposite parity; each row's red cells need the
+      // other row's black values (registers) and one more row from shared
+      // memory; the x neighbours come from the adjacent lanes' registers
+      // (black values, which this phase does not change) and, at the tile
+      // edges, from the staged halo columns
+      const int par = (jown[0] + p) & 1;          // red offset of row 2ty
       float Lx[2], Rx[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const float* row = cA + rown[h] * kW;
-        U[h] = lds4(row - kW + 4 * q);
-        D[h] = lds4(row + kW + 4 * q);
-        Lx[h] = row[4 * q - 1];
-        Rx[h] = row[4 * q + 4];
-        Bv[h] = lds4(cB + (rown[h] - 1) * kW + 4 * q);
+        Lx[h] = __shfl_up_sync(0xffffffffu, V[h].w, 1);
+        Rx[h] = __shfl_down_sync(0xffffffffu, V[h].x, 1);
+        if (gx == 0) Lx[h] = cA[rown[h] * kW + kHX - 1];
+        if (gx == 31) Rx[h] = cA[rown[h] * kW + kHX + kTX];
       }
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        V[h] = rb_group(V[h], U[h], D[h], M[h], P[h], Lx[h], Rx[h], Bv[h], par, beta,
-                        srow(jown[h], p), h2, zw ? rco[h][1] : rco[h][0]);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float* dst = cA + rown[h] * kW + 4 * q;
-        if (par == 0) { dst[0] = V[h].x; dst[2] = V[h].z; }
-        else { dst[1] = V[h].y; dst[3] = V[h].w; }
+      const float4 U0 = lds4(cA + (rown[0] - 1) * kW + 4 * q);
+      const float4 D1 = lds4(cA + (rown[1] + 1) * kW + 4 * q);
+      const float4 B0 = lds4(cB + (rown[0] - 1) * kW + 4 * q);
+      const float4 B1 = lds4(cB + (rown[1] - 1) * kW + 4 * q);
+      const float4 V0 = V[0];
+      V[0] = rb_group(V[0], U0, V[1], M[0], P[0], Lx[0], Rx[0], B0, par, beta, srow(jown[0], p), h2,
+                      zw ? rco[0][1] : rco[0][0]);
+      V[1] = rb_group(V[1], V0, D1, M[1], P[1], Lx[1], Rx[1], B1, 1 - par, beta, srow(jown[1], p),
+                      h2, zw ? rco[1][1] : rco[1][0]);
+      {
+        float* dst = cA + rown[0] * kW + 4 * q;
+        if (par == 0) { dst[0] = V[0].x; dst[2] = V[0].z; }
+        else { dst[1] = V[0].y; dst[3] = V[0].w; }
+        dst += kW;
+        if (par == 0) { dst[1] = V[1].y; dst[3] = V[1].w; }
+        else { dst[0] = V[1].x; dst[2] = V[1].z; }
       }
       if (ty == 0 || ty == 7) {   // halo rows y0 - 1 and y0 + kTY
         const int r = (ty == 0) ? 1 : kRA - 2;
@@ -261,22 +269,26 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       const int zw = zwall(qp);
       const float* cAq = slotA(qp);
       const float* cBq = slotB(qp);
-      const int par = (jown[0] + qp + 1) & 1;
-      float4 U[2], D[2], Bv[2];
-      float Lx[2], Rx[2];
+      const int par = (jown[0] + qp + 1) & 1;     // black offset of row 2ty
+      float Lq[2], Rq[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const float* row = cAq + rown[h] * kW;
-        U[h] = lds4(row - kW + 4 * q);
-        D[h] = lds4(row + kW + 4 * q);
-        Lx[h] = row[4 * q - 1];
-        Rx[h] = row[4 * q + 4];
-        Bv[h] = lds4(cBq + (rown[h] - 1) * kW + 4 * q);
+        Lq[h] = __shfl_up_sync(0xffffffffu, M[h].w, 1);
+        Rq[h] = __shfl_down_sync(0xffffffffu, M[h].x, 1);
+        if (gx == 0) Lq[h] = cAq[rown[h] * kW + kHX - 1];
+        if (gx == 31) Rq[h] = cAq[rown[h] * kW + kHX + kTX];
       }
+      const float4 U0 = lds4(cAq + (rown[0] - 1) * kW + 4 * q);
+      const float4 D1 = lds4(cAq + (rown[1] + 1) * kW + 4 * q);
+      const float4 Bq0 = lds4(cBq + (rown[0] - 1) * kW + 4 * q);
+      const float4 Bq1 = lds4(cBq + (rown[1] - 1) * kW + 4 * q);
+      const float4 M0 = M[0];
+      M[0] = rb_group(M[0], U0, M[1], MM[0], V[0], Lq[0], Rq[0], Bq0, par, beta,
+                      srow(jown[0], qp), h2, zw ? rco[0][1] : rco[0][0]);
+      M[1] = rb_group(M[1], M0, D1, MM[1], V[1], Lq[1], Rq[1], Bq1, 1 - par, beta,
+                      srow(jown[1], qp), h2, zw ? rco[1][1] : rco[1][0]);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        M[h] = rb_group(M[h], U[h], D[h], MM[h], V[h], Lx[h], Rx[h], Bv[h], par, beta,
-                        srow(jown[h], qp), h2, zw ? rco[h][1] : rco[h][0]);
         const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
         if constexpr (UPD) {
           const FF v0 = ff_add_f(FF{XHp[h].x, XLp[h].x}, M[h].x);
