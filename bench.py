@@ -142,12 +142,12 @@ GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
          2: "extrapolated guess 3x^n - 3x^(n-1) + x^(n-2)"}
 
 # DRAM traffic of the finest-level fused sweeps per launch, averaged over the
-# four sweeps of a correction (zero input, plain, plain, iterate update): ncu
-# dram__bytes_read.sum + dram__bytes_write.sum at 512 x 256 x 128 (692 MB),
-# scaled by the cells to the launch at hand.  From one ncu capture of the
-# current kernel; to be retaken (and set to None meanwhile) whenever
-# k_rbgs_fused changes.
-FUSED_SWEEP_TRAFFIC_PER_CELL = None   # kernel changed since the last ncu capture
+# four sweeps of a correction (zero input, plain, plain, iterate update):
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of all 280 such launches
+# in one launch-list capture of this benchmark at 512 x 256 x 256 (one ncu
+# pass), 1.409 GB per launch, per cell and component here.  To be retaken
+# (and set to None meanwhile) whenever k_rbgs_fused changes.
+FUSED_SWEEP_TRAFFIC_PER_CELL = 1.409e9 / (512 * 256 * 256 * 3)
 
 
 def make_sim(w, prec, cycles, extrapolate=1):
@@ -256,7 +256,7 @@ def run_gpu(args, ws, rank, local):
                        "avg_launch_us": round(per_launch_s * 1e6, 2),
                        "traffic": (None if FUSED_SWEEP_TRAFFIC_PER_CELL is None else
                                    round(FUSED_SWEEP_TRAFFIC_PER_CELL * N * 3)),
-                       "traffic_source": "ncu capture at 512x256x128, scaled by cells"}
+                       "traffic_source": "ncu launch list of this benchmark at 512x256x256"}
     out["clocks"] = clk.summary()
     # plain FP64 step with the same schedule, and the accuracy of mixed vs FP64
     if not args.no_fp64:
