@@ -79,3 +79,21 @@ def test_batch_needs_fixed_cycles(V):
     assert e.value.status == V.VSV_EINVAL
     b.close()
     sim.close()
+
+
+def test_autotune_picks_cheapest_schedule_meeting_target(V):
+    from paper_2601_05031_gb300 import autotune
+    w = inputs.vesicle(64, 32, 32, inputs.COUETTE, 0.9, 1.0, dt=1e-4, b_range=(0.2, 0.24))
+    cands = ((1, 1), (2, 1), (4, 1), (6, 1))
+    s = autotune.tune(w, target=1e-6, steps=4, candidates=cands, use_cache=False)
+    ok = [t for t in s.trials if t["vel_err"] * 3.0 <= 1e-6]
+    assert ok, s.trials
+    assert s.vel_err * 3.0 <= 1e-6
+    assert s.ms_per_step == min(t["ms_per_step"] for t in ok)
+    # errors shrink with more cycles
+    errs = [t["vel_err"] for t in s.trials]
+    assert errs[0] > errs[-1]
+    # the cache serves the size class without re-running
+    s1 = autotune.tune(w, steps=4, candidates=cands)
+    s2 = autotune.tune(w, steps=4, candidates=cands)
+    assert s1 is s2
