@@ -96,6 +96,8 @@ def _mu_field(phi, p, gamma_a):
         f = phi[k, j, i]
         out[k, j, i] = (2.0 * cf * ((3 * f * f - 1) * g[k, j, i] - p.eps ** 2 * _lap_at(Gf, k, j, i, p.h))
                         - gamma_a * _lap_at(P, k, j, i, p.h))
+        # membrane tension sigma: derivative of sigma times the face area
+        out[k, j, i] += p.sigma * 3.0 / (2.0 * math.sqrt(2.0) * p.eps) * g[k, j, i]
     return out
 
 

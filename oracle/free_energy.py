@@ -13,6 +13,12 @@
   added as printed, with the penalty multiplier
   gamma_A = K_A (A - A0) * 3 eps / (2 sqrt 2) (the coefficient of lap phi in
   the derivative of the area functional SM eq. 32).
+* Membrane tension (Helfrich kind with sigma != 0): F = C_F int g^2 +
+  sigma A_f[phi], where A_f is the area functional of SM eq. 32 with the
+  gradient summed over cell faces; its derivative adds (c_A / eps) sigma g to
+  mu.  Reading: the paper treats tension (Cahn-Hilliard) and bending
+  (Helfrich) as alternatives; the combination is the tension-plus-bending
+  energy of a membrane, F_m(kappa) + sigma A, with sigma the tension.
 * Area functional (SM eq. 32): A = 3/(2 sqrt 2) int eps/2 |grad phi|^2 +
   (phi^2 - 1)^2 / (4 eps), with central differences for grad phi.
 * Volume (SM eq. 37 with phi = -1 inside the body): V = 1/2 int (1 - phi).
@@ -21,7 +27,8 @@ Discrete definitions use the face-mirror (no-flux) ghosts of ``grid``.
 
 Pinned by: exact discrete energy-gradient identity mu_i = h^-3 dF_h/dphi_i
 (central finite differences of F_h), flat tanh interface, tanh sphere area
--> 4 pi R^2 and Helfrich energy -> 8 pi kappa, Gibbs-Thomson mu = gamma H.
+-> 4 pi R^2 and Helfrich energy -> 8 pi kappa, Gibbs-Thomson mu = gamma H,
+mu of the tension-plus-bending energy = h^-3 d(F_h + sigma A_f)/dphi_i.
 """
 from __future__ import annotations
 
@@ -54,7 +61,26 @@ def chem_potential(phi, fe_kind, h, zper, sigma=0.0, kappa=0.0, eps=1.0, gamma_a
     mu = pref * ((3.0 * phi ** 2 - 1.0) * g - eps * eps * lap_g)
     if gamma_a != 0.0:
         mu = mu - gamma_a * lap(pad_mirror(phi, 1, zper), h)
+    if sigma != 0.0:
+        mu = mu + sigma * tension_mu_coefficient(eps) * g
     return mu
+
+
+def tension_mu_coefficient(eps):
+    """c_A / eps with c_A = 3 / (2 sqrt 2): the membrane tension sigma adds
+    sigma * A_f[phi] to the Helfrich energy, and the derivative of the
+    face-difference area A_f (``area_faces``) is (c_A / eps) g."""
+    return 3.0 / (2.0 * math.sqrt(2.0) * eps)
+
+
+def area_faces(phi, eps, h, zper):
+    """Area functional of SM eq. 32 with |grad phi|^2 summed over cell faces
+    (forward differences, as in ``ch_energy``): A_f = (c_A / eps) *
+    h^3 sum [1/4 (phi^2 - 1)^2 + eps^2 / 2 sum_faces (D+ phi)^2], i.e. the
+    Cahn-Hilliard energy with gradient coefficient eps^2 scaled by c_A / eps.
+    Its exact discrete gradient h^-3 dA_f/dphi = (c_A / eps) (phi^3 - phi -
+    eps^2 lap phi) = (c_A / eps) g."""
+    return tension_mu_coefficient(eps) * ch_energy(phi, eps * eps, h, zper)
 
 
 def volume(phi, h):

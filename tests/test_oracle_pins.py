@@ -288,19 +288,31 @@ def test_div_curl_vanishes():
 
 
 # ------------------------------------------------------------ chemical potential (C-P7..10)
-@pytest.mark.parametrize("fe_kind,zper", [(inputs.CAHN_HILLIARD, False),
-                                          (inputs.HELFRICH, False), (inputs.HELFRICH, True)])
-def test_energy_gradient_identity(fe_kind, zper):
+@pytest.mark.parametrize("fe_kind,zper,sigma", [(inputs.CAHN_HILLIARD, False, 0.7),
+                                                (inputs.HELFRICH, False, 0.0),
+                                                (inputs.HELFRICH, True, 0.0),
+                                                (inputs.HELFRICH, False, 0.7),
+                                                (inputs.HELFRICH, True, 0.4)])
+def test_energy_gradient_identity(fe_kind, zper, sigma):
     """mu_i = h^-3 dF_h/dphi_i exactly (symmetric mirror / periodic
     Laplacian), checked by central finite differences of the discrete
-    energy; fixes the prefactor 2 C_F, the signs and the wall treatment."""
+    energy; fixes the prefactor 2 C_F, the signs and the wall treatment.
+    Helfrich with sigma != 0: F = C_F h^3 sum g^2 + sigma A_f, the area of
+    SM eq. 32 with face differences, 3 / (2 sqrt 2) h^3 sum [(phi^2 - 1)^2 /
+    (4 eps) + eps / 2 |D+ phi|^2]."""
     nz, ny, nx, h = 4, 5, 3, 0.8
     rng = np.random.default_rng(4)
     phi = 0.6 * rng.standard_normal((nz, ny, nx))
-    sigma, kappa, eps = 0.7, 1.3, 1.1
+    kappa, eps = 1.3, 1.1
     mu = chem_potential(phi, fe_kind, h, zper, sigma=sigma, kappa=kappa, eps=eps)
     if fe_kind == inputs.HELFRICH:
-        F = lambda ph: helfrich_energy(ph, kappa, eps, h, zper)
+        def area_f(ph):
+            bulk = np.sum((ph * ph - 1.0) ** 2) / (4.0 * eps)
+            faces = np.sum((np.roll(ph, -1, axis=2) - ph) ** 2)
+            faces += np.sum((ph[:, 1:] - ph[:, :-1]) ** 2)
+            faces += np.sum((np.roll(ph, -1, axis=0) - ph) ** 2 if zper else (ph[1:] - ph[:-1]) ** 2)
+            return 3.0 / (2.0 * math.sqrt(2.0)) * h ** 3 * (bulk + 0.5 * eps * faces / h ** 2)
+        F = lambda ph: helfrich_energy(ph, kappa, eps, h, zper) + sigma * area_f(ph)
     else:
         F = lambda ph: ch_energy(ph, sigma, h, zper)
     d = 1e-5
@@ -488,17 +500,20 @@ def test_energy_decreases_and_flow_dissipates():
 
 
 # ------------------------------------------------------------ transcription (C-P12)
-@pytest.mark.parametrize("case", ["ch_duct", "helfrich_couette", "helfrich_planar"])
+@pytest.mark.parametrize("case", ["ch_duct", "helfrich_couette", "helfrich_planar",
+                                  "helfrich_tension"])
 def test_brute_force_step_matches(case):
     if case == "ch_duct":
         w = inputs.droplet_duct(nx=6, ny=4, nz=5, radius=1.6, u_max=0.05, dt=0.01)
         p = oracle.params_from_workload(w)
         p.k_vol, p.k_area = 0.3, 0.2
     else:
-        kind = inputs.COUETTE if case == "helfrich_couette" else inputs.POISEUILLE_PLANAR
+        kind = inputs.POISEUILLE_PLANAR if case == "helfrich_planar" else inputs.COUETTE
         w = inputs.vesicle(8, 5, 4, kind, 0.9, 1.0, dt=1e-3, b_range=(0.3, 0.35))
         p = oracle.params_from_workload(w)
         p.k_area, p.k_vol = 0.3, 0.01
+        if case == "helfrich_tension":
+            p.sigma = 0.4
     st = init_state(p, w.phi0)
     st.V0 += 0.5
     st.A0 -= 0.3
@@ -516,3 +531,114 @@ def test_workload_shapes():
     assert (w.nx, w.ny, w.nz) == (48, 24, 24) and w.phi0.shape == (24, 24, 48)
     assert abs(w.eta - 0.1 * GOLD["surface_tension_sigma1"]["value"] / 0.05) < 1e-12
     assert w.phi0.min() < -0.99 and w.phi0.max() > 0.99
+
+
+# ------------------------------------------------------------ discrete adjoint (f1)
+from oracle import adjoint as adj
+
+
+def _dot(a, b):
+    return float(np.sum(np.asarray(a) * np.asarray(b)))
+
+
+@pytest.mark.parametrize("zper", [False, True])
+def test_adjoint_transposes_dot_product(zper):
+    """<A u, w> = <u, A^T w> for each transpose against the forward operator
+    it transposes: mirror central differences (oracle.grid.grad of the mirror
+    padding), the curl of a stream vector with zero wall data
+    (oracle.grid.curl), the mirror Laplacian and the Poisson solve."""
+    nz, ny, nx, h = 5, 6, 7, 0.9
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal((nz, ny, nx))
+    w = [rng.standard_normal((nz, ny, nx)) for _ in range(3)]
+    Du = grad(pad_mirror(u, 1, zper), h)
+    lhs = sum(_dot(Du[a], w[a]) for a in range(3))
+    assert abs(lhs - _dot(u, adj.grad_mirror_t(w, h, zper))) < 1e-12 * max(1.0, abs(lhs))
+    us = [rng.standard_normal((nz, ny, nx)) for _ in range(3)]
+    zero = [np.zeros((nz + 2, ny + 2)) for _ in range(3)]
+    cu = curl(us, zero, h, zper)
+    lhs = sum(_dot(cu[c], w[c]) for c in range(3))
+    cw = adj.curl_zero(w, h, zper)
+    assert abs(lhs - sum(_dot(us[c], cw[c]) for c in range(3))) < 1e-12 * max(1.0, abs(lhs))
+    lu = lap(pad_mirror(u, 1, zper), h)
+    assert abs(_dot(lu, w[0]) - _dot(u, lap(pad_mirror(w[0], 1, zper), h))) < 1e-11
+    per = (True, False, zper)
+    a1 = _dot(solve_poisson(u, h, per), w[1])
+    assert abs(a1 - _dot(u, solve_poisson(w[1], h, per))) < 1e-11 * max(1.0, abs(a1))
+
+
+@pytest.mark.parametrize("fe_kind,sigma,gamma", [(inputs.HELFRICH, 0.0, 0.0),
+                                                 (inputs.HELFRICH, 0.6, 0.3),
+                                                 (inputs.CAHN_HILLIARD, 0.8, 0.0)])
+def test_mu_vjp_against_central_differences(fe_kind, sigma, gamma):
+    """(d mu / d phi)^T mubar and the parameter sums against central
+    differences of oracle.free_energy.chem_potential."""
+    nz, ny, nx, h, eps, kappa = 4, 5, 6, 1.0, 1.2, 1.4
+    rng = np.random.default_rng(5)
+    phi = np.tanh(rng.standard_normal((nz, ny, nx)))
+    d = rng.standard_normal((nz, ny, nx))
+    mubar = rng.standard_normal((nz, ny, nx))
+    p = _params(nx, ny, nz, fe_kind=fe_kind, sigma=sigma, kappa=kappa, eps=eps)
+    mu = lambda ph, **kw: chem_potential(ph, fe_kind, h, False, **{**dict(
+        sigma=sigma, kappa=kappa, eps=eps, gamma_a=gamma), **kw})
+    pb, kb, sb, gb = adj.mu_vjp(phi, gamma, mubar, p)
+    t = 1e-6
+    fd = _dot(mubar, (mu(phi + t * d) - mu(phi - t * d)) / (2 * t))
+    assert abs(fd - _dot(pb, d)) < 1e-7 * max(1.0, abs(fd)), (fd, _dot(pb, d))
+    if fe_kind == inputs.HELFRICH:
+        fdk = _dot(mubar, (mu(phi, kappa=kappa + t) - mu(phi, kappa=kappa - t)) / (2 * t))
+        assert abs(fdk - kb) < 1e-7 * max(1.0, abs(fdk))
+        fdg = _dot(mubar, (mu(phi, gamma_a=gamma + t) - mu(phi, gamma_a=gamma - t)) / (2 * t))
+        assert abs(fdg - gb) < 1e-7 * max(1.0, abs(fdg))
+    fds = _dot(mubar, (mu(phi, sigma=sigma + t) - mu(phi, sigma=sigma - t)) / (2 * t))
+    assert abs(fds - sb) < 1e-7 * max(1.0, abs(fds))
+
+
+def _adjoint_case(case):
+    if case == "ch_duct":
+        w = inputs.droplet_duct(nx=10, ny=8, nz=8, radius=2.5, u_max=0.05, dt=0.02)
+        p = oracle.params_from_workload(w)
+        p.k_vol = 0.002
+        dt = 0.02
+    else:
+        kind = inputs.COUETTE if case == "helfrich_couette" else inputs.POISEUILLE_DUCT
+        w = inputs.vesicle(12, 8, 8, kind, 0.85, 1.0, dt=2e-3, b_range=(0.3, 0.35),
+                           u_max=0.2, v_wall=0.2)
+        p = oracle.params_from_workload(w)
+        p.k_area, p.k_vol, p.sigma, p.kappa = 0.4, 0.02, 0.3, 1.3
+        dt = 2e-3
+    return w, p, dt
+
+
+@pytest.mark.parametrize("case", ["helfrich_duct", "helfrich_couette", "ch_duct"])
+def test_trajectory_gradient_against_central_differences(case):
+    """Gradient of J = h^3/2 sum (phi^N - target)^2 after 4 steps with
+    respect to kappa, sigma and two random directions of phi^0, against
+    central differences of the forward oracle."""
+    import dataclasses
+    w, p, dt = _adjoint_case(case)
+    N = 4
+    rng = np.random.default_rng(3)
+    target = w.phi0 + 0.05 * rng.standard_normal(w.phi0.shape)
+
+    def J(pp, phi0):
+        return adj.forward(pp, phi0, dt, N)[-1]["phi"]
+
+    def loss(pp, phi0):
+        return adj.loss(J(pp, phi0), target, pp.h)
+
+    J0, gphi, gk, gs = adj.gradient(p, w.phi0, dt, N, target)
+    assert abs(J0 - loss(p, w.phi0)) < 1e-14 * J0
+    t = 1e-5
+    for name, g in (("kappa", gk), ("sigma", gs)):
+        if name == "kappa" and p.fe_kind != inputs.HELFRICH:
+            continue
+        v = getattr(p, name)
+        lp = loss(dataclasses.replace(p, **{name: v + t}), w.phi0)
+        lm = loss(dataclasses.replace(p, **{name: v - t}), w.phi0)
+        fd = (lp - lm) / (2 * t)
+        assert abs(fd - g) < 1e-6 * abs(fd), (name, fd, g)
+    for seed in (1, 2):
+        d = np.random.default_rng(seed).standard_normal(w.phi0.shape)
+        fd = (loss(p, w.phi0 + t * d) - loss(p, w.phi0 - t * d)) / (2 * t)
+        assert abs(fd - _dot(gphi, d)) < 1e-6 * abs(fd), (seed, fd, _dot(gphi, d))
