@@ -109,7 +109,10 @@ typedef struct {
   double rho;
 } vsv_flow_params;
 
-/* Free energy.  sigma: CH gradient coefficient; kappa, eps: Helfrich bending
+/* Free energy.  sigma: CH gradient coefficient, or for the Helfrich kind the
+ * membrane tension, which adds sigma A_f[phi] to the energy (A_f: the area
+ * functional of SM eq. 32 with the gradient summed over cell faces) and
+ * (3 / (2 sqrt2 eps)) sigma g to mu; kappa, eps: Helfrich bending
  * modulus and interface width (also the width in the area functional, SM
  * eq. 32); mobility M; k_area, k_vol: penalty stiffnesses of the area and
  * volume multipliers (gamma_A = k_area (A - A0) 3 eps / (2 sqrt 2),
@@ -315,7 +318,8 @@ typedef enum {
   VSV_KCLASS_RESTRICT = 2,      /* exact residual + restriction                */
   VSV_KCLASS_PROLONG = 3,       /* prolongation + correction                   */
   VSV_KCLASS_PHASE = 4,         /* phi update, mu, source, reductions          */
-  VSV_KCLASS_COUNT = 5
+  VSV_KCLASS_ADJOINT = 5,       /* stencil kernels of the discrete adjoint     */
+  VSV_KCLASS_COUNT = 6
 } vsv_kernel_class;
 int64_t vsv_kernel_launches(const vsv_grid* g);
 /* Algorithmic memory traffic, in bytes, of all kernels this handle has
@@ -360,6 +364,53 @@ typedef struct vsv_batch vsv_batch;
 vsv_status vsv_batch_create(vsv_batch** out, vsv_grid* const* grids, int n, void* cuda_stream);
 vsv_status vsv_batch_step(vsv_batch* b, int nsteps, double dt);
 vsv_status vsv_batch_destroy(vsv_batch* b);
+
+/* Discrete adjoint with checkpointing.  Differentiates the map
+ * (phi^0, kappa, sigma) -> phi^N of vsv_set_phi followed by N steps of
+ * vsv_step (eqs. gen2, gen1, gen3 in the segregated order of the
+ * numerical-implementation section), as the kernels compute it: reverse mode
+ * of the discrete step, with the transposes of its central-difference and
+ * mirror stencils and adjoint Poisson problems that are the same problems as
+ * the forward ones (the 7-point operator with zero wall data is symmetric).
+ * Adjoint fields are FP64; the adjoint solves use the grid's precision
+ * (FP64 multigrid, or FP32 V-cycles with double-word defect correction) to
+ * the relative residual `tol`.  The inertial variant (rho > 0) is not
+ * covered.  The area and volume constants A0 = A[phi^0], V0 = V[phi^0]
+ * depend on phi^0 and are differentiated.
+ *
+ * vsv_tape_create binds a tape to grid g (which must outlive it): every >= 1
+ * steps between checkpoints, tol > 0 (0 selects 1e-11).  It allocates the
+ * device memory of one segment's record ((every + 1) x 5 FP64 fields) and of
+ * the adjoint fields.  VSV_EINVAL on bad arguments, VSV_ECUDA when memory
+ * runs out.
+ *
+ * vsv_tape_forward runs vsv_set_phi(phi0, dtype, on_device) and nsteps steps
+ * of dt, saving the full state on the device at step 0, every `every` steps
+ * and at step nsteps.  The grid's flow, free energy and solver settings
+ * must stay unchanged until the matching backward pass.  VSV_EINVAL for
+ * rho > 0 or bad arguments; errors of vsv_set_phi / vsv_step pass through.
+ *
+ * vsv_tape_backward takes phibar_final = dJ/dphi^N (N cells, FP64, device
+ * memory when on_device, else host) and writes phibar0 = dJ/dphi^0 (same
+ * memory kind) and, when param_bar is not NULL, param_bar[0] = dJ/dkappa and
+ * param_bar[1] = dJ/dsigma (host).  It re-runs each segment from its
+ * checkpoint and leaves the grid at the state of step nsteps.  It returns
+ * when the results are written.  VSV_ESTATE without a forward pass.
+ *
+ * vsv_tape_destroy frees the tape's device memory (NULL is a no-op).
+ * vsv_tape_bytes: device bytes held by the tape (checkpoints included).
+ * vsv_tape_info: adjoint solve cycles and re-run steps of the last backward
+ * pass, checkpoints held. */
+typedef struct vsv_tape vsv_tape;
+vsv_status vsv_tape_create(vsv_tape** out, vsv_grid* g, int every, double tol);
+vsv_status vsv_tape_destroy(vsv_tape* t);
+vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_device, int nsteps,
+                            double dt);
+vsv_status vsv_tape_backward(vsv_tape* t, const double* phibar_final, double* phibar0,
+                             int on_device, double* param_bar);
+size_t vsv_tape_bytes(const vsv_tape* t);
+vsv_status vsv_tape_info(const vsv_tape* t, int64_t* adjoint_cycles, int64_t* recomputed_steps,
+                         int* checkpoints);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,95 @@
+"""Gradients of a trajectory through the library's discrete adjoint.
+
+``Tape`` wraps the C tape (vsv_tape_*): a checkpointed forward run from phi^0
+and the reverse pass that returns dJ/dphi^0, dJ/dkappa and dJ/dsigma for a
+given dJ/dphi^N.  ``trajectory`` exposes the map (phi^0, kappa, sigma) ->
+phi^N as a torch.autograd.Function, so a loss written in torch on phi^N
+back-propagates through the hand-written adjoint kernels.  This module only
+marshals arguments; every step, forward and reverse, runs in libvsv.so.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import vsv as V
+from .sim import Simulation
+
+
+class Tape:
+    """A trajectory tape bound to a configured Simulation.
+
+    ``every``: steps between checkpoints; ``tol``: relative residual of the
+    adjoint Poisson solves (0: the library's default 1e-11)."""
+
+    def __init__(self, sim: Simulation, fe: dict, every: int = 20, tol: float = 0.0):
+        self.sim = sim
+        self.fe = dict(fe)
+        self.t = V.vsv_tape_create(sim.g, every, tol)
+        self.every = every
+
+    @classmethod
+    def from_workload(cls, w, precision=V.VSV_MIXED, every=20, tol=0.0, solver=None, stream=None):
+        sim = Simulation.from_workload(w, precision, solver=solver, stream=stream)
+        fe = dict(kind=w.fe_kind, sigma=w.sigma, kappa=w.kappa, eps=w.eps, mobility=w.mobility,
+                  k_area=w.k_area, k_vol=w.k_vol)
+        return cls(sim, fe, every, tol)
+
+    def set_params(self, kappa: float, sigma: float):
+        self.fe["kappa"], self.fe["sigma"] = float(kappa), float(sigma)
+        f = self.fe
+        V.vsv_set_free_energy(self.sim.g, f["kind"], f["sigma"], f["kappa"], f["eps"],
+                              f["mobility"], f["k_area"], f["k_vol"])
+
+    def forward(self, phi0: torch.Tensor, nsteps: int, dt: float) -> torch.Tensor:
+        """phi^N (FP64 device tensor) after nsteps steps from phi0."""
+        p0 = phi0.detach().to(device=self.sim.device, dtype=torch.float64).contiguous()
+        V.vsv_tape_forward(self.t, self.sim.g, p0.data_ptr(), V.VSV_DTYPE_F64, 1, nsteps, dt)
+        return self.sim.field(V.VSV_FIELD_PHI, torch.float64, on_device=True)
+
+    def backward(self, phibar: torch.Tensor):
+        """(dJ/dphi^0 tensor, dJ/dkappa, dJ/dsigma) for phibar = dJ/dphi^N."""
+        pb = phibar.detach().to(device=self.sim.device, dtype=torch.float64).contiguous()
+        out = torch.empty_like(pb)
+        dk, ds = V.vsv_tape_backward(self.t, self.sim.g, pb.data_ptr(), out.data_ptr(), 1)
+        return out, dk, ds
+
+    def info(self):
+        cyc, rerun, nck = V.vsv_tape_info(self.t)
+        return {"adjoint_cycles": cyc, "recomputed_steps": rerun, "checkpoints": nck,
+                "device_bytes": V.vsv_tape_bytes(self.t)}
+
+    def close(self):
+        if self.t is not None:
+            V.vsv_tape_destroy(self.t)
+            self.t = None
+        if self.sim is not None:
+            self.sim.close()
+            self.sim = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Trajectory(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, phi0, kappa, sigma, tape, nsteps, dt):
+        tape.set_params(float(kappa), float(sigma))
+        ctx.tape = tape
+        return tape.forward(phi0, nsteps, dt)
+
+    @staticmethod
+    def backward(ctx, grad_phi):
+        pb0, dk, ds = ctx.tape.backward(grad_phi)
+        dev = grad_phi.device
+        return (pb0, torch.tensor(dk, dtype=torch.float64, device=dev),
+                torch.tensor(ds, dtype=torch.float64, device=dev), None, None, None)
+
+
+def trajectory(phi0: torch.Tensor, kappa: torch.Tensor, sigma: torch.Tensor, tape: Tape,
+               nsteps: int, dt: float) -> torch.Tensor:
+    """phi^N of nsteps steps from phi0 with bending modulus kappa and
+    tension sigma (0-dim tensors), differentiable in all three."""
+    return _Trajectory.apply(phi0, kappa, sigma, tape, nsteps, dt)

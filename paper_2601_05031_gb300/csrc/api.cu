@@ -571,6 +571,9 @@ PhaseParams phase_params(const vsv_grid* g) {
   P.eps = g->fe.eps;
   const double cf = 3.0 * std::sqrt(2.0) * g->fe.kappa / (8.0 * std::pow(g->fe.eps, 3));
   P.cf2 = g->fe.mu_prefactor_half ? cf : 2.0 * cf;
+  // membrane tension: sigma times the face-difference area functional adds
+  // (c_A / eps) sigma g to the Helfrich mu, c_A = 3 / (2 sqrt 2)
+  P.beta_t = g->fe.kind == VSV_HELFRICH ? g->fe.sigma * 3.0 / (2.0 * std::sqrt(2.0) * g->fe.eps) : 0.0;
   P.mobility = g->fe.mobility;
   P.inv_eta = 1.0 / g->flow.eta;
   auto split = [](double v, float& hi, float& lo) {
@@ -586,6 +589,7 @@ PhaseParams phase_params(const vsv_grid* g) {
   split(0.25 / g->fe.eps, P.q_hi, P.q_lo);
   split(3.0 / (2.0 * std::sqrt(2.0)), P.ca_hi, P.ca_lo);
   split(1.0 / g->flow.eta, P.ie_hi, P.ie_lo);
+  split(P.beta_t, P.bt_hi, P.bt_lo);
   std::memset(P.vwall, 0, sizeof P.vwall);
   if (g->flow.kind == VSV_COUETTE) {
     P.vwall[0][0] = g->flow.v_lo;
@@ -1195,7 +1199,8 @@ vsv_status vsv_stability_limit(const vsv_grid* g, double* dt_max) {
       const double cf = 3.0 * std::sqrt(2.0) * g->fe.kappa / (8.0 * std::pow(g->fe.eps, 3));
       const double c2 = g->fe.mu_prefactor_half ? cf : 2.0 * cf;
       const double t = 2.0 + e2 * lam;
-      lim = 2.0 / (M * c2 * lam * t * t);
+      const double beta = g->fe.sigma * 3.0 / (2.0 * std::sqrt(2.0) * g->fe.eps);
+      lim = 2.0 / (M * lam * t * (c2 * t + std::max(beta, 0.0)));
     }
     if (g->fe.k_vol > 0) {
       const double v = 4.0 / (M * g->fe.k_vol * (double)g->N * g->h * h2);
@@ -1785,6 +1790,372 @@ vsv_status vsv_profile_read(vsv_grid* g, int kclass, double* total_ms, int64_t* 
   *total_ms = t;
   *launches = g->cx.prof_launches;
   if (alg_bytes) *alg_bytes = g->cx.prof_bytes;
+  return VSV_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- adjoint tape
+// Reverse mode over a recorded trajectory with checkpointing: the forward
+// pass keeps the full state (the state blob's fields, on the device) every
+// `every` steps and at the last step; the backward pass walks the segments
+// from the last to the first, re-runs each segment from its checkpoint while
+// recording phi, mu, psi' (FP64) and gamma_A of every step, then reverses its
+// steps with the adjoint kernels.  Memory: checkpoints of the state plus one
+// segment of (every + 1) x 5 fields, instead of the whole trajectory.
+struct vsv_tape {
+  vsv_grid* g = nullptr;
+  int every = 20;
+  double tol = 1e-11;
+  int nsteps = 0;
+  double dt = 0.0;
+  bool recorded = false;
+  size_t ck_bytes = 0;                 // bytes of one checkpoint
+  std::vector<char*> ck;               // device checkpoints ...
+  std::vector<int> ck_step;            // ... of the states at these steps
+  std::vector<StateHeader> ck_hdr;     // their host-side counters
+  double* rec = nullptr;               // (every + 1) x 5 N doubles: phi, mu, psi'(3)
+  double* gam = nullptr;               // (every + 1) gamma_A (device)
+  double* buf = nullptr;               // adjoint fields, FP64
+  float* fbuf = nullptr;               // mixed path: double-word solve iterates and rhs
+  double* acc = nullptr;               // kAccCount accumulators
+  double* partials = nullptr;          // 3 per reduction block
+  size_t dev_bytes = 0;
+  long long adj_cycles = 0;            // cycles of the adjoint solves, last backward pass
+  long long recomputed = 0;            // steps re-run by the last backward pass
+  // views into buf / fbuf
+  double *phib, *mub, *psib[3], *ab[3], *bb[3], *fb[3], *x1[3], *gsc, *wsc;
+  float *x1h[3], *x1l[3], *fbh[3], *fbl[3], *bh[3], *bl[3];
+};
+
+namespace {
+
+AdjParams adj_params(const vsv_grid* g) {
+  AdjParams P{};
+  P.nx = g->nx; P.ny = g->ny; P.nz = g->nz;
+  P.zper = z_periodic(g) ? 1 : 0;
+  P.h = g->h; P.hih = 0.5 / g->h; P.ih2 = 1.0 / (g->h * g->h); P.h3 = g->h * g->h * g->h;
+  P.fe_kind = g->fe.kind;
+  P.sigma = g->fe.sigma;
+  P.eps = g->fe.eps;
+  P.e2 = g->fe.eps * g->fe.eps;
+  const double cf1 = 3.0 * std::sqrt(2.0) / (8.0 * std::pow(g->fe.eps, 3));   // C_F per unit kappa
+  P.cf2_per_kappa = g->fe.mu_prefactor_half ? cf1 : 2.0 * cf1;
+  P.cf2 = P.cf2_per_kappa * g->fe.kappa;
+  P.beta = g->fe.kind == VSV_HELFRICH ? g->fe.sigma * 3.0 / (2.0 * std::sqrt(2.0) * g->fe.eps) : 0.0;
+  P.inv_eta = 1.0 / g->flow.eta;
+  P.mobility = g->fe.mobility;
+  P.k_vol = g->fe.k_vol;
+  P.k_area = g->fe.k_area;
+  return P;
+}
+
+template <class T>
+Comp3<const T> cc3(T* const a[3]) { return Comp3<const T>{{a[0], a[1], a[2]}}; }
+template <class T>
+Comp3<T> mc3(T* const a[3]) { return Comp3<T>{{a[0], a[1], a[2]}}; }
+
+void tape_free_ckpts(vsv_tape* t) {
+  for (char* p : t->ck) cudaFree(p);
+  t->ck.clear();
+  t->ck_step.clear();
+  t->ck_hdr.clear();
+}
+
+vsv_status tape_alloc(vsv_tape* t) {
+  vsv_grid* g = t->g;
+  const long long N = g->N;
+  auto dmalloc = [&](void** p, size_t b) -> vsv_status {
+    CK(cudaMalloc(p, b));
+    t->dev_bytes += b;
+    return VSV_OK;
+  };
+  vsv_status st;
+  if ((st = dmalloc((void**)&t->rec, (size_t)(t->every + 1) * 5 * N * 8)) != VSV_OK) return st;
+  if ((st = dmalloc((void**)&t->gam, (size_t)(t->every + 1) * 8)) != VSV_OK) return st;
+  if ((st = dmalloc((void**)&t->buf, (size_t)19 * N * 8)) != VSV_OK) return st;
+  if ((st = dmalloc((void**)&t->acc, kAccCount * 8)) != VSV_OK) return st;
+  if ((st = dmalloc((void**)&t->partials, (size_t)3 * adj_blocks(N) * 8)) != VSV_OK) return st;
+  double* p = t->buf;
+  auto take = [&]() { double* q = p; p += N; return q; };
+  t->phib = take();
+  t->mub = take();
+  for (int c = 0; c < 3; ++c) t->psib[c] = take();
+  for (int c = 0; c < 3; ++c) t->ab[c] = take();
+  for (int c = 0; c < 3; ++c) t->bb[c] = take();
+  for (int c = 0; c < 3; ++c) t->fb[c] = take();
+  for (int c = 0; c < 3; ++c) t->x1[c] = take();
+  t->gsc = take();
+  t->wsc = take();
+  if (g->prec == VSV_MIXED) {
+    if ((st = dmalloc((void**)&t->fbuf, (size_t)18 * N * 4)) != VSV_OK) return st;
+    float* f = t->fbuf;
+    auto takef = [&]() { float* q = f; f += N; return q; };
+    for (int c = 0; c < 3; ++c) t->x1h[c] = takef();
+    for (int c = 0; c < 3; ++c) t->x1l[c] = takef();
+    for (int c = 0; c < 3; ++c) t->fbh[c] = takef();
+    for (int c = 0; c < 3; ++c) t->fbl[c] = takef();
+    for (int c = 0; c < 3; ++c) t->bh[c] = takef();
+    for (int c = 0; c < 3; ++c) t->bl[c] = takef();
+  }
+  return VSV_OK;
+}
+
+// state -> checkpoint slot (device to device, asynchronous)
+vsv_status tape_save(vsv_tape* t, int step) {
+  vsv_grid* g = t->g;
+  char* dst = nullptr;
+  CK(cudaMalloc((void**)&dst, t->ck_bytes));
+  t->dev_bytes += t->ck_bytes;
+  size_t off = 0;
+  for (auto& f : state_fields(g)) {
+    CK(cudaMemcpyAsync(dst + off, f.first, f.second, cudaMemcpyDeviceToDevice, g->cx.stream));
+    off += f.second;
+  }
+  CK(cudaMemcpyAsync(dst + off, &g->S->V0, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                     g->cx.stream));   // V0, A0 (adjacent in Scalars)
+  StateHeader hd{};
+  hd.time = g->time;
+  hd.steps = g->steps;
+  hd.hist = g->hist;
+  t->ck.push_back(dst);
+  t->ck_step.push_back(step);
+  t->ck_hdr.push_back(hd);
+  return VSV_OK;
+}
+
+vsv_status tape_restore(vsv_tape* t, int i) {
+  vsv_grid* g = t->g;
+  const char* src = t->ck[i];
+  size_t off = 0;
+  for (auto& f : state_fields(g)) {
+    CK(cudaMemcpyAsync(f.first, src + off, f.second, cudaMemcpyDeviceToDevice, g->cx.stream));
+    off += f.second;
+  }
+  CK(cudaMemcpyAsync(&g->S->V0, src + off, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                     g->cx.stream));
+  g->time = t->ck_hdr[i].time;
+  g->steps = t->ck_hdr[i].steps;
+  g->hist = t->ck_hdr[i].hist;
+  g->phi_set = true;
+  g->phase_stale = true;
+  return VSV_OK;
+}
+
+double* rec_field(vsv_tape* t, int slot, int q) { return t->rec + ((size_t)slot * 5 + q) * t->g->N; }
+
+// phi, mu, psi' (FP64) and gamma_A of the grid's current state into a slot
+vsv_status tape_record(vsv_tape* t, int slot) {
+  vsv_grid* g = t->g;
+  const int fields[5] = {VSV_FIELD_PHI, VSV_FIELD_MU, VSV_FIELD_PSI_PERT_X, VSV_FIELD_PSI_PERT_Y,
+                         VSV_FIELD_PSI_PERT_Z};
+  for (int q = 0; q < 5; ++q) {
+    vsv_status st = g->prec == VSV_FP64
+                        ? get_field_impl<double>(g, fields[q], rec_field(t, slot, q), VSV_DTYPE_F64, 1)
+                        : get_field_impl<float>(g, fields[q], rec_field(t, slot, q), VSV_DTYPE_F64, 1);
+    if (st != VSV_OK) return st;
+  }
+  // mu's export refreshed the phase of a restored state: gamma_A is current
+  CK(cudaMemcpyAsync(t->gam + slot, &g->S->gamma_a, sizeof(double), cudaMemcpyDeviceToDevice,
+                     g->cx.stream));
+  return VSV_OK;
+}
+
+// fbar = L^-1 (-L^-1 psibar) per component: the adjoint of the vorticity and
+// stream-vector solves (L symmetric, zero wall data), warm-started from the
+// previous reverse step's solutions
+vsv_status tape_solves(vsv_tape* t) {
+  vsv_grid* g = t->g;
+  const int every = std::max(1, g->sol.check_every);
+  int c1 = 0, c2 = 0;
+  double r1 = 0.0, r2 = 0.0;
+  vsv_status st;
+  if (g->prec == VSV_FP64) {
+    Rhs3<double> R1{{t->psib[0], t->psib[1], t->psib[2]}, {nullptr, nullptr, nullptr}, 1.0};
+    st = solve<double>(g, g->flow_levels, mc3(t->x1), R1, 3, VSV_SOLVER_MG, 0, t->tol, 400, every,
+                       &c1, &r1);
+    if (st != VSV_OK) return st;
+    Rhs3<double> R2{{t->x1[0], t->x1[1], t->x1[2]}, {nullptr, nullptr, nullptr}, -1.0};
+    st = solve<double>(g, g->flow_levels, mc3(t->fb), R2, 3, VSV_SOLVER_MG, 0, t->tol, 400, every,
+                       &c2, &r2);
+    if (st != VSV_OK) return st;
+  } else {
+    for (int c = 0; c < 3; ++c) launch_split_ff(g->cx, t->psib[c], t->bh[c], t->bl[c], g->N);
+    Rhs3<float> R1{{t->bh[0], t->bh[1], t->bh[2]}, {nullptr, nullptr, nullptr}, 1.f};
+    st = solve_dc(g, g->flow_levels, mc3(t->x1h), mc3(t->x1l), R1, mc3(t->bl), 3, 0, t->tol, 400,
+                  every, &c1, &r1);
+    if (st != VSV_OK) return st;
+    Rhs3<float> R2{{t->x1h[0], t->x1h[1], t->x1h[2]}, {nullptr, nullptr, nullptr}, -1.f};
+    st = solve_dc(g, g->flow_levels, mc3(t->fbh), mc3(t->fbl), R2, mc3(t->x1l), 3, 0, t->tol, 400,
+                  every, &c2, &r2);
+    if (st != VSV_OK) return st;
+    for (int c = 0; c < 3; ++c) launch_merge_ff(g->cx, t->fbh[c], t->fbl[c], t->fb[c], g->N);
+  }
+  t->adj_cycles += c1 + c2;
+  return VSV_OK;
+}
+
+// adjoint of the flow solve and of mu at a recorded state (slot s); with
+// `step` the area penalty of gamma_A = K_A c_g (A - A0) too
+vsv_status tape_state_adjoint(vsv_tape* t, const AdjParams& P, int s, bool step) {
+  vsv_grid* g = t->g;
+  vsv_status st = tape_solves(t);
+  if (st != VSV_OK) return st;
+  const double* phi = rec_field(t, s, 0);
+  const double* mu = rec_field(t, s, 1);
+  launch_adj_source(g->cx, P, phi, mu, cc3(t->fb), mc3(t->ab), mc3(t->bb));
+  launch_adj_divt(g->cx, P, cc3(t->ab), t->phib, cc3(t->bb), t->mub);
+  launch_adj_mu(g->cx, P, phi, t->mub, step ? t->gam + s : nullptr, t->gsc, t->wsc, t->phib,
+                t->partials, t->acc, step);
+  if (step && P.fe_kind == VSV_HELFRICH && P.k_area != 0.0)
+    launch_adj_area(g->cx, P, phi, t->acc + kAccAreaCoef, nullptr, 0.0, t->phib);
+  CKL();
+  return VSV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vsv_status vsv_tape_create(vsv_tape** out, vsv_grid* g, int every, double tol) {
+  if (!out || !g || every < 1 || !(tol >= 0) || !std::isfinite(tol)) return VSV_EINVAL;
+  *out = nullptr;
+  vsv_tape* t = new vsv_tape();
+  t->g = g;
+  t->every = every;
+  t->tol = tol > 0 ? tol : 1e-11;
+  vsv_status st = tape_alloc(t);
+  if (st != VSV_OK) {
+    vsv_tape_destroy(t);
+    return st;
+  }
+  *out = t;
+  return VSV_OK;
+}
+
+vsv_status vsv_tape_destroy(vsv_tape* t) {
+  if (!t) return VSV_OK;
+  if (t->g) cudaStreamSynchronize(t->g->cx.stream);
+  tape_free_ckpts(t);
+  cudaFree(t->rec);
+  cudaFree(t->gam);
+  cudaFree(t->buf);
+  cudaFree(t->fbuf);
+  cudaFree(t->acc);
+  cudaFree(t->partials);
+  delete t;
+  return VSV_OK;
+}
+
+size_t vsv_tape_bytes(const vsv_tape* t) { return t ? t->dev_bytes : 0; }
+
+vsv_status vsv_tape_info(const vsv_tape* t, int64_t* adjoint_cycles, int64_t* recomputed_steps,
+                         int* checkpoints) {
+  if (!t) return VSV_EINVAL;
+  if (adjoint_cycles) *adjoint_cycles = t->adj_cycles;
+  if (recomputed_steps) *recomputed_steps = t->recomputed;
+  if (checkpoints) *checkpoints = (int)t->ck.size();
+  return VSV_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_device, int nsteps,
+                            double dt) {
+  if (!t || !phi0 || nsteps < 1 || !(dt > 0)) return VSV_EINVAL;
+  vsv_grid* g = t->g;
+  if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_tape_forward%s");
+  if (g->flow.rho > 0.0)
+    return fail(g, VSV_EINVAL, "the adjoint covers the Stokes step (rho = 0)%s");
+  CK(cudaStreamSynchronize(g->cx.stream));
+  tape_free_ckpts(t);
+  t->dev_bytes = (size_t)(t->every + 1) * 5 * g->N * 8 + (size_t)(t->every + 1) * 8 +
+                 (size_t)19 * g->N * 8 + kAccCount * 8 + (size_t)3 * adj_blocks(g->N) * 8 +
+                 (g->prec == VSV_MIXED ? (size_t)18 * g->N * 4 : 0);
+  t->recorded = false;
+  t->ck_bytes = 2 * sizeof(double);
+  for (auto& f : state_fields(g)) t->ck_bytes += f.second;
+  vsv_status st = vsv_set_phi(g, phi0, dtype, on_device);
+  if (st != VSV_OK) return st;
+  if ((st = tape_save(t, 0)) != VSV_OK) return st;
+  int done = 0;
+  while (done < nsteps) {
+    const int k = std::min(t->every, nsteps - done);
+    if ((st = vsv_step(g, k, dt)) != VSV_OK) return st;
+    done += k;
+    if ((st = tape_save(t, done)) != VSV_OK) return st;
+  }
+  if ((st = vsv_check(g)) != VSV_OK) return st;
+  t->nsteps = nsteps;
+  t->dt = dt;
+  t->recorded = true;
+  return VSV_OK;
+}
+
+vsv_status vsv_tape_backward(vsv_tape* t, const double* phibar_final, double* phibar0,
+                             int on_device, double* param_bar) {
+  if (!t || !phibar_final || !phibar0) return VSV_EINVAL;
+  vsv_grid* g = t->g;
+  if (!t->recorded) return fail(g, VSV_ESTATE, "vsv_tape_forward must precede vsv_tape_backward%s");
+  const long long N = g->N;
+  const AdjParams P = adj_params(g);
+  cudaStream_t s = g->cx.stream;
+  t->adj_cycles = 0;
+  t->recomputed = 0;
+  // terminal adjoint: phibar^N given, mubar^N = psibar'^N = 0; zero warm starts
+  CK(cudaMemcpyAsync(t->phib, phibar_final, N * 8,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(t->mub, 0, N * 8, s));
+  for (int c = 0; c < 3; ++c) {
+    CK(cudaMemsetAsync(t->psib[c], 0, N * 8, s));
+    CK(cudaMemsetAsync(t->fb[c], 0, N * 8, s));
+    CK(cudaMemsetAsync(t->x1[c], 0, N * 8, s));
+  }
+  if (t->fbuf) CK(cudaMemsetAsync(t->fbuf, 0, (size_t)18 * N * 4, s));
+  CK(cudaMemsetAsync(t->acc, 0, kAccCount * 8, s));
+  Comp3<const double> V0{{g->v0d[0], g->v0d[1], g->v0d[2]}};
+  vsv_status st;
+  const int nck = (int)t->ck.size();
+  for (int seg = nck - 2; seg >= 0; --seg) {
+    const int a = t->ck_step[seg], b = t->ck_step[seg + 1];
+    // re-run the segment from its checkpoint, recording every state
+    if ((st = tape_restore(t, seg)) != VSV_OK) return st;
+    if ((st = tape_record(t, 0)) != VSV_OK) return st;
+    for (int n = a; n < b; ++n) {
+      st = g->prec == VSV_FP64 ? step_impl<double>(g, t->dt) : step_impl<float>(g, t->dt);
+      if (st != VSV_OK) return st;
+      if ((st = tape_record(t, n + 1 - a)) != VSV_OK) return st;
+      ++t->recomputed;
+    }
+    // reverse its steps: state n + 1 (flow solve, mu, gamma_A), then the update n -> n + 1
+    for (int n = b - 1; n >= a; --n) {
+      if ((st = tape_state_adjoint(t, P, n + 1 - a, true)) != VSV_OK) return st;
+      launch_adj_update(g->cx, P, t->phib, rec_field(t, n - a, 0),
+                        Comp3<const double>{{rec_field(t, n - a, 2), rec_field(t, n - a, 3),
+                                             rec_field(t, n - a, 4)}},
+                        V0, t->dt, mc3(t->ab), mc3(t->bb), t->mub, mc3(t->psib), t->partials, t->acc);
+      CKL();
+    }
+  }
+  // the initial state: mu^0 and psi^0 of phi^0 (gamma^0 = 0 identically),
+  // then V0 = V[phi^0] and A0 = A[phi^0]
+  if ((st = tape_state_adjoint(t, P, 0, false)) != VSV_OK) return st;
+  launch_adj_area(g->cx, P, rec_field(t, 0, 0), P.fe_kind == VSV_HELFRICH ? t->acc + kAccA0 : nullptr,
+                  t->acc + kAccV0, -0.5 * P.h3, t->phib);
+  CKL();
+  CK(cudaMemcpyAsync(phibar0, t->phib, N * 8,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  double hacc[kAccCount];
+  CK(cudaMemcpyAsync(hacc, t->acc, sizeof hacc, cudaMemcpyDeviceToHost, s));
+  // leave the grid at the end of the trajectory
+  if ((st = tape_restore(t, nck - 1)) != VSV_OK) return st;
+  CK(cudaStreamSynchronize(s));
+  if (param_bar) {
+    param_bar[0] = hacc[kAccKappa];
+    param_bar[1] = hacc[kAccSigma];
+  }
   return VSV_OK;
 }
 

@@ -166,11 +166,13 @@ struct PhaseParams {
   double h, inv_h, inv_h2;
   int fe_kind;
   double sigma, eps, cf2;       // cf2 = prefactor of the Helfrich mu
+  double beta_t;                // Helfrich with tension sigma: mu += beta_t g, beta_t = sigma c_A / eps
   double mobility, inv_eta;
   // the same coefficients as double-word FP32 pairs (hi, lo) for the mixed path
   float ih2_hi, ih2_lo, e2_hi, e2_lo, cf2_hi, cf2_lo, sig_hi, sig_lo;
   float hih_hi, hih_lo, he_hi, he_lo, q_hi, q_lo, ca_hi, ca_lo;   // area density
   float ie_hi, ie_lo;                                              // 1 / eta
+  float bt_hi, bt_lo;                                              // beta_t
   // wall velocity on the wall nodes: [0] y = 0 wall, [1] y = H, [2] z = 0, [3] z = H
   double vwall[4][3];
 };
@@ -230,5 +232,43 @@ void launch_base_derived(Ctx& cx, int ny, int nz, int zper, double h, const doub
                          const double* ps_ring[3], double* v0[3], double* s_om[3], double* s_ps[3]);
 double device_max_abs(Ctx& cx, const double* x, long long n, double* scratch);
 void launch_fill(Ctx& cx, double* x, long long n, double v);
+
+// ---------------------------------------------------------------- discrete adjoint (adjoint.cu)
+// Coefficients of the adjoint kernels (FP64 throughout).
+struct AdjParams {
+  int nx, ny, nz, zper;
+  double h, hih, ih2, h3;            // h, 1 / (2h), 1 / h^2, h^3
+  int fe_kind;
+  double sigma, eps, e2;             // e2 = eps^2
+  double cf2, cf2_per_kappa;         // prefactor of the bending mu, and per unit kappa
+  double beta;                       // Helfrich tension coefficient sigma c_A / eps
+  double inv_eta, mobility, k_vol, k_area;
+};
+// slots of the device accumulator array (doubles)
+constexpr int kAccKappa = 0;     // dJ / dkappa
+constexpr int kAccSigma = 1;     // dJ / dsigma
+constexpr int kAccV0 = 2;        // adjoint of the constant V0
+constexpr int kAccA0 = 3;        // adjoint of the constant A0
+constexpr int kAccAreaCoef = 4;  // gammabar K_A c_g of the current step
+constexpr int kAccPhiAdd = 5;    // constant added to phibar by the volume penalty
+constexpr int kAccGamma = 6;     // gammabar of the current step
+constexpr int kAccLambda = 7;    // lambdabar of the current step
+constexpr int kAccCount = 8;
+int adj_blocks(long long ncells);   // partial-sum blocks of one reduction (3 doubles each)
+void launch_adj_source(Ctx& cx, const AdjParams& P, const double* phi, const double* mu,
+                       Comp3<const double> fb, Comp3<double> ab, Comp3<double> bb);
+void launch_adj_divt(Ctx& cx, const AdjParams& P, Comp3<const double> A, double* outA,
+                     Comp3<const double> B, double* outB);
+void launch_adj_mu(Ctx& cx, const AdjParams& P, const double* phi, const double* mub,
+                   const double* gamma, double* g, double* w, double* phib, double* partials,
+                   double* acc, bool area);
+// phib += (*coef) dA/dphi + add_scale (*add); null pointers read as 0
+void launch_adj_area(Ctx& cx, const AdjParams& P, const double* phi, const double* coef,
+                     const double* add, double add_scale, double* phib);
+void launch_adj_update(Ctx& cx, const AdjParams& P, double* phib, const double* phi,
+                       Comp3<const double> psi, Comp3<const double> v0, double dt, Comp3<double> s,
+                       Comp3<double> vb, double* mub, Comp3<double> psib, double* partials,
+                       double* acc);
+void launch_adj_scale(Ctx& cx, const double* y, double* x, long long n, double a);
 
 }  // namespace vsv

@@ -199,7 +199,8 @@ __global__ void k_helfrich_g(PhaseParams P, const T* __restrict__ phi, T* __rest
 }
 
 // CH (fe_kind 0): mu = phi^3 - phi - sigma lap phi.
-// Helfrich: mu = cf2 [(3 phi^2 - 1) g - eps^2 lap g] - gamma_A lap phi.
+// Helfrich: mu = cf2 [(3 phi^2 - 1) g - eps^2 lap g] - gamma_A lap phi
+//           (+ beta_t g with a membrane tension).
 template <class T>
 __global__ void k_mu(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ g,
                      const Scalars* S, T* __restrict__ mu) {
@@ -215,8 +216,10 @@ __global__ void k_mu(PhaseParams P, const T* __restrict__ phi, const T* __restri
   } else {
     ScalarView<T> G{g, P.nx, P.ny, P.nz, P.zper};
     const T lg = lap7<T>(G, i, j, k, ih2);
-    mu[t] = (T)P.cf2 * (((T)3 * f * f - (T)1) * g[t] - (T)(P.eps * P.eps) * lg) -
-            sc_gamma<T>(S) * lphi;
+    T m = (T)P.cf2 * (((T)3 * f * f - (T)1) * g[t] - (T)(P.eps * P.eps) * lg) -
+          sc_gamma<T>(S) * lphi;
+    if (P.beta_t != 0.0) m += (T)P.beta_t * g[t];
+    mu[t] = m;
   }
 }
 
@@ -660,7 +663,7 @@ __global__ void k_helfrich_g_ff(PhaseParams P, const float* __restrict__ phi,
 }
 
 // CH:       mu = phi^3 - phi - sigma lap phi
-// Helfrich: mu = cf2 [(3 phi^2 - 1) g - eps^2 lap g] - gamma_A lap phi
+// Helfrich: mu = cf2 [(3 phi^2 - 1) g - eps^2 lap g] - gamma_A lap phi (+ beta_t g)
 __global__ void k_mu_ff(PhaseParams P, const float* __restrict__ phi, const float* __restrict__ phi_lo,
                         const float* __restrict__ g, const float* __restrict__ g_lo,
                         const Scalars* S, float* __restrict__ mu, float* __restrict__ mu_lo) {
@@ -684,7 +687,8 @@ __global__ void k_mu_ff(PhaseParams P, const float* __restrict__ phi, const floa
   const FF lg = lap7_ff(GH, GL, i, j, k, P.ih2_hi, P.ih2_lo);
   const FF w = ff_add_f(ff_mul_f(ff_mul(f, f), 3.f), -1.f);
   const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2_hi, P.e2_lo})));
-  const FF m = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, S->gamma_af)));
+  FF m = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, S->gamma_af)));
+  if (P.bt_hi != 0.f) m = ff_add(m, ff_mul(gg, FF{P.bt_hi, P.bt_lo}));
   mu[t] = m.hi;
   mu_lo[t] = m.lo;
 }
@@ -895,7 +899,8 @@ __global__ void __launch_bounds__(256) k_mu_ff4(PhaseParams P, const float* __re
       const FF lg = lap7_ff4(GH, GL, o, P.ih2_hi, P.ih2_lo);
       const FF w = ff_add_f(ff_mul_f(ff_mul(f, f), 3.f), -1.f);
       const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2_hi, P.e2_lo})));
-      const FF mm = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, gam)));
+      FF mm = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, gam)));
+      if (P.bt_hi != 0.f) mm = ff_add(mm, ff_mul(gg, FF{P.bt_hi, P.bt_lo}));
       oh[o] = mm.hi;
       ol[o] = mm.lo;
     }

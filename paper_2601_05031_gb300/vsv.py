@@ -28,7 +28,7 @@ VSV_DTYPE_F32, VSV_DTYPE_F64 = 0, 1
  VSV_FIELD_OMEGA_PERT_Z, VSV_FIELD_PSI_PERT_X, VSV_FIELD_PSI_PERT_Y, VSV_FIELD_PSI_PERT_Z,
  VSV_FIELD_COUNT) = range(19)
 (VSV_KCLASS_SMOOTH, VSV_KCLASS_SMOOTH_FINE, VSV_KCLASS_RESTRICT, VSV_KCLASS_PROLONG,
- VSV_KCLASS_PHASE, VSV_KCLASS_COUNT) = range(6)
+ VSV_KCLASS_PHASE, VSV_KCLASS_ADJOINT, VSV_KCLASS_COUNT) = range(7)
 
 
 class vsv_flow_params(C.Structure):
@@ -83,7 +83,8 @@ EXPORTS = [
     "vsv_get_diagnostics", "vsv_get_stress_profile", "vsv_state_bytes", "vsv_get_state",
     "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_last_error", "vsv_kernel_launches",
     "vsv_kernel_bytes", "vsv_profile_enable", "vsv_profile_read", "vsv_batch_create",
-    "vsv_batch_step", "vsv_batch_destroy",
+    "vsv_batch_step", "vsv_batch_destroy", "vsv_tape_create", "vsv_tape_destroy",
+    "vsv_tape_forward", "vsv_tape_backward", "vsv_tape_bytes", "vsv_tape_info",
 ]
 
 
@@ -125,6 +126,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_batch_create": (i32, [C.POINTER(vp), C.POINTER(vp), i32, vp]),
         "vsv_batch_step": (i32, [vp, i32, dbl]),
         "vsv_batch_destroy": (i32, [vp]),
+        "vsv_tape_create": (i32, [C.POINTER(vp), vp, i32, dbl]),
+        "vsv_tape_destroy": (i32, [vp]),
+        "vsv_tape_forward": (i32, [vp, vp, i32, i32, i32, dbl]),
+        "vsv_tape_backward": (i32, [vp, vp, vp, i32, C.POINTER(dbl)]),
+        "vsv_tape_bytes": (sz, [vp]),
+        "vsv_tape_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -317,3 +324,39 @@ def vsv_batch_step(b, nsteps, dt, grids=()):
 
 def vsv_batch_destroy(b):
     return lib().vsv_batch_destroy(b)
+
+
+def vsv_tape_create(g, every, tol=0.0):
+    out = C.c_void_p()
+    st = lib().vsv_tape_create(C.byref(out), g, every, tol)
+    if st != VSV_OK:
+        _check(g, st, "vsv_tape_create")
+    return out
+
+
+def vsv_tape_destroy(t):
+    return lib().vsv_tape_destroy(t)
+
+
+def vsv_tape_forward(t, g, phi0_ptr, dtype, on_device, nsteps, dt):
+    return _check(g, lib().vsv_tape_forward(t, C.c_void_p(phi0_ptr), dtype, int(on_device),
+                                            nsteps, dt), "vsv_tape_forward")
+
+
+def vsv_tape_backward(t, g, phibar_ptr, phibar0_ptr, on_device):
+    """Returns (dJ/dkappa, dJ/dsigma); dJ/dphi^0 is written to phibar0_ptr."""
+    pb = (C.c_double * 2)()
+    _check(g, lib().vsv_tape_backward(t, C.c_void_p(phibar_ptr), C.c_void_p(phibar0_ptr),
+                                      int(on_device), pb), "vsv_tape_backward")
+    return pb[0], pb[1]
+
+
+def vsv_tape_bytes(t) -> int:
+    return lib().vsv_tape_bytes(t)
+
+
+def vsv_tape_info(t):
+    """(adjoint solve cycles, re-run steps, checkpoints) of the last backward pass."""
+    a, r, c = C.c_int64(), C.c_int64(), C.c_int()
+    lib().vsv_tape_info(t, C.byref(a), C.byref(r), C.byref(c))
+    return a.value, r.value, c.value

@@ -80,6 +80,13 @@ def test_null_handles_are_rejected(V):
     arr2 = (ctypes.c_void_p * 1)(1234)   # never dereferenced: the NULL stream is rejected first
     assert lib.vsv_batch_create(ctypes.byref(out), arr2, 1, None) == V.VSV_EINVAL
     assert out.value is None
+    assert lib.vsv_tape_create(ctypes.byref(out), None, 20, 0.0) == V.VSV_EINVAL
+    assert out.value is None
+    assert lib.vsv_tape_destroy(None) == V.VSV_OK
+    assert lib.vsv_tape_forward(None, None, V.VSV_DTYPE_F64, 1, 1, 0.1) == V.VSV_EINVAL
+    assert lib.vsv_tape_backward(None, None, None, 1, None) == V.VSV_EINVAL
+    assert lib.vsv_tape_bytes(None) == 0
+    assert lib.vsv_tape_info(None, None, None, None) == V.VSV_EINVAL
     p = V.vsv_default_solver(V.VSV_MIXED)
     assert p.kind == V.VSV_SOLVER_MG and p.nu1 >= 1 and p.max_cycles > 0
 
