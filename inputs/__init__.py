@@ -223,6 +223,14 @@ def vesicle_poiseuille_256x128x128(seed=0, nx=256, ny=128, nz=128, nsteps=2000) 
                    name=f"vesicle_duct_{nx}x{ny}x{nz}")
 
 
+def vesicle_poiseuille_128x64x64(seed=0, nx=128, ny=64, nz=64, nsteps=200) -> Workload:
+    """Differentiable run: Helfrich vesicle, V_r = 0.8, eps = 1, duct
+    Poiseuille at Ca = 1, kappa = 1 and no tension as the starting point of a
+    parameter fit."""
+    return vesicle(nx, ny, nz, POISEUILLE_DUCT, 0.8, 1.0, seed=seed, nsteps=nsteps,
+                   name=f"vesicle_duct_{nx}x{ny}x{nz}")
+
+
 def vesicle_couette_512x256x256(seed=0, nx=512, ny=256, nz=256, nsteps=500) -> Workload:
     """Helfrich vesicle, V_r = 0.9, eps = 1.5, Couette walls at +-0.05."""
     return vesicle(nx, ny, nz, COUETTE, 0.9, 1.5, seed=seed, nsteps=nsteps,

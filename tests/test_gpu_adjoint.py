@@ -171,3 +171,18 @@ def test_inertial_variant_rejected(V):
     with pytest.raises(V.VsvError):
         t.forward(torch.from_numpy(w.phi0), 2, dt)
     t.close()
+
+
+def test_fit_module_small(V):
+    """The fitting run end to end on a small grid: central differences of
+    the mixed forward map agree with the adjoint within 1e-4 relative, and
+    Adam lowers the loss."""
+    from paper_2601_05031_gb300 import fit
+    res = fit.run(nx=64, ny=32, nz=32, nsteps=20, every=5, adam_steps=4)
+    fd = res["finite_differences"]
+    print({k: v["rel_err"] for k, v in fd.items() if isinstance(v, dict)})
+    for name in ("kappa", "sigma", "phi0_direction"):
+        assert fd[name]["rel_err"] < 1e-4, (name, fd[name])
+    assert res["fit"]["final"]["loss"] < res["start"]["loss"]
+    assert res["tape"]["checkpoints"] == 5 and res["tape"]["recomputed_steps"] == 20
+    assert res["adjoint_kernels"]["launches"] > 0
