@@ -141,8 +141,11 @@ typedef struct {
  * picks the optimal SOR weight for the grid.  variant 0 uses the fastest
  * kernels available for each level (fused single-pass red-black sweeps,
  * tiled transfers and defects where the tile shape allows, the lower levels
- * of a V-cycle in one launch); 1 forces the reference per-level, per-colour
- * kernels (same arithmetic, bit-identical results; for cross-checks).
+ * of a V-cycle in one launch), with partial edge tiles on levels whose
+ * extents are not multiples of the 128 x 16 tile; 1 forces the reference
+ * per-level, per-colour kernels (same arithmetic, bit-identical results; for
+ * cross-checks); 2 is 0 without partial tiles (fast kernels on tile-aligned
+ * levels only, per-colour kernels elsewhere; also bit-identical).
  * extrapolate: order of the first guess of each solve of a time step, from
  * the previous solutions: 0 starts from x^n; 1 from 2 x^n - x^{n-1} (linear
  * extrapolation in time, initial error O(dt^2) instead of O(dt)); 2 from

@@ -334,7 +334,7 @@ bool smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp
   const double h2 = 1.0 / L.inv_h2;
   const int kc = (l == 0) ? VSV_KCLASS_SMOOTH_FINE : VSV_KCLASS_SMOOTH;
   if constexpr (std::is_same<T, float>::value) {
-    if (g->sol.variant == 0 && fused_sweep_ok(L) && g->mg_t[l][0] && nu >= 2) {
+    if (g->sol.variant != 1 && fused_sweep_ok(L, g->sol.variant == 0) && g->mg_t[l][0] && nu >= 2) {
       Comp3<float> Tt = comp3<float>(g->mg_t[l][0], g->mg_t[l][1], g->mg_t[l][2]);
       const int zchunk = 0;   // chosen by the launcher
       const bool fuse_upd = uh && ul && nu % 2 == 0;
@@ -386,7 +386,7 @@ bool vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
     }
     return false;
   }
-  if (l > 0 && x_zero && g->sol.variant == 0 && R.beta == (T)1 && !R.S[0] && !R.S[1] && !R.S[2]) {
+  if (l > 0 && x_zero && g->sol.variant != 1 && R.beta == (T)1 && !R.S[0] && !R.S[1] && !R.S[2]) {
     // the remaining levels fit in one CTA's shared memory: one launch
     CoarseCycle CC{};
     CC.first = l;
@@ -513,7 +513,7 @@ vsv_status solve_dc(vsv_grid* g, const std::vector<Level>& lv, Comp3<float> XH, 
   // number of partial-sum blocks per component written when `norms`
   auto defect = [&](bool norms) -> int {
     double* part = norms ? g->partials : nullptr;
-    if (g->sol.variant == 0) {
+    if (g->sol.variant != 1) {
       const int nb = launch_defect_tiled(g->cx, L, XH, XL, R, BL, RR, ncomp, part,
                                          g->red_blocks * 32 / (2 * ncomp));
       if (nb > 0) return nb;
@@ -1153,10 +1153,10 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
     return fail(g, VSV_EINVAL, "SOR is provided for the FP64 precision only%s");
   if (sp->nu1 < 0 || sp->nu2 < 0 || sp->nu1 + sp->nu2 < 1 || sp->coarse_sweeps < 1 ||
       sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->fixed_cycles_psi < 0 || sp->max_levels < 1 || !(sp->tol >= 0) ||
-      sp->variant < 0 || sp->variant > 1 || sp->extrapolate < 0 || sp->extrapolate > 2)
+      sp->variant < 0 || sp->variant > 2 || sp->extrapolate < 0 || sp->extrapolate > 2)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
-  g->cx.tiled = sp->variant == 0;
+  g->cx.tiled = sp->variant != 1;
   if (g->flow_set) {
     const int per[3] = {1, 0, z_periodic(g) ? 1 : 0};
     g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);

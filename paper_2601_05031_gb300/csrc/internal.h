@@ -155,7 +155,9 @@ bool launch_prolong_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> 
                           int ncomp);
 
 // fused single-pass red-black sweep (smooth.cu)
-bool fused_sweep_ok(const Level& L);
+// ragged: also levels whose extents are not multiples of the tile (partial
+// edge tiles), where enough of the tiles' cells exist
+bool fused_sweep_ok(const Level& L, bool ragged);
 void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
                        int ncomp, int zchunk, int kclass, bool zero_in,
                        const Comp3<float>* upd_hi = nullptr, const Comp3<float>* upd_lo = nullptr);

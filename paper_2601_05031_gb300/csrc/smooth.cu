@@ -91,7 +91,7 @@ __device__ __forceinline__ float* ring(float* base, int plane, int slots, int sl
 // finished one step earlier, plus registers; the ring is deep enough (six x
 // and five rhs slots) that the copies a step issues never land in a slot a
 // warp still in the previous step may read.
-template <bool ZERO_IN, bool HAS_S, bool UPD>
+template <bool ZERO_IN, bool HAS_S, bool UPD, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<float> XH,
              Comp3<float> XL) {
@@ -120,7 +120,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   auto srow = [&](int j, int p) -> float {
     if (!HAS_S) return 0.f;
     const int kk = G.per_z ? wrapi(p, G.nz) : p;
-    return S[(G.per_y ? wrapi(j, G.ny) : j) + (long long)kk * G.ny];
+    return S[(G.per_y ? (RAGGED ? modi(j, G.ny) : wrapi(j, G.ny)) : j) + (long long)kk * G.ny];
   };
 
   StageDesc<kStageA> da;
@@ -133,10 +133,18 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   // planes
   int rown[2], jown[2];
   float rco[2][2];
+  // RAGGED (partial edge tiles): a row past a wall stays the staged zero
+  // ghost (not updated); a row or column past the extent of a periodic axis
+  // holds a wrapped copy whose updates repeat its owner's (same inputs, same
+  // arithmetic), so only the stores to memory are masked
+  bool upd_row[2], st_row[2];
+  const bool xok = !RAGGED || x0 + 4 * gx < G.nx;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     rown[h] = 2 * ty + h + kH;
     jown[h] = y0 + 2 * ty + h;
+    upd_row[h] = !RAGGED || G.per_y || jown[h] < G.ny;
+    st_row[h] = !RAGGED || (jown[h] < G.ny && xok);
     const int yw = G.per_y ? 0 : (jown[h] == 0) + (jown[h] == G.ny - 1);
     rco[h][0] = rc_of(G, yw);
     rco[h][1] = rc_of(G, yw + 1);
@@ -182,6 +190,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       if (black) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
+          if (!st_row[h]) continue;
           const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
           XHp[h] = *reinterpret_cast<const float4*>(uh + gi);
           XLp[h] = *reinterpret_cast<const float4*>(ul + gi);
@@ -217,17 +226,23 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       const float4 B0 = lds4(cB + (rown[0] - 1) * kW + 4 * q);
       const float4 B1 = lds4(cB + (rown[1] - 1) * kW + 4 * q);
       const float4 V0 = V[0];
-      V[0] = rb_group(V[0], U0, V[1], M[0], P[0], Lx[0], Rx[0], B0, par, beta, srow(jown[0], p), h2,
-                      zw ? rco[0][1] : rco[0][0]);
-      V[1] = rb_group(V[1], V0, D1, M[1], P[1], Lx[1], Rx[1], B1, 1 - par, beta, srow(jown[1], p),
-                      h2, zw ? rco[1][1] : rco[1][0]);
+      if (upd_row[0])
+        V[0] = rb_group(V[0], U0, V[1], M[0], P[0], Lx[0], Rx[0], B0, par, beta, srow(jown[0], p),
+                        h2, zw ? rco[0][1] : rco[0][0]);
+      if (upd_row[1])
+        V[1] = rb_group(V[1], V0, D1, M[1], P[1], Lx[1], Rx[1], B1, 1 - par, beta, srow(jown[1], p),
+                        h2, zw ? rco[1][1] : rco[1][0]);
       {
         float* dst = cA + rown[0] * kW + 4 * q;
-        if (par == 0) { dst[0] = V[0].x; dst[2] = V[0].z; }
-        else { dst[1] = V[0].y; dst[3] = V[0].w; }
+        if (upd_row[0]) {
+          if (par == 0) { dst[0] = V[0].x; dst[2] = V[0].z; }
+          else { dst[1] = V[0].y; dst[3] = V[0].w; }
+        }
         dst += kW;
-        if (par == 0) { dst[1] = V[1].y; dst[3] = V[1].w; }
-        else { dst[0] = V[1].x; dst[2] = V[1].z; }
+        if (upd_row[1]) {
+          if (par == 0) { dst[1] = V[1].y; dst[3] = V[1].w; }
+          else { dst[0] = V[1].x; dst[2] = V[1].z; }
+        }
       }
       if (ty == 0 || ty == 7) {   // halo rows y0 - 1 and y0 + kTY
         const int r = (ty == 0) ? 1 : kRA - 2;
@@ -283,12 +298,15 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       const float4 Bq0 = lds4(cBq + (rown[0] - 1) * kW + 4 * q);
       const float4 Bq1 = lds4(cBq + (rown[1] - 1) * kW + 4 * q);
       const float4 M0 = M[0];
-      M[0] = rb_group(M[0], U0, M[1], MM[0], V[0], Lq[0], Rq[0], Bq0, par, beta,
-                      srow(jown[0], qp), h2, zw ? rco[0][1] : rco[0][0]);
-      M[1] = rb_group(M[1], M0, D1, MM[1], V[1], Lq[1], Rq[1], Bq1, 1 - par, beta,
-                      srow(jown[1], qp), h2, zw ? rco[1][1] : rco[1][0]);
+      if (upd_row[0])
+        M[0] = rb_group(M[0], U0, M[1], MM[0], V[0], Lq[0], Rq[0], Bq0, par, beta,
+                        srow(jown[0], qp), h2, zw ? rco[0][1] : rco[0][0]);
+      if (upd_row[1])
+        M[1] = rb_group(M[1], M0, D1, MM[1], V[1], Lq[1], Rq[1], Bq1, 1 - par, beta,
+                        srow(jown[1], qp), h2, zw ? rco[1][1] : rco[1][0]);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
+        if (!st_row[h]) continue;
         const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
         if constexpr (UPD) {
           const FF v0 = ff_add_f(FF{XHp[h].x, XLp[h].x}, M[h].x);
@@ -306,24 +324,48 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   cp_async_wait0();
 }
 
-// Can the fused sweep handle this level?  (All three axes active, x
-// periodic, tile-aligned extents.)
-bool fused_sweep_ok(const Level& L) { return level_ok(L); }
+// Can the fused sweep handle this level?  Tile-aligned levels always; other
+// levels with ragged edge tiles when at least a quarter of the tiles' cells
+// exist (below that the idle lanes cost more than the second per-colour
+// launch saves) and the level has at least 2^17 cells (on smaller levels
+// the few CTAs' z-march takes longer than two per-colour launches: measured
+// 16.8 us against 2 x 5.9 us at 64 x 32 x 32).
+bool fused_sweep_ok(const Level& L, bool ragged) {
+  if (level_ok(L)) return true;
+  return ragged && ragged_ok(L) && tile_fill(L) >= 0.25 && L.cells() >= (1 << 17);
+}
 
 size_t fused_sweep_smem() { return (size_t)(kNA * kRA + kNB * kRB) * kW * sizeof(float); }
 
-template <bool Z, bool HS, bool U>
+template <bool Z, bool HS, bool U, bool RG>
 static void launch_variant(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G,
                            Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<float> XH,
                            Comp3<float> XL) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_rbgs_fused<Z, HS, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_rbgs_fused<Z, HS, U, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    cudaFuncSetAttribute(k_rbgs_fused<Z, HS, U>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_rbgs_fused<Z, HS, U, RG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
     attr_set = true;
   }
-  k_rbgs_fused<Z, HS, U><<<grid, kThreads, smem, s>>>(G, A, B, R, XH, XL);
+  k_rbgs_fused<Z, HS, U, RG><<<grid, kThreads, smem, s>>>(G, A, B, R, XH, XL);
+}
+
+template <bool RG>
+static void launch_pick(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G, Comp3<float> A,
+                        Comp3<float> B, Rhs3<float> R, Comp3<float> XH, Comp3<float> XL, bool upd,
+                        bool zero_in, bool hs) {
+  if (upd) {
+    if (hs) launch_variant<false, true, true, RG>(grid, smem, s, G, A, B, R, XH, XL);
+    else launch_variant<false, false, true, RG>(grid, smem, s, G, A, B, R, XH, XL);
+  } else if (zero_in) {
+    if (hs) launch_variant<true, true, false, RG>(grid, smem, s, G, A, B, R, XH, XL);
+    else launch_variant<true, false, false, RG>(grid, smem, s, G, A, B, R, XH, XL);
+  } else {
+    if (hs) launch_variant<false, true, false, RG>(grid, smem, s, G, A, B, R, XH, XL);
+    else launch_variant<false, false, false, RG>(grid, smem, s, G, A, B, R, XH, XL);
+  }
 }
 
 // One fused full sweep A -> B on `ncomp` components (zero_in: A taken as 0;
@@ -337,7 +379,7 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   FusedGeom G;
   G.nx = L.n[0]; G.ny = L.n[1]; G.nz = L.n[2];
   G.per_y = L.per[1]; G.per_z = L.per[2];
-  G.ntx = L.n[0] / kTX; G.nty = L.n[1] / kTY;
+  G.ntx = (L.n[0] + kTX - 1) / kTX; G.nty = (L.n[1] + kTY - 1) / kTY;
   if (zchunk <= 0) zchunk = pick_zchunk(L, ncomp, 2 * cx.sms, 2);
   G.zchunk = std::min(zchunk, L.n[2]);
   G.rc0 = L.rcf[0];
@@ -355,16 +397,8 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   // iterate's two words read and written when updating)
   const double bpc = zero_in ? 8.0 : (upd ? 24.0 : 12.0);
   cx.before(kclass);
-  if (upd) {
-    if (hs) launch_variant<false, true, true>(grid, smem, cx.stream, G, A, B, R, XH, XL);
-    else launch_variant<false, false, true>(grid, smem, cx.stream, G, A, B, R, XH, XL);
-  } else if (zero_in) {
-    if (hs) launch_variant<true, true, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
-    else launch_variant<true, false, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
-  } else {
-    if (hs) launch_variant<false, true, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
-    else launch_variant<false, false, false>(grid, smem, cx.stream, G, A, B, R, XH, XL);
-  }
+  if (level_ok(L)) launch_pick<false>(grid, smem, cx.stream, G, A, B, R, XH, XL, upd, zero_in, hs);
+  else launch_pick<true>(grid, smem, cx.stream, G, A, B, R, XH, XL, upd, zero_in, hs);
   cx.after(kclass, bpc * (double)L.cells() * ncomp);
 }
 

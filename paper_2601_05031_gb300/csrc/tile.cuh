@@ -33,6 +33,11 @@ struct Geom {
 };
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// i mod n in [0, n) for any i (a tile may span several periods of a short axis)
+__device__ __forceinline__ int modi(int i, int n) {
+  const int r = i % n;
+  return r < 0 ? r + n : r;
+}
 
 // Per-thread staging descriptors for the (up to three) 16-byte vectors a
 // thread copies per plane: shared offset (-1: unused), global row offset
@@ -45,9 +50,9 @@ struct StageVec {
     const int r = t / kNV, v = t - r * kNV;
     int j = y0 - hr + r;
     ok = true;
-    if (G.per_y) j = wrapi(j, G.ny);
+    if (G.per_y) j = modi(j, G.ny);
     else if (j < 0 || j >= G.ny) ok = false;
-    const int x = wrapi(x0 - kHX + 4 * v, G.nx);
+    const int x = modi(x0 - kHX + 4 * v, G.nx);   // nx is a multiple of 4
     soff = t < rows * kNV ? r * kW + 4 * v : -1;
     goff = ok ? j * G.nx + x : 0;
   }
@@ -87,13 +92,29 @@ inline bool level_ok(const Level& L) {
          L.n[1] % kTY == 0 && L.n[2] >= 2;
 }
 
+// Ragged tiling (partial tiles at the x and y edges): every axis active, x
+// periodic with an extent that is a multiple of one 16-byte vector, and at
+// least two cells along y and z so that a cell meets at most one wall per
+// axis.
+inline bool ragged_ok(const Level& L) {
+  return L.act[0] && L.act[1] && L.act[2] && L.per[0] && L.n[0] % 4 == 0 && L.n[1] >= 2 &&
+         L.n[2] >= 2;
+}
+
+// Fraction of a level's tiles that holds cells (1 for tile-aligned levels).
+inline double tile_fill(const Level& L) {
+  const int tx = (L.n[0] + kTX - 1) / kTX, ty = (L.n[1] + kTY - 1) / kTY;
+  return (double)L.n[0] * L.n[1] / ((double)tx * kTX * ty * kTY);
+}
+
 // z-chunk length for a tiled z-marching kernel on level L: the grid is
 // (tiles x chunks x ncomp) CTAs, `slots` of which are resident at a time, and
 // a chunk costs its planes plus about `halo` extra planes of pipeline fill.
 // Picks the chunk that minimises waves x (chunk + halo).
 inline int pick_zchunk(const Level& L, int ncomp, int slots, int halo) {
   const int nz = L.n[2];
-  const long long tiles = (long long)(L.n[0] / kTX) * (L.n[1] / kTY) * ncomp;
+  const long long tiles =
+      (long long)((L.n[0] + kTX - 1) / kTX) * ((L.n[1] + kTY - 1) / kTY) * ncomp;
   if (slots < 1) slots = 1;
   double best = 0.0;
   int best_chunk = nz;
@@ -115,7 +136,7 @@ inline Geom geom(const Level& L, int zchunk) {
   Geom G;
   G.nx = L.n[0]; G.ny = L.n[1]; G.nz = L.n[2];
   G.per_y = L.per[1]; G.per_z = L.per[2];
-  G.ntx = L.n[0] / kTX; G.nty = L.n[1] / kTY;
+  G.ntx = (L.n[0] + kTX - 1) / kTX; G.nty = (L.n[1] + kTY - 1) / kTY;
   G.zchunk = zchunk > 0 ? (zchunk < L.n[2] ? zchunk : L.n[2]) : L.n[2];
   return G;
 }
