@@ -400,6 +400,11 @@ vsv_status vsv_batch_destroy(vsv_batch* b);
  * checkpoint and leaves the grid at the state of step nsteps.  It returns
  * when the results are written.  VSV_ESTATE without a forward pass.
  *
+ * vsv_tape_set_cycles: fixed_cycles > 0 runs every adjoint solve for exactly
+ * that many cycles (V-cycles, or defect corrections on the mixed path) from
+ * the previous reverse step's solution, with no host synchronisation; 0
+ * (the default) solves to `tol`.  VSV_EINVAL for a NULL tape or a negative
+ * count.
  * vsv_tape_destroy frees the tape's device memory (NULL is a no-op).
  * vsv_tape_bytes: device bytes held by the tape (checkpoints included).
  * vsv_tape_info: adjoint solve cycles and re-run steps of the last backward
@@ -411,6 +416,7 @@ vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_dev
                             double dt);
 vsv_status vsv_tape_backward(vsv_tape* t, const double* phibar_final, double* phibar0,
                              int on_device, double* param_bar);
+vsv_status vsv_tape_set_cycles(vsv_tape* t, int fixed_cycles);
 size_t vsv_tape_bytes(const vsv_tape* t);
 vsv_status vsv_tape_info(const vsv_tape* t, int64_t* adjoint_cycles, int64_t* recomputed_steps,
                          int* checkpoints);

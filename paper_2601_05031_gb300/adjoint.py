@@ -34,6 +34,11 @@ class Tape:
                   k_area=w.k_area, k_vol=w.k_vol)
         return cls(sim, fe, every, tol)
 
+    def set_cycles(self, fixed_cycles: int):
+        """Fixed cycles per adjoint solve (no host synchronisation); 0 solves
+        to the tape's tolerance."""
+        V.vsv_tape_set_cycles(self.t, self.sim.g, fixed_cycles)
+
     def set_params(self, kappa: float, sigma: float):
         self.fe["kappa"], self.fe["sigma"] = float(kappa), float(sigma)
         f = self.fe

@@ -1807,6 +1807,7 @@ struct vsv_tape {
   vsv_grid* g = nullptr;
   int every = 20;
   double tol = 1e-11;
+  int fixed = 0;                       // > 0: cycles per adjoint solve, no host synchronisation
   int nsteps = 0;
   double dt = 0.0;
   bool recorded = false;
@@ -1972,21 +1973,21 @@ vsv_status tape_solves(vsv_tape* t) {
   vsv_status st;
   if (g->prec == VSV_FP64) {
     Rhs3<double> R1{{t->psib[0], t->psib[1], t->psib[2]}, {nullptr, nullptr, nullptr}, 1.0};
-    st = solve<double>(g, g->flow_levels, mc3(t->x1), R1, 3, VSV_SOLVER_MG, 0, t->tol, 400, every,
+    st = solve<double>(g, g->flow_levels, mc3(t->x1), R1, 3, VSV_SOLVER_MG, t->fixed, t->tol, 400, every,
                        &c1, &r1);
     if (st != VSV_OK) return st;
     Rhs3<double> R2{{t->x1[0], t->x1[1], t->x1[2]}, {nullptr, nullptr, nullptr}, -1.0};
-    st = solve<double>(g, g->flow_levels, mc3(t->fb), R2, 3, VSV_SOLVER_MG, 0, t->tol, 400, every,
+    st = solve<double>(g, g->flow_levels, mc3(t->fb), R2, 3, VSV_SOLVER_MG, t->fixed, t->tol, 400, every,
                        &c2, &r2);
     if (st != VSV_OK) return st;
   } else {
     for (int c = 0; c < 3; ++c) launch_split_ff(g->cx, t->psib[c], t->bh[c], t->bl[c], g->N);
     Rhs3<float> R1{{t->bh[0], t->bh[1], t->bh[2]}, {nullptr, nullptr, nullptr}, 1.f};
-    st = solve_dc(g, g->flow_levels, mc3(t->x1h), mc3(t->x1l), R1, mc3(t->bl), 3, 0, t->tol, 400,
+    st = solve_dc(g, g->flow_levels, mc3(t->x1h), mc3(t->x1l), R1, mc3(t->bl), 3, t->fixed, t->tol, 400,
                   every, &c1, &r1);
     if (st != VSV_OK) return st;
     Rhs3<float> R2{{t->x1h[0], t->x1h[1], t->x1h[2]}, {nullptr, nullptr, nullptr}, -1.f};
-    st = solve_dc(g, g->flow_levels, mc3(t->fbh), mc3(t->fbl), R2, mc3(t->x1l), 3, 0, t->tol, 400,
+    st = solve_dc(g, g->flow_levels, mc3(t->fbh), mc3(t->fbl), R2, mc3(t->x1l), 3, t->fixed, t->tol, 400,
                   every, &c2, &r2);
     if (st != VSV_OK) return st;
     for (int c = 0; c < 3; ++c) launch_merge_ff(g->cx, t->fbh[c], t->fbl[c], t->fb[c], g->N);
@@ -2048,6 +2049,12 @@ vsv_status vsv_tape_destroy(vsv_tape* t) {
 }
 
 size_t vsv_tape_bytes(const vsv_tape* t) { return t ? t->dev_bytes : 0; }
+
+vsv_status vsv_tape_set_cycles(vsv_tape* t, int fixed_cycles) {
+  if (!t || fixed_cycles < 0) return VSV_EINVAL;
+  t->fixed = fixed_cycles;
+  return VSV_OK;
+}
 
 vsv_status vsv_tape_info(const vsv_tape* t, int64_t* adjoint_cycles, int64_t* recomputed_steps,
                          int* checkpoints) {

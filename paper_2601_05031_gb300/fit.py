@@ -62,7 +62,7 @@ def _timed(fn):
 
 def run(nx=128, ny=64, nz=64, nsteps=200, every=20, kappa_true=2.0, sigma_true=0.5, kappa0=1.0,
         sigma0=0.0, adam_steps=50, lr=0.08, fd_step=1e-4, precision=V.VSV_MIXED, seed=0,
-        solve_tol=None):
+        solve_tol=None, adjoint_cycles=4):
     w = inputs.vesicle_poiseuille_128x64x64(seed=seed, nx=nx, ny=ny, nz=nz, nsteps=nsteps)
     dt = w.dt
     tape = Tape.from_workload(w, precision, every=every)
@@ -70,6 +70,8 @@ def run(nx=128, ny=64, nz=64, nsteps=200, every=20, kappa_true=2.0, sigma_true=0
     if solve_tol is not None:
         sp.tol = solve_tol
     V.vsv_set_solver(tape.sim.g, sp)
+    if adjoint_cycles:
+        tape.set_cycles(adjoint_cycles)
     dev = tape.sim.device
     phi0 = torch.from_numpy(w.phi0).to(dev)
     h3 = w.h ** 3
@@ -137,6 +139,8 @@ def run(nx=128, ny=64, nz=64, nsteps=200, every=20, kappa_true=2.0, sigma_true=0
     out = {
         "workload": w.name, "precision": "mixed" if precision == V.VSV_MIXED else "fp64",
         "steps": nsteps, "checkpoint_every": every, "dt": dt,
+        "adjoint_solves": (f"{adjoint_cycles} fixed cycles" if adjoint_cycles
+                           else "to a relative residual of 1e-11"),
         "target": {"kappa": kappa_true, "sigma": sigma_true},
         "start": {"kappa": kappa0, "sigma": sigma0, "loss": float(J0)},
         "gradient": {"kappa": g_kappa, "sigma": g_sigma,
@@ -166,11 +170,13 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=0.08)
     ap.add_argument("--fd-step", type=float, default=1e-4)
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--adjoint-cycles", type=int, default=4,
+                    help="fixed cycles per adjoint solve (0: to a relative residual of 1e-11)")
     ap.add_argument("--grid", type=int, nargs=3, default=(128, 64, 64), metavar=("NX", "NY", "NZ"))
     ap.add_argument("--out", default=None, help="also write the JSON here")
     a = ap.parse_args(argv)
     res = run(nx=a.grid[0], ny=a.grid[1], nz=a.grid[2], nsteps=a.steps, every=a.every,
-              adam_steps=a.adam, lr=a.lr, fd_step=a.fd_step,
+              adam_steps=a.adam, lr=a.lr, fd_step=a.fd_step, adjoint_cycles=a.adjoint_cycles,
               precision=V.VSV_MIXED if a.precision == "mixed" else V.VSV_FP64)
     line = json.dumps(res)
     print(line)

@@ -84,7 +84,8 @@ EXPORTS = [
     "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_last_error", "vsv_kernel_launches",
     "vsv_kernel_bytes", "vsv_profile_enable", "vsv_profile_read", "vsv_batch_create",
     "vsv_batch_step", "vsv_batch_destroy", "vsv_tape_create", "vsv_tape_destroy",
-    "vsv_tape_forward", "vsv_tape_backward", "vsv_tape_bytes", "vsv_tape_info",
+    "vsv_tape_forward", "vsv_tape_backward", "vsv_tape_set_cycles", "vsv_tape_bytes",
+    "vsv_tape_info",
 ]
 
 
@@ -130,6 +131,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_tape_destroy": (i32, [vp]),
         "vsv_tape_forward": (i32, [vp, vp, i32, i32, i32, dbl]),
         "vsv_tape_backward": (i32, [vp, vp, vp, i32, C.POINTER(dbl)]),
+        "vsv_tape_set_cycles": (i32, [vp, i32]),
         "vsv_tape_bytes": (sz, [vp]),
         "vsv_tape_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
     }
@@ -349,6 +351,10 @@ def vsv_tape_backward(t, g, phibar_ptr, phibar0_ptr, on_device):
     _check(g, lib().vsv_tape_backward(t, C.c_void_p(phibar_ptr), C.c_void_p(phibar0_ptr),
                                       int(on_device), pb), "vsv_tape_backward")
     return pb[0], pb[1]
+
+
+def vsv_tape_set_cycles(t, g, fixed_cycles):
+    return _check(g, lib().vsv_tape_set_cycles(t, fixed_cycles), "vsv_tape_set_cycles")
 
 
 def vsv_tape_bytes(t) -> int:

@@ -86,6 +86,7 @@ def test_null_handles_are_rejected(V):
     assert lib.vsv_tape_forward(None, None, V.VSV_DTYPE_F64, 1, 1, 0.1) == V.VSV_EINVAL
     assert lib.vsv_tape_backward(None, None, None, 1, None) == V.VSV_EINVAL
     assert lib.vsv_tape_bytes(None) == 0
+    assert lib.vsv_tape_set_cycles(None, 3) == V.VSV_EINVAL
     assert lib.vsv_tape_info(None, None, None, None) == V.VSV_EINVAL
     p = V.vsv_default_solver(V.VSV_MIXED)
     assert p.kind == V.VSV_SOLVER_MG and p.nu1 >= 1 and p.max_cycles > 0

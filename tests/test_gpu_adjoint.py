@@ -140,6 +140,34 @@ def test_gradient_vs_central_differences_of_gpu_forward(V):
     assert abs(fd - float(np.sum(g * d))) <= 1e-4 * abs(fd)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fixed_cycle_adjoint_solves(V, prec):
+    """Adjoint solves with a fixed number of cycles from the previous reverse
+    step's solution (no host synchronisation) stay close to the converged
+    gradient, and run exactly that many cycles."""
+    import torch
+    w, dt, target = _case("helfrich_duct")
+    N = 6
+    ref = _gpu_gradient(V, w, dt, target, N, prec, 3)
+    errs = {}
+    for fixed in (2, 4):
+        t = _tape(V, w, prec, 3)
+        t.set_cycles(fixed)
+        phiN = t.forward(torch.from_numpy(w.phi0), N, dt)
+        pb = w.h ** 3 * (phiN - torch.from_numpy(target).to(phiN.device))
+        g0, dk, ds = t.backward(pb)
+        assert t.info()["adjoint_cycles"] == 2 * fixed * (N + 1)
+        errs[fixed] = (rel(g0.cpu().numpy(), ref[1]), abs(dk - ref[2]) / abs(ref[2]),
+                       abs(ds - ref[3]) / abs(ref[3]))
+        t.close()
+    print(prec, errs)
+    # measured in FP64: 4 cycles 4e-6, 2 cycles 6e-4 (dJ/dsigma, the most
+    # sensitive of the three); more cycles, smaller differences
+    assert max(errs[4]) < 2e-5, errs
+    assert max(errs[2]) < 2e-3, errs
+    assert all(a < b for a, b in zip(errs[4], errs[2])), errs
+
+
 def test_autograd_function_matches_tape(V):
     """The torch.autograd.Function returns the tape's gradients for a loss
     written in torch."""
