@@ -515,7 +515,7 @@ vsv_status solve_dc(vsv_grid* g, const std::vector<Level>& lv, Comp3<float> XH, 
     double* part = norms ? g->partials : nullptr;
     if (g->sol.variant != 1) {
       const int nb = launch_defect_tiled(g->cx, L, XH, XL, R, BL, RR, ncomp, part,
-                                         g->red_blocks * 32 / (2 * ncomp));
+                                         g->red_blocks * 32 / (2 * ncomp), g->sol.variant == 0);
       if (nb > 0) return nb;
     }
     launch_defect_dw(g->cx, L, XH, XL, R, BL, RR, ncomp, part, g->red_blocks);
@@ -1157,6 +1157,7 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
   g->cx.tiled = sp->variant != 1;
+  g->cx.ragged = sp->variant == 0;
   if (g->flow_set) {
     const int per[3] = {1, 0, z_periodic(g) ? 1 : 0};
     g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);

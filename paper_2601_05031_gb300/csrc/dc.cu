@@ -229,7 +229,9 @@ __device__ __forceinline__ float defect_cell(float xmh, float xph, float ymh, fl
 }
 }  // namespace
 
-template <int ROWS>
+// RAGGED: partial edge tiles; cells past the extent (wrapped copies or zero
+// ghost rows in the staged planes) are skipped.
+template <int ROWS, bool RAGGED>
 __global__ void __launch_bounds__(tile::kThreads, ROWS == 1 ? 3 : 2)
 k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3<float> BL,
                Comp3<float> OUT, double* partials) {
@@ -307,6 +309,7 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
 #pragma unroll
     for (int h = 0; h < ROWS; ++h) {
       const int r = rown[h], j = jown[h];
+      if (RAGGED && (j >= G.ny || x0 + 4 * gx >= G.nx)) continue;
       const float* rowH = cH + r * kW;
       const float* rowL = cL + r * kW;
       const float4 Uh = lds4(rowH - kW + 4 * q), Dh = lds4(rowH + kW + 4 * q);
@@ -355,12 +358,17 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
 // launches the tiled defect when the level allows it; returns the number of
 // partial-sum blocks per component (0 if it did not launch)
 int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
-                        Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int max_blocks) {
-  if (!tile::level_ok(L)) return 0;
+                        Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int max_blocks,
+                        bool ragged) {
+  const bool aligned = tile::level_ok(L);
+  if (!aligned && !(ragged && tile::ragged_ok(L) && tile::tile_fill(L) >= 0.25 &&
+                    L.cells() >= (1 << 17)))
+    return 0;
   // one row per thread: 8-row tiles, three CTAs per SM
   constexpr int ROWS = 1;
   using Sh = DefShape<ROWS>;
-  const int tiles = (L.n[0] / tile::kTX) * (L.n[1] / Sh::kRows);
+  const int ntx = (L.n[0] + tile::kTX - 1) / tile::kTX, nty = (L.n[1] + Sh::kRows - 1) / Sh::kRows;
+  const int tiles = ntx * nty;
   int chunk = tile::pick_zchunk(L, ncomp, 3 * cx.sms, 2);
   chunk = std::max(chunk, 1);
   // pick_zchunk counts 128 x 16 tiles; there are twice as many 8-row tiles
@@ -370,7 +378,7 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
   if (tiles * nz * ncomp > max_blocks) return 0;
   DefGeom G;
   static_cast<tile::Geom&>(G) = tile::geom(L, chunk);
-  G.nty = L.n[1] / Sh::kRows;
+  G.nty = nty;
   G.ih_hi = (float)L.inv_h2;
   G.ih_lo = (float)(L.inv_h2 - (double)G.ih_hi);
   G.beta = R.beta;
@@ -378,13 +386,24 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
   G.dcl = L.cdl[0];
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_defect_tiled<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmem);
-    cudaFuncSetAttribute(k_defect_tiled<ROWS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_defect_tiled<ROWS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Sh::kSmem);
+    cudaFuncSetAttribute(k_defect_tiled<ROWS, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
+    cudaFuncSetAttribute(k_defect_tiled<ROWS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Sh::kSmem);
+    cudaFuncSetAttribute(k_defect_tiled<ROWS, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
     attr = true;
   }
   dim3 grid(tiles, nz, ncomp);
   cx.before(VSV_KCLASS_RESTRICT);
-  k_defect_tiled<ROWS><<<grid, tile::kThreads, Sh::kSmem, cx.stream>>>(G, XH, XL, R, BL, OUT, partials);
+  if (aligned)
+    k_defect_tiled<ROWS, false><<<grid, tile::kThreads, Sh::kSmem, cx.stream>>>(G, XH, XL, R, BL, OUT,
+                                                                                partials);
+  else
+    k_defect_tiled<ROWS, true><<<grid, tile::kThreads, Sh::kSmem, cx.stream>>>(G, XH, XL, R, BL, OUT,
+                                                                               partials);
   // x_hi, x_lo, b_hi (, b_lo) read, r written
   cx.after(VSV_KCLASS_RESTRICT, (BL.p[0] ? 20.0 : 16.0) * (double)L.cells() * ncomp);
   return tiles * nz;

@@ -15,7 +15,8 @@ namespace vsv {
 struct Ctx {
   cudaStream_t stream = nullptr;
   int sms = 148;                 // multiprocessors of the grid's device (set at create)
-  int tiled = 1;                 // use the tiled transfer kernels (solver variant 0)
+  int tiled = 1;                 // use the tiled transfer kernels (solver variants 0 and 2)
+  int ragged = 1;                // also with partial edge tiles (solver variant 0)
   long long launches = 0;
   int prof_class = -1;
   std::vector<cudaEvent_t> ev;   // pairs (start, stop)
@@ -135,9 +136,10 @@ void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL,
                       Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int nblocks);
 void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E, long long n,
                       int ncomp);
+// ragged: also levels that are not tile multiples (partial edge tiles)
 int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
                         Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials,
-                        int max_blocks);
+                        int max_blocks, bool ragged);
 // first guess of order 0..2 from (A, B, C) = (x^n, x^{n-1}, x^{n-2}), written into C
 void launch_extrapolate_rot_dw(Ctx& cx, Comp3<float> AH, Comp3<float> AL, Comp3<float> BH,
                                Comp3<float> BL, Comp3<float> CH, Comp3<float> CL, long long n,

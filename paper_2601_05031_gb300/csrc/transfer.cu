@@ -35,7 +35,10 @@ __device__ __forceinline__ float c4(const float4& v, int o) {
 // neighbours in x / y come from the staged plane, z neighbours from the
 // thread's registers.  Copies run two steps ahead; five ring slots make one
 // barrier per step enough (as in the tiled defect kernel).
-template <bool HAS_S>
+// RAGGED: partial edge tiles; threads whose fine cells lie past the extent
+// read no rhs and store nothing (their staged neighbours are wrapped copies
+// or zero ghosts, never used for an owned cell's result).
+template <bool HAS_S, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 3)
 k_restrict_tiled(RGeom G, Comp3<float> X, Rhs3<float> R, Comp3<float> RC) {
   extern __shared__ float4 smem_r4[];
@@ -63,15 +66,20 @@ k_restrict_tiled(RGeom G, Comp3<float> X, Rhs3<float> R, Comp3<float> RC) {
     rown[h] = 2 * ty + h + 1;
     yw[h] = G.per_y ? 0 : (jown[h] == 0) + (jown[h] == G.ny - 1);
   }
+  // both fine rows of a thread lie inside or outside together (ny is even)
+  const bool act = !RAGGED || (jown[0] < G.ny && x0 + 4 * gx < G.nx);
   for (int pl = zb - 1; pl <= zb + 1; ++pl) ds.stage(slot(pl), x, G, pl, false);
   cp_async_commit();
   if (zb + 2 <= ze) ds.stage(slot(zb + 2), x, G, zb + 2, false);
   cp_async_commit();
   // rhs of plane zb
-  float4 Bn[2];
+  float4 Bn[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+  if (act) {
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
-    Bn[h] = *reinterpret_cast<const float4*>(bsrc + ((long long)zb * G.ny + jown[h]) * G.nx + x0 + 4 * gx);
+    for (int h = 0; h < 2; ++h)
+      Bn[h] = *reinterpret_cast<const float4*>(bsrc + ((long long)zb * G.ny + jown[h]) * G.nx + x0 +
+                                               4 * gx);
+  }
   cp_async_wait1();
   __syncthreads();
   float4 Mz[2], Vz[2], Pz[2];
@@ -88,7 +96,7 @@ k_restrict_tiled(RGeom G, Comp3<float> X, Rhs3<float> R, Comp3<float> RC) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       Bc[h] = Bn[h];
-      if (p + 1 < ze)
+      if (p + 1 < ze && act)
         Bn[h] = *reinterpret_cast<const float4*>(bsrc + ((long long)(p + 1) * G.ny + jown[h]) * G.nx +
                                                  x0 + 4 * gx);
     }
@@ -107,7 +115,7 @@ k_restrict_tiled(RGeom G, Comp3<float> X, Rhs3<float> R, Comp3<float> RC) {
       const float* row = cX + rown[h] * kW;
       const float4 U = lds4(row - kW + 4 * q), D = lds4(row + kW + 4 * q);
       const float Lx = row[4 * q - 1], Rx = row[4 * q + 4];
-      const float s_ = HAS_S ? S[jown[h] + (long long)p * G.ny] : 0.f;
+      const float s_ = (HAS_S && act) ? S[jown[h] + (long long)p * G.ny] : 0.f;
       const int nwall = yw[h] + zw;
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
@@ -119,7 +127,7 @@ k_restrict_tiled(RGeom G, Comp3<float> X, Rhs3<float> R, Comp3<float> RC) {
         if (o < 2) acc0 += r; else acc1 += r;
       }
     }
-    if (p & 1) {   // plane pair complete: store the two coarse cells
+    if ((p & 1) && act) {   // plane pair complete: store the two coarse cells
       const int K = p >> 1, J = (y0 >> 1) + ty, I = (x0 >> 1) + 2 * gx;
       *reinterpret_cast<float2*>(rc + ((long long)K * G.cny + J) * G.cnx + I) =
           make_float2(acc0 * 0.125f, acc1 * 0.125f);
@@ -153,6 +161,9 @@ struct PGeom {
 // planes are staged (rows J0 - 1 .. J0 + 8) two steps ahead into a six-slot
 // ring; a step handles the fine planes 2K and 2K + 1 of coarse plane K, whose
 // fine values are read and written straight from registers.
+// RAGGED: partial edge tiles (coarse x extent a multiple of 4); threads whose
+// fine cells lie past the extent read and write nothing.
+template <bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 3)
 k_prolong_tiled(PGeom G, Comp3<float> X, Comp3<float> E) {
   __shared__ __align__(16) float sE[kPS * kPRows * kPW];
@@ -171,9 +182,10 @@ k_prolong_tiled(PGeom G, Comp3<float> X, Comp3<float> E) {
   const int st_r = tid / kPNV, st_v = tid - st_r * kPNV;
   int st_j = J0 - 1 + st_r;
   bool st_ok = st_used;
-  if (G.per_y) st_j = wrapi(st_j, G.cny);
+  if (G.per_y) st_j = RAGGED ? modi(st_j, G.cny) : wrapi(st_j, G.cny);
   else if (st_j < 0 || st_j >= G.cny) st_ok = false;
-  const int st_i = wrapi(I0 - kHX + 4 * st_v, G.cnx);
+  const int st_i = RAGGED ? modi(I0 - kHX + 4 * st_v, G.cnx) : wrapi(I0 - kHX + 4 * st_v, G.cnx);
+  const bool act = !RAGGED || (y0 + 2 * ty < G.ny && x0 + 4 * gx < G.nx);
   const int st_goff = st_ok ? st_j * G.cnx + st_i : 0;
   const int st_soff = st_r * kPW + 4 * st_v;
   auto stage = [&](int K) {
@@ -213,8 +225,9 @@ k_prolong_tiled(PGeom G, Comp3<float> X, Comp3<float> E) {
     for (int c = 0; c < 2; ++c)
 #pragma unroll
       for (int b = 0; b < 2; ++b)
-        F[c][b] = *reinterpret_cast<const float4*>(
-            x + ((long long)(2 * K + c) * G.ny + y0 + 2 * ty + b) * G.nx + x0 + 4 * gx);
+        F[c][b] = act ? *reinterpret_cast<const float4*>(
+                            x + ((long long)(2 * K + c) * G.ny + y0 + 2 * ty + b) * G.nx + x0 + 4 * gx)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
     cp_async_wait2();
     __syncthreads();
     // coarse planes: centre K and the neighbour below (c = 0) / above (c = 1)
@@ -264,7 +277,8 @@ k_prolong_tiled(PGeom G, Comp3<float> X, Comp3<float> E) {
         v.y += out[1];
         v.z += out[2];
         v.w += out[3];
-        *reinterpret_cast<float4*>(x + ((long long)(2 * K + c) * G.ny + y0 + 2 * ty + b) * G.nx +
+        if (act)
+          *reinterpret_cast<float4*>(x + ((long long)(2 * K + c) * G.ny + y0 + 2 * ty + b) * G.nx +
                                    x0 + 4 * gx) = v;
       }
     }
@@ -273,11 +287,15 @@ k_prolong_tiled(PGeom G, Comp3<float> X, Comp3<float> E) {
 }
 
 // ---------------------------------------------------------------- launchers
-bool tiled_transfer_ok(const Level& F, const Level& C) {
-  if (!level_ok(F)) return false;
+// ragged: also levels with partial edge tiles (fine x extent a multiple of 8,
+// so that coarse rows stage as whole 16-byte vectors), under the size and
+// fill thresholds of the fused sweep
+bool tiled_transfer_ok(const Level& F, const Level& C, bool ragged) {
   for (int a = 0; a < 3; ++a)
     if (F.n[a] != 2 * C.n[a]) return false;
-  return true;
+  if (level_ok(F)) return true;
+  return ragged && ragged_ok(F) && F.n[0] % 8 == 0 && tile_fill(F) >= 0.25 &&
+         F.cells() >= (1 << 17);
 }
 
 static int even_chunk(const Level& F, int ncomp, int sms, int halo) {
@@ -288,7 +306,8 @@ static int even_chunk(const Level& F, int ncomp, int sms, int halo) {
 
 bool launch_restrict_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> X,
                            Rhs3<float> R, Comp3<float> RC, int ncomp) {
-  if (!tiled_transfer_ok(F, C)) return false;
+  if (!tiled_transfer_ok(F, C, cx.ragged)) return false;
+  const bool rg = !level_ok(F);
   RGeom G;
   static_cast<Geom&>(G) = geom(F, even_chunk(F, ncomp, cx.sms, 2));
   G.ih2 = F.inv_h2f;
@@ -300,31 +319,40 @@ bool launch_restrict_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float>
   const size_t smem = (size_t)kRS * kRR * kW * sizeof(float);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_restrict_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_restrict_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_restrict_tiled<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_restrict_tiled<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_restrict_tiled<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_restrict_tiled<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   dim3 grid(G.ntx * G.nty, (F.n[2] + G.zchunk - 1) / G.zchunk, ncomp);
   cx.before(VSV_KCLASS_RESTRICT);
-  if (R.S[0]) k_restrict_tiled<true><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
-  else k_restrict_tiled<false><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
+  if (R.S[0]) {
+    if (rg) k_restrict_tiled<true, true><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
+    else k_restrict_tiled<true, false><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
+  } else {
+    if (rg) k_restrict_tiled<false, true><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
+    else k_restrict_tiled<false, false><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
+  }
   cx.after(VSV_KCLASS_RESTRICT, 8.5 * (double)F.cells() * ncomp);   // e, b read; r_c written
   return true;
 }
 
 bool launch_prolong_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> X, Comp3<float> E,
                           int ncomp) {
-  if (!tiled_transfer_ok(F, C)) return false;
+  if (!tiled_transfer_ok(F, C, cx.ragged)) return false;
+  const bool rg = !level_ok(F);
   PGeom G;
   G.nx = F.n[0]; G.ny = F.n[1]; G.nz = F.n[2];
   G.cnx = C.n[0]; G.cny = C.n[1]; G.cnz = C.n[2];
   G.per_y = C.per[1]; G.per_z = C.per[2];
-  G.ntx = F.n[0] / kTX; G.nty = F.n[1] / kTY;
+  G.ntx = (F.n[0] + kTX - 1) / kTX; G.nty = (F.n[1] + kTY - 1) / kTY;
   G.zchunk = even_chunk(F, ncomp, cx.sms, 2);
   G.malpha = -C.alphaf;
   dim3 grid(G.ntx * G.nty, (F.n[2] + G.zchunk - 1) / G.zchunk, ncomp);
   cx.before(VSV_KCLASS_PROLONG);
-  k_prolong_tiled<<<grid, kThreads, 0, cx.stream>>>(G, X, E);
+  if (rg) k_prolong_tiled<true><<<grid, kThreads, 0, cx.stream>>>(G, X, E);
+  else k_prolong_tiled<false><<<grid, kThreads, 0, cx.stream>>>(G, X, E);
   cx.after(VSV_KCLASS_PROLONG, 8.5 * (double)F.cells() * ncomp);   // e read and written, e_c read
   return true;
 }
