@@ -1,6 +1,9 @@
 """Schedule autotuner for the mixed path: per size class, the cheapest fixed
 multigrid schedule (V-cycles per solve, order of the first guess in time)
-whose velocity stays within a target of the converged answer.
+whose velocity stays within a target of the converged answer, and the
+faster tiling mode for it (solver variant 0: fused and tiled kernels with
+partial edge tiles; variant 2: those kernels on tile-aligned levels only,
+per-colour and row kernels elsewhere).
 
 A fixed schedule (``fixed_cycles`` > 0) is what batched stepping and the
 benchmark use: no host synchronisation inside a step.  How many cycles it
@@ -9,7 +12,8 @@ body, so it is measured rather than guessed: each candidate runs a few steps
 from the workload's initial state and is compared with the same steps solved
 to a relative residual of ``ref_tol`` (FP64-class on the mixed path).  The
 cheapest candidate by measured step time that stays below ``target / margin``
-wins.  Results are cached per size class (flow, free energy, and the powers of
+wins.  The two tiling modes give bit-identical results, so they are compared
+by time alone, on the winning schedule.  Results are cached per size class (flow, free energy, and the powers of
 two nearest to the extents), so a batch of many problems tunes each class
 once.
 
@@ -37,6 +41,8 @@ class TunedSchedule:
     ms_per_step: float
     vel_err: float
     trials: list
+    variant: int = 0          # tiling mode (solver variant 0 or 2)
+    tiling_ms: dict = None    # ms per step of the winning schedule per tiling mode
 
 
 _CACHE: dict = {}
@@ -73,7 +79,7 @@ def _run(w, steps, solver_setup):
 
 
 def tune(w, target=1e-6, margin=3.0, steps=6, candidates=DEFAULT_CANDIDATES, ref_tol=1e-11,
-         use_cache=True) -> TunedSchedule:
+         use_cache=True, tilings=(0, 2)) -> TunedSchedule:
     """Cheapest (fixed_cycles, extrapolate) for workload ``w`` whose relative
     L2 velocity error after ``steps`` steps is below target / margin."""
     key = size_class(w)
@@ -102,7 +108,17 @@ def tune(w, target=1e-6, margin=3.0, steps=6, candidates=DEFAULT_CANDIDATES, ref
     if best is None:   # nothing met the target: the most accurate candidate
         t = min(trials, key=lambda r: r["vel_err"])
         best = (t["fixed_cycles"], t["extrapolate"], t["ms_per_step"], t["vel_err"])
-    out = TunedSchedule(best[0], best[1], best[2], best[3], trials)
+    # tiling mode on the winning schedule: best of two timed runs each
+    tiling_ms = {}
+    for variant in tilings:
+        def tsetup(sp, variant=variant):
+            sp.fixed_cycles = best[0]
+            sp.extrapolate = best[1]
+            sp.variant = variant
+        tiling_ms[variant] = min(_run(w, steps, tsetup)[1] for _ in range(2))
+    var = min(tiling_ms, key=tiling_ms.get) if tiling_ms else 0
+    out = TunedSchedule(best[0], best[1], tiling_ms.get(var, best[2]), best[3], trials, var,
+                        tiling_ms)
     if use_cache:
         _CACHE[key] = out
     return out
@@ -113,4 +129,5 @@ def apply(sim, schedule: TunedSchedule):
     sp = sim.solver_params()
     sp.fixed_cycles = schedule.fixed_cycles
     sp.extrapolate = schedule.extrapolate
+    sp.variant = schedule.variant
     V.vsv_set_solver(sim.g, sp)

@@ -89,7 +89,11 @@ def test_autotune_picks_cheapest_schedule_meeting_target(V):
     ok = [t for t in s.trials if t["vel_err"] * 3.0 <= 1e-6]
     assert ok, s.trials
     assert s.vel_err * 3.0 <= 1e-6
-    assert s.ms_per_step == min(t["ms_per_step"] for t in ok)
+    best = min(ok, key=lambda t: t["ms_per_step"])
+    assert (s.fixed_cycles, s.extrapolate) == (best["fixed_cycles"], best["extrapolate"])
+    # the tiling mode is the faster of the two timed on that schedule
+    assert set(s.tiling_ms) == {0, 2} and s.ms_per_step == min(s.tiling_ms.values())
+    assert s.tiling_ms[s.variant] == s.ms_per_step
     # errors shrink with more cycles
     errs = [t["vel_err"] for t in s.trials]
     assert errs[0] > errs[-1]
