@@ -28,7 +28,7 @@ import numpy as np
 from inputs import CAHN_HILLIARD, cell_coords
 from .grid import pad_flow, grad
 from .flow import body_free_fields
-from .free_energy import volume, area, helfrich_energy, ch_energy
+from .free_energy import volume, area, helfrich_energy, ch_energy, area_faces
 from .step import velocity
 
 
@@ -69,6 +69,8 @@ def diagnostics(st, with_reference=True):
         energy = ch_energy(st.phi, p.sigma, h, zp)
     else:
         energy = helfrich_energy(st.phi, p.kappa, p.eps, h, zp)
+        if p.sigma != 0.0:   # membrane tension times the face-difference area
+            energy += p.sigma * area_faces(st.phi, p.eps, h, zp)
     w = 0.5 * (1.0 - st.phi)
     wsum = float(np.sum(w))
     xs = cell_coords(p.nx, h, False)

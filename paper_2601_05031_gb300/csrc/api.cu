@@ -1620,6 +1620,9 @@ vsv_status vsv_get_diagnostics(vsv_grid* g, vsv_diag* out) {
   if (g->fe.kind == VSV_HELFRICH) {
     const double cf = 3.0 * std::sqrt(2.0) * g->fe.kappa / (8.0 * std::pow(g->fe.eps, 3));
     out->energy = cf * h3 * q[8];
+    // membrane tension sigma times the face-difference area, (c_A / eps) h^3 q12
+    if (g->fe.sigma != 0.0)
+      out->energy += g->fe.sigma * 3.0 / (2.0 * std::sqrt(2.0) * g->fe.eps) * h3 * q[12];
   } else {
     out->energy = h3 * q[8];
   }

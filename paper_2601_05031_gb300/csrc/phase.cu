@@ -313,7 +313,8 @@ struct V0View {
 
 // q: 0 dissipation integrand, 1 body-free dissipation integrand, 2 |omega'|^2,
 // 3 |psi'|^2, 4 w = (1-phi)/2, 5..7 w x, w y, w z, 8 energy density,
-// 9 max |div v|, 10 max |div psi|, 11 max sigma_t.
+// 9 max |div v|, 10 max |div psi|, 11 max sigma_t, 12 (Helfrich with a
+// membrane tension) the face-difference area density over c_A / eps.
 template <class T>
 __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ phi_lo,
                        const T* __restrict__ g, const T* __restrict__ g_lo, Comp3<T> vel, Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0r,
@@ -364,6 +365,24 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
     if (P.fe_kind == VSV_HELFRICH) {
       const double gg = (double)g[t] + (g_lo ? (double)g_lo[t] : 0.0);
       q[8] += gg * gg;
+      if (P.beta_t != 0.0) {   // membrane tension: the face-difference area density
+        ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
+        ScalarView<T> FL{phi_lo ? phi_lo : phi, P.nx, P.ny, P.nz, P.zper};
+        auto val = [&](int ii, int jj, int kk) {
+          return (double)F(ii, jj, kk) + (phi_lo ? (double)FL(ii, jj, kk) : 0.0);
+        };
+        const double dx = (val(i + 1, j, k) - f) * P.inv_h;
+        double faces = dx * dx;
+        if (j + 1 < P.ny) {
+          const double dy = (val(i, j + 1, k) - f) * P.inv_h;
+          faces += dy * dy;
+        }
+        if (P.zper || k + 1 < P.nz) {
+          const double dz = (val(i, j, k + 1) - f) * P.inv_h;
+          faces += dz * dz;
+        }
+        q[12] += 0.25 * (f * f - 1.0) * (f * f - 1.0) + 0.5 * P.eps * P.eps * faces;
+      }
     } else {
       ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
       double e = 0.25 * (f * f - 1.0) * (f * f - 1.0);
@@ -410,16 +429,21 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
     const double s = block_max(q[a]);
     if (threadIdx.x == 0) partials[(long long)blockIdx.x * kDiagQ + a] = s;
   }
+  {
+    const double s = block_sum(q[12]);
+    if (threadIdx.x == 0) partials[(long long)blockIdx.x * kDiagQ + 12] = s;
+  }
 }
 
 __global__ void k_diag_finalize(const double* partials, int nblocks, double* out) {
-  for (int a = 0; a < 12; ++a) {
+  for (int a = 0; a < 13; ++a) {   // 0..8 and 12 are sums, 9..11 maxima
+    const bool sum = a < 9 || a == 12;
     double s = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
       const double v = partials[(long long)b * kDiagQ + a];
-      s = (a < 9) ? s + v : fmax(s, v);
+      s = sum ? s + v : fmax(s, v);
     }
-    s = (a < 9) ? block_sum(s) : block_max(s);
+    s = sum ? block_sum(s) : block_max(s);
     if (threadIdx.x == 0) out[a] = s;
   }
 }

@@ -227,8 +227,12 @@ def test_fixed_cycle_schedule_matches_converged(V):
 
 
 # ------------------------------------------------------------ diagnostics
-def test_diagnostics_vs_oracle(V):
+@pytest.mark.parametrize("sigma", [0.0, 0.4])
+def test_diagnostics_vs_oracle(V, sigma):
+    """All diagnostics against the oracle; with sigma > 0 a membrane tension
+    enters the step and the energy (sigma times the face-difference area)."""
     w = small_vesicle(inputs.COUETTE)
+    w.sigma = sigma
     st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
     for _ in range(2):
         oracle.step(st, w.dt)
