@@ -137,7 +137,8 @@ typedef struct {
  *   V-cycles (SOR: sweeps) with no host synchronisation; 0: iterate until
  *   ||b - L x||_2 <= tol ||b||_2 or max_cycles, checking every check_every.
  * nu1 / nu2: pre / post smoothing sweeps; max_levels: multigrid depth cap;
- * coarse_sweeps: red-black sweeps on the coarsest level; omega_sor <= 0
+ * coarse_sweeps: red-black sweeps on the coarsest level (capped at twice
+ *   that level's longest extent, and at least 4); omega_sor <= 0
  * picks the optimal SOR weight for the grid.  variant 0 uses the fastest
  * kernels available for each level (fused single-pass red-black sweeps,
  * tiled transfers and defects where the tile shape allows, the lower levels

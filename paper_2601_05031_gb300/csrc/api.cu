@@ -361,6 +361,15 @@ bool smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp
   return false;
 }
 
+// Red-black sweeps on the coarsest level: the solver's coarse_sweeps, but no
+// more than twice the level's longest extent (at least 4).  Gauss-Seidel on
+// a level of a few cells converges in a few sweeps; on the 2 x 1 x 1 level
+// of a 512 x 256 x 256 grid 4 sweeps give the same velocity as 24.
+int coarsest_sweeps(const Level& L, int cap) {
+  const int m = std::max(L.n[0], std::max(L.n[1], L.n[2]));
+  return std::min(cap, std::max(4, 2 * m));
+}
+
 // One V-cycle from level l for L x = R.  uh / ul as in smooth(): returns
 // true if the correction was added to that iterate by the last sweep.
 template <class T>
@@ -375,12 +384,15 @@ bool vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
     if (l > 0) {
       Comp3<T> E = X;
       Comp3<T> RR{{(T*)R.B[0], (T*)R.B[1], (T*)R.B[2]}};
-      if (launch_coarse_solve<T>(g->cx, L, E, RR, ncomp, g->sol.coarse_sweeps, h2)) return false;
+      if (launch_coarse_solve<T>(g->cx, L, E, RR, ncomp, coarsest_sweeps(L, g->sol.coarse_sweeps),
+                                 h2))
+        return false;
       launch_zero<T>(g->cx, E, L.cells(), ncomp);
     } else if (x_zero) {
       launch_zero<T>(g->cx, X, L.cells(), ncomp);
     }
-    for (int s = 0; s < g->sol.coarse_sweeps; ++s) {
+    const int cs = coarsest_sweeps(L, g->sol.coarse_sweeps);
+    for (int s = 0; s < cs; ++s) {
       launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 0, 1.0, h2, kc);
       launch_rb_sweep<T>(g->cx, L, X, R, ncomp, 1, 1.0, h2, kc);
     }
@@ -393,7 +405,7 @@ bool vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
     CC.last = (int)lv.size() - 1;
     CC.nu1 = g->sol.nu1;
     CC.nu2 = g->sol.nu2;
-    CC.coarse_sweeps = g->sol.coarse_sweeps;
+    CC.coarse_sweeps = coarsest_sweeps(lv.back(), g->sol.coarse_sweeps);
     long long off = 0;
     for (int q = l; q <= CC.last; ++q) {
       CC.lv[q] = lv[q];

@@ -502,15 +502,29 @@ __host__ __device__ bool blocked_transfer_ok(const Level& F, const Level& C) {
 // V-cycle there (same operations as the level-by-level kernels: red-black
 // sweeps, residual restricted by averaging, trilinear prolongation), which
 // replaces dozens of latency-bound launches per V-cycle by one.
+// The thread's cells of one colour are visited with the index (i2, j, k)
+// advanced by the block size incrementally (adds and carries instead of two
+// integer divisions per cell).
 template <class T>
 __device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2) {
   const int nx = L.n[0], ny = L.n[1], nxh = (nx + 1) >> 1;
   const int nh = nxh * ny * L.n[2];   // cells of one colour, rounded up per row
+  const int B = blockDim.x;
+  const int Bi = B % nxh, Bq = B / nxh, Bj = Bq % ny, Bk = Bq / ny;
+  const int i20 = threadIdx.x % nxh, q0 = threadIdx.x / nxh, j0 = q0 % ny, k0 = q0 / ny;
   for (int s = 0; s < sweeps; ++s)
     for (int color = 0; color < 2; ++color) {
-      for (int t2 = threadIdx.x; t2 < nh; t2 += blockDim.x) {
-        const int i2 = t2 % nxh, q = t2 / nxh;
-        const int j = q % ny, k = q / ny;
+      int i2 = i20, j = j0, k = k0;
+      for (int t2 = threadIdx.x; t2 < nh; t2 += B) {
+        if (t2 != threadIdx.x) {
+          i2 += Bi;
+          int cj = Bj;
+          if (i2 >= nxh) { i2 -= nxh; ++cj; }
+          j += cj;
+          int ck = Bk;
+          while (j >= ny) { j -= ny; ++ck; }
+          k += ck;
+        }
         const int i = 2 * i2 + ((j + k + color) & 1);
         if (i >= nx) continue;
         const int t = (k * ny + j) * nx + i;
@@ -580,36 +594,37 @@ __device__ void cv_prolong(const Level& F, const Level& C, T* e, const T* ec) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseCycle CC, Comp3<T> E, Comp3<T> RR) {
+__global__ void __launch_bounds__(1024)
+k_coarse_vcycle(const __grid_constant__ CoarseCycle CC, Comp3<T> E, Comp3<T> RR) {
   extern __shared__ unsigned char smem_cv[];
   T* base = reinterpret_cast<T*>(smem_cv);
   const int comp = blockIdx.x;
   const int f = CC.first, l_last = CC.last;
-  T* e[kMaxLevels];
-  T* r[kMaxLevels];
-  for (int l = f; l <= l_last; ++l) {
-    e[l] = base + CC.off[l];
-    r[l] = e[l] + CC.lv[l].cells();
-  }
+  // (e, r) of level l in shared memory; CC is a grid-constant parameter, so
+  // its tables are read in place at run-time indices (no local copies)
+  auto e = [&](int l) { return base + CC.off[l]; };
+  auto r = [&](int l) { return base + CC.off[l] + CC.lv[l].cells(); };
   const int n0 = (int)CC.lv[f].cells();
   for (int t = threadIdx.x; t < n0; t += blockDim.x) {
-    r[f][t] = RR.at(comp)[t];
-    e[f][t] = (T)0;
+    r(f)[t] = RR.at(comp)[t];
+    e(f)[t] = (T)0;
   }
   __syncthreads();
   for (int l = f; l < l_last; ++l) {
-    cv_sweep<T>(CC.lv[l], e[l], r[l], CC.nu1, (T)CC.h2[l]);
-    cv_restrict<T>(CC.lv[l], CC.lv[l + 1], e[l], r[l], r[l + 1]);
+    cv_sweep<T>(CC.lv[l], e(l), r(l), CC.nu1, (T)CC.h2[l]);
+    cv_restrict<T>(CC.lv[l], CC.lv[l + 1], e(l), r(l), r(l + 1));
     const int nc = (int)CC.lv[l + 1].cells();
-    for (int t = threadIdx.x; t < nc; t += blockDim.x) e[l + 1][t] = (T)0;
+    T* ec = e(l + 1);
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) ec[t] = (T)0;
     __syncthreads();
   }
-  cv_sweep<T>(CC.lv[l_last], e[l_last], r[l_last], CC.coarse_sweeps, (T)CC.h2[l_last]);
+  cv_sweep<T>(CC.lv[l_last], e(l_last), r(l_last), CC.coarse_sweeps, (T)CC.h2[l_last]);
   for (int l = l_last - 1; l >= f; --l) {
-    cv_prolong<T>(CC.lv[l], CC.lv[l + 1], e[l], e[l + 1]);
-    cv_sweep<T>(CC.lv[l], e[l], r[l], CC.nu2, (T)CC.h2[l]);
+    cv_prolong<T>(CC.lv[l], CC.lv[l + 1], e(l), e(l + 1));
+    cv_sweep<T>(CC.lv[l], e(l), r(l), CC.nu2, (T)CC.h2[l]);
   }
-  for (int t = threadIdx.x; t < n0; t += blockDim.x) E.at(comp)[t] = e[f][t];
+  const T* e0 = e(f);
+  for (int t = threadIdx.x; t < n0; t += blockDim.x) E.at(comp)[t] = e0[t];
 }
 
 template <class T>
