@@ -150,14 +150,27 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     rco[h][1] = rc_of(G, yw + 1);
   }
 
+  // ZERO_IN: x is not staged at all.  The ring is zeroed once; afterwards
+  // only red positions of in-range cells are ever written (the ring length 6
+  // is even, so a slot position keeps its colour), and within a plane no red
+  // value is read before that plane's red phase writes it.  So every value a
+  // sweep from zero reads -- black cells, wall rows, halo values -- is the
+  // zero that staging would have copied.  Planes beyond a z wall are taken
+  // as zero in registers (their slots hold an earlier plane's red values).
+  if constexpr (ZERO_IN) {
+    float4* a4 = reinterpret_cast<float4*>(sA);
+    for (int t = tid; t < kNA * kRA * kW / 4; t += kThreads) a4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   // prologue: group 0 = x planes zb-2 .. zb, rhs plane zb-1 (step zb-1);
   // group 1 = x plane zb+1, rhs plane zb (step zb)
-  da.stage(slotA(zb - 2), a, G, zb - 2, ZERO_IN);
-  da.stage(slotA(zb - 1), a, G, zb - 1, ZERO_IN);
-  da.stage(slotA(zb), a, G, zb, ZERO_IN);
+  if constexpr (!ZERO_IN) {
+    da.stage(slotA(zb - 2), a, G, zb - 2, false);
+    da.stage(slotA(zb - 1), a, G, zb - 1, false);
+    da.stage(slotA(zb), a, G, zb, false);
+  }
   db.stage(slotB(zb - 1), bsrc, G, zb - 1, false);
   cp_async_commit();
-  da.stage(slotA(zb + 1), a, G, zb + 1, ZERO_IN);
+  if constexpr (!ZERO_IN) da.stage(slotA(zb + 1), a, G, zb + 1, false);
   db.stage(slotB(zb), bsrc, G, zb, false);
   cp_async_commit();
   cp_async_wait1();
@@ -175,7 +188,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
 
   for (int p = zb - 1; p <= ze; ++p) {
     if (p + 2 <= ze) {
-      da.stage(slotA(p + 3), a, G, p + 3, ZERO_IN);
+      if constexpr (!ZERO_IN) da.stage(slotA(p + 3), a, G, p + 3, false);
       db.stage(slotB(p + 2), bsrc, G, p + 2, false);
     }
     cp_async_commit();
@@ -202,7 +215,8 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       MM[h] = M[h];
       M[h] = V[h];
       V[h] = P[h];
-      P[h] = lds4(slotA(p + 1) + rown[h] * kW + 4 * q);
+      P[h] = (ZERO_IN && ghost_plane(p + 1)) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                             : lds4(slotA(p + 1) + rown[h] * kW + 4 * q);
     }
     // ---- red cells of plane p: own groups, halo rows, halo columns
     if (!ghost_plane(p)) {
