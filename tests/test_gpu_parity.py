@@ -226,6 +226,61 @@ def test_fixed_cycle_schedule_matches_converged(V):
     sim.close()
 
 
+# ------------------------------------------------------------ degenerate cases
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_no_body_keeps_the_base_flow(V, prec):
+    """phi = 1 everywhere (no interface): no source, so omega' and psi' stay
+    at the round-off of the tabulated body-free fields, the velocity is the
+    body-free Couette profile, and phi does not move."""
+    w = small_vesicle(inputs.COUETTE)
+    w.phi0 = np.ones_like(w.phi0)
+    st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
+    for _ in range(2):
+        oracle.step(st, w.dt)
+    sim = make_sim(V, w, V.VSV_FP64 if prec == "fp64" else V.VSV_MIXED,
+                   tol=1e-13 if prec == "fp64" else 1e-11)
+    sim.set_phi(w.phi0)
+    sim.step(2, w.dt)
+    assert np.array_equal(sim.field(V.VSV_FIELD_PHI), w.phi0)
+    for c in range(3):
+        assert np.max(np.abs(sim.field(V.VSV_FIELD_PSI_PERT_X + c))) < 1e-10
+        assert np.max(np.abs(sim.field(V.VSV_FIELD_OMEGA_PERT_X + c))) < 1e-10
+    vel = np.stack([sim.field(V.VSV_FIELD_VEL_X + c) for c in range(3)])
+    assert rel(vel, np.stack(oracle.velocity(st))) < (1e-12 if prec == "fp64" else 1e-7)
+    sim.close()
+
+
+def test_tension_without_bending_vs_oracle(V):
+    """Helfrich kind with kappa = 0 and a membrane tension: mu is the
+    tension term and the area multiplier alone."""
+    w = small_vesicle(inputs.POISEUILLE_DUCT)
+    w.kappa, w.sigma = 0.0, 0.5
+    st = oracle.init_state(oracle.params_from_workload(w), w.phi0)
+    for _ in range(3):
+        oracle.step(st, w.dt)
+    sim = make_sim(V, w, V.VSV_FP64, tol=1e-13)
+    sim.set_phi(w.phi0)
+    sim.step(3, w.dt)
+    e = field_errors(gpu_fields(V, sim), oracle_fields(st))
+    assert max(e.values()) < 1e-10, e
+    sim.close()
+
+
+def test_zero_steps_is_a_no_op(V):
+    w = small_droplet()
+    sim = make_sim(V, w, V.VSV_MIXED, fixed=2)
+    sim.set_phi(w.phi0)
+    sim.step(1, w.dt)
+    before = [sim.field(f) for f in (V.VSV_FIELD_PHI, V.VSV_FIELD_PSI_PERT_X, V.VSV_FIELD_MU)]
+    d0 = sim.diagnostics()
+    assert V.vsv_step(sim.g, 0, w.dt) == V.VSV_OK
+    after = [sim.field(f) for f in (V.VSV_FIELD_PHI, V.VSV_FIELD_PSI_PERT_X, V.VSV_FIELD_MU)]
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    assert sim.diagnostics()["steps"] == d0["steps"]
+    sim.close()
+
+
 # ------------------------------------------------------------ diagnostics
 @pytest.mark.parametrize("sigma", [0.0, 0.4])
 def test_diagnostics_vs_oracle(V, sigma):
