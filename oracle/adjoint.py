@@ -40,14 +40,18 @@ The initial state has gamma^0 = 0 identically (A[phi^0] - A0 = 0 for every
 phi^0), so only mu^0's explicit phi dependence and the flow solve enter
 there, and the constants V0, A0 pass their adjoints back to phi^0.
 
-The inertial variant (rho > 0) is not differentiated here.
+Inertial variant (rho > 0): omega^{n+1} = omega_lift + (L - s)^-1 (f -
+s omega^n), s = rho / (eta dt), so the adjoint of omega is carried from step
+to step: fbar = (L - s)^-1 omegabar_total and omegabar^n = -s fbar.  The
+initial vorticity is the Stokes one (L^-1 f^0).
 
 Pinned by (tests/test_oracle_pins.py): dot-product identities of each
 transpose against the forward operator it transposes; the vector-Jacobian
 product of mu against central differences of ``chem_potential``; the
 trajectory gradient in kappa, sigma and random directions of phi^0 against
 central differences of the forward oracle (Helfrich with tension, the
-area and volume penalties, duct and Couette flows, and Cahn-Hilliard).
+area and volume penalties, duct and Couette flows, the inertial variant,
+and Cahn-Hilliard).
 """
 from __future__ import annotations
 
@@ -59,7 +63,7 @@ from inputs import CAHN_HILLIARD, HELFRICH
 from .grid import pad_mirror, pad_homogeneous, lap, grad
 from .poisson import solve_poisson
 from .free_energy import prefactor_cf, helfrich_g
-from .step import init_state, step, velocity
+from .step import init_state, step, velocity, inertial_shift
 
 C_A = 3.0 / (2.0 * math.sqrt(2.0))
 
@@ -145,13 +149,23 @@ def _with(p, **kw):
     return dataclasses.replace(p, **kw)
 
 
-def flow_vjp(phi, mu, psibar, p):
-    """Adjoint of psi(phi, mu) (source, vorticity solve, stream solve):
-    omegabar = -L^-1 psibar, fbar = L^-1 omegabar, then the cross product
-    f = (D_m phi x D_m mu) / eta.  Returns (phibar, mubar) contributions."""
+def flow_vjp(phi, mu, psibar, p, omegabar=None, shift=0.0):
+    """Adjoint of psi(phi, mu) (source, vorticity solve, stream solve).
+
+    omegabar_total = omegabar - L^-1 psibar (omegabar: the adjoint of omega
+    from the next step's backward-Euler vorticity update, inertial variant),
+    fbar = (L - shift)^-1 omegabar_total, then the cross product
+    f = (D_m phi x D_m mu) / eta.  Returns (phibar, mubar, omegabar_prev)
+    with omegabar_prev = -shift fbar, the adjoint passed to the previous
+    vorticity (zero for the Stokes step, shift = 0)."""
     h, zp = p.h, p.z_periodic
     per = (True, False, zp)
-    fbar = [solve_poisson(-solve_poisson(psibar[c], h, per), h, per) for c in range(3)]
+    fbar = []
+    for c in range(3):
+        ob = -solve_poisson(psibar[c], h, per)
+        if omegabar is not None:
+            ob = ob + omegabar[c]
+        fbar.append(solve_poisson(ob, h, per, shift))
     a = grad(pad_mirror(phi, 1, zp), h)
     b = grad(pad_mirror(mu, 1, zp), h)
     ie = 1.0 / p.eta
@@ -161,7 +175,8 @@ def flow_vjp(phi, mu, psibar, p):
     bbar = [(fbar[1] * a[2] - fbar[2] * a[1]) * ie,      # (fbar x a) / eta
             (fbar[2] * a[0] - fbar[0] * a[2]) * ie,
             (fbar[0] * a[1] - fbar[1] * a[0]) * ie]
-    return grad_mirror_t(abar, h, zp), grad_mirror_t(bbar, h, zp)
+    return (grad_mirror_t(abar, h, zp), grad_mirror_t(bbar, h, zp),
+            [-shift * fbar[c] for c in range(3)])
 
 
 def update_vjp(phi, vel, phibar_next, p, dt):
@@ -184,8 +199,6 @@ def update_vjp(phi, vel, phibar_next, p, dt):
 # ---------------------------------------------------------------- trajectory
 def forward(p, phi0, dt, nsteps):
     """States 0..N of the forward oracle: phi, mu, gamma_A and the velocity."""
-    if p.rho > 0.0:
-        raise NotImplementedError("the adjoint covers the Stokes step (rho = 0)")
     st = init_state(p, phi0)
     traj = [dict(phi=st.phi, mu=st.mu, gamma=0.0, vel=velocity(st))]
     for _ in range(nsteps):
@@ -212,11 +225,13 @@ def gradient(p, phi0, dt, nsteps, target=None, phibar_final=None):
         phibar = np.array(phibar_final, dtype=np.float64, copy=True)
     mubar = np.zeros_like(phibar)
     psibar = [np.zeros_like(phibar) for _ in range(3)]
+    omegabar = [np.zeros_like(phibar) for _ in range(3)]
+    shift = inertial_shift(p, dt)   # 0 for the Stokes step
     kb = sb = v0b = a0b = 0.0
     cg = p.k_area * 3.0 * p.eps / (2.0 * math.sqrt(2.0))
     for n in range(nsteps - 1, -1, -1):
         s1 = traj[n + 1]
-        fp, fm = flow_vjp(s1["phi"], s1["mu"], psibar, p)
+        fp, fm, omegabar = flow_vjp(s1["phi"], s1["mu"], psibar, p, omegabar, shift)
         phibar = phibar + fp
         mubar = mubar + fm
         dp, dk, ds, dg = mu_vjp(s1["phi"], s1["gamma"], mubar, p)
@@ -229,8 +244,8 @@ def gradient(p, phi0, dt, nsteps, target=None, phibar_final=None):
         s0 = traj[n]
         phibar, mubar, psibar, dv = update_vjp(s0["phi"], s0["vel"], phibar, p, dt)
         v0b += dv
-    s0 = traj[0]
-    fp, fm = flow_vjp(s0["phi"], s0["mu"], psibar, p)
+    s0 = traj[0]   # the initial vorticity is the Stokes one of phi^0
+    fp, fm, _ = flow_vjp(s0["phi"], s0["mu"], psibar, p, omegabar, 0.0)
     phibar = phibar + fp
     mubar = mubar + fm
     dp, dk, ds, _ = mu_vjp(s0["phi"], 0.0, mubar, p)

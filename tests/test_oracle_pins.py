@@ -607,10 +607,13 @@ def _adjoint_case(case):
         p = oracle.params_from_workload(w)
         p.k_area, p.k_vol, p.sigma, p.kappa = 0.4, 0.02, 0.3, 1.3
         dt = 2e-3
+        if case == "helfrich_inertial":   # backward-Euler vorticity, s = rho / (eta dt) = 3
+            p.rho = 3.0 * p.eta * dt
     return w, p, dt
 
 
-@pytest.mark.parametrize("case", ["helfrich_duct", "helfrich_couette", "ch_duct"])
+@pytest.mark.parametrize("case", ["helfrich_duct", "helfrich_couette", "ch_duct",
+                                  "helfrich_inertial"])
 def test_trajectory_gradient_against_central_differences(case):
     """Gradient of J = h^3/2 sum (phi^N - target)^2 after 4 steps with
     respect to kappa, sigma and two random directions of phi^0, against
