@@ -378,9 +378,11 @@ vsv_status vsv_batch_destroy(vsv_batch* b);
  * the forward ones (the 7-point operator with zero wall data is symmetric).
  * Adjoint fields are FP64; the adjoint solves use the grid's precision
  * (FP64 multigrid, or FP32 V-cycles with double-word defect correction) to
- * the relative residual `tol`.  The inertial variant (rho > 0) is not
- * covered.  The area and volume constants A0 = A[phi^0], V0 = V[phi^0]
- * depend on phi^0 and are differentiated.
+ * the relative residual `tol`.  With the inertial variant (rho > 0) the
+ * adjoint of the vorticity is carried from step to step through the same
+ * shifted operator L - s as the backward-Euler step.  The area and volume
+ * constants A0 = A[phi^0], V0 = V[phi^0] depend on phi^0 and are
+ * differentiated.
  *
  * vsv_tape_create binds a tape to grid g (which must outlive it): every >= 1
  * steps between checkpoints, tol > 0 (0 selects 1e-11).  It allocates the
@@ -392,7 +394,7 @@ vsv_status vsv_batch_destroy(vsv_batch* b);
  * of dt, saving the full state on the device at step 0, every `every` steps
  * and at step nsteps.  The grid's flow, free energy and solver settings
  * must stay unchanged until the matching backward pass.  VSV_EINVAL for
- * rho > 0 or bad arguments; errors of vsv_set_phi / vsv_step pass through.
+ * bad arguments; errors of vsv_set_phi / vsv_step pass through.
  *
  * vsv_tape_backward takes phibar_final = dJ/dphi^N (N cells, FP64, device
  * memory when on_device, else host) and writes phibar0 = dJ/dphi^0 (same

@@ -334,6 +334,13 @@ __global__ void k_adj_scale(const double* __restrict__ y, double* __restrict__ x
   if (t < n) x[t] = a * y[t];
 }
 
+// z = a x + b y (n doubles); z may alias x or y
+__global__ void k_adj_axpby(double* z, const double* x, const double* y, long long n, double a,
+                            double b) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) z[t] = a * x[t] + b * y[t];
+}
+
 unsigned nb_(long long n) { return (unsigned)((n + kAB - 1) / kAB); }
 
 }  // namespace
@@ -400,6 +407,13 @@ void launch_adj_update(Ctx& cx, const AdjParams& P, double* phib, const double* 
                                            Comp3<const double>{{vb.p[0], vb.p[1], vb.p[2]}}, dt, acc,
                                            psib);
   cx.after(VSV_KCLASS_ADJOINT, 8.0 * 11 * (double)n);   // phib, s, vb read; phib, psib written
+}
+
+void launch_adj_axpby(Ctx& cx, double* z, double a, const double* x, double b, const double* y,
+                      long long n) {
+  cx.before(VSV_KCLASS_ADJOINT);
+  k_adj_axpby<<<nb_(n), kAB, 0, cx.stream>>>(z, x, y, n, a, b);
+  cx.after(VSV_KCLASS_ADJOINT, 24.0 * (double)n);
 }
 
 void launch_adj_scale(Ctx& cx, const double* y, double* x, long long n, double a) {

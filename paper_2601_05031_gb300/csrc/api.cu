@@ -1842,6 +1842,7 @@ struct vsv_tape {
   long long recomputed = 0;            // steps re-run by the last backward pass
   // views into buf / fbuf
   double *phib, *mub, *psib[3], *ab[3], *bb[3], *fb[3], *x1[3], *gsc, *wsc;
+  double *omc[3], *omt[3];   // inertial variant: the carried vorticity adjoint, a temporary
   float *x1h[3], *x1l[3], *fbh[3], *fbl[3], *bh[3], *bl[3];
 };
 
@@ -1890,7 +1891,7 @@ vsv_status tape_alloc(vsv_tape* t) {
   vsv_status st;
   if ((st = dmalloc((void**)&t->rec, (size_t)(t->every + 1) * 5 * N * 8)) != VSV_OK) return st;
   if ((st = dmalloc((void**)&t->gam, (size_t)(t->every + 1) * 8)) != VSV_OK) return st;
-  if ((st = dmalloc((void**)&t->buf, (size_t)19 * N * 8)) != VSV_OK) return st;
+  if ((st = dmalloc((void**)&t->buf, (size_t)25 * N * 8)) != VSV_OK) return st;
   if ((st = dmalloc((void**)&t->acc, kAccCount * 8)) != VSV_OK) return st;
   if ((st = dmalloc((void**)&t->partials, (size_t)3 * adj_blocks(N) * 8)) != VSV_OK) return st;
   double* p = t->buf;
@@ -1904,6 +1905,8 @@ vsv_status tape_alloc(vsv_tape* t) {
   for (int c = 0; c < 3; ++c) t->x1[c] = take();
   t->gsc = take();
   t->wsc = take();
+  for (int c = 0; c < 3; ++c) t->omc[c] = take();
+  for (int c = 0; c < 3; ++c) t->omt[c] = take();
   if (g->prec == VSV_MIXED) {
     if ((st = dmalloc((void**)&t->fbuf, (size_t)18 * N * 4)) != VSV_OK) return st;
     float* f = t->fbuf;
@@ -1980,9 +1983,16 @@ vsv_status tape_record(vsv_tape* t, int slot) {
 
 // fbar = L^-1 (-L^-1 psibar) per component: the adjoint of the vorticity and
 // stream-vector solves (L symmetric, zero wall data), warm-started from the
-// previous reverse step's solutions
-vsv_status tape_solves(vsv_tape* t) {
+// previous reverse step's solutions.  Inertial variant (rho > 0): the
+// vorticity of a step came from (L - s) omega = f - s omega_prev, so
+// fbar = (L - s)^-1 (omc - L^-1 psibar) with omc the vorticity adjoint
+// carried from the later step, and the carry becomes omc = -s fbar;
+// `shifted` false (the initial state, whose vorticity is the Stokes one)
+// solves with L and leaves the carry alone.
+vsv_status tape_solves_inertial(vsv_tape* t, bool shifted);
+vsv_status tape_solves(vsv_tape* t, bool shifted) {
   vsv_grid* g = t->g;
+  if (g->flow.rho > 0.0) return tape_solves_inertial(t, shifted);
   const int every = std::max(1, g->sol.check_every);
   int c1 = 0, c2 = 0;
   double r1 = 0.0, r2 = 0.0;
@@ -2012,11 +2022,56 @@ vsv_status tape_solves(vsv_tape* t) {
   return VSV_OK;
 }
 
+vsv_status tape_solves_inertial(vsv_tape* t, bool shifted) {
+  vsv_grid* g = t->g;
+  const long long N = g->N;
+  const int every = std::max(1, g->sol.check_every);
+  const double s = g->flow.rho / (g->flow.eta * t->dt);
+  if (shifted && g->omega_levels.empty())
+    return fail(g, VSV_ESTATE, "no shifted hierarchy for the inertial adjoint%s");
+  const std::vector<Level>& lv2 = shifted ? g->omega_levels : g->flow_levels;
+  int c1 = 0, c2 = 0;
+  double r1 = 0.0, r2 = 0.0;
+  vsv_status st;
+  if (g->prec == VSV_FP64) {
+    Rhs3<double> R1{{t->psib[0], t->psib[1], t->psib[2]}, {nullptr, nullptr, nullptr}, 1.0};
+    st = solve<double>(g, g->flow_levels, mc3(t->x1), R1, 3, VSV_SOLVER_MG, t->fixed, t->tol, 400,
+                       every, &c1, &r1);
+    if (st != VSV_OK) return st;
+    for (int c = 0; c < 3; ++c) launch_adj_axpby(g->cx, t->omt[c], 1.0, t->omc[c], -1.0, t->x1[c], N);
+    Rhs3<double> R2{{t->omt[0], t->omt[1], t->omt[2]}, {nullptr, nullptr, nullptr}, 1.0};
+    st = solve<double>(g, lv2, mc3(t->fb), R2, 3, VSV_SOLVER_MG, t->fixed, t->tol, 400, every, &c2,
+                       &r2);
+    if (st != VSV_OK) return st;
+  } else {
+    for (int c = 0; c < 3; ++c) launch_split_ff(g->cx, t->psib[c], t->bh[c], t->bl[c], N);
+    Rhs3<float> R1{{t->bh[0], t->bh[1], t->bh[2]}, {nullptr, nullptr, nullptr}, 1.f};
+    st = solve_dc(g, g->flow_levels, mc3(t->x1h), mc3(t->x1l), R1, mc3(t->bl), 3, t->fixed, t->tol,
+                  400, every, &c1, &r1);
+    if (st != VSV_OK) return st;
+    for (int c = 0; c < 3; ++c) {
+      launch_merge_ff(g->cx, t->x1h[c], t->x1l[c], t->omt[c], N);
+      launch_adj_axpby(g->cx, t->omt[c], 1.0, t->omc[c], -1.0, t->omt[c], N);
+      launch_split_ff(g->cx, t->omt[c], t->bh[c], t->bl[c], N);
+    }
+    Rhs3<float> R2{{t->bh[0], t->bh[1], t->bh[2]}, {nullptr, nullptr, nullptr}, 1.f};
+    st = solve_dc(g, lv2, mc3(t->fbh), mc3(t->fbl), R2, mc3(t->bl), 3, t->fixed, t->tol, 400, every,
+                  &c2, &r2);
+    if (st != VSV_OK) return st;
+    for (int c = 0; c < 3; ++c) launch_merge_ff(g->cx, t->fbh[c], t->fbl[c], t->fb[c], N);
+  }
+  if (shifted)
+    for (int c = 0; c < 3; ++c) launch_adj_scale(g->cx, t->fb[c], t->omc[c], N, -s);
+  CKL();
+  t->adj_cycles += c1 + c2;
+  return VSV_OK;
+}
+
 // adjoint of the flow solve and of mu at a recorded state (slot s); with
 // `step` the area penalty of gamma_A = K_A c_g (A - A0) too
 vsv_status tape_state_adjoint(vsv_tape* t, const AdjParams& P, int s, bool step) {
   vsv_grid* g = t->g;
-  vsv_status st = tape_solves(t);
+  vsv_status st = tape_solves(t, step);
   if (st != VSV_OK) return st;
   const double* phi = rec_field(t, s, 0);
   const double* mu = rec_field(t, s, 1);
@@ -2090,12 +2145,10 @@ vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_dev
   if (!t || !phi0 || nsteps < 1 || !(dt > 0)) return VSV_EINVAL;
   vsv_grid* g = t->g;
   if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_tape_forward%s");
-  if (g->flow.rho > 0.0)
-    return fail(g, VSV_EINVAL, "the adjoint covers the Stokes step (rho = 0)%s");
   CK(cudaStreamSynchronize(g->cx.stream));
   tape_free_ckpts(t);
   t->dev_bytes = (size_t)(t->every + 1) * 5 * g->N * 8 + (size_t)(t->every + 1) * 8 +
-                 (size_t)19 * g->N * 8 + kAccCount * 8 + (size_t)3 * adj_blocks(g->N) * 8 +
+                 (size_t)25 * g->N * 8 + kAccCount * 8 + (size_t)3 * adj_blocks(g->N) * 8 +
                  (g->prec == VSV_MIXED ? (size_t)18 * g->N * 4 : 0);
   t->recorded = false;
   t->ck_bytes = 2 * sizeof(double);
@@ -2132,6 +2185,7 @@ vsv_status vsv_tape_backward(vsv_tape* t, const double* phibar_final, double* ph
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(t->mub, 0, N * 8, s));
   for (int c = 0; c < 3; ++c) {
+    CK(cudaMemsetAsync(t->omc[c], 0, N * 8, s));
     CK(cudaMemsetAsync(t->psib[c], 0, N * 8, s));
     CK(cudaMemsetAsync(t->fb[c], 0, N * 8, s));
     CK(cudaMemsetAsync(t->x1[c], 0, N * 8, s));

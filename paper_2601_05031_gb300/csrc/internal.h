@@ -274,5 +274,8 @@ void launch_adj_update(Ctx& cx, const AdjParams& P, double* phib, const double* 
                        Comp3<double> vb, double* mub, Comp3<double> psib, double* partials,
                        double* acc);
 void launch_adj_scale(Ctx& cx, const double* y, double* x, long long n, double a);
+// z = a x + b y (n doubles)
+void launch_adj_axpby(Ctx& cx, double* z, double a, const double* x, double b, const double* y,
+                      long long n);
 
 }  // namespace vsv

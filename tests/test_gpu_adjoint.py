@@ -3,7 +3,7 @@ gradients of J = h^3/2 sum (phi^N - target)^2 with respect to phi^0, kappa
 and sigma against the oracle's adjoint (oracle/adjoint.py) on the same
 seeded inputs, against central differences of the GPU forward map, and the
 checkpointing invariances (gradient independent of the checkpoint interval,
-grid left at phi^N)."""
+grid left at phi^N), also for the inertial variant."""
 import dataclasses
 
 import numpy as np
@@ -190,15 +190,27 @@ def test_autograd_function_matches_tape(V):
     t.close()
 
 
-def test_inertial_variant_rejected(V):
-    import torch
-    from paper_2601_05031_gb300.adjoint import Tape
-    w, dt, target = _case("ch_duct")
-    w.rho = 1.0
-    t = Tape.from_workload(w, V.VSV_FP64, every=2)
-    with pytest.raises(V.VsvError):
-        t.forward(torch.from_numpy(w.phi0), 2, dt)
-    t.close()
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_inertial_gradient_vs_oracle_adjoint(V, prec):
+    """Inertial variant (backward-Euler vorticity, s = rho / (eta dt) = 3):
+    the vorticity adjoint is carried between steps through the shifted
+    solve; gradients against the oracle."""
+    w, dt, target = _case("helfrich_duct")
+    w.rho = 3.0 * w.eta * dt
+    N = 5
+    p = oracle.params_from_workload(w)
+    Jo, go, ko, so = oadj.gradient(p, w.phi0, dt, N, target)
+    J, g, k, s, phiN, phi_after, info = _gpu_gradient(V, w, dt, target, N, prec, 2)
+    lim = 1e-9 if prec == "fp64" else 1e-6
+    print("inertial", prec, "phi0bar", rel(g, go), "kappa", k, ko, "sigma", s, so)
+    assert abs(J - Jo) <= lim * Jo
+    assert rel(g, go) < lim, rel(g, go)
+    assert abs(k - ko) <= lim * abs(ko), (k, ko)
+    assert abs(s - so) <= lim * abs(so), (s, so)
+    # the inertial term changes the gradient by far more than the bar
+    p.rho = 0.0
+    _, go0, ko0, _ = oadj.gradient(p, w.phi0, dt, N, target)
+    assert abs(ko0 - ko) > 100 * lim * abs(ko)
 
 
 def test_fit_module_small(V):
