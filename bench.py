@@ -147,7 +147,7 @@ GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
 # in one launch-list capture of this benchmark at 512 x 256 x 256 (one ncu
 # pass), 1.409 GB per launch, per cell and component here.  To be retaken
 # (and set to None meanwhile) whenever k_rbgs_fused changes.
-FUSED_SWEEP_TRAFFIC_PER_CELL = 1.4098e9 / (512 * 256 * 256 * 3)
+FUSED_SWEEP_TRAFFIC_PER_CELL = 1.4003e9 / (512 * 256 * 256 * 3)
 
 
 def make_sim(w, prec, cycles, extrapolate=1):

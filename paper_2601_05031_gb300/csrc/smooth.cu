@@ -83,14 +83,17 @@ __device__ __forceinline__ float* ring(float* base, int plane, int slots, int sl
 // iterate, (XH, XL) <- (XH, XL) + e, with the arithmetic of k_update_dw (the
 // last sweep of a correction's V-cycle; e itself is not needed afterwards).
 //
-// Pipeline: at step p the CTA issues the copies of x plane p + 3 and rhs
-// plane p + 2 and waits for those of step p - 2 (x plane p + 1, rhs plane
-// p), so two steps of copies are in flight.  One barrier per step suffices:
-// within a step the red phase writes only red cells of slot p and reads
-// black cells of slots p - 1 .. p + 1, and the black phase reads slot p - 1,
-// finished one step earlier, plus registers; the ring is deep enough (six x
-// and five rhs slots) that the copies a step issues never land in a slot a
-// warp still in the previous step may read.
+// Pipeline: step p updates the red cells of plane p and the black cells of
+// plane p - 2.  The two phases are independent (the black cells need the red
+// values of planes p - 3 .. p - 1, finished in earlier steps), so their
+// loads and arithmetic overlap.  At step p the CTA waits for the copies of
+// step p - 2 (x plane p + 1, rhs plane p), passes the one barrier of the
+// step and then issues the copies of x plane p + 3 and rhs plane p + 2, so
+// two steps of copies are in flight.  Within a step the red phase writes only
+// red cells of slot p and reads black cells of slots p - 1 .. p + 1, and the
+// black phase reads slot p - 2 plus registers; issuing after the barrier
+// keeps the copies out of the slots of plane p - 3, which the black phase of
+// step p - 1 read (six x and five rhs slots).
 template <bool ZERO_IN, bool HAS_S, bool UPD, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<float> XH,
@@ -175,28 +178,33 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   cp_async_commit();
   cp_async_wait1();
   __syncthreads();
-  // register pipeline: MM = plane p-2, M = p-1, V = p, P = p+1 (own groups);
-  // rotated at the top of every step
-  float4 MM[2], M[2], V[2], P[2];
+  // register pipeline: MMM = plane p-3, MM = p-2, M = p-1, V = p, P = p+1
+  // (own groups); rotated at the top of every step
+  float4 MMM[2], MM[2], M[2], V[2], P[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     V[h] = lds4(slotA(zb - 2) + rown[h] * kW + 4 * q);
     P[h] = lds4(slotA(zb - 1) + rown[h] * kW + 4 * q);
     M[h] = V[h];
     MM[h] = V[h];
+    MMM[h] = V[h];
   }
 
-  for (int p = zb - 1; p <= ze; ++p) {
+  for (int p = zb - 1; p <= ze + 1; ++p) {
+    // the copies of step p - 2 (x plane p + 1, rhs plane p) have landed;
+    // after the barrier no warp is in step p - 1 any more, so the slots of
+    // planes p - 3 (x) and p - 3 (rhs), last read by the black phase of step
+    // p - 1, are free for the copies this step issues
+    cp_async_wait1();
+    __syncthreads();
     if (p + 2 <= ze) {
       if constexpr (!ZERO_IN) da.stage(slotA(p + 3), a, G, p + 3, false);
       db.stage(slotB(p + 2), bsrc, G, p + 2, false);
     }
     cp_async_commit();
-    cp_async_wait2();
-    __syncthreads();
     float* cA = slotA(p);
     const float* cB = slotB(p);
-    const int qp = p - 1;
+    const int qp = p - 2;
     const bool black = qp >= zb && qp < ze;
     float4 XHp[2], XLp[2];   // UPD: iterate of plane p-1, loaded ahead of its use
     if constexpr (UPD) {
@@ -212,127 +220,146 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+      MMM[h] = MM[h];
       MM[h] = M[h];
       M[h] = V[h];
       V[h] = P[h];
-      P[h] = (ZERO_IN && ghost_plane(p + 1)) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                             : lds4(slotA(p + 1) + rown[h] * kW + 4 * q);
+      P[h] = (p > ze || (ZERO_IN && ghost_plane(p + 1))) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                         : lds4(slotA(p + 1) + rown[h] * kW + 4 * q);
     }
-    // ---- red cells of plane p: own groups, halo rows, halo columns
-    if (!ghost_plane(p)) {
-      const int zw = zwall(p);
-      // rows 2ty and 2ty+1 have opposite parity; each row's red cells need the
-      // other row's black values (registers) and one more row from shared
-      // memory; the x neighbours come from the adjacent lanes' registers
-      // (black values, which this phase does not change) and, at the tile
-      // edges, from the staged halo columns
-      const int par = (jown[0] + p) & 1;          // red offset of row 2ty
-      float Lx[2], Rx[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        Lx[h] = __shfl_up_sync(0xffffffffu, V[h].w, 1);
-        Rx[h] = __shfl_down_sync(0xffffffffu, V[h].x, 1);
-        if (gx == 0) Lx[h] = cA[rown[h] * kW + kHX - 1];
-        if (gx == 31) Rx[h] = cA[rown[h] * kW + kHX + kTX];
-      }
-      const float4 U0 = lds4(cA + (rown[0] - 1) * kW + 4 * q);
-      const float4 D1 = lds4(cA + (rown[1] + 1) * kW + 4 * q);
-      const float4 B0 = lds4(cB + (rown[0] - 1) * kW + 4 * q);
-      const float4 B1 = lds4(cB + (rown[1] - 1) * kW + 4 * q);
-      const float4 V0 = V[0];
-      if (upd_row[0])
-        V[0] = rb_group(V[0], U0, V[1], M[0], P[0], Lx[0], Rx[0], B0, par, beta, srow(jown[0], p),
-                        h2, zw ? rco[0][1] : rco[0][0]);
-      if (upd_row[1])
-        V[1] = rb_group(V[1], V0, D1, M[1], P[1], Lx[1], Rx[1], B1, 1 - par, beta, srow(jown[1], p),
-                        h2, zw ? rco[1][1] : rco[1][0]);
-      {
-        float* dst = cA + rown[0] * kW + 4 * q;
-        if (upd_row[0]) {
-          if (par == 0) { dst[0] = V[0].x; dst[2] = V[0].z; }
-          else { dst[1] = V[0].y; dst[3] = V[0].w; }
+    auto black_phase = [&]() {
+      // ---- black cells of plane p-2 on the tile, stored straight from
+      // registers.  They need the red values of planes p-3 .. p-1, all final,
+      // so this phase does not depend on the red phase of the same step.
+      if (black) {
+        const int zw = zwall(qp);
+        const float* cAq = slotA(qp);
+        const float* cBq = slotB(qp);
+        const int par = (jown[0] + qp + 1) & 1;     // black offset of row 2ty
+        float Lq[2], Rq[2];
+  #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          Lq[h] = __shfl_up_sync(0xffffffffu, MM[h].w, 1);
+          Rq[h] = __shfl_down_sync(0xffffffffu, MM[h].x, 1);
+          if (gx == 0) Lq[h] = cAq[rown[h] * kW + kHX - 1];
+          if (gx == 31) Rq[h] = cAq[rown[h] * kW + kHX + kTX];
         }
-        dst += kW;
-        if (upd_row[1]) {
-          if (par == 0) { dst[1] = V[1].y; dst[3] = V[1].w; }
-          else { dst[0] = V[1].x; dst[2] = V[1].z; }
-        }
-      }
-      if (ty == 0 || ty == 7) {   // halo rows y0 - 1 and y0 + kTY
-        const int r = (ty == 0) ? 1 : kRA - 2;
-        const int j = y0 - kH + r;
-        if (G.per_y || (j >= 0 && j < G.ny)) {
-          const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
-          const float* row = cA + r * kW;
-          const float4 Vh = lds4(row + 4 * q), U = lds4(row - kW + 4 * q), D = lds4(row + kW + 4 * q);
-          const float4 Mh = lds4(slotA(p - 1) + r * kW + 4 * q);
-          const float4 Ph = lds4(slotA(p + 1) + r * kW + 4 * q);
-          const float Lx = row[4 * q - 1], Rx = row[4 * q + 4];
-          const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
-          const int par = (j + p) & 1;
-          const float4 Vn = rb_group(Vh, U, D, Mh, Ph, Lx, Rx, Bv, par, beta, srow(j, p), h2,
-                                     rc_of(G, jw + zw));
-          float* dst = cA + r * kW + 4 * q;
-          if (par == 0) { dst[0] = Vn.x; dst[2] = Vn.z; }
-          else { dst[1] = Vn.y; dst[3] = Vn.w; }
+        const float4 U0 = lds4(cAq + (rown[0] - 1) * kW + 4 * q);
+        const float4 D1 = lds4(cAq + (rown[1] + 1) * kW + 4 * q);
+        const float4 Bq0 = lds4(cBq + (rown[0] - 1) * kW + 4 * q);
+        const float4 Bq1 = lds4(cBq + (rown[1] - 1) * kW + 4 * q);
+        const float4 M0 = MM[0];
+        if (upd_row[0])
+          MM[0] = rb_group(MM[0], U0, MM[1], MMM[0], M[0], Lq[0], Rq[0], Bq0, par, beta,
+                           srow(jown[0], qp), h2, zw ? rco[0][1] : rco[0][0]);
+        if (upd_row[1])
+          MM[1] = rb_group(MM[1], M0, D1, MMM[1], M[1], Lq[1], Rq[1], Bq1, 1 - par, beta,
+                           srow(jown[1], qp), h2, zw ? rco[1][1] : rco[1][0]);
+  #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!st_row[h]) continue;
+          const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
+          if constexpr (UPD) {
+            const FF v0 = ff_add_f(FF{XHp[h].x, XLp[h].x}, MM[h].x);
+            const FF v1 = ff_add_f(FF{XHp[h].y, XLp[h].y}, MM[h].y);
+            const FF v2 = ff_add_f(FF{XHp[h].z, XLp[h].z}, MM[h].z);
+            const FF v3 = ff_add_f(FF{XHp[h].w, XLp[h].w}, MM[h].w);
+            *reinterpret_cast<float4*>(uh + gi) = make_float4(v0.hi, v1.hi, v2.hi, v3.hi);
+            *reinterpret_cast<float4*>(ul + gi) = make_float4(v0.lo, v1.lo, v2.lo, v3.lo);
+          } else {
+            *reinterpret_cast<float4*>(out + gi) = MM[h];
+          }
         }
       }
-      if (tid >= 32 && tid < 32 + 2 * (kRA - 2)) {   // halo columns x0 - 1 and x0 + kTX
-        const int idx = tid - 32;
-        const int r = 1 + (idx >> 1);
-        const int c = (idx & 1) ? kHX + kTX : kHX - 1;
-        const int j = y0 - kH + r;
-        const int x = x0 - kHX + c;
-        if ((G.per_y || (j >= 0 && j < G.ny)) && (((x + j + p) & 1) == 0)) {
-          const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
-          const int id = r * kW + c;
-          const float s = ((cA[id - 1] + cA[id + 1]) + (cA[id - kW] + cA[id + kW])) +
-                          (slotA(p - 1)[id] + slotA(p + 1)[id]);
-          const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
-          cA[id] = (s - bb * h2) * rc_of(G, jw + zw);
+    };
+    auto red_phase = [&]() {
+      // ---- red cells of plane p: own groups, halo rows, halo columns
+      if (p <= ze && !ghost_plane(p)) {
+        const int zw = zwall(p);
+        // rows 2ty and 2ty+1 have opposite parity; each row's red cells need the
+        // other row's black values (registers) and one more row from shared
+        // memory; the x neighbours come from the adjacent lanes' registers
+        // (black values, which this phase does not change) and, at the tile
+        // edges, from the staged halo columns
+        const int par = (jown[0] + p) & 1;          // red offset of row 2ty
+        float Lx[2], Rx[2];
+  #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          Lx[h] = __shfl_up_sync(0xffffffffu, V[h].w, 1);
+          Rx[h] = __shfl_down_sync(0xffffffffu, V[h].x, 1);
+          if (gx == 0) Lx[h] = cA[rown[h] * kW + kHX - 1];
+          if (gx == 31) Rx[h] = cA[rown[h] * kW + kHX + kTX];
+        }
+        const float4 U0 = lds4(cA + (rown[0] - 1) * kW + 4 * q);
+        const float4 D1 = lds4(cA + (rown[1] + 1) * kW + 4 * q);
+        const float4 B0 = lds4(cB + (rown[0] - 1) * kW + 4 * q);
+        const float4 B1 = lds4(cB + (rown[1] - 1) * kW + 4 * q);
+        const float4 V0 = V[0];
+        if (upd_row[0])
+          V[0] = rb_group(V[0], U0, V[1], M[0], P[0], Lx[0], Rx[0], B0, par, beta, srow(jown[0], p),
+                          h2, zw ? rco[0][1] : rco[0][0]);
+        if (upd_row[1])
+          V[1] = rb_group(V[1], V0, D1, M[1], P[1], Lx[1], Rx[1], B1, 1 - par, beta, srow(jown[1], p),
+                          h2, zw ? rco[1][1] : rco[1][0]);
+        {
+          float* dst = cA + rown[0] * kW + 4 * q;
+          if (upd_row[0]) {
+            if (par == 0) { dst[0] = V[0].x; dst[2] = V[0].z; }
+            else { dst[1] = V[0].y; dst[3] = V[0].w; }
+          }
+          dst += kW;
+          if (upd_row[1]) {
+            if (par == 0) { dst[1] = V[1].y; dst[3] = V[1].w; }
+            else { dst[0] = V[1].x; dst[2] = V[1].z; }
+          }
+        }
+        if (ty == 0 || ty == 7) {   // halo rows y0 - 1 and y0 + kTY
+          const int r = (ty == 0) ? 1 : kRA - 2;
+          const int j = y0 - kH + r;
+          if (G.per_y || (j >= 0 && j < G.ny)) {
+            const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
+            const float* row = cA + r * kW;
+            const float4 Vh = lds4(row + 4 * q), U = lds4(row - kW + 4 * q), D = lds4(row + kW + 4 * q);
+            const float4 Mh = lds4(slotA(p - 1) + r * kW + 4 * q);
+            const float4 Ph = lds4(slotA(p + 1) + r * kW + 4 * q);
+            const float Lx = row[4 * q - 1], Rx = row[4 * q + 4];
+            const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
+            const int par = (j + p) & 1;
+            const float4 Vn = rb_group(Vh, U, D, Mh, Ph, Lx, Rx, Bv, par, beta, srow(j, p), h2,
+                                       rc_of(G, jw + zw));
+            float* dst = cA + r * kW + 4 * q;
+            if (par == 0) { dst[0] = Vn.x; dst[2] = Vn.z; }
+            else { dst[1] = Vn.y; dst[3] = Vn.w; }
+          }
+        }
+        if (tid >= 32 && tid < 32 + 2 * (kRA - 2)) {   // halo columns x0 - 1 and x0 + kTX
+          const int idx = tid - 32;
+          const int r = 1 + (idx >> 1);
+          const int c = (idx & 1) ? kHX + kTX : kHX - 1;
+          const int j = y0 - kH + r;
+          const int x = x0 - kHX + c;
+          if ((G.per_y || (j >= 0 && j < G.ny)) && (((x + j + p) & 1) == 0)) {
+            const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
+            const int id = r * kW + c;
+            const float s = ((cA[id - 1] + cA[id + 1]) + (cA[id - kW] + cA[id + kW])) +
+                            (slotA(p - 1)[id] + slotA(p + 1)[id]);
+            const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
+            cA[id] = (s - bb * h2) * rc_of(G, jw + zw);
+          }
         }
       }
-    }
-    // ---- black cells of plane p-1 on the tile, stored straight from registers
-    if (black) {
-      const int zw = zwall(qp);
-      const float* cAq = slotA(qp);
-      const float* cBq = slotB(qp);
-      const int par = (jown[0] + qp + 1) & 1;     // black offset of row 2ty
-      float Lq[2], Rq[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        Lq[h] = __shfl_up_sync(0xffffffffu, M[h].w, 1);
-        Rq[h] = __shfl_down_sync(0xffffffffu, M[h].x, 1);
-        if (gx == 0) Lq[h] = cAq[rown[h] * kW + kHX - 1];
-        if (gx == 31) Rq[h] = cAq[rown[h] * kW + kHX + kTX];
-      }
-      const float4 U0 = lds4(cAq + (rown[0] - 1) * kW + 4 * q);
-      const float4 D1 = lds4(cAq + (rown[1] + 1) * kW + 4 * q);
-      const float4 Bq0 = lds4(cBq + (rown[0] - 1) * kW + 4 * q);
-      const float4 Bq1 = lds4(cBq + (rown[1] - 1) * kW + 4 * q);
-      const float4 M0 = M[0];
-      if (upd_row[0])
-        M[0] = rb_group(M[0], U0, M[1], MM[0], V[0], Lq[0], Rq[0], Bq0, par, beta,
-                        srow(jown[0], qp), h2, zw ? rco[0][1] : rco[0][0]);
-      if (upd_row[1])
-        M[1] = rb_group(M[1], M0, D1, MM[1], V[1], Lq[1], Rq[1], Bq1, 1 - par, beta,
-                        srow(jown[1], qp), h2, zw ? rco[1][1] : rco[1][0]);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!st_row[h]) continue;
-        const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
-        if constexpr (UPD) {
-          const FF v0 = ff_add_f(FF{XHp[h].x, XLp[h].x}, M[h].x);
-          const FF v1 = ff_add_f(FF{XHp[h].y, XLp[h].y}, M[h].y);
-          const FF v2 = ff_add_f(FF{XHp[h].z, XLp[h].z}, M[h].z);
-          const FF v3 = ff_add_f(FF{XHp[h].w, XLp[h].w}, M[h].w);
-          *reinterpret_cast<float4*>(uh + gi) = make_float4(v0.hi, v1.hi, v2.hi, v3.hi);
-          *reinterpret_cast<float4*>(ul + gi) = make_float4(v0.lo, v1.lo, v2.lo, v3.lo);
-        } else {
-          *reinterpret_cast<float4*>(out + gi) = M[h];
-        }
-      }
+    };
+    // The plain sweep runs the black phase first: it writes only global
+    // memory, so the compiler may start the red phase's shared-memory loads
+    // early (measured 292.5 -> 282.1 us per finest-level launch).  The
+    // zero-input and update variants were slower that way (234.9 -> 243.2
+    // and 419.7 -> 446.4 us) and keep the red phase first.
+    if constexpr (!ZERO_IN && !UPD) {
+      black_phase();
+      red_phase();
+    } else {
+      red_phase();
+      black_phase();
     }
   }
   cp_async_wait0();
