@@ -1,11 +1,13 @@
 // Outer defect correction of the mixed path with a double-word iterate.
 //
 // The iterate x = x_hi + x_lo (two FP32 words, about 44 significant bits) is
-// refined by   r = b - L_h x  (exact: cascaded summation of every FP32 term,
-// one final rounding),   L_h e = r  (one FP32 multigrid V-cycle from e = 0),
-// x <- x + e (double-word addition).  The defect sees x to FP64-class
-// accuracy, so the refinement converges to the discrete solution below FP32
-// rounding and the relative residual is a meaningful stopping test.
+// refined by   r = b - L_h x  (the hi words of the stencil by error-free
+// cascaded summation, the cancelling rhs and stencil terms by error-free
+// sums, only O(u)-small terms added in FP32: the error is a rounding of r
+// plus O(u^2) of the terms),   L_h e = r  (one FP32 multigrid V-cycle from
+// e = 0),   x <- x + e (double-word addition).  The defect sees x to
+// FP64-class accuracy, so the refinement converges to the discrete solution
+// below FP32 rounding and the relative residual is a meaningful stopping test.
 #include <algorithm>
 
 #include "tile.cuh"
@@ -28,10 +30,28 @@ struct NbFetch {
   }
 };
 
+// r = (b1 + b2 + s) - (p + rest) where b1 + b2 is the rhs pair, s the row
+// source, p the leading word of L x and rest its O(u) remainder.  b1 (+ s)
+// and p cancel almost completely near convergence, so they go through
+// error-free TwoSums; b2, rest and the TwoSum errors are O(u) of the terms
+// and are added in FP32 (their rounding is O(u^2) of the terms).
+__device__ __forceinline__ float defect_combine(float b1, float b2, bool has_b2, float s,
+                                                bool has_s, float p, float rest) {
+  float h = b1, lo = 0.f;
+  if (has_s) two_sum(b1, s, h, lo);
+  float d, e;
+  two_sum(h, -p, d, e);
+  lo = has_s ? __fadd_rn(lo, e) : e;
+  if (has_b2) lo = __fadd_rn(lo, b2);
+  lo = __fsub_rn(lo, rest);
+  return __fadd_rn(d, lo);
+}
+
 }  // namespace
 
-// r = beta (B_hi + B_lo) + S(y, z) - L_h (x_hi + x_lo), exactly up to the final
-// rounding; optional FP64 partial sums of ||r||^2 and ||b||^2 per block.
+// r = beta (B_hi + B_lo) + S(y, z) - L_h (x_hi + x_lo) to a rounding of r plus
+// O(u^2) of the terms; optional FP64 partial sums of ||r||^2 and ||b||^2 per
+// block.
 __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
                             Comp3<float> BL, Comp3<float> OUT, double* partials, float ih_hi,
                             float ih_lo) {
@@ -53,19 +73,20 @@ __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<floa
     float r2 = 0.f, b2 = 0.f;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const long long t = lin(i, j, k, nx, ny);
+      // hi words: cascade from the first active direction's x- neighbour
+      // on, in the order x-, x+, y-, y+, z-, z+; lo words: the per-axis
+      // pair sums added in axis order
       CascadeSum lh(0.f);
       float llo = 0.f;
-      if (L.act[0]) {
-        lh.add(H.get(i - 1, j, k)); lh.add(H.get(i + 1, j, k));
-        llo += Lo.get(i - 1, j, k) + Lo.get(i + 1, j, k);
-      }
-      if (L.act[1]) {
-        lh.add(H.get(i, j - 1, k)); lh.add(H.get(i, j + 1, k));
-        llo += Lo.get(i, j - 1, k) + Lo.get(i, j + 1, k);
-      }
-      if (L.act[2]) {
-        lh.add(H.get(i, j, k - 1)); lh.add(H.get(i, j, k + 1));
-        llo += Lo.get(i, j, k - 1) + Lo.get(i, j, k + 1);
+      bool first = true;
+      for (int a = 0; a < 3; ++a) {
+        if (!L.act[a]) continue;
+        const int di = a == 0, dj = a == 1, dk = a == 2;
+        const float hm = H.get(i - di, j - dj, k - dk), hp = H.get(i + di, j + dj, k + dk);
+        const float pl = __fadd_rn(Lo.get(i - di, j - dj, k - dk), Lo.get(i + di, j + dj, k + dk));
+        if (first) { lh = CascadeSum(hm); llo = pl; first = false; }
+        else { lh.add(hm); llo = __fadd_rn(llo, pl); }
+        lh.add(hp);
       }
       lh.add_scaled(-dch, H.a[t]);
       if (dcl != 0.f) lh.add(-dcl * H.a[t]);   // adding -0 would change nothing
@@ -75,12 +96,8 @@ __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<floa
       const float pe = __fmaf_rn(ih_hi, lh.hi, -p);
       const float rest = __fmaf_rn(ih_hi, __fadd_rn(lh.lo, llo), __fmaf_rn(ih_lo, lh.hi, pe));
       const float b1 = beta * bh[t];
-      CascadeSum r(b1);
-      if (bl) r.add(beta * bl[t]);
-      r.add(s);
-      r.add(-p);
-      r.add(-rest);
-      const float rv = r.value();
+      const float rv = defect_combine(b1, bl ? beta * bl[t] : 0.f, bl != nullptr, s, S != nullptr,
+                                      p, rest);
       out[t] = rv;
       if (partials) {
         const float bv = b1 + (bl ? beta * bl[t] : 0.f) + s;
@@ -171,7 +188,7 @@ void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL,
 }
 
 // ---------------------------------------------------------------- tiled defect
-// The same exact defect as k_defect_dw (same summation order, hence the same
+// The same defect as k_defect_dw (same summation order, hence the same
 // bits) on a 128 x 16 tile marching along z: x_hi and x_lo planes staged in
 // shared memory (one-cell halo), each thread's own float4 groups of the
 // planes below and above held in registers, rhs read straight from memory.
@@ -199,39 +216,33 @@ __device__ __forceinline__ float comp4(const float4& v, int o) {
   return o == 0 ? v.x : (o == 1 ? v.y : (o == 2 ? v.z : v.w));
 }
 
-// exact b - L x at one cell: hi neighbours by cascaded summation in the
-// order x-, x+, y-, y+, z-, z+, then -6 x_c; lo parts in FP32.
+// b - L x at one cell, the same arithmetic as k_defect_dw with every axis
+// active: hi neighbours by cascaded summation in the order x-, x+, y-, y+,
+// z-, z+, then -6 x_c; lo parts as per-axis pair sums in FP32.
 __device__ __forceinline__ float defect_cell(float xmh, float xph, float ymh, float yph, float zmh,
                                              float zph, float ch, float xml, float xpl, float yml,
                                              float ypl, float zml, float zpl, float cl, float b1,
-                                             float b2, bool has_b2, float s, float ih_hi,
-                                             float ih_lo, float dch, float dcl) {
-  CascadeSum lh(0.f);
-  lh.add(xmh); lh.add(xph);
+                                             float b2, bool has_b2, float s, bool has_s,
+                                             float ih_hi, float ih_lo, float dch, float dcl) {
+  CascadeSum lh(xmh);
+  lh.add(xph);
   lh.add(ymh); lh.add(yph);
   lh.add(zmh); lh.add(zph);
-  float llo = 0.f;
-  llo += xml + xpl;
-  llo += yml + ypl;
-  llo += zml + zpl;
+  float llo = __fadd_rn(__fadd_rn(__fadd_rn(xml, xpl), __fadd_rn(yml, ypl)), __fadd_rn(zml, zpl));
   lh.add_scaled(-dch, ch);
   if (dcl != 0.f) lh.add(-dcl * ch);   // adding -0 would change nothing
   llo = __fmaf_rn(-dch, cl, llo);
   const float p = __fmul_rn(ih_hi, lh.hi);
   const float pe = __fmaf_rn(ih_hi, lh.hi, -p);
   const float rest = __fmaf_rn(ih_hi, __fadd_rn(lh.lo, llo), __fmaf_rn(ih_lo, lh.hi, pe));
-  CascadeSum r(b1);
-  if (has_b2) r.add(b2);
-  r.add(s);
-  r.add(-p);
-  r.add(-rest);
-  return r.value();
+  return defect_combine(b1, b2, has_b2, s, has_s, p, rest);
 }
 }  // namespace
 
 // RAGGED: partial edge tiles; cells past the extent (wrapped copies or zero
-// ghost rows in the staged planes) are skipped.
-template <int ROWS, bool RAGGED>
+// ghost rows in the staged planes) are skipped.  NORMS: FP64 partial sums of
+// ||r||^2 and ||b||^2 per block (the fixed-cycle solves go without).
+template <int ROWS, bool RAGGED, bool NORMS>
 __global__ void __launch_bounds__(tile::kThreads, ROWS == 1 ? 3 : 2)
 k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3<float> BL,
                Comp3<float> OUT, double* partials) {
@@ -329,9 +340,9 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
         const float b1v = beta * comp4(B1, o), b2v = beta * comp4(B2, o);
         res[o] = defect_cell(xmh, xph, comp4(Uh, o), comp4(Dh, o), comp4(Mh[h], o), comp4(Ph[h], o),
                              comp4(Vh[h], o), xml, xpl, comp4(Ul, o), comp4(Dl, o), comp4(Ml[h], o),
-                             comp4(Pl[h], o), comp4(Vl[h], o), b1v, b2v, bl != nullptr, s, G.ih_hi,
-                             G.ih_lo, G.dch, G.dcl);
-        if (partials) {
+                             comp4(Pl[h], o), comp4(Vl[h], o), b1v, b2v, bl != nullptr, s,
+                             S != nullptr, G.ih_hi, G.ih_lo, G.dch, G.dcl);
+        if (NORMS) {
           const float bv = b1v + (bl ? b2v : 0.f) + s;
           r2 = __fmaf_rn(res[o], res[o], r2);
           b2 = __fmaf_rn(bv, bv, b2);
@@ -339,11 +350,13 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
       }
       *reinterpret_cast<float4*>(out + gi) = make_float4(res[0], res[1], res[2], res[3]);
     }
-    rr += (double)r2;
-    bb += (double)b2;
+    if (NORMS) {
+      rr += (double)r2;
+      bb += (double)b2;
+    }
   }
   cp_async_wait0();
-  if (partials) {
+  if (NORMS) {
     rr = block_sum(rr);
     bb = block_sum(bb);
     if (threadIdx.x == 0) {
@@ -364,7 +377,8 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
   if (!aligned && !(ragged && tile::ragged_ok(L) && tile::tile_fill(L) >= 0.25 &&
                     L.cells() >= (1 << 17)))
     return 0;
-  // one row per thread: 8-row tiles, three CTAs per SM
+  // one row per thread: 8-row tiles, three CTAs per SM (four, at 64
+  // registers, spill and run slower)
   constexpr int ROWS = 1;
   using Sh = DefShape<ROWS>;
   const int ntx = (L.n[0] + tile::kTX - 1) / tile::kTX, nty = (L.n[1] + Sh::kRows - 1) / Sh::kRows;
@@ -386,24 +400,21 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
   G.dcl = L.cdl[0];
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_defect_tiled<ROWS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)Sh::kSmem);
-    cudaFuncSetAttribute(k_defect_tiled<ROWS, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         100);
-    cudaFuncSetAttribute(k_defect_tiled<ROWS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)Sh::kSmem);
-    cudaFuncSetAttribute(k_defect_tiled<ROWS, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         100);
+    auto set = [](auto kern) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmem);
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    };
+    set(k_defect_tiled<ROWS, false, false>);
+    set(k_defect_tiled<ROWS, true, false>);
+    set(k_defect_tiled<ROWS, false, true>);
+    set(k_defect_tiled<ROWS, true, true>);
     attr = true;
   }
   dim3 grid(tiles, nz, ncomp);
+  auto kern = aligned ? (partials ? k_defect_tiled<ROWS, false, true> : k_defect_tiled<ROWS, false, false>)
+                      : (partials ? k_defect_tiled<ROWS, true, true> : k_defect_tiled<ROWS, true, false>);
   cx.before(VSV_KCLASS_RESTRICT);
-  if (aligned)
-    k_defect_tiled<ROWS, false><<<grid, tile::kThreads, Sh::kSmem, cx.stream>>>(G, XH, XL, R, BL, OUT,
-                                                                                partials);
-  else
-    k_defect_tiled<ROWS, true><<<grid, tile::kThreads, Sh::kSmem, cx.stream>>>(G, XH, XL, R, BL, OUT,
-                                                                               partials);
+  kern<<<grid, tile::kThreads, Sh::kSmem, cx.stream>>>(G, XH, XL, R, BL, OUT, partials);
   // x_hi, x_lo, b_hi (, b_lo) read, r written
   cx.after(VSV_KCLASS_RESTRICT, (BL.p[0] ? 20.0 : 16.0) * (double)L.cells() * ncomp);
   return tiles * nz;
