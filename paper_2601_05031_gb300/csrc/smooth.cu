@@ -227,27 +227,40 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       P[h] = (p > ze || (ZERO_IN && ghost_plane(p + 1))) ? make_float4(0.f, 0.f, 0.f, 0.f)
                                                          : lds4(slotA(p + 1) + rown[h] * kW + 4 * q);
     }
+    // the black phase's operands from shared memory: the y neighbours of
+    // the two rows, their rhs groups and, at the tile edges, the x halo
+    float4 U0, D1, Bq0, Bq1;
+    float Le[2], Re[2];
+    auto black_load = [&]() {
+      if (black) {
+        const float* cAq = slotA(qp);
+        const float* cBq = slotB(qp);
+  #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          Le[h] = gx == 0 ? cAq[rown[h] * kW + kHX - 1] : 0.f;
+          Re[h] = gx == 31 ? cAq[rown[h] * kW + kHX + kTX] : 0.f;
+        }
+        U0 = lds4(cAq + (rown[0] - 1) * kW + 4 * q);
+        D1 = lds4(cAq + (rown[1] + 1) * kW + 4 * q);
+        Bq0 = lds4(cBq + (rown[0] - 1) * kW + 4 * q);
+        Bq1 = lds4(cBq + (rown[1] - 1) * kW + 4 * q);
+      }
+    };
     auto black_phase = [&]() {
       // ---- black cells of plane p-2 on the tile, stored straight from
       // registers.  They need the red values of planes p-3 .. p-1, all final,
       // so this phase does not depend on the red phase of the same step.
       if (black) {
         const int zw = zwall(qp);
-        const float* cAq = slotA(qp);
-        const float* cBq = slotB(qp);
         const int par = (jown[0] + qp + 1) & 1;     // black offset of row 2ty
         float Lq[2], Rq[2];
   #pragma unroll
         for (int h = 0; h < 2; ++h) {
           Lq[h] = __shfl_up_sync(0xffffffffu, MM[h].w, 1);
           Rq[h] = __shfl_down_sync(0xffffffffu, MM[h].x, 1);
-          if (gx == 0) Lq[h] = cAq[rown[h] * kW + kHX - 1];
-          if (gx == 31) Rq[h] = cAq[rown[h] * kW + kHX + kTX];
+          if (gx == 0) Lq[h] = Le[h];
+          if (gx == 31) Rq[h] = Re[h];
         }
-        const float4 U0 = lds4(cAq + (rown[0] - 1) * kW + 4 * q);
-        const float4 D1 = lds4(cAq + (rown[1] + 1) * kW + 4 * q);
-        const float4 Bq0 = lds4(cBq + (rown[0] - 1) * kW + 4 * q);
-        const float4 Bq1 = lds4(cBq + (rown[1] - 1) * kW + 4 * q);
         const float4 M0 = MM[0];
         if (upd_row[0])
           MM[0] = rb_group(MM[0], U0, MM[1], MMM[0], M[0], Lq[0], Rq[0], Bq0, par, beta,
@@ -272,9 +285,27 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         }
       }
     };
+    // the red phase's shared-memory operands for the own groups (same
+    // roles as the black phase's)
+    const bool red = p <= ze && !ghost_plane(p);
+    float4 U0r, D1r, B0r, B1r;
+    float Ler[2], Rer[2];
+    auto red_load = [&]() {
+      if (red) {
+  #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          Ler[h] = gx == 0 ? cA[rown[h] * kW + kHX - 1] : 0.f;
+          Rer[h] = gx == 31 ? cA[rown[h] * kW + kHX + kTX] : 0.f;
+        }
+        U0r = lds4(cA + (rown[0] - 1) * kW + 4 * q);
+        D1r = lds4(cA + (rown[1] + 1) * kW + 4 * q);
+        B0r = lds4(cB + (rown[0] - 1) * kW + 4 * q);
+        B1r = lds4(cB + (rown[1] - 1) * kW + 4 * q);
+      }
+    };
     auto red_phase = [&]() {
       // ---- red cells of plane p: own groups, halo rows, halo columns
-      if (p <= ze && !ghost_plane(p)) {
+      if (red) {
         const int zw = zwall(p);
         // rows 2ty and 2ty+1 have opposite parity; each row's red cells need the
         // other row's black values (registers) and one more row from shared
@@ -287,13 +318,10 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         for (int h = 0; h < 2; ++h) {
           Lx[h] = __shfl_up_sync(0xffffffffu, V[h].w, 1);
           Rx[h] = __shfl_down_sync(0xffffffffu, V[h].x, 1);
-          if (gx == 0) Lx[h] = cA[rown[h] * kW + kHX - 1];
-          if (gx == 31) Rx[h] = cA[rown[h] * kW + kHX + kTX];
+          if (gx == 0) Lx[h] = Ler[h];
+          if (gx == 31) Rx[h] = Rer[h];
         }
-        const float4 U0 = lds4(cA + (rown[0] - 1) * kW + 4 * q);
-        const float4 D1 = lds4(cA + (rown[1] + 1) * kW + 4 * q);
-        const float4 B0 = lds4(cB + (rown[0] - 1) * kW + 4 * q);
-        const float4 B1 = lds4(cB + (rown[1] - 1) * kW + 4 * q);
+        const float4 U0 = U0r, D1 = D1r, B0 = B0r, B1 = B1r;
         const float4 V0 = V[0];
         if (upd_row[0])
           V[0] = rb_group(V[0], U0, V[1], M[0], P[0], Lx[0], Rx[0], B0, par, beta, srow(jown[0], p),
@@ -353,12 +381,25 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     // memory, so the compiler may start the red phase's shared-memory loads
     // early (measured 292.5 -> 282.1 us per finest-level launch).  The
     // zero-input and update variants were slower that way (234.9 -> 243.2
-    // and 419.7 -> 446.4 us) and keep the red phase first.
+    // and 419.7 -> 446.4 us) and keep the red phase first.  The zero-input
+    // variant loads both phases' shared-memory operands ahead of the red
+    // phase, whose stores the compiler cannot tell apart from the black
+    // phase's loads (234.4 -> 218.2 us); in the plain sweep the same
+    // hoisting raises the registers to 128 and costs 5 %.
     if constexpr (!ZERO_IN && !UPD) {
+      black_load();
       black_phase();
+      red_load();
       red_phase();
+    } else if constexpr (ZERO_IN) {
+      black_load();
+      red_load();
+      red_phase();
+      black_phase();
     } else {
+      red_load();
       red_phase();
+      black_load();
       black_phase();
     }
   }
