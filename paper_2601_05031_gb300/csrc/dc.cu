@@ -300,6 +300,19 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
   }
   double rr = 0.0, bb = 0.0;
   for (int p = zb; p < ze; ++p) {
+    // the step's rhs words and row source, loaded ahead of the barrier so
+    // that their latency overlaps the wait for the staged planes
+    float4 B1s[ROWS], B2s[ROWS];
+    float Ss[ROWS];
+#pragma unroll
+    for (int h = 0; h < ROWS; ++h) {
+      const int j = jown[h];
+      const bool ok = !RAGGED || (j < G.ny && x0 + 4 * gx < G.nx);
+      const long long gi = ((long long)p * G.ny + j) * G.nx + x0 + 4 * gx;
+      B1s[h] = ok ? *reinterpret_cast<const float4*>(bh + gi) : make_float4(0.f, 0.f, 0.f, 0.f);
+      B2s[h] = ok && bl ? *reinterpret_cast<const float4*>(bl + gi) : make_float4(0.f, 0.f, 0.f, 0.f);
+      Ss[h] = ok && S ? S[j + (long long)p * G.ny] : 0.f;
+    }
     if (p + 3 <= ze) {   // plane p+3 is needed by step p+2
       ds.stage(slot(sH, p + 3), xh, G, p + 3, false);
       ds.stage(slot(sL, p + 3), xl, G, p + 3, false);
@@ -328,10 +341,8 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
       const float Lh = rowH[4 * q - 1], Rh = rowH[4 * q + 4];
       const float Ll = rowL[4 * q - 1], Rl = rowL[4 * q + 4];
       const long long gi = ((long long)p * G.ny + j) * G.nx + x0 + 4 * gx;
-      const float4 B1 = *reinterpret_cast<const float4*>(bh + gi);
-      float4 B2 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (bl) B2 = *reinterpret_cast<const float4*>(bl + gi);
-      const float s = S ? S[j + (long long)p * G.ny] : 0.f;
+      const float4 B1 = B1s[h], B2 = B2s[h];
+      const float s = Ss[h];
       float res[4];
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
