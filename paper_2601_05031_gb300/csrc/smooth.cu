@@ -191,6 +191,22 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   }
 
   for (int p = zb - 1; p <= ze + 1; ++p) {
+    const int qp = p - 2;
+    const bool black = qp >= zb && qp < ze;
+    // UPD: the iterate of plane p - 2, loaded ahead of the barrier so that
+    // its latency overlaps the wait
+    float4 XHp[2], XLp[2];
+    if constexpr (UPD) {
+      if (black) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!st_row[h]) continue;
+          const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
+          XHp[h] = *reinterpret_cast<const float4*>(uh + gi);
+          XLp[h] = *reinterpret_cast<const float4*>(ul + gi);
+        }
+      }
+    }
     // the copies of step p - 2 (x plane p + 1, rhs plane p) have landed;
     // after the barrier no warp is in step p - 1 any more, so the slots of
     // planes p - 3 (x) and p - 3 (rhs), last read by the black phase of step
@@ -204,20 +220,6 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     cp_async_commit();
     float* cA = slotA(p);
     const float* cB = slotB(p);
-    const int qp = p - 2;
-    const bool black = qp >= zb && qp < ze;
-    float4 XHp[2], XLp[2];   // UPD: iterate of plane p-1, loaded ahead of its use
-    if constexpr (UPD) {
-      if (black) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (!st_row[h]) continue;
-          const long long gi = ((long long)qp * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
-          XHp[h] = *reinterpret_cast<const float4*>(uh + gi);
-          XLp[h] = *reinterpret_cast<const float4*>(ul + gi);
-        }
-      }
-    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       MMM[h] = MM[h];
