@@ -593,14 +593,12 @@ PhaseParams phase_params(const vsv_grid* g) {
     lo = (float)(v - (double)hi);
   };
   split(P.inv_h2, P.ih2_hi, P.ih2_lo);
-  split(g->fe.eps * g->fe.eps, P.e2_hi, P.e2_lo);
+  split(g->fe.eps * g->fe.eps * P.inv_h2, P.e2ih_hi, P.e2ih_lo);
   split(P.cf2, P.cf2_hi, P.cf2_lo);
-  split(g->fe.sigma, P.sig_hi, P.sig_lo);
-  split(0.5 * P.inv_h, P.hih_hi, P.hih_lo);
-  split(0.5 * g->fe.eps, P.he_hi, P.he_lo);
-  split(0.25 / g->fe.eps, P.q_hi, P.q_lo);
-  split(3.0 / (2.0 * std::sqrt(2.0)), P.ca_hi, P.ca_lo);
-  split(1.0 / g->flow.eta, P.ie_hi, P.ie_lo);
+  split(g->fe.sigma * P.inv_h2, P.sgih_hi, P.sgih_lo);
+  split(0.25 * P.inv_h2 / g->flow.eta, P.src_hi, P.src_lo);
+  split(3.0 / (2.0 * std::sqrt(2.0)) * 0.5 * g->fe.eps * 0.25 * P.inv_h2, P.ag_hi, P.ag_lo);
+  split(3.0 / (2.0 * std::sqrt(2.0)) * 0.25 / g->fe.eps, P.aw_hi, P.aw_lo);
   split(P.beta_t, P.bt_hi, P.bt_lo);
   std::memset(P.vwall, 0, sizeof P.vwall);
   if (g->flow.kind == VSV_COUETTE) {

@@ -173,9 +173,10 @@ struct PhaseParams {
   double beta_t;                // Helfrich with tension sigma: mu += beta_t g, beta_t = sigma c_A / eps
   double mobility, inv_eta;
   // the same coefficients as double-word FP32 pairs (hi, lo) for the mixed path
-  float ih2_hi, ih2_lo, e2_hi, e2_lo, cf2_hi, cf2_lo, sig_hi, sig_lo;
-  float hih_hi, hih_lo, he_hi, he_lo, q_hi, q_lo, ca_hi, ca_lo;   // area density
-  float ie_hi, ie_lo;                                              // 1 / eta
+  float ih2_hi, ih2_lo, cf2_hi, cf2_lo;
+  float e2ih_hi, e2ih_lo, sgih_hi, sgih_lo;   // eps^2 / h^2 and sigma / h^2
+  float src_hi, src_lo;   // (1 / 2h)^2 / eta: scale of the raw-difference cross product
+  float ag_hi, ag_lo, aw_hi, aw_lo;   // area density: c_A eps/2 (1/2h)^2 and c_A / (4 eps)
   float bt_hi, bt_lo;                                              // beta_t
   // wall velocity on the wall nodes: [0] y = 0 wall, [1] y = H, [2] z = 0, [3] z = H
   double vwall[4][3];

@@ -111,8 +111,9 @@ __global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, const T* _
     // so both sums are formed in double-word arithmetic from phi = hi + lo.
     ScalarView<float> FL{phi_lo, P.nx, P.ny, P.nz, P.zper};
     CascadeSum cp(0.f), ca(0.f);
-    const FF hihf{P.hih_hi, P.hih_lo}, hef{P.he_hi, P.he_lo}, qf{P.q_hi, P.q_lo},
-        caf{P.ca_hi, P.ca_lo};
+    // density c_A (eps/2 |grad phi|^2 + (phi^2 - 1)^2 / (4 eps)) from the
+    // raw central differences, the constant factors folded into two pairs
+    const FF agf{P.ag_hi, P.ag_lo}, awf{P.aw_hi, P.aw_lo};
     for (int row = blockIdx.x; row < P.ny * P.nz; row += gridDim.x) {
      const int j = row % P.ny, k = row / P.ny;
      for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
@@ -120,14 +121,14 @@ __global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, const T* _
       const FF f{phi[t], phi_lo[t]};
       auto diff = [&](int i1, int j1, int k1, int i0, int j0, int k0) {
         const FF a{F(i1, j1, k1), FL(i1, j1, k1)}, b{F(i0, j0, k0), FL(i0, j0, k0)};
-        return ff_mul(ff_add(a, ff_neg(b)), hihf);
+        return ff_add(a, ff_neg(b));
       };
       const FF gx = diff(i + 1, j, k, i - 1, j, k);
       const FF gy = diff(i, j + 1, k, i, j - 1, k);
       const FF gz = diff(i, j, k + 1, i, j, k - 1);
       const FF g2 = ff_add(ff_add(ff_mul(gx, gx), ff_mul(gy, gy)), ff_mul(gz, gz));
       const FF w = ff_add_f(ff_mul(f, f), -1.f);
-      const FF dens = ff_mul(ff_add(ff_mul(g2, hef), ff_mul(ff_mul(w, w), qf)), caf);
+      const FF dens = ff_add(ff_mul(g2, agf), ff_mul(ff_mul(w, w), awf));
       cp.add(f.hi);
       cp.add(f.lo);
       ca.add(dens.hi);
@@ -619,14 +620,14 @@ __global__ void k_fill(double* x, long long n, double v) {
 }
 
 // ---------------------------------------------------------------- mixed path: double-word phi
-// Exact 7-point Laplacian of a double-word field: the hi parts are summed by
-// cascaded summation (error-free up to the final rounding), the lo parts in
-// FP32 (their own rounding is below 2^-48 of the field).
+// Unscaled 7-point Laplacian sum (x+ + x- + y+ + y- + z+ + z- - 6 c) of a
+// double-word field: the hi parts are summed by cascaded summation
+// (error-free up to the final rounding), the lo parts in FP32 (their own
+// rounding is below 2^-48 of the field).  Callers apply 1/h^2 together with
+// their own coefficient, as one double-word product.
 template <class V>
-__device__ __forceinline__ FF lap7_ff(const V& H, const V& L, int i, int j, int k, float ih_hi,
-                                      float ih_lo) {
-  CascadeSum s(0.f);
-  s.add(H(i + 1, j, k));
+__device__ __forceinline__ FF lap7_ff(const V& H, const V& L, int i, int j, int k) {
+  CascadeSum s(H(i + 1, j, k));
   s.add(H(i - 1, j, k));
   s.add(H(i, j + 1, k));
   s.add(H(i, j - 1, k));
@@ -635,8 +636,7 @@ __device__ __forceinline__ FF lap7_ff(const V& H, const V& L, int i, int j, int 
   s.add_scaled(-6.f, H(i, j, k));
   const float lsum = L(i + 1, j, k) + L(i - 1, j, k) + L(i, j + 1, k) + L(i, j - 1, k) +
                      L(i, j, k + 1) + L(i, j, k - 1) - 6.f * L(i, j, k);
-  const FF v = fast_two_sum(s.hi, __fadd_rn(s.lo, lsum));
-  return ff_mul(v, FF{ih_hi, ih_lo});
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, lsum));
 }
 
 // phi^{n+1} = phi^n + dt * rate with phi^n = hi + lo; the rate itself is an
@@ -679,9 +679,9 @@ __global__ void k_helfrich_g_ff(PhaseParams P, const float* __restrict__ phi,
   ScalarView<float> H{phi, P.nx, P.ny, P.nz, P.zper};
   ScalarView<float> L{phi_lo, P.nx, P.ny, P.nz, P.zper};
   const FF f{phi[t], phi_lo[t]};
-  const FF lphi = lap7_ff(H, L, i, j, k, P.ih2_hi, P.ih2_lo);
+  const FF lphi = lap7_ff(H, L, i, j, k);
   const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
-  const FF r = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.e2_hi, P.e2_lo})));
+  const FF r = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.e2ih_hi, P.e2ih_lo})));
   g[t] = r.hi;
   g_lo[t] = r.lo;
 }
@@ -697,10 +697,10 @@ __global__ void k_mu_ff(PhaseParams P, const float* __restrict__ phi, const floa
   ScalarView<float> H{phi, P.nx, P.ny, P.nz, P.zper};
   ScalarView<float> L{phi_lo, P.nx, P.ny, P.nz, P.zper};
   const FF f{phi[t], phi_lo[t]};
-  const FF lphi = lap7_ff(H, L, i, j, k, P.ih2_hi, P.ih2_lo);
+  const FF lphi = lap7_ff(H, L, i, j, k);
   if (P.fe_kind == VSV_CAHN_HILLIARD) {
     const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
-    const FF m = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.sig_hi, P.sig_lo})));
+    const FF m = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.sgih_hi, P.sgih_lo})));
     mu[t] = m.hi;
     mu_lo[t] = m.lo;
     return;
@@ -708,10 +708,11 @@ __global__ void k_mu_ff(PhaseParams P, const float* __restrict__ phi, const floa
   ScalarView<float> GH{g, P.nx, P.ny, P.nz, P.zper};
   ScalarView<float> GL{g_lo, P.nx, P.ny, P.nz, P.zper};
   const FF gg{g[t], g_lo[t]};
-  const FF lg = lap7_ff(GH, GL, i, j, k, P.ih2_hi, P.ih2_lo);
+  const FF lg = lap7_ff(GH, GL, i, j, k);
   const FF w = ff_add_f(ff_mul_f(ff_mul(f, f), 3.f), -1.f);
-  const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2_hi, P.e2_lo})));
-  FF m = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, S->gamma_af)));
+  const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2ih_hi, P.e2ih_lo})));
+  const FF gih = ff_mul_f(FF{P.ih2_hi, P.ih2_lo}, S->gamma_af);   // gamma_A / h^2
+  FF m = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul(lphi, gih)));
   if (P.bt_hi != 0.f) m = ff_add(m, ff_mul(gg, FF{P.bt_hi, P.bt_lo}));
   mu[t] = m.hi;
   mu_lo[t] = m.lo;
@@ -805,9 +806,9 @@ __device__ __forceinline__ float xp4(const St4& S, int o) { return o == 3 ? S.xr
 __device__ __forceinline__ float xm4(const St4& S, int o) { return o == 0 ? S.xl : e4(S.c, o - 1); }
 
 // lap7_ff on cell o (same order of operations)
-__device__ __forceinline__ FF lap7_ff4(const St4& H, const St4& L, int o, float ih_hi, float ih_lo) {
-  CascadeSum s(0.f);
-  s.add(xp4(H, o));
+// lap7_ff on cell o of a 4-cell group: the unscaled sum, same order
+__device__ __forceinline__ FF lap7_ff4(const St4& H, const St4& L, int o) {
+  CascadeSum s(xp4(H, o));
   s.add(xm4(H, o));
   s.add(e4(H.yp, o));
   s.add(e4(H.ym, o));
@@ -816,8 +817,7 @@ __device__ __forceinline__ FF lap7_ff4(const St4& H, const St4& L, int o, float 
   s.add_scaled(-6.f, e4(H.c, o));
   const float lsum = xp4(L, o) + xm4(L, o) + e4(L.yp, o) + e4(L.ym, o) + e4(L.zp, o) +
                      e4(L.zm, o) - 6.f * e4(L.c, o);
-  const FF v = fast_two_sum(s.hi, __fadd_rn(s.lo, lsum));
-  return ff_mul(v, FF{ih_hi, ih_lo});
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, lsum));
 }
 
 // lap7 in plain FP32 on cell o (same order as lap7)
@@ -835,7 +835,7 @@ __device__ __forceinline__ bool cell4(const PhaseParams& P, int& i0, int& j, int
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_phi_update_ff4(PhaseParams P, const float* __restrict__ phi,
+__global__ void __launch_bounds__(256, 3) k_phi_update_ff4(PhaseParams P, const float* __restrict__ phi,
                                  const float* __restrict__ phi_lo, const float* __restrict__ mu,
                                  Comp3<float> psi, Comp3<float> v0, Scalars* S, float dt,
                                  float* __restrict__ out, float* __restrict__ out_lo) {
@@ -882,9 +882,9 @@ __global__ void __launch_bounds__(256) k_helfrich_g_ff4(PhaseParams P, const flo
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
     const FF f{e4(H.c, o), e4(L.c, o)};
-    const FF lphi = lap7_ff4(H, L, o, P.ih2_hi, P.ih2_lo);
+    const FF lphi = lap7_ff4(H, L, o);
     const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
-    const FF r = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.e2_hi, P.e2_lo})));
+    const FF r = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.e2ih_hi, P.e2ih_lo})));
     oh[o] = r.hi;
     ol[o] = r.lo;
   }
@@ -906,24 +906,24 @@ __global__ void __launch_bounds__(256) k_mu_ff4(PhaseParams P, const float* __re
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
       const FF f{e4(H.c, o), e4(L.c, o)};
-      const FF lphi = lap7_ff4(H, L, o, P.ih2_hi, P.ih2_lo);
+      const FF lphi = lap7_ff4(H, L, o);
       const FF cubic = ff_mul(f, ff_add_f(ff_mul(f, f), -1.f));
-      const FF mm = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.sig_hi, P.sig_lo})));
+      const FF mm = ff_add(cubic, ff_neg(ff_mul(lphi, FF{P.sgih_hi, P.sgih_lo})));
       oh[o] = mm.hi;
       ol[o] = mm.lo;
     }
   } else {
     const St4 GH = load4(g, G), GL = load4(g_lo, G);
-    const float gam = S->gamma_af;
+    const FF gih = ff_mul_f(FF{P.ih2_hi, P.ih2_lo}, S->gamma_af);   // gamma_A / h^2
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
       const FF f{e4(H.c, o), e4(L.c, o)};
-      const FF lphi = lap7_ff4(H, L, o, P.ih2_hi, P.ih2_lo);
+      const FF lphi = lap7_ff4(H, L, o);
       const FF gg{e4(GH.c, o), e4(GL.c, o)};
-      const FF lg = lap7_ff4(GH, GL, o, P.ih2_hi, P.ih2_lo);
+      const FF lg = lap7_ff4(GH, GL, o);
       const FF w = ff_add_f(ff_mul_f(ff_mul(f, f), 3.f), -1.f);
-      const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2_hi, P.e2_lo})));
-      FF mm = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul_f(lphi, gam)));
+      const FF inner = ff_add(ff_mul(w, gg), ff_neg(ff_mul(lg, FF{P.e2ih_hi, P.e2ih_lo})));
+      FF mm = ff_add(ff_mul(inner, FF{P.cf2_hi, P.cf2_lo}), ff_neg(ff_mul(lphi, gih)));
       if (P.bt_hi != 0.f) mm = ff_add(mm, ff_mul(gg, FF{P.bt_hi, P.bt_lo}));
       oh[o] = mm.hi;
       ol[o] = mm.lo;
@@ -943,12 +943,13 @@ __global__ void __launch_bounds__(256) k_source_ff4(PhaseParams P, const float* 
   if (!cell4(P, i0, j, k)) return;
   const Geo4 G = geo4(P, i0, j, k, false);
   const St4 FH = load4(phi, G), FL = load4(phi_lo, G), MH = load4(mu, G), ML = load4(mu_lo, G);
-  const FF hih{P.hih_hi, P.hih_lo};
-  const FF ie{P.ie_hi, P.ie_lo};
+  // raw central differences; (1/2h)^2 / eta is applied once to each
+  // component of the cross product
+  const FF ie{P.src_hi, P.src_lo};
   const long long jk = j + (long long)k * P.ny;
   const float s0 = s_omega.p[0][jk], s1 = s_omega.p[1][jk], s2 = s_omega.p[2][jk];
   auto dd = [&](float ah, float al, float bh, float bl) {
-    return ff_mul(ff_add(FF{ah, al}, ff_neg(FF{bh, bl})), hih);
+    return ff_add(FF{ah, al}, ff_neg(FF{bh, bl}));
   };
   float o0h[4], o0l[4], o1h[4], o1l[4], o2h[4], o2l[4];
 #pragma unroll
@@ -982,7 +983,7 @@ __global__ void __launch_bounds__(256) k_reduce_va_ff4(PhaseParams P, const floa
                                                        double* partials) {
   const int ng = P.nx >> 2;
   const long long total = (long long)ng * P.ny * P.nz;
-  const FF hihf{P.hih_hi, P.hih_lo}, hef{P.he_hi, P.he_lo}, qf{P.q_hi, P.q_lo}, caf{P.ca_hi, P.ca_lo};
+  const FF agf{P.ag_hi, P.ag_lo}, awf{P.aw_hi, P.aw_lo};
   CascadeSum cp(0.f), ca(0.f);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -995,14 +996,14 @@ __global__ void __launch_bounds__(256) k_reduce_va_ff4(PhaseParams P, const floa
     for (int o = 0; o < 4; ++o) {
       const FF f{e4(H.c, o), e4(L.c, o)};
       auto diff = [&](float ah, float al, float bh, float bl) {
-        return ff_mul(ff_add(FF{ah, al}, ff_neg(FF{bh, bl})), hihf);
+        return ff_add(FF{ah, al}, ff_neg(FF{bh, bl}));
       };
       const FF gx = diff(xp4(H, o), xp4(L, o), xm4(H, o), xm4(L, o));
       const FF gy = diff(e4(H.yp, o), e4(L.yp, o), e4(H.ym, o), e4(L.ym, o));
       const FF gz = diff(e4(H.zp, o), e4(L.zp, o), e4(H.zm, o), e4(L.zm, o));
       const FF g2 = ff_add(ff_add(ff_mul(gx, gx), ff_mul(gy, gy)), ff_mul(gz, gz));
       const FF w = ff_add_f(ff_mul(f, f), -1.f);
-      const FF dens = ff_mul(ff_add(ff_mul(g2, hef), ff_mul(ff_mul(w, w), qf)), caf);
+      const FF dens = ff_add(ff_mul(g2, agf), ff_mul(ff_mul(w, w), awf));
       cp.add(f.hi);
       cp.add(f.lo);
       ca.add(dens.hi);
@@ -1072,17 +1073,18 @@ __global__ void k_source_ff(PhaseParams P, const float* __restrict__ phi, const 
   const long long t = lin(i, j, k, P.nx, P.ny);
   ScalarView<float> FH{phi, P.nx, P.ny, P.nz, P.zper}, FL{phi_lo, P.nx, P.ny, P.nz, P.zper};
   ScalarView<float> MH{mu, P.nx, P.ny, P.nz, P.zper}, ML{mu_lo, P.nx, P.ny, P.nz, P.zper};
-  const FF hih{P.hih_hi, P.hih_lo};
+  // raw central differences; (1/2h)^2 / eta is applied once to each
+  // component of the cross product
   auto dd = [&](const ScalarView<float>& H, const ScalarView<float>& L, int i1, int j1, int k1, int i0,
                 int j0, int k0) {
     const FF a{H(i1, j1, k1), L(i1, j1, k1)}, b{H(i0, j0, k0), L(i0, j0, k0)};
-    return ff_mul(ff_add(a, ff_neg(b)), hih);
+    return ff_add(a, ff_neg(b));
   };
   const FF ax = dd(FH, FL, i + 1, j, k, i - 1, j, k), ay = dd(FH, FL, i, j + 1, k, i, j - 1, k),
            az = dd(FH, FL, i, j, k + 1, i, j, k - 1);
   const FF bx = dd(MH, ML, i + 1, j, k, i - 1, j, k), by = dd(MH, ML, i, j + 1, k, i, j - 1, k),
            bz = dd(MH, ML, i, j, k + 1, i, j, k - 1);
-  const FF ie{P.ie_hi, P.ie_lo};
+  const FF ie{P.src_hi, P.src_lo};
   const long long jk = j + (long long)k * P.ny;
   const FF c0 = ff_add_f(ff_mul(ff_add(ff_mul(ay, bz), ff_neg(ff_mul(az, by))), ie), -s_omega.p[0][jk]);
   const FF c1 = ff_add_f(ff_mul(ff_add(ff_mul(az, bx), ff_neg(ff_mul(ax, bz))), ie), -s_omega.p[1][jk]);
