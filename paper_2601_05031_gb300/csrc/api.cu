@@ -837,6 +837,35 @@ vsv_status export_field(vsv_grid* g, const T* src, int dt, int on_device, void* 
   return VSV_OK;
 }
 
+// Device address of host memory that the GPU may access in place: page-
+// locked memory mapped into the device's address space (cudaHostAlloc,
+// cudaMallocHost, or cudaHostRegister'ed memory under unified addressing),
+// as the runtime reports it.  nullptr for anything else (pageable memory,
+// unknown pointers): that goes through a copy.  A kernel then moves the data
+// across the host link itself, fused with the split or merge of the words,
+// instead of a copy into a staging buffer followed by a kernel.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// FP64 host or device words split into the hi + lo pair (hi, lo): in place
+// from mapped host memory, else through the staging buffer.
+vsv_status split_in(vsv_grid* g, const void* src, int on_device, float* hi, float* lo) {
+  const void* m = on_device ? src : mapped_host(src);
+  if (m) {
+    launch_split_ff(g->cx, (const double*)m, hi, lo, g->N);
+  } else {
+    CK(cudaMemcpyAsync(g->stage_b, src, g->N * 8, cudaMemcpyHostToDevice, g->cx.stream));
+    launch_split_ff(g->cx, (const double*)g->stage_b, hi, lo, g->N);
+  }
+  return VSV_OK;
+}
+
 // phi in: FP64 input splits into hi + lo words on the mixed path.
 template <class T>
 vsv_status import_phi(vsv_grid* g, const void* src, int dt, int on_device) {
@@ -845,8 +874,8 @@ vsv_status import_phi(vsv_grid* g, const void* src, int dt, int on_device) {
     float* lo = g->phi_lo[g->cur];
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (dt == VSV_DTYPE_F64) {
-      CK(cudaMemcpyAsync(g->stage_b, src, g->N * 8, kind, g->cx.stream));
-      launch_split_ff(g->cx, (const double*)g->stage_b, hi, lo, g->N);
+      const vsv_status st = split_in(g, src, on_device, hi, lo);
+      if (st != VSV_OK) return st;
     } else {
       CK(cudaMemcpyAsync(hi, src, g->N * 4, kind, g->cx.stream));
       CK(cudaMemsetAsync(lo, 0, g->N * 4, g->cx.stream));
@@ -863,11 +892,18 @@ template <class T>
 vsv_status export_phi(vsv_grid* g, int dt, int on_device, void* dst) {
   if constexpr (std::is_same<T, float>::value) {
     if (dt == VSV_DTYPE_F64) {
-      launch_merge_ff(g->cx, (const float*)g->phi[g->cur], g->phi_lo[g->cur], (double*)g->stage_a,
-                      g->N);
-      CKL();
-      CK(cudaMemcpyAsync(dst, g->stage_a, g->N * 8,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->cx.stream));
+      // merged in place into device or mapped host memory, else through the
+      // staging buffer
+      void* m = on_device ? dst : const_cast<void*>(mapped_host(dst));
+      if (m) {
+        launch_merge_ff(g->cx, (const float*)g->phi[g->cur], g->phi_lo[g->cur], (double*)m, g->N);
+        CKL();
+      } else {
+        launch_merge_ff(g->cx, (const float*)g->phi[g->cur], g->phi_lo[g->cur], (double*)g->stage_a,
+                        g->N);
+        CKL();
+        CK(cudaMemcpyAsync(dst, g->stage_a, g->N * 8, cudaMemcpyDeviceToHost, g->cx.stream));
+      }
       if (!on_device) CK(cudaStreamSynchronize(g->cx.stream));
       return VSV_OK;
     }
@@ -1575,8 +1611,8 @@ vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int
                                                    : g->ps_lo[field - VSV_FIELD_PSI_PERT_X];
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (dtype == VSV_DTYPE_F64) {
-      CK(cudaMemcpyAsync(g->stage_b, src, g->N * 8, kind, g->cx.stream));
-      launch_split_ff(g->cx, (const double*)g->stage_b, (float*)dst, lo, g->N);
+      const vsv_status sst = split_in(g, src, on_device, (float*)dst, lo);
+      if (sst != VSV_OK) return sst;
     } else {
       CK(cudaMemcpyAsync(dst, src, g->N * 4, kind, g->cx.stream));
       CK(cudaMemsetAsync(lo, 0, g->N * 4, g->cx.stream));

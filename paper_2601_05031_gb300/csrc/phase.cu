@@ -8,7 +8,9 @@
 // Fields are [nz][ny][nx] without halos.  Scalars (phi, mu, g) use the
 // face mirror at walls and wrap on periodic axes; the flow perturbation
 // psi' = psi - psi0 is zero on the wall nodes.
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 
 #include "internal.h"
 
@@ -734,6 +736,47 @@ __global__ void k_merge_ff(const float* __restrict__ hi, const float* __restrict
   if (t < n) out[t] = (double)hi[t] + (double)lo[t];
 }
 
+// The same splits and merges four elements per thread with 16-byte accesses
+// (every array 16-byte aligned), grid-strided; the last n % 4 elements are
+// done one per thread.  Used for device buffers and for mapped host memory,
+// where fewer, wider requests cross the host link.
+__global__ void k_split_ff_v4(const double* __restrict__ in, float* __restrict__ hi,
+                              float* __restrict__ lo, long long n) {
+  const long long n4 = n >> 2, stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double2* in2 = reinterpret_cast<const double2*>(in);
+  for (long long t = t0; t < n4; t += stride) {
+    const double2 a = in2[2 * t], b = in2[2 * t + 1];
+    const float4 h = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    const float4 l = make_float4((float)(a.x - (double)h.x), (float)(a.y - (double)h.y),
+                                 (float)(b.x - (double)h.z), (float)(b.y - (double)h.w));
+    reinterpret_cast<float4*>(hi)[t] = h;
+    reinterpret_cast<float4*>(lo)[t] = l;
+  }
+  const long long r = 4 * n4 + t0;
+  if (r < n) {
+    const double d = in[r];
+    const float h = (float)d;
+    hi[r] = h;
+    lo[r] = (float)(d - (double)h);
+  }
+}
+
+__global__ void k_merge_ff_v4(const float* __restrict__ hi, const float* __restrict__ lo,
+                              double* __restrict__ out, long long n) {
+  const long long n4 = n >> 2, stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double2* out2 = reinterpret_cast<double2*>(out);
+  for (long long t = t0; t < n4; t += stride) {
+    const float4 h = reinterpret_cast<const float4*>(hi)[t];
+    const float4 l = reinterpret_cast<const float4*>(lo)[t];
+    out2[2 * t] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    out2[2 * t + 1] = make_double2((double)h.z + (double)l.z, (double)h.w + (double)l.w);
+  }
+  const long long r = 4 * n4 + t0;
+  if (r < n) out[r] = (double)hi[r] + (double)lo[r];
+}
+
 // ---------------------------------------------------------------- 4-cell kernels
 // The same double-word kernels with one thread per 4 consecutive x cells
 // (nx a multiple of 4): the own cells and the y / z neighbours are 16-byte
@@ -1107,15 +1150,27 @@ void launch_source_ff(Ctx& cx, const PhaseParams& P, const float* phi, const flo
   cx.after(VSV_KCLASS_PHASE, 40.0 * (double)((long long)P.nx * P.ny * P.nz));
 }
 
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+static unsigned v4_blocks(const Ctx& cx, long long n) {
+  const long long want = (n / 4 + kBlock - 1) / kBlock;
+  return (unsigned)std::max<long long>(1, std::min<long long>(want, 16LL * cx.sms));
+}
+
 void launch_split_ff(Ctx& cx, const double* in, float* hi, float* lo, long long n) {
   cx.before(-1);
-  k_split_ff<<<nblk(n), kBlock, 0, cx.stream>>>(in, hi, lo, n);
+  if (aligned16(in) && aligned16(hi) && aligned16(lo))
+    k_split_ff_v4<<<v4_blocks(cx, n), kBlock, 0, cx.stream>>>(in, hi, lo, n);
+  else
+    k_split_ff<<<nblk(n), kBlock, 0, cx.stream>>>(in, hi, lo, n);
   cx.after(-1);
 }
 
 void launch_merge_ff(Ctx& cx, const float* hi, const float* lo, double* out, long long n) {
   cx.before(-1);
-  k_merge_ff<<<nblk(n), kBlock, 0, cx.stream>>>(hi, lo, out, n);
+  if (aligned16(out) && aligned16(hi) && aligned16(lo))
+    k_merge_ff_v4<<<v4_blocks(cx, n), kBlock, 0, cx.stream>>>(hi, lo, out, n);
+  else
+    k_merge_ff<<<nblk(n), kBlock, 0, cx.stream>>>(hi, lo, out, n);
   cx.after(-1);
 }
 
