@@ -146,10 +146,10 @@ GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per variant, averaged over
 # the finest-level launches of an 80-launch window of one launch-list capture
 # of this benchmark at 512 x 256 x 256 (one ncu pass) and weighted 1:2:1
-# (0.768, 1.213, 2.419 GB), 1.403 GB per launch, per cell and component
+# (0.769, 1.214, 2.421 GB), 1.405 GB per launch, per cell and component
 # here.  To be retaken (and set to None meanwhile) whenever k_rbgs_fused
 # changes.
-FUSED_SWEEP_TRAFFIC_PER_CELL = 1.4034e9 / (512 * 256 * 256 * 3)
+FUSED_SWEEP_TRAFFIC_PER_CELL = 1.4045e9 / (512 * 256 * 256 * 3)
 
 
 def make_sim(w, prec, cycles, extrapolate=1):

@@ -226,8 +226,10 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       MM[h] = M[h];
       M[h] = V[h];
       V[h] = P[h];
-      P[h] = (p > ze || (ZERO_IN && ghost_plane(p + 1))) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                                         : lds4(slotA(p + 1) + rown[h] * kW + 4 * q);
+      // ZERO_IN: the black values of plane p + 1 are zero and its red ones
+      // are written by the red phase of the next step before any read
+      P[h] = (ZERO_IN || p > ze) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                 : lds4(slotA(p + 1) + rown[h] * kW + 4 * q);
     }
     // the black phase's operands from shared memory: the y neighbours of
     // the two rows, their rhs groups and, at the tile edges, the x halo
@@ -309,8 +311,65 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         B1r = lds4(cB + (rown[1] - 1) * kW + 4 * q);
       }
     };
+    // ZERO_IN: every neighbour of a red cell is black and still zero, so the
+    // red update is the scaled rhs alone: (0 - b h^2) rc, the value the
+    // general form gives with a zero neighbour sum
+    auto red_phase_zero = [&]() {
+      if (!red) return;
+      const int zw = zwall(p);
+      const int par = (jown[0] + p) & 1;          // red offset of row 2ty
+  #pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!upd_row[h]) continue;
+        const float4 Bv = h == 0 ? B0r : B1r;
+        const float sr = srow(jown[h], p), rc = zw ? rco[h][1] : rco[h][0];
+        float* dst = cA + rown[h] * kW + 4 * q;
+        if ((h == 0 ? par : 1 - par) == 0) {
+          V[h].x = (0.f - (beta * Bv.x + sr) * h2) * rc;
+          V[h].z = (0.f - (beta * Bv.z + sr) * h2) * rc;
+          dst[0] = V[h].x; dst[2] = V[h].z;
+        } else {
+          V[h].y = (0.f - (beta * Bv.y + sr) * h2) * rc;
+          V[h].w = (0.f - (beta * Bv.w + sr) * h2) * rc;
+          dst[1] = V[h].y; dst[3] = V[h].w;
+        }
+      }
+      if (ty == 0 || ty == 7) {   // halo rows y0 - 1 and y0 + kTY
+        const int r = (ty == 0) ? 1 : kRA - 2;
+        const int j = y0 - kH + r;
+        if (G.per_y || (j >= 0 && j < G.ny)) {
+          const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
+          const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
+          const float sr = srow(j, p), rc = rc_of(G, jw + zw);
+          float* dst = cA + r * kW + 4 * q;
+          if (((j + p) & 1) == 0) {
+            dst[0] = (0.f - (beta * Bv.x + sr) * h2) * rc;
+            dst[2] = (0.f - (beta * Bv.z + sr) * h2) * rc;
+          } else {
+            dst[1] = (0.f - (beta * Bv.y + sr) * h2) * rc;
+            dst[3] = (0.f - (beta * Bv.w + sr) * h2) * rc;
+          }
+        }
+      }
+      if (tid >= 32 && tid < 32 + 2 * (kRA - 2)) {   // halo columns x0 - 1 and x0 + kTX
+        const int idx = tid - 32;
+        const int r = 1 + (idx >> 1);
+        const int c = (idx & 1) ? kHX + kTX : kHX - 1;
+        const int j = y0 - kH + r;
+        const int x = x0 - kHX + c;
+        if ((G.per_y || (j >= 0 && j < G.ny)) && (((x + j + p) & 1) == 0)) {
+          const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
+          const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
+          cA[r * kW + c] = (0.f - bb * h2) * rc_of(G, jw + zw);
+        }
+      }
+    };
     auto red_phase = [&]() {
       // ---- red cells of plane p: own groups, halo rows, halo columns
+      if constexpr (ZERO_IN) {
+        red_phase_zero();
+        return;
+      }
       if (red) {
         const int zw = zwall(p);
         // rows 2ty and 2ty+1 have opposite parity; each row's red cells need the
