@@ -134,3 +134,27 @@ def test_full_size_step_sampled_against_oracle(V):
     assert rps <= 2e-7 * ommax, (rps, ommax)
     # a property at any size: the velocity is divergence-free
     assert d1["max_div_v"] <= 1e-6 * vmax / h, (d1["max_div_v"], vmax)
+
+
+def test_full_size_graph_replay_matches_plain_steps(V):
+    """bench.py times the steps as replays of the library's captured graph
+    (a one-grid batch); at full size they give the same bits as one
+    vsv_step call per step."""
+    import torch
+    import bench
+    from paper_2601_05031_gb300.sim import Batch
+    w = inputs.vesicle_couette_512x256x256()
+    a = bench.make_sim(w, V.VSV_MIXED, 4, 1)
+    a.step(2 + bench.GRAPH_STEPS, w.dt)
+    b = bench.make_sim(w, V.VSV_MIXED, 4, 1, stream=torch.cuda.Stream())
+    batch = Batch([b])
+    batch.step(2 + bench.GRAPH_STEPS, w.dt)      # two plain steps, then one capture + replay
+    torch.cuda.synchronize()
+    for fid in (V.VSV_FIELD_PHI, V.VSV_FIELD_PSI_PERT_X, V.VSV_FIELD_OMEGA_PERT_Z):
+        x = a.field(fid, np.float64, on_device=True)
+        y = b.field(fid, np.float64, on_device=True)
+        assert torch.equal(x, y), fid
+    assert b.kernel_launches() == a.kernel_launches()
+    batch.close()
+    a.close()
+    b.close()
