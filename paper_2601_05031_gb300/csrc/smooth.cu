@@ -532,7 +532,9 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   G.nx = L.n[0]; G.ny = L.n[1]; G.nz = L.n[2];
   G.per_y = L.per[1]; G.per_z = L.per[2];
   G.ntx = (L.n[0] + kTX - 1) / kTX; G.nty = (L.n[1] + kTY - 1) / kTY;
-  if (zchunk <= 0) zchunk = pick_zchunk(L, ncomp, 2 * cx.sms, 2);
+  // a step costs about three planes of pipeline fill; chunks down to four
+  // planes let the small levels spread over more SMs
+  if (zchunk <= 0) zchunk = pick_zchunk(L, ncomp, 2 * cx.sms, 3, 4);
   G.zchunk = std::min(zchunk, L.n[2]);
   G.rc0 = L.rcf[0];
   G.rc1 = L.rcf[1];

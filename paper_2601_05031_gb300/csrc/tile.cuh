@@ -110,8 +110,9 @@ inline double tile_fill(const Level& L) {
 // z-chunk length for a tiled z-marching kernel on level L: the grid is
 // (tiles x chunks x ncomp) CTAs, `slots` of which are resident at a time, and
 // a chunk costs its planes plus about `halo` extra planes of pipeline fill.
-// Picks the chunk that minimises waves x (chunk + halo).
-inline int pick_zchunk(const Level& L, int ncomp, int slots, int halo) {
+// Picks the chunk that minimises waves x (chunk + halo), chunks of at least
+// `min_chunk` planes unless the whole extent is shorter.
+inline int pick_zchunk(const Level& L, int ncomp, int slots, int halo, int min_chunk = 8) {
   const int nz = L.n[2];
   const long long tiles =
       (long long)((L.n[0] + kTX - 1) / kTX) * ((L.n[1] + kTY - 1) / kTY) * ncomp;
@@ -120,7 +121,7 @@ inline int pick_zchunk(const Level& L, int ncomp, int slots, int halo) {
   int best_chunk = nz;
   for (int nzc = 1; nzc <= nz; ++nzc) {
     const int chunk = (nz + nzc - 1) / nzc;
-    if (chunk < 8 && nzc > 1) break;
+    if (chunk < min_chunk && nzc > 1) break;
     const long long blocks = tiles * ((nz + chunk - 1) / chunk);
     const long long waves = (blocks + slots - 1) / slots;
     const double eff = (double)(tiles * nz) / ((double)waves * slots * (chunk + halo));
