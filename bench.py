@@ -143,13 +143,11 @@ GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
 
 # DRAM traffic of the finest-level fused sweeps per launch, averaged over the
 # four sweeps of a correction (zero input, plain, plain, iterate update):
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per variant, averaged over
-# the finest-level launches of an 80-launch window of one launch-list capture
-# of this benchmark at 512 x 256 x 256 (one ncu pass) and weighted 1:2:1
-# (0.769, 1.214, 2.421 GB), 1.405 GB per launch, per cell and component
-# here.  To be retaken (and set to None meanwhile) whenever k_rbgs_fused
-# changes.
-FUSED_SWEEP_TRAFFIC_PER_CELL = 1.4045e9 / (512 * 256 * 256 * 3)
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of all 888 such launches
+# in one launch-list capture of this benchmark at 512 x 256 x 256 (one ncu
+# pass), 1.4038 GB per launch, per cell and component here.  To be retaken
+# (and set to None meanwhile) whenever k_rbgs_fused changes.
+FUSED_SWEEP_TRAFFIC_PER_CELL = 1.4038e9 / (512 * 256 * 256 * 3)
 
 # steps per captured graph (the library's replay length)
 GRAPH_STEPS = 6
