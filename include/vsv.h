@@ -257,11 +257,18 @@ vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, i
                              double* relres_out);
 
 /* Copy a field out (full omega / psi include the base flow).  Synchronous
- * for host destinations. */
+ * for host destinations.  On the mixed path an FP64 phi goes to page-locked,
+ * mapped host memory (cudaHostAlloc / cudaMallocHost, or cudaHostRegister
+ * under unified addressing) straight from the kernel that merges the two
+ * words; any other host memory is filled through a device staging buffer
+ * and a copy.  The bits are the same either way; dst needs no alignment. */
 vsv_status vsv_get_field(vsv_grid* g, int field, void* dst, int dtype, int on_device);
 
 /* Replace phi (mu, V, A are recomputed before the next step; V0, A0 and the
- * flow are kept) or a perturbation component OMEGA_PERT_* / PSI_PERT_*. */
+ * flow are kept) or a perturbation component OMEGA_PERT_* / PSI_PERT_*.  On
+ * the mixed path FP64 input in page-locked, mapped host memory is read in
+ * place by the kernel that splits it into the two words; other host memory
+ * is copied through a staging buffer first. */
 vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int on_device);
 
 /* Observables of the current state; synchronises. */
