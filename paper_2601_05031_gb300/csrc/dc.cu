@@ -299,7 +299,18 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
     Pl[h] = lds4(slot(sL, zb) + rown[h] * kW + 4 * q);
   }
   double rr = 0.0, bb = 0.0;
-  for (int p = zb; p < ze; ++p) {
+  // global offsets of the thread's groups in plane zb, advanced by a plane
+  // per step, and the ring slot of plane p, advanced with p
+  const long long plane_n = (long long)G.ny * G.nx;
+  long long gown[ROWS];
+#pragma unroll
+  for (int h = 0; h < ROWS; ++h) gown[h] = ((long long)zb * G.ny + jown[h]) * G.nx + x0 + 4 * gx;
+  for (int p = zb, is = zb % kDS; p < ze;
+       ++p, is = (is == kDS - 1) ? 0 : is + 1) {
+    auto sl = [&](float* base, int k) {   // slot of plane p + k, 0 <= k < kDS
+      const int t = is + k;
+      return base + (t >= kDS ? t - kDS : t) * (kDR * kW);
+    };
     // the step's rhs words and row source, loaded ahead of the barrier so
     // that their latency overlaps the wait for the staged planes
     float4 B1s[ROWS], B2s[ROWS];
@@ -308,26 +319,26 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
     for (int h = 0; h < ROWS; ++h) {
       const int j = jown[h];
       const bool ok = !RAGGED || (j < G.ny && x0 + 4 * gx < G.nx);
-      const long long gi = ((long long)p * G.ny + j) * G.nx + x0 + 4 * gx;
+      const long long gi = gown[h] + (long long)(p - zb) * plane_n;
       B1s[h] = ok ? *reinterpret_cast<const float4*>(bh + gi) : make_float4(0.f, 0.f, 0.f, 0.f);
       B2s[h] = ok && bl ? *reinterpret_cast<const float4*>(bl + gi) : make_float4(0.f, 0.f, 0.f, 0.f);
       Ss[h] = ok && S ? S[j + (long long)p * G.ny] : 0.f;
     }
     if (p + 3 <= ze) {   // plane p+3 is needed by step p+2
-      ds.stage(slot(sH, p + 3), xh, G, p + 3, false);
-      ds.stage(slot(sL, p + 3), xl, G, p + 3, false);
+      ds.stage(sl(sH, 3), xh, G, p + 3, false);
+      ds.stage(sl(sL, 3), xl, G, p + 3, false);
     }
     cp_async_commit();
     cp_async_wait2();
     __syncthreads();
-    const float* cH = slot(sH, p);
-    const float* cL = slot(sL, p);
+    const float* cH = sl(sH, 0);
+    const float* cL = sl(sL, 0);
 #pragma unroll
     for (int h = 0; h < ROWS; ++h) {
       Mh[h] = Vh[h]; Ml[h] = Vl[h];
       Vh[h] = Ph[h]; Vl[h] = Pl[h];
-      Ph[h] = lds4(slot(sH, p + 1) + rown[h] * kW + 4 * q);
-      Pl[h] = lds4(slot(sL, p + 1) + rown[h] * kW + 4 * q);
+      Ph[h] = lds4(sl(sH, 1) + rown[h] * kW + 4 * q);
+      Pl[h] = lds4(sl(sL, 1) + rown[h] * kW + 4 * q);
     }
     float r2 = 0.f, b2 = 0.f;
 #pragma unroll
@@ -340,7 +351,7 @@ k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3
       const float4 Ul = lds4(rowL - kW + 4 * q), Dl = lds4(rowL + kW + 4 * q);
       const float Lh = rowH[4 * q - 1], Rh = rowH[4 * q + 4];
       const float Ll = rowL[4 * q - 1], Rl = rowL[4 * q + 4];
-      const long long gi = ((long long)p * G.ny + j) * G.nx + x0 + 4 * gx;
+      const long long gi = gown[h] + (long long)(p - zb) * plane_n;
       const float4 B1 = B1s[h], B2 = B2s[h];
       const float s = Ss[h];
       float res[4];
