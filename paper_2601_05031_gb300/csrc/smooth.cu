@@ -481,7 +481,9 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
 // exist (below that the idle lanes cost more than the second per-colour
 // launch saves) and the level has at least 2^17 cells (on smaller levels
 // the few CTAs' z-march takes longer than two per-colour launches: measured
-// 16.8 us against 2 x 5.9 us at 64 x 32 x 32).
+// 16.8 us against 2 x 5.9 us at 64 x 32 x 32; with four-plane chunks 11.0 us,
+// yet the graph-replayed step was slower with it, 1,795 against 1,801
+// Mcell-steps/s).
 bool fused_sweep_ok(const Level& L, bool ragged) {
   if (level_ok(L)) return true;
   return ragged && ragged_ok(L) && tile_fill(L) >= 0.25 && L.cells() >= (1 << 17);
