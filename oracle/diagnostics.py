@@ -15,9 +15,18 @@
   (weights (1 - phi)/2), max |div v| and max |div psi|.
 
 Velocity derivatives use central differences with the no-slip wall velocity
-on the wall nodes.  Parity unpinned beyond the closed forms of the Couette /
-Poiseuille profiles (uniform sigma_xy, D0 of a linear shear) checked in the
-tests.
+on the wall nodes.
+
+Pinned by (tests/test_oracle_diagnostics_pins.py): the body-free Couette flow
+(uniform <sigma_xy> = eta (v_hi - v_lo) / H, sigma_t = |sigma_xy|,
+D = D0 = eta g^2 N h^3, zero resistance and deviations); the body-free planar
+Poiseuille profile (linear <sigma_xy>(y) with its wall-row offsets, D from
+it); a trigonometric stream vector whose stress tensor, dissipation and
+max |div psi| are closed forms of the discrete calculus (with and without
+velocity on the wall nodes); flow deviations of trigonometric fields by
+orthogonality; the centre of mass of a sharp ball on any cell; the tanh
+sphere's volume, area, reduced volume and energies against their
+finite-width closed forms at second order.
 """
 from __future__ import annotations
 
