@@ -81,6 +81,21 @@ __device__ __forceinline__ T prolong_value(T aC, T aX, T bC, T bX, T cC, T cX, T
   return acc;
 }
 
+// Weighted red-black update of one cell from its old value x and its
+// Gauss-Seidel value gs: gs itself for omega = 1, else x + omega (gs - x) as
+// one fused multiply-add (red-black SOR smoothing; an over-relaxed smoother
+// contracts a multigrid V-cycle faster).  The difference gs - x is a
+// separately rounded subtraction (the _rn intrinsics are never contracted
+// into a multiply-add with the product that forms gs), so every kernel
+// rounds the same way.  Every sweep kernel updates its cells through this
+// function, so the fused and per-colour sweeps agree bit for bit.
+template <class T>
+__device__ __forceinline__ T relax(T x, T gs, T omega) {
+  if (omega == (T)1) return gs;
+  if constexpr (sizeof(T) == 4) return __fmaf_rn(omega, __fsub_rn(gs, x), x);
+  else return __fma_rn(omega, __dsub_rn(gs, x), x);
+}
+
 // Right-hand side b = beta * B[c] + S[j + k * ny] (S may be null).
 template <class T>
 struct Rhs3 {

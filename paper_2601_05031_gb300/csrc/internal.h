@@ -123,6 +123,7 @@ struct CoarseCycle {
   Level lv[kMaxLevels];
   int first, last;
   int nu1, nu2, coarse_sweeps;
+  double omega;                // relaxation weight of the nu1 / nu2 sweeps (coarsest: 1)
   double h2[kMaxLevels];       // 1 / inv_h2 of each level (rounded to T in the kernel)
   long long off[kMaxLevels];   // element offset of level l's (e, r) pair
   long long total;             // elements of shared memory
@@ -160,9 +161,11 @@ bool launch_prolong_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> 
 // ragged: also levels whose extents are not multiples of the tile (partial
 // edge tiles), where enough of the tiles' cells exist
 bool fused_sweep_ok(const Level& L, bool ragged);
+// omega: relaxation weight of the sweep (1: Gauss-Seidel)
 void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
                        int ncomp, int zchunk, int kclass, bool zero_in,
-                       const Comp3<float>* upd_hi = nullptr, const Comp3<float>* upd_lo = nullptr);
+                       const Comp3<float>* upd_hi = nullptr, const Comp3<float>* upd_lo = nullptr,
+                       float omega = 1.f);
 
 // ---------------------------------------------------------------- phase-field (phase.cu)
 struct PhaseParams {
@@ -210,13 +213,20 @@ void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> psi_l
                      Comp3<T> v);
 // Diagnostic partial sums; out has kDiagQ doubles per block.
 constexpr int kDiagQ = 16;
+// vel_lo, om_lo, ps_lo: low words of the double-word velocity, omega' and
+// psi' of the mixed path (null pointers on the FP64 path)
 template <class T>
 void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo, const T* g,
-                 const T* g_lo, Comp3<T> vel,
-                 Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0_ring,
+                 const T* g_lo, Comp3<T> vel, Comp3<T> vel_lo, Comp3<T> omega, Comp3<T> om_lo,
+                 Comp3<T> psi, Comp3<T> ps_lo, Comp3<const double> psi0_ring,
                  Comp3<const double> v0d, T* sigma_t, double* partials, int nblocks, double* out);
 template <class T>
-void launch_stress_profile(Ctx& cx, const PhaseParams& P, Comp3<T> vel, double* out);
+void launch_stress_profile(Ctx& cx, const PhaseParams& P, Comp3<T> vel, Comp3<T> vel_lo,
+                           double* out);
+// Mixed path: v = v0 + curl psi' in FP64 from the double-word psi' and the
+// FP64 base-flow table, stored as a double word (v, v_lo).
+void launch_velocity_dw(Ctx& cx, const PhaseParams& P, Comp3<float> psi, Comp3<float> psi_lo,
+                        Comp3<const double> v0d, Comp3<float> v, Comp3<float> v_lo);
 template <class Tin, class Tout>
 void launch_convert(Ctx& cx, const Tin* in, Tout* out, long long n);
 template <class T>

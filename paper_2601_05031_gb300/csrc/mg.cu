@@ -123,7 +123,8 @@ __device__ __forceinline__ T resid_at(const T* __restrict__ x, const Level& L, i
 }
 
 // ---------------------------------------------------------------- sweeps
-// One colour of a red-black Gauss-Seidel sweep (omega = 1) or SOR sweep,
+// One colour of a red-black Gauss-Seidel sweep (omega = 1) or SOR sweep
+// (the red-black SOR solver, or over-relaxed multigrid smoothing),
 // colour = (i + j + k) & 1, in place.  Thread t handles the t-th cell of the
 // colour in its x row.
 template <class T>
@@ -139,7 +140,7 @@ __global__ void k_rb_sweep(Level L, Comp3<T> X, Rhs3<T> R, int color, T omega, T
   const T s = sum_nb(x, L, i, j, k, c, nwall);
   const T b = rhs_at(R, comp, c, j, k, ny);
   const T gs = (s - b * h2) * lv_rc<T>(L, nwall);
-  x[c] = (omega == (T)1) ? gs : x[c] + omega * (gs - x[c]);
+  x[c] = relax(x[c], gs, omega);
 }
 
 // Residual of the fine (or any) level, restricted to the next coarser level
@@ -506,7 +507,7 @@ __host__ __device__ bool blocked_transfer_ok(const Level& F, const Level& C) {
 // advanced by the block size incrementally (adds and carries instead of two
 // integer divisions per cell).
 template <class T>
-__device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2) {
+__device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2, T omega) {
   const int nx = L.n[0], ny = L.n[1], nxh = (nx + 1) >> 1;
   const int nh = nxh * ny * L.n[2];   // cells of one colour, rounded up per row
   const int B = blockDim.x;
@@ -530,7 +531,7 @@ __device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2) {
         const int t = (k * ny + j) * nx + i;
         int nwall;
         const T sum = sum_nb(e, L, i, j, k, t, nwall);
-        e[t] = (sum - r[t] * h2) * lv_rc<T>(L, nwall);
+        e[t] = relax(e[t], (sum - r[t] * h2) * lv_rc<T>(L, nwall), omega);
       }
       __syncthreads();
     }
@@ -611,17 +612,17 @@ k_coarse_vcycle(const __grid_constant__ CoarseCycle CC, Comp3<T> E, Comp3<T> RR)
   }
   __syncthreads();
   for (int l = f; l < l_last; ++l) {
-    cv_sweep<T>(CC.lv[l], e(l), r(l), CC.nu1, (T)CC.h2[l]);
+    cv_sweep<T>(CC.lv[l], e(l), r(l), CC.nu1, (T)CC.h2[l], (T)CC.omega);
     cv_restrict<T>(CC.lv[l], CC.lv[l + 1], e(l), r(l), r(l + 1));
     const int nc = (int)CC.lv[l + 1].cells();
     T* ec = e(l + 1);
     for (int t = threadIdx.x; t < nc; t += blockDim.x) ec[t] = (T)0;
     __syncthreads();
   }
-  cv_sweep<T>(CC.lv[l_last], e(l_last), r(l_last), CC.coarse_sweeps, (T)CC.h2[l_last]);
+  cv_sweep<T>(CC.lv[l_last], e(l_last), r(l_last), CC.coarse_sweeps, (T)CC.h2[l_last], (T)1);
   for (int l = l_last - 1; l >= f; --l) {
     cv_prolong<T>(CC.lv[l], CC.lv[l + 1], e(l), e(l + 1));
-    cv_sweep<T>(CC.lv[l], e(l), r(l), CC.nu2, (T)CC.h2[l]);
+    cv_sweep<T>(CC.lv[l], e(l), r(l), CC.nu2, (T)CC.h2[l], (T)CC.omega);
   }
   const T* e0 = e(f);
   for (int t = threadIdx.x; t < n0; t += blockDim.x) E.at(comp)[t] = e0[t];

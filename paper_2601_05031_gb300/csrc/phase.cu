@@ -281,11 +281,47 @@ __global__ void k_velocity(PhaseParams P, Comp3<T> psi, Comp3<T> psi_lo, Comp3<T
   v.p[2][t] = v0.p[2][jk] + ((Y(i + 1, j, k) - Y(i - 1, j, k)) - (X(i, j + 1, k) - X(i, j - 1, k))) * hih;
 }
 
+// Velocity of the mixed path as a double word (hi + lo) for the observables
+// and FP64 exports: v = v0 + curl psi' formed in FP64 from the double-word
+// stream vector and the FP64 base-flow table, then split into its rounded
+// FP32 value and the FP32 rounding of the remainder (about 48 significant
+// bits).  Not on the time-stepping path.
+__global__ void k_velocity_dw(PhaseParams P, Comp3<float> psi, Comp3<float> psi_lo,
+                              Comp3<const double> v0d, Comp3<float> v, Comp3<float> v_lo) {
+  int i, j, k, comp_;
+  if (!cell3(P.nx, P.ny, P.nz, i, j, k, comp_)) return;
+  const long long t = lin(i, j, k, P.nx, P.ny);
+  const double hih = 0.5 * P.inv_h;
+  PertView<float> X{psi.p[0], P.nx, P.ny, P.nz, P.zper};
+  PertView<float> Y{psi.p[1], P.nx, P.ny, P.nz, P.zper};
+  PertView<float> Z{psi.p[2], P.nx, P.ny, P.nz, P.zper};
+  PertView<float> XL{psi_lo.p[0], P.nx, P.ny, P.nz, P.zper};
+  PertView<float> YL{psi_lo.p[1], P.nx, P.ny, P.nz, P.zper};
+  PertView<float> ZL{psi_lo.p[2], P.nx, P.ny, P.nz, P.zper};
+  auto d = [&](const PertView<float>& H, const PertView<float>& L, int i1, int j1, int k1, int i0,
+               int j0, int k0) {
+    return (((double)H(i1, j1, k1) + (double)L(i1, j1, k1)) -
+            ((double)H(i0, j0, k0) + (double)L(i0, j0, k0))) * hih;
+  };
+  const long long jk = j + (long long)k * P.ny;
+  double w[3];
+  w[0] = v0d.p[0][jk] + (d(Z, ZL, i, j + 1, k, i, j - 1, k) - d(Y, YL, i, j, k + 1, i, j, k - 1));
+  w[1] = v0d.p[1][jk] + (d(X, XL, i, j, k + 1, i, j, k - 1) - d(Z, ZL, i + 1, j, k, i - 1, j, k));
+  w[2] = v0d.p[2][jk] + (d(Y, YL, i + 1, j, k, i - 1, j, k) - d(X, XL, i, j + 1, k, i, j - 1, k));
+  for (int c = 0; c < 3; ++c) {
+    const float hi = __double2float_rn(w[c]);
+    v.at(c)[t] = hi;
+    v_lo.at(c)[t] = __double2float_rn(w[c] - (double)hi);
+  }
+}
+
 // ---------------------------------------------------------------- observables
-// Velocity (materialised) with the no-slip wall velocity on the wall nodes.
+// Velocity (materialised; lo: the low words of a double-word velocity, or
+// null) with the no-slip wall velocity on the wall nodes.
 template <class T>
 struct VelView {
   const T* __restrict__ a;
+  const T* __restrict__ lo;
   int nx, ny, nz, zper, comp;
   const PhaseParams* P;
   __device__ __forceinline__ double operator()(int i, int j, int k) const {
@@ -295,7 +331,19 @@ struct VelView {
     if (j >= ny) return P->vwall[1][comp];
     if (k < 0) return P->vwall[2][comp];
     if (k >= nz) return P->vwall[3][comp];
-    return (double)a[lin(i, j, k, nx, ny)];
+    const long long t = lin(i, j, k, nx, ny);
+    return lo ? (double)a[t] + (double)lo[t] : (double)a[t];
+  }
+};
+
+// A double-word perturbation field (hi + lo; lo may be null) read in FP64,
+// zero on the wall nodes.
+template <class T>
+struct PertView2 {
+  PertView<T> hi, lo;
+  bool has_lo;
+  __device__ __forceinline__ double operator()(int i, int j, int k) const {
+    return has_lo ? (double)hi(i, j, k) + (double)lo(i, j, k) : (double)hi(i, j, k);
   }
 };
 
@@ -318,10 +366,14 @@ struct V0View {
 // 3 |psi'|^2, 4 w = (1-phi)/2, 5..7 w x, w y, w z, 8 energy density,
 // 9 max |div v|, 10 max |div psi|, 11 max sigma_t, 12 (Helfrich with a
 // membrane tension) the face-difference area density over c_A / eps.
+// vel_lo, om_lo, ps_lo: low words of double-word velocity, omega' and psi'
+// (mixed path), or null pointers.
 template <class T>
 __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ phi_lo,
-                       const T* __restrict__ g, const T* __restrict__ g_lo, Comp3<T> vel, Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0r,
-                       Comp3<const double> v0d, T* sigma_t, double* partials) {
+                       const T* __restrict__ g, const T* __restrict__ g_lo, Comp3<T> vel,
+                       Comp3<T> vel_lo, Comp3<T> omega, Comp3<T> om_lo, Comp3<T> psi,
+                       Comp3<T> ps_lo, Comp3<const double> psi0r, Comp3<const double> v0d,
+                       T* sigma_t, double* partials) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   double q[kDiagQ];
   for (int a = 0; a < kDiagQ; ++a) q[a] = 0.0;
@@ -333,7 +385,7 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
     const long long t = lin(i, j, k, P.nx, P.ny);
     double G[3][3], G0[3][3];
     for (int c = 0; c < 3; ++c) {
-      VelView<T> V{vel.p[c], P.nx, P.ny, P.nz, P.zper, c, &P};
+      VelView<T> V{vel.p[c], vel_lo.p[c], P.nx, P.ny, P.nz, P.zper, c, &P};
       G[c][0] = (V(i + 1, j, k) - V(i - 1, j, k)) * hih;
       G[c][1] = (V(i, j + 1, k) - V(i, j - 1, k)) * hih;
       G[c][2] = (V(i, j, k + 1) - V(i, j, k - 1)) * hih;
@@ -353,7 +405,8 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
     q[1] += d0;
     double o2 = 0.0, p2 = 0.0;
     for (int c = 0; c < 3; ++c) {
-      const double o = omega.p[c][t], p = psi.p[c][t];
+      const double o = (double)omega.p[c][t] + (om_lo.p[c] ? (double)om_lo.p[c][t] : 0.0);
+      const double p = (double)psi.p[c][t] + (ps_lo.p[c] ? (double)ps_lo.p[c][t] : 0.0);
       o2 += o * o;
       p2 += p * p;
     }
@@ -403,17 +456,18 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
     }
     q[9] = fmax(q[9], fabs(G[0][0] + G[1][1] + G[2][2]));
     // div psi with psi = psi0(y, z) + psi'; psi0 ring table holds the wall data
-    PertView<T> PX{psi.p[0], P.nx, P.ny, P.nz, P.zper};
-    PertView<T> PY{psi.p[1], P.nx, P.ny, P.nz, P.zper};
-    PertView<T> PZ{psi.p[2], P.nx, P.ny, P.nz, P.zper};
+    const bool pl = ps_lo.p[0] != nullptr;
+    PertView2<T> PX{{psi.p[0], P.nx, P.ny, P.nz, P.zper}, {pl ? ps_lo.p[0] : psi.p[0], P.nx, P.ny, P.nz, P.zper}, pl};
+    PertView2<T> PY{{psi.p[1], P.nx, P.ny, P.nz, P.zper}, {pl ? ps_lo.p[1] : psi.p[1], P.nx, P.ny, P.nz, P.zper}, pl};
+    PertView2<T> PZ{{psi.p[2], P.nx, P.ny, P.nz, P.zper}, {pl ? ps_lo.p[2] : psi.p[2], P.nx, P.ny, P.nz, P.zper}, pl};
     auto r0 = [&](int c, int jj, int kk) -> double {
       if (P.zper) kk = wrap_idx(kk, P.nz);
       return psi0r.p[c][(jj + 1) + (long long)(kk + 1) * ny2];
     };
-    const double dpx = ((double)PX(i + 1, j, k) - (double)PX(i - 1, j, k)) * hih;
-    const double dpy = ((double)PY(i, j + 1, k) - (double)PY(i, j - 1, k) + r0(1, j + 1, k) -
+    const double dpx = (PX(i + 1, j, k) - PX(i - 1, j, k)) * hih;
+    const double dpy = (PY(i, j + 1, k) - PY(i, j - 1, k) + r0(1, j + 1, k) -
                         r0(1, j - 1, k)) * hih;
-    const double dpz = ((double)PZ(i, j, k + 1) - (double)PZ(i, j, k - 1) + r0(2, j, k + 1) -
+    const double dpz = (PZ(i, j, k + 1) - PZ(i, j, k - 1) + r0(2, j, k + 1) -
                         r0(2, j, k - 1)) * hih;
     q[10] = fmax(q[10], fabs(dpx + dpy + dpz));
     const double sxy = eta * (G[0][1] + G[1][0]);
@@ -453,11 +507,11 @@ __global__ void k_diag_finalize(const double* partials, int nblocks, double* out
 
 // <sigma_xy>(y): one block per y row, fixed-order sum over x and z.
 template <class T>
-__global__ void k_stress_profile(PhaseParams P, Comp3<T> vel, double* out) {
+__global__ void k_stress_profile(PhaseParams P, Comp3<T> vel, Comp3<T> vel_lo, double* out) {
   const int j = blockIdx.x;
   const double hih = 0.5 * P.inv_h, eta = 1.0 / P.inv_eta;
-  VelView<T> VX{vel.p[0], P.nx, P.ny, P.nz, P.zper, 0, &P};
-  VelView<T> VY{vel.p[1], P.nx, P.ny, P.nz, P.zper, 1, &P};
+  VelView<T> VX{vel.p[0], vel_lo.p[0], P.nx, P.ny, P.nz, P.zper, 0, &P};
+  VelView<T> VY{vel.p[1], vel_lo.p[1], P.nx, P.ny, P.nz, P.zper, 1, &P};
   double s = 0.0;
   const long long m = (long long)P.nx * P.nz;
   for (long long t = threadIdx.x; t < m; t += blockDim.x) {
@@ -1235,14 +1289,22 @@ void launch_velocity(Ctx& cx, const PhaseParams& P, Comp3<T> psi, Comp3<T> psi_l
   cx.after(-1);
 }
 
+void launch_velocity_dw(Ctx& cx, const PhaseParams& P, Comp3<float> psi, Comp3<float> psi_lo,
+                        Comp3<const double> v0d, Comp3<float> v, Comp3<float> v_lo) {
+  cx.before(-1);
+  k_velocity_dw<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, psi, psi_lo, v0d, v,
+                                                                        v_lo);
+  cx.after(-1);
+}
+
 template <class T>
 void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo, const T* g,
-                 const T* g_lo, Comp3<T> vel,
-                 Comp3<T> omega, Comp3<T> psi, Comp3<const double> psi0_ring,
+                 const T* g_lo, Comp3<T> vel, Comp3<T> vel_lo, Comp3<T> omega, Comp3<T> om_lo,
+                 Comp3<T> psi, Comp3<T> ps_lo, Comp3<const double> psi0_ring,
                  Comp3<const double> v0d, T* sigma_t, double* partials, int nblocks, double* out) {
   cx.before(-1);
-  k_diag<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, vel, omega, psi, psi0_ring, v0d, sigma_t,
-                                               partials);
+  k_diag<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, vel, vel_lo, omega, om_lo,
+                                               psi, ps_lo, psi0_ring, v0d, sigma_t, partials);
   cx.after(-1);
   cx.before(-1);
   k_diag_finalize<<<1, kBlock, 0, cx.stream>>>(partials, nblocks, out);
@@ -1250,9 +1312,10 @@ void launch_diag(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo, c
 }
 
 template <class T>
-void launch_stress_profile(Ctx& cx, const PhaseParams& P, Comp3<T> vel, double* out) {
+void launch_stress_profile(Ctx& cx, const PhaseParams& P, Comp3<T> vel, Comp3<T> vel_lo,
+                           double* out) {
   cx.before(-1);
-  k_stress_profile<T><<<P.ny, kBlock, 0, cx.stream>>>(P, vel, out);
+  k_stress_profile<T><<<P.ny, kBlock, 0, cx.stream>>>(P, vel, vel_lo, out);
   cx.after(-1);
 }
 
@@ -1337,10 +1400,10 @@ void launch_fill(Ctx& cx, double* x, long long n, double v) {
   template void launch_velocity<T>(Ctx&, const PhaseParams&, Comp3<T>, Comp3<T>, Comp3<T>,       \
                                    Comp3<T>);                                                     \
   template void launch_diag<T>(Ctx&, const PhaseParams&, const T*, const T*, const T*, const T*,  \
-                               Comp3<T>, Comp3<T>,                                                \
-                               Comp3<T>, Comp3<const double>, Comp3<const double>, T*, double*,   \
-                               int, double*);                                                     \
-  template void launch_stress_profile<T>(Ctx&, const PhaseParams&, Comp3<T>, double*);            \
+                               Comp3<T>, Comp3<T>, Comp3<T>, Comp3<T>, Comp3<T>, Comp3<T>,        \
+                               Comp3<const double>, Comp3<const double>, T*, double*, int,        \
+                               double*);                                                          \
+  template void launch_stress_profile<T>(Ctx&, const PhaseParams&, Comp3<T>, Comp3<T>, double*);  \
   template void launch_full_field<T>(Ctx&, const PhaseParams&, const T*, const T*, const double*,  \
                                      int, T*);                                                    \
   template void launch_scale_copy<T>(Ctx&, const T*, T*, long long, double);

@@ -47,7 +47,7 @@ class vsv_solver_params(C.Structure):
                 ("fixed_cycles", C.c_int), ("check_every", C.c_int), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("max_levels", C.c_int), ("coarse_sweeps", C.c_int),
                 ("omega_sor", C.c_double), ("variant", C.c_int), ("extrapolate", C.c_int),
-                ("fixed_cycles_psi", C.c_int)]
+                ("fixed_cycles_psi", C.c_int), ("omega_mg", C.c_double)]
 
 
 class vsv_bc(C.Structure):

@@ -1,9 +1,10 @@
 """The Couette workload at its full size, 512 x 256 x 256, over 500 steps
-(vesicle of reduced volume 0.9, kappa = 1, walls at +-0.05, eps = 1.5),
-mixed path in the schedule bench.py times: the wall-normal profile of the
-mean shear stress <sigma_xy>(y), the hydrodynamic resistance (dissipation
-relative to the body-free flow) and the shape diagnostics, against the
-plain FP64 path run with the same schedule."""
+(vesicle of reduced volume 0.9, kappa = 1, walls at +-0.05, eps = 1.5).
+The mixed path in the schedule bench.py times is compared along the run
+with the FP64 GPU path solved to a relative residual of 1e-12 every step:
+every field at steps 10, 100 and 500, and at the end the wall-normal profile
+of the mean shear stress <sigma_xy>(y), the hydrodynamic resistance
+(dissipation relative to the body-free flow) and the shape diagnostics."""
 import numpy as np
 import pytest
 
@@ -24,40 +25,44 @@ def V():
     return vsv
 
 
-def test_500_steps_stress_profile_and_resistance(V):
+def test_500_steps_against_converged_fp64(V):
     import torch
     import bench
     w = inputs.vesicle_couette_512x256x256()
-    out = {}
-    for name, prec in (("mixed", V.VSV_MIXED), ("fp64", V.VSV_FP64)):
-        sim = bench.make_sim(w, prec, 4, 1)
-        sim.step(w.nsteps, w.dt)
-        d = sim.diagnostics()
-        out[name] = {"diag": d, "profile": sim.stress_profile(),
-                     "phi": sim.field(V.VSV_FIELD_PHI, np.float64, on_device=True).cpu(),
-                     "vel": torch.stack([sim.field(V.VSV_FIELD_VEL_X + c, np.float64,
-                                                   on_device=True).cpu() for c in range(3)])}
-        sim.close()
-        torch.cuda.empty_cache()
-    m, f = out["mixed"], out["fp64"]
-    prof_rel = float(np.linalg.norm(m["profile"] - f["profile"]) / np.linalg.norm(f["profile"]))
-    res_rel = abs(m["diag"]["resistance_rel"] - f["diag"]["resistance_rel"]) / \
-        abs(f["diag"]["resistance_rel"])
-    phi_rel = float(torch.linalg.vector_norm(m["phi"] - f["phi"]) / torch.linalg.vector_norm(f["phi"]))
-    vel_rel = float(torch.linalg.vector_norm(m["vel"] - f["vel"]) / torch.linalg.vector_norm(f["vel"]))
+    mixed = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, 1)
+    fp64 = bench.make_sim(w, V.VSV_FP64, 0)        # every solve to relative residual 1e-12
+    done, errs = 0, {}
+    for mark in (10, 100, w.nsteps):
+        mixed.step(mark - done, w.dt)
+        fp64.step(mark - done, w.dt)
+        done = mark
+        errs[mark] = bench.field_errors(mixed, fp64, V, torch)
+        print(f"step {mark}:", {k: float("%.3g" % v) for k, v in errs[mark].items()})
+    dm, df = mixed.diagnostics(), fp64.diagnostics()
+    pm, pf = mixed.stress_profile(), fp64.stress_profile()
+    mixed.close()
+    fp64.close()
+    prof_rel = float(np.linalg.norm(pm - pf) / np.linalg.norm(pf))
+    res_rel = abs(dm["resistance_rel"] - df["resistance_rel"]) / abs(df["resistance_rel"])
+    vr_rel = abs(dm["reduced_volume"] - df["reduced_volume"]) / df["reduced_volume"]
     keys = ("time", "reduced_volume", "energy", "dissipation", "dissipation0", "resistance_rel",
-            "max_div_v")
-    print("Couette 512x256x256, 500 steps:",
-          {k: (m["diag"][k], f["diag"][k]) for k in keys})
-    print("stress profile mixed vs FP64 %.3e, resistance %.3e, phi %.3e, velocity %.3e" %
-          (prof_rel, res_rel, phi_rel, vel_rel))
+            "max_div_v", "last_cycles_omega", "last_cycles_psi")
+    print("Couette 512x256x256, 500 steps (mixed, FP64):", {k: (dm[k], df[k]) for k in keys})
+    print("stress profile %.3e, resistance %.3e, reduced volume %.3e (relative)" %
+          (prof_rel, res_rel, vr_rel))
     ny = w.ny
     print("<sigma_xy>(y) at y = 0, ny/4, ny/2, 3ny/4, ny-1:",
-          [float(m["profile"][j]) for j in (0, ny // 4, ny // 2, 3 * ny // 4, ny - 1)])
-    assert np.all(np.isfinite(m["profile"])) and np.isfinite(m["diag"]["resistance_rel"])
-    # both paths take the same 4 V-cycles per solve; they differ by the FP32
-    # arithmetic of the mixed path only
-    assert phi_rel <= 1e-6 and vel_rel <= 1e-5, (phi_rel, vel_rel)
-    assert prof_rel <= 1e-4 and res_rel <= 1e-4, (prof_rel, res_rel)
+          [float(pm[j]) for j in (0, ny // 4, ny // 2, 3 * ny // 4, ny - 1)])
+    assert np.all(np.isfinite(pm)) and np.isfinite(dm["resistance_rel"])
+    # the bar on velocity and phi, at every checkpoint; the other fields
+    # are held to the same bar (measured on GB300, largest over steps 10,
+    # 100 and 500: phi 1.3e-11, velocity 5.5e-8, mu 8.4e-8, omega 9.6e-8,
+    # psi 4.5e-8)
+    for mark, e in errs.items():
+        for k in ("phi", "vel", "mu", "omega", "psi"):
+            assert e[k] <= 1e-6, (mark, k, e[k])
+    # stress profile and resistance at step 500, about five times what
+    # GB300 gave (profile 1.5e-8, resistance 3.6e-8, reduced volume 7e-13)
+    assert prof_rel <= 1e-7 and res_rel <= 2e-7 and vr_rel <= 1e-10, (prof_rel, res_rel, vr_rel)
     # the body raises the dissipation above that of the plain Couette flow
-    assert m["diag"]["resistance_rel"] > 0
+    assert dm["resistance_rel"] > 0

@@ -1,7 +1,8 @@
 """The single-vesicle duct workload at 256 x 128 x 128 (x the flow axis):
 Helfrich vesicle of reduced volume 0.8 with area and volume penalties in
 Poiseuille flow, 2000 steps of dt = 1e-4.  The mixed path in the schedule
-bench.py times (4 fixed V(2,2)-cycles per solve, extrapolated guess) is
+bench.py times (bench.BENCH_CYCLES fixed V(2,2)-cycles per solve with
+over-relaxed smoothing, extrapolated guess) is
 compared along the run with the FP64 GPU path solved to a relative residual
 of 1e-12 each step; at the end one step is checked cell by cell against the
 oracle's operators on sampled windows (the oracle cannot run 2000 steps of
@@ -34,7 +35,7 @@ def test_mixed_against_fp64_over_2000_steps_and_oracle_sample(V):
     import torch
     import bench
     w = inputs.vesicle_poiseuille_256x128x128()
-    mixed = bench.make_sim(w, V.VSV_MIXED, 4, 1)
+    mixed = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, 1)
     fp64 = bench.make_sim(w, V.VSV_FP64, 0)
     sp = fp64.solver_params()
     sp.tol = 1e-12
