@@ -297,14 +297,20 @@ vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes);
  * allocate device memory -- a plugin whose host application owns every
  * device allocation, or a latency-critical loop that cannot afford the
  * device-wide synchronisation a cudaMalloc / cudaFree may cause.
- * It computes what vsv_get_diagnostics reports as volume and area
- * (V = h^3/2 sum (1 - phi); A of SM eq. 32 with central differences,
- * periodic x, mirror y, mirror or periodic z) with its scratch in a
- * fixed 1 MiB file-scope device array of per-row partial sums.
+ * It computes the two numbers vsv_get_diagnostics reports as volume and
+ * area: V = h^3/2 sum (1 - phi), and A = h^3 sum of the area density
+ * 3/(2 sqrt2) [eps/2 |grad phi|^2 + (phi^2 - 1)^2 / (4 eps)] with central
+ * differences (periodic x, mirror y, mirror or periodic z), with its
+ * scratch in a fixed 1 MiB file-scope device array of per-row partial sums.
  *   phi: device pointer to an FP64 [nz][ny][nx] field (read only).
  *   out: device pointer to two doubles, written V then A.
  *   cuda_stream: cudaStream_t to run on (NULL = legacy default stream); the
  *   call is asynchronous on it.
+ * phi and out must be device (or managed) memory of the current device, and
+ * the stream a stream of that device; otherwise VSV_EINVAL and nothing is
+ * launched.  An error already pending from earlier work on this thread
+ * (cudaPeekAtLastError) makes the call return VSV_ECUDA without launching
+ * and without clearing it.
  * Limit: ny * nz <= 65536 (y, z) rows; larger shapes return VSV_EINVAL and
  * launch nothing.  The first call on a device looks up the array's device
  * address while that device is current; make that first call before any

@@ -2007,14 +2007,19 @@ vsv_status tape_save(vsv_tape* t, int step) {
   vsv_grid* g = t->g;
   char* dst = nullptr;
   CK(cudaMalloc((void**)&dst, t->ck_bytes));
-  t->dev_bytes += t->ck_bytes;
+  // a failed copy frees the new slot before returning (not yet on the tape)
+  auto copy = [&](void* to, const void* from, size_t n) -> cudaError_t {
+    const cudaError_t e = cudaMemcpyAsync(to, from, n, cudaMemcpyDeviceToDevice, g->cx.stream);
+    if (e != cudaSuccess) cudaFree(dst);
+    return e;
+  };
   size_t off = 0;
   for (auto& f : state_fields(g)) {
-    CK(cudaMemcpyAsync(dst + off, f.first, f.second, cudaMemcpyDeviceToDevice, g->cx.stream));
+    CK(copy(dst + off, f.first, f.second));
     off += f.second;
   }
-  CK(cudaMemcpyAsync(dst + off, &g->S->V0, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
-                     g->cx.stream));   // V0, A0 (adjacent in Scalars)
+  CK(copy(dst + off, &g->S->V0, 2 * sizeof(double)));   // V0, A0 (adjacent in Scalars)
+  t->dev_bytes += t->ck_bytes;
   StateHeader hd{};
   hd.time = g->time;
   hd.steps = g->steps;

@@ -85,6 +85,18 @@ __global__ void k_static_total(const double* rows, int nrows, long long ncells, 
 std::mutex g_static_mutex;
 double* g_static_ptr[kStaticMaxDevices] = {};
 
+// True if p is device (or managed) memory of device dev: a pointer into
+// another GPU's memory, or host memory, would make the kernels read through
+// an address this device may not map.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // the query's own error (an unknown pointer), not a launch's
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 
 }  // namespace vsv
@@ -95,8 +107,18 @@ extern "C" vsv_status vsv_volume_area_static(const double* phi, int nx, int ny, 
   using namespace vsv;
   if (!phi || !out || nx < 1 || ny < 1 || nz < 1 || !(h > 0) || !(eps > 0)) return VSV_EINVAL;
   if ((long long)ny * nz > kStaticMaxRows) return VSV_EINVAL;   // beyond the static scratch
+  // an error left pending by earlier work is reported, not cleared: it
+  // belongs to its owner
+  if (cudaPeekAtLastError() != cudaSuccess) return VSV_ECUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return VSV_ECUDA;
+  if (!on_device(phi, dev) || !on_device(out, dev)) return VSV_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (s) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return VSV_ECUDA;
+    if (sdev != dev) return VSV_EINVAL;
+  }
   double* rows = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mutex);
@@ -109,9 +131,9 @@ extern "C" vsv_status vsv_volume_area_static(const double* phi, int nx, int ny, 
     }
     rows = g_static_ptr[dev];
   }
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   const int nrows = ny * nz;
   k_static_rows<<<nrows, kBlock, 0, s>>>(phi, nx, ny, nz, z_periodic ? 1 : 0, 1.0 / h, eps, rows);
+  if (cudaGetLastError() != cudaSuccess) return VSV_ECUDA;
   k_static_total<<<1, kBlock, 0, s>>>(rows, nrows, (long long)nx * ny * nz, h * h * h, out);
   return cudaGetLastError() == cudaSuccess ? VSV_OK : VSV_ECUDA;
 }

@@ -67,3 +67,22 @@ def test_no_alloc_rejects_shapes_beyond_its_scratch(V):
     st = V.vsv_volume_area_static(dummy.data_ptr(), 2, 300, 300, 1.0, 1.0, 0, dummy.data_ptr(),
                                   torch.cuda.current_stream().cuda_stream)
     assert st == V.VSV_EINVAL
+
+
+def test_no_alloc_rejects_host_memory(V):
+    """phi and out must be device memory of the current device: a host
+    buffer is refused before anything is launched (the kernels never see
+    it), and a valid call afterwards still matches."""
+    import torch
+    host = torch.zeros(16 * 12 * 12, dtype=torch.float64)
+    dev = torch.zeros(2, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert V.vsv_volume_area_static(host.data_ptr(), 16, 12, 12, 1.0, 1.0, 0, dev.data_ptr(),
+                                    stream) == V.VSV_EINVAL
+    phi = torch.ones(16 * 12 * 12, dtype=torch.float64, device="cuda")
+    assert V.vsv_volume_area_static(phi.data_ptr(), 16, 12, 12, 1.0, 1.0, 0, host.data_ptr(),
+                                    stream) == V.VSV_EINVAL
+    w = inputs.droplet_duct(nx=16, ny=12, nz=12, radius=3.5)
+    v_ref, a_ref = _reference(V, w)
+    v, a = _static(V, w)
+    assert abs(v - v_ref) <= TOL * abs(v_ref) and abs(a - a_ref) <= TOL * abs(a_ref)
