@@ -142,13 +142,11 @@ def job_throughput(world_size, cells_per_rank, steps, ms_max):
 GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
          2: "extrapolated guess 3x^n - 3x^(n-1) + x^(n-2)"}
 
-# DRAM traffic of the finest-level fused sweeps per launch, averaged over the
-# four sweeps of a correction (zero input, plain, plain, iterate update):
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of all 888 such launches
-# in one launch-list capture of this benchmark at 512 x 256 x 256 (one ncu
-# pass), 1.4038 GB per launch, per cell and component here.  To be retaken
-# (and set to None meanwhile) whenever k_rbgs_fused changes.
-FUSED_SWEEP_TRAFFIC_PER_CELL = 1.4038e9 / (512 * 256 * 256 * 3)
+# DRAM traffic of the finest-level fused sweeps per launch and cell
+# (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
+# kernel), or None while no capture of the current kernel build exists.
+FUSED_SWEEP_TRAFFIC_PER_CELL = None
+FUSED_SWEEP_TRAFFIC_SOURCE = "not yet captured for the current kernel build"
 
 # steps per captured graph (the library's replay length)
 GRAPH_STEPS = 6
@@ -314,7 +312,7 @@ def run_gpu(args, ws, rank, local):
                        "avg_launch_us": round(per_launch_s * 1e6, 2),
                        "traffic": (None if FUSED_SWEEP_TRAFFIC_PER_CELL is None else
                                    round(FUSED_SWEEP_TRAFFIC_PER_CELL * N * 3)),
-                       "traffic_source": "ncu launch list of this benchmark at 512x256x256"}
+                       "traffic_source": FUSED_SWEEP_TRAFFIC_SOURCE}
     out["clocks"] = clk.summary()
     # plain FP64 step with the same schedule, and the accuracy of mixed vs FP64
     if not args.no_fp64:

@@ -178,6 +178,15 @@ typedef struct {
                              the error about 3x more than with 1.  It
                              changes the iterate, not the converged answer.
                              Outside [0, 2): VSV_EINVAL. */
+  int lower_cycle;        /* the levels below the finest of a V-cycle (variant
+                             0 only): 0 (default) level by level; 1 in one
+                             cooperative launch (grid-wide red-black sweeps
+                             and transfers separated by bounded grid
+                             barriers, then the one-CTA coarse cycle) where
+                             those levels do not fit one CTA's shared memory.
+                             Bit-identical results either way; on GB300 the
+                             single launch measured slower at every size
+                             tried.  Outside 0..1: VSV_EINVAL. */
 } vsv_solver_params;
 
 /* Per-axis boundary of a standalone Poisson problem: periodic (1) or zero
@@ -320,8 +329,25 @@ vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes);
 vsv_status vsv_volume_area_static(const double* phi, int nx, int ny, int nz, double h, double eps,
                                   int z_periodic, double* out, void* cuda_stream);
 
-/* Synchronise the stream and report deferred kernel errors / flags. */
+/* Synchronise the stream and report deferred kernel errors / flags: a
+ * non-finite phi (VSV_ENONFINITE), or a grid barrier of the single-launch
+ * lower V-cycle whose wait ran out (VSV_ECUDA; every such wait gives up
+ * after about a second, so no launch can hang; the flag stays set). */
 vsv_status vsv_check(vsv_grid* g);
+
+/* Check of the bounded grid barrier that the single-launch lower V-cycle
+ * uses (the paper has no counterpart; this serves tests).  Runs `rounds`
+ * barriers of a cooperative launch of `blocks` CTAs on the grid's stream,
+ * each barrier expecting `extra_arrivals` more CTAs than the launch has:
+ * with 0 every barrier completes; with more, arrivals that never come, so
+ * every wait runs out after limit_ms milliseconds and the kernel returns.
+ * Synchronises.  Returns VSV_OK when all barriers completed, VSV_ECUDA (the
+ * timeout message) when a wait ran out, VSV_EINVAL for bad arguments
+ * (blocks < 1 or more than can be co-resident, rounds < 1, limit_ms <= 0
+ * or above 10000).  It uses the grid's barrier counter and a flag bit it
+ * clears again before returning; it touches no field. */
+vsv_status vsv_barrier_check(vsv_grid* g, int blocks, int rounds, int extra_arrivals,
+                             double limit_ms);
 
 /* Message of the last failure on this handle ("" if none); the pointer stays
  * valid until the next call on the handle. */

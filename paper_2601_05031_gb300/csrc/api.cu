@@ -90,6 +90,7 @@ struct vsv_grid {
   std::vector<Level> omega_levels;
   double omega_dt = 0.0;
   int* flag_host = nullptr;        // pinned copy of the device non-finite flag
+  unsigned* bar_count = nullptr;   // arrival counter of the persistent V-cycle's grid barriers
   cudaEvent_t flag_event = nullptr;
   bool flag_pending = false;
   int last_cycles[2] = {0, 0};
@@ -214,6 +215,7 @@ size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
   d = df(kDiagQ); if (g) g->dout = d;
   d = df(ny); if (g) g->profile = d;
   d = df(8); if (g) g->scratch1 = d;
+  p = take(sizeof(unsigned)); if (g) g->bar_count = (unsigned*)p;
   return off;
 }
 
@@ -228,6 +230,16 @@ vsv_status fail(vsv_grid* g, vsv_status s, const char* fmt, const char* detail =
     g->err = buf;
   }
   return s;
+}
+
+// Status of the device flag word: bit 1 non-finite phi, bit kSyncTimeout a
+// grid barrier of the persistent V-cycle whose wait ran out (its
+// correction is then unusable; the flag stays set).
+vsv_status flag_status(vsv_grid* g, int flag) {
+  if (flag & 1) return fail(g, VSV_ENONFINITE, "non-finite phi%s");
+  if (flag & kSyncTimeout)
+    return fail(g, VSV_ECUDA, "a grid barrier of the persistent multigrid launch ran out of time%s");
+  return VSV_OK;
 }
 
 #define CK(call)                                                                      \
@@ -417,6 +429,74 @@ int coarsest_sweeps(const Level& L, int cap) {
   return std::min(cap, std::max(4, 2 * m));
 }
 
+// Levels m .. last of hierarchy lv as a one-CTA coarse cycle plan (shared
+// memory offsets of every level's (e, r) pair); false if they do not fit.
+bool coarse_plan(const vsv_grid* g, const std::vector<Level>& lv, int m, CoarseCycle* CC,
+                 size_t elem) {
+  *CC = CoarseCycle{};
+  CC->first = m;
+  CC->last = (int)lv.size() - 1;
+  CC->nu1 = g->sol.nu1;
+  CC->nu2 = g->sol.nu2;
+  CC->omega = mg_weight(g);
+  CC->coarse_sweeps = coarsest_sweeps(lv.back(), g->sol.coarse_sweeps);
+  long long off = 0;
+  for (int q = m; q <= CC->last; ++q) {
+    CC->lv[q] = lv[q];
+    CC->h2[q] = 1.0 / lv[q].inv_h2;
+    CC->off[q] = off;
+    off += 2 * lv[q].cells();
+  }
+  CC->total = off;
+  return (size_t)off * elem <= kCoarseCycleSmem;
+}
+
+// Should the levels from l down run as one cooperative launch?  Only when
+// the solver asks for it (lower_cycle = 1) and where the levels do not all
+// fit the one-CTA coarse cycle (which is then the cheaper single launch).
+// It is not the default: measured on GB300 it is slower than the
+// level-by-level kernels at every size tried (512 x 256 x 256: 16.7 ms per
+// step from the 4.2 M-cell level, 15.0 from the 0.5 M-cell level, against
+// 14.7 level by level; 256 x 128 x 128: 3.06 against 2.75 ms), because
+// per-colour grid-wide sweeps move twice the bytes of the fused sweep and
+// its grid barriers (about 1.45 us each) do not beat the launches they
+// replace.
+bool lower_cycle_wanted(const vsv_grid* g, const std::vector<Level>& lv, int l) {
+  if (g->sol.lower_cycle != 1 || l + 1 >= (int)lv.size()) return false;
+  CoarseCycle CC;
+  return !coarse_plan(g, lv, l, &CC, g->prec == VSV_FP64 ? 8 : 4);
+}
+
+template <class T>
+bool run_lower_cycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> E, Comp3<T> R,
+                     int ncomp) {
+  LowerCycle<T> P{};
+  P.first = l;
+  P.last = (int)lv.size() - 1;
+  P.ncomp = ncomp;
+  P.nu1 = g->sol.nu1;
+  P.nu2 = g->sol.nu2;
+  P.coarse_sweeps = coarsest_sweeps(lv.back(), g->sol.coarse_sweeps);
+  P.omega = mg_weight(g);
+  for (int q = l; q <= P.last; ++q) {
+    P.lv[q] = lv[q];
+    P.h2[q] = 1.0 / lv[q].inv_h2;
+    for (int c = 0; c < 3; ++c) {
+      P.e[q][c] = q == l ? E.p[c] : (T*)g->mg_e[q][c];
+      P.r[q][c] = q == l ? R.p[c] : (T*)g->mg_r[q][c];
+    }
+  }
+  // the one-CTA part: the first level below l from which the rest fits
+  P.cc = P.last + 1;
+  for (int m = l + 1; m <= P.last; ++m)
+    if (coarse_plan(g, lv, m, &P.cc_plan, sizeof(T))) {
+      P.cc = m;
+      break;
+    }
+  P.bar = GridBarrier{g->bar_count, &g->S->nonfinite, kSyncLimitNs, 0u};
+  return launch_lower_vcycle<T>(g->cx, P);
+}
+
 // One V-cycle from level l for L x = R.  uh / ul as in smooth(): returns
 // true if the correction was added to that iterate by the last sweep.
 template <class T>
@@ -445,23 +525,16 @@ bool vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
     }
     return false;
   }
+  if (l > 0 && x_zero && g->sol.variant == 0 && R.beta == (T)1 && !R.S[0] && !R.S[1] && !R.S[2] &&
+      lower_cycle_wanted(g, lv, l)) {
+    // the levels from l down in one cooperative launch
+    Comp3<T> RR{{(T*)R.B[0], (T*)R.B[1], (T*)R.B[2]}};
+    if (run_lower_cycle<T>(g, lv, l, X, RR, ncomp)) return false;
+  }
   if (l > 0 && x_zero && g->sol.variant != 1 && R.beta == (T)1 && !R.S[0] && !R.S[1] && !R.S[2]) {
     // the remaining levels fit in one CTA's shared memory: one launch
-    CoarseCycle CC{};
-    CC.first = l;
-    CC.last = (int)lv.size() - 1;
-    CC.nu1 = g->sol.nu1;
-    CC.nu2 = g->sol.nu2;
-    CC.omega = mg_weight(g);
-    CC.coarse_sweeps = coarsest_sweeps(lv.back(), g->sol.coarse_sweeps);
-    long long off = 0;
-    for (int q = l; q <= CC.last; ++q) {
-      CC.lv[q] = lv[q];
-      CC.h2[q] = 1.0 / lv[q].inv_h2;
-      CC.off[q] = off;
-      off += 2 * lv[q].cells();
-    }
-    CC.total = off;
+    CoarseCycle CC;
+    coarse_plan(g, lv, l, &CC, sizeof(T));
     Comp3<T> RR{{(T*)R.B[0], (T*)R.B[1], (T*)R.B[2]}};
     if (launch_coarse_vcycle<T>(g->cx, CC, X, RR, ncomp)) return false;
   }
@@ -1144,6 +1217,7 @@ void default_solver(vsv_solver_params* s, int prec) {
   s->extrapolate = 1;
   s->fixed_cycles_psi = 0;
   s->omega_mg = kDefaultMgWeight;
+  s->lower_cycle = 0;
 }
 
 }  // namespace
@@ -1249,7 +1323,8 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
   if (sp->nu1 < 0 || sp->nu2 < 0 || sp->nu1 + sp->nu2 < 1 || sp->coarse_sweeps < 1 ||
       sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->fixed_cycles_psi < 0 || sp->max_levels < 1 || !(sp->tol >= 0) ||
       sp->variant < 0 || sp->variant > 2 || sp->extrapolate < 0 || sp->extrapolate > 2 ||
-      !(sp->omega_mg >= 0.0 && sp->omega_mg < 2.0))
+      !(sp->omega_mg >= 0.0 && sp->omega_mg < 2.0) || sp->lower_cycle < 0 ||
+      sp->lower_cycle > 1)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
   g->cx.tiled = sp->variant != 1;
@@ -1321,7 +1396,7 @@ vsv_status vsv_step(vsv_grid* g, int nsteps, double dt) {
   // flag of an earlier call, read without waiting if its copy has landed
   if (g->flag_pending && cudaEventQuery(g->flag_event) == cudaSuccess) {
     g->flag_pending = false;
-    if (*g->flag_host) return fail(g, VSV_ENONFINITE, "non-finite phi%s");
+    if (*g->flag_host) return flag_status(g, *g->flag_host);
   }
   for (int s = 0; s < nsteps; ++s) {
     vsv_status st = g->prec == VSV_FP64 ? step_impl<double>(g, dt) : step_impl<float>(g, dt);
@@ -1850,7 +1925,28 @@ vsv_status vsv_check(vsv_grid* g) {
   CKL();
   int flag = 0;
   CK(cudaMemcpy(&flag, &g->S->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
-  if (flag) return fail(g, VSV_ENONFINITE, "non-finite phi%s");
+  if (flag) return flag_status(g, flag);
+  return VSV_OK;
+}
+
+vsv_status vsv_barrier_check(vsv_grid* g, int blocks, int rounds, int extra_arrivals,
+                             double limit_ms) {
+  if (!g || blocks < 1 || rounds < 1 || extra_arrivals < 0 || !(limit_ms > 0) || limit_ms > 1e4)
+    return VSV_EINVAL;
+  if (blocks > barrier_probe_max_blocks(g->cx.sms))
+    return fail(g, VSV_EINVAL, "more CTAs than can be co-resident%s");
+  const GridBarrier B{g->bar_count, &g->S->nonfinite,
+                      (unsigned long long)(limit_ms * 1e6), (unsigned)extra_arrivals};
+  if (!launch_barrier_probe(g->cx.stream, B, blocks, rounds))
+    return fail(g, VSV_ECUDA, "barrier check launch failed%s");
+  CK(cudaStreamSynchronize(g->cx.stream));
+  int flag = 0;
+  CK(cudaMemcpy(&flag, &g->S->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag & kSyncTimeout) {
+    const int cleared = flag & ~kSyncTimeout;
+    CK(cudaMemcpy(&g->S->nonfinite, &cleared, sizeof(int), cudaMemcpyHostToDevice));
+    return flag_status(g, kSyncTimeout);
+  }
   return VSV_OK;
 }
 

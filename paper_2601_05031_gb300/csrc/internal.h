@@ -132,6 +132,41 @@ constexpr size_t kCoarseCycleSmem = 200 * 1024;
 template <class T>
 bool launch_coarse_vcycle(Ctx& cx, const CoarseCycle& CC, Comp3<T> E, Comp3<T> R, int ncomp);
 
+// Bounded grid-wide barrier of a cooperative launch.  count: arrival
+// counter in device memory, zeroed before each launch; status: device flag
+// word, bit kSyncTimeout set when a CTA's wait exceeded limit_ns
+// nanoseconds (the global timer); extra: arrivals expected beyond the
+// grid's CTAs per barrier (0; a test sets it to make the wait run out).
+constexpr int kSyncTimeout = 2;
+constexpr unsigned long long kSyncLimitNs = 1000000000ull;   // 1 s
+struct GridBarrier {
+  unsigned* count;
+  int* status;
+  unsigned long long limit_ns;
+  unsigned extra;
+};
+
+// The levels first .. last of a V-cycle in one cooperative launch (mg.cu):
+// levels first .. cc-1 grid-wide, levels cc .. last (cc <= last) as the
+// one-CTA coarse cycle cc_plan.  e[first] <- correction for rhs r[first].
+template <class T>
+struct LowerCycle {
+  Level lv[kMaxLevels];
+  double h2[kMaxLevels];
+  T* e[kMaxLevels][3];
+  T* r[kMaxLevels][3];
+  int first, cc, last;
+  int ncomp, nu1, nu2, coarse_sweeps;
+  double omega;
+  CoarseCycle cc_plan;
+  GridBarrier bar;
+};
+template <class T>
+bool launch_lower_vcycle(Ctx& cx, const LowerCycle<T>& P);
+// `rounds` bounded barriers of `blocks` co-resident CTAs (tests of the bound)
+bool launch_barrier_probe(cudaStream_t s, GridBarrier B, int blocks, int rounds);
+int barrier_probe_max_blocks(int sms);
+
 // outer defect correction with double-word iterates (dc.cu)
 void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
                       Comp3<float> BL, Comp3<float> OUT, int ncomp, double* partials, int nblocks);

@@ -594,12 +594,11 @@ __device__ void cv_prolong(const Level& F, const Level& C, T* e, const T* ec) {
   __syncthreads();
 }
 
+// The lower V-cycle of one component in one CTA: rhs rr (level CC.first,
+// global memory) -> correction e_out, every level in shared memory `base`.
 template <class T>
-__global__ void __launch_bounds__(1024)
-k_coarse_vcycle(const __grid_constant__ CoarseCycle CC, Comp3<T> E, Comp3<T> RR) {
-  extern __shared__ unsigned char smem_cv[];
-  T* base = reinterpret_cast<T*>(smem_cv);
-  const int comp = blockIdx.x;
+__device__ void coarse_vcycle_cta(const CoarseCycle& CC, const T* __restrict__ rr,
+                                  T* __restrict__ e_out, T* base) {
   const int f = CC.first, l_last = CC.last;
   // (e, r) of level l in shared memory; CC is a grid-constant parameter, so
   // its tables are read in place at run-time indices (no local copies)
@@ -607,7 +606,7 @@ k_coarse_vcycle(const __grid_constant__ CoarseCycle CC, Comp3<T> E, Comp3<T> RR)
   auto r = [&](int l) { return base + CC.off[l] + CC.lv[l].cells(); };
   const int n0 = (int)CC.lv[f].cells();
   for (int t = threadIdx.x; t < n0; t += blockDim.x) {
-    r(f)[t] = RR.at(comp)[t];
+    r(f)[t] = rr[t];
     e(f)[t] = (T)0;
   }
   __syncthreads();
@@ -625,7 +624,15 @@ k_coarse_vcycle(const __grid_constant__ CoarseCycle CC, Comp3<T> E, Comp3<T> RR)
     cv_sweep<T>(CC.lv[l], e(l), r(l), CC.nu2, (T)CC.h2[l], (T)CC.omega);
   }
   const T* e0 = e(f);
-  for (int t = threadIdx.x; t < n0; t += blockDim.x) E.at(comp)[t] = e0[t];
+  for (int t = threadIdx.x; t < n0; t += blockDim.x) e_out[t] = e0[t];
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024)
+k_coarse_vcycle(const __grid_constant__ CoarseCycle CC, Comp3<T> E, Comp3<T> RR) {
+  extern __shared__ unsigned char smem_cv[];
+  const int comp = blockIdx.x;
+  coarse_vcycle_cta<T>(CC, RR.at(comp), E.at(comp), reinterpret_cast<T*>(smem_cv));
 }
 
 template <class T>
@@ -641,6 +648,320 @@ bool launch_coarse_vcycle(Ctx& cx, const CoarseCycle& CC, Comp3<T> E, Comp3<T> R
   // r of the first level read, e written; the rest stays in shared memory
   cx.after(VSV_KCLASS_SMOOTH, 2.0 * (double)sizeof(T) * (double)CC.lv[CC.first].cells() * ncomp);
   return true;
+}
+
+// ---------------------------------------------------------------- persistent lower V-cycle
+// The levels below the finest fit in L2 and are bound by launch and
+// barrier latency when run level by level (dozens of launches of a few to
+// tens of microseconds each per V-cycle).  One cooperative launch runs them
+// instead: every CTA of the grid (all co-resident) sweeps, restricts and
+// prolongs levels first .. cc-1 with grid-stride loops, separated by grid
+// barriers, and the levels cc .. last run as the one-CTA coarse cycle above
+// (CTAs 0 .. ncomp-1, one component each) while the others wait.  Every
+// operation is the per-colour reference kernels' arithmetic (sum_nb, relax,
+// resid_plain, prolong_children / interp_axis), so the result is bit for
+// bit that of the level-by-level V-cycle.
+
+// Cells (a, j, k, comp) of a [ncomp][nz][ny][na] index space visited by a
+// grid-stride loop: the flat index advances by the total thread count with
+// carries instead of divisions.
+struct StrideWalk {
+  int a, j, k, c;
+  int sa, sj, sk, sc;
+  int na, ny, nz;
+  __device__ __forceinline__ void init(long long t0, long long stride, int na_, int ny_, int nz_) {
+    na = na_; ny = ny_; nz = nz_;
+    long long q = t0;
+    a = (int)(q % na); q /= na; j = (int)(q % ny); q /= ny; k = (int)(q % nz); c = (int)(q / nz);
+    q = stride;
+    sa = (int)(q % na); q /= na; sj = (int)(q % ny); q /= ny; sk = (int)(q % nz);
+    sc = (int)(q / nz);
+  }
+  __device__ __forceinline__ void next() {
+    a += sa;
+    int cj = sj;
+    if (a >= na) { a -= na; ++cj; }
+    j += cj;
+    int ck = sk;
+    if (j >= ny) { j -= ny; ++ck; }
+    k += ck;
+    int cc = sc;
+    if (k >= nz) { k -= nz; ++cc; }
+    c += cc;
+  }
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded grid barrier (see GridBarrier).  Arrivals count up monotonically
+// from zero (the host zeroes the counter before each launch), so barrier n
+// waits until n * (gridDim.x + extra) arrivals.  Returns false when the
+// wait ran out (bit kSyncTimeout of *status set, by this CTA or another);
+// the caller then leaves the kernel.
+__device__ __forceinline__ bool grid_sync(const GridBarrier& B, unsigned& epoch) {
+  __shared__ int ok_s;
+  __syncthreads();
+  ++epoch;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();                                    // publish this CTA's writes
+    atomicAdd(B.count, 1u);
+    const unsigned target = epoch * (gridDim.x + B.extra);
+    const volatile unsigned* vc = B.count;
+    const volatile int* vs = B.status;
+    const unsigned long long t0 = global_ns();
+    while (*vc < target) {
+      if (*vs & kSyncTimeout) { ok = 0; break; }
+      if (global_ns() - t0 > B.limit_ns) {
+        atomicOr(B.status, kSyncTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();                                    // see the other CTAs' writes
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Number of Dirichlet ghosts among the 7-point neighbours of (i, j, k).
+__device__ __forceinline__ int wall_count(const Level& L, int i, int j, int k) {
+  int n = 0;
+  if (L.act[0] && !L.per[0]) n += (i == 0) + (i == L.n[0] - 1);
+  if (L.act[1] && !L.per[1]) n += (j == 0) + (j == L.n[1] - 1);
+  if (L.act[2] && !L.per[2]) n += (k == 0) + (k == L.n[2] - 1);
+  return n;
+}
+
+// One colour of a red-black sweep of level l, every component.  first:
+// e is not yet initialised (a correction from zero): the red cells take
+// their value from the rhs alone and the black cells are set to zero, as
+// zeroing e and sweeping its red cells does.
+template <class T>
+__device__ void lc_sweep(const LowerCycle<T>& P, int l, int color, bool first, T omega) {
+  const Level& L = P.lv[l];
+  const int nx = L.n[0], nxh = (nx + 1) >> 1;
+  const T h2 = (T)P.h2[l];
+  StrideWalk w;
+  w.init((long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, nxh,
+         L.n[1], L.n[2]);
+  for (; w.c < P.ncomp; w.next()) {
+    T* __restrict__ x = P.e[l][w.c];
+    const T* __restrict__ b = P.r[l][w.c];
+    const int red = 2 * w.a + ((w.j + w.k + color) & 1);
+    const long long row = lin(0, w.j, w.k, nx, L.n[1]);
+    if (first) {
+      // color is 0 here: the pair (2a, 2a + 1) holds one red and one black cell
+      const int blk = red ^ 1;
+      if (red < nx) {
+        const long long c = row + red;
+        const T gs = ((T)0 - b[c] * h2) * lv_rc<T>(L, wall_count(L, red, w.j, w.k));
+        x[c] = relax((T)0, gs, omega);
+      }
+      if (blk < nx) x[row + blk] = (T)0;
+      continue;
+    }
+    if (red >= nx) continue;
+    const long long c = row + red;
+    int nwall;
+    const T sn = sum_nb(x, L, red, w.j, w.k, c, nwall);
+    const T gs = (sn - b[c] * h2) * lv_rc<T>(L, nwall);
+    x[c] = relax(x[c], gs, omega);
+  }
+}
+
+// Residual of level l restricted to level l + 1 (as k_resid_restrict).
+template <class T>
+__device__ void lc_restrict(const LowerCycle<T>& P, int l) {
+  const Level& F = P.lv[l];
+  const Level& C = P.lv[l + 1];
+  const int fx = F.n[0] / C.n[0], fy = F.n[1] / C.n[1], fz = F.n[2] / C.n[2];
+  StrideWalk w;
+  w.init((long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x,
+         C.n[0], C.n[1], C.n[2]);
+  for (; w.c < P.ncomp; w.next()) {
+    const T* __restrict__ x = P.e[l][w.c];
+    const T* __restrict__ b = P.r[l][w.c];
+    T acc = 0;
+    for (int dk = 0; dk < fz; ++dk)
+      for (int dj = 0; dj < fy; ++dj)
+        for (int di = 0; di < fx; ++di) {
+          const int i = w.a * fx + di, j = w.j * fy + dj, k = w.k * fz + dk;
+          const long long c = lin(i, j, k, F.n[0], F.n[1]);
+          acc += resid_plain(x, F, i, j, k, c, b[c]);
+        }
+    P.r[l + 1][w.c][lin(w.a, w.j, w.k, C.n[0], C.n[1])] = acc / (T)(fx * fy * fz);
+  }
+}
+
+// e(l) += P e(l + 1) (as k_prolong_block, or k_prolong_add where an axis
+// is not coarsened).
+template <class T>
+__device__ void lc_prolong(const LowerCycle<T>& P, int l) {
+  const Level& F = P.lv[l];
+  const Level& C = P.lv[l + 1];
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  StrideWalk w;
+  if (blocked_transfer_ok(F, C)) {
+    w.init(t0, stride, C.n[0], C.n[1], C.n[2]);
+    for (; w.c < P.ncomp; w.next()) {
+      T v[2][2][2];
+      prolong_children<T>(C, P.e[l + 1][w.c], w.a, w.j, w.k, v);
+      T* __restrict__ x = P.e[l][w.c];
+      for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b) {
+          T* p = x + ((long long)(2 * w.k + c) * F.n[1] + 2 * w.j + b) * F.n[0] + 2 * w.a;
+          p[0] += v[c][b][0];
+          p[1] += v[c][b][1];
+        }
+    }
+    return;
+  }
+  const T al = lv_alpha<T>(C);
+  w.init(t0, stride, F.n[0], F.n[1], F.n[2]);
+  for (; w.c < P.ncomp; w.next()) {
+    const Interp1<T> ax = interp_axis<T>(w.a, F.n[0] / C.n[0], C.n[0], C.per[0], al);
+    const Interp1<T> ay = interp_axis<T>(w.j, F.n[1] / C.n[1], C.n[1], C.per[1], al);
+    const Interp1<T> az = interp_axis<T>(w.k, F.n[2] / C.n[2], C.n[2], C.per[2], al);
+    const T* __restrict__ ec = P.e[l + 1][w.c];
+    T acc = 0;
+    for (int c2 = 0; c2 < 2; ++c2)
+      for (int b2 = 0; b2 < 2; ++b2)
+        for (int a2 = 0; a2 < 2; ++a2) {
+          const T wt = ax.w[a2] * ay.w[b2] * az.w[c2];
+          if (wt != (T)0) acc += wt * ec[lin(ax.idx[a2], ay.idx[b2], az.idx[c2], C.n[0], C.n[1])];
+        }
+    P.e[l][w.c][lin(w.a, w.j, w.k, F.n[0], F.n[1])] += acc;
+  }
+}
+
+// e(l) = 0 (a correction from zero that takes no pre-smoothing sweep).
+template <class T>
+__device__ void lc_zero(const LowerCycle<T>& P, int l) {
+  const Level& L = P.lv[l];
+  StrideWalk w;
+  w.init((long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x,
+         L.n[0], L.n[1], L.n[2]);
+  for (; w.c < P.ncomp; w.next()) P.e[l][w.c][lin(w.a, w.j, w.k, L.n[0], L.n[1])] = (T)0;
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024)
+k_lower_vcycle(const __grid_constant__ LowerCycle<T> P) {
+  extern __shared__ unsigned char smem_lc[];
+  unsigned epoch = 0;
+  const T om = (T)P.omega;
+  auto sweeps = [&](int l, int nu, bool from_zero) -> bool {
+    if (nu == 0 && from_zero) {
+      lc_zero<T>(P, l);
+      return grid_sync(P.bar, epoch);
+    }
+    for (int s = 0; s < nu; ++s)
+      for (int color = 0; color < 2; ++color) {
+        lc_sweep<T>(P, l, color, from_zero && s == 0 && color == 0, om);
+        if (!grid_sync(P.bar, epoch)) return false;
+      }
+    return true;
+  };
+  const int lw = P.cc;   // first level of the one-CTA part (last + 1: none)
+  for (int l = P.first; l < lw; ++l) {
+    if (l == P.last) {   // coarsest level solved grid-wide: plain Gauss-Seidel from zero
+      for (int s = 0; s < P.coarse_sweeps; ++s)
+        for (int color = 0; color < 2; ++color) {
+          lc_sweep<T>(P, l, color, s == 0 && color == 0, (T)1);
+          if (!grid_sync(P.bar, epoch)) return;
+        }
+      break;
+    }
+    if (!sweeps(l, P.nu1, true)) return;
+    lc_restrict<T>(P, l);
+    if (!grid_sync(P.bar, epoch)) return;
+  }
+  if (lw <= P.last) {
+    if (blockIdx.x < (unsigned)P.ncomp)
+      coarse_vcycle_cta<T>(P.cc_plan, P.r[lw][blockIdx.x], P.e[lw][blockIdx.x],
+                           reinterpret_cast<T*>(smem_lc));
+    if (!grid_sync(P.bar, epoch)) return;
+  }
+  for (int l = min(lw, P.last) - 1; l >= P.first; --l) {
+    lc_prolong<T>(P, l);
+    if (!grid_sync(P.bar, epoch)) return;
+    if (!sweeps(l, P.nu2, false)) return;
+  }
+}
+
+// The barrier alone, for tests of its bound: `rounds` barriers of a grid
+// that expects `extra` arrivals more per barrier than it has CTAs (extra > 0
+// means the wait can only end by running out).
+__global__ void k_barrier_probe(GridBarrier B, int rounds) {
+  unsigned epoch = 0;
+  for (int r = 0; r < rounds; ++r)
+    if (!grid_sync(B, epoch)) return;
+}
+
+template <class T>
+int lower_cycle_blocks(int sms, size_t smem) {
+  int per_sm = 0;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_lower_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lower_vcycle<T>, 1024, smem) !=
+      cudaSuccess)
+    return 0;
+  return per_sm * sms;
+}
+
+template <class T>
+bool launch_lower_vcycle(Ctx& cx, const LowerCycle<T>& P) {
+  const size_t smem = P.cc <= P.last ? (size_t)P.cc_plan.total * sizeof(T) : 0;
+  if (smem > kCoarseCycleSmem) return false;
+  const int nb = lower_cycle_blocks<T>(cx.sms, smem);
+  if (nb < P.ncomp || nb < 1) return false;
+  if (cudaMemsetAsync(P.bar.count, 0, sizeof(unsigned), cx.stream) != cudaSuccess) return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nb);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = cx.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs co-resident, or no launch
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cx.before(VSV_KCLASS_SMOOTH);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_lower_vcycle<T>, P);
+  // r of the first level read, e written; the lower levels stay in L2
+  cx.after(VSV_KCLASS_SMOOTH, 2.0 * (double)sizeof(T) * (double)P.lv[P.first].cells() * P.ncomp);
+  return e == cudaSuccess;
+}
+
+int barrier_probe_max_blocks(int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_probe, 128, 0) != cudaSuccess)
+    return 0;
+  return per_sm * sms;
+}
+
+bool launch_barrier_probe(cudaStream_t s, GridBarrier B, int blocks, int rounds) {
+  if (cudaMemsetAsync(B.count, 0, sizeof(unsigned), s) != cudaSuccess) return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(128);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_barrier_probe, B, rounds) == cudaSuccess;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -779,6 +1100,7 @@ void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncom
   template void launch_axpy<T>(Ctx&, Comp3<T>, Comp3<T>, double, long long, int);                  \
   template void launch_extrapolate_rot<T>(Ctx&, Comp3<T>, Comp3<T>, Comp3<T>, long long, int, int); \
   template bool launch_coarse_vcycle<T>(Ctx&, const CoarseCycle&, Comp3<T>, Comp3<T>, int);        \
+  template bool launch_lower_vcycle<T>(Ctx&, const LowerCycle<T>&);                                \
   template bool launch_coarse_solve<T>(Ctx&, const Level&, Comp3<T>, Comp3<T>, int, int, double);  \
   template void launch_resid_norm<T>(Ctx&, const Level&, Comp3<T>, Rhs3<T>, int, bool, double*,    \
                                      int, Scalars*);

@@ -47,7 +47,8 @@ class vsv_solver_params(C.Structure):
                 ("fixed_cycles", C.c_int), ("check_every", C.c_int), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("max_levels", C.c_int), ("coarse_sweeps", C.c_int),
                 ("omega_sor", C.c_double), ("variant", C.c_int), ("extrapolate", C.c_int),
-                ("fixed_cycles_psi", C.c_int), ("omega_mg", C.c_double)]
+                ("fixed_cycles_psi", C.c_int), ("omega_mg", C.c_double),
+                ("lower_cycle", C.c_int)]
 
 
 class vsv_bc(C.Structure):
@@ -81,7 +82,8 @@ EXPORTS = [
     "vsv_set_free_energy", "vsv_set_solver", "vsv_default_solver", "vsv_set_phi", "vsv_step",
     "vsv_stability_limit", "vsv_solve_poisson", "vsv_get_field", "vsv_set_field",
     "vsv_get_diagnostics", "vsv_get_stress_profile", "vsv_state_bytes", "vsv_get_state",
-    "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_last_error", "vsv_kernel_launches",
+    "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_barrier_check", "vsv_last_error",
+    "vsv_kernel_launches",
     "vsv_kernel_bytes", "vsv_profile_enable", "vsv_profile_read", "vsv_batch_create",
     "vsv_batch_step", "vsv_batch_destroy", "vsv_tape_create", "vsv_tape_destroy",
     "vsv_tape_forward", "vsv_tape_backward", "vsv_tape_set_cycles", "vsv_tape_bytes",
@@ -119,6 +121,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_set_state": (i32, [vp, vp, sz]),
         "vsv_volume_area_static": (i32, [vp, i32, i32, i32, dbl, dbl, i32, vp, vp]),
         "vsv_check": (i32, [vp]),
+        "vsv_barrier_check": (i32, [vp, i32, i32, i32, dbl]),
         "vsv_last_error": (C.c_char_p, [vp]),
         "vsv_kernel_launches": (i64, [vp]),
         "vsv_kernel_bytes": (dbl, [vp]),
@@ -280,6 +283,11 @@ def vsv_volume_area_static(phi_ptr, nx, ny, nz, h, eps, z_periodic, out_ptr, str
 def vsv_check(g, check=True):
     st = lib().vsv_check(g)
     return _check(g, st, "vsv_check") if check else st
+
+
+def vsv_barrier_check(g, blocks, rounds, extra_arrivals, limit_ms):
+    """Bounded grid barrier check (see the header); returns the vsv_status."""
+    return lib().vsv_barrier_check(g, blocks, rounds, extra_arrivals, limit_ms)
 
 
 def vsv_last_error(g) -> str:
