@@ -19,6 +19,15 @@ Stokes for the current interface); advection uses the velocity of the
 previous stream vector, as the segregated order implies; the initial state
 solves 5-8 for phi^0 with gamma_A = 0 (A = A0).
 
+Time-dependent walls (supplementary material, the time-dependency
+paragraph after eq. 36: a flow that speeds up, slows down or oscillates
+changes only the boundary conditions, not the system of equations).  With
+``wall_motion`` set, each wall speed of the body-free flow becomes
+s(t) = s0 + ramp t + amplitude sin(2 pi frequency t + phase): index 0 is the
+Couette wall at y = 0 or the Poiseuille speed U, index 1 the Couette wall at
+y = H.  Step n -> n+1 advects phi with the flow of time t^n (its wall data
+are those of t^n) and solves steps 7-8 with the wall data of t^{n+1}.
+
 Inertial variant (SM eq. 36, density rho > 0): the vorticity obeys
 (rho / eta) d omega / dt - lap omega = -f, a heat equation.  Reading: one
 backward-Euler step per time step, so step 7 becomes
@@ -29,7 +38,9 @@ with the same wall data; phi and psi are unchanged.  The initial vorticity
 is the non-inertial (Stokes) solution for phi^0.  rho = 0 is eq. gen1.
 
 Pinned by the module pins of grid / poisson / flow / free_energy, by the
-Couette and Poiseuille body-free steady states, by the closed-form
+Couette and Poiseuille body-free steady states, by the closed-form profiles
+of oscillating and ramped walls at every step and the exact base-flow
+difference one moving-wall step makes with a body present, by the closed-form
 advection of a sine profile, by the free-energy dissipation identity and by a
 pure-loop transcription of the whole step on a tiny grid.
 """
@@ -66,6 +77,9 @@ class OracleParams:
     k_vol: float
     mu_prefactor_half: bool = False
     rho: float = 0.0            # fluid density; > 0 selects SM eq. 36
+    # time-dependent walls: (ramp, amplitude, frequency, phase), each a pair
+    # (wall 0, wall 1); None for steady walls
+    wall_motion: tuple = None
 
     @property
     def z_periodic(self):
@@ -140,9 +154,32 @@ def flow_solve(phi, mu, p, bf, omega_prev=None, dt=None):
     return omega, psi
 
 
+def wall_speeds(p: OracleParams, t: float):
+    """(u_max, v_lo, v_hi) of the body-free flow at time t: the steady values,
+    or with ``wall_motion`` s(t) = s0 + ramp t + amplitude sin(2 pi f t + phase)
+    (wall 0: v_lo, or u_max for Poiseuille; wall 1: v_hi)."""
+    if p.wall_motion is None:
+        return p.u_max, p.v_lo, p.v_hi
+    ramp, amp, freq, phase = p.wall_motion
+
+    def s(w, s0):
+        return s0 + ramp[w] * t + amp[w] * np.sin(2.0 * np.pi * freq[w] * t + phase[w])
+    from inputs import COUETTE
+    if p.flow_kind == COUETTE:
+        return p.u_max, s(0, p.v_lo), s(1, p.v_hi)
+    return s(0, p.u_max), p.v_lo, p.v_hi
+
+
+def base_flow_at(p: OracleParams, t: float) -> BaseFlow:
+    """The body-free flow's wall data at time t (steady walls: any t)."""
+    u, vlo, vhi = wall_speeds(p, t)
+    return base_flow(p.flow_kind, p.nx, p.ny, p.nz, p.h, u_max=u, v_lo=vlo, v_hi=vhi)
+
+
 def init_state(p: OracleParams, phi0: np.ndarray) -> OracleState:
-    bf = base_flow(p.flow_kind, p.nx, p.ny, p.nz, p.h, u_max=p.u_max, v_lo=p.v_lo,
-                   v_hi=p.v_hi)
+    if p.wall_motion is not None and p.rho > 0.0:
+        raise ValueError("time-dependent walls are provided for the non-inertial flow only")
+    bf = base_flow_at(p, 0.0)
     phi = np.array(phi0, dtype=np.float64, copy=True)
     V0 = volume(phi, p.h)
     A0 = area(phi, p.eps, p.h, p.z_periodic)
@@ -172,6 +209,8 @@ def step(st: OracleState, dt: float) -> OracleState:
     V_new = volume(phi_new, p.h)
     gamma_a = area_multiplier(p.k_area, A_new, st.A0, p.eps)
     mu_new = _mu(phi_new, p, gamma_a)
+    if p.wall_motion is not None:      # wall data of t^{n+1} for the solves
+        st.bf = base_flow_at(p, st.t + dt)
     omega, psi = flow_solve(phi_new, mu_new, p, st.bf, omega_prev=st.omega, dt=dt)
     st.phi, st.mu, st.omega, st.psi = phi_new, mu_new, omega, psi
     st.V, st.A, st.gamma_a, st.lambda_v = V_new, A_new, gamma_a, lam_v
