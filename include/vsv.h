@@ -109,6 +109,21 @@ typedef struct {
   double rho;
 } vsv_flow_params;
 
+/* Time-dependent walls (supplementary material, the time-dependency
+ * paragraph after eq. 36: a flow that speeds up, slows down or oscillates
+ * changes only the boundary conditions).  Wall w's speed at time t becomes
+ *   s_w(t) = s_w + ramp[w] t + amplitude[w] sin(2 pi frequency[w] t + phase[w])
+ * where s_w is the steady speed of vsv_set_flow: w = 0 is the Couette wall at
+ * y = 0 (v_lo) or the Poiseuille speed u_max, w = 1 the Couette wall at
+ * y = H (v_hi; must be all zero for Poiseuille).  t is the simulation time
+ * (0 at vsv_set_phi; restored by vsv_set_state). */
+typedef struct {
+  double ramp[2];
+  double amplitude[2];
+  double frequency[2];
+  double phase[2];
+} vsv_wall_motion;
+
 /* Free energy.  sigma: CH gradient coefficient, or for the Helfrich kind the
  * membrane tension, which adds sigma A_f[phi] to the energy (A_f: the area
  * functional of SM eq. 32 with the gradient summed over cell faces) and
@@ -243,6 +258,19 @@ vsv_status vsv_destroy(vsv_grid* g);
  * the device; a duct runs 2-D FP64 Poisson solves).  Must precede set_phi. */
 vsv_status vsv_set_flow(vsv_grid* g, const vsv_flow_params* fp);
 vsv_status vsv_set_free_energy(vsv_grid* g, const vsv_fe_params* fe);
+
+/* Make the walls of the flow time-dependent (vsv_wall_motion; NULL or all
+ * zero: steady walls again).  A step n -> n+1 advects phi with the flow of
+ * time t^n and solves for omega, psi with the wall data of t^{n+1}; the
+ * base-flow tables are recombined on the device every step from tables of
+ * unit wall speeds, so CUDA graphs of steps (vsv_batch_step) replay it too.
+ * Exports and observables see the walls of the current time.  Must follow
+ * vsv_set_flow (which resets the walls to steady); takes effect at the
+ * current time.  VSV_EINVAL: non-finite entries, motion of a quiescent flow
+ * or of wall 1 of a Poiseuille flow, or an inertial flow (rho > 0);
+ * VSV_ESTATE before vsv_set_flow.  The adjoint tape refuses a grid with
+ * moving walls (VSV_EINVAL from vsv_tape_forward). */
+vsv_status vsv_set_wall_motion(vsv_grid* g, const vsv_wall_motion* m);
 vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp);
 vsv_status vsv_default_solver(vsv_solver_params* out, int precision);
 

@@ -66,6 +66,9 @@ class Workload:
     body: dict = field(default_factory=dict)   # geometry actually drawn
     phi0: Optional[np.ndarray] = None          # float64 [nz][ny][nx]
     rho: float = 0.0                           # fluid density (0: no inertia)
+    # time-dependent walls: (ramp, amplitude, frequency, phase), each a pair
+    # (wall 0, wall 1), or None for steady walls
+    wall_motion: Optional[tuple] = None
 
     @property
     def z_periodic(self) -> bool:

@@ -92,7 +92,8 @@ def params_from_workload(w) -> OracleParams:
                         u_max=w.u_max, v_lo=w.v_lo, v_hi=w.v_hi, eta=w.eta,
                         fe_kind=w.fe_kind, sigma=w.sigma, kappa=w.kappa, eps=w.eps,
                         mobility=w.mobility, k_area=w.k_area, k_vol=w.k_vol,
-                        rho=getattr(w, "rho", 0.0))
+                        rho=getattr(w, "rho", 0.0),
+                        wall_motion=getattr(w, "wall_motion", None))
 
 
 @dataclass

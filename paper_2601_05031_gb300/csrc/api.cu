@@ -72,6 +72,17 @@ struct vsv_grid {
   void* v0t[3] = {};         // typed copies (T)
   void* s_om_t[3] = {};
   void* s_ps_neg_t[3] = {};
+  // time-dependent walls: the base-flow tables of unit wall speeds (basis 0:
+  // the y = 0 wall or the Poiseuille speed, basis 1: the y = H wall), of
+  // which the current tables are the combination at the device time t_dev
+  double* wb_om[2][3] = {};
+  double* wb_ps[2][3] = {};
+  double* wb_v0[2][3] = {};
+  double* wb_som[2][3] = {};
+  double* wb_sps[2][3] = {};
+  double* t_dev = nullptr;
+  bool motion_on = false;
+  vsv_wall_motion motion{};
   double* su0 = nullptr;     // 2-D set-up scratch (ny nz each)
   double* schi = nullptr;
   double* sx = nullptr;
@@ -216,6 +227,15 @@ size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
   d = df(ny); if (g) g->profile = d;
   d = df(8); if (g) g->scratch1 = d;
   p = take(sizeof(unsigned)); if (g) g->bar_count = (unsigned*)p;
+  for (int b = 0; b < 2; ++b)
+    for (int c = 0; c < 3; ++c) {
+      d = df(R2); if (g) g->wb_om[b][c] = d;
+      d = df(R2); if (g) g->wb_ps[b][c] = d;
+      d = df(N2); if (g) g->wb_v0[b][c] = d;
+      d = df(N2); if (g) g->wb_som[b][c] = d;
+      d = df(N2); if (g) g->wb_sps[b][c] = d;
+    }
+  d = df(1); if (g) g->t_dev = d;
   return off;
 }
 
@@ -694,6 +714,50 @@ vsv_status solve_dc(vsv_grid* g, const std::vector<Level>& lv, Comp3<float> XH, 
 }
 
 // ---------------------------------------------------------------- phase-field helpers
+// Speed of wall w (0: y = 0 wall or Poiseuille speed, 1: y = H wall) at time t.
+double wall_speed(const vsv_grid* g, int w, double t) {
+  const double s0 = g->flow.kind == VSV_COUETTE ? (w == 0 ? g->flow.v_lo : g->flow.v_hi)
+                                                : (w == 0 ? g->flow.u_max : 0.0);
+  if (!g->motion_on) return s0;
+  const vsv_wall_motion& m = g->motion;
+  return s0 + m.ramp[w] * t + m.amplitude[w] * std::sin(2.0 * M_PI * m.frequency[w] * t + m.phase[w]);
+}
+
+WallTables wall_tables(const vsv_grid* g) {
+  WallTables W{};
+  W.n_ring = (g->ny + 2) * (g->nz + 2);
+  W.n_tab = g->ny * g->nz;
+  for (int b = 0; b < 2; ++b)
+    for (int c = 0; c < 3; ++c) {
+      W.bom[b][c] = g->wb_om[b][c];
+      W.bps[b][c] = g->wb_ps[b][c];
+      W.bv0[b][c] = g->wb_v0[b][c];
+      W.bsom[b][c] = g->wb_som[b][c];
+      W.bsps[b][c] = g->wb_sps[b][c];
+    }
+  for (int c = 0; c < 3; ++c) {
+    W.om[c] = g->om_ring[c];
+    W.ps[c] = g->ps_ring[c];
+    W.v0[c] = g->v0d[c];
+    W.som[c] = g->s_om_d[c];
+    W.sps[c] = g->s_ps_d[c];
+    W.v0t[c] = g->v0t[c];
+    W.somt[c] = g->s_om_t[c];
+    W.spsnt[c] = g->s_ps_neg_t[c];
+  }
+  const bool cou = g->flow.kind == VSV_COUETTE;
+  W.s0[0] = cou ? g->flow.v_lo : g->flow.u_max;
+  W.s0[1] = cou ? g->flow.v_hi : 0.0;
+  for (int w = 0; w < 2; ++w) {
+    W.ramp[w] = g->motion.ramp[w];
+    W.amp[w] = g->motion.amplitude[w];
+    W.freq[w] = g->motion.frequency[w];
+    W.phase[w] = g->motion.phase[w];
+  }
+  W.t_dev = g->t_dev;
+  return W;
+}
+
 PhaseParams phase_params(const vsv_grid* g) {
   PhaseParams P{};
   P.nx = g->nx; P.ny = g->ny; P.nz = g->nz;
@@ -722,9 +786,9 @@ PhaseParams phase_params(const vsv_grid* g) {
   split(3.0 / (2.0 * std::sqrt(2.0)) * 0.25 / g->fe.eps, P.aw_hi, P.aw_lo);
   split(P.beta_t, P.bt_hi, P.bt_lo);
   std::memset(P.vwall, 0, sizeof P.vwall);
-  if (g->flow.kind == VSV_COUETTE) {
-    P.vwall[0][0] = g->flow.v_lo;
-    P.vwall[1][0] = g->flow.v_hi;
+  if (g->flow.kind == VSV_COUETTE) {   // the walls of the current time
+    P.vwall[0][0] = wall_speed(g, 0, g->time);
+    P.vwall[1][0] = wall_speed(g, 1, g->time);
   }
   return P;
 }
@@ -878,6 +942,8 @@ vsv_status step_impl(vsv_grid* g, double dt) {
   else
     launch_phi_update<T>(g->cx, P, phi, (const T*)g->mu, Pp, V0, g->S, (T)dt, phin);
   g->cur = 1 - g->cur;
+  // moving walls: the base-flow tables of t^{n+1} for the solves
+  if (g->motion_on) launch_wall_tables<T>(g->cx, wall_tables(g), dt, false, 0.0);
   // 4-5: V, A of phi^{n+1}, gamma_A, then mu^{n+1}
   refresh_phase<T>(g, 0);
   // 6: source f = grad phi x grad mu / eta - s_omega
@@ -1294,6 +1360,7 @@ vsv_status vsv_set_flow(vsv_grid* g, const vsv_flow_params* fp) {
   const bool zper = fp->kind == VSV_COUETTE || fp->kind == VSV_POISEUILLE_PLANAR;
   if (zper && g->nz > 1 && g->nz % 2) return fail(g, VSV_EINVAL, "periodic z needs even nz%s");
   g->flow = *fp;
+  g->motion_on = false;
   const int per[3] = {1, 0, zper ? 1 : 0};
   g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);
   g->omega_levels.clear();
@@ -1311,6 +1378,80 @@ vsv_status vsv_set_free_energy(vsv_grid* g, const vsv_fe_params* fe) {
     return fail(g, VSV_EINVAL, "invalid free-energy parameters%s");
   g->fe = *fe;
   upload_scalar_params(g);
+  if (g->phi_set) g->phase_stale = true;
+  return VSV_OK;
+}
+
+vsv_status vsv_set_wall_motion(vsv_grid* g, const vsv_wall_motion* m) {
+  if (!g) return VSV_EINVAL;
+  if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_set_wall_motion%s");
+  bool any = false;
+  if (m) {
+    for (int w = 0; w < 2; ++w) {
+      const double v[4] = {m->ramp[w], m->amplitude[w], m->frequency[w], m->phase[w]};
+      for (double x : v) {
+        if (!std::isfinite(x)) return fail(g, VSV_EINVAL, "non-finite wall motion%s");
+        any = any || x != 0.0;
+      }
+    }
+    const bool w1 = m->ramp[1] != 0.0 || m->amplitude[1] != 0.0;
+    if (any && g->flow.kind == VSV_QUIESCENT)
+      return fail(g, VSV_EINVAL, "a quiescent flow has no moving walls%s");
+    if (w1 && g->flow.kind != VSV_COUETTE)
+      return fail(g, VSV_EINVAL, "wall 1 moves in Couette flow only%s");
+    if (any && g->flow.rho > 0.0)
+      return fail(g, VSV_EINVAL, "moving walls are provided for the non-inertial flow only%s");
+  }
+  if (!any) {   // steady walls: the tables of vsv_set_flow, exactly
+    const bool was = g->motion_on;
+    g->motion_on = false;
+    g->motion = vsv_wall_motion{};
+    return was ? build_base_flow(g) : VSV_OK;
+  }
+  // tables of unit wall speeds (the base flow is linear in them)
+  const vsv_flow_params keep = g->flow;
+  const long long R2 = (long long)(g->ny + 2) * (g->nz + 2), n2 = (long long)g->ny * g->nz;
+  vsv_status st = VSV_OK;
+  for (int w = 0; w < 2 && st == VSV_OK; ++w) {
+    if (keep.kind != VSV_COUETTE && w == 1) {
+      for (int c = 0; c < 3; ++c) {
+        launch_fill(g->cx, g->wb_om[1][c], R2, 0.0);
+        launch_fill(g->cx, g->wb_ps[1][c], R2, 0.0);
+        launch_fill(g->cx, g->wb_v0[1][c], n2, 0.0);
+        launch_fill(g->cx, g->wb_som[1][c], n2, 0.0);
+        launch_fill(g->cx, g->wb_sps[1][c], n2, 0.0);
+      }
+      break;
+    }
+    g->flow = keep;
+    if (keep.kind == VSV_COUETTE) {
+      g->flow.v_lo = w == 0 ? 1.0 : 0.0;
+      g->flow.v_hi = w == 1 ? 1.0 : 0.0;
+    } else {
+      g->flow.u_max = 1.0;
+    }
+    g->motion_on = false;
+    st = build_base_flow(g);
+    for (int c = 0; c < 3 && st == VSV_OK; ++c) {
+      const cudaStream_t s = g->cx.stream;
+      if (cudaMemcpyAsync(g->wb_om[w][c], g->om_ring[c], R2 * 8, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(g->wb_ps[w][c], g->ps_ring[c], R2 * 8, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(g->wb_v0[w][c], g->v0d[c], n2 * 8, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(g->wb_som[w][c], g->s_om_d[c], n2 * 8, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(g->wb_sps[w][c], g->s_ps_d[c], n2 * 8, cudaMemcpyDeviceToDevice, s))
+        st = fail(g, VSV_ECUDA, "copy of the wall-speed tables failed%s");
+    }
+  }
+  g->flow = keep;
+  if (st != VSV_OK) {
+    build_base_flow(g);
+    return st;
+  }
+  g->motion = *m;
+  g->motion_on = true;
+  if (g->prec == VSV_FP64) launch_wall_tables<double>(g->cx, wall_tables(g), 0.0, true, g->time);
+  else launch_wall_tables<float>(g->cx, wall_tables(g), 0.0, true, g->time);
+  CKL();
   if (g->phi_set) g->phase_stale = true;
   return VSV_OK;
 }
@@ -1342,6 +1483,11 @@ vsv_status vsv_set_phi(vsv_grid* g, const void* phi, int dtype, int on_device) {
   if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_set_phi%s");
   g->err.clear();
   vsv_status st;
+  if (g->motion_on) {   // the walls of t = 0 for the initial solves
+    if (g->prec == VSV_FP64) launch_wall_tables<double>(g->cx, wall_tables(g), 0.0, true, 0.0);
+    else launch_wall_tables<float>(g->cx, wall_tables(g), 0.0, true, 0.0);
+    CKL();
+  }
   if (g->prec == VSV_FP64) {
     st = import_phi<double>(g, phi, dtype, on_device);
     if (st == VSV_OK) st = set_phi_impl<double>(g);
@@ -1916,6 +2062,11 @@ vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes) {
   g->phi_set = true;
   g->phase_stale = true;
   g->hist = (hd.hist >= 0 && hd.hist <= 2) ? hd.hist : 0;
+  if (g->motion_on) {   // the walls of the restored time
+    if (g->prec == VSV_FP64) launch_wall_tables<double>(g->cx, wall_tables(g), 0.0, true, g->time);
+    else launch_wall_tables<float>(g->cx, wall_tables(g), 0.0, true, g->time);
+    CKL();
+  }
   return VSV_OK;
 }
 
@@ -2327,6 +2478,8 @@ vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_dev
   if (!t || !phi0 || nsteps < 1 || !(dt > 0)) return VSV_EINVAL;
   vsv_grid* g = t->g;
   if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_tape_forward%s");
+  if (g->motion_on)
+    return fail(g, VSV_EINVAL, "the adjoint tape needs steady walls (vsv_set_wall_motion)%s");
   CK(cudaStreamSynchronize(g->cx.stream));
   tape_free_ckpts(t);
   t->dev_bytes = (size_t)(t->every + 1) * 5 * g->N * 8 + (size_t)(t->every + 1) * 8 +

@@ -278,6 +278,22 @@ void launch_duct_ring(Ctx& cx, int ny, int nz, double h, const double* u0, const
 void launch_ring_boundary_rhs(Ctx& cx, int ny, int nz, double h, const double* ring, double scale_in,
                               const double* in, double* out);
 void launch_ring_fill_interior(Ctx& cx, int ny, int nz, const double* interior, double* ring);
+// Time-dependent walls: the current base-flow tables as the combination
+// s_0(t) B_0 + s_1(t) B_1 of the unit-speed tables B_w at the device time
+// *t_dev (advanced by dt, or set to t_set when set_time), with the typed
+// copies the kernels read (T: v0t, s_om_t, and s_ps_neg_t = -s_ps).
+struct WallTables {
+  int n_ring, n_tab;                       // (ny+2)(nz+2), ny nz
+  const double* bom[2][3]; const double* bps[2][3];
+  const double* bv0[2][3]; const double* bsom[2][3]; const double* bsps[2][3];
+  double* om[3]; double* ps[3]; double* v0[3]; double* som[3]; double* sps[3];
+  void* v0t[3]; void* somt[3]; void* spsnt[3];
+  double s0[2], ramp[2], amp[2], freq[2], phase[2];
+  double* t_dev;
+};
+template <class T>
+void launch_wall_tables(Ctx& cx, const WallTables& W, double dt, bool set_time, double t_set);
+
 void launch_base_derived(Ctx& cx, int ny, int nz, int zper, double h, const double* om_ring[3],
                          const double* ps_ring[3], double* v0[3], double* s_om[3], double* s_ps[3]);
 double device_max_abs(Ctx& cx, const double* x, long long n, double* scratch);

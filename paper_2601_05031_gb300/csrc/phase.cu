@@ -565,6 +565,66 @@ __global__ void k_scale_copy(const T* __restrict__ in, T* __restrict__ out, long
   if (t < n) out[t] = a * in[t];
 }
 
+// ---------------------------------------------------------------- time-dependent walls
+// One thread: the device time of the wall data, advanced by one step (or
+// set), so that a captured graph of steps carries the time with it.
+__global__ void k_wall_time(double* t_dev, double dt, int set_time, double t_set) {
+  *t_dev = set_time ? t_set : *t_dev + dt;
+}
+
+__device__ __forceinline__ double wall_speed(const WallTables& W, int w, double t) {
+  return W.s0[w] + W.ramp[w] * t + W.amp[w] * sin(2.0 * 3.14159265358979323846 * W.freq[w] * t +
+                                                  W.phase[w]);
+}
+
+// Current tables = s_0(t) B_0 + s_1(t) B_1, every table and component in
+// one grid-stride loop over a flat index.
+template <class T>
+__global__ void k_wall_tables(const __grid_constant__ WallTables W) {
+  const double t = *W.t_dev;
+  const double a = wall_speed(W, 0, t), b = wall_speed(W, 1, t);
+  const long long nr = W.n_ring, nt = W.n_tab;
+  const long long total = 3 * (2 * nr + 3 * nt);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long r = q;
+    const int c = (int)(r / (2 * nr + 3 * nt));
+    r -= c * (2 * nr + 3 * nt);
+    if (r < nr) {
+      W.om[c][r] = a * W.bom[0][c][r] + b * W.bom[1][c][r];
+    } else if ((r -= nr) < nr) {
+      W.ps[c][r] = a * W.bps[0][c][r] + b * W.bps[1][c][r];
+    } else if ((r -= nr) < nt) {
+      const double v = a * W.bv0[0][c][r] + b * W.bv0[1][c][r];
+      W.v0[c][r] = v;
+      ((T*)W.v0t[c])[r] = (T)v;
+    } else if ((r -= nt) < nt) {
+      const double v = a * W.bsom[0][c][r] + b * W.bsom[1][c][r];
+      W.som[c][r] = v;
+      ((T*)W.somt[c])[r] = (T)v;
+    } else {
+      r -= nt;
+      const double v = a * W.bsps[0][c][r] + b * W.bsps[1][c][r];
+      W.sps[c][r] = v;
+      ((T*)W.spsnt[c])[r] = (T)(-v);
+    }
+  }
+}
+
+template <class T>
+void launch_wall_tables(Ctx& cx, const WallTables& W, double dt, bool set_time, double t_set) {
+  cx.before(-1);
+  k_wall_time<<<1, 1, 0, cx.stream>>>(W.t_dev, dt, set_time ? 1 : 0, t_set);
+  cx.after(-1);
+  const long long total = 3LL * (2LL * W.n_ring + 3LL * W.n_tab);
+  const unsigned blocks = (unsigned)std::min<long long>((total + kBlock - 1) / kBlock, 4LL * cx.sms);
+  cx.before(-1);
+  k_wall_tables<T><<<blocks, kBlock, 0, cx.stream>>>(W);
+  cx.after(-1, 8.0 * (double)total * 3.0);
+}
+template void launch_wall_tables<float>(Ctx&, const WallTables&, double, bool, double);
+template void launch_wall_tables<double>(Ctx&, const WallTables&, double, bool, double);
+
 // ---------------------------------------------------------------- base-flow tables (FP64)
 // Ring layout: entry (j, k), j in [-1, ny], k in [-1, nz], at (j+1) + (k+1)(ny+2).
 __device__ __forceinline__ long long ring_at(int j, int k, int ny) {

@@ -45,6 +45,8 @@ class Simulation:
         V.vsv_set_flow(self.g, w.flow_kind, w.u_max, w.v_lo, w.v_hi, w.eta, getattr(w, "rho", 0.0))
         V.vsv_set_free_energy(self.g, w.fe_kind, w.sigma, w.kappa, w.eps, w.mobility, w.k_area,
                               w.k_vol)
+        if getattr(w, "wall_motion", None) is not None:
+            V.vsv_set_wall_motion(self.g, w.wall_motion)
         if solver is not None:
             V.vsv_set_solver(self.g, solver)
 

@@ -42,6 +42,11 @@ class vsv_fe_params(C.Structure):
                 ("k_vol", C.c_double), ("mu_prefactor_half", C.c_int)]
 
 
+class vsv_wall_motion(C.Structure):
+    _fields_ = [("ramp", C.c_double * 2), ("amplitude", C.c_double * 2),
+                ("frequency", C.c_double * 2), ("phase", C.c_double * 2)]
+
+
 class vsv_solver_params(C.Structure):
     _fields_ = [("kind", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("fixed_cycles", C.c_int), ("check_every", C.c_int), ("nu1", C.c_int),
@@ -79,7 +84,7 @@ class vsv_diag(C.Structure):
 # exported names, in header order (used by the ABI test)
 EXPORTS = [
     "vsv_version", "vsv_workspace_bytes", "vsv_create", "vsv_destroy", "vsv_set_flow",
-    "vsv_set_free_energy", "vsv_set_solver", "vsv_default_solver", "vsv_set_phi", "vsv_step",
+    "vsv_set_free_energy", "vsv_set_wall_motion", "vsv_set_solver", "vsv_default_solver", "vsv_set_phi", "vsv_step",
     "vsv_stability_limit", "vsv_solve_poisson", "vsv_get_field", "vsv_set_field",
     "vsv_get_diagnostics", "vsv_get_stress_profile", "vsv_state_bytes", "vsv_get_state",
     "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_barrier_check", "vsv_last_error",
@@ -105,6 +110,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_destroy": (i32, [vp]),
         "vsv_set_flow": (i32, [vp, C.POINTER(vsv_flow_params)]),
         "vsv_set_free_energy": (i32, [vp, C.POINTER(vsv_fe_params)]),
+        "vsv_set_wall_motion": (i32, [vp, C.POINTER(vsv_wall_motion)]),
         "vsv_set_solver": (i32, [vp, C.POINTER(vsv_solver_params)]),
         "vsv_default_solver": (i32, [C.POINTER(vsv_solver_params), i32]),
         "vsv_set_phi": (i32, [vp, vp, i32, i32]),
@@ -199,6 +205,19 @@ def vsv_set_free_energy(g, kind, sigma=1.0, kappa=0.0, eps=1.0, mobility=1.0, k_
                         k_vol=0.0, mu_prefactor_half=0):
     p = vsv_fe_params(kind, sigma, kappa, eps, mobility, k_area, k_vol, mu_prefactor_half)
     return _check(g, lib().vsv_set_free_energy(g, C.byref(p)), "vsv_set_free_energy")
+
+
+def vsv_set_wall_motion(g, motion, check=True):
+    """motion: None (steady walls) or (ramp, amplitude, frequency, phase),
+    each a pair (wall 0, wall 1)."""
+    if motion is None:
+        st = lib().vsv_set_wall_motion(g, None)
+    else:
+        ramp, amp, freq, phase = motion
+        m = vsv_wall_motion((C.c_double * 2)(*ramp), (C.c_double * 2)(*amp),
+                            (C.c_double * 2)(*freq), (C.c_double * 2)(*phase))
+        st = lib().vsv_set_wall_motion(g, C.byref(m))
+    return _check(g, st, "vsv_set_wall_motion") if check else st
 
 
 def vsv_default_solver(precision) -> vsv_solver_params:
