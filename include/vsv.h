@@ -189,7 +189,7 @@ typedef struct {
                              sweeps, red-black SOR (every level but the
                              coarsest, which keeps Gauss-Seidel): x <- x +
                              omega_mg (x_GS - x).  0 or 1: Gauss-Seidel.
-                             Default 1.25, where a V(2,2)-cycle contracts
+                             Default 1.3, where a V(2,2)-cycle contracts
                              the error about 3x more than with 1.  It
                              changes the iterate, not the converged answer.
                              Outside [0, 2): VSV_EINVAL. */

@@ -70,7 +70,7 @@ def test_full_size_step_sampled_against_oracle(V):
     import bench
     w = inputs.vesicle_couette_512x256x256()
     p = oracle.params_from_workload(w)
-    sim = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, 1)
+    sim = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, bench.BENCH_EXTRAPOLATE)
     sim.step(3, w.dt)                      # history full, as in the timed steps
     d0 = sim.diagnostics()
     phi0 = sim.field(V.VSV_FIELD_PHI)
@@ -145,9 +145,9 @@ def test_full_size_graph_replay_matches_plain_steps(V):
     import bench
     from paper_2601_05031_gb300.sim import Batch
     w = inputs.vesicle_couette_512x256x256()
-    a = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, 1)
+    a = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, bench.BENCH_EXTRAPOLATE)
     a.step(2 + bench.GRAPH_STEPS, w.dt)
-    b = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, 1, stream=torch.cuda.Stream())
+    b = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, bench.BENCH_EXTRAPOLATE, stream=torch.cuda.Stream())
     batch = Batch([b])
     batch.step(2 + bench.GRAPH_STEPS, w.dt)      # two plain steps, then one capture + replay
     torch.cuda.synchronize()

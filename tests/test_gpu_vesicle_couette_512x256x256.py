@@ -29,7 +29,7 @@ def test_500_steps_against_converged_fp64(V):
     import torch
     import bench
     w = inputs.vesicle_couette_512x256x256()
-    mixed = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, 1)
+    mixed = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, bench.BENCH_EXTRAPOLATE)
     fp64 = bench.make_sim(w, V.VSV_FP64, 0)        # every solve to relative residual 1e-12
     done, errs = 0, {}
     for mark in (10, 100, w.nsteps):

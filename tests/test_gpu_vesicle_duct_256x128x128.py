@@ -35,7 +35,7 @@ def test_mixed_against_fp64_over_2000_steps_and_oracle_sample(V):
     import torch
     import bench
     w = inputs.vesicle_poiseuille_256x128x128()
-    mixed = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, 1)
+    mixed = bench.make_sim(w, V.VSV_MIXED, bench.BENCH_CYCLES, bench.BENCH_EXTRAPOLATE)
     fp64 = bench.make_sim(w, V.VSV_FP64, 0)
     sp = fp64.solver_params()
     sp.tol = 1e-12
