@@ -81,19 +81,29 @@ __device__ __forceinline__ T prolong_value(T aC, T aX, T bC, T bX, T cC, T cX, T
   return acc;
 }
 
-// Weighted red-black update of one cell from its old value x and its
-// Gauss-Seidel value gs: gs itself for omega = 1, else x + omega (gs - x) as
-// one fused multiply-add (red-black SOR smoothing; an over-relaxed smoother
-// contracts a multigrid V-cycle faster).  The difference gs - x is a
-// separately rounded subtraction (the _rn intrinsics are never contracted
-// into a multiply-add with the product that forms gs), so every kernel
-// rounds the same way.  Every sweep kernel updates its cells through this
-// function, so the fused and per-colour sweeps agree bit for bit.
+// Weighted red-black update of one cell (red-black SOR smoothing; an
+// over-relaxed smoother contracts a multigrid V-cycle faster):
+// x <- x + omega (gs - x) with the Gauss-Seidel value gs = t rc, where
+// t = (neighbour sum) - b h^2 and rc = 1 / diagonal, evaluated as
+// t (omega rc) + (1 - omega) x in one fused multiply-add.  Every sweep
+// kernel forms t with nb_term and updates through relax, with the same
+// rounded constants wrc = omega rc and c1 = 1 - omega, so the fused and
+// per-colour sweeps agree bit for bit; omega = 1 (c1 = 0, wrc = rc) gives
+// the Gauss-Seidel value t rc itself.
 template <class T>
-__device__ __forceinline__ T relax(T x, T gs, T omega) {
-  if (omega == (T)1) return gs;
-  if constexpr (sizeof(T) == 4) return __fmaf_rn(omega, __fsub_rn(gs, x), x);
-  else return __fma_rn(omega, __dsub_rn(gs, x), x);
+__device__ __forceinline__ T nb_term(T s, T b, T h2) {
+  if constexpr (sizeof(T) == 4) return __fmaf_rn(-b, h2, s);
+  else return __fma_rn(-b, h2, s);
+}
+template <class T>
+__device__ __forceinline__ T relax(T x, T t, T wrc, T c1) {
+  if constexpr (sizeof(T) == 4) return __fmaf_rn(t, wrc, __fmul_rn(c1, x));
+  else return __fma_rn(t, wrc, __dmul_rn(c1, x));
+}
+template <class T>
+__device__ __forceinline__ T wscale(T omega, T rc) {
+  if constexpr (sizeof(T) == 4) return __fmul_rn(omega, rc);
+  else return __dmul_rn(omega, rc);
 }
 
 // Right-hand side b = beta * B[c] + S[j + k * ny] (S may be null).

@@ -133,17 +133,19 @@ __global__ void k_update_dw(Comp3<float> XH, Comp3<float> XL, Comp3<float> E, lo
   }
 }
 
-// First guess from the history, in double-word arithmetic, written into the
-// oldest buffer C: order 0: A; 1: 2A - B; 2: 3A - 3B + C (A = x^n, B =
-// x^{n-1}, C = x^{n-2}).
+// First guess from the history, written into the oldest buffer C (A = x^n,
+// B = x^{n-1}, C = x^{n-2}): A plus the extrapolation increment
+// d = 0 (order 0), A - B (order 1: 2A - B) or 2A - 3B + C (order 2:
+// 3A - 3B + C).  Only A must be exact (its two words); d is formed in FP32
+// from the high words, so its rounding, of order u |x|, is an error of the
+// first guess, which the cycles of the solve contract like any other.  The
+// low words of B and C are not read.
 __global__ void k_extrapolate_rot_dw(Comp3<float> AH, Comp3<float> AL, Comp3<float> BH,
-                                     Comp3<float> BL, Comp3<float> CH, Comp3<float> CL, long long n,
-                                     int order) {
+                                     Comp3<float> CH, Comp3<float> CL, long long n, int order) {
   const int comp = blockIdx.y;
   const float* __restrict__ ah = AH.at(comp);
   const float* __restrict__ al = AL.at(comp);
   const float* __restrict__ bh = BH.at(comp);
-  const float* __restrict__ bl = BL.at(comp);
   float* __restrict__ ch = CH.at(comp);
   float* __restrict__ cl = CL.at(comp);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
@@ -151,10 +153,9 @@ __global__ void k_extrapolate_rot_dw(Comp3<float> AH, Comp3<float> AL, Comp3<flo
     const FF a{ah[t], al[t]};
     FF v = a;
     if (order == 1) {
-      v = ff_add(FF{2.f * a.hi, 2.f * a.lo}, ff_neg(FF{bh[t], bl[t]}));
+      v = ff_add_f(a, a.hi - bh[t]);
     } else if (order == 2) {
-      const FF d = ff_add(a, ff_neg(FF{bh[t], bl[t]}));   // A - B
-      v = ff_add(ff_mul_f(d, 3.f), FF{ch[t], cl[t]});
+      v = ff_add_f(a, __fmaf_rn(2.f, a.hi, __fmaf_rn(-3.f, bh[t], ch[t])));
     }
     ch[t] = v.hi;
     cl[t] = v.lo;
@@ -457,9 +458,10 @@ void launch_extrapolate_rot_dw(Ctx& cx, Comp3<float> AH, Comp3<float> AL, Comp3<
   const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
-  k_extrapolate_rot_dw<<<grid, kBlock, 0, cx.stream>>>(AH, AL, BH, BL, CH, CL, n, order);
-  // the history words read (A; A, B; A, B, C), the guess written (two words each)
-  cx.after(-1, 8.0 * (double)(order + 2) * (double)n * ncomp);
+  k_extrapolate_rot_dw<<<grid, kBlock, 0, cx.stream>>>(AH, AL, BH, CH, CL, n, order);
+  // read: A's two words and the high words of B (order >= 1) and C (order
+  // 2); written: the guess's two words
+  cx.after(-1, (16.0 + 4.0 * (double)order) * (double)n * ncomp);
 }
 
 void launch_axpy_dw(Ctx& cx, Comp3<float> YH, Comp3<float> YL, Comp3<float> XH, Comp3<float> XL,

@@ -139,8 +139,7 @@ __global__ void k_rb_sweep(Level L, Comp3<T> X, Rhs3<T> R, int color, T omega, T
   int nwall;
   const T s = sum_nb(x, L, i, j, k, c, nwall);
   const T b = rhs_at(R, comp, c, j, k, ny);
-  const T gs = (s - b * h2) * lv_rc<T>(L, nwall);
-  x[c] = relax(x[c], gs, omega);
+  x[c] = relax(x[c], nb_term(s, b, h2), wscale(omega, lv_rc<T>(L, nwall)), (T)1 - omega);
 }
 
 // Residual of the fine (or any) level, restricted to the next coarser level
@@ -286,7 +285,7 @@ __global__ void k_coarse_solve(Level L, Comp3<T> E, Comp3<T> RR, int sweeps, T h
         const int t = (k * ny + j) * nx + i;
         int nwall;
         const T sum = sum_nb(e, L, i, j, k, t, nwall);
-        e[t] = (sum - rs[t] * h2) * lv_rc<T>(L, nwall);
+        e[t] = relax(e[t], nb_term(sum, rs[t], h2), lv_rc<T>(L, nwall), (T)0);
       }
       __syncthreads();
     }
@@ -531,7 +530,8 @@ __device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2, T o
         const int t = (k * ny + j) * nx + i;
         int nwall;
         const T sum = sum_nb(e, L, i, j, k, t, nwall);
-        e[t] = relax(e[t], (sum - r[t] * h2) * lv_rc<T>(L, nwall), omega);
+        e[t] = relax(e[t], nb_term(sum, r[t], h2), wscale(omega, lv_rc<T>(L, nwall)),
+                     (T)1 - omega);
       }
       __syncthreads();
     }
@@ -761,8 +761,8 @@ __device__ void lc_sweep(const LowerCycle<T>& P, int l, int color, bool first, T
       const int blk = red ^ 1;
       if (red < nx) {
         const long long c = row + red;
-        const T gs = ((T)0 - b[c] * h2) * lv_rc<T>(L, wall_count(L, red, w.j, w.k));
-        x[c] = relax((T)0, gs, omega);
+        x[c] = relax((T)0, nb_term((T)0, b[c], h2),
+                     wscale(omega, lv_rc<T>(L, wall_count(L, red, w.j, w.k))), (T)1 - omega);
       }
       if (blk < nx) x[row + blk] = (T)0;
       continue;
@@ -771,8 +771,7 @@ __device__ void lc_sweep(const LowerCycle<T>& P, int l, int color, bool first, T
     const long long c = row + red;
     int nwall;
     const T sn = sum_nb(x, L, red, w.j, w.k, c, nwall);
-    const T gs = (sn - b[c] * h2) * lv_rc<T>(L, nwall);
-    x[c] = relax(x[c], gs, omega);
+    x[c] = relax(x[c], nb_term(sn, b[c], h2), wscale(omega, lv_rc<T>(L, nwall)), (T)1 - omega);
   }
 }
 

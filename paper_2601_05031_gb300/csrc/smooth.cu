@@ -35,10 +35,12 @@ constexpr int kStageA = (kRA * kNV + kThreads - 1) / kThreads;   // vectors per 
 constexpr int kStageB = (kRB * kNV + kThreads - 1) / kThreads;
 
 struct FusedGeom : Geom {
-  float rc0, rc1, rc2;   // 1 / (6 + alpha * nwall) for nwall = 0, 1, 2 (Level::rcf)
+  // omega / (6 + alpha * nwall) for nwall = 0, 1, 2: the relaxation weight
+  // times Level::rcf, rounded as relax() expects
+  float rc0, rc1, rc2;
   float h2;
   float beta;            // b = beta * B + S
-  float omega;           // relaxation weight (1: Gauss-Seidel)
+  float c1;              // 1 - omega
 };
 
 // nwall is at most 2 on a tile-aligned level (ny >= 16 and nz >= 2 keep the
@@ -55,19 +57,19 @@ __device__ __forceinline__ float rc_of(const FusedGeom& G, int nwall) {
 // (z- + z+), as in the per-colour kernel.
 __device__ __forceinline__ float4 rb_group(float4 V, float4 U, float4 D, float4 M, float4 P, float Lx,
                                            float Rx, float4 Bv, int par, float beta, float S,
-                                           float h2, float rc, float omega) {
+                                           float h2, float wrc, float c1) {
   if (par == 0) {
     const float b0 = beta * Bv.x + S, b2 = beta * Bv.z + S;
     const float s0 = ((Lx + V.y) + (U.x + D.x)) + (M.x + P.x);
     const float s2 = ((V.y + V.w) + (U.z + D.z)) + (M.z + P.z);
-    V.x = relax(V.x, (s0 - b0 * h2) * rc, omega);
-    V.z = relax(V.z, (s2 - b2 * h2) * rc, omega);
+    V.x = relax(V.x, nb_term(s0, b0, h2), wrc, c1);
+    V.z = relax(V.z, nb_term(s2, b2, h2), wrc, c1);
   } else {
     const float b1 = beta * Bv.y + S, b3 = beta * Bv.w + S;
     const float s1 = ((V.x + V.z) + (U.y + D.y)) + (M.y + P.y);
     const float s3 = ((V.z + Rx) + (U.w + D.w)) + (M.w + P.w);
-    V.y = relax(V.y, (s1 - b1 * h2) * rc, omega);
-    V.w = relax(V.w, (s3 - b3 * h2) * rc, omega);
+    V.y = relax(V.y, nb_term(s1, b1, h2), wrc, c1);
+    V.w = relax(V.w, nb_term(s3, b3, h2), wrc, c1);
   }
   return V;
 }
@@ -114,7 +116,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   const int x0 = tx * kTX, y0 = tyb * kTY;
   const int zb = blockIdx.y * G.zchunk;
   const int ze = min(zb + G.zchunk, G.nz);
-  const float beta = G.beta, h2 = G.h2, om = G.omega;
+  const float beta = G.beta, h2 = G.h2, c1 = G.c1;
   const int tid = threadIdx.x, gx = tid & 31, ty = tid >> 5;
   const int q = gx + 1;                    // own float4 group (staged columns 4q .. 4q+3)
 
@@ -270,10 +272,10 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         const float4 M0 = MM[0];
         if (upd_row[0])
           MM[0] = rb_group(MM[0], U0, MM[1], MMM[0], M[0], Lq[0], Rq[0], Bq0, par, beta,
-                           srow(jown[0], qp), h2, zw ? rco[0][1] : rco[0][0], om);
+                           srow(jown[0], qp), h2, zw ? rco[0][1] : rco[0][0], c1);
         if (upd_row[1])
           MM[1] = rb_group(MM[1], M0, D1, MMM[1], M[1], Lq[1], Rq[1], Bq1, 1 - par, beta,
-                           srow(jown[1], qp), h2, zw ? rco[1][1] : rco[1][0], om);
+                           srow(jown[1], qp), h2, zw ? rco[1][1] : rco[1][0], c1);
       }
     };
     auto black_store = [&]() {
@@ -327,12 +329,12 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         const float sr = srow(jown[h], p), rc = zw ? rco[h][1] : rco[h][0];
         float* dst = cA + rown[h] * kW + 4 * q;
         if ((h == 0 ? par : 1 - par) == 0) {
-          V[h].x = relax(0.f, (0.f - (beta * Bv.x + sr) * h2) * rc, om);
-          V[h].z = relax(0.f, (0.f - (beta * Bv.z + sr) * h2) * rc, om);
+          V[h].x = relax(0.f, nb_term(0.f, beta * Bv.x + sr, h2), rc, c1);
+          V[h].z = relax(0.f, nb_term(0.f, beta * Bv.z + sr, h2), rc, c1);
           dst[0] = V[h].x; dst[2] = V[h].z;
         } else {
-          V[h].y = relax(0.f, (0.f - (beta * Bv.y + sr) * h2) * rc, om);
-          V[h].w = relax(0.f, (0.f - (beta * Bv.w + sr) * h2) * rc, om);
+          V[h].y = relax(0.f, nb_term(0.f, beta * Bv.y + sr, h2), rc, c1);
+          V[h].w = relax(0.f, nb_term(0.f, beta * Bv.w + sr, h2), rc, c1);
           dst[1] = V[h].y; dst[3] = V[h].w;
         }
       }
@@ -345,11 +347,11 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
           const float sr = srow(j, p), rc = rc_of(G, jw + zw);
           float* dst = cA + r * kW + 4 * q;
           if (((j + p) & 1) == 0) {
-            dst[0] = relax(0.f, (0.f - (beta * Bv.x + sr) * h2) * rc, om);
-            dst[2] = relax(0.f, (0.f - (beta * Bv.z + sr) * h2) * rc, om);
+            dst[0] = relax(0.f, nb_term(0.f, beta * Bv.x + sr, h2), rc, c1);
+            dst[2] = relax(0.f, nb_term(0.f, beta * Bv.z + sr, h2), rc, c1);
           } else {
-            dst[1] = relax(0.f, (0.f - (beta * Bv.y + sr) * h2) * rc, om);
-            dst[3] = relax(0.f, (0.f - (beta * Bv.w + sr) * h2) * rc, om);
+            dst[1] = relax(0.f, nb_term(0.f, beta * Bv.y + sr, h2), rc, c1);
+            dst[3] = relax(0.f, nb_term(0.f, beta * Bv.w + sr, h2), rc, c1);
           }
         }
       }
@@ -362,7 +364,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         if ((G.per_y || (j >= 0 && j < G.ny)) && (((x + j + p) & 1) == 0)) {
           const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
           const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
-          cA[r * kW + c] = relax(0.f, (0.f - bb * h2) * rc_of(G, jw + zw), om);
+          cA[r * kW + c] = relax(0.f, nb_term(0.f, bb, h2), rc_of(G, jw + zw), c1);
         }
       }
     };
@@ -392,10 +394,10 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         const float4 V0 = V[0];
         if (upd_row[0])
           V[0] = rb_group(V[0], U0, V[1], M[0], P[0], Lx[0], Rx[0], B0, par, beta, srow(jown[0], p),
-                          h2, zw ? rco[0][1] : rco[0][0], om);
+                          h2, zw ? rco[0][1] : rco[0][0], c1);
         if (upd_row[1])
           V[1] = rb_group(V[1], V0, D1, M[1], P[1], Lx[1], Rx[1], B1, 1 - par, beta, srow(jown[1], p),
-                          h2, zw ? rco[1][1] : rco[1][0], om);
+                          h2, zw ? rco[1][1] : rco[1][0], c1);
         {
           float* dst = cA + rown[0] * kW + 4 * q;
           if (upd_row[0]) {
@@ -421,7 +423,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
             const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
             const int par = (j + p) & 1;
             const float4 Vn = rb_group(Vh, U, D, Mh, Ph, Lx, Rx, Bv, par, beta, srow(j, p), h2,
-                                       rc_of(G, jw + zw), om);
+                                       rc_of(G, jw + zw), c1);
             float* dst = cA + r * kW + 4 * q;
             if (par == 0) { dst[0] = Vn.x; dst[2] = Vn.z; }
             else { dst[1] = Vn.y; dst[3] = Vn.w; }
@@ -439,7 +441,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
             const float s = ((cA[id - 1] + cA[id + 1]) + (cA[id - kW] + cA[id + kW])) +
                             (slotA(p - 1)[id] + slotA(p + 1)[id]);
             const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
-            cA[id] = relax(cA[id], (s - bb * h2) * rc_of(G, jw + zw), om);
+            cA[id] = relax(cA[id], nb_term(s, bb, h2), rc_of(G, jw + zw), c1);
           }
         }
       }
@@ -540,12 +542,13 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   // planes let the small levels spread over more SMs
   if (zchunk <= 0) zchunk = pick_zchunk(L, ncomp, 2 * cx.sms, 3, 4);
   G.zchunk = std::min(zchunk, L.n[2]);
-  G.rc0 = L.rcf[0];
-  G.rc1 = L.rcf[1];
-  G.rc2 = L.rcf[2];
+  // omega rc and 1 - omega rounded in FP32 as relax() and wscale() form them
+  G.rc0 = omega * L.rcf[0];
+  G.rc1 = omega * L.rcf[1];
+  G.rc2 = omega * L.rcf[2];
+  G.c1 = 1.f - omega;
   G.h2 = (float)(1.0 / L.inv_h2);
   G.beta = R.beta;
-  G.omega = omega;
   const int nzc = (L.n[2] + G.zchunk - 1) / G.zchunk;
   dim3 grid(G.ntx * G.nty, nzc, ncomp);
   const bool hs = R.S[0] != nullptr;
