@@ -358,9 +358,10 @@ vsv_status vsv_volume_area_static(const double* phi, int nx, int ny, int nz, dou
                                   int z_periodic, double* out, void* cuda_stream);
 
 /* Synchronise the stream and report deferred kernel errors / flags: a
- * non-finite phi (VSV_ENONFINITE), or a grid barrier of the single-launch
- * lower V-cycle whose wait ran out (VSV_ECUDA; every such wait gives up
- * after about a second, so no launch can hang; the flag stays set). */
+ * non-finite phi (VSV_ENONFINITE), a grid barrier of the single-launch lower
+ * V-cycle whose wait ran out, or a fused smoothing sweep whose staged planes
+ * did not arrive in time (VSV_ECUDA; every such wait gives up after about a
+ * second, so no launch can hang; the flag stays set). */
 vsv_status vsv_check(vsv_grid* g);
 
 /* Check of the bounded grid barrier that the single-launch lower V-cycle
@@ -376,6 +377,21 @@ vsv_status vsv_check(vsv_grid* g);
  * clears again before returning; it touches no field. */
 vsv_status vsv_barrier_check(vsv_grid* g, int blocks, int rounds, int extra_arrivals,
                              double limit_ms);
+
+/* Check of the bounded waits of the fused smoothing sweep for its staged
+ * planes (the paper has no counterpart; this serves tests).  On tile-aligned
+ * mixed-precision grids (nx a multiple of 128, ny of 16) the sweep stages
+ * rows of x and of the right-hand side by bulk copies whose arrival a
+ * shared-memory barrier counts in bytes.  This runs one such sweep on the
+ * grid's finest-level scratch buffers with every copy group expecting
+ * probe_bytes bytes (a multiple of 16, 16 .. 524288) that no copy delivers:
+ * every wait runs out after limit_ms milliseconds, the kernel sets a flag bit
+ * and returns.  Synchronises.  Returns VSV_ECUDA (the timeout message) when
+ * the waits ran out, as they must; VSV_EINVAL for bad arguments or a grid
+ * the sweep does not serve.  It clears the flag bit again before returning;
+ * the scratch buffers' contents are not defined afterwards (every solve
+ * rewrites them), no field is touched. */
+vsv_status vsv_copy_wait_check(vsv_grid* g, int probe_bytes, double limit_ms);
 
 /* Message of the last failure on this handle ("" if none); the pointer stays
  * valid until the next call on the handle. */

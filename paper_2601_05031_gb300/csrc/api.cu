@@ -254,12 +254,15 @@ vsv_status fail(vsv_grid* g, vsv_status s, const char* fmt, const char* detail =
 }
 
 // Status of the device flag word: bit 1 non-finite phi, bit kSyncTimeout a
-// grid barrier of the persistent V-cycle whose wait ran out (its
-// correction is then unusable; the flag stays set).
+// grid barrier of the persistent V-cycle whose wait ran out, bit
+// kCopyTimeout a fused sweep whose staged planes did not arrive in time
+// (the sweep's result is then unusable; the flag stays set).
 vsv_status flag_status(vsv_grid* g, int flag) {
   if (flag & 1) return fail(g, VSV_ENONFINITE, "non-finite phi%s");
   if (flag & kSyncTimeout)
     return fail(g, VSV_ECUDA, "a grid barrier of the persistent multigrid launch ran out of time%s");
+  if (flag & kCopyTimeout)
+    return fail(g, VSV_ECUDA, "a wait of the fused sweep for its staged planes ran out of time%s");
   return VSV_OK;
 }
 
@@ -1323,6 +1326,7 @@ vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int prec
       g->cx.sms = sms;
   }
   carve(nx, ny, nz, precision, g, g->ws);
+  g->cx.status = &g->S->nonfinite;
   g->flow = vsv_flow_params{VSV_QUIESCENT, 0.0, 0.0, 0.0, 1.0, 0.0};
   g->fe = vsv_fe_params{VSV_CAHN_HILLIARD, 1.0, 0.0, 1.0, 1.0, 0.0, 0.0, 0};
   default_solver(&g->sol, precision);
@@ -2098,6 +2102,30 @@ vsv_status vsv_barrier_check(vsv_grid* g, int blocks, int rounds, int extra_arri
     const int cleared = flag & ~kSyncTimeout;
     CK(cudaMemcpy(&g->S->nonfinite, &cleared, sizeof(int), cudaMemcpyHostToDevice));
     return flag_status(g, kSyncTimeout);
+  }
+  return VSV_OK;
+}
+
+vsv_status vsv_copy_wait_check(vsv_grid* g, int probe_bytes, double limit_ms) {
+  if (!g || probe_bytes < 16 || probe_bytes > (1 << 19) || probe_bytes % 16 || !(limit_ms > 0) ||
+      limit_ms > 1e4)
+    return VSV_EINVAL;
+  if (g->prec != VSV_MIXED || !g->mg_t[0][0] || !g->r0[0])
+    return fail(g, VSV_EINVAL, "the fused sweep runs on mixed-precision grids only%s");
+  const int per[3] = {1, 0, 1};
+  const std::vector<Level> lv = build_levels(g->nx, g->ny, g->nz, g->h, per, 1, 1);
+  const Comp3<float> B{{(float*)g->mg_t[0][0], nullptr, nullptr}};
+  const Rhs3<float> R{{(const float*)g->r0[0], nullptr, nullptr}, {nullptr, nullptr, nullptr}, 1.f};
+  if (!launch_copy_wait_probe(g->cx, lv[0], B, R, (unsigned)probe_bytes,
+                              (unsigned long long)(limit_ms * 1e6)))
+    return fail(g, VSV_EINVAL, "copy wait check: the grid is not tile-aligned or the launch failed%s");
+  CK(cudaStreamSynchronize(g->cx.stream));
+  int flag = 0;
+  CK(cudaMemcpy(&flag, &g->S->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag & kCopyTimeout) {
+    const int cleared = flag & ~kCopyTimeout;
+    CK(cudaMemcpy(&g->S->nonfinite, &cleared, sizeof(int), cudaMemcpyHostToDevice));
+    return flag_status(g, kCopyTimeout);
   }
   return VSV_OK;
 }

@@ -106,6 +106,14 @@ __device__ __forceinline__ T wscale(T omega, T rc) {
   else return __dmul_rn(omega, rc);
 }
 
+// The GPU's global timer in nanoseconds (bounds of every wait on other
+// threads, CTAs or copies).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Right-hand side b = beta * B[c] + S[j + k * ny] (S may be null).
 template <class T>
 struct Rhs3 {

@@ -10,6 +10,15 @@
 
 namespace vsv {
 
+// An encoded TMA tensor map (the driver's opaque 128-byte object) of one
+// FP32 field of extent n[0] x n[1] x n[2] with boxes of kTX x rows x 1.
+struct TensorMapEntry {
+  const void* ptr;
+  int n[3];
+  int rows;
+  alignas(64) unsigned char map[128];
+};
+
 // Launch context: the caller's stream, a launch counter and optional CUDA
 // event brackets around every launch of one kernel class.
 struct Ctx {
@@ -17,6 +26,8 @@ struct Ctx {
   int sms = 148;                 // multiprocessors of the grid's device (set at create)
   int tiled = 1;                 // use the tiled transfer kernels (solver variants 0 and 2)
   int ragged = 1;                // also with partial edge tiles (solver variant 0)
+  int* status = nullptr;         // device flag word (bounded waits report timeouts here)
+  std::vector<TensorMapEntry> tmaps;   // tensor maps encoded so far (fields do not move)
   long long launches = 0;
   int prof_class = -1;
   std::vector<cudaEvent_t> ev;   // pairs (start, stop)
@@ -138,6 +149,9 @@ bool launch_coarse_vcycle(Ctx& cx, const CoarseCycle& CC, Comp3<T> E, Comp3<T> R
 // nanoseconds (the global timer); extra: arrivals expected beyond the
 // grid's CTAs per barrier (0; a test sets it to make the wait run out).
 constexpr int kSyncTimeout = 2;
+// bit of the same word set when a wait of the fused sweep for its staged
+// planes (bulk copies) exceeded one second
+constexpr int kCopyTimeout = 4;
 constexpr unsigned long long kSyncLimitNs = 1000000000ull;   // 1 s
 struct GridBarrier {
   unsigned* count;
@@ -201,6 +215,10 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
                        int ncomp, int zchunk, int kclass, bool zero_in,
                        const Comp3<float>* upd_hi = nullptr, const Comp3<float>* upd_lo = nullptr,
                        float omega = 1.f);
+// Check of the bound of the fused sweep's waits for staged planes (no copy
+// issued; every wait gives up after limit_ns): false unless L is tile-aligned.
+bool launch_copy_wait_probe(Ctx& cx, const Level& L, Comp3<float> B, Rhs3<float> R,
+                            unsigned probe_tx, unsigned long long limit_ns);
 
 // ---------------------------------------------------------------- phase-field (phase.cu)
 struct PhaseParams {

@@ -691,12 +691,6 @@ struct StrideWalk {
   }
 };
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Bounded grid barrier (see GridBarrier).  Arrivals count up monotonically
 // from zero (the host zeroes the counter before each launch), so barrier n
 // waits until n * (gridDim.x + extra) arrivals.  Returns false when the

@@ -15,9 +15,20 @@
 // in registers (z-neighbours never touch shared memory); x / y neighbours come
 // from the staged plane in shared memory by 128-bit loads.  Warps 0 and 7
 // also do the red cells of the halo rows, 36 threads the two halo columns.
-// Planes are staged by cp.async (16-byte vectors, zero fill on Dirichlet
-// ghosts, wrap on periodic axes; two steps of copies in flight) into a ring
-// of six x-planes and five rhs planes.
+//
+// Staging (two steps of copies in flight, a ring of six x planes and five
+// rhs planes in shared memory, split layout of tile.cuh: body rows of the
+// tile's 128 columns, then the 4-column halo groups left and right of it):
+// on tile-aligned levels without periodic y the body of a plane is one box
+// of a TMA tensor map (zeros beyond a y or z wall come from the box's
+// out-of-bounds fill), the halo groups -- wrapped around periodic x, which a
+// box cannot do -- are 16-byte cp.async copies; elsewhere every 16-byte
+// vector is a cp.async copy with zero fill on Dirichlet ghosts.
+#include <cuda.h>   // CUtensorMap and the encoder's types; the driver is reached at run time
+
+#include <algorithm>
+#include <cstring>
+
 #include "tile.cuh"
 
 namespace vsv {
@@ -31,8 +42,16 @@ constexpr int kRA = kTY + 2 * kH;        // staged x rows
 constexpr int kRB = kTY + 2 * (kH - 1);  // staged rhs rows
 constexpr int kNA = 6;                   // x-plane ring slots
 constexpr int kNB = 5;                   // rhs-plane ring slots
+// slot sizes (floats): body and halo rows, rounded up to 128 bytes so that
+// every slot can take a box
+constexpr int kSlotA = (kRA * (kTX + kHP) + 31) / 32 * 32;
+constexpr int kSlotB = (kRB * (kTX + kHP) + 31) / 32 * 32;
 constexpr int kStageA = (kRA * kNV + kThreads - 1) / kThreads;   // vectors per thread
 constexpr int kStageB = (kRB * kNV + kThreads - 1) / kThreads;
+constexpr int kIssueTid = 160;           // issues the boxes (warp 5: no halo duties)
+constexpr int kHaloTid = 128;            // first of the 2 kRA + 2 kRB halo-copy threads
+constexpr unsigned kBoxA = kRA * kTX * 4, kBoxB = kRB * kTX * 4;   // bytes per box
+static_assert(kHaloTid + 2 * (kRA + kRB) <= kThreads, "halo copies need a thread each");
 
 struct FusedGeom : Geom {
   // omega / (6 + alpha * nwall) for nwall = 0, 1, 2: the relaxation weight
@@ -41,6 +60,18 @@ struct FusedGeom : Geom {
   float h2;
   float beta;            // b = beta * B + S
   float c1;              // 1 - omega
+  int* status;           // device flag word (kCopyTimeout)
+  unsigned long long limit_ns;   // bound of each wait for staged planes
+  // > 0 only in the check of that bound: every copy group expects this
+  // many bytes and no box is loaded, so each wait runs out
+  unsigned probe_tx;
+};
+
+// tensor maps of the three components' x (boxes of kRA rows) and rhs (kRB
+// rows); unused by the cp.async variant
+struct FusedMaps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
 };
 
 // nwall is at most 2 on a tile-aligned level (ny >= 16 and nz >= 2 keep the
@@ -86,6 +117,9 @@ __device__ __forceinline__ float* ring(float* base, int plane, int slots, int sl
 // UPD: the swept values are not stored to B but added to the double-word
 // iterate, (XH, XL) <- (XH, XL) + e, with the arithmetic of k_update_dw (the
 // last sweep of a correction's V-cycle; e itself is not needed afterwards).
+// RAGGED: partial edge tiles, every staged vector a cp.async copy; else a
+// tile-aligned level without periodic y whose plane bodies are boxes of the
+// tensor maps M.
 //
 // Pipeline: step p updates the red cells of plane p and the black cells of
 // plane p - 2.  The two phases are independent (the black cells need the red
@@ -97,14 +131,19 @@ __device__ __forceinline__ float* ring(float* base, int plane, int slots, int sl
 // red cells of slot p and reads black cells of slots p - 1 .. p + 1, and the
 // black phase reads slot p - 2 plus registers; issuing after the barrier
 // keeps the copies out of the slots of plane p - 3, which the black phase of
-// step p - 1 read (six x and five rhs slots).
+// step p - 1 read (six x and five rhs slots).  The boxes of step group s
+// (the planes step zb - 1 + s needs) are counted on mbarrier s & 1.
 template <bool ZERO_IN, bool HAS_S, bool UPD, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<float> XH,
-             Comp3<float> XL) {
+             Comp3<float> XL, const __grid_constant__ FusedMaps M) {
+  constexpr bool TMA = !RAGGED;
   extern __shared__ float4 smem_f4[];
-  float* sA = reinterpret_cast<float*>(smem_f4);
-  float* sB = sA + kNA * kRA * kW;
+  // boxes land on 128-byte boundaries: align the rings' base
+  float* sA = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_f4) + 127) &
+                                       ~static_cast<uintptr_t>(127));
+  float* sB = sA + kNA * kSlotA;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(sB + kNB * kSlotB);
   const int comp = blockIdx.z;
   const float* __restrict__ a = A.at(comp);
   float* __restrict__ out = B.at(comp);
@@ -116,12 +155,15 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   const int x0 = tx * kTX, y0 = tyb * kTY;
   const int zb = blockIdx.y * G.zchunk;
   const int ze = min(zb + G.zchunk, G.nz);
+  const int sLast = ze - zb + 1;             // last copy group
   const float beta = G.beta, h2 = G.h2, c1 = G.c1;
   const int tid = threadIdx.x, gx = tid & 31, ty = tid >> 5;
-  const int q = gx + 1;                    // own float4 group (staged columns 4q .. 4q+3)
 
-  auto slotA = [&](int plane) { return ring(sA, plane, kNA, kRA * kW); };
-  auto slotB = [&](int plane) { return ring(sB, plane, kNB, kRB * kW); };
+  auto slotA = [&](int plane) { return ring(sA, plane, kNA, kSlotA); };
+  auto slotB = [&](int plane) { return ring(sB, plane, kNB, kSlotB); };
+  // halo row r of an x or rhs slot: [0, kHX) left of the tile, [kHX, kHP) right
+  auto hA = [&](auto* slot, int r) { return halo_row(slot, kRA, r); };
+  auto hB = [&](auto* slot, int r) { return halo_row(slot, kRB, r); };
   auto ghost_plane = [&](int p) { return !G.per_z && (p < 0 || p >= G.nz); };
   auto zwall = [&](int p) { return G.per_z ? 0 : (p == 0) + (p == G.nz - 1); };
   auto srow = [&](int j, int p) -> float {
@@ -130,10 +172,44 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     return S[(G.per_y ? (RAGGED ? modi(j, G.ny) : wrapi(j, G.ny)) : j) + (long long)kk * G.ny];
   };
 
-  StageDesc<kStageA> da;
-  StageDesc<kStageB> db;
-  da.init(G, x0, y0, kH, kRA);
-  db.init(G, x0, y0, kH - 1, kRB);
+  // cp.async vectors of this thread: whole planes (RAGGED) or one halo group
+  // of an x or rhs row (threads kHaloTid ..)
+  SplitDesc<kStageA> da;
+  SplitDesc<kStageB> db;
+  if constexpr (RAGGED) {
+    da.init(G, x0, y0, kH, kRA);
+    db.init(G, x0, y0, kH - 1, kRB);
+  } else {
+    da.init_halo(G, tid - kHaloTid, x0, y0, kH, kRA);
+    db.init_halo(G, tid - kHaloTid - 2 * kRA, x0, y0, kH - 1, kRB);
+  }
+  auto stage_vectors = [&](int pa, int na, int pb) {
+    if constexpr (!ZERO_IN)
+      for (int i = 0; i < na; ++i) da.stage(slotA(pa + i), a, G, pa + i);
+    db.stage(slotB(pb), bsrc, G, pb);
+  };
+  // boxes of copy group grp: x planes pa .. pa + na - 1, rhs plane pb (one
+  // thread; planes beyond a z wall lie outside the tensor and read as zero)
+  auto tma_issue = [&](int grp, int pa, int na, int pb) {
+    unsigned long long* bar = &bars[grp & 1];
+    if (G.probe_tx) {
+      mbar_arrive_expect_tx(bar, G.probe_tx);
+      return;
+    }
+    mbar_arrive_expect_tx(bar, (unsigned)na * kBoxA + kBoxB);
+    for (int i = 0; i < na; ++i)
+      tma_load_3d(slotA(pa + i), &M.a[comp], x0, y0 - kH, G.per_z ? wrapi(pa + i, G.nz) : pa + i,
+                  bar);
+    tma_load_3d(slotB(pb), &M.b[comp], x0, y0 - (kH - 1), G.per_z ? wrapi(pb, G.nz) : pb, bar);
+  };
+  // after a wait that ran out: boxes of groups grp and grp + 1 may still be
+  // in flight into this CTA's shared memory, and this thread's cp.async copies
+  auto bail = [&](int grp) {
+    cp_async_wait0();
+    if (tid == 0)
+      for (int g = grp; g <= grp + 1 && g <= sLast; ++g)
+        mbar_drain(&bars[g & 1], (g >> 1) & 1, G.limit_ns);
+  };
 
   // own rows (2 ty and 2 ty + 1: each is the other's y neighbour, straight
   // from registers) and their 1 / diagonal for z-interior (0) and z-wall (1)
@@ -157,6 +233,13 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     rco[h][1] = rc_of(G, yw + 1);
   }
 
+  if constexpr (TMA) {
+    if (tid == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      fence_mbar_init();
+    }
+  }
   // ZERO_IN: x is not staged at all.  The ring is zeroed once; afterwards
   // only red positions of in-range cells are ever written (the ring length 6
   // is even, so a slot position keeps its colour), and within a plane no red
@@ -166,30 +249,36 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   // as zero in registers (their slots hold an earlier plane's red values).
   if constexpr (ZERO_IN) {
     float4* a4 = reinterpret_cast<float4*>(sA);
-    for (int t = tid; t < kNA * kRA * kW / 4; t += kThreads) a4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = tid; t < kNA * kSlotA / 4; t += kThreads) a4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  if constexpr (TMA) __syncthreads();   // initialised barriers before the first box
   // prologue: group 0 = x planes zb-2 .. zb, rhs plane zb-1 (step zb-1);
   // group 1 = x plane zb+1, rhs plane zb (step zb)
-  if constexpr (!ZERO_IN) {
-    da.stage(slotA(zb - 2), a, G, zb - 2, false);
-    da.stage(slotA(zb - 1), a, G, zb - 1, false);
-    da.stage(slotA(zb), a, G, zb, false);
-  }
-  db.stage(slotB(zb - 1), bsrc, G, zb - 1, false);
+  if constexpr (TMA)
+    if (tid == kIssueTid) tma_issue(0, zb - 2, ZERO_IN ? 0 : 3, zb - 1);
+  stage_vectors(zb - 2, 3, zb - 1);
   cp_async_commit();
-  if constexpr (!ZERO_IN) da.stage(slotA(zb + 1), a, G, zb + 1, false);
-  db.stage(slotB(zb), bsrc, G, zb, false);
+  if constexpr (TMA)
+    if (tid == kIssueTid) tma_issue(1, zb + 1, ZERO_IN ? 0 : 1, zb);
+  stage_vectors(zb + 1, 1, zb);
   cp_async_commit();
   cp_async_wait1();
-  __syncthreads();
+  if constexpr (TMA) {
+    if (!mbar_wait_cta(&bars[0], 0u, G.status, G.limit_ns)) {
+      bail(0);
+      return;
+    }
+  } else {
+    __syncthreads();
+  }
   // register pipeline: MMM = plane p-3, MM = p-2, M = p-1, V = p, P = p+1
   // (own groups); rotated at the top of every step
-  float4 MMM[2], MM[2], M[2], V[2], P[2];
+  float4 MMM[2], MM[2], M_[2], V[2], P[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    V[h] = lds4(slotA(zb - 2) + rown[h] * kW + 4 * q);
-    P[h] = lds4(slotA(zb - 1) + rown[h] * kW + 4 * q);
-    M[h] = V[h];
+    V[h] = lds4(slotA(zb - 2) + rown[h] * kTX + 4 * gx);
+    P[h] = lds4(slotA(zb - 1) + rown[h] * kTX + 4 * gx);
+    M_[h] = V[h];
     MM[h] = V[h];
     MMM[h] = V[h];
   }
@@ -216,10 +305,26 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     // planes p - 3 (x) and p - 3 (rhs), last read by the black phase of step
     // p - 1, are free for the copies this step issues
     cp_async_wait1();
-    __syncthreads();
+    if constexpr (TMA) {
+      // this thread's earlier shared-memory writes (red values) are ordered
+      // before the boxes loaded after the barrier
+      fence_proxy_async();
+      const int grp = p - zb + 1;
+      if (grp <= sLast) {
+        if (!mbar_wait_cta(&bars[grp & 1], (unsigned)(grp >> 1) & 1u, G.status, G.limit_ns)) {
+          bail(grp);
+          return;
+        }
+      } else {
+        __syncthreads();
+      }
+    } else {
+      __syncthreads();
+    }
     if (p + 2 <= ze) {
-      if constexpr (!ZERO_IN) da.stage(slotA(p + 3), a, G, p + 3, false);
-      db.stage(slotB(p + 2), bsrc, G, p + 2, false);
+      if constexpr (TMA)
+        if (tid == kIssueTid) tma_issue(p - zb + 3, p + 3, ZERO_IN ? 0 : 1, p + 2);
+      stage_vectors(p + 3, 1, p + 2);
     }
     cp_async_commit();
     float* cA = slotA(p);
@@ -227,13 +332,13 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       MMM[h] = MM[h];
-      MM[h] = M[h];
-      M[h] = V[h];
+      MM[h] = M_[h];
+      M_[h] = V[h];
       V[h] = P[h];
       // ZERO_IN: the black values of plane p + 1 are zero and its red ones
       // are written by the red phase of the next step before any read
       P[h] = (ZERO_IN || p > ze) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                 : lds4(slotA(p + 1) + rown[h] * kW + 4 * q);
+                                 : lds4(slotA(p + 1) + rown[h] * kTX + 4 * gx);
     }
     // the black phase's operands from shared memory: the y neighbours of
     // the two rows, their rhs groups and, at the tile edges, the x halo
@@ -245,13 +350,13 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         const float* cBq = slotB(qp);
   #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          Le[h] = gx == 0 ? cAq[rown[h] * kW + kHX - 1] : 0.f;
-          Re[h] = gx == 31 ? cAq[rown[h] * kW + kHX + kTX] : 0.f;
+          Le[h] = gx == 0 ? hA(cAq, rown[h])[kHX - 1] : 0.f;
+          Re[h] = gx == 31 ? hA(cAq, rown[h])[kHX] : 0.f;
         }
-        U0 = lds4(cAq + (rown[0] - 1) * kW + 4 * q);
-        D1 = lds4(cAq + (rown[1] + 1) * kW + 4 * q);
-        Bq0 = lds4(cBq + (rown[0] - 1) * kW + 4 * q);
-        Bq1 = lds4(cBq + (rown[1] - 1) * kW + 4 * q);
+        U0 = lds4(cAq + (rown[0] - 1) * kTX + 4 * gx);
+        D1 = lds4(cAq + (rown[1] + 1) * kTX + 4 * gx);
+        Bq0 = lds4(cBq + (rown[0] - 1) * kTX + 4 * gx);
+        Bq1 = lds4(cBq + (rown[1] - 1) * kTX + 4 * gx);
       }
     };
     auto black_phase = [&]() {
@@ -271,10 +376,10 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         }
         const float4 M0 = MM[0];
         if (upd_row[0])
-          MM[0] = rb_group(MM[0], U0, MM[1], MMM[0], M[0], Lq[0], Rq[0], Bq0, par, beta,
+          MM[0] = rb_group(MM[0], U0, MM[1], MMM[0], M_[0], Lq[0], Rq[0], Bq0, par, beta,
                            srow(jown[0], qp), h2, zw ? rco[0][1] : rco[0][0], c1);
         if (upd_row[1])
-          MM[1] = rb_group(MM[1], M0, D1, MMM[1], M[1], Lq[1], Rq[1], Bq1, 1 - par, beta,
+          MM[1] = rb_group(MM[1], M0, D1, MMM[1], M_[1], Lq[1], Rq[1], Bq1, 1 - par, beta,
                            srow(jown[1], qp), h2, zw ? rco[1][1] : rco[1][0], c1);
       }
     };
@@ -306,13 +411,13 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       if (red) {
   #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          Ler[h] = gx == 0 ? cA[rown[h] * kW + kHX - 1] : 0.f;
-          Rer[h] = gx == 31 ? cA[rown[h] * kW + kHX + kTX] : 0.f;
+          Ler[h] = gx == 0 ? hA(cA, rown[h])[kHX - 1] : 0.f;
+          Rer[h] = gx == 31 ? hA(cA, rown[h])[kHX] : 0.f;
         }
-        U0r = lds4(cA + (rown[0] - 1) * kW + 4 * q);
-        D1r = lds4(cA + (rown[1] + 1) * kW + 4 * q);
-        B0r = lds4(cB + (rown[0] - 1) * kW + 4 * q);
-        B1r = lds4(cB + (rown[1] - 1) * kW + 4 * q);
+        U0r = lds4(cA + (rown[0] - 1) * kTX + 4 * gx);
+        D1r = lds4(cA + (rown[1] + 1) * kTX + 4 * gx);
+        B0r = lds4(cB + (rown[0] - 1) * kTX + 4 * gx);
+        B1r = lds4(cB + (rown[1] - 1) * kTX + 4 * gx);
       }
     };
     // ZERO_IN: every neighbour of a red cell is black and still zero, so the
@@ -327,7 +432,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         if (!upd_row[h]) continue;
         const float4 Bv = h == 0 ? B0r : B1r;
         const float sr = srow(jown[h], p), rc = zw ? rco[h][1] : rco[h][0];
-        float* dst = cA + rown[h] * kW + 4 * q;
+        float* dst = cA + rown[h] * kTX + 4 * gx;
         if ((h == 0 ? par : 1 - par) == 0) {
           V[h].x = relax(0.f, nb_term(0.f, beta * Bv.x + sr, h2), rc, c1);
           V[h].z = relax(0.f, nb_term(0.f, beta * Bv.z + sr, h2), rc, c1);
@@ -343,9 +448,9 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         const int j = y0 - kH + r;
         if (G.per_y || (j >= 0 && j < G.ny)) {
           const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
-          const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
+          const float4 Bv = lds4(cB + (r - 1) * kTX + 4 * gx);
           const float sr = srow(j, p), rc = rc_of(G, jw + zw);
-          float* dst = cA + r * kW + 4 * q;
+          float* dst = cA + r * kTX + 4 * gx;
           if (((j + p) & 1) == 0) {
             dst[0] = relax(0.f, nb_term(0.f, beta * Bv.x + sr, h2), rc, c1);
             dst[2] = relax(0.f, nb_term(0.f, beta * Bv.z + sr, h2), rc, c1);
@@ -358,13 +463,14 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       if (tid >= 32 && tid < 32 + 2 * (kRA - 2)) {   // halo columns x0 - 1 and x0 + kTX
         const int idx = tid - 32;
         const int r = 1 + (idx >> 1);
-        const int c = (idx & 1) ? kHX + kTX : kHX - 1;
+        const int side = idx & 1;                     // 0: x0 - 1, 1: x0 + kTX
+        const int hc = side ? kHX : kHX - 1;          // its place in the halo row
         const int j = y0 - kH + r;
-        const int x = x0 - kHX + c;
+        const int x = side ? x0 + kTX : x0 - 1;
         if ((G.per_y || (j >= 0 && j < G.ny)) && (((x + j + p) & 1) == 0)) {
           const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
-          const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
-          cA[r * kW + c] = relax(0.f, nb_term(0.f, bb, h2), rc_of(G, jw + zw), c1);
+          const float bb = beta * hB(cB, r - 1)[hc] + srow(j, p);
+          hA(cA, r)[hc] = relax(0.f, nb_term(0.f, bb, h2), rc_of(G, jw + zw), c1);
         }
       }
     };
@@ -393,18 +499,18 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         const float4 U0 = U0r, D1 = D1r, B0 = B0r, B1 = B1r;
         const float4 V0 = V[0];
         if (upd_row[0])
-          V[0] = rb_group(V[0], U0, V[1], M[0], P[0], Lx[0], Rx[0], B0, par, beta, srow(jown[0], p),
-                          h2, zw ? rco[0][1] : rco[0][0], c1);
+          V[0] = rb_group(V[0], U0, V[1], M_[0], P[0], Lx[0], Rx[0], B0, par, beta,
+                          srow(jown[0], p), h2, zw ? rco[0][1] : rco[0][0], c1);
         if (upd_row[1])
-          V[1] = rb_group(V[1], V0, D1, M[1], P[1], Lx[1], Rx[1], B1, 1 - par, beta, srow(jown[1], p),
-                          h2, zw ? rco[1][1] : rco[1][0], c1);
+          V[1] = rb_group(V[1], V0, D1, M_[1], P[1], Lx[1], Rx[1], B1, 1 - par, beta,
+                          srow(jown[1], p), h2, zw ? rco[1][1] : rco[1][0], c1);
         {
-          float* dst = cA + rown[0] * kW + 4 * q;
+          float* dst = cA + rown[0] * kTX + 4 * gx;
           if (upd_row[0]) {
             if (par == 0) { dst[0] = V[0].x; dst[2] = V[0].z; }
             else { dst[1] = V[0].y; dst[3] = V[0].w; }
           }
-          dst += kW;
+          dst += kTX;
           if (upd_row[1]) {
             if (par == 0) { dst[1] = V[1].y; dst[3] = V[1].w; }
             else { dst[0] = V[1].x; dst[2] = V[1].z; }
@@ -415,16 +521,18 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
           const int j = y0 - kH + r;
           if (G.per_y || (j >= 0 && j < G.ny)) {
             const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
-            const float* row = cA + r * kW;
-            const float4 Vh = lds4(row + 4 * q), U = lds4(row - kW + 4 * q), D = lds4(row + kW + 4 * q);
-            const float4 Mh = lds4(slotA(p - 1) + r * kW + 4 * q);
-            const float4 Ph = lds4(slotA(p + 1) + r * kW + 4 * q);
-            const float Lx = row[4 * q - 1], Rx = row[4 * q + 4];
-            const float4 Bv = lds4(cB + (r - 1) * kW + 4 * q);
+            const float* row = cA + r * kTX;
+            const float4 Vh = lds4(row + 4 * gx), U = lds4(row - kTX + 4 * gx),
+                         D = lds4(row + kTX + 4 * gx);
+            const float4 Mh = lds4(slotA(p - 1) + r * kTX + 4 * gx);
+            const float4 Ph = lds4(slotA(p + 1) + r * kTX + 4 * gx);
+            const float Lx = gx == 0 ? hA(cA, r)[kHX - 1] : row[4 * gx - 1];
+            const float Rx = gx == 31 ? hA(cA, r)[kHX] : row[4 * gx + 4];
+            const float4 Bv = lds4(cB + (r - 1) * kTX + 4 * gx);
             const int par = (j + p) & 1;
             const float4 Vn = rb_group(Vh, U, D, Mh, Ph, Lx, Rx, Bv, par, beta, srow(j, p), h2,
                                        rc_of(G, jw + zw), c1);
-            float* dst = cA + r * kW + 4 * q;
+            float* dst = cA + r * kTX + 4 * gx;
             if (par == 0) { dst[0] = Vn.x; dst[2] = Vn.z; }
             else { dst[1] = Vn.y; dst[3] = Vn.w; }
           }
@@ -432,16 +540,21 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         if (tid >= 32 && tid < 32 + 2 * (kRA - 2)) {   // halo columns x0 - 1 and x0 + kTX
           const int idx = tid - 32;
           const int r = 1 + (idx >> 1);
-          const int c = (idx & 1) ? kHX + kTX : kHX - 1;
+          const int side = idx & 1;                     // 0: x0 - 1, 1: x0 + kTX
+          const int hc = side ? kHX : kHX - 1;          // its place in the halo row
           const int j = y0 - kH + r;
-          const int x = x0 - kHX + c;
+          const int x = side ? x0 + kTX : x0 - 1;
           if ((G.per_y || (j >= 0 && j < G.ny)) && (((x + j + p) & 1) == 0)) {
             const int jw = G.per_y ? 0 : (j == 0) + (j == G.ny - 1);
-            const int id = r * kW + c;
-            const float s = ((cA[id - 1] + cA[id + 1]) + (cA[id - kW] + cA[id + kW])) +
-                            (slotA(p - 1)[id] + slotA(p + 1)[id]);
-            const float bb = beta * cB[(r - 1) * kW + c] + srow(j, p);
-            cA[id] = relax(cA[id], nb_term(s, bb, h2), rc_of(G, jw + zw), c1);
+            float* hr = hA(cA, r);
+            // x - 1 and x + 1: the halo group's inner neighbour and the tile's
+            // edge column
+            const float xm = side ? cA[r * kTX + kTX - 1] : hr[kHX - 2];
+            const float xp = side ? hr[kHX + 1] : cA[r * kTX];
+            const float s = ((xm + xp) + (hA(cA, r - 1)[hc] + hA(cA, r + 1)[hc])) +
+                            (hA(slotA(p - 1), r)[hc] + hA(slotA(p + 1), r)[hc]);
+            const float bb = beta * hB(cB, r - 1)[hc] + srow(j, p);
+            hr[hc] = relax(hr[hc], nb_term(s, bb, h2), rc_of(G, jw + zw), c1);
           }
         }
       }
@@ -493,12 +606,83 @@ bool fused_sweep_ok(const Level& L, bool ragged) {
   return ragged && ragged_ok(L) && tile_fill(L) >= 0.25 && L.cells() >= (1 << 17);
 }
 
-size_t fused_sweep_smem() { return (size_t)(kNA * kRA + kNB * kRB) * kW * sizeof(float); }
+// the two rings, two mbarriers and the slack that aligns the rings to 128 bytes
+size_t fused_sweep_smem() {
+  return (size_t)(kNA * kSlotA + kNB * kSlotB) * sizeof(float) + 2 * sizeof(unsigned long long) +
+         128;
+}
+
+namespace {
+
+static_assert(sizeof(CUtensorMap) == sizeof(TensorMapEntry::map), "opaque tensor map size");
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library); null if unavailable
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of the FP32 field `ptr` of level L (x fastest, then y, then z)
+// with boxes of kTX x rows x 1, zero fill outside; encoded once per context
+// (the grid's fields never move).  False if it cannot be encoded.
+bool field_map(Ctx& cx, const float* ptr, const Level& L, int rows, CUtensorMap* out) {
+  for (const TensorMapEntry& e : cx.tmaps)
+    if (e.ptr == ptr && e.rows == rows && e.n[0] == L.n[0] && e.n[1] == L.n[1] && e.n[2] == L.n[2]) {
+      std::memcpy(out, e.map, sizeof(CUtensorMap));
+      return true;
+    }
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc || !ptr || (reinterpret_cast<uintptr_t>(ptr) & 15)) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)L.n[0], (cuuint64_t)L.n[1], (cuuint64_t)L.n[2]};
+  const cuuint64_t strides[2] = {(cuuint64_t)L.n[0] * 4, (cuuint64_t)L.n[0] * L.n[1] * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)kTX, (cuuint32_t)rows, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  TensorMapEntry e{};
+  e.ptr = ptr;
+  e.n[0] = L.n[0]; e.n[1] = L.n[1]; e.n[2] = L.n[2];
+  e.rows = rows;
+  CUtensorMap m;
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(ptr), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  std::memcpy(e.map, &m, sizeof(CUtensorMap));
+  if (cx.tmaps.size() >= 512) cx.tmaps.clear();   // bounded (a handful of fields per level)
+  cx.tmaps.push_back(e);
+  *out = m;
+  return true;
+}
+
+// tensor maps for a launch of the TMA variant (x unless zero_in, rhs)
+bool fused_maps(Ctx& cx, const Level& L, Comp3<float> A, Rhs3<float> R, int ncomp, bool zero_in,
+                FusedMaps* M) {
+  for (int c = 0; c < ncomp; ++c) {
+    if (!zero_in && !field_map(cx, A.at(c), L, kRA, &M->a[c])) return false;
+    if (!field_map(cx, R.b_at(c), L, kRB, &M->b[c])) return false;
+  }
+  return true;
+}
 
 template <bool Z, bool HS, bool U, bool RG>
-static void launch_variant(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G,
-                           Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<float> XH,
-                           Comp3<float> XL) {
+void launch_variant(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G, Comp3<float> A,
+                    Comp3<float> B, Rhs3<float> R, Comp3<float> XH, Comp3<float> XL,
+                    const FusedMaps& M) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_rbgs_fused<Z, HS, U, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -507,33 +691,26 @@ static void launch_variant(dim3 grid, size_t smem, cudaStream_t s, const FusedGe
                          100);
     attr_set = true;
   }
-  k_rbgs_fused<Z, HS, U, RG><<<grid, kThreads, smem, s>>>(G, A, B, R, XH, XL);
+  k_rbgs_fused<Z, HS, U, RG><<<grid, kThreads, smem, s>>>(G, A, B, R, XH, XL, M);
 }
 
 template <bool RG>
-static void launch_pick(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G, Comp3<float> A,
-                        Comp3<float> B, Rhs3<float> R, Comp3<float> XH, Comp3<float> XL, bool upd,
-                        bool zero_in, bool hs) {
+void launch_pick(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G, Comp3<float> A,
+                 Comp3<float> B, Rhs3<float> R, Comp3<float> XH, Comp3<float> XL,
+                 const FusedMaps& M, bool upd, bool zero_in, bool hs) {
   if (upd) {
-    if (hs) launch_variant<false, true, true, RG>(grid, smem, s, G, A, B, R, XH, XL);
-    else launch_variant<false, false, true, RG>(grid, smem, s, G, A, B, R, XH, XL);
+    if (hs) launch_variant<false, true, true, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
+    else launch_variant<false, false, true, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
   } else if (zero_in) {
-    if (hs) launch_variant<true, true, false, RG>(grid, smem, s, G, A, B, R, XH, XL);
-    else launch_variant<true, false, false, RG>(grid, smem, s, G, A, B, R, XH, XL);
+    if (hs) launch_variant<true, true, false, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
+    else launch_variant<true, false, false, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
   } else {
-    if (hs) launch_variant<false, true, false, RG>(grid, smem, s, G, A, B, R, XH, XL);
-    else launch_variant<false, false, false, RG>(grid, smem, s, G, A, B, R, XH, XL);
+    if (hs) launch_variant<false, true, false, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
+    else launch_variant<false, false, false, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
   }
 }
 
-// One fused full sweep A -> B on `ncomp` components (zero_in: A taken as 0;
-// zchunk <= 0: chosen for whole waves of two CTAs per SM).  With upd_hi /
-// upd_lo given (and zero_in false) the result is added to that double-word
-// iterate instead of being stored to B.
-void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
-                       int ncomp, int zchunk, int kclass, bool zero_in, const Comp3<float>* upd_hi,
-                       const Comp3<float>* upd_lo, float omega) {
-  const size_t smem = fused_sweep_smem();
+FusedGeom fused_geom(Ctx& cx, const Level& L, Rhs3<float> R, int ncomp, int zchunk, float omega) {
   FusedGeom G;
   G.nx = L.n[0]; G.ny = L.n[1]; G.nz = L.n[2];
   G.per_y = L.per[1]; G.per_z = L.per[2];
@@ -549,19 +726,62 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   G.c1 = 1.f - omega;
   G.h2 = (float)(1.0 / L.inv_h2);
   G.beta = R.beta;
+  G.status = cx.status;
+  G.limit_ns = kCopyLimitNs;
+  G.probe_tx = 0u;
+  return G;
+}
+
+}  // namespace
+
+// One fused full sweep A -> B on `ncomp` components (zero_in: A taken as 0;
+// zchunk <= 0: chosen for whole waves of two CTAs per SM).  With upd_hi /
+// upd_lo given (and zero_in false) the result is added to that double-word
+// iterate instead of being stored to B.  Tile-aligned levels without
+// periodic y stage by TMA boxes, the others by cp.async.
+void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, Rhs3<float> R,
+                       int ncomp, int zchunk, int kclass, bool zero_in, const Comp3<float>* upd_hi,
+                       const Comp3<float>* upd_lo, float omega) {
+  const size_t smem = fused_sweep_smem();
+  const FusedGeom G = fused_geom(cx, L, R, ncomp, zchunk, omega);
   const int nzc = (L.n[2] + G.zchunk - 1) / G.zchunk;
   dim3 grid(G.ntx * G.nty, nzc, ncomp);
   const bool hs = R.S[0] != nullptr;
   const bool upd = upd_hi && upd_lo && !zero_in;
   const Comp3<float> XH = upd ? *upd_hi : Comp3<float>{{nullptr, nullptr, nullptr}};
   const Comp3<float> XL = upd ? *upd_lo : Comp3<float>{{nullptr, nullptr, nullptr}};
+  FusedMaps M;
+  std::memset(&M, 0, sizeof M);
+  const bool tma = level_ok(L) && !L.per[1] && fused_maps(cx, L, A, R, ncomp, zero_in, &M);
   // algorithmic bytes per cell: rhs and result (+ x unless zero_in, + the
   // iterate's two words read and written when updating)
   const double bpc = zero_in ? 8.0 : (upd ? 24.0 : 12.0);
   cx.before(kclass);
-  if (level_ok(L)) launch_pick<false>(grid, smem, cx.stream, G, A, B, R, XH, XL, upd, zero_in, hs);
-  else launch_pick<true>(grid, smem, cx.stream, G, A, B, R, XH, XL, upd, zero_in, hs);
+  if (tma) launch_pick<false>(grid, smem, cx.stream, G, A, B, R, XH, XL, M, upd, zero_in, hs);
+  else launch_pick<true>(grid, smem, cx.stream, G, A, B, R, XH, XL, M, upd, zero_in, hs);
   cx.after(kclass, bpc * (double)L.cells() * ncomp);
+}
+
+// The bound of the fused sweep's waits for its staged planes: one sweep from
+// zero of component 0 of R into B on the tile-aligned level L (without
+// periodic y), every copy group armed with probe_tx bytes (> 0) and no box
+// loaded, so that every wait gives up after limit_ns and sets kCopyTimeout
+// in the flag word.  Returns false (nothing launched) unless L is such a
+// level.
+bool launch_copy_wait_probe(Ctx& cx, const Level& L, Comp3<float> B, Rhs3<float> R,
+                            unsigned probe_tx, unsigned long long limit_ns) {
+  if (!level_ok(L) || L.per[1] || probe_tx == 0u) return false;
+  FusedGeom G = fused_geom(cx, L, R, 1, 0, 1.f);
+  G.limit_ns = limit_ns;
+  G.probe_tx = probe_tx;
+  const int nzc = (L.n[2] + G.zchunk - 1) / G.zchunk;
+  dim3 grid(G.ntx * G.nty, nzc, 1);
+  const Comp3<float> none{{nullptr, nullptr, nullptr}};
+  FusedMaps M;
+  std::memset(&M, 0, sizeof M);
+  launch_pick<false>(grid, fused_sweep_smem(), cx.stream, G, none, B, R, none, none, M, false, true,
+                     R.S[0] != nullptr);
+  return cudaPeekAtLastError() == cudaSuccess;
 }
 
 }  // namespace vsv

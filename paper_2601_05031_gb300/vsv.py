@@ -87,7 +87,8 @@ EXPORTS = [
     "vsv_set_free_energy", "vsv_set_wall_motion", "vsv_set_solver", "vsv_default_solver", "vsv_set_phi", "vsv_step",
     "vsv_stability_limit", "vsv_solve_poisson", "vsv_get_field", "vsv_set_field",
     "vsv_get_diagnostics", "vsv_get_stress_profile", "vsv_state_bytes", "vsv_get_state",
-    "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_barrier_check", "vsv_last_error",
+    "vsv_set_state", "vsv_volume_area_static", "vsv_check", "vsv_barrier_check", "vsv_copy_wait_check",
+    "vsv_last_error",
     "vsv_kernel_launches",
     "vsv_kernel_bytes", "vsv_profile_enable", "vsv_profile_read", "vsv_batch_create",
     "vsv_batch_step", "vsv_batch_destroy", "vsv_tape_create", "vsv_tape_destroy",
@@ -128,6 +129,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_volume_area_static": (i32, [vp, i32, i32, i32, dbl, dbl, i32, vp, vp]),
         "vsv_check": (i32, [vp]),
         "vsv_barrier_check": (i32, [vp, i32, i32, i32, dbl]),
+        "vsv_copy_wait_check": (i32, [vp, i32, dbl]),
         "vsv_last_error": (C.c_char_p, [vp]),
         "vsv_kernel_launches": (i64, [vp]),
         "vsv_kernel_bytes": (dbl, [vp]),
@@ -307,6 +309,12 @@ def vsv_check(g, check=True):
 def vsv_barrier_check(g, blocks, rounds, extra_arrivals, limit_ms):
     """Bounded grid barrier check (see the header); returns the vsv_status."""
     return lib().vsv_barrier_check(g, blocks, rounds, extra_arrivals, limit_ms)
+
+
+def vsv_copy_wait_check(g, probe_bytes, limit_ms):
+    """Bounded copy-wait check of the fused sweep (see the header); returns
+    the vsv_status."""
+    return lib().vsv_copy_wait_check(g, probe_bytes, limit_ms)
 
 
 def vsv_last_error(g) -> str:

@@ -119,3 +119,34 @@ def test_grid_barrier_completes_and_its_bound_runs_out(V):
     assert V.vsv_barrier_check(sim.g, 10 ** 6, 1, 0, 10.0) == V.VSV_EINVAL
     assert V.vsv_barrier_check(sim.g, 2, 1, 0, 0.0) == V.VSV_EINVAL
     sim.close()
+
+
+def test_fused_sweep_copy_wait_bound_runs_out(V):
+    """The fused sweep's waits for its bulk-copied planes are bounded: with
+    every copy group expecting bytes that no copy delivers, each wait gives
+    up after 20 ms, the call reports the timeout, and the grid's next solve
+    (through the same fused sweep) is unaffected."""
+    import time
+    from paper_2601_05031_gb300.sim import Simulation
+    sim = Simulation(128, 32, 32, 1.0, V.VSV_MIXED)
+    t0 = time.perf_counter()
+    st = V.vsv_copy_wait_check(sim.g, 4096, 20.0)
+    dt = time.perf_counter() - t0
+    assert st == V.VSV_ECUDA, st
+    assert "ran out of time" in V.vsv_last_error(sim.g)
+    assert dt < 5.0, dt
+    assert V.vsv_check(sim.g, check=False) == V.VSV_OK
+    b = inputs.random_field((32, 32, 128), seed=7)
+    x, cyc, rr, st = sim.solve_poisson(b, periodic=(True, False, True), tol=1e-6, max_cycles=30,
+                                       check=False)
+    assert st == V.VSV_OK and rr <= 1e-6
+    # arguments and grids the sweep does not serve are refused before any launch
+    assert V.vsv_copy_wait_check(sim.g, 10, 20.0) == V.VSV_EINVAL
+    assert V.vsv_copy_wait_check(sim.g, 4096, 0.0) == V.VSV_EINVAL
+    sim.close()
+    sim = Simulation(64, 32, 32, 1.0, V.VSV_MIXED)
+    assert V.vsv_copy_wait_check(sim.g, 4096, 20.0) == V.VSV_EINVAL
+    sim.close()
+    sim = Simulation(128, 32, 32, 1.0, V.VSV_FP64)
+    assert V.vsv_copy_wait_check(sim.g, 4096, 20.0) == V.VSV_EINVAL
+    sim.close()
