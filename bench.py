@@ -15,6 +15,7 @@ slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -54,7 +55,29 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the 512x256x256 line: N independent seeded problems of "
                          "a parameter sweep stepped together (batched CUDA graph)")
+    ap.add_argument("--poisson-case", action="store_true",
+                    help="instead of the benchmark: one single-component mixed Poisson solve "
+                         "(2 V-cycles, seeded rhs) on the nx x ny x nz grid, for kernel profiles")
     return ap.parse_args()
+
+
+def run_poisson_case(args):
+    """A small, fixed launch sequence for ncu captures of the solver kernels:
+    every multigrid kernel of the mixed path at the benchmark's plane size,
+    with a single component (fields of nx*ny*nz*4 bytes, 134 MB at the
+    default size: above L2, a few GB on the device in all)."""
+    import inputs
+    from paper_2601_05031_gb300 import build
+    build.build()
+    from paper_2601_05031_gb300 import vsv as V
+    from paper_2601_05031_gb300.sim import Simulation
+    b = inputs.random_field((args.nz, args.ny, args.nx), seed=3)
+    sim = Simulation(args.nx, args.ny, args.nz, 1.0, V.VSV_MIXED)
+    x, cyc, rr, st = sim.solve_poisson(b, periodic=(True, False, True), tol=0.0, max_cycles=2,
+                                       check=False)
+    sim.close()
+    print(json.dumps({"poisson_case": [args.nx, args.ny, args.nz], "cycles": cyc,
+                      "rel_residual": rr}), flush=True)
 
 
 def dist_env():
@@ -143,11 +166,26 @@ def job_throughput(world_size, cells_per_rank, steps, ms_max):
 GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
          2: "extrapolated guess 3x^n - 3x^(n-1) + x^(n-2)"}
 
-# DRAM traffic of the finest-level fused sweeps per launch and cell
-# (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
-# kernel), or None while no capture of the current kernel build exists.
-FUSED_SWEEP_TRAFFIC_PER_CELL = None
-FUSED_SWEEP_TRAFFIC_SOURCE = "not yet captured for the current kernel build"
+# DRAM traffic of the finest-level fused sweeps per cell and component:
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of each
+# variant (zero-input 6.87, plain 11.77, update 23.45 B per cell) on a
+# single-component 512 x 256 x 256 solve, weighted 1:2:1 as a V(2,2)-cycle
+# launches them.  It belongs to the kernel sources whose digest is
+# FUSED_SWEEP_TRAFFIC_BUILD; with any other sources the line reports null.
+FUSED_SWEEP_TRAFFIC_PER_CELL = 13.47
+FUSED_SWEEP_TRAFFIC_BUILD = "7266785be77bf2da"
+FUSED_SWEEP_SOURCES = ("paper_2601_05031_gb300/csrc/smooth.cu", "paper_2601_05031_gb300/csrc/tile.cuh",
+                       "paper_2601_05031_gb300/csrc/common.cuh", "paper_2601_05031_gb300/csrc/internal.h")
+
+
+def fused_sweep_build():
+    """Digest of the fused sweep's kernel sources (first 16 hex digits of
+    their SHA-256)."""
+    h = hashlib.sha256()
+    for f in FUSED_SWEEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 # steps per captured graph (the library's replay length)
 GRAPH_STEPS = 6
@@ -303,6 +341,8 @@ def run_gpu(args, ws, rank, local):
     timed_steps(sim, nprof, w.dt, torch, barrier)
     pms, pn, pbytes = V.vsv_profile_read(sim.g, V.VSV_KCLASS_SMOOTH_FINE, with_bytes=True)
     V.vsv_profile_enable(sim.g, V.VSV_KCLASS_SMOOTH_FINE, False)
+    build = fused_sweep_build()
+    traffic_ok = build == FUSED_SWEEP_TRAFFIC_BUILD
     per_launch_s = pms * 1e-3 / max(pn, 1)
     algo = pbytes / max(pn, 1)
     achieved = algo / per_launch_s / 1e9
@@ -313,9 +353,13 @@ def run_gpu(args, ws, rank, local):
                        "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                        "algorithmic_bytes_per_launch": round(algo), "launches_timed": int(pn),
                        "avg_launch_us": round(per_launch_s * 1e6, 2),
-                       "traffic": (None if FUSED_SWEEP_TRAFFIC_PER_CELL is None else
-                                   round(FUSED_SWEEP_TRAFFIC_PER_CELL * N * 3)),
-                       "traffic_source": FUSED_SWEEP_TRAFFIC_SOURCE}
+                       "traffic": (round(FUSED_SWEEP_TRAFFIC_PER_CELL * N * 3) if traffic_ok
+                                   else None),
+                       "traffic_source": ("ncu capture of this kernel build (profiles/"
+                                          "fused_sweep_poisson_512x256x256.md), per cell "
+                                          "and component x cells x 3" if traffic_ok else
+                                          "no ncu capture of this kernel build"),
+                       "kernel_build": build}
     out["clocks"] = clk.summary()
     # plain FP64 step with the same schedule, and the accuracy of mixed vs FP64
     if not args.no_fp64:
@@ -547,6 +591,10 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.poisson_case:
+        if rank == 0:
+            run_poisson_case(args)
         return
     if args.batch > 0:
         run_batch(args, ws, rank, local)

@@ -106,7 +106,7 @@ __device__ __forceinline__ float4 rb_group(float4 V, float4 U, float4 D, float4 
 }
 
 __device__ __forceinline__ float* ring(float* base, int plane, int slots, int slot_elems) {
-  return base + ((unsigned)(plane + slots) % (unsigned)slots) * slot_elems;   // plane >= -2
+  return base + ((unsigned)(plane + slots) % (unsigned)slots) * slot_elems;   // plane >= -slots
 }
 
 }  // namespace
@@ -139,9 +139,9 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
              Comp3<float> XL, const __grid_constant__ FusedMaps M) {
   constexpr bool TMA = !RAGGED;
   extern __shared__ float4 smem_f4[];
-  // boxes land on 128-byte boundaries: align the rings' base
-  float* sA = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_f4) + 127) &
-                                       ~static_cast<uintptr_t>(127));
+  // boxes land on 128-byte boundaries: align the rings' base (by pointer
+  // arithmetic on the shared array, so that accesses stay shared-space ones)
+  float* sA = reinterpret_cast<float*>(smem_f4) + (((128u - (smem_u32(smem_f4) & 127u)) & 127u) >> 2);
   float* sB = sA + kNA * kSlotA;
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(sB + kNB * kSlotB);
   const int comp = blockIdx.z;
@@ -183,24 +183,22 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     da.init_halo(G, tid - kHaloTid, x0, y0, kH, kRA);
     db.init_halo(G, tid - kHaloTid - 2 * kRA, x0, y0, kH - 1, kRB);
   }
-  auto stage_vectors = [&](int pa, int na, int pb) {
-    if constexpr (!ZERO_IN)
-      for (int i = 0; i < na; ++i) da.stage(slotA(pa + i), a, G, pa + i);
-    db.stage(slotB(pb), bsrc, G, pb);
+  auto stage_x = [&](float* slot, int plane) {
+    if constexpr (!ZERO_IN) da.stage(slot, a, G, plane);
   };
-  // boxes of copy group grp: x planes pa .. pa + na - 1, rhs plane pb (one
-  // thread; planes beyond a z wall lie outside the tensor and read as zero)
-  auto tma_issue = [&](int grp, int pa, int na, int pb) {
-    unsigned long long* bar = &bars[grp & 1];
-    if (G.probe_tx) {
-      mbar_arrive_expect_tx(bar, G.probe_tx);
-      return;
-    }
-    mbar_arrive_expect_tx(bar, (unsigned)na * kBoxA + kBoxB);
-    for (int i = 0; i < na; ++i)
-      tma_load_3d(slotA(pa + i), &M.a[comp], x0, y0 - kH, G.per_z ? wrapi(pa + i, G.nz) : pa + i,
-                  bar);
-    tma_load_3d(slotB(pb), &M.b[comp], x0, y0 - (kH - 1), G.per_z ? wrapi(pb, G.nz) : pb, bar);
+  auto stage_b = [&](float* slot, int plane) { db.stage(slot, bsrc, G, plane); };
+  // boxes (one thread; planes beyond a z wall lie outside the tensor and
+  // read as zero): arm the group's barrier with its bytes -- false in the
+  // check of the wait bound, which loads no box -- then load
+  auto arm = [&](unsigned long long* bar, unsigned bytes) {
+    mbar_arrive_expect_tx(bar, G.probe_tx ? G.probe_tx : bytes);
+    return G.probe_tx == 0u;
+  };
+  auto box_x = [&](float* slot, int plane, unsigned long long* bar) {
+    tma_load_3d(slot, &M.a[comp], x0, y0 - kH, G.per_z ? wrapi(plane, G.nz) : plane, bar);
+  };
+  auto box_b = [&](float* slot, int plane, unsigned long long* bar) {
+    tma_load_3d(slot, &M.b[comp], x0, y0 - (kH - 1), G.per_z ? wrapi(plane, G.nz) : plane, bar);
   };
   // after a wait that ran out: boxes of groups grp and grp + 1 may still be
   // in flight into this CTA's shared memory, and this thread's cp.async copies
@@ -254,13 +252,24 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
   if constexpr (TMA) __syncthreads();   // initialised barriers before the first box
   // prologue: group 0 = x planes zb-2 .. zb, rhs plane zb-1 (step zb-1);
   // group 1 = x plane zb+1, rhs plane zb (step zb)
-  if constexpr (TMA)
-    if (tid == kIssueTid) tma_issue(0, zb - 2, ZERO_IN ? 0 : 3, zb - 1);
-  stage_vectors(zb - 2, 3, zb - 1);
+  if constexpr (TMA) {
+    if (tid == kIssueTid && arm(&bars[0], (ZERO_IN ? 0u : 3u * kBoxA) + kBoxB)) {
+      if constexpr (!ZERO_IN)
+        for (int i = -2; i <= 0; ++i) box_x(slotA(zb + i), zb + i, &bars[0]);
+      box_b(slotB(zb - 1), zb - 1, &bars[0]);
+    }
+  }
+  for (int i = -2; i <= 0; ++i) stage_x(slotA(zb + i), zb + i);
+  stage_b(slotB(zb - 1), zb - 1);
   cp_async_commit();
-  if constexpr (TMA)
-    if (tid == kIssueTid) tma_issue(1, zb + 1, ZERO_IN ? 0 : 1, zb);
-  stage_vectors(zb + 1, 1, zb);
+  if constexpr (TMA) {
+    if (tid == kIssueTid && arm(&bars[1], (ZERO_IN ? 0u : kBoxA) + kBoxB)) {
+      if constexpr (!ZERO_IN) box_x(slotA(zb + 1), zb + 1, &bars[1]);
+      box_b(slotB(zb), zb, &bars[1]);
+    }
+  }
+  stage_x(slotA(zb + 1), zb + 1);
+  stage_b(slotB(zb), zb);
   cp_async_commit();
   cp_async_wait1();
   if constexpr (TMA) {
@@ -282,8 +291,24 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     MM[h] = V[h];
     MMM[h] = V[h];
   }
+  // ring slots (offsets into the rings, in floats) of x planes p - 2 .. p + 3
+  // and rhs planes p - 2 .. p + 2 at the top of step p, rotated at its end
+  // (no divisions in the loop)
+  auto offA = [&](int plane) { return (int)(slotA(plane) - sA); };
+  auto offB = [&](int plane) { return (int)(slotB(plane) - sB); };
+  int oa0 = offA(zb - 3), oa1 = offA(zb - 2), oa2 = offA(zb - 1), oa3 = offA(zb), oa4 = offA(zb + 1),
+      oa5 = offA(zb + 2);
+  int ob0 = offB(zb - 3), ob1 = offB(zb - 2), ob2 = offB(zb - 1), ob3 = offB(zb), ob4 = offB(zb + 1);
 
   for (int p = zb - 1; p <= ze + 1; ++p) {
+    float* const xa0 = sA + oa0;
+    float* const xa1 = sA + oa1;
+    float* const xa2 = sA + oa2;
+    float* const xa3 = sA + oa3;
+    float* const xa5 = sA + oa5;
+    const float* const rb0 = sB + ob0;
+    const float* const rb2 = sB + ob2;
+    float* const rb4 = sB + ob4;
     const int qp = p - 2;
     const bool black = qp >= zb && qp < ze;
     // UPD: the iterate of plane p - 2, loaded ahead of the barrier so that
@@ -322,13 +347,19 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       __syncthreads();
     }
     if (p + 2 <= ze) {
-      if constexpr (TMA)
-        if (tid == kIssueTid) tma_issue(p - zb + 3, p + 3, ZERO_IN ? 0 : 1, p + 2);
-      stage_vectors(p + 3, 1, p + 2);
+      if constexpr (TMA) {
+        unsigned long long* bar = &bars[(p - zb + 3) & 1];
+        if (tid == kIssueTid && arm(bar, (ZERO_IN ? 0u : kBoxA) + kBoxB)) {
+          if constexpr (!ZERO_IN) box_x(xa5, p + 3, bar);
+          box_b(rb4, p + 2, bar);
+        }
+      }
+      stage_x(xa5, p + 3);
+      stage_b(rb4, p + 2);
     }
     cp_async_commit();
-    float* cA = slotA(p);
-    const float* cB = slotB(p);
+    float* cA = xa2;
+    const float* cB = rb2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       MMM[h] = MM[h];
@@ -338,7 +369,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       // ZERO_IN: the black values of plane p + 1 are zero and its red ones
       // are written by the red phase of the next step before any read
       P[h] = (ZERO_IN || p > ze) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                 : lds4(slotA(p + 1) + rown[h] * kTX + 4 * gx);
+                                 : lds4(xa3 + rown[h] * kTX + 4 * gx);
     }
     // the black phase's operands from shared memory: the y neighbours of
     // the two rows, their rhs groups and, at the tile edges, the x halo
@@ -346,8 +377,8 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
     float Le[2], Re[2];
     auto black_load = [&]() {
       if (black) {
-        const float* cAq = slotA(qp);
-        const float* cBq = slotB(qp);
+        const float* cAq = xa0;
+        const float* cBq = rb0;
   #pragma unroll
         for (int h = 0; h < 2; ++h) {
           Le[h] = gx == 0 ? hA(cAq, rown[h])[kHX - 1] : 0.f;
@@ -524,8 +555,8 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
             const float* row = cA + r * kTX;
             const float4 Vh = lds4(row + 4 * gx), U = lds4(row - kTX + 4 * gx),
                          D = lds4(row + kTX + 4 * gx);
-            const float4 Mh = lds4(slotA(p - 1) + r * kTX + 4 * gx);
-            const float4 Ph = lds4(slotA(p + 1) + r * kTX + 4 * gx);
+            const float4 Mh = lds4(xa1 + r * kTX + 4 * gx);
+            const float4 Ph = lds4(xa3 + r * kTX + 4 * gx);
             const float Lx = gx == 0 ? hA(cA, r)[kHX - 1] : row[4 * gx - 1];
             const float Rx = gx == 31 ? hA(cA, r)[kHX] : row[4 * gx + 4];
             const float4 Bv = lds4(cB + (r - 1) * kTX + 4 * gx);
@@ -552,7 +583,7 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
             const float xm = side ? cA[r * kTX + kTX - 1] : hr[kHX - 2];
             const float xp = side ? hr[kHX + 1] : cA[r * kTX];
             const float s = ((xm + xp) + (hA(cA, r - 1)[hc] + hA(cA, r + 1)[hc])) +
-                            (hA(slotA(p - 1), r)[hc] + hA(slotA(p + 1), r)[hc]);
+                            (hA(xa1, r)[hc] + hA(xa3, r)[hc]);
             const float bb = beta * hB(cB, r - 1)[hc] + srow(j, p);
             hr[hc] = relax(hr[hc], nb_term(s, bb, h2), rc_of(G, jw + zw), c1);
           }
@@ -588,6 +619,12 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       black_load();
       black_phase();
       black_store();
+    }
+    {
+      const int t = oa0;
+      oa0 = oa1; oa1 = oa2; oa2 = oa3; oa3 = oa4; oa4 = oa5; oa5 = t;
+      const int u = ob0;
+      ob0 = ob1; ob1 = ob2; ob2 = ob3; ob3 = ob4; ob4 = u;
     }
   }
   cp_async_wait0();
