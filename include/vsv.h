@@ -247,11 +247,16 @@ size_t vsv_workspace_bytes(int nx, int ny, int nz, int precision);
  * aligned, ws_bytes >= vsv_workspace_bytes) and caller stream `cuda_stream`
  * (a cudaStream_t, NULL = legacy default stream).  Periodic axes must have
  * even extent or extent 1.  Defaults: quiescent flow, eta = 1, CH with
- * sigma = eps = M = 1, default solver for the precision. */
+ * sigma = eps = M = 1, default solver for the precision.  The handle holds
+ * all the library's own memory: host state, one page-locked 4-byte word
+ * into which vsv_step copies its deferred status, and CUDA events; no call
+ * on the grid allocates device memory (the tape's convenience constructor
+ * vsv_tape_create aside). */
 vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int precision,
                       void* workspace, size_t ws_bytes, void* cuda_stream);
 
-/* Free the host handle (the workspace stays the caller's).  NULL is a no-op. */
+/* Free the host handle with its page-locked word and events (the
+ * workspace stays the caller's).  NULL is a no-op. */
 vsv_status vsv_destroy(vsv_grid* g);
 
 /* Choose the body-free flow (builds the wall data and base-flow tables on
@@ -475,17 +480,31 @@ vsv_status vsv_batch_destroy(vsv_batch* b);
  * constants A0 = A[phi^0], V0 = V[phi^0] depend on phi^0 and are
  * differentiated.
  *
- * vsv_tape_create binds a tape to grid g (which must outlive it): every >= 1
- * steps between checkpoints, tol > 0 (0 selects 1e-11).  It allocates the
- * device memory of one segment's record ((every + 1) x 5 FP64 fields) and of
- * the adjoint fields.  VSV_EINVAL on bad arguments, VSV_ECUDA when memory
- * runs out.
+ * vsv_tape_create_in binds a tape to grid g (which must outlive it): every
+ * >= 1 steps between checkpoints, forward passes of up to max_steps >= 1
+ * steps, tol > 0 (0 selects 1e-11).  All its device memory -- one segment's
+ * record ((every + 1) x 5 FP64 fields), the adjoint fields and the
+ * checkpoint slots -- is carved from `workspace`: caller-owned device memory
+ * on the current device, 256-byte aligned, of workspace_bytes >=
+ * vsv_tape_workspace_bytes(g, every, max_steps) bytes, which the caller
+ * keeps until vsv_tape_destroy.  The tape allocates and frees no device
+ * memory.  VSV_EINVAL on bad arguments (including a host or misaligned
+ * workspace), VSV_ENOMEM when workspace_bytes is too small.
+ * vsv_tape_workspace_bytes: that size (buffers plus 1 + ceil(max_steps /
+ * every) checkpoints of the grid's state); VSV_EINVAL on bad arguments.
+ *
+ * vsv_tape_create: the same, with the tape allocating its device memory
+ * itself (cudaMalloc; checkpoints as they are saved) and freeing it in
+ * vsv_tape_destroy; no step limit.  VSV_EINVAL on bad arguments,
+ * VSV_ECUDA when memory runs out.
  *
  * vsv_tape_forward runs vsv_set_phi(phi0, dtype, on_device) and nsteps steps
  * of dt, saving the full state on the device at step 0, every `every` steps
  * and at step nsteps.  The grid's flow, free energy and solver settings
  * must stay unchanged until the matching backward pass.  VSV_EINVAL for
- * bad arguments; errors of vsv_set_phi / vsv_step pass through.
+ * bad arguments, VSV_ENOMEM (nothing run) when nsteps exceeds the max_steps
+ * of a tape over caller-owned memory; errors of vsv_set_phi / vsv_step pass
+ * through.
  *
  * vsv_tape_backward takes phibar_final = dJ/dphi^N (N cells, FP64, device
  * memory when on_device, else host) and writes phibar0 = dJ/dphi^0 (same
@@ -499,11 +518,16 @@ vsv_status vsv_batch_destroy(vsv_batch* b);
  * the previous reverse step's solution, with no host synchronisation; 0
  * (the default) solves to `tol`.  VSV_EINVAL for a NULL tape or a negative
  * count.
- * vsv_tape_destroy frees the tape's device memory (NULL is a no-op).
- * vsv_tape_bytes: device bytes held by the tape (checkpoints included).
+ * vsv_tape_destroy frees the tape (and, for vsv_tape_create, its device
+ * memory; NULL is a no-op).
+ * vsv_tape_bytes: device bytes the tape uses (checkpoints included; the
+ * workspace size it needs for vsv_tape_create_in).
  * vsv_tape_info: adjoint solve cycles and re-run steps of the last backward
  * pass, checkpoints held. */
 typedef struct vsv_tape vsv_tape;
+vsv_status vsv_tape_workspace_bytes(const vsv_grid* g, int every, int max_steps, size_t* bytes);
+vsv_status vsv_tape_create_in(vsv_tape** out, vsv_grid* g, int every, int max_steps, double tol,
+                              void* workspace, size_t workspace_bytes);
 vsv_status vsv_tape_create(vsv_tape** out, vsv_grid* g, int every, double tol);
 vsv_status vsv_tape_destroy(vsv_tape* t);
 vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_device, int nsteps,

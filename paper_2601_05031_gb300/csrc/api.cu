@@ -1334,6 +1334,16 @@ vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int prec
     delete g;
     return VSV_ECUDA;
   }
+  // the handle's page-locked word for vsv_step's deferred status, and the
+  // event that marks its arrival (created here: stepping allocates nothing)
+  if (cudaMallocHost((void**)&g->flag_host, sizeof(int)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->flag_event, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (g->flag_host) cudaFreeHost(g->flag_host);
+    delete g;
+    return VSV_ECUDA;
+  }
+  *g->flag_host = 0;
   upload_scalar_params(g);
   *out = g;
   return VSV_OK;
@@ -1554,10 +1564,6 @@ vsv_status vsv_step(vsv_grid* g, int nsteps, double dt) {
     if (st != VSV_OK) return st;
   }
   CKL();
-  if (!g->flag_host) {
-    CK(cudaMallocHost((void**)&g->flag_host, sizeof(int)));
-    CK(cudaEventCreateWithFlags(&g->flag_event, cudaEventDisableTiming));
-  }
   CK(cudaMemcpyAsync(g->flag_host, &g->S->nonfinite, sizeof(int), cudaMemcpyDeviceToHost,
                      g->cx.stream));
   CK(cudaEventRecord(g->flag_event, g->cx.stream));
@@ -2195,6 +2201,12 @@ struct vsv_tape {
   double* acc = nullptr;               // kAccCount accumulators
   double* partials = nullptr;          // 3 per reduction block
   size_t dev_bytes = 0;
+  // caller-owned device memory (vsv_tape_create_in): every buffer and the
+  // checkpoint slots are carved from it; nothing is allocated or freed
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int max_ck = 0;                      // checkpoint slots in ws
+  char* ck_pool = nullptr;             // the first of them
   long long adj_cycles = 0;            // cycles of the adjoint solves, last backward pass
   long long recomputed = 0;            // steps re-run by the last backward pass
   // views into buf / fbuf
@@ -2231,16 +2243,45 @@ template <class T>
 Comp3<T> mc3(T* const a[3]) { return Comp3<T>{{a[0], a[1], a[2]}}; }
 
 void tape_free_ckpts(vsv_tape* t) {
-  for (char* p : t->ck) cudaFree(p);
+  if (!t->ws)
+    for (char* p : t->ck) cudaFree(p);
   t->ck.clear();
   t->ck_step.clear();
   t->ck_hdr.clear();
 }
 
+// Bytes of one checkpoint: the state fields plus V0 and A0.
+size_t tape_ck_bytes(const vsv_grid* g) {
+  size_t b = 2 * sizeof(double);
+  for (auto& f : state_fields(g)) b += f.second;
+  return b;
+}
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Device bytes of a tape's buffers (without checkpoints), each rounded up
+// to 256 bytes as the caller-owned layout carves them.
+size_t tape_buffer_bytes(const vsv_grid* g, int every) {
+  const size_t N = (size_t)g->N;
+  size_t b = round256((size_t)(every + 1) * 5 * N * 8) + round256((size_t)(every + 1) * 8) +
+             round256(25 * N * 8) + round256(kAccCount * 8) + round256((size_t)3 * adj_blocks(g->N) * 8);
+  if (g->prec == VSV_MIXED) b += round256(18 * N * 4);
+  return b;
+}
+
+// checkpoints a forward pass of nsteps records: step 0 and every segment end
+int tape_ck_count(int nsteps, int every) { return 1 + (nsteps + every - 1) / every; }
+
 vsv_status tape_alloc(vsv_tape* t) {
   vsv_grid* g = t->g;
   const long long N = g->N;
+  size_t carved = 0;
   auto dmalloc = [&](void** p, size_t b) -> vsv_status {
+    if (t->ws) {
+      *p = t->ws + carved;
+      carved += round256(b);
+      return VSV_OK;
+    }
     CK(cudaMalloc(p, b));
     t->dev_bytes += b;
     return VSV_OK;
@@ -2275,6 +2316,7 @@ vsv_status tape_alloc(vsv_tape* t) {
     for (int c = 0; c < 3; ++c) t->bh[c] = takef();
     for (int c = 0; c < 3; ++c) t->bl[c] = takef();
   }
+  if (t->ws) t->ck_pool = t->ws + carved;   // checkpoint slots follow the buffers
   return VSV_OK;
 }
 
@@ -2282,11 +2324,16 @@ vsv_status tape_alloc(vsv_tape* t) {
 vsv_status tape_save(vsv_tape* t, int step) {
   vsv_grid* g = t->g;
   char* dst = nullptr;
-  CK(cudaMalloc((void**)&dst, t->ck_bytes));
-  // a failed copy frees the new slot before returning (not yet on the tape)
+  if (t->ws) {
+    if ((int)t->ck.size() >= t->max_ck) return fail(g, VSV_ENOMEM, "tape checkpoint slots exhausted%s");
+    dst = t->ck_pool + t->ck.size() * round256(t->ck_bytes);
+  } else {
+    CK(cudaMalloc((void**)&dst, t->ck_bytes));
+  }
+  // a failed copy frees a new slot before returning (not yet on the tape)
   auto copy = [&](void* to, const void* from, size_t n) -> cudaError_t {
     const cudaError_t e = cudaMemcpyAsync(to, from, n, cudaMemcpyDeviceToDevice, g->cx.stream);
-    if (e != cudaSuccess) cudaFree(dst);
+    if (e != cudaSuccess && !t->ws) cudaFree(dst);
     return e;
   };
   size_t off = 0;
@@ -2295,7 +2342,7 @@ vsv_status tape_save(vsv_tape* t, int step) {
     off += f.second;
   }
   CK(copy(dst + off, &g->S->V0, 2 * sizeof(double)));   // V0, A0 (adjacent in Scalars)
-  t->dev_bytes += t->ck_bytes;
+  if (!t->ws) t->dev_bytes += t->ck_bytes;
   StateHeader hd{};
   hd.time = g->time;
   hd.steps = g->steps;
@@ -2467,16 +2514,60 @@ vsv_status vsv_tape_create(vsv_tape** out, vsv_grid* g, int every, double tol) {
   return VSV_OK;
 }
 
+vsv_status vsv_tape_workspace_bytes(const vsv_grid* g, int every, int max_steps, size_t* bytes) {
+  if (!g || !bytes || every < 1 || max_steps < 1) return VSV_EINVAL;
+  *bytes = tape_buffer_bytes(g, every) +
+           (size_t)tape_ck_count(max_steps, every) * round256(tape_ck_bytes(g));
+  return VSV_OK;
+}
+
+vsv_status vsv_tape_create_in(vsv_tape** out, vsv_grid* g, int every, int max_steps, double tol,
+                              void* workspace, size_t workspace_bytes) {
+  if (!out) return VSV_EINVAL;
+  *out = nullptr;
+  if (!g || every < 1 || max_steps < 1 || !(tol >= 0) || !std::isfinite(tol) || !workspace ||
+      ((uintptr_t)workspace & 255))
+    return VSV_EINVAL;
+  size_t need = 0;
+  vsv_tape_workspace_bytes(g, every, max_steps, &need);
+  if (workspace_bytes < need) return VSV_ENOMEM;
+  cudaPointerAttributes pa{};
+  int dev = -1;
+  if (cudaPointerGetAttributes(&pa, workspace) != cudaSuccess || pa.type != cudaMemoryTypeDevice ||
+      cudaGetDevice(&dev) != cudaSuccess || pa.device != dev) {
+    cudaGetLastError();
+    return VSV_EINVAL;
+  }
+  vsv_tape* t = new vsv_tape();
+  t->g = g;
+  t->every = every;
+  t->tol = tol > 0 ? tol : 1e-11;
+  t->ws = (char*)workspace;
+  t->ws_bytes = workspace_bytes;
+  t->max_ck = tape_ck_count(max_steps, every);
+  t->ck_bytes = tape_ck_bytes(g);
+  t->dev_bytes = need;
+  vsv_status st = tape_alloc(t);
+  if (st != VSV_OK) {
+    vsv_tape_destroy(t);
+    return st;
+  }
+  *out = t;
+  return VSV_OK;
+}
+
 vsv_status vsv_tape_destroy(vsv_tape* t) {
   if (!t) return VSV_OK;
   if (t->g) cudaStreamSynchronize(t->g->cx.stream);
   tape_free_ckpts(t);
-  cudaFree(t->rec);
-  cudaFree(t->gam);
-  cudaFree(t->buf);
-  cudaFree(t->fbuf);
-  cudaFree(t->acc);
-  cudaFree(t->partials);
+  if (!t->ws) {
+    cudaFree(t->rec);
+    cudaFree(t->gam);
+    cudaFree(t->buf);
+    cudaFree(t->fbuf);
+    cudaFree(t->acc);
+    cudaFree(t->partials);
+  }
   delete t;
   return VSV_OK;
 }
@@ -2509,14 +2600,16 @@ vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_dev
   if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_tape_forward%s");
   if (g->motion_on)
     return fail(g, VSV_EINVAL, "the adjoint tape needs steady walls (vsv_set_wall_motion)%s");
+  if (t->ws && tape_ck_count(nsteps, t->every) > t->max_ck)
+    return fail(g, VSV_ENOMEM, "more steps than the tape's workspace was sized for%s");
   CK(cudaStreamSynchronize(g->cx.stream));
   tape_free_ckpts(t);
-  t->dev_bytes = (size_t)(t->every + 1) * 5 * g->N * 8 + (size_t)(t->every + 1) * 8 +
-                 (size_t)25 * g->N * 8 + kAccCount * 8 + (size_t)3 * adj_blocks(g->N) * 8 +
-                 (g->prec == VSV_MIXED ? (size_t)18 * g->N * 4 : 0);
+  if (!t->ws)
+    t->dev_bytes = (size_t)(t->every + 1) * 5 * g->N * 8 + (size_t)(t->every + 1) * 8 +
+                   (size_t)25 * g->N * 8 + kAccCount * 8 + (size_t)3 * adj_blocks(g->N) * 8 +
+                   (g->prec == VSV_MIXED ? (size_t)18 * g->N * 4 : 0);
   t->recorded = false;
-  t->ck_bytes = 2 * sizeof(double);
-  for (auto& f : state_fields(g)) t->ck_bytes += f.second;
+  t->ck_bytes = tape_ck_bytes(g);
   vsv_status st = vsv_set_phi(g, phi0, dtype, on_device);
   if (st != VSV_OK) return st;
   if ((st = tape_save(t, 0)) != VSV_OK) return st;

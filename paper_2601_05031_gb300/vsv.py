@@ -91,7 +91,7 @@ EXPORTS = [
     "vsv_last_error",
     "vsv_kernel_launches",
     "vsv_kernel_bytes", "vsv_profile_enable", "vsv_profile_read", "vsv_batch_create",
-    "vsv_batch_step", "vsv_batch_destroy", "vsv_tape_create", "vsv_tape_destroy",
+    "vsv_batch_step", "vsv_batch_destroy", "vsv_tape_create", "vsv_tape_workspace_bytes", "vsv_tape_create_in", "vsv_tape_destroy",
     "vsv_tape_forward", "vsv_tape_backward", "vsv_tape_set_cycles", "vsv_tape_bytes",
     "vsv_tape_info",
 ]
@@ -139,6 +139,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vsv_batch_step": (i32, [vp, i32, dbl]),
         "vsv_batch_destroy": (i32, [vp]),
         "vsv_tape_create": (i32, [C.POINTER(vp), vp, i32, dbl]),
+        "vsv_tape_workspace_bytes": (i32, [vp, i32, i32, C.POINTER(C.c_size_t)]),
+        "vsv_tape_create_in": (i32, [C.POINTER(vp), vp, i32, i32, dbl, vp, C.c_size_t]),
         "vsv_tape_destroy": (i32, [vp]),
         "vsv_tape_forward": (i32, [vp, vp, i32, i32, i32, dbl]),
         "vsv_tape_backward": (i32, [vp, vp, vp, i32, C.POINTER(dbl)]),
@@ -368,6 +370,27 @@ def vsv_tape_create(g, every, tol=0.0):
     st = lib().vsv_tape_create(C.byref(out), g, every, tol)
     if st != VSV_OK:
         _check(g, st, "vsv_tape_create")
+    return out
+
+
+def vsv_tape_workspace_bytes(g, every, max_steps):
+    """Device bytes of a tape over caller-owned memory (see the header)."""
+    n = C.c_size_t()
+    _check(g, lib().vsv_tape_workspace_bytes(g, every, max_steps, C.byref(n)),
+           "vsv_tape_workspace_bytes")
+    return n.value
+
+
+def vsv_tape_create_in(g, every, max_steps, tol, workspace_ptr, workspace_bytes, check=True):
+    """A tape whose device memory is the caller's workspace (see the
+    header); returns the handle, or (handle, status) with check=False."""
+    out = C.c_void_p()
+    st = lib().vsv_tape_create_in(C.byref(out), g, every, max_steps, tol,
+                                  C.c_void_p(workspace_ptr), workspace_bytes)
+    if not check:
+        return out, st
+    if st != VSV_OK:
+        _check(g, st, "vsv_tape_create_in")
     return out
 
 

@@ -226,3 +226,76 @@ def test_fit_module_small(V):
     assert res["fit"]["final"]["loss"] < res["start"]["loss"]
     assert res["tape"]["checkpoints"] == 5 and res["tape"]["recomputed_steps"] == 20
     assert res["adjoint_kernels"]["launches"] > 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tape_over_caller_owned_memory(V, prec):
+    """A tape whose device memory is the caller's (vsv_tape_create_in, as
+    adjoint.Tape uses it) gives the gradient of a library-allocated tape
+    (vsv_tape_create) bit for bit; it allocates no device memory of its own,
+    rejects a forward pass longer than it was sized for (nothing run), and
+    refuses too small, misaligned or host workspaces."""
+    import ctypes
+    import torch
+    from paper_2601_05031_gb300.sim import Simulation
+    w, dt, target = _case("helfrich_duct")
+    N, every = 5, 2
+    p = V.VSV_FP64 if prec == "fp64" else V.VSV_MIXED
+    res = []
+    for owned in (False, True):
+        sim = Simulation.from_workload(w, p)
+        sp = sim.solver_params()
+        sp.tol = 1e-13 if prec == "fp64" else 1e-11
+        V.vsv_set_solver(sim.g, sp)
+        nb = V.vsv_tape_workspace_bytes(sim.g, every, N)
+        phi0 = torch.from_numpy(w.phi0).to(sim.device).contiguous()
+        tgt = torch.from_numpy(target).to(sim.device)
+        g0 = torch.empty_like(phi0)
+        drops = []
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        if owned:
+            ws = torch.empty(nb, dtype=torch.uint8, device=sim.device)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            t = V.vsv_tape_create_in(sim.g, every, N, 0.0, ws.data_ptr(), nb)
+        else:
+            t = V.vsv_tape_create(sim.g, every, 0.0)
+        V.vsv_tape_forward(t, sim.g, phi0.data_ptr(), V.VSV_DTYPE_F64, 1, N, dt)
+        torch.cuda.synchronize()
+        drops.append(free0 - torch.cuda.mem_get_info()[0])
+        phiN = sim.field(V.VSV_FIELD_PHI, torch.float64, on_device=True)
+        pb = (w.h ** 3 * (phiN - tgt)).contiguous()
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        dk, ds = V.vsv_tape_backward(t, sim.g, pb.data_ptr(), g0.data_ptr(), 1)
+        torch.cuda.synchronize()
+        drops.append(free1 - torch.cuda.mem_get_info()[0])
+        if owned:
+            # the library allocated no device memory for the tape's passes
+            assert drops == [0, 0], drops
+            assert V.vsv_tape_bytes(t) == nb
+            # a longer forward pass than the workspace holds: refused, nothing run
+            st = V.lib().vsv_tape_forward(t, ctypes.c_void_p(phi0.data_ptr()), V.VSV_DTYPE_F64, 1,
+                                          N + every, dt)
+            assert st == V.VSV_ENOMEM
+        else:
+            assert drops[0] > 0, drops   # the allocating tape's checkpoints
+        res.append((g0.cpu().numpy(), dk, ds))
+        V.vsv_tape_destroy(t)
+        if owned:
+            # bad workspaces
+            assert V.vsv_tape_create_in(sim.g, every, N, 0.0, ws.data_ptr(), nb - 1,
+                                        check=False)[1] == V.VSV_ENOMEM
+            assert V.vsv_tape_create_in(sim.g, every, N, 0.0, ws.data_ptr() + 16, nb - 256,
+                                        check=False)[1] == V.VSV_EINVAL
+            host = np.zeros(nb + 256, dtype=np.uint8)
+            hp = (host.ctypes.data + 255) // 256 * 256
+            assert V.vsv_tape_create_in(sim.g, every, N, 0.0, hp, nb, check=False)[1] == V.VSV_EINVAL
+            assert V.vsv_tape_create_in(sim.g, 0, N, 0.0, ws.data_ptr(), nb,
+                                        check=False)[1] == V.VSV_EINVAL
+            del ws
+        sim.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2]
+    assert np.any(res[0][0] != 0)
