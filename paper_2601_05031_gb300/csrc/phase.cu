@@ -102,7 +102,6 @@ __global__ void k_phi_update(PhaseParams P, const T* __restrict__ phi, const T* 
 template <class T>
 __global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, const T* __restrict__ phi_lo,
                             double* partials) {
-  const long long n = (long long)P.nx * P.ny * P.nz;
   ScalarView<T> F{phi, P.nx, P.ny, P.nz, P.zper};
   const T hih = (T)(0.5 * P.inv_h);
   const T c_a = (T)(3.0 / (2.0 * 1.4142135623730951));
@@ -374,7 +373,6 @@ __global__ void k_diag(PhaseParams P, const T* __restrict__ phi, const T* __rest
                        Comp3<T> vel_lo, Comp3<T> omega, Comp3<T> om_lo, Comp3<T> psi,
                        Comp3<T> ps_lo, Comp3<const double> psi0r, Comp3<const double> v0d,
                        T* sigma_t, double* partials) {
-  const long long n = (long long)P.nx * P.ny * P.nz;
   double q[kDiagQ];
   for (int a = 0; a < kDiagQ; ++a) q[a] = 0.0;
   const double hih = 0.5 * P.inv_h, eta = 1.0 / P.inv_eta, h = P.h;
@@ -1133,21 +1131,22 @@ __global__ void __launch_bounds__(256) k_source_ff4(PhaseParams P, const float* 
   *reinterpret_cast<float4*>(f_lo.p[2] + t) = make_float4(o2l[0], o2l[1], o2l[2], o2l[3]);
 }
 
-// Partial sums of sum(phi) and of the area density over 4-cell groups,
-// grid-strided; one (phi, area) pair per block, as k_reduce_va.
+// Partial sums of sum(phi) and of the area density over 4-cell groups; one
+// (phi, area) pair per block, as k_reduce_va.  Each warp takes whole x rows
+// (row index and plane from one 32-bit division per row), its lanes the
+// rows' 4-cell groups.
 __global__ void __launch_bounds__(256) k_reduce_va_ff4(PhaseParams P, const float* __restrict__ phi,
                                                        const float* __restrict__ phi_lo,
                                                        double* partials) {
   const int ng = P.nx >> 2;
-  const long long total = (long long)ng * P.ny * P.nz;
+  const int rows = P.ny * P.nz;
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   const FF agf{P.ag_hi, P.ag_lo}, awf{P.aw_hi, P.aw_lo};
   CascadeSum cp(0.f), ca(0.f);
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long row = t / ng;
-    const int i0 = 4 * (int)(t - row * ng);
-    const int j = (int)(row % P.ny), k = (int)(row / P.ny);
-    const Geo4 G = geo4(P, i0, j, k, false);
+  for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += gridDim.x * wpb)
+  for (int gi = lane; gi < ng; gi += 32) {
+    const int k = row / P.ny, j = row - k * P.ny;
+    const Geo4 G = geo4(P, 4 * gi, j, k, false);
     const St4 H = load4(phi, G), L = load4(phi_lo, G);
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
@@ -1389,7 +1388,6 @@ void launch_convert(Ctx& cx, const Tin* in, Tout* out, long long n) {
 template <class T>
 void launch_full_field(Ctx& cx, const PhaseParams& P, const T* pert, const T* lo, const double* tab,
                        int ring, T* out) {
-  const long long n = (long long)P.nx * P.ny * P.nz;
   cx.before(-1);
   k_full_field<T><<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, pert, lo, tab, ring, out);
   cx.after(-1);
