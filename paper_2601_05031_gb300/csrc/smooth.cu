@@ -14,7 +14,9 @@
 // x = x0 + 4 gx, rows ty and ty + 8.  It keeps its groups of planes p-2 .. p+1
 // in registers (z-neighbours never touch shared memory); x / y neighbours come
 // from the staged plane in shared memory by 128-bit loads.  Warps 0 and 7
-// also do the red cells of the halo rows, 36 threads the two halo columns.
+// also do the red cells of the halo rows, warp 1 those of the two halo
+// columns beside the owned rows (the ring's corners are never read: the
+// black cells next to them are not updated).
 //
 // Staging (two steps of copies in flight, a ring of six x planes and five
 // rhs planes in shared memory, split layout of tile.cuh: body rows of the
@@ -381,8 +383,10 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
         const float* cBq = rb0;
   #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          Le[h] = gx == 0 ? hA(cAq, rown[h])[kHX - 1] : 0.f;
-          Re[h] = gx == 31 ? hA(cAq, rown[h])[kHX] : 0.f;
+          // lanes 0 and 31 need x0 - 1 and x0 + kTX: one load for both
+          const float e = hA(cAq, rown[h])[gx == 31 ? kHX : kHX - 1];
+          Le[h] = gx == 0 ? e : 0.f;
+          Re[h] = gx == 31 ? e : 0.f;
         }
         U0 = lds4(cAq + (rown[0] - 1) * kTX + 4 * gx);
         D1 = lds4(cAq + (rown[1] + 1) * kTX + 4 * gx);
@@ -442,8 +446,9 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
       if (red) {
   #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          Ler[h] = gx == 0 ? hA(cA, rown[h])[kHX - 1] : 0.f;
-          Rer[h] = gx == 31 ? hA(cA, rown[h])[kHX] : 0.f;
+          const float e = hA(cA, rown[h])[gx == 31 ? kHX : kHX - 1];
+          Ler[h] = gx == 0 ? e : 0.f;
+          Rer[h] = gx == 31 ? e : 0.f;
         }
         U0r = lds4(cA + (rown[0] - 1) * kTX + 4 * gx);
         D1r = lds4(cA + (rown[1] + 1) * kTX + 4 * gx);
@@ -491,9 +496,9 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
           }
         }
       }
-      if (tid >= 32 && tid < 32 + 2 * (kRA - 2)) {   // halo columns x0 - 1 and x0 + kTX
+      if ((tid >> 5) == 1) {   // halo columns x0 - 1 and x0 + kTX beside the own rows
         const int idx = tid - 32;
-        const int r = 1 + (idx >> 1);
+        const int r = kH + (idx >> 1);
         const int side = idx & 1;                     // 0: x0 - 1, 1: x0 + kTX
         const int hc = side ? kHX : kHX - 1;          // its place in the halo row
         const int j = y0 - kH + r;
@@ -568,9 +573,9 @@ k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<f
             else { dst[1] = Vn.y; dst[3] = Vn.w; }
           }
         }
-        if (tid >= 32 && tid < 32 + 2 * (kRA - 2)) {   // halo columns x0 - 1 and x0 + kTX
+        if ((tid >> 5) == 1) {   // halo columns x0 - 1 and x0 + kTX beside the own rows
           const int idx = tid - 32;
-          const int r = 1 + (idx >> 1);
+          const int r = kH + (idx >> 1);
           const int side = idx & 1;                     // 0: x0 - 1, 1: x0 + kTX
           const int hc = side ? kHX : kHX - 1;          // its place in the halo row
           const int j = y0 - kH + r;
