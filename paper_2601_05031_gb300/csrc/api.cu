@@ -101,6 +101,13 @@ struct vsv_grid {
   std::vector<Level> omega_levels;
   double omega_dt = 0.0;
   int* flag_host = nullptr;        // pinned copy of the device non-finite flag
+  // component-parallel flow solves: the first component of the
+  // per-component scratch the current solve uses, the two extra streams the
+  // components 1 and 2 run on, and the events that fork and join them
+  int c0 = 0;
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[2] = {nullptr, nullptr};
   unsigned* bar_count = nullptr;   // arrival counter of the persistent V-cycle's grid barriers
   cudaEvent_t flag_event = nullptr;
   bool flag_pending = false;
@@ -397,6 +404,14 @@ Comp3<T> ps_low(vsv_grid* g) {
 }
 
 // ---------------------------------------------------------------- solvers
+// Components c0, c0 + 1, ... of a per-component buffer array (a solve of
+// fewer than three components from component c0 uses the leading ones).
+template <class T, class P>
+Comp3<T> cview(P* const a[3], int c0) {
+  return Comp3<T>{{(T*)a[c0], c0 + 1 < 3 ? (T*)a[c0 + 1] : nullptr,
+                   c0 + 2 < 3 ? (T*)a[c0 + 2] : nullptr}};
+}
+
 // Relaxation weight of the multigrid smoothing sweeps (all levels but the
 // coarsest, which is solved by plain Gauss-Seidel sweeps): omega_mg, with 0
 // meaning 1.
@@ -417,7 +432,7 @@ bool smooth(vsv_grid* g, const Level& L, int l, Comp3<T> X, Rhs3<T> R, int ncomp
   const double w = mg_weight(g);
   if constexpr (std::is_same<T, float>::value) {
     if (g->sol.variant != 1 && fused_sweep_ok(L, g->sol.variant == 0) && g->mg_t[l][0] && nu >= 2) {
-      Comp3<float> Tt = comp3<float>(g->mg_t[l][0], g->mg_t[l][1], g->mg_t[l][2]);
+      Comp3<float> Tt = cview<float>(g->mg_t[l], g->c0);
       const int zchunk = 0;   // chosen by the launcher
       const bool fuse_upd = uh && ul && nu % 2 == 0;
       bool z = x_zero;
@@ -564,8 +579,8 @@ bool vcycle(vsv_grid* g, const std::vector<Level>& lv, int l, Comp3<T> X, Rhs3<T
   }
   smooth<T>(g, L, l, X, R, ncomp, g->sol.nu1, x_zero);
   const Level& C = lv[l + 1];
-  Comp3<T> EC = comp3<T>(g->mg_e[l + 1][0], g->mg_e[l + 1][1], g->mg_e[l + 1][2]);
-  Comp3<T> RC = comp3<T>(g->mg_r[l + 1][0], g->mg_r[l + 1][1], g->mg_r[l + 1][2]);
+  Comp3<T> EC = cview<T>(g->mg_e[l + 1], g->c0);
+  Comp3<T> RC = cview<T>(g->mg_r[l + 1], g->c0);
   const bool exact = std::is_same<T, float>::value && l == 0 && exact_fine;
   launch_resid_restrict<T>(g->cx, L, C, X, R, RC, ncomp, exact);
   Rhs3<T> RCr{{RC.p[0], RC.p[1], RC.p[2]}, {nullptr, nullptr, nullptr}, (T)1};
@@ -659,8 +674,8 @@ vsv_status solve_dc(vsv_grid* g, const std::vector<Level>& lv, Comp3<float> XH, 
                     Rhs3<float> R, Comp3<float> BL, int ncomp, int fixed, double tol,
                     int max_cycles, int check_every, int* cycles_out, double* relres_out) {
   const Level& L = lv[0];
-  Comp3<float> E = comp3<float>(g->e0[0], g->e0[1], g->e0[2]);
-  Comp3<float> RR = comp3<float>(g->r0[0], g->r0[1], g->r0[2]);
+  Comp3<float> E = cview<float>(g->e0, g->c0);
+  Comp3<float> RR = cview<float>(g->r0, g->c0);
   Rhs3<float> RE{{RR.p[0], RR.p[1], RR.p[2]}, {nullptr, nullptr, nullptr}, 1.f};
   auto correct = [&]() {
     if (!vcycle<float>(g, lv, 0, E, RE, ncomp, false, true, &XH, &XL))
@@ -822,17 +837,16 @@ Rhs3<T> rhs_psi(vsv_grid* g) {
 // x^{n-1}), so no field is copied.
 template <class T>
 void guess_from_history(vsv_grid* g, void* x[3], void* xp[3], void* xpp[3], float* xl[3],
-                        float* xpl[3], float* xppl[3], int order) {
+                        float* xpl[3], float* xppl[3], int order, int c0 = 0, int ncomp = 3) {
   const bool mixed = std::is_same<T, float>::value && g->prec == VSV_MIXED;
   if (mixed)
-    launch_extrapolate_rot_dw(g->cx, comp3<float>(x[0], x[1], x[2]), comp3<float>(xl[0], xl[1], xl[2]),
-                              comp3<float>(xp[0], xp[1], xp[2]), comp3<float>(xpl[0], xpl[1], xpl[2]),
-                              comp3<float>(xpp[0], xpp[1], xpp[2]),
-                              comp3<float>(xppl[0], xppl[1], xppl[2]), g->N, 3, order);
+    launch_extrapolate_rot_dw(g->cx, cview<float>(x, c0), cview<float>(xl, c0), cview<float>(xp, c0),
+                              cview<float>(xpl, c0), cview<float>(xpp, c0), cview<float>(xppl, c0),
+                              g->N, ncomp, order);
   else
-    launch_extrapolate_rot<T>(g->cx, comp3<T>(x[0], x[1], x[2]), comp3<T>(xp[0], xp[1], xp[2]),
-                              comp3<T>(xpp[0], xpp[1], xpp[2]), g->N, 3, order);
-  for (int c = 0; c < 3; ++c) {
+    launch_extrapolate_rot<T>(g->cx, cview<T>(x, c0), cview<T>(xp, c0), cview<T>(xpp, c0), g->N,
+                              ncomp, order);
+  for (int c = c0; c < c0 + ncomp; ++c) {
     void* t = xpp[c];
     xpp[c] = xp[c];
     xp[c] = x[c];
@@ -846,12 +860,70 @@ void guess_from_history(vsv_grid* g, void* x[3], void* xp[3], void* xpp[3], floa
   }
 }
 
+// The fixed-cycle mixed solves with the three components on three streams:
+// component c's vorticity solve, then its stream-vector solve (whose rhs is
+// -omega'_c - s_psi,c alone), forked from the grid's stream after the source
+// and joined back before the step goes on.  Every kernel sees the component
+// it would see in the three-component launches, with the same arithmetic,
+// so the results are bit-identical; what changes is that one component's
+// latency-bound lower levels overlap the other components' bandwidth-bound
+// finest-level kernels.
+vsv_status flow_solves_branched(vsv_grid* g, int fixed, int fixed_psi, int order) {
+  const vsv_solver_params& s = g->sol;
+  const cudaStream_t main = g->cx.stream;
+  struct Restore {
+    vsv_grid* g;
+    cudaStream_t main;
+    ~Restore() {
+      g->cx.stream = main;
+      g->c0 = 0;
+    }
+  } restore{g, main};
+  CK(cudaEventRecord(g->fork_ev, main));
+  for (int i = 0; i < 2; ++i) CK(cudaStreamWaitEvent(g->aux[i], g->fork_ev, 0));
+  const std::vector<Level>& lvo =
+      (g->flow.rho > 0.0 && !g->omega_levels.empty()) ? g->omega_levels : g->flow_levels;
+  for (int c = 0; c < 3; ++c) {
+    g->cx.stream = c == 0 ? main : g->aux[c - 1];
+    g->c0 = c;
+    guess_from_history<float>(g, g->om, g->om_prev, g->om_prev2, g->om_lo, g->om_prev_lo,
+                              g->om_prev2_lo, order, c, 1);
+    const Rhs3<float> RO{{(const float*)g->f[c], nullptr, nullptr}, {nullptr, nullptr, nullptr}, 1.f};
+    vsv_status st = solve_dc(g, lvo, cview<float>(g->om, c), cview<float>(g->om_lo, c), RO,
+                             cview<float>(g->f_lo, c), 1, fixed, s.tol, s.max_cycles,
+                             s.check_every, &g->last_cycles[0], &g->last_relres[0]);
+    if (st != VSV_OK) return st;
+    guess_from_history<float>(g, g->ps, g->ps_prev, g->ps_prev2, g->ps_lo, g->ps_prev_lo,
+                              g->ps_prev2_lo, order, c, 1);
+    const Rhs3<float> RP{{(const float*)g->om[c], nullptr, nullptr},
+                         {(const float*)g->s_ps_neg_t[c], nullptr, nullptr}, -1.f};
+    st = solve_dc(g, g->flow_levels, cview<float>(g->ps, c), cview<float>(g->ps_lo, c), RP,
+                  cview<float>(g->om_lo, c), 1, fixed_psi, s.tol, s.max_cycles, s.check_every,
+                  &g->last_cycles[1], &g->last_relres[1]);
+    if (st != VSV_OK) return st;
+  }
+  for (int i = 0; i < 2; ++i) {
+    CK(cudaEventRecord(g->join_ev[i], g->aux[i]));
+    CK(cudaStreamWaitEvent(main, g->join_ev[i], 0));
+  }
+  return VSV_OK;
+}
+
 vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
   const vsv_solver_params& s = g->sol;
   const int fixed = initial ? 0 : s.fixed_cycles;
   const int fixed_psi = (initial || !s.fixed_cycles) ? fixed
                         : (s.fixed_cycles_psi > 0 ? s.fixed_cycles_psi : s.fixed_cycles);
   const int order = std::min(s.extrapolate, g->hist);
+  // component streams: fixed cycles (no norms across components), no
+  // single-launch lower cycle (its barrier counter is shared), and no kernel
+  // class being timed by events (they assume one launch at a time)
+  if (!initial && fixed > 0 && fixed_psi > 0 && s.component_streams && s.lower_cycle == 0 &&
+      g->cx.prof_class < 0) {
+    const vsv_status st = flow_solves_branched(g, fixed, fixed_psi, order);
+    g->hist = std::min(g->hist + 1, 2);
+    return st;
+  }
   if (!initial)
     guess_from_history<float>(g, g->om, g->om_prev, g->om_prev2, g->om_lo, g->om_prev_lo,
                               g->om_prev2_lo, order);
@@ -1289,6 +1361,7 @@ void default_solver(vsv_solver_params* s, int prec) {
   s->fixed_cycles_psi = 0;
   s->omega_mg = kDefaultMgWeight;
   s->lower_cycle = 0;
+  s->component_streams = 1;
 }
 
 }  // namespace
@@ -1337,11 +1410,15 @@ vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int prec
   }
   // the handle's page-locked word for vsv_step's deferred status, and the
   // event that marks its arrival (created here: stepping allocates nothing)
-  if (cudaMallocHost((void**)&g->flag_host, sizeof(int)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&g->flag_event, cudaEventDisableTiming) != cudaSuccess) {
+  bool ok = cudaMallocHost((void**)&g->flag_host, sizeof(int)) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->flag_event, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
-    if (g->flag_host) cudaFreeHost(g->flag_host);
-    delete g;
+    vsv_destroy(g);
     return VSV_ECUDA;
   }
   *g->flag_host = 0;
@@ -1358,6 +1435,14 @@ vsv_status vsv_destroy(vsv_grid* g) {
     cudaEventDestroy(g->flag_event);
   }
   if (g->flag_host) cudaFreeHost(g->flag_host);
+  for (int i = 0; i < 2; ++i) {
+    if (g->aux[i]) {
+      cudaStreamSynchronize(g->aux[i]);
+      cudaStreamDestroy(g->aux[i]);
+    }
+    if (g->join_ev[i]) cudaEventDestroy(g->join_ev[i]);
+  }
+  if (g->fork_ev) cudaEventDestroy(g->fork_ev);
   delete g;
   return VSV_OK;
 }
@@ -1481,7 +1566,7 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
       sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->fixed_cycles_psi < 0 || sp->max_levels < 1 || !(sp->tol >= 0) ||
       sp->variant < 0 || sp->variant > 2 || sp->extrapolate < 0 || sp->extrapolate > 2 ||
       !(sp->omega_mg >= 0.0 && sp->omega_mg < 2.0) || sp->lower_cycle < 0 ||
-      sp->lower_cycle > 1)
+      sp->lower_cycle > 1 || sp->component_streams < 0 || sp->component_streams > 1)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
   g->cx.tiled = sp->variant != 1;

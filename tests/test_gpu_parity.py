@@ -544,3 +544,38 @@ def test_fused_mixed_solve_vs_oracle(V):
     ref = solve_poisson(b, 1.0, (True, False, True))
     assert st == V.VSV_OK and rel(x, ref) < 1e-9, (rel(x, ref), cyc, rr)
     sim.close()
+
+
+@pytest.mark.parametrize("kind", ["couette", "duct", "inertial"])
+def test_component_streams_bit_identical(V, kind):
+    """Fixed-cycle steps with each component's vorticity and stream-vector
+    solves on a stream of its own give the bits of the three components
+    together on the grid's stream: over plain steps, and over the replays of
+    a captured graph (the component streams fork and join inside it)."""
+    import torch
+    from paper_2601_05031_gb300.sim import Batch
+    flow = inputs.POISEUILLE_DUCT if kind == "duct" else inputs.COUETTE
+    w = inputs.vesicle(256, 32, 32, flow, 0.85, 1.0, dt=1e-4, b_range=(0.25, 0.3))
+    if kind == "inertial":
+        w.rho = 0.5
+    res = []
+    for cs in (0, 1):
+        from paper_2601_05031_gb300.sim import Simulation
+        sim = Simulation.from_workload(w, V.VSV_MIXED, stream=torch.cuda.Stream())
+        sp = sim.solver_params()
+        sp.fixed_cycles = 2
+        sp.extrapolate = 2
+        sp.component_streams = cs
+        V.vsv_set_solver(sim.g, sp)
+        sim.set_phi(w.phi0)
+        sim.step(4, w.dt)
+        b = Batch([sim])
+        b.step(6, w.dt)
+        b.close()
+        assert V.vsv_check(sim.g, check=False) == V.VSV_OK
+        res.append([sim.field(V.VSV_FIELD_PHI)] +
+                   [sim.field(V.VSV_FIELD_VEL_X + c) for c in range(3)] +
+                   [sim.field(V.VSV_FIELD_OMEGA_X + c) for c in range(3)])
+        sim.close()
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
