@@ -202,18 +202,20 @@ typedef struct {
                              Bit-identical results either way; on GB300 the
                              single launch measured slower at every size
                              tried.  Outside 0..1: VSV_EINVAL. */
-  int component_streams;  /* 1 (default): fixed-cycle mixed-precision steps
-                             run each component's vorticity and
-                             stream-vector solves on a stream of its own
-                             (two created with the grid, forked from and
-                             joined back to the grid's stream within the
-                             step, also inside captured graphs), so that
-                             one component's latency-bound coarse levels
-                             overlap the others' finest-level kernels;
-                             bit-identical results.  0: the components
-                             together on the grid's stream.  Off while a
-                             kernel class is being profiled or with
-                             lower_cycle = 1.  Outside 0..1: VSV_EINVAL. */
+  int component_streams;  /* 1: fixed-cycle mixed-precision steps run each
+                             component's vorticity and stream-vector solves
+                             on a stream of its own (two created with the
+                             grid, forked from and joined back to the grid's
+                             stream within the step, also inside captured
+                             graphs), so that one component's latency-bound
+                             coarse levels overlap the others' finest-level
+                             kernels; bit-identical results.  0: the
+                             components together on the grid's stream.  2
+                             (default): 1 on grids of at least 2^24 cells,
+                             else 0 (on small grids the tripled launch count
+                             costs more than the overlap gains).  Off while
+                             a kernel class is being profiled or with
+                             lower_cycle = 1.  Outside 0..2: VSV_EINVAL. */
 } vsv_solver_params;
 
 /* Per-axis boundary of a standalone Poisson problem: periodic (1) or zero
