@@ -78,6 +78,15 @@ typedef enum { VSV_CAHN_HILLIARD = 0, VSV_HELFRICH = 1 } vsv_fe_kind;
 typedef enum { VSV_SOLVER_MG = 0, VSV_SOLVER_SOR = 1 } vsv_solver_kind;
 typedef enum { VSV_DTYPE_F32 = 0, VSV_DTYPE_F64 = 1 } vsv_dtype;
 
+/* Memory kind of the on_device argument of the transfer calls: 0 host
+ * memory (synchronous: the call returns when the data has moved), 1 device
+ * memory, VSV_HOST_ASYNC page-locked host memory moved asynchronously (FP64
+ * phi on the mixed path: vsv_set_field and vsv_get_field enqueue the copy on
+ * a copy stream of the grid's and return at once; the host buffer must stay
+ * unchanged after a set, and holds the data after a get, only once vsv_check
+ * has returned; for every other field, dtype or precision it acts as 0). */
+#define VSV_HOST_ASYNC 2
+
 typedef enum {
   VSV_FIELD_PHI = 0,
   VSV_FIELD_MU = 1,
@@ -321,18 +330,23 @@ vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, i
                              double* relres_out);
 
 /* Copy a field out (full omega / psi include the base flow).  Synchronous
- * for host destinations.  On the mixed path an FP64 phi goes to page-locked,
- * mapped host memory (cudaHostAlloc / cudaMallocHost, or cudaHostRegister
- * under unified addressing) straight from the kernel that merges the two
- * words; any other host memory is filled through a device staging buffer
- * and a copy.  The bits are the same either way; dst needs no alignment. */
+ * for host destinations (on_device 0).  On the mixed path an FP64 phi is
+ * merged from its two words into a device staging buffer and crosses to
+ * host memory by the copy engine (faster over the host link than a kernel
+ * writing mapped memory); with on_device = VSV_HOST_ASYNC that copy runs on
+ * the grid's export stream and the call returns at once (valid after
+ * vsv_check).  The bits are the same either way; dst needs no alignment. */
 vsv_status vsv_get_field(vsv_grid* g, int field, void* dst, int dtype, int on_device);
 
 /* Replace phi (mu, V, A are recomputed before the next step; V0, A0 and the
  * flow are kept) or a perturbation component OMEGA_PERT_* / PSI_PERT_*.  On
  * the mixed path FP64 input in page-locked, mapped host memory is read in
  * place by the kernel that splits it into the two words; other host memory
- * is copied through a staging buffer first. */
+ * is copied through a staging buffer first.  With on_device =
+ * VSV_HOST_ASYNC (FP64 phi, mixed path) the copy engine fills a staging
+ * buffer on the grid's import stream, overlapping the grid's earlier work,
+ * the split waits for it, and the call returns at once (src must stay
+ * unchanged until vsv_check). */
 vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int on_device);
 
 /* Observables of the current state; synchronises. */

@@ -58,6 +58,13 @@ struct vsv_grid {
   float* r0[3] = {};
   void* stage_a = nullptr;   // N * 8 bytes
   void* stage_b = nullptr;   // N * 8 bytes
+  // mixed path: staging of the asynchronous FP64 phi transfers (N * 8 bytes
+  // each), used by nothing else, the copy streams that move them and the
+  // events that order them against the grid's stream
+  void* stage_in = nullptr;
+  void* stage_out = nullptr;
+  cudaStream_t io_in = nullptr, io_out = nullptr;
+  cudaEvent_t in_ready = nullptr, in_free = nullptr, out_ready = nullptr, out_free = nullptr;
   void* mg_e[kMaxLevels][3] = {};
   void* mg_r[kMaxLevels][3] = {};
   void* mg_t[kMaxLevels][3] = {};  // ping-pong partner of the fused sweep (mixed path)
@@ -101,6 +108,7 @@ struct vsv_grid {
   std::vector<Level> omega_levels;
   double omega_dt = 0.0;
   int* flag_host = nullptr;        // pinned copy of the device non-finite flag
+  int* flag_dev = nullptr;         // its device address (mapped)
   // component-parallel flow solves: the first component of the
   // per-component scratch the current solve uses, the two extra streams the
   // components 1 and 2 run on, and the events that fork and join them
@@ -204,6 +212,10 @@ size_t carve(int nx, int ny, int nz, int prec, vsv_grid* g, char* base) {
   for (int c = 0; c < 3; ++c) { p = tf(N); if (g) g->ps_prev2[c] = p; }
   p = take((size_t)N * 8); if (g) g->stage_a = p;
   p = take((size_t)N * 8); if (g) g->stage_b = p;
+  if (prec == VSV_MIXED) {
+    p = take((size_t)N * 8); if (g) g->stage_in = p;
+    p = take((size_t)N * 8); if (g) g->stage_out = p;
+  }
   long long cells[kMaxLevels];
   const int nl = plan_levels(nx, ny, nz, cells);
   if (g) g->mg_nlev_cap = nl;
@@ -271,6 +283,14 @@ vsv_status flag_status(vsv_grid* g, int flag) {
   if (flag & kCopyTimeout)
     return fail(g, VSV_ECUDA, "a wait of the fused sweep for its staged planes ran out of time%s");
   return VSV_OK;
+}
+
+// The step's status word into the handle's page-locked, mapped host word.
+// A kernel writes it rather than a copy, so it does not queue behind large
+// transfers on the copy engines (an asynchronous export of phi, say).
+__global__ void k_flag_out(const int* __restrict__ flag, int* host_flag) {
+  *reinterpret_cast<volatile int*>(host_flag) = *flag;
+  __threadfence_system();
 }
 
 #define CK(call)                                                                      \
@@ -1141,6 +1161,19 @@ vsv_status import_phi(vsv_grid* g, const void* src, int dt, int on_device) {
   if constexpr (std::is_same<T, float>::value) {
     float* lo = g->phi_lo[g->cur];
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (dt == VSV_DTYPE_F64 && on_device == VSV_HOST_ASYNC) {
+      // the copy engine fills the import stage on its own stream once the
+      // previous split has read it; the split waits for the copy; the call
+      // returns at once
+      CK(cudaStreamWaitEvent(g->io_in, g->in_free, 0));
+      CK(cudaMemcpyAsync(g->stage_in, src, g->N * 8, cudaMemcpyHostToDevice, g->io_in));
+      CK(cudaEventRecord(g->in_ready, g->io_in));
+      CK(cudaStreamWaitEvent(g->cx.stream, g->in_ready, 0));
+      launch_split_ff(g->cx, (const double*)g->stage_in, hi, lo, g->N);
+      CKL();
+      CK(cudaEventRecord(g->in_free, g->cx.stream));
+      return VSV_OK;
+    }
     if (dt == VSV_DTYPE_F64) {
       const vsv_status st = split_in(g, src, on_device, hi, lo);
       if (st != VSV_OK) return st;
@@ -1164,6 +1197,19 @@ vsv_status export_phi(vsv_grid* g, int dt, int on_device, void* dst) {
       // the merged words from the staging buffer by the copy engine, which
       // crosses the host link about twice as fast as a kernel writing mapped
       // memory (193 against 81 GB/s measured on GB300 at 268 MB)
+      if (on_device == VSV_HOST_ASYNC) {
+        // merged into the export stage once its previous copy has left, then
+        // copied out on the export stream while the grid's stream goes on
+        CK(cudaStreamWaitEvent(g->cx.stream, g->out_free, 0));
+        launch_merge_ff(g->cx, (const float*)g->phi[g->cur], g->phi_lo[g->cur],
+                        (double*)g->stage_out, g->N);
+        CKL();
+        CK(cudaEventRecord(g->out_ready, g->cx.stream));
+        CK(cudaStreamWaitEvent(g->io_out, g->out_ready, 0));
+        CK(cudaMemcpyAsync(dst, g->stage_out, g->N * 8, cudaMemcpyDeviceToHost, g->io_out));
+        CK(cudaEventRecord(g->out_free, g->io_out));
+        return VSV_OK;
+      }
       if (on_device) {
         launch_merge_ff(g->cx, (const float*)g->phi[g->cur], g->phi_lo[g->cur], (double*)dst, g->N);
         CKL();
@@ -1416,11 +1462,16 @@ vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int prec
   // the handle's page-locked word for vsv_step's deferred status, and the
   // event that marks its arrival (created here: stepping allocates nothing)
   bool ok = cudaMallocHost((void**)&g->flag_host, sizeof(int)) == cudaSuccess &&
+            cudaHostGetDevicePointer((void**)&g->flag_dev, g->flag_host, 0) == cudaSuccess &&
             cudaEventCreateWithFlags(&g->flag_event, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; i < 2 && ok; ++i)
     ok = cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&g->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&g->io_in, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&g->io_out, cudaStreamNonBlocking) == cudaSuccess;
+  for (cudaEvent_t* e : {&g->in_ready, &g->in_free, &g->out_ready, &g->out_free})
+    ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     vsv_destroy(g);
@@ -1448,6 +1499,13 @@ vsv_status vsv_destroy(vsv_grid* g) {
     if (g->join_ev[i]) cudaEventDestroy(g->join_ev[i]);
   }
   if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+  for (cudaStream_t st : {g->io_in, g->io_out})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (cudaEvent_t e : {g->in_ready, g->in_free, g->out_ready, g->out_free})
+    if (e) cudaEventDestroy(e);
   delete g;
   return VSV_OK;
 }
@@ -1584,8 +1642,19 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
   return VSV_OK;
 }
 
+// on_device as the transfer calls take it: VSV_HOST_ASYNC is honoured for
+// FP64 phi on the mixed path; anywhere else it means synchronous host memory.
+static int transfer_kind(const vsv_grid* g, int field, int dtype, int on_device) {
+  if (on_device != VSV_HOST_ASYNC) return on_device;
+  return (field == VSV_FIELD_PHI && dtype == VSV_DTYPE_F64 && g->prec == VSV_MIXED) ? VSV_HOST_ASYNC
+                                                                                    : 0;
+}
+
 vsv_status vsv_set_phi(vsv_grid* g, const void* phi, int dtype, int on_device) {
-  if (!g || !phi || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64)) return VSV_EINVAL;
+  if (!g || !phi || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64) || on_device < 0 ||
+      on_device > VSV_HOST_ASYNC)
+    return VSV_EINVAL;
+  if (on_device == VSV_HOST_ASYNC) on_device = 0;   // the initial solves synchronise anyway
   if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_set_phi%s");
   g->err.clear();
   vsv_status st;
@@ -1655,8 +1724,10 @@ vsv_status vsv_step(vsv_grid* g, int nsteps, double dt) {
     if (st != VSV_OK) return st;
   }
   CKL();
-  CK(cudaMemcpyAsync(g->flag_host, &g->S->nonfinite, sizeof(int), cudaMemcpyDeviceToHost,
-                     g->cx.stream));
+  // (not counted in the grid's launches, like the copy it replaces: a
+  // captured batch of the same steps reads the word its own way)
+  k_flag_out<<<1, 1, 0, g->cx.stream>>>(&g->S->nonfinite, g->flag_dev);
+  CKL();
   CK(cudaEventRecord(g->flag_event, g->cx.stream));
   g->flag_pending = true;
   return VSV_OK;
@@ -1879,8 +1950,10 @@ vsv_status vsv_batch_step(vsv_batch* b, int nsteps, double dt) {
 vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, int on_device,
                              const vsv_bc* bc, double tol, int max_cycles, int* cycles_out,
                              double* relres_out) {
-  if (!g || !rhs || !x || !bc || max_cycles < 1 || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64))
+  if (!g || !rhs || !x || !bc || max_cycles < 1 || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64) ||
+      on_device < 0 || on_device > VSV_HOST_ASYNC)
     return VSV_EINVAL;
+  if (on_device == VSV_HOST_ASYNC) on_device = 0;
   const int per[3] = {bc->periodic[0] ? 1 : 0, bc->periodic[1] ? 1 : 0, bc->periodic[2] ? 1 : 0};
   const int n[3] = {g->nx, g->ny, g->nz};
   for (int a = 0; a < 3; ++a)
@@ -1954,15 +2027,20 @@ vsv_status vsv_solve_poisson(vsv_grid* g, const void* rhs, void* x, int dtype, i
 
 vsv_status vsv_get_field(vsv_grid* g, int field, void* dst, int dtype, int on_device) {
   if (!g || !dst || field < 0 || field >= VSV_FIELD_COUNT ||
-      (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64))
+      (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64) || on_device < 0 ||
+      on_device > VSV_HOST_ASYNC)
     return VSV_EINVAL;
+  on_device = transfer_kind(g, field, dtype, on_device);
   if (!g->phi_set) return fail(g, VSV_ESTATE, "no state: call vsv_set_phi first%s");
   return g->prec == VSV_FP64 ? get_field_impl<double>(g, field, dst, dtype, on_device)
                              : get_field_impl<float>(g, field, dst, dtype, on_device);
 }
 
 vsv_status vsv_set_field(vsv_grid* g, int field, const void* src, int dtype, int on_device) {
-  if (!g || !src || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64)) return VSV_EINVAL;
+  if (!g || !src || (dtype != VSV_DTYPE_F32 && dtype != VSV_DTYPE_F64) || on_device < 0 ||
+      on_device > VSV_HOST_ASYNC)
+    return VSV_EINVAL;
+  on_device = transfer_kind(g, field, dtype, on_device);
   if (!g->phi_set) return fail(g, VSV_ESTATE, "no state: call vsv_set_phi first%s");
   void* dst = nullptr;
   if (field == VSV_FIELD_PHI) {
@@ -2175,6 +2253,8 @@ vsv_status vsv_set_state(vsv_grid* g, const void* src, size_t bytes) {
 vsv_status vsv_check(vsv_grid* g) {
   if (!g) return VSV_EINVAL;
   CK(cudaStreamSynchronize(g->cx.stream));
+  if (g->io_in) CK(cudaStreamSynchronize(g->io_in));
+  if (g->io_out) CK(cudaStreamSynchronize(g->io_out));
   CKL();
   int flag = 0;
   CK(cudaMemcpy(&flag, &g->S->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
@@ -2686,7 +2766,9 @@ extern "C" {
 
 vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_device, int nsteps,
                             double dt) {
-  if (!t || !phi0 || nsteps < 1 || !(dt > 0)) return VSV_EINVAL;
+  if (!t || !phi0 || nsteps < 1 || !(dt > 0) || on_device < 0 || on_device > VSV_HOST_ASYNC)
+    return VSV_EINVAL;
+  if (on_device == VSV_HOST_ASYNC) on_device = 0;
   vsv_grid* g = t->g;
   if (!g->flow_set) return fail(g, VSV_ESTATE, "vsv_set_flow must precede vsv_tape_forward%s");
   if (g->motion_on)
@@ -2720,7 +2802,9 @@ vsv_status vsv_tape_forward(vsv_tape* t, const void* phi0, int dtype, int on_dev
 
 vsv_status vsv_tape_backward(vsv_tape* t, const double* phibar_final, double* phibar0,
                              int on_device, double* param_bar) {
-  if (!t || !phibar_final || !phibar0) return VSV_EINVAL;
+  if (!t || !phibar_final || !phibar0 || on_device < 0 || on_device > VSV_HOST_ASYNC)
+    return VSV_EINVAL;
+  if (on_device == VSV_HOST_ASYNC) on_device = 0;
   vsv_grid* g = t->g;
   if (!t->recorded) return fail(g, VSV_ESTATE, "vsv_tape_forward must precede vsv_tape_backward%s");
   const long long N = g->N;

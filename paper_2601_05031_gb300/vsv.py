@@ -22,6 +22,7 @@ VSV_POISEUILLE_DUCT, VSV_POISEUILLE_PLANAR, VSV_COUETTE, VSV_QUIESCENT = 0, 1, 2
 VSV_CAHN_HILLIARD, VSV_HELFRICH = 0, 1
 VSV_SOLVER_MG, VSV_SOLVER_SOR = 0, 1
 VSV_DTYPE_F32, VSV_DTYPE_F64 = 0, 1
+VSV_HOST_ASYNC = 2   # on_device: page-locked host memory, asynchronous (see the header)
 (VSV_FIELD_PHI, VSV_FIELD_MU, VSV_FIELD_OMEGA_X, VSV_FIELD_OMEGA_Y, VSV_FIELD_OMEGA_Z,
  VSV_FIELD_PSI_X, VSV_FIELD_PSI_Y, VSV_FIELD_PSI_Z, VSV_FIELD_VEL_X, VSV_FIELD_VEL_Y,
  VSV_FIELD_VEL_Z, VSV_FIELD_STRESS_T, VSV_FIELD_OMEGA_PERT_X, VSV_FIELD_OMEGA_PERT_Y,

@@ -1,6 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
 same seeded inputs.  FP64 path: relative L2 <= 1e-10 on phi and velocity;
 mixed path: <= 1e-6 (tolerances of the hot-path specification)."""
+import ctypes
 import math
 
 import numpy as np
@@ -579,3 +580,39 @@ def test_component_streams_bit_identical(V, kind):
         sim.close()
     for a, b in zip(*res):
         assert np.array_equal(a, b)
+
+
+def test_async_host_transfers_of_phi(V):
+    """VSV_HOST_ASYNC: FP64 phi set from and read into page-locked host
+    memory on the grid's copy streams gives the bits of the synchronous
+    calls, in a loop of set / step / get with no synchronisation but one
+    vsv_check at the end; for other fields the kind acts synchronously; an
+    unknown memory kind is refused."""
+    import torch
+    from paper_2601_05031_gb300.sim import Simulation
+    w = inputs.vesicle(256, 32, 32, inputs.COUETTE, 0.85, 1.0, dt=1e-4, b_range=(0.25, 0.3))
+    shape = (w.nz, w.ny, w.nx)
+    outs = []
+    for kind in (0, V.VSV_HOST_ASYNC):
+        sim = make_sim(V, w, V.VSV_MIXED, fixed=2)
+        sim.set_phi(w.phi0)
+        sim.step(2, w.dt)
+        src = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        src.copy_(torch.from_numpy(sim.field(V.VSV_FIELD_PHI)))
+        dst = [torch.zeros(shape, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+        for n in range(3):
+            V.vsv_set_field(sim.g, V.VSV_FIELD_PHI, src.data_ptr(), V.VSV_DTYPE_F64, kind)
+            sim.step(1, w.dt)
+            V.vsv_get_field(sim.g, V.VSV_FIELD_PHI, dst[n].data_ptr(), V.VSV_DTYPE_F64, kind)
+        V.vsv_check(sim.g)
+        mu = np.zeros(shape)
+        assert V.vsv_get_field(sim.g, V.VSV_FIELD_MU, mu.ctypes.data, V.VSV_DTYPE_F64,
+                               V.VSV_HOST_ASYNC) == V.VSV_OK
+        assert np.array_equal(mu, sim.field(V.VSV_FIELD_MU))   # acted synchronously
+        assert V.lib().vsv_get_field(sim.g, V.VSV_FIELD_PHI, ctypes.c_void_p(dst[0].data_ptr()),
+                                     V.VSV_DTYPE_F64, 3) == V.VSV_EINVAL
+        outs.append([d.numpy().copy() for d in dst])
+        sim.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+        assert np.any(a != 0)
