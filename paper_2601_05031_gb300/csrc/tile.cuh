@@ -1,6 +1,8 @@
 // Plane staging for z-marching tile kernels: cp.async 16-byte copies of a
 // (rows x kW) window of one x-y plane into shared memory, with zero fill on
-// Dirichlet ghost rows / planes and wrap on periodic axes.
+// Dirichlet ghost rows / planes and wrap on periodic axes; and, for the fused
+// sweep, a split layout (tile body, then its halo groups) whose body a TMA
+// tensor-map box fills, with mbarrier helpers whose waits are bounded.
 #pragma once
 
 #include "internal.h"
@@ -105,7 +107,7 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 // orders this thread's earlier shared-memory accesses before later copies
-// of the bulk-copy engine into the same memory
+// of the tensor memory accelerator into the same memory
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
