@@ -897,8 +897,10 @@ vsv_status flow_solves_branched(vsv_grid* g, int fixed, int fixed_psi, int order
     ~Restore() {
       g->cx.stream = main;
       g->c0 = 0;
+      g->cx.chunk_comps = 0;
     }
   } restore{g, main};
+  g->cx.chunk_comps = 3;
   CK(cudaEventRecord(g->fork_ev, main));
   for (int i = 0; i < 2; ++i) CK(cudaStreamWaitEvent(g->aux[i], g->fork_ev, 0));
   const std::vector<Level>& lvo =

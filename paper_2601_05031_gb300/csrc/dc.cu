@@ -406,7 +406,7 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
   using Sh = DefShape<ROWS>;
   const int ntx = (L.n[0] + tile::kTX - 1) / tile::kTX, nty = (L.n[1] + Sh::kRows - 1) / Sh::kRows;
   const int tiles = ntx * nty;
-  int chunk = tile::pick_zchunk(L, ncomp, 3 * cx.sms, 2);
+  int chunk = tile::pick_zchunk(L, std::max(ncomp, cx.chunk_comps), 3 * cx.sms, 2);
   chunk = std::max(chunk, 1);
   // pick_zchunk counts 128 x 16 tiles; there are twice as many 8-row tiles
   chunk = std::min(L.n[2], 2 * chunk);

@@ -27,6 +27,10 @@ struct Ctx {
   int tiled = 1;                 // use the tiled transfer kernels (solver variants 0 and 2)
   int ragged = 1;                // also with partial edge tiles (solver variant 0)
   int* status = nullptr;         // device flag word (bounded waits report timeouts here)
+  // > 0: the z-marching kernels pick their z-chunks as for this many
+  // components (one-component launches of the component streams, which run
+  // side by side, keep the chunks of the three-component launch)
+  int chunk_comps = 0;
   std::vector<TensorMapEntry> tmaps;   // tensor maps encoded so far (fields do not move)
   long long launches = 0;
   int prof_class = -1;

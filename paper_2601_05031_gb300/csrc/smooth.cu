@@ -759,7 +759,7 @@ FusedGeom fused_geom(Ctx& cx, const Level& L, Rhs3<float> R, int ncomp, int zchu
   G.ntx = (L.n[0] + kTX - 1) / kTX; G.nty = (L.n[1] + kTY - 1) / kTY;
   // a step costs about three planes of pipeline fill; chunks down to four
   // planes let the small levels spread over more SMs
-  if (zchunk <= 0) zchunk = pick_zchunk(L, ncomp, 2 * cx.sms, 3, 4);
+  if (zchunk <= 0) zchunk = pick_zchunk(L, std::max(ncomp, cx.chunk_comps), 2 * cx.sms, 3, 4);
   G.zchunk = std::min(zchunk, L.n[2]);
   // omega rc and 1 - omega rounded in FP32 as relax() and wscale() form them
   G.rc0 = omega * L.rcf[0];

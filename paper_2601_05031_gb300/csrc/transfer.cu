@@ -309,7 +309,7 @@ bool launch_restrict_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float>
   if (!tiled_transfer_ok(F, C, cx.ragged)) return false;
   const bool rg = !level_ok(F);
   RGeom G;
-  static_cast<Geom&>(G) = geom(F, even_chunk(F, ncomp, cx.sms, 2));
+  static_cast<Geom&>(G) = geom(F, even_chunk(F, std::max(ncomp, cx.chunk_comps), cx.sms, 2));
   G.ih2 = F.inv_h2f;
   G.alpha = F.alphaf;
   G.sh2 = F.sh2f;
@@ -347,7 +347,7 @@ bool launch_prolong_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> 
   G.cnx = C.n[0]; G.cny = C.n[1]; G.cnz = C.n[2];
   G.per_y = C.per[1]; G.per_z = C.per[2];
   G.ntx = (F.n[0] + kTX - 1) / kTX; G.nty = (F.n[1] + kTY - 1) / kTY;
-  G.zchunk = even_chunk(F, ncomp, cx.sms, 2);
+  G.zchunk = even_chunk(F, std::max(ncomp, cx.chunk_comps), cx.sms, 2);
   G.malpha = -C.alphaf;
   dim3 grid(G.ntx * G.nty, (F.n[2] + G.zchunk - 1) / G.zchunk, ncomp);
   cx.before(VSV_KCLASS_PROLONG);
