@@ -891,18 +891,26 @@ void guess_from_history(vsv_grid* g, void* x[3], void* xp[3], void* xpp[3], floa
 vsv_status flow_solves_branched(vsv_grid* g, int fixed, int fixed_psi, int order) {
   const vsv_solver_params& s = g->sol;
   const cudaStream_t main = g->cx.stream;
+  // on every way out (errors included) the grid's stream waits for both
+  // component streams again, so nothing later overlaps their work
   struct Restore {
     vsv_grid* g;
     cudaStream_t main;
+    bool forked = false;
     ~Restore() {
       g->cx.stream = main;
       g->c0 = 0;
       g->cx.chunk_comps = 0;
+      if (forked)
+        for (int i = 0; i < 2; ++i)
+          if (cudaEventRecord(g->join_ev[i], g->aux[i]) == cudaSuccess)
+            cudaStreamWaitEvent(main, g->join_ev[i], 0);
     }
   } restore{g, main};
   g->cx.chunk_comps = 3;
   CK(cudaEventRecord(g->fork_ev, main));
   for (int i = 0; i < 2; ++i) CK(cudaStreamWaitEvent(g->aux[i], g->fork_ev, 0));
+  restore.forked = true;
   const std::vector<Level>& lvo =
       (g->flow.rho > 0.0 && !g->omega_levels.empty()) ? g->omega_levels : g->flow_levels;
   for (int c = 0; c < 3; ++c) {
@@ -924,11 +932,7 @@ vsv_status flow_solves_branched(vsv_grid* g, int fixed, int fixed_psi, int order
                   &g->last_cycles[1], &g->last_relres[1]);
     if (st != VSV_OK) return st;
   }
-  for (int i = 0; i < 2; ++i) {
-    CK(cudaEventRecord(g->join_ev[i], g->aux[i]));
-    CK(cudaStreamWaitEvent(main, g->join_ev[i], 0));
-  }
-  return VSV_OK;
+  return VSV_OK;   // joined by the guard
 }
 
 vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
