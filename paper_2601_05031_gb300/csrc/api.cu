@@ -116,6 +116,10 @@ struct vsv_grid {
   cudaStream_t aux[2] = {nullptr, nullptr};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[2] = {nullptr, nullptr};
+  // the step's first guesses, extrapolated on component stream 0 while the
+  // grid's stream runs the phase kernels: done (this step) and their event
+  bool guesses_done = false;
+  cudaEvent_t ext_ev = nullptr;
   unsigned* bar_count = nullptr;   // arrival counter of the persistent V-cycle's grid barriers
   cudaEvent_t flag_event = nullptr;
   bool flag_pending = false;
@@ -880,6 +884,22 @@ void guess_from_history(vsv_grid* g, void* x[3], void* xp[3], void* xpp[3], floa
   }
 }
 
+// Whether a step's mixed fixed-cycle solves run on the component streams:
+// fixed cycles (no norms across components), component streams wanted (2:
+// grids of at least 2^24 cells; on smaller ones the tripled launch count
+// costs more than the overlap gains: a batch of 64 grids of 0.5 M cells on
+// average ran at 859 instead of 1,456 Mcell-steps/s on streams, 1,284
+// instead of 1,359 through the graph), no single-launch lower cycle (its
+// barrier counter is shared), and no kernel class being timed by events
+// (they assume one launch at a time).
+bool solves_branched(const vsv_grid* g) {
+  const vsv_solver_params& s = g->sol;
+  const int fixed_psi = s.fixed_cycles_psi > 0 ? s.fixed_cycles_psi : s.fixed_cycles;
+  const bool streams = s.component_streams == 1 || (s.component_streams == 2 && g->N >= (1LL << 24));
+  return g->prec == VSV_MIXED && s.fixed_cycles > 0 && fixed_psi > 0 && streams &&
+         s.lower_cycle == 0 && g->cx.prof_class < 0;
+}
+
 // The fixed-cycle mixed solves with the three components on three streams:
 // component c's vorticity solve, then its stream-vector solve (whose rhs is
 // -omega'_c - s_psi,c alone), forked from the grid's stream after the source
@@ -888,7 +908,7 @@ void guess_from_history(vsv_grid* g, void* x[3], void* xp[3], void* xpp[3], floa
 // so the results are bit-identical; what changes is that one component's
 // latency-bound lower levels overlap the other components' bandwidth-bound
 // finest-level kernels.
-vsv_status flow_solves_branched(vsv_grid* g, int fixed, int fixed_psi, int order) {
+vsv_status flow_solves_branched(vsv_grid* g, int fixed, int fixed_psi, int order, bool guessed) {
   const vsv_solver_params& s = g->sol;
   const cudaStream_t main = g->cx.stream;
   // on every way out (errors included) the grid's stream waits for both
@@ -916,15 +936,18 @@ vsv_status flow_solves_branched(vsv_grid* g, int fixed, int fixed_psi, int order
   for (int c = 0; c < 3; ++c) {
     g->cx.stream = c == 0 ? main : g->aux[c - 1];
     g->c0 = c;
-    guess_from_history<float>(g, g->om, g->om_prev, g->om_prev2, g->om_lo, g->om_prev_lo,
-                              g->om_prev2_lo, order, c, 1);
+    if (guessed) CK(cudaStreamWaitEvent(g->cx.stream, g->ext_ev, 0));
+    else
+      guess_from_history<float>(g, g->om, g->om_prev, g->om_prev2, g->om_lo, g->om_prev_lo,
+                                g->om_prev2_lo, order, c, 1);
     const Rhs3<float> RO{{(const float*)g->f[c], nullptr, nullptr}, {nullptr, nullptr, nullptr}, 1.f};
     vsv_status st = solve_dc(g, lvo, cview<float>(g->om, c), cview<float>(g->om_lo, c), RO,
                              cview<float>(g->f_lo, c), 1, fixed, s.tol, s.max_cycles,
                              s.check_every, &g->last_cycles[0], &g->last_relres[0]);
     if (st != VSV_OK) return st;
-    guess_from_history<float>(g, g->ps, g->ps_prev, g->ps_prev2, g->ps_lo, g->ps_prev_lo,
-                              g->ps_prev2_lo, order, c, 1);
+    if (!guessed)
+      guess_from_history<float>(g, g->ps, g->ps_prev, g->ps_prev2, g->ps_lo, g->ps_prev_lo,
+                                g->ps_prev2_lo, order, c, 1);
     const Rhs3<float> RP{{(const float*)g->om[c], nullptr, nullptr},
                          {(const float*)g->s_ps_neg_t[c], nullptr, nullptr}, -1.f};
     st = solve_dc(g, g->flow_levels, cview<float>(g->ps, c), cview<float>(g->ps_lo, c), RP,
@@ -941,21 +964,16 @@ vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
   const int fixed_psi = (initial || !s.fixed_cycles) ? fixed
                         : (s.fixed_cycles_psi > 0 ? s.fixed_cycles_psi : s.fixed_cycles);
   const int order = std::min(s.extrapolate, g->hist);
-  // component streams: fixed cycles (no norms across components), no
-  // single-launch lower cycle (its barrier counter is shared), and no kernel
-  // class being timed by events (they assume one launch at a time)
-  // (auto, 2: grids of at least 2^24 cells; on smaller ones the tripled
-  // launch count costs more than the overlap gains: a batch of 64 grids of
-  // 0.5 M cells on average ran at 859 instead of 1,456 Mcell-steps/s on
-  // streams, 1,284 instead of 1,359 through the graph)
-  const bool streams = s.component_streams == 1 || (s.component_streams == 2 && g->N >= (1LL << 24));
-  if (!initial && fixed > 0 && fixed_psi > 0 && streams && s.lower_cycle == 0 &&
-      g->cx.prof_class < 0) {
-    const vsv_status st = flow_solves_branched(g, fixed, fixed_psi, order);
+  // the first guesses were already extrapolated early in the step
+  const bool guessed = !initial && g->guesses_done;
+  g->guesses_done = false;
+  if (!initial && solves_branched(g)) {
+    const vsv_status st = flow_solves_branched(g, fixed, fixed_psi, order, guessed);
     g->hist = std::min(g->hist + 1, 2);
     return st;
   }
-  if (!initial)
+  if (guessed) CK(cudaStreamWaitEvent(g->cx.stream, g->ext_ev, 0));
+  if (!initial && !guessed)
     guess_from_history<float>(g, g->om, g->om_prev, g->om_prev2, g->om_lo, g->om_prev_lo,
                               g->om_prev2_lo, order);
   Comp3<float> OH = comp3<float>(g->om[0], g->om[1], g->om[2]);
@@ -966,7 +984,7 @@ vsv_status flow_solves_mixed(vsv_grid* g, bool initial) {
   vsv_status st = solve_dc(g, lvo, OH, OL, rhs_omega<float>(g), FL, 3, fixed, s.tol,
                            s.max_cycles, s.check_every, &g->last_cycles[0], &g->last_relres[0]);
   if (st != VSV_OK) return st;
-  if (!initial)
+  if (!initial && !guessed)
     guess_from_history<float>(g, g->ps, g->ps_prev, g->ps_prev2, g->ps_lo, g->ps_prev_lo,
                               g->ps_prev2_lo, order);
   Comp3<float> PH = comp3<float>(g->ps[0], g->ps[1], g->ps[2]);
@@ -1034,6 +1052,7 @@ void launch_flow_source(vsv_grid* g, const PhaseParams& P) {
 template <class T>
 vsv_status step_impl(vsv_grid* g, double dt) {
   PhaseParams P = phase_params(g);
+  g->guesses_done = false;
   if (g->phase_stale) {
     refresh_phase<T>(g, 0);
     g->phase_stale = false;
@@ -1042,12 +1061,33 @@ vsv_status step_impl(vsv_grid* g, double dt) {
   T* phin = (T*)g->phi[1 - g->cur];
   Comp3<T> Pp = comp3<T>(g->ps[0], g->ps[1], g->ps[2]);
   Comp3<T> V0 = comp3<T>(g->v0t[0], g->v0t[1], g->v0t[2]);
+  // With the component streams (and no inertia, whose right-hand side reads
+  // omega'^n), the first guesses of the step's solves depend on the history
+  // alone: component stream 0 extrapolates them (bandwidth-bound) while the
+  // grid's stream runs the phi update and the phase kernels (ALU-bound).  The
+  // fork is recorded before the phi update, which reads psi'^n (the newest
+  // history word, never overwritten by a guess).
+  const bool early = std::is_same<T, float>::value && solves_branched(g) && g->flow.rho == 0.0;
+  if (early) CK(cudaEventRecord(g->fork_ev, g->cx.stream));
   // 1-3: explicit phi update with v^n = v0 + curl psi'^n and lambda_V^n
   if constexpr (std::is_same<T, float>::value)
     launch_phi_update_ff(g->cx, P, phi, g->phi_lo[g->cur], (const float*)g->mu, Pp, V0, g->S,
                          (float)dt, phin, g->phi_lo[1 - g->cur]);
   else
     launch_phi_update<T>(g->cx, P, phi, (const T*)g->mu, Pp, V0, g->S, (T)dt, phin);
+  if (early) {
+    const cudaStream_t main = g->cx.stream;
+    const int order = std::min(g->sol.extrapolate, g->hist);
+    CK(cudaStreamWaitEvent(g->aux[0], g->fork_ev, 0));
+    g->cx.stream = g->aux[0];
+    guess_from_history<T>(g, g->om, g->om_prev, g->om_prev2, g->om_lo, g->om_prev_lo,
+                          g->om_prev2_lo, order);
+    guess_from_history<T>(g, g->ps, g->ps_prev, g->ps_prev2, g->ps_lo, g->ps_prev_lo,
+                          g->ps_prev2_lo, order);
+    g->cx.stream = main;
+    CK(cudaEventRecord(g->ext_ev, g->aux[0]));
+    g->guesses_done = true;
+  }
   g->cur = 1 - g->cur;
   // moving walls: the base-flow tables of t^{n+1} for the solves
   if (g->motion_on) launch_wall_tables<T>(g->cx, wall_tables(g), dt, false, 0.0);
@@ -1470,7 +1510,8 @@ vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int prec
   bool ok = cudaMallocHost((void**)&g->flag_host, sizeof(int)) == cudaSuccess &&
             cudaHostGetDevicePointer((void**)&g->flag_dev, g->flag_host, 0) == cudaSuccess &&
             cudaEventCreateWithFlags(&g->flag_event, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->ext_ev, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; i < 2 && ok; ++i)
     ok = cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&g->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
@@ -1505,6 +1546,7 @@ vsv_status vsv_destroy(vsv_grid* g) {
     if (g->join_ev[i]) cudaEventDestroy(g->join_ev[i]);
   }
   if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+  if (g->ext_ev) cudaEventDestroy(g->ext_ev);
   for (cudaStream_t st : {g->io_in, g->io_out})
     if (st) {
       cudaStreamSynchronize(st);
