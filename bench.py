@@ -168,12 +168,12 @@ GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
 
 # DRAM traffic of the finest-level fused sweeps per cell and component:
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of each
-# variant (zero-input 6.88, plain 11.79, update 23.44 B per cell) on a
+# variant (zero-input 6.86, plain 11.78, update 23.45 B per cell) on a
 # single-component 512 x 256 x 256 solve, weighted 1:2:1 as a V(2,2)-cycle
 # launches them.  It belongs to the kernel sources whose digest is
 # FUSED_SWEEP_TRAFFIC_BUILD; with any other sources the line reports null.
-FUSED_SWEEP_TRAFFIC_PER_CELL = 13.48
-FUSED_SWEEP_TRAFFIC_BUILD = "d18dc5eddb0d2439"
+FUSED_SWEEP_TRAFFIC_PER_CELL = 13.47
+FUSED_SWEEP_TRAFFIC_BUILD = "d584d6f3619c0887"
 FUSED_SWEEP_SOURCES = ("paper_2601_05031_gb300/csrc/smooth.cu", "paper_2601_05031_gb300/csrc/tile.cuh",
                        "paper_2601_05031_gb300/csrc/common.cuh", "paper_2601_05031_gb300/csrc/internal.h")
 
