@@ -1,9 +1,12 @@
 """Schedule autotuner for the mixed path: per size class, the cheapest fixed
 multigrid schedule (V-cycles per solve, order of the first guess in time)
-whose velocity stays within a target of the converged answer, and the
-faster tiling mode for it (solver variant 0: fused and tiled kernels with
-partial edge tiles; variant 2: those kernels on tile-aligned levels only,
-per-colour and row kernels elsewhere).
+whose velocity stays within a target of the converged answer, the faster
+tiling mode for it (solver variant 0: fused and tiled kernels with partial
+edge tiles; variant 2: those kernels on tile-aligned levels only, per-colour
+and row kernels elsewhere), and the fastest launch shape (the components'
+solves on one stream or on a stream each, programmatic dependent launches
+on or off, the levels below the finest level by level or as one cooperative
+launch).
 
 A fixed schedule (``fixed_cycles`` > 0) is what batched stepping and the
 benchmark use: no host synchronisation inside a step.  How many cycles it
@@ -12,8 +15,9 @@ body, so it is measured rather than guessed: each candidate runs a few steps
 from the workload's initial state and is compared with the same steps solved
 to a relative residual of ``ref_tol`` (FP64-class on the mixed path).  The
 cheapest candidate by measured step time that stays below ``target / margin``
-wins.  The two tiling modes give bit-identical results, so they are compared
-by time alone, on the winning schedule.  Results are cached per size class (flow, free energy, and the powers of
+wins.  The tiling modes and launch shapes give bit-identical results, so
+they are compared by time alone, on the winning schedule (plain stepping:
+each candidate's step time over one vsv_step call).  Results are cached per size class (flow, free energy, and the powers of
 two nearest to the extents), so a batch of many problems tunes each class
 once.
 
@@ -32,6 +36,9 @@ from . import vsv as V
 from .sim import Simulation
 
 DEFAULT_CANDIDATES = ((2, 2), (3, 1), (3, 2), (4, 1), (4, 2), (5, 1), (6, 1))
+# launch shapes (component_streams, launch_overlap, lower_cycle); the
+# component streams are off with the cooperative lower cycle
+DEFAULT_SHAPES = ((0, 0, 0), (0, 1, 0), (1, 0, 0), (1, 1, 0), (0, 1, 1))
 
 
 @dataclass
@@ -43,6 +50,8 @@ class TunedSchedule:
     trials: list
     variant: int = 0          # tiling mode (solver variant 0 or 2)
     tiling_ms: dict = None    # ms per step of the winning schedule per tiling mode
+    shape: tuple = (2, 1, 0)  # (component_streams, launch_overlap, lower_cycle)
+    shape_ms: dict = None     # ms per step of the winning schedule and mode per shape
 
 
 _CACHE: dict = {}
@@ -79,9 +88,10 @@ def _run(w, steps, solver_setup):
 
 
 def tune(w, target=1e-6, margin=3.0, steps=6, candidates=DEFAULT_CANDIDATES, ref_tol=1e-11,
-         use_cache=True, tilings=(0, 2)) -> TunedSchedule:
+         use_cache=True, tilings=(0, 2), shapes=DEFAULT_SHAPES) -> TunedSchedule:
     """Cheapest (fixed_cycles, extrapolate) for workload ``w`` whose relative
-    L2 velocity error after ``steps`` steps is below target / margin."""
+    L2 velocity error after ``steps`` steps is below target / margin; then
+    the faster tiling mode and the fastest launch shape for it."""
     key = size_class(w)
     if use_cache and key in _CACHE:
         return _CACHE[key]
@@ -117,8 +127,23 @@ def tune(w, target=1e-6, margin=3.0, steps=6, candidates=DEFAULT_CANDIDATES, ref
             sp.variant = variant
         tiling_ms[variant] = min(_run(w, steps, tsetup)[1] for _ in range(2))
     var = min(tiling_ms, key=tiling_ms.get) if tiling_ms else 0
-    out = TunedSchedule(best[0], best[1], tiling_ms.get(var, best[2]), best[3], trials, var,
-                        tiling_ms)
+    ms = tiling_ms.get(var, best[2])
+    # launch shape on the winning schedule and tiling mode (the cooperative
+    # lower cycle exists for variant 0 only)
+    shape_ms = {}
+    for shape in shapes:
+        if shape[2] and var != 0:
+            continue
+        def ssetup(sp, shape=shape):
+            sp.fixed_cycles = best[0]
+            sp.extrapolate = best[1]
+            sp.variant = var
+            sp.component_streams, sp.launch_overlap, sp.lower_cycle = shape
+        shape_ms[shape] = min(_run(w, steps, ssetup)[1] for _ in range(2))
+    shape = min(shape_ms, key=shape_ms.get) if shape_ms else TunedSchedule.shape
+    if shape_ms:
+        ms = shape_ms[shape]
+    out = TunedSchedule(best[0], best[1], ms, best[3], trials, var, tiling_ms, shape, shape_ms)
     if use_cache:
         _CACHE[key] = out
     return out
@@ -130,4 +155,5 @@ def apply(sim, schedule: TunedSchedule):
     sp.fixed_cycles = schedule.fixed_cycles
     sp.extrapolate = schedule.extrapolate
     sp.variant = schedule.variant
+    sp.component_streams, sp.launch_overlap, sp.lower_cycle = schedule.shape
     V.vsv_set_solver(sim.g, sp)

@@ -1459,6 +1459,7 @@ void default_solver(vsv_solver_params* s, int prec) {
   s->omega_mg = kDefaultMgWeight;
   s->lower_cycle = 0;
   s->component_streams = 2;
+  s->launch_overlap = 1;
 }
 
 }  // namespace
@@ -1677,11 +1678,13 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
       sp->max_cycles < 1 || sp->fixed_cycles < 0 || sp->fixed_cycles_psi < 0 || sp->max_levels < 1 || !(sp->tol >= 0) ||
       sp->variant < 0 || sp->variant > 2 || sp->extrapolate < 0 || sp->extrapolate > 2 ||
       !(sp->omega_mg >= 0.0 && sp->omega_mg < 2.0) || sp->lower_cycle < 0 ||
-      sp->lower_cycle > 1 || sp->component_streams < 0 || sp->component_streams > 2)
+      sp->lower_cycle > 1 || sp->component_streams < 0 || sp->component_streams > 2 ||
+      sp->launch_overlap < 0 || sp->launch_overlap > 1)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
   g->cx.tiled = sp->variant != 1;
   g->cx.ragged = sp->variant == 0;
+  g->cx.overlap = sp->launch_overlap;
   if (g->flow_set) {
     const int per[3] = {1, 0, z_periodic(g) ? 1 : 0};
     g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);

@@ -114,6 +114,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// First statement of every kernel that launch_k() launches.  Under
+// programmatic stream serialisation a kernel can be scheduled while the
+// kernel before it in the stream is still running: griddepcontrol.wait
+// blocks until every prerequisite grid has completed and its memory
+// operations are visible (it returns at once for a plain launch), so nothing
+// before it may touch global memory.  launch_dependents then lets the next
+// kernel of the stream be scheduled once every CTA of this one has got here;
+// its CTAs take SM slots that this kernel's last wave leaves free and wait
+// in the same way.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Right-hand side b = beta * B[c] + S[j + k * ny] (S may be null).
 template <class T>
 struct Rhs3 {

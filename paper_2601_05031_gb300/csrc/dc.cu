@@ -55,6 +55,7 @@ __device__ __forceinline__ float defect_combine(float b1, float b2, bool has_b2,
 __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R,
                             Comp3<float> BL, Comp3<float> OUT, double* partials, float ih_hi,
                             float ih_lo) {
+  pdl_begin();
   const int comp = blockIdx.y;
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
   NbFetch H{XH.at(comp), nx, ny, nz, {L.per[0], L.per[1], L.per[2]}, {L.act[0], L.act[1], L.act[2]}};
@@ -121,6 +122,7 @@ __global__ void k_defect_dw(Level L, Comp3<float> XH, Comp3<float> XL, Rhs3<floa
 
 // (x_hi, x_lo) <- (x_hi, x_lo) + e
 __global__ void k_update_dw(Comp3<float> XH, Comp3<float> XL, Comp3<float> E, long long n) {
+  pdl_begin();
   const int comp = blockIdx.y;
   float* __restrict__ xh = XH.at(comp);
   float* __restrict__ xl = XL.at(comp);
@@ -142,6 +144,7 @@ __global__ void k_update_dw(Comp3<float> XH, Comp3<float> XL, Comp3<float> E, lo
 // low words of B and C are not read.
 __global__ void k_extrapolate_rot_dw(Comp3<float> AH, Comp3<float> AL, Comp3<float> BH,
                                      Comp3<float> CH, Comp3<float> CL, long long n, int order) {
+  pdl_begin();
   const int comp = blockIdx.y;
   const float* __restrict__ ah = AH.at(comp);
   const float* __restrict__ al = AL.at(comp);
@@ -166,6 +169,7 @@ __global__ void k_extrapolate_rot_dw(Comp3<float> AH, Comp3<float> AL, Comp3<flo
 // split into an FP32 pair (the inertial right-hand side f - s omega'^n).
 __global__ void k_axpy_dw(Comp3<float> YH, Comp3<float> YL, Comp3<float> XH, Comp3<float> XL,
                           float a_hi, float a_lo, long long n) {
+  pdl_begin();
   const int comp = blockIdx.y;
   float* __restrict__ yh = YH.at(comp);
   float* __restrict__ yl = YL.at(comp);
@@ -184,7 +188,7 @@ void launch_defect_dw(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> XL,
   const float ih_hi = (float)L.inv_h2, ih_lo = (float)(L.inv_h2 - (double)ih_hi);
   dim3 grid(nblocks, ncomp);
   cx.before(VSV_KCLASS_RESTRICT);
-  k_defect_dw<<<grid, kBlock, 0, cx.stream>>>(L, XH, XL, R, BL, OUT, partials, ih_hi, ih_lo);
+  launch_k(cx, k_defect_dw, grid, kBlock, 0, L, XH, XL, R, BL, OUT, partials, ih_hi, ih_lo);
   cx.after(VSV_KCLASS_RESTRICT, (BL.p[0] ? 20.0 : 16.0) * (double)L.cells() * ncomp);
 }
 
@@ -247,6 +251,7 @@ template <int ROWS, bool RAGGED, bool NORMS>
 __global__ void __launch_bounds__(tile::kThreads, ROWS == 1 ? 3 : 2)
 k_defect_tiled(DefGeom G, Comp3<float> XH, Comp3<float> XL, Rhs3<float> R, Comp3<float> BL,
                Comp3<float> OUT, double* partials) {
+  pdl_begin();
   using namespace tile;
   constexpr int kDR = DefShape<ROWS>::kDR, kRows = DefShape<ROWS>::kRows;
   constexpr int kDStage = DefShape<ROWS>::kStage;
@@ -437,7 +442,7 @@ int launch_defect_tiled(Ctx& cx, const Level& L, Comp3<float> XH, Comp3<float> X
   auto kern = aligned ? (partials ? k_defect_tiled<ROWS, false, true> : k_defect_tiled<ROWS, false, false>)
                       : (partials ? k_defect_tiled<ROWS, true, true> : k_defect_tiled<ROWS, true, false>);
   cx.before(VSV_KCLASS_RESTRICT);
-  kern<<<grid, tile::kThreads, Sh::kSmem, cx.stream>>>(G, XH, XL, R, BL, OUT, partials);
+  launch_k(cx, kern, grid, tile::kThreads, Sh::kSmem, G, XH, XL, R, BL, OUT, partials);
   // x_hi, x_lo, b_hi (, b_lo) read, r written
   cx.after(VSV_KCLASS_RESTRICT, (BL.p[0] ? 20.0 : 16.0) * (double)L.cells() * ncomp);
   return tiles * nz;
@@ -448,7 +453,7 @@ void launch_update_dw(Ctx& cx, Comp3<float> XH, Comp3<float> XL, Comp3<float> E,
   const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(VSV_KCLASS_PROLONG);
-  k_update_dw<<<grid, kBlock, 0, cx.stream>>>(XH, XL, E, n);
+  launch_k(cx, k_update_dw, grid, kBlock, 0, XH, XL, E, n);
   cx.after(VSV_KCLASS_PROLONG, 20.0 * (double)n * ncomp);   // x_hi, x_lo, e read; x_hi, x_lo written
 }
 
@@ -458,7 +463,7 @@ void launch_extrapolate_rot_dw(Ctx& cx, Comp3<float> AH, Comp3<float> AL, Comp3<
   const long long b = std::min<long long>((n + kBlock - 1) / kBlock, 8LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
-  k_extrapolate_rot_dw<<<grid, kBlock, 0, cx.stream>>>(AH, AL, BH, CH, CL, n, order);
+  launch_k(cx, k_extrapolate_rot_dw, grid, kBlock, 0, AH, AL, BH, CH, CL, n, order);
   // read: A's two words and the high words of B (order >= 1) and C (order
   // 2); written: the guess's two words
   cx.after(-1, (16.0 + 4.0 * (double)order) * (double)n * ncomp);
@@ -470,7 +475,7 @@ void launch_axpy_dw(Ctx& cx, Comp3<float> YH, Comp3<float> YL, Comp3<float> XH, 
   dim3 grid((unsigned)b, ncomp);
   const float a_hi = (float)a, a_lo = (float)(a - (double)a_hi);
   cx.before(-1);
-  k_axpy_dw<<<grid, kBlock, 0, cx.stream>>>(YH, YL, XH, XL, a_hi, a_lo, n);
+  launch_k(cx, k_axpy_dw, grid, kBlock, 0, YH, YL, XH, XL, a_hi, a_lo, n);
   cx.after(-1, 24.0 * (double)n * ncomp);   // y, x read, y written (two words each)
 }
 

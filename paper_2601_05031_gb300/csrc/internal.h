@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/vsv.h"
@@ -31,6 +32,10 @@ struct Ctx {
   // components (one-component launches of the component streams, which run
   // side by side, keep the chunks of the three-component launch)
   int chunk_comps = 0;
+  // launch the kernels that begin with pdl_begin() with programmatic stream
+  // serialisation (solver launch_overlap); never while events bracket a
+  // kernel class, so that those brackets time one kernel alone
+  int overlap = 1;
   std::vector<TensorMapEntry> tmaps;   // tensor maps encoded so far (fields do not move)
   long long launches = 0;
   int prof_class = -1;
@@ -66,6 +71,26 @@ struct Ctx {
     }
   }
 };
+
+// Launch of kernel `kern` on cx.stream (grid, block, dynamic shared memory,
+// arguments as for <<< >>>).  With cx.overlap the launch carries programmatic
+// stream serialisation: the kernel may be scheduled while the previous kernel
+// of the stream finishes and waits for it in pdl_begin(), which must be its
+// first statement.  Errors are left for cudaGetLastError, as with <<< >>>.
+template <class... P, class... A>
+void launch_k(const Ctx& cx, void (*kern)(P...), dim3 grid, dim3 block, size_t smem, A&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = cx.stream;
+  cfg.attrs = at;
+  cfg.numAttrs = (cx.overlap && cx.prof_class < 0) ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 // FP64 block reduction (all threads get the block total); blockDim.x must be a
 // multiple of 32 and at most 1024.

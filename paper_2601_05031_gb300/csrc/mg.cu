@@ -129,6 +129,7 @@ __device__ __forceinline__ T resid_at(const T* __restrict__ x, const Level& L, i
 // colour in its x row.
 template <class T>
 __global__ void k_rb_sweep(Level L, Comp3<T> X, Rhs3<T> R, int color, T omega, T h2) {
+  pdl_begin();
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
   int i2, j, k, comp;
   if (!cell3((nx + 1) >> 1, ny, nz, i2, j, k, comp)) return;
@@ -147,6 +148,7 @@ __global__ void k_rb_sweep(Level L, Comp3<T> X, Rhs3<T> R, int color, T omega, T
 template <class T, bool EXACT>
 __global__ void k_resid_restrict(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<T> RC, float ih_hi,
                                  float ih_lo) {
+  pdl_begin();
   int I, J, K, comp;
   if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
   const T* __restrict__ x = X.at(comp);
@@ -205,6 +207,7 @@ __device__ __forceinline__ Interp1<T> interp_axis(int i, int f, int nC, int per,
 // x_fine += P e_coarse (trilinear, cell centred).
 template <class T>
 __global__ void k_prolong_add(Level F, Level C, Comp3<T> X, Comp3<T> E) {
+  pdl_begin();
   int i, j, k, comp;
   if (!cell3(F.n[0], F.n[1], F.n[2], i, j, k, comp)) return;
   const long long t = lin(i, j, k, F.n[0], F.n[1]);
@@ -225,6 +228,7 @@ __global__ void k_prolong_add(Level F, Level C, Comp3<T> X, Comp3<T> E) {
 
 template <class T>
 __global__ void k_zero(Comp3<T> X, long long n) {
+  pdl_begin();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) X.at(blockIdx.y)[t] = (T)0;
 }
@@ -234,6 +238,7 @@ __global__ void k_zero(Comp3<T> X, long long n) {
 // x^{n-2}; extrapolation in time of order 0, 1, 2).
 template <class T>
 __global__ void k_extrapolate_rot(Comp3<T> A, Comp3<T> B, Comp3<T> C, long long n, int order) {
+  pdl_begin();
   const int comp = blockIdx.y;
   const T* __restrict__ a = A.at(comp);
   const T* __restrict__ b = B.at(comp);
@@ -250,6 +255,7 @@ __global__ void k_extrapolate_rot(Comp3<T> A, Comp3<T> B, Comp3<T> C, long long 
 // y += a x (the inertial right-hand side f - s omega'^n, FP64 path).
 template <class T>
 __global__ void k_axpy(Comp3<T> Y, Comp3<T> X, T a, long long n) {
+  pdl_begin();
   const int comp = blockIdx.y;
   T* __restrict__ y = Y.at(comp);
   const T* __restrict__ x = X.at(comp);
@@ -262,6 +268,7 @@ __global__ void k_axpy(Comp3<T> Y, Comp3<T> X, T a, long long n) {
 // shared memory by one block per component.
 template <class T>
 __global__ void k_coarse_solve(Level L, Comp3<T> E, Comp3<T> RR, int sweeps, T h2) {
+  pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   T* e = reinterpret_cast<T*>(smem_raw);
   const int comp = blockIdx.y;
@@ -296,6 +303,7 @@ __global__ void k_coarse_solve(Level L, Comp3<T> E, Comp3<T> RR, int sweeps, T h
 template <class T, bool EXACT>
 __global__ void k_resid_norm(Level L, Comp3<T> X, Rhs3<T> R, double* partials, float ih_hi,
                              float ih_lo) {
+  pdl_begin();
   const int comp = blockIdx.y;
   const T* __restrict__ x = X.at(comp);
   const int rows = L.n[1] * L.n[2];
@@ -324,6 +332,7 @@ __global__ void k_resid_norm(Level L, Comp3<T> X, Rhs3<T> R, double* partials, f
 
 // Sum the partials of k_resid_norm in a fixed order (one block per comp).
 __global__ void k_norm_finalize(const double* partials, int nblocks, Scalars* S) {
+  pdl_begin();
   const int comp = blockIdx.x;
   double rr = 0.0, bb = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -367,6 +376,7 @@ __device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
 // children of coarse x index I are fine 2I, 2I+1 (an aligned pair).
 template <class T>
 __global__ void k_restrict_block(Level F, Level C, Comp3<T> X, Rhs3<T> R, Comp3<T> RC) {
+  pdl_begin();
   int I, J, K, comp;
   if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
   const T* __restrict__ x = X.at(comp);
@@ -472,6 +482,7 @@ __device__ __forceinline__ void prolong_children(const Level& C, const T* __rest
 // x_fine += P e for the 8 children of one coarse cell per thread.
 template <class T>
 __global__ void k_prolong_block(Level F, Level C, Comp3<T> X, Comp3<T> E) {
+  pdl_begin();
   int I, J, K, comp;
   if (!cell3(C.n[0], C.n[1], C.n[2], I, J, K, comp)) return;
   T v[2][2][2];
@@ -630,6 +641,7 @@ __device__ void coarse_vcycle_cta(const CoarseCycle& CC, const T* __restrict__ r
 template <class T>
 __global__ void __launch_bounds__(1024)
 k_coarse_vcycle(const __grid_constant__ CoarseCycle CC, Comp3<T> E, Comp3<T> RR) {
+  pdl_begin();
   extern __shared__ unsigned char smem_cv[];
   const int comp = blockIdx.x;
   coarse_vcycle_cta<T>(CC, RR.at(comp), E.at(comp), reinterpret_cast<T*>(smem_cv));
@@ -644,7 +656,7 @@ bool launch_coarse_vcycle(Ctx& cx, const CoarseCycle& CC, Comp3<T> E, Comp3<T> R
                            (int)smem) != cudaSuccess)
     return false;
   cx.before(VSV_KCLASS_SMOOTH);
-  k_coarse_vcycle<T><<<ncomp, 1024, smem, cx.stream>>>(CC, E, R);
+  launch_k(cx, k_coarse_vcycle<T>, ncomp, 1024, smem, CC, E, R);
   // r of the first level read, e written; the rest stays in shared memory
   cx.after(VSV_KCLASS_SMOOTH, 2.0 * (double)sizeof(T) * (double)CC.lv[CC.first].cells() * ncomp);
   return true;
@@ -965,7 +977,7 @@ void launch_rb_sweep(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp, 
                      double omega, double h2, int kclass) {
   const dim3 grid = grid3((L.n[0] + 1) / 2, L.n[1], L.n[2], ncomp);
   cx.before(kclass);
-  k_rb_sweep<T><<<grid, block3(), 0, cx.stream>>>(L, X, R, color, (T)omega, (T)h2);
+  launch_k(cx, k_rb_sweep<T>, grid, block3(), 0, L, X, R, color, (T)omega, (T)h2);
   // one colour: the other colour's values and this colour's rhs read, this colour written
   // (and read, for SOR): 1.5 words per cell
   cx.after(kclass, (omega == 1.0 ? 1.5 : 2.0) * (double)sizeof(T) * (double)L.cells() * ncomp);
@@ -980,7 +992,7 @@ void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, 
   }
   if (!exact && blocked_transfer_ok(F, C)) {
     cx.before(VSV_KCLASS_RESTRICT);
-    k_restrict_block<T><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC);
+    launch_k(cx, k_restrict_block<T>, grid, block3(), 0, F, C, X, R, RC);
     cx.after(VSV_KCLASS_RESTRICT, 2.125 * (double)sizeof(T) * (double)F.cells() * ncomp);
     return;
   }
@@ -988,11 +1000,11 @@ void launch_resid_restrict(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, 
   float ih_hi = (float)F.inv_h2, ih_lo = (float)(F.inv_h2 - (double)ih_hi);
   if constexpr (std::is_same<T, float>::value) {
     if (exact)
-      k_resid_restrict<float, true><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
+      launch_k(cx, k_resid_restrict<float, true>, grid, block3(), 0, F, C, X, R, RC, ih_hi, ih_lo);
     else
-      k_resid_restrict<float, false><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
+      launch_k(cx, k_resid_restrict<float, false>, grid, block3(), 0, F, C, X, R, RC, ih_hi, ih_lo);
   } else {
-    k_resid_restrict<T, false><<<grid, block3(), 0, cx.stream>>>(F, C, X, R, RC, ih_hi, ih_lo);
+    launch_k(cx, k_resid_restrict<T, false>, grid, block3(), 0, F, C, X, R, RC, ih_hi, ih_lo);
   }
   cx.after(VSV_KCLASS_RESTRICT, (2.0 * (double)F.cells() + (double)C.cells()) * (double)sizeof(T) * ncomp);
 }
@@ -1004,13 +1016,13 @@ void launch_prolong_add(Ctx& cx, const Level& F, const Level& C, Comp3<T> X, Com
   }
   if (blocked_transfer_ok(F, C)) {
     cx.before(VSV_KCLASS_PROLONG);
-    k_prolong_block<T><<<grid3(C.n[0], C.n[1], C.n[2], ncomp), block3(), 0, cx.stream>>>(F, C, X, E);
+    launch_k(cx, k_prolong_block<T>, grid3(C.n[0], C.n[1], C.n[2], ncomp), block3(), 0, F, C, X, E);
     cx.after(VSV_KCLASS_PROLONG, 2.125 * (double)sizeof(T) * (double)F.cells() * ncomp);
     return;
   }
   const dim3 grid = grid3(F.n[0], F.n[1], F.n[2], ncomp);
   cx.before(VSV_KCLASS_PROLONG);
-  k_prolong_add<T><<<grid, block3(), 0, cx.stream>>>(F, C, X, E);
+  launch_k(cx, k_prolong_add<T>, grid, block3(), 0, F, C, X, E);
   cx.after(VSV_KCLASS_PROLONG, (2.0 * (double)F.cells() + (double)C.cells()) * (double)sizeof(T) * ncomp);
 }
 
@@ -1018,7 +1030,7 @@ template <class T>
 void launch_zero(Ctx& cx, Comp3<T> X, long long n, int ncomp) {
   dim3 grid(blocks_for(n), ncomp);
   cx.before(-1);
-  k_zero<T><<<grid, kBlock, 0, cx.stream>>>(X, n);
+  launch_k(cx, k_zero<T>, grid, kBlock, 0, X, n);
   cx.after(-1, (double)sizeof(T) * (double)n * ncomp);
 }
 
@@ -1028,7 +1040,7 @@ void launch_extrapolate_rot(Ctx& cx, Comp3<T> A, Comp3<T> B, Comp3<T> C, long lo
   const long long b = std::min<long long>(blocks_for(n), 4LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
-  k_extrapolate_rot<T><<<grid, kBlock, 0, cx.stream>>>(A, B, C, n, order);
+  launch_k(cx, k_extrapolate_rot<T>, grid, kBlock, 0, A, B, C, n, order);
   // the history words read (A; A, B; A, B, C), the guess written
   cx.after(-1, (double)(order + 2) * (double)sizeof(T) * (double)n * ncomp);
 }
@@ -1038,7 +1050,7 @@ void launch_axpy(Ctx& cx, Comp3<T> Y, Comp3<T> X, double a, long long n, int nco
   const long long b = std::min<long long>(blocks_for(n), 4LL * cx.sms);
   dim3 grid((unsigned)b, ncomp);
   cx.before(-1);
-  k_axpy<T><<<grid, kBlock, 0, cx.stream>>>(Y, X, (T)a, n);
+  launch_k(cx, k_axpy<T>, grid, kBlock, 0, Y, X, (T)a, n);
   cx.after(-1, 3.0 * (double)sizeof(T) * (double)n * ncomp);
 }
 
@@ -1052,7 +1064,7 @@ bool launch_coarse_solve(Ctx& cx, const Level& L, Comp3<T> E, Comp3<T> R, int nc
     cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(1, ncomp);
   cx.before(VSV_KCLASS_SMOOTH);
-  k_coarse_solve<T><<<grid, 512, smem, cx.stream>>>(L, E, R, sweeps, (T)h2);
+  launch_k(cx, k_coarse_solve<T>, grid, 512, smem, L, E, R, sweeps, (T)h2);
   cx.after(VSV_KCLASS_SMOOTH, 2.0 * (double)sizeof(T) * (double)n * ncomp);
   return true;
 }
@@ -1065,21 +1077,21 @@ void launch_resid_norm(Ctx& cx, const Level& L, Comp3<T> X, Rhs3<T> R, int ncomp
   cx.before(-1);
   if constexpr (std::is_same<T, float>::value) {
     if (exact)
-      k_resid_norm<float, true><<<grid, kBlock, 0, cx.stream>>>(L, X, R, partials, ih_hi, ih_lo);
+      launch_k(cx, k_resid_norm<float, true>, grid, kBlock, 0, L, X, R, partials, ih_hi, ih_lo);
     else
-      k_resid_norm<float, false><<<grid, kBlock, 0, cx.stream>>>(L, X, R, partials, ih_hi, ih_lo);
+      launch_k(cx, k_resid_norm<float, false>, grid, kBlock, 0, L, X, R, partials, ih_hi, ih_lo);
   } else {
-    k_resid_norm<T, false><<<grid, kBlock, 0, cx.stream>>>(L, X, R, partials, ih_hi, ih_lo);
+    launch_k(cx, k_resid_norm<T, false>, grid, kBlock, 0, L, X, R, partials, ih_hi, ih_lo);
   }
   cx.after(-1);
   cx.before(-1);
-  k_norm_finalize<<<ncomp, kBlock, 0, cx.stream>>>(partials, nblocks, S);
+  launch_k(cx, k_norm_finalize, ncomp, kBlock, 0, partials, nblocks, S);
   cx.after(-1);
 }
 
 void launch_norm_finalize(Ctx& cx, const double* partials, int nblocks, int ncomp, Scalars* S) {
   cx.before(-1);
-  k_norm_finalize<<<ncomp, kBlock, 0, cx.stream>>>(partials, nblocks, S);
+  launch_k(cx, k_norm_finalize, ncomp, kBlock, 0, partials, nblocks, S);
   cx.after(-1);
 }
 

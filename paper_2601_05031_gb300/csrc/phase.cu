@@ -165,6 +165,7 @@ __global__ void k_reduce_va(PhaseParams P, const T* __restrict__ phi, const T* _
 // lambda_V = K_V (V - V0), gamma_A = K_A (A - A0) 3 eps / (2 sqrt 2).
 __global__ void k_va_finalize(const double* partials, int nblocks, long long ncells, Scalars* S,
                               int init) {
+  pdl_begin();
   double sp = 0.0, sa = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
     sp += partials[2 * b];
@@ -994,6 +995,7 @@ __global__ void __launch_bounds__(256, 3) k_phi_update_ff4(PhaseParams P, const 
                                  const float* __restrict__ phi_lo, const float* __restrict__ mu,
                                  Comp3<float> psi, Comp3<float> v0, Scalars* S, float dt,
                                  float* __restrict__ out, float* __restrict__ out_lo) {
+  pdl_begin();
   int i0, j, k;
   if (!cell4(P, i0, j, k)) return;
   const float ih2 = (float)P.inv_h2, hih = (float)(0.5 * P.inv_h);
@@ -1029,6 +1031,7 @@ __global__ void __launch_bounds__(256, 3) k_phi_update_ff4(PhaseParams P, const 
 __global__ void __launch_bounds__(256) k_helfrich_g_ff4(PhaseParams P, const float* __restrict__ phi,
                                  const float* __restrict__ phi_lo, float* __restrict__ g,
                                  float* __restrict__ g_lo) {
+  pdl_begin();
   int i0, j, k;
   if (!cell4(P, i0, j, k)) return;
   const Geo4 G = geo4(P, i0, j, k, false);
@@ -1052,6 +1055,7 @@ __global__ void __launch_bounds__(256) k_mu_ff4(PhaseParams P, const float* __re
                                                 const float* __restrict__ g,
                                                 const float* __restrict__ g_lo, const Scalars* S,
                                                 float* __restrict__ mu, float* __restrict__ mu_lo) {
+  pdl_begin();
   int i0, j, k;
   if (!cell4(P, i0, j, k)) return;
   const Geo4 G = geo4(P, i0, j, k, false);
@@ -1094,6 +1098,7 @@ __global__ void __launch_bounds__(256) k_source_ff4(PhaseParams P, const float* 
                                                     const float* __restrict__ mu_lo,
                                                     Comp3<float> s_omega, Comp3<float> f,
                                                     Comp3<float> f_lo) {
+  pdl_begin();
   int i0, j, k;
   if (!cell4(P, i0, j, k)) return;
   const Geo4 G = geo4(P, i0, j, k, false);
@@ -1138,6 +1143,7 @@ __global__ void __launch_bounds__(256) k_source_ff4(PhaseParams P, const float* 
 __global__ void __launch_bounds__(256) k_reduce_va_ff4(PhaseParams P, const float* __restrict__ phi,
                                                        const float* __restrict__ phi_lo,
                                                        double* partials) {
+  pdl_begin();
   const int ng = P.nx >> 2;
   const int rows = P.ny * P.nz;
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -1187,8 +1193,8 @@ void launch_phi_update_ff(Ctx& cx, const PhaseParams& P, const float* phi, const
   const long long n = (long long)P.nx * P.ny * P.nz;
   cx.before(VSV_KCLASS_PHASE);
   if (use4(P))
-    k_phi_update_ff4<<<grid4(P), dim3(32, 8), 0, cx.stream>>>(P, phi, phi_lo, mu, psi, v0,
-                                                             const_cast<Scalars*>(S), dt, out, out_lo);
+    launch_k(cx, k_phi_update_ff4, grid4(P), dim3(32, 8), 0, P, phi, phi_lo, mu, psi, v0,
+             const_cast<Scalars*>(S), dt, out, out_lo);
   else
     k_phi_update_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(
         P, phi, phi_lo, mu, psi, v0, const_cast<Scalars*>(S), dt, out, out_lo);
@@ -1202,14 +1208,14 @@ void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* 
   if (P.fe_kind == VSV_HELFRICH) {
     cx.before(VSV_KCLASS_PHASE);
     if (use4(P))
-      k_helfrich_g_ff4<<<grid4(P), dim3(32, 8), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo);
+      launch_k(cx, k_helfrich_g_ff4, grid4(P), dim3(32, 8), 0, P, phi, phi_lo, g, g_lo);
     else
       k_helfrich_g_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo);
     cx.after(VSV_KCLASS_PHASE, 16.0 * (double)n);   // phi read, g written (two words each)
   }
   cx.before(VSV_KCLASS_PHASE);
   if (use4(P))
-    k_mu_ff4<<<grid4(P), dim3(32, 8), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, S, mu, mu_lo);
+    launch_k(cx, k_mu_ff4, grid4(P), dim3(32, 8), 0, P, phi, phi_lo, g, g_lo, S, mu, mu_lo);
   else
     k_mu_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, g, g_lo, S, mu,
                                                                        mu_lo);
@@ -1255,7 +1261,7 @@ void launch_source_ff(Ctx& cx, const PhaseParams& P, const float* phi, const flo
                       Comp3<float> f_lo) {
   cx.before(VSV_KCLASS_PHASE);
   if (use4(P))
-    k_source_ff4<<<grid4(P), dim3(32, 8), 0, cx.stream>>>(P, phi, phi_lo, mu, mu_lo, s_omega, f, f_lo);
+    launch_k(cx, k_source_ff4, grid4(P), dim3(32, 8), 0, P, phi, phi_lo, mu, mu_lo, s_omega, f, f_lo);
   else
     k_source_ff<<<grid3(P.nx, P.ny, P.nz, 1), block3(), 0, cx.stream>>>(P, phi, phi_lo, mu, mu_lo,
                                                                          s_omega, f, f_lo);
@@ -1304,7 +1310,7 @@ void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_
   cx.before(VSV_KCLASS_PHASE);
   if constexpr (std::is_same<T, float>::value) {
     if (use4(P))
-      k_reduce_va_ff4<<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
+      launch_k(cx, k_reduce_va_ff4, nblocks, kBlock, 0, P, phi, phi_lo, partials);
     else
       k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
   } else {
@@ -1313,8 +1319,8 @@ void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_
   // phi read (two FP32 words, or one FP64)
   cx.after(VSV_KCLASS_PHASE, 8.0 * (double)((long long)P.nx * P.ny * P.nz));
   cx.before(-1);
-  k_va_finalize<<<1, kBlock, 0, cx.stream>>>(partials, nblocks, (long long)P.nx * P.ny * P.nz, S,
-                                             init);
+  launch_k(cx, k_va_finalize, 1, kBlock, 0, partials, nblocks, (long long)P.nx * P.ny * P.nz, S,
+           init);
   cx.after(-1);
 }
 

@@ -139,6 +139,7 @@ template <bool ZERO_IN, bool HAS_S, bool UPD, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rbgs_fused(FusedGeom G, Comp3<float> A, Comp3<float> B, Rhs3<float> R, Comp3<float> XH,
              Comp3<float> XL, const __grid_constant__ FusedMaps M) {
+  pdl_begin();
   constexpr bool TMA = !RAGGED;
   extern __shared__ float4 smem_f4[];
   // boxes land on 128-byte boundaries: align the rings' base (by pointer
@@ -722,7 +723,7 @@ bool fused_maps(Ctx& cx, const Level& L, Comp3<float> A, Rhs3<float> R, int ncom
 }
 
 template <bool Z, bool HS, bool U, bool RG>
-void launch_variant(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G, Comp3<float> A,
+void launch_variant(dim3 grid, size_t smem, const Ctx& cx, const FusedGeom& G, Comp3<float> A,
                     Comp3<float> B, Rhs3<float> R, Comp3<float> XH, Comp3<float> XL,
                     const FusedMaps& M) {
   static bool attr_set = false;
@@ -733,22 +734,22 @@ void launch_variant(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G, 
                          100);
     attr_set = true;
   }
-  k_rbgs_fused<Z, HS, U, RG><<<grid, kThreads, smem, s>>>(G, A, B, R, XH, XL, M);
+  launch_k(cx, k_rbgs_fused<Z, HS, U, RG>, grid, kThreads, smem, G, A, B, R, XH, XL, M);
 }
 
 template <bool RG>
-void launch_pick(dim3 grid, size_t smem, cudaStream_t s, const FusedGeom& G, Comp3<float> A,
+void launch_pick(dim3 grid, size_t smem, const Ctx& cx, const FusedGeom& G, Comp3<float> A,
                  Comp3<float> B, Rhs3<float> R, Comp3<float> XH, Comp3<float> XL,
                  const FusedMaps& M, bool upd, bool zero_in, bool hs) {
   if (upd) {
-    if (hs) launch_variant<false, true, true, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
-    else launch_variant<false, false, true, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
+    if (hs) launch_variant<false, true, true, RG>(grid, smem, cx, G, A, B, R, XH, XL, M);
+    else launch_variant<false, false, true, RG>(grid, smem, cx, G, A, B, R, XH, XL, M);
   } else if (zero_in) {
-    if (hs) launch_variant<true, true, false, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
-    else launch_variant<true, false, false, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
+    if (hs) launch_variant<true, true, false, RG>(grid, smem, cx, G, A, B, R, XH, XL, M);
+    else launch_variant<true, false, false, RG>(grid, smem, cx, G, A, B, R, XH, XL, M);
   } else {
-    if (hs) launch_variant<false, true, false, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
-    else launch_variant<false, false, false, RG>(grid, smem, s, G, A, B, R, XH, XL, M);
+    if (hs) launch_variant<false, true, false, RG>(grid, smem, cx, G, A, B, R, XH, XL, M);
+    else launch_variant<false, false, false, RG>(grid, smem, cx, G, A, B, R, XH, XL, M);
   }
 }
 
@@ -799,8 +800,8 @@ void launch_rbgs_fused(Ctx& cx, const Level& L, Comp3<float> A, Comp3<float> B, 
   // iterate's two words read and written when updating)
   const double bpc = zero_in ? 8.0 : (upd ? 24.0 : 12.0);
   cx.before(kclass);
-  if (tma) launch_pick<false>(grid, smem, cx.stream, G, A, B, R, XH, XL, M, upd, zero_in, hs);
-  else launch_pick<true>(grid, smem, cx.stream, G, A, B, R, XH, XL, M, upd, zero_in, hs);
+  if (tma) launch_pick<false>(grid, smem, cx, G, A, B, R, XH, XL, M, upd, zero_in, hs);
+  else launch_pick<true>(grid, smem, cx, G, A, B, R, XH, XL, M, upd, zero_in, hs);
   cx.after(kclass, bpc * (double)L.cells() * ncomp);
 }
 
@@ -821,7 +822,7 @@ bool launch_copy_wait_probe(Ctx& cx, const Level& L, Comp3<float> B, Rhs3<float>
   const Comp3<float> none{{nullptr, nullptr, nullptr}};
   FusedMaps M;
   std::memset(&M, 0, sizeof M);
-  launch_pick<false>(grid, fused_sweep_smem(), cx.stream, G, none, B, R, none, none, M, false, true,
+  launch_pick<false>(grid, fused_sweep_smem(), cx, G, none, B, R, none, none, M, false, true,
                      R.S[0] != nullptr);
   return cudaPeekAtLastError() == cudaSuccess;
 }

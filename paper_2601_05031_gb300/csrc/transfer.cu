@@ -41,6 +41,7 @@ __device__ __forceinline__ float c4(const float4& v, int o) {
 template <bool HAS_S, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 3)
 k_restrict_tiled(RGeom G, Comp3<float> X, Rhs3<float> R, Comp3<float> RC) {
+  pdl_begin();
   extern __shared__ float4 smem_r4[];
   float* sX = reinterpret_cast<float*>(smem_r4);
   const int comp = blockIdx.z;
@@ -166,6 +167,7 @@ struct PGeom {
 template <bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 3)
 k_prolong_tiled(PGeom G, Comp3<float> X, Comp3<float> E) {
+  pdl_begin();
   __shared__ __align__(16) float sE[kPS * kPRows * kPW];
   const int comp = blockIdx.z;
   float* __restrict__ x = X.at(comp);
@@ -328,11 +330,11 @@ bool launch_restrict_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float>
   dim3 grid(G.ntx * G.nty, (F.n[2] + G.zchunk - 1) / G.zchunk, ncomp);
   cx.before(VSV_KCLASS_RESTRICT);
   if (R.S[0]) {
-    if (rg) k_restrict_tiled<true, true><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
-    else k_restrict_tiled<true, false><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
+    if (rg) launch_k(cx, k_restrict_tiled<true, true>, grid, kThreads, smem, G, X, R, RC);
+    else launch_k(cx, k_restrict_tiled<true, false>, grid, kThreads, smem, G, X, R, RC);
   } else {
-    if (rg) k_restrict_tiled<false, true><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
-    else k_restrict_tiled<false, false><<<grid, kThreads, smem, cx.stream>>>(G, X, R, RC);
+    if (rg) launch_k(cx, k_restrict_tiled<false, true>, grid, kThreads, smem, G, X, R, RC);
+    else launch_k(cx, k_restrict_tiled<false, false>, grid, kThreads, smem, G, X, R, RC);
   }
   cx.after(VSV_KCLASS_RESTRICT, 8.5 * (double)F.cells() * ncomp);   // e, b read; r_c written
   return true;
@@ -351,8 +353,8 @@ bool launch_prolong_tiled(Ctx& cx, const Level& F, const Level& C, Comp3<float> 
   G.malpha = -C.alphaf;
   dim3 grid(G.ntx * G.nty, (F.n[2] + G.zchunk - 1) / G.zchunk, ncomp);
   cx.before(VSV_KCLASS_PROLONG);
-  if (rg) k_prolong_tiled<true><<<grid, kThreads, 0, cx.stream>>>(G, X, E);
-  else k_prolong_tiled<false><<<grid, kThreads, 0, cx.stream>>>(G, X, E);
+  if (rg) launch_k(cx, k_prolong_tiled<true>, grid, kThreads, 0, G, X, E);
+  else launch_k(cx, k_prolong_tiled<false>, grid, kThreads, 0, G, X, E);
   cx.after(VSV_KCLASS_PROLONG, 8.5 * (double)F.cells() * ncomp);   // e read and written, e_c read
   return true;
 }

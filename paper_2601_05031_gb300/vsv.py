@@ -54,7 +54,8 @@ class vsv_solver_params(C.Structure):
                 ("nu2", C.c_int), ("max_levels", C.c_int), ("coarse_sweeps", C.c_int),
                 ("omega_sor", C.c_double), ("variant", C.c_int), ("extrapolate", C.c_int),
                 ("fixed_cycles_psi", C.c_int), ("omega_mg", C.c_double),
-                ("lower_cycle", C.c_int), ("component_streams", C.c_int)]
+                ("lower_cycle", C.c_int), ("component_streams", C.c_int),
+                ("launch_overlap", C.c_int)]
 
 
 class vsv_bc(C.Structure):

@@ -92,8 +92,22 @@ def test_autotune_picks_cheapest_schedule_meeting_target(V):
     best = min(ok, key=lambda t: t["ms_per_step"])
     assert (s.fixed_cycles, s.extrapolate) == (best["fixed_cycles"], best["extrapolate"])
     # the tiling mode is the faster of the two timed on that schedule
-    assert set(s.tiling_ms) == {0, 2} and s.ms_per_step == min(s.tiling_ms.values())
-    assert s.tiling_ms[s.variant] == s.ms_per_step
+    assert set(s.tiling_ms) == {0, 2} and s.tiling_ms[s.variant] == min(s.tiling_ms.values())
+    # the launch shape is the fastest timed on that schedule and mode; the
+    # cooperative lower cycle is a candidate on variant 0 only
+    shapes = set(autotune.DEFAULT_SHAPES)
+    if s.variant != 0:
+        shapes = {t for t in shapes if not t[2]}
+    assert set(s.shape_ms) == shapes
+    assert s.ms_per_step == s.shape_ms[s.shape] == min(s.shape_ms.values())
+    # applied to a simulation, the tuned schedule is what its solver runs
+    from paper_2601_05031_gb300.sim import Simulation
+    sim = Simulation.from_workload(w, V.VSV_MIXED)
+    autotune.apply(sim, s)
+    sim.set_phi(w.phi0)
+    sim.step(2, w.dt)
+    assert V.vsv_check(sim.g, check=False) == V.VSV_OK
+    sim.close()
     # errors shrink with more cycles
     errs = [t["vel_err"] for t in s.trials]
     assert errs[0] > errs[-1]

@@ -582,6 +582,57 @@ def test_component_streams_bit_identical(V, kind):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind,prec,cs", [("couette", "mixed", 0), ("couette", "mixed", 1),
+                                          ("duct", "mixed", 1), ("couette", "fp64", 0)])
+def test_launch_overlap_bit_identical(V, kind, prec, cs):
+    """Steps whose solver and phase-field kernels are launched with
+    programmatic stream serialisation (launch_overlap 1: each kernel waits
+    for its predecessor inside the kernel) give the bits of plain launches,
+    over plain steps and over replays of a captured graph, with and without
+    the component streams; and a converged standalone solve (residual-norm
+    kernels, host reads between cycles) gives the same iterate.  A value
+    outside 0..1 is refused."""
+    import torch
+    from paper_2601_05031_gb300.sim import Batch, Simulation
+    flow = inputs.POISEUILLE_DUCT if kind == "duct" else inputs.COUETTE
+    w = inputs.vesicle(256, 32, 32, flow, 0.85, 1.0, dt=1e-4, b_range=(0.25, 0.3))
+    p = V.VSV_MIXED if prec == "mixed" else V.VSV_FP64
+    rng = np.random.default_rng(11)
+    rhs = rng.standard_normal((w.nz, w.ny, w.nx))
+    res = []
+    for ov in (0, 1):
+        sim = Simulation.from_workload(w, p, stream=torch.cuda.Stream())
+        sp = sim.solver_params()
+        assert sp.launch_overlap == 1   # the default
+        sp.fixed_cycles = 2
+        sp.extrapolate = 2
+        sp.component_streams = cs
+        sp.launch_overlap = ov
+        V.vsv_set_solver(sim.g, sp)
+        sim.set_phi(w.phi0)
+        sim.step(3, w.dt)
+        b = Batch([sim])
+        b.step(6, w.dt)
+        b.close()
+        assert V.vsv_check(sim.g, check=False) == V.VSV_OK
+        fields = ([sim.field(V.VSV_FIELD_PHI), sim.field(V.VSV_FIELD_MU)] +
+                  [sim.field(V.VSV_FIELD_VEL_X + c) for c in range(3)] +
+                  [sim.field(V.VSV_FIELD_PSI_PERT_X + c) for c in range(3)])
+        # the standalone solve takes over the grid's workspace (no state after it)
+        x, cyc, rr, st = sim.solve_poisson(rhs, periodic=(True, False, True), tol=1e-9)
+        assert st == V.VSV_OK and rr <= 1e-9
+        res.append(fields + [x, cyc])
+        if ov == 1:
+            sp.launch_overlap = 2
+            with pytest.raises(V.VsvError) as e:
+                V.vsv_set_solver(sim.g, sp)
+            assert e.value.status == V.VSV_EINVAL
+        sim.close()
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
 def test_async_host_transfers_of_phi(V):
     """VSV_HOST_ASYNC: FP64 phi set from and read into page-locked host
     memory on the grid's copy streams gives the bits of the synchronous
