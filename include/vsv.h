@@ -225,16 +225,20 @@ typedef struct {
                              costs more than the overlap gains).  Off while
                              a kernel class is being profiled or with
                              lower_cycle = 1.  Outside 0..2: VSV_EINVAL. */
-  int launch_overlap;     /* 1 (default): the step's solver and phase-field
-                             kernels are launched with programmatic stream
+  int launch_overlap;     /* 1: the step's solver and phase-field kernels
+                             are launched with programmatic stream
                              serialisation, so that each is scheduled onto
                              the SMs while the kernel before it in its
                              stream drains and starts work the moment that
                              kernel has completed (it waits for it before
                              its first memory access); 0: plain launches.
-                             Bit-identical results.  Plain launches while a
-                             kernel class is being profiled.  Outside 0..1:
-                             VSV_EINVAL. */
+                             2 (default): 1 on grids of at least 2^24
+                             cells, else 0 (small grids usually run many
+                             side by side, where the waiting kernels hold
+                             SM slots that the other grids' kernels would
+                             use).  Bit-identical results.  Plain launches
+                             while a kernel class is being profiled.
+                             Outside 0..2: VSV_EINVAL. */
 } vsv_solver_params;
 
 /* Per-axis boundary of a standalone Poisson problem: periodic (1) or zero

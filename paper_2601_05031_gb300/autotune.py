@@ -17,7 +17,10 @@ to a relative residual of ``ref_tol`` (FP64-class on the mixed path).  The
 cheapest candidate by measured step time that stays below ``target / margin``
 wins.  The tiling modes and launch shapes give bit-identical results, so
 they are compared by time alone, on the winning schedule (plain stepping:
-each candidate's step time over one vsv_step call).  Results are cached per size class (flow, free energy, and the powers of
+each candidate's step time over one vsv_step call, the grid alone on the
+GPU).  Many small grids stepped side by side favour other shapes than one
+grid alone (the library's size-based defaults); pass ``shapes=()`` to keep
+those for a batch.  Results are cached per size class (flow, free energy, and the powers of
 two nearest to the extents), so a batch of many problems tunes each class
 once.
 
@@ -50,7 +53,7 @@ class TunedSchedule:
     trials: list
     variant: int = 0          # tiling mode (solver variant 0 or 2)
     tiling_ms: dict = None    # ms per step of the winning schedule per tiling mode
-    shape: tuple = (2, 1, 0)  # (component_streams, launch_overlap, lower_cycle)
+    shape: tuple = (2, 2, 0)  # (component_streams, launch_overlap, lower_cycle)
     shape_ms: dict = None     # ms per step of the winning schedule and mode per shape
 
 

@@ -1442,6 +1442,14 @@ vsv_status build_base_flow(vsv_grid* g) {
   return VSV_OK;
 }
 
+// Programmatic dependent launches for this grid (solver launch_overlap; 2:
+// on grids of at least 2^24 cells).  Small grids usually run many at a time
+// on their own streams, where the CTAs that wait for their predecessor hold
+// SM slots the other streams' kernels would use: measured slower there.
+bool overlap_on(const vsv_grid* g) {
+  return g->sol.launch_overlap == 1 || (g->sol.launch_overlap == 2 && g->N >= (1LL << 24));
+}
+
 void default_solver(vsv_solver_params* s, int prec) {
   s->kind = VSV_SOLVER_MG;
   s->tol = prec == VSV_FP64 ? 1e-12 : 1e-10;
@@ -1459,7 +1467,7 @@ void default_solver(vsv_solver_params* s, int prec) {
   s->omega_mg = kDefaultMgWeight;
   s->lower_cycle = 0;
   s->component_streams = 2;
-  s->launch_overlap = 1;
+  s->launch_overlap = 2;
 }
 
 }  // namespace
@@ -1502,6 +1510,7 @@ vsv_status vsv_create(vsv_grid** out, int nx, int ny, int nz, double h, int prec
   g->flow = vsv_flow_params{VSV_QUIESCENT, 0.0, 0.0, 0.0, 1.0, 0.0};
   g->fe = vsv_fe_params{VSV_CAHN_HILLIARD, 1.0, 0.0, 1.0, 1.0, 0.0, 0.0, 0};
   default_solver(&g->sol, precision);
+  g->cx.overlap = overlap_on(g);
   if (cudaMemsetAsync(g->S, 0, sizeof(Scalars), g->cx.stream) != cudaSuccess) {
     delete g;
     return VSV_ECUDA;
@@ -1679,12 +1688,12 @@ vsv_status vsv_set_solver(vsv_grid* g, const vsv_solver_params* sp) {
       sp->variant < 0 || sp->variant > 2 || sp->extrapolate < 0 || sp->extrapolate > 2 ||
       !(sp->omega_mg >= 0.0 && sp->omega_mg < 2.0) || sp->lower_cycle < 0 ||
       sp->lower_cycle > 1 || sp->component_streams < 0 || sp->component_streams > 2 ||
-      sp->launch_overlap < 0 || sp->launch_overlap > 1)
+      sp->launch_overlap < 0 || sp->launch_overlap > 2)
     return fail(g, VSV_EINVAL, "invalid solver parameters%s");
   g->sol = *sp;
   g->cx.tiled = sp->variant != 1;
   g->cx.ragged = sp->variant == 0;
-  g->cx.overlap = sp->launch_overlap;
+  g->cx.overlap = overlap_on(g);
   if (g->flow_set) {
     const int per[3] = {1, 0, z_periodic(g) ? 1 : 0};
     g->flow_levels = build_levels(g->nx, g->ny, g->nz, g->h, per, g->sol.max_levels, g->mg_nlev_cap);

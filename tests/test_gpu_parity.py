@@ -592,7 +592,7 @@ def test_launch_overlap_bit_identical(V, kind, prec, cs):
     over plain steps and over replays of a captured graph, with and without
     the component streams; and a converged standalone solve (residual-norm
     kernels, host reads between cycles) gives the same iterate.  A value
-    outside 0..1 is refused."""
+    outside 0..2 is refused."""
     import torch
     from paper_2601_05031_gb300.sim import Batch, Simulation
     flow = inputs.POISEUILLE_DUCT if kind == "duct" else inputs.COUETTE
@@ -604,7 +604,7 @@ def test_launch_overlap_bit_identical(V, kind, prec, cs):
     for ov in (0, 1):
         sim = Simulation.from_workload(w, p, stream=torch.cuda.Stream())
         sp = sim.solver_params()
-        assert sp.launch_overlap == 1   # the default
+        assert sp.launch_overlap == 2   # the default: by grid size
         sp.fixed_cycles = 2
         sp.extrapolate = 2
         sp.component_streams = cs
@@ -624,7 +624,7 @@ def test_launch_overlap_bit_identical(V, kind, prec, cs):
         assert st == V.VSV_OK and rr <= 1e-9
         res.append(fields + [x, cyc])
         if ov == 1:
-            sp.launch_overlap = 2
+            sp.launch_overlap = 3
             with pytest.raises(V.VsvError) as e:
                 V.vsv_set_solver(sim.g, sp)
             assert e.value.status == V.VSV_EINVAL
