@@ -513,16 +513,41 @@ __host__ __device__ bool blocked_transfer_ok(const Level& F, const Level& C) {
 // V-cycle there (same operations as the level-by-level kernels: red-black
 // sweeps, residual restricted by averaging, trilinear prolongation), which
 // replaces dozens of latency-bound launches per V-cycle by one.
+
+// q = a / d, with rem = a - q d (0 <= a, 0 < d): a shift and a mask where d
+// is a power of two (every level of a power-of-two grid), else a division.
+__device__ __forceinline__ int cv_divmod(int a, int d, int& rem) {
+  if ((d & (d - 1)) == 0) {
+    rem = a & (d - 1);
+    return a >> (__ffs(d) - 1);
+  }
+  const int q = a / d;
+  rem = a - q * d;
+  return q;
+}
+
 // The thread's cells of one colour are visited with the index (i2, j, k)
 // advanced by the block size incrementally (adds and carries instead of two
-// integer divisions per cell).
+// integer divisions per cell).  The neighbour sum, the wall count and the
+// update are those of sum_nb and the per-colour sweep (same operands, same
+// order of the additions), with 32-bit offsets into shared memory, and with
+// the level's geometry and the weights omega rc (one per count of wall
+// neighbours, in shared memory) formed once per call instead of per cell.
 template <class T>
 __device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2, T omega) {
-  const int nx = L.n[0], ny = L.n[1], nxh = (nx + 1) >> 1;
-  const int nh = nxh * ny * L.n[2];   // cells of one colour, rounded up per row
+  __shared__ T wtab[8];
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2], nxh = (nx + 1) >> 1;
+  const int sz = nx * ny;
+  const int nh = nxh * ny * nz;   // cells of one colour, rounded up per row
+  const bool ax = L.act[0], ay = L.act[1], az = L.act[2];
+  const bool px = L.per[0], py = L.per[1], pz = L.per[2];
+  const T c1 = (T)1 - omega;
   const int B = blockDim.x;
-  const int Bi = B % nxh, Bq = B / nxh, Bj = Bq % ny, Bk = Bq / ny;
-  const int i20 = threadIdx.x % nxh, q0 = threadIdx.x / nxh, j0 = q0 % ny, k0 = q0 / ny;
+  int Bi, Bj, i20, j0;
+  const int Bk = cv_divmod(cv_divmod(B, nxh, Bi), ny, Bj);
+  const int k0 = cv_divmod(cv_divmod((int)threadIdx.x, nxh, i20), ny, j0);
+  if (threadIdx.x < 7) wtab[threadIdx.x] = wscale(omega, lv_rc<T>(L, (int)threadIdx.x));
+  __syncthreads();
   for (int s = 0; s < sweeps; ++s)
     for (int color = 0; color < 2; ++color) {
       int i2 = i20, j = j0, k = k0;
@@ -539,10 +564,26 @@ __device__ void cv_sweep(const Level& L, T* e, const T* r, int sweeps, T h2, T o
         const int i = 2 * i2 + ((j + k + color) & 1);
         if (i >= nx) continue;
         const int t = (k * ny + j) * nx + i;
-        int nwall;
-        const T sum = sum_nb(e, L, i, j, k, t, nwall);
-        e[t] = relax(e[t], nb_term(sum, r[t], h2), wscale(omega, lv_rc<T>(L, nwall)),
-                     (T)1 - omega);
+        int nwall = 0;
+        T a = 0, b = 0;
+        if (ax) {
+          if (i > 0) a = e[t - 1]; else if (px) a = e[t + nx - 1]; else ++nwall;
+          if (i < nx - 1) b = e[t + 1]; else if (px) b = e[t - (nx - 1)]; else ++nwall;
+        }
+        const T s0 = a + b;
+        a = 0; b = 0;
+        if (ay) {
+          if (j > 0) a = e[t - nx]; else if (py) a = e[t + (ny - 1) * nx]; else ++nwall;
+          if (j < ny - 1) b = e[t + nx]; else if (py) b = e[t - (ny - 1) * nx]; else ++nwall;
+        }
+        const T s1 = a + b;
+        a = 0; b = 0;
+        if (az) {
+          if (k > 0) a = e[t - sz]; else if (pz) a = e[t + (nz - 1) * sz]; else ++nwall;
+          if (k < nz - 1) b = e[t + sz]; else if (pz) b = e[t - (nz - 1) * sz]; else ++nwall;
+        }
+        const T s2 = a + b;
+        e[t] = relax(e[t], nb_term((s0 + s1) + s2, r[t], h2), wtab[nwall], c1);
       }
       __syncthreads();
     }
@@ -553,8 +594,8 @@ __device__ void cv_restrict(const Level& F, const Level& C, const T* e, const T*
   const int nc = (int)C.cells();
   const int fx = F.n[0] / C.n[0], fy = F.n[1] / C.n[1], fz = F.n[2] / C.n[2];
   for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-    const int I = t % C.n[0], q = t / C.n[0];
-    const int J = q % C.n[1], K = q / C.n[1];
+    int I, J;
+    const int K = cv_divmod(cv_divmod(t, C.n[0], I), C.n[1], J);
     T acc = 0;
     for (int dk = 0; dk < fz; ++dk)
       for (int dj = 0; dj < fy; ++dj)
@@ -573,8 +614,8 @@ __device__ void cv_prolong(const Level& F, const Level& C, T* e, const T* ec) {
   if (blocked_transfer_ok(F, C)) {   // as k_prolong_block
     const int nc = (int)C.cells();
     for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-      const int I = t % C.n[0], q = t / C.n[0];
-      const int J = q % C.n[1], K = q / C.n[1];
+      int I, J;
+      const int K = cv_divmod(cv_divmod(t, C.n[0], I), C.n[1], J);
       T v[2][2][2];
       prolong_children<T>(C, ec, I, J, K, v);
       for (int c = 0; c < 2; ++c)
