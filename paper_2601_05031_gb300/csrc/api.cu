@@ -1028,8 +1028,13 @@ void refresh_phase(vsv_grid* g, int init) {
   T* phi = (T*)g->phi[g->cur];
   if constexpr (std::is_same<T, float>::value) {
     const float* lo = g->phi_lo[g->cur];
-    launch_reduce_va<float>(g->cx, P, phi, lo, g->partials, g->red_blocks, g->S, init);
-    launch_mu_ff(g->cx, P, phi, lo, (float*)g->g, g->g_lo, (float*)g->mu, g->mu_lo, g->S);
+    // Helfrich: g from the reduction's pass over phi (variant 1: the
+    // separate kernel, same values)
+    const bool fuse_g = P.fe_kind == VSV_HELFRICH && g->sol.variant != 1;
+    const bool g_ready =
+        launch_reduce_va<float>(g->cx, P, phi, lo, g->partials, g->red_blocks, g->S, init,
+                                fuse_g ? (float*)g->g : nullptr, fuse_g ? g->g_lo : nullptr);
+    launch_mu_ff(g->cx, P, phi, lo, (float*)g->g, g->g_lo, (float*)g->mu, g->mu_lo, g->S, g_ready);
   } else {
     launch_reduce_va<T>(g->cx, P, phi, nullptr, g->partials, g->red_blocks, g->S, init);
     launch_mu<T>(g->cx, P, phi, (T*)g->g, (T*)g->mu, g->S);

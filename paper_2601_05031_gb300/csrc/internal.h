@@ -270,16 +270,21 @@ struct PhaseParams {
 template <class T>
 void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu, Comp3<T> psi,
                        Comp3<T> v0, const Scalars* S, T dt, T* phi_out);
+// V, A (and the multipliers) of phi into S.  On the mixed path with g and
+// g_lo given and x extents in 4-cell groups, the same pass also stores the
+// Helfrich g of phi there; returns whether it did.
 template <class T>
-void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo,
-                      double* partials, int nblocks, Scalars* S, int init);
+bool launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo,
+                      double* partials, int nblocks, Scalars* S, int init, float* g = nullptr,
+                      float* g_lo = nullptr);
 // Mixed path: phi carried as FP32 pairs (hi, lo); mu and g computed with
 // double-word FP32 arithmetic, mu rounded to FP32.
 void launch_phi_update_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo,
                           const float* mu, Comp3<float> psi, Comp3<float> v0, const Scalars* S,
                           float dt, float* out, float* out_lo);
+// g_ready: the Helfrich g of phi is already in g, g_lo (launch_reduce_va)
 void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo, float* g,
-                  float* g_lo, float* mu, float* mu_lo, const Scalars* S);
+                  float* g_lo, float* mu, float* mu_lo, const Scalars* S, bool g_ready = false);
 void launch_source_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo,
                       const float* mu, const float* mu_lo, Comp3<float> s_omega, Comp3<float> f,
                       Comp3<float> f_lo);

@@ -1139,10 +1139,14 @@ __global__ void __launch_bounds__(256) k_source_ff4(PhaseParams P, const float* 
 // Partial sums of sum(phi) and of the area density over 4-cell groups; one
 // (phi, area) pair per block, as k_reduce_va.  Each warp takes whole x rows
 // (row index and plane from one 32-bit division per row), its lanes the
-// rows' 4-cell groups.
+// rows' 4-cell groups.  WITH_G: the Helfrich g of the same cells is formed
+// from the same staged stencil and stored as k_helfrich_g_ff4 stores it
+// (same operations, same values), saving that kernel's pass over phi.
+template <bool WITH_G>
 __global__ void __launch_bounds__(256) k_reduce_va_ff4(PhaseParams P, const float* __restrict__ phi,
                                                        const float* __restrict__ phi_lo,
-                                                       double* partials) {
+                                                       double* partials, float* __restrict__ g,
+                                                       float* __restrict__ g_lo) {
   pdl_begin();
   const int ng = P.nx >> 2;
   const int rows = P.ny * P.nz;
@@ -1154,6 +1158,7 @@ __global__ void __launch_bounds__(256) k_reduce_va_ff4(PhaseParams P, const floa
     const int k = row / P.ny, j = row - k * P.ny;
     const Geo4 G = geo4(P, 4 * gi, j, k, false);
     const St4 H = load4(phi, G), L = load4(phi_lo, G);
+    float oh[4], ol[4];
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
       const FF f{e4(H.c, o), e4(L.c, o)};
@@ -1170,6 +1175,18 @@ __global__ void __launch_bounds__(256) k_reduce_va_ff4(PhaseParams P, const floa
       cp.add(f.lo);
       ca.add(dens.hi);
       ca.add(dens.lo);
+      if constexpr (WITH_G) {
+        // g = phi (phi^2 - 1) - eps^2 lap phi, as k_helfrich_g_ff4 (w is its
+        // phi^2 - 1)
+        const FF r = ff_add(ff_mul(f, w),
+                            ff_neg(ff_mul(lap7_ff4(H, L, o), FF{P.e2ih_hi, P.e2ih_lo})));
+        oh[o] = r.hi;
+        ol[o] = r.lo;
+      }
+    }
+    if constexpr (WITH_G) {
+      *reinterpret_cast<float4*>(g + G.rc + 4 * gi) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+      *reinterpret_cast<float4*>(g_lo + G.rc + 4 * gi) = make_float4(ol[0], ol[1], ol[2], ol[3]);
     }
   }
   double sphi = (double)cp.hi + (double)cp.lo;
@@ -1203,9 +1220,9 @@ void launch_phi_update_ff(Ctx& cx, const PhaseParams& P, const float* phi, const
 }
 
 void launch_mu_ff(Ctx& cx, const PhaseParams& P, const float* phi, const float* phi_lo, float* g,
-                  float* g_lo, float* mu, float* mu_lo, const Scalars* S) {
+                  float* g_lo, float* mu, float* mu_lo, const Scalars* S, bool g_ready) {
   const long long n = (long long)P.nx * P.ny * P.nz;
-  if (P.fe_kind == VSV_HELFRICH) {
+  if (P.fe_kind == VSV_HELFRICH && !g_ready) {
     cx.before(VSV_KCLASS_PHASE);
     if (use4(P))
       launch_k(cx, k_helfrich_g_ff4, grid4(P), dim3(32, 8), 0, P, phi, phi_lo, g, g_lo);
@@ -1305,23 +1322,31 @@ void launch_phi_update(Ctx& cx, const PhaseParams& P, const T* phi, const T* mu,
 }
 
 template <class T>
-void launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo,
-                      double* partials, int nblocks, Scalars* S, int init) {
+bool launch_reduce_va(Ctx& cx, const PhaseParams& P, const T* phi, const T* phi_lo,
+                      double* partials, int nblocks, Scalars* S, int init, float* g, float* g_lo) {
+  bool with_g = false;
   cx.before(VSV_KCLASS_PHASE);
   if constexpr (std::is_same<T, float>::value) {
-    if (use4(P))
-      launch_k(cx, k_reduce_va_ff4, nblocks, kBlock, 0, P, phi, phi_lo, partials);
-    else
+    if (use4(P)) {
+      with_g = g && g_lo;
+      if (with_g)
+        launch_k(cx, k_reduce_va_ff4<true>, nblocks, kBlock, 0, P, phi, phi_lo, partials, g, g_lo);
+      else
+        launch_k(cx, k_reduce_va_ff4<false>, nblocks, kBlock, 0, P, phi, phi_lo, partials,
+                 (float*)nullptr, (float*)nullptr);
+    } else {
       k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
+    }
   } else {
     k_reduce_va<T><<<nblocks, kBlock, 0, cx.stream>>>(P, phi, phi_lo, partials);
   }
-  // phi read (two FP32 words, or one FP64)
-  cx.after(VSV_KCLASS_PHASE, 8.0 * (double)((long long)P.nx * P.ny * P.nz));
+  // phi read (two FP32 words, or one FP64); g written (two words)
+  cx.after(VSV_KCLASS_PHASE, (with_g ? 16.0 : 8.0) * (double)((long long)P.nx * P.ny * P.nz));
   cx.before(-1);
   launch_k(cx, k_va_finalize, 1, kBlock, 0, partials, nblocks, (long long)P.nx * P.ny * P.nz, S,
            init);
   cx.after(-1);
+  return with_g;
 }
 
 template <class T>
@@ -1456,8 +1481,8 @@ void launch_fill(Ctx& cx, double* x, long long n, double v) {
 #define VSV_INST(T)                                                                               \
   template void launch_phi_update<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>,      \
                                      Comp3<T>, const Scalars*, T, T*);                            \
-  template void launch_reduce_va<T>(Ctx&, const PhaseParams&, const T*, const T*, double*, int,   \
-                                    Scalars*, int);                                               \
+  template bool launch_reduce_va<T>(Ctx&, const PhaseParams&, const T*, const T*, double*, int,   \
+                                    Scalars*, int, float*, float*);                               \
   template void launch_mu<T>(Ctx&, const PhaseParams&, const T*, T*, T*, const Scalars*);         \
   template void launch_source<T>(Ctx&, const PhaseParams&, const T*, const T*, Comp3<T>,          \
                                  Comp3<T>);                                                       \
