@@ -101,3 +101,21 @@ def test_binding_structs_match_header_sizes(V):
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         names = re.findall(r"\b([a-z_0-9]+)\s*(?:\[\d+\])?\s*[;,]", body)
         assert [n for n, _ in pyt._fields_] == names, cname
+
+
+def test_solver_defaults_and_autotune_launch_shapes(V):
+    """The library's size-based launch defaults (component streams and
+    programmatic dependent launches: 2, by grid size; level-by-level lower
+    cycle) are the autotuner's untuned shape, and every candidate shape is
+    one the solver accepts (the cooperative lower cycle without the
+    component streams), with both launch-overlap settings among them."""
+    from paper_2601_05031_gb300 import autotune
+    p = V.vsv_default_solver(V.VSV_MIXED)
+    assert (p.component_streams, p.launch_overlap, p.lower_cycle) == (2, 2, 0)
+    assert autotune.TunedSchedule(2, 2, 0.0, 0.0, []).shape == (2, 2, 0)
+    shapes = autotune.DEFAULT_SHAPES
+    assert len(set(shapes)) == len(shapes)
+    for cs, ov, lc in shapes:
+        assert cs in (0, 1) and ov in (0, 1) and lc in (0, 1)
+        assert not (lc and cs)
+    assert {ov for _, ov, _ in shapes} == {0, 1}
